@@ -1,0 +1,166 @@
+"""Pins of the oracle's PIBM coupling (Eqs lbm5-lbm13) against closed forms,
+kernel identities and exact momentum / heat exchange between fluid and particles."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+
+def test_delta_h_partition_of_unity():
+    # Eq lbm12: the four cosines cancel, so sum_k delta_h(x - k) = 1 for every x
+    gen = np.random.default_rng(0)
+    for x in gen.random(50) * 10 - 5:
+        s = sum(oracle.delta_h(x - k) for k in range(int(np.floor(x)) - 3, int(np.floor(x)) + 4))
+        assert abs(s - 1.0) < 1e-15
+    assert oracle.delta_h(0.0) == 0.5
+    assert oracle.delta_h(1.0) == 0.25 and oracle.delta_h(-1.0) == 0.25
+    assert oracle.delta_h(2.0) < 1e-16 and oracle.delta_h(2.5) == 0.0
+
+
+def test_lagrange_weights_reproduce_cubics():
+    # Eq lbm6 with four points reproduces polynomials up to degree 3 exactly
+    gen = np.random.default_rng(1)
+    for x in gen.random(20) * 20 + 2:
+        base, w = oracle.lagrange_weights(x, 4)
+        nodes = base + np.arange(4)
+        for p in (lambda t: 1.0 + 0 * t, lambda t: t, lambda t: t ** 2 - 3 * t, lambda t: t ** 3):
+            assert abs(np.dot(w, p(nodes)) - p(x)) < 1e-10 * max(1.0, abs(p(x)))
+    base, w = oracle.lagrange_weights(7.0, 4)
+    assert base == 6 and np.allclose(w, [0, 1, 0, 0], atol=0)
+
+
+def _quiet_case(shape=(24, 24, 1), dim=2):
+    case = W.periodic_box(shape=shape, dim=dim, buoyancy=False)
+    case["walls"] = [(1, 1, 0.0)] * (2 * dim)
+    case["T_init"] = 0.3
+    case["contact"] = W.spring_dashpot()
+    case["pibm"] = True
+    return case
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_single_node_point_closed_form(dim):
+    # A particle of radius 1/2 centred on a node covers exactly that node with
+    # eps = 1.  In fluid at rest (rho = 1, j = 0, T = 0.3), Eq lbm7 + lbm8 give
+    # F_f = 2 rho U and Eq lbm7.5 gives Q = 2 (T_p - T); the particle receives
+    # -F_f (Eq lbm13) and the fluid the spread F_B with weights (1/2)^dim at the node.
+    shape = (12, 12, 1) if dim == 2 else (12, 12, 12)
+    case = _quiet_case(shape, dim)
+    c = 6.0
+    U = np.array([[0.01, -0.02, 0.03 if dim == 3 else 0.0]])
+    case["particles"] = dict(X=[[c, c, c if dim == 3 else 0.0]], U=U, R=[0.5], rho_p=[2.0], T_p=[1.0])
+    o = oracle.Oracle(case)
+    F = o.particle_forces()
+    assert np.allclose(F["F"], -2.0 * U, rtol=1e-14, atol=1e-18)
+    assert abs(F["H"][0] - 2.0 * (1.0 - 0.3)) < 1e-14
+    FBx = o.field("FBx")
+    z = 6 if dim == 3 else 0
+    assert abs(FBx[z, 6, 6] - 0.5 ** dim * 2.0 * U[0, 0]) < 1e-18
+    assert abs(FBx.sum() - 2.0 * U[0, 0]) < 1e-17
+    assert abs(o.field("QB").sum() - F["H"][0]) < 1e-14
+
+
+def test_translating_disk_area():
+    # F = -2 U sum(eps): sum of the covered-node fractions approximates the disk area pi R^2
+    case = _quiet_case((40, 40, 1))
+    R = 6.3
+    U = np.array([[0.004, 0.001, 0.0]])
+    case["particles"] = dict(X=[[19.7, 20.2, 0.0]], U=U, R=[R], rho_p=[2.0], T_p=[0.3])
+    o = oracle.Oracle(case)
+    area = -o.particle_forces()["F"][0, 0] / (2 * U[0, 0])
+    assert abs(area / (np.pi * R * R) - 1) < 0.01
+
+
+def test_rotating_disk_torque():
+    # fluid at rest, U_l = omega x (r - X): torque = -2 omega sum(eps |r - X|^2)
+    # approximates -2 omega (pi R^4 / 2) and opposes the rotation
+    case = _quiet_case((40, 40, 1))
+    R, w = 7.2, 1e-3
+    # centre on a node row / half-node column: the covered set is mirror-symmetric about X
+    case["particles"] = dict(X=[[20.0, 19.5, 0.0]], W=[[0.0, 0.0, w]], R=[R], rho_p=[2.0], T_p=[0.3])
+    o = oracle.Oracle(case)
+    F = o.particle_forces()
+    tz = F["T"][0, 2]
+    assert tz < 0
+    assert abs(tz / (-2 * w * np.pi * R ** 4 / 2) - 1) < 0.03
+    assert np.max(np.abs(F["F"])) < 1e-12  # a symmetric spinning disk feels no net force
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_momentum_and_heat_exchange_exact(dim):
+    # The delta_h weights sum to one (Eq lbm12), so the spread force (Eq lbm10)
+    # summed over the lattice equals the particles' reaction (Eq lbm13) and the
+    # spread heat equals the particles' heat release, for any fluid state.
+    shape = (48, 40, 1) if dim == 2 else (24, 22, 20)
+    case = _quiet_case(shape, dim)
+    gen = W.rng(11)
+    n = 6
+    R = 2.5 if dim == 3 else 4.0
+    lo = [R + 3] * dim
+    hi = [s - R - 4 for s in shape[:dim]]
+    X = W.rsa_positions(gen, n, R, lo, hi, gap=-1.0)  # allow near-touching footprints
+    parts = dict(X=X, U=gen.normal(size=(n, 3)) * 1e-3, W=gen.normal(size=(n, 3)) * 1e-3,
+                 R=np.full(n, R), rho_p=np.full(n, 1.5), T_p=gen.random(n))
+    if dim == 2:
+        parts["U"][:, 2] = 0
+        parts["W"][:, :2] = 0
+    case["particles"] = parts
+    o = oracle.Oracle(case)
+    f, g = W.random_populations(case, amp=0.05)
+    o.set_populations(f.ravel(), g.ravel())
+    F = o.particle_forces()
+    FB = np.array([o.field(k).sum() for k in ("FBx", "FBy", "FBz")])
+    assert np.allclose(FB, -F["F"].sum(axis=0), rtol=1e-12, atol=1e-16)
+    assert abs(o.field("QB").sum() - F["H"].sum()) < 1e-12 * np.abs(F["H"]).sum()
+
+
+def test_overlapping_footprints_exclusive_ownership():
+    # Two disks closer than R1 + R2 + 1: the shared nodes belong to one disk
+    # only (largest eps, ties to the lower index), so the total force still
+    # balances and no node is counted twice.
+    case = _quiet_case((40, 30, 1))
+    U = np.array([[0.01, 0, 0], [-0.01, 0, 0]])
+    case["particles"] = dict(X=[[15.0, 15.0, 0], [24.5, 15.0, 0]], U=U, R=[5.0, 5.0],
+                             rho_p=[1.5, 1.5], T_p=[1.0, 1.0])
+    o = oracle.Oracle(case)
+    F = o.particle_forces()["F"]
+    a1 = -F[0, 0] / (2 * 0.01)
+    a2 = F[1, 0] / (2 * 0.01)
+    single = _quiet_case((40, 30, 1))
+    single["particles"] = dict(X=[[15.0, 15.0, 0]], U=U[:1], R=[5.0], rho_p=[1.5], T_p=[1.0])
+    a_single = -oracle.Oracle(single).particle_forces()["F"][0, 0] / (2 * 0.01)
+    assert a1 + a2 < 2 * a_single  # the shared nodes are not counted twice
+    assert abs(a1 + a2 - 2 * a_single) < 2.0
+    assert abs(o.field("FBx").sum() + F[:, 0].sum()) < 1e-15
+
+
+def test_static_markers_uniform_fluid():
+    # Off-node markers in fluid at rest with T = 0.3: Lagrange interpolation of
+    # a uniform field is exact, F_f = 0, Q = 2 (T_p - 0.3), and the Nusselt sum
+    # is sum A (T_p - T) / (alpha dT).
+    case = W.cavity(n=32, Ar=4.0)
+    case["T_init"] = 0.3
+    o = oracle.Oracle(case)
+    m = case["markers"]
+    alpha = o.relaxation()["alpha"]
+    expect = np.sum(m["A"] * (1.0 - 0.3)) / alpha
+    assert abs(o.nusselt() - expect) < 1e-13 * expect
+    assert abs(o.field("QB").sum() - np.sum(m["A"] * 2 * (1.0 - 0.3))) < 1e-12
+    assert np.max(np.abs(o.field("FBx"))) < 1e-16
+
+
+def test_cavity_symmetry_about_vertical_bisector():
+    # the cavity flow stays mirror-symmetric about x = (n-1)/2 (paper: isotherms and
+    # streamlines symmetric about the perpendicular bisector of the annulus)
+    case = W.cavity(n=32, Ar=2.5)
+    o = oracle.Oracle(case)
+    o.step(300)
+    T = o.field("T")[0]
+    ux = o.field("ux")[0]
+    assert np.max(np.abs(T - T[:, ::-1])) < 1e-12
+    assert np.max(np.abs(ux + ux[:, ::-1])) < 1e-12
+    assert o.nusselt() > 0
+    # hot cylinder: the fluid above it rises
+    uy = o.field("uy")[0]
+    assert uy[24, 16] > 0 or uy[22, 15] > 0

@@ -1,0 +1,186 @@
+"""Seeded synthetic workloads shaped like the cases of Zhang et al. (arXiv 1502.01159).
+
+This module holds input generation only -- lattice sizes, physical parameters,
+wall settings, particle placement, marker placement -- and none of the
+method's arithmetic.  Both the CUDA library's binding and the CPU oracle are
+fed from these dicts, so the two sides always see bit-identical inputs.
+
+Case dict keys
+--------------
+dim, shape=(nx, ny, nz), Ra, Pr, U_c, L_c, T_ref, T_init, buoyancy,
+gravity_axis, body_force[3], g_particle[3], dem_substeps, kappa_T, cell_size,
+nu_dT, pibm, walls = 2*dim entries (kind, thermal, T_w) ordered
+x-lo, x-hi, y-lo, y-hi, z-lo, z-hi (kind 0 periodic / 1 wall; thermal 0
+adiabatic / 1 isothermal), contact = contact-law dict, particles = dict of
+arrays (X n*3, U, W, R, rho_p, T_p, heat_cap, fixed) or None, markers =
+dict (X n*3, A, T) or None.
+
+Recipes (units: lattice units, h = dt = 1)
+------------------------------------------
+cavity   : square cavity with concentric isothermal cylinder (paper's
+           natural-convection case): four cold walls T = 0, cylinder of
+           radius L/(2 Ar) built from static points of diameter h/2 on a
+           square sub-lattice of spacing h/2 (area pi/16 each), T = 1;
+           fluid starts at 0.5; Ra, Pr, U_c = 0.25, L_c = L.
+sed2d    : 2-D sedimentation of heated disks: n_p disks placed by random
+           sequential addition (gap >= 1 to each other and to the walls) in
+           the upper half; density ratio 1.5; T_p = 1; walls T = 0; fluid 0.5;
+           linear spring-dashpot contacts; 10 DEM substeps.
+sed3d    : 3-D sedimentation of heated spheres: random sequential addition in
+           the upper 3/5; density ratio 1.2; Hertz / Mindlin-Deresiewicz.
+poiseuille, conduction, periodic_box : closed-form and invariant checks.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SEED_BASE = 1502011590
+
+D2Q9_E = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (-1, 0, 0), (0, -1, 0),
+          (1, 1, 0), (-1, 1, 0), (-1, -1, 0), (1, -1, 0)]
+D3Q19_E = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+           (1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1),
+           (1, 0, -1), (-1, 0, 1), (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1)]
+
+
+def rng(config_index: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(SEED_BASE + config_index))
+
+
+def _base(dim, shape, **kw):
+    case = dict(dim=dim, shape=tuple(int(v) for v in shape), Ra=1e4, Pr=0.71, U_c=0.1,
+                L_c=float(shape[dim - 1]), T_ref=0.5, T_init=0.5, buoyancy=True,
+                gravity_axis=dim - 1, body_force=[0.0, 0.0, 0.0], g_particle=[0.0, 0.0, 0.0],
+                dem_substeps=10, kappa_T=1.0, cell_size=0.0, nu_dT=1.0, pibm=True,
+                walls=[(1, 1, 0.0)] * (2 * dim), contact=None, particles=None, markers=None,
+                storage="f32")
+    case.update(kw)
+    return case
+
+
+def spring_dashpot(kn=100.0, kt=28.6, gamma_n=5.15, gamma_t=0.0, mu=0.3):
+    return dict(law=0, E=0.0, poisson=0.0, mu=mu, kn=kn, kt=kt, gamma_n=gamma_n, gamma_t=gamma_t)
+
+
+def hertz(E=2000.0, poisson=0.33, mu=0.3, gamma_n=0.0, gamma_t=0.0):
+    return dict(law=1, E=E, poisson=poisson, mu=mu, kn=0.0, kt=0.0, gamma_n=gamma_n, gamma_t=gamma_t)
+
+
+def rsa_positions(gen, n, radius, lo, hi, gap=1.0, max_tries=200000):
+    """Random sequential addition of n equal spheres/disks with centres drawn
+    uniformly in the box [lo, hi] (per-axis arrays), rejecting any candidate
+    closer than 2*radius + gap to an accepted one."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    dim = len(lo)
+    cell = 2 * radius + gap
+    grid: dict = {}
+    out = []
+    tries = 0
+    while len(out) < n:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError(f"random sequential addition placed only {len(out)} of {n}")
+        c = lo + gen.random(dim) * (hi - lo)
+        key = tuple((c // cell).astype(int))
+        ok = True
+        for off in np.ndindex(*([3] * dim)):
+            nb = tuple(k + o - 1 for k, o in zip(key, off))
+            for q in grid.get(nb, ()):
+                if np.sum((out[q] - c) ** 2) < cell * cell:
+                    ok = False
+                    break
+            if not ok:
+                break
+        if ok:
+            grid.setdefault(key, []).append(len(out))
+            out.append(c)
+    X = np.zeros((n, 3))
+    if n:
+        X[:, :dim] = np.array(out)
+    return X
+
+
+def cavity(n=128, Ra=1e4, Pr=0.71, Ar=2.5, U_c=0.25, storage="f64"):
+    """Natural convection in a square cavity with a concentric cylinder built
+    from static points of diameter h/2 (the paper's cavity case)."""
+    R = n / (2.0 * Ar)
+    c = (n - 1) / 2.0
+    k = np.arange(-int(2 * R) - 2, int(2 * R) + 3)
+    off = (k + 0.5) * 0.5
+    xs, ys = np.meshgrid(c + off, c + off, indexing="xy")
+    inside = (xs - c) ** 2 + (ys - c) ** 2 < R * R
+    X = np.zeros((int(inside.sum()), 3))
+    X[:, 0] = xs[inside]
+    X[:, 1] = ys[inside]
+    m = X.shape[0]
+    markers = dict(X=X, A=np.full(m, np.pi / 16.0), T=np.ones(m))
+    return _base(2, (n, n, 1), Ra=Ra, Pr=Pr, U_c=U_c, L_c=float(n), markers=markers,
+                 dem_substeps=1, storage=storage, name=f"cavity{n}_Ra{Ra:g}_Ar{Ar:g}")
+
+
+def sed2d(nx=512, ny=1024, n_p=500, d=10.0, rho_ratio=1.5, g=1e-4, config_index=1, storage="f32",
+          T_p=1.0):
+    gen = rng(config_index)
+    R = d / 2
+    X = rsa_positions(gen, n_p, R, [R + 1.0, ny / 2 + R + 1.0], [nx - 1.5 - R - 1.0, ny - 1.5 - R - 1.0])
+    parts = dict(X=X, R=np.full(n_p, R), rho_p=np.full(n_p, rho_ratio), T_p=np.full(n_p, T_p))
+    return _base(2, (nx, ny, 1), particles=parts, contact=spring_dashpot(),
+                 g_particle=[0.0, -g, 0.0], storage=storage, name=f"sed2d_{nx}x{ny}_{n_p}p")
+
+
+def sed3d(nx=256, ny=256, nz=512, n_p=2000, d=8.0, rho_ratio=1.2, g=1e-4, config_index=2,
+          storage="f32", T_p=1.0, heat_cap=None, T_p_random=False):
+    gen = rng(config_index)
+    R = d / 2
+    lo = [R + 1.0, R + 1.0, nz * 2.0 / 5.0 + R]
+    hi = [nx - 1.5 - R - 1.0, ny - 1.5 - R - 1.0, nz - 1.5 - R - 1.0]
+    X = rsa_positions(gen, n_p, R, lo, hi)
+    Tp = gen.random(n_p) if T_p_random else np.full(n_p, T_p)
+    parts = dict(X=X, R=np.full(n_p, R), rho_p=np.full(n_p, rho_ratio), T_p=Tp)
+    if heat_cap is not None:
+        parts["heat_cap"] = np.full(n_p, heat_cap)
+    return _base(3, (nx, ny, nz), particles=parts, contact=hertz(),
+                 g_particle=[0.0, 0.0, -g], storage=storage, name=f"sed3d_{nx}x{ny}x{nz}_{n_p}p")
+
+
+def poiseuille(ny=16, nx=4, nu=np.sqrt(3.0 / 16.0) / 3.0, F=1e-6, dim=2, nz=1):
+    """Channel periodic in x (and z), no-slip walls in y, constant body force along x."""
+    walls = [(0, 0, 0.0), (0, 0, 0.0), (1, 0, 0.0), (1, 0, 0.0)]
+    if dim == 3:
+        walls += [(0, 0, 0.0), (0, 0, 0.0)]
+    return _base(dim, (nx, ny, nz), Ra=1.0, Pr=1.0, U_c=nu, L_c=1.0, buoyancy=False,
+                 body_force=[F, 0.0, 0.0], walls=walls, pibm=False, name="poiseuille")
+
+
+def conduction(ny=16, nx=4, alpha=0.1, T_lo=1.0, T_hi=0.0, dim=2, nz=1):
+    """Periodic in x (and z), isothermal walls in y, fluid at rest."""
+    walls = [(0, 0, 0.0), (0, 0, 0.0), (1, 1, T_lo), (1, 1, T_hi)]
+    if dim == 3:
+        walls += [(0, 0, 0.0), (0, 0, 0.0)]
+    nu = alpha  # Pr = 1
+    return _base(dim, (nx, ny, nz), Ra=1.0, Pr=1.0, U_c=nu, L_c=1.0, buoyancy=False, T_init=0.5,
+                 walls=walls, pibm=False, name="conduction")
+
+
+def periodic_box(shape=(16, 12, 1), dim=2, buoyancy=True, body=(0.0, 0.0, 0.0)):
+    walls = [(0, 0, 0.0)] * (2 * dim)
+    return _base(dim, shape, U_c=0.05, L_c=float(shape[dim - 1]), buoyancy=buoyancy,
+                 body_force=list(body), walls=walls, pibm=False, name="periodic")
+
+
+def random_populations(case, config_index=7, amp=0.01):
+    """Positive populations near rest equilibrium with seeded perturbations
+    (for invariant tests): returns (f, g) in the [q][z][y][x] layout."""
+    gen = rng(config_index)
+    dim = case["dim"]
+    nx, ny, nz = case["shape"]
+    if dim == 2:
+        w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+        wg = np.array([1 / 3] + [1 / 6] * 4)
+    else:
+        w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+        wg = np.array([1 / 4] + [1 / 8] * 6)
+    f = w[:, None, None, None] * (1.0 + amp * (gen.random((len(w), nz, ny, nx)) - 0.5))
+    g = wg[:, None, None, None] * (0.5 + amp * (gen.random((len(wg), nz, ny, nx)) - 0.5))
+    return f, g
