@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Throughput of the fused LBM-PIBM-DEM lattice step on one GB300 per rank.
+
+Default workload: 2-D sedimentation of 500 heated disks (diameter 10 lattice
+units) in a 512 x 1024 cavity, D2Q9 + D2Q5, FP32 storage, spring-dashpot DEM
+with 10 substeps per lattice step.  One "step" = one lattice step: fused
+collide-and-stream, DEM substeps (concurrent branch), PIBM coupling.  The
+metric is fluid+thermal lattice-node updates per second (MLUPS), plus
+particle-steps/s; the 29 MB state fits in L2, so L2 is flushed (256 MB write)
+between timed steps and each step is timed on its own with CUDA events.
+
+Under torchrun each rank runs an independent replica on its own GPU (the
+method does not shard here: replicas only); value = all ranks' node updates /
+the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle on the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fluid+thermal MLUPS and particle-steps/s at 1 GB300; % HBM peak; speedup vs plain FP32 at error"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def bytes_per_node(case) -> int:
+    """Algorithmic bytes of one node update of the fused kernel: every flow and
+    thermal population read once and written once (A-A in place)."""
+    q = (9 + 5) if case["dim"] == 2 else (19 + 7)
+    es = 8 if case.get("storage") == "f64" else 4
+    return 2 * q * es
+
+
+def workload(name: str):
+    import workloads as W
+    if name == "sed2d":
+        case = W.sed2d()
+        desc = "sed2d: 2-D sedimentation, 512x1024 lattice, 500 heated disks d=10, D2Q9+D2Q5 FP32, spring-dashpot, 10 DEM substeps"
+    elif name == "sed3d":
+        case = W.sed3d()
+        desc = "sed3d: 3-D sedimentation, 256x256x512 lattice, 2000 heated spheres d=8, D3Q19+D3Q7 FP32, Hertz, 10 DEM substeps"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return case, desc
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_record(kernel: str, workload_name: str):
+    """DRAM bytes per launch from a committed ncu summary, valid only while the
+    kernel source is unchanged since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh)
+    entry = rec.get(kernel, {}).get(workload_name)
+    if not entry:
+        return None
+    src = os.path.join(ROOT, "paper_1502_01159_gb300", "csrc", entry["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return entry["bytes_per_launch"] if sha == entry["source_sha256"] else None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        self.proc.wait()
+        self.fh.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and self.uuid not in parts[1]:
+                continue
+            try:
+                sm.append(float(parts[2]))
+                smax = max(smax, float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[6:10]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_run(case, steps, warmup):
+    import oracle
+    o = oracle.Oracle(case)
+    o.step(warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    nodes = case["shape"][0] * case["shape"][1] * case["shape"][2]
+    n_p = len(case["particles"]["R"]) if case.get("particles") else 0
+    return nodes * steps / dt / 1e6, n_p * steps / dt, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    case, desc = workload(args.workload)
+    mlups, psps, dt = oracle_run(case, args.steps, args.warmup)
+    sample = f"{args.steps} lattice steps (after {args.warmup} untimed) of the full {args.workload} workload"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "implementation": "FP64 single-threaded C oracle on the host"},
+        "particle_steps_per_s": round(psps, 2),
+        "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def measure_gpu(case, steps, warmup, torch, flush):
+    """Device time per lattice step (graph replay), L2 flushed before each step."""
+    from paper_1502_01159_gb300 import Simulation
+    sim = Simulation(case)
+    s = sim.stream
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(s):
+            flush.fill_(k & 0xFF)
+        ev[k][0].record(s)
+        sim.step(1)
+        ev[k][1].record(s)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return sim, ms
+
+
+def kernel_times(sim, steps, torch, flush):
+    """Per-kernel-group device times of un-graphed steps (CUDA events on each launching stream)."""
+    out = []
+    for k in range(steps):
+        with torch.cuda.stream(sim.stream):
+            flush.fill_((k + 7) & 0xFF)
+        out.append(sim.step_timed())
+    return {key: statistics.mean(o[key] for o in out) for key in out[0]}
+
+
+def e2e_run(case, steps, torch):
+    """Whole job through the public API with host buffers: create, upload the
+    initial populations from pinned host memory, then per step: step + read
+    the particle state back; finally read the temperature field."""
+    import numpy as np
+
+    import workloads as W
+    from paper_1502_01159_gb300 import Simulation
+    f0, g0 = W.random_populations(case, amp=0.0)
+    fp = torch.empty(f0.size, dtype=torch.float64, pin_memory=True).numpy()
+    gp = torch.empty(g0.size, dtype=torch.float64, pin_memory=True).numpy()
+    fp[:] = f0.ravel()
+    gp[:] = g0.ravel()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = Simulation(case)
+    sim.set_populations(fp, gp)
+    n_p = sim.np
+    d2h = 0
+    for _ in range(steps):
+        sim.step(1)
+        p = sim.read_particles()
+        d2h += sum(v.nbytes for v in p.values())
+    T = sim.read_field("T")
+    d2h += T.nbytes
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h2d = fp.nbytes + gp.nbytes + n_p * 8 * 14
+    nodes = case["shape"][0] * case["shape"][1] * case["shape"][2]
+    sim.close()
+    return {"value": round(nodes * steps / dt / 1e6, 3), "unit": "MLUPS",
+            "h2d_bytes_per_step": int(h2d // steps), "d2h_bytes_per_step": int(d2h // steps),
+            "what": "create + upload of the initial populations and particles from host memory, "
+                    "then per step: step + particle state read-back; final temperature field read-back"}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+        __graft_entry__.build()
+
+    case, desc = workload(args.workload)
+    nodes = case["shape"][0] * case["shape"][1] * case["shape"][2]
+    n_p = len(case["particles"]["R"]) if case.get("particles") else 0
+
+    # CPU baseline first (before the first GPU call of the timed part), rank 0 at N = 1 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cs = max(1, args.cpu_steps)
+        mlups, psps, dt = oracle_run(case, cs, 1)
+        cpu = {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{cs} lattice steps of the full {args.workload} workload ({dt:.1f} s, FP64, 1 thread)"}
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_wall = time.perf_counter()
+    sim, ms = measure_gpu(case, args.steps, args.warmup, torch, flush)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    ms_step = statistics.mean(ms)
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+        dist.barrier()
+    value = world * nodes / (ms_step * 1e-3) / 1e6
+    kps = sim.kernels_per_step()
+
+    kt = kernel_times(sim, max(5, args.steps // 2), torch, flush)
+    peak, peak_kind = peaks()
+    bpn = bytes_per_node(case)
+    achieved = nodes * bpn / (kt["stream_collide"] * 1e-3) / 1e9
+    traffic = traffic_record("k_stream_collide", args.workload)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "k_stream_collide", "bytes_per_node": bpn, "nodes_per_launch": nodes,
+                "kernel_ms": round(kt["stream_collide"], 4), "peak_source": f"{peak_kind} hbm_gbs (copy, burst)"}
+    diag = sim.diagnostics()
+    sim.close()
+    del sim
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_run(case, args.steps, torch)
+
+    secondary = None
+    if rank == 0 and world == 1 and args.workload == "sed2d" and not args.no_3d:
+        c3, d3 = workload("sed3d")
+        sim3, ms3 = measure_gpu(c3, max(5, args.steps // 2), 3, torch, flush)
+        kt3 = kernel_times(sim3, 5, torch, flush)
+        n3 = c3["shape"][0] * c3["shape"][1] * c3["shape"][2]
+        b3 = bytes_per_node(c3)
+        a3 = n3 * b3 / (kt3["stream_collide"] * 1e-3) / 1e9
+        secondary = {"workload": d3, "value": round(n3 / (statistics.mean(ms3) * 1e-3) / 1e6, 1), "unit": "MLUPS",
+                     "ms_per_step": round(statistics.mean(ms3), 4),
+                     "particle_steps_per_s": round(2000 / (statistics.mean(ms3) * 1e-3), 1),
+                     "kernel_ms": {k: round(v, 4) for k, v in kt3.items()},
+                     "roofline": {"bound": "hbm", "achieved": round(a3, 1), "peak": peak, "unit": "GB/s",
+                                  "frac": round(a3 / peak, 4), "traffic": traffic_record("k_stream_collide", "sed3d"),
+                                  "kernel": "k_stream_collide", "bytes_per_node": b3, "nodes_per_launch": n3}}
+        sim3.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "flushed before every timed step (256 MB write); per-step device time excludes the flush",
+                       "wall_s_timed_region": round(t_wall, 3)},
+            "particle_steps_per_s": round(world * n_p / (ms_step * 1e-3), 1),
+            "kernel_ms": {k: round(v, 4) for k, v in kt.items()},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps * kps,
+            "clocks": clocks,
+            "diagnostics_after": {k: diag[k] for k in ("mass", "min_height", "umax", "nonfinite")},
+        }
+        if secondary:
+            line["secondary"] = secondary
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sed2d", choices=["sed2d", "sed3d"])
+    ap.add_argument("--cpu-steps", type=int, default=60)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-3d", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * pibm.h -- C ABI of the GB300 (sm_103a) library for the thermal lattice
+ * Boltzmann / particulate immersed boundary / discrete element step of
+ * Zhang, Yuan, Trias, Yu, Tan, Oliva, "Particulate immersed boundary method
+ * for complex fluid-particle interaction problems with heat transfer"
+ * (arXiv 1502.01159).
+ *
+ * One lattice step t -> t+1 runs, on one GPU:
+ *   1. BGK collision of the flow populations f (D2Q9 / D3Q19) and thermal
+ *      populations g (D2Q5 / D3Q7) with the immersed-boundary force F_B, the
+ *      heat source Q_B and Boussinesq buoyancy, then streaming, fused in one
+ *      in-place kernel (Section 2.1, Eqs lbm2, lbm2.5, lbm3, lbm3.5, lbm9,
+ *      lbm12.5);
+ *   2. the particle equations of motion in n_sub DEM substeps with the
+ *      hydrodynamic force of time t held fixed and Hertz / Mindlin-Deresiewicz
+ *      or linear spring-dashpot contacts found with a cell list (Section 2.3,
+ *      Eq demgov);
+ *   3. the PIBM coupling of time t+1: no-slip velocity and particle
+ *      temperature imposed on the lattice nodes each particle covers, spread
+ *      back as F_B, Q_B, and reduced to per-particle force, torque and heat
+ *      flux (Section 2.2, Eqs lbm5-lbm13).
+ *
+ * Units: lattice units (h = dt = 1, reference density 1).  Node (x, y, z) has
+ * linear index (z*ny + y)*nx + x.  Walls sit half a node outside the first and
+ * last node of a walled axis (at -0.5 and n-0.5).  Vectors are interleaved
+ * n*3 (z component 0 in 2-D).  Direction order:
+ *   D2Q9 : 0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1) 7 (-1,-1) 8 (1,-1)
+ *   D2Q5 : directions 0..4 of D2Q9
+ *   D3Q19: 0 (0,0,0) 1 (1,0,0) 2 (-1,0,0) 3 (0,1,0) 4 (0,-1,0) 5 (0,0,1) 6 (0,0,-1)
+ *          7 (1,1,0) 8 (-1,-1,0) 9 (1,-1,0) 10 (-1,1,0) 11 (1,0,1) 12 (-1,0,-1)
+ *          13 (1,0,-1) 14 (-1,0,1) 15 (0,1,1) 16 (0,-1,-1) 17 (0,1,-1) 18 (0,-1,1)
+ *   D3Q7 : directions 0..6 of D3Q19
+ *
+ * Ownership: the caller owns every pointer it passes; the library copies
+ * inputs during the call and never keeps a caller pointer.  The context owns
+ * all device memory; it comes from the optional allocator (for instance the
+ * PyTorch caching allocator) or from cudaMalloc, and pibm_destroy releases it.
+ *
+ * Errors: every call returns a status and never aborts, exits or traps.  On
+ * failure the context keeps its previous state unless the status says
+ * otherwise; pibm_last_error gives a one-line message.
+ *
+ * Streams: all device work is ordered on the stream given at creation (plus
+ * one internal stream forked and joined inside each step).  Calls that return
+ * data to host memory synchronise that stream.  A context is not thread-safe.
+ */
+#ifndef PIBM_H
+#define PIBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pibm_ctx pibm_ctx;
+
+typedef enum {
+    PIBM_OK = 0,
+    PIBM_ERR_ARG = 1,       /* invalid argument or description */
+    PIBM_ERR_OOM = 2,       /* device allocation failed */
+    PIBM_ERR_CUDA = 3,      /* a CUDA call failed; see pibm_last_error */
+    PIBM_ERR_STATE = 4,     /* call not valid in the current state, or a device-side
+                               consistency check failed (e.g. neighbour list overflow) */
+    PIBM_ERR_UNSTABLE = 5,  /* non-finite values detected; state kept for inspection */
+    PIBM_ERR_TIMEOUT = 6    /* a bounded device-side wait gave up */
+} pibm_status;
+
+enum { PIBM_PERIODIC = 0, PIBM_WALL = 1 };           /* wall kind per face */
+enum { PIBM_ADIABATIC = 0, PIBM_ISOTHERMAL = 1 };    /* thermal condition per wall face */
+enum { PIBM_SPRING_DASHPOT = 0, PIBM_HERTZ_MD = 1 }; /* contact law */
+enum { PIBM_STORE_F32 = 0, PIBM_STORE_F64 = 1 };     /* population storage (deviation form) */
+enum {                                                /* fields for pibm_read_field */
+    PIBM_RHO = 0, PIBM_UX, PIBM_UY, PIBM_UZ, PIBM_T, PIBM_FBX, PIBM_FBY, PIBM_FBZ, PIBM_QB
+};
+
+/* Device allocator hook.  alloc returns a device pointer aligned to >= 256
+ * bytes or NULL; free releases it.  user is passed back unchanged. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* user);
+    void (*free)(void* ptr, void* user);
+    void* user;
+} pibm_allocator;
+
+/* Problem description (Section 2.1; Eqs lbm2.6, lbm2.7 give the relaxation
+ * times from Ra, Pr, U_c, L_c: nu = U_c L_c sqrt(Pr/Ra), alpha = nu/Pr,
+ * tau_f = 3 nu + 1/2, tau_g = alpha / cs_T^2 + 1/2). */
+typedef struct {
+    int dim;                /* 2 or 3 */
+    int nx, ny, nz;         /* lattice size; nz = 1 in 2-D */
+    int storage;            /* PIBM_STORE_F32 or PIBM_STORE_F64 */
+    double Ra, Pr;          /* Rayleigh and Prandtl numbers */
+    double U_c, L_c;        /* characteristic velocity (lattice units) and length (nodes) */
+    double T_ref;           /* Boussinesq reference temperature */
+    double T_init;          /* initial fluid temperature */
+    int buoyancy;           /* 1: buoyancy (U_c^2/L_c)(T - T_ref) along -gravity */
+    int gravity_axis;       /* gravity points along -axis */
+    double body_force[3];   /* constant body force at every node */
+    double g_particle[3];   /* gravitational acceleration of the particles */
+    int dem_substeps;       /* DEM substeps per lattice step (>= 1) */
+    double kappa_T;         /* prefactor of the thermal correction Q = 2 kappa_T (T_p - T) */
+    double cell_size;       /* minimum DEM cell side; <= 0 selects 2 R_max + 1.5 */
+    double nu_dT;           /* T_hot - T_inf in the Nusselt number */
+    int pibm;               /* 1: couple fluid and particles */
+} pibm_desc;
+
+/* Create a context: allocates the lattice (f and g initialised to the rest
+ * equilibrium at density 1 and temperature T_init, Eqs lbm3, lbm3.5) with all
+ * faces periodic.  stream: a cudaStream_t, or NULL for the default stream.
+ * alloc: NULL uses cudaMalloc / cudaFree.  Returns PIBM_ERR_ARG for an
+ * invalid description, PIBM_ERR_OOM if the device memory cannot be obtained. */
+pibm_status pibm_create(const pibm_desc* desc, void* stream, const pibm_allocator* alloc, pibm_ctx** out);
+
+/* Release every device buffer of the context and the context itself. */
+pibm_status pibm_destroy(pibm_ctx* ctx);
+
+/* Boundary of face 0..2*dim-1 (x-lo, x-hi, y-lo, y-hi, z-lo, z-hi).  Both
+ * faces of an axis must end up with the same kind.  A wall is a halfway
+ * bounce-back no-slip wall for f; for g it is isothermal at T_w
+ * (anti-bounce-back) or adiabatic (bounce-back).  Recomputes the coupling. */
+pibm_status pibm_set_wall(pibm_ctx* ctx, int face, int kind, int thermal, double T_w);
+
+/* Contact law (text after Eq demgov).  HERTZ_MD: F_n = 4/3 E* sqrt(R*) d^1.5 +
+ * gamma_n v_n with 1/E* = (1-nu^2)/E + (1-nu^2)/E, tangential stiffness
+ * 8 G* sqrt(d R*).  SPRING_DASHPOT: F_n = kn d + gamma_n v_n, stiffness kt.
+ * Both: tangential force capped at mu |F_n|, tangential damping gamma_t. */
+pibm_status pibm_set_contact_law(pibm_ctx* ctx, int law, double E, double poisson, double mu,
+                                 double kn, double kt, double gamma_n, double gamma_t);
+
+/* Particles (host arrays, copied).  X, U, W: n*3; R, rho_p, T_p: n;
+ * heat_cap: n or NULL (isothermal); fixed: n bytes or NULL (all free).
+ * Requires every axis to be walled when n > 0.  Resets the contact history,
+ * rebuilds the cell list and recomputes the coupling of the current time. */
+pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const double* U, const double* W,
+                               const double* R, const double* rho_p, const double* T_p,
+                               const double* heat_cap, const uint8_t* fixed);
+
+/* Static off-node markers (the concentric cylinder of the cavity case):
+ * positions n*3, areas A_p, temperatures T_p.  Each marker needs its 4-point
+ * interpolation stencil inside the lattice.  Recomputes the coupling. */
+pibm_status pibm_set_markers(pibm_ctx* ctx, int n, const double* X, const double* A, const double* T_p);
+
+/* Overwrite the populations of the current time with host arrays in the
+ * layout [q][z][y][x] (either pointer may be NULL).  Recomputes the coupling. */
+pibm_status pibm_set_populations(pibm_ctx* ctx, const double* f, const double* g);
+
+/* Advance nsteps lattice steps (replayed CUDA graphs).  Asynchronous: returns
+ * once the work is enqueued.  PIBM_ERR_STATE / PIBM_ERR_UNSTABLE from an
+ * earlier step are reported by the next synchronising call. */
+pibm_status pibm_step(pibm_ctx* ctx, int nsteps);
+
+/* Macroscopic field of the current time into host_dst (n = nx*ny*nz doubles):
+ * rho, u = (j + F/2)/rho, T = sum g + Q_B/2, F_B, Q_B. */
+pibm_status pibm_read_field(pibm_ctx* ctx, int field, double* host_dst, size_t n);
+
+/* Populations of the current time (before collision) as doubles [q][z][y][x]. */
+pibm_status pibm_read_populations(pibm_ctx* ctx, double* f, double* g);
+
+/* Particle state: X, U, W (n*3) and T_p (n); NULL pointers are skipped. */
+pibm_status pibm_read_particles(pibm_ctx* ctx, double* X, double* U, double* W, double* T_p);
+
+/* Hydrodynamic force, torque (n*3) and heat release H (n) of the current
+ * time (Eq lbm13 summed over each particle's nodes). */
+pibm_status pibm_read_particle_forces(pibm_ctx* ctx, double* F, double* T, double* H);
+
+/* Average Nusselt number over the static markers (sum A (T_p - T) / (alpha nu_dT)). */
+pibm_status pibm_nusselt(pibm_ctx* ctx, double* nu);
+
+/* Contacts at the current positions: pairs (i < j) with |X_i - X_j| < R_i + R_j,
+ * sorted by (i, j), written as 2*min(cap, n) ints; *n_out = total count. */
+pibm_status pibm_read_contacts(pibm_ctx* ctx, int32_t* pairs, int cap, int* n_out);
+
+/* Cell of each particle at the current positions (cell side n_a / nc_a with
+ * nc_a = floor(n_a / cell_min); index (cz*ncy + cy)*ncx + cx); ncell: 3 ints or NULL. */
+pibm_status pibm_read_cells(pibm_ctx* ctx, int32_t* cell, int32_t* ncell);
+
+/* out[6]: sum rho, sum of g, particle kinetic energy, minimum particle
+ * coordinate along the gravity axis, max |u|, 1 if any value is non-finite. */
+pibm_status pibm_diagnostics(pibm_ctx* ctx, double* out);
+
+/* out[5]: nu, alpha, tau_f, tau_g, buoyancy coefficient U_c^2/L_c. */
+pibm_status pibm_relaxation(pibm_ctx* ctx, double* out);
+
+/* Current lattice time (number of steps taken). */
+pibm_status pibm_time(pibm_ctx* ctx, int64_t* t);
+
+/* One lattice step launched without a graph, with CUDA events around each
+ * kernel group on the stream it runs on.  ms[0] collide-and-stream, ms[1] DEM,
+ * ms[2] PIBM coupling, ms[3] the whole step (fork to join).  Synchronises. */
+pibm_status pibm_step_timed(pibm_ctx* ctx, double* ms);
+
+/* Number of kernels one lattice step launches (for launch accounting). */
+pibm_status pibm_kernels_per_step(pibm_ctx* ctx, int* n);
+
+const char* pibm_status_string(pibm_status s);
+/* Copies the last error message of the context (or of the last failed
+ * pibm_create when ctx is NULL) into buf; returns its length. */
+int pibm_last_error(pibm_ctx* ctx, char* buf, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -84,6 +84,8 @@ def lib():
             "orc_contacts": (C.c_int, [P, I, C.c_int]),
             "orc_contacts_bruteforce": (C.c_int, [P, I, C.c_int]),
             "orc_cells": (C.c_int, [P, I, I]),
+            "orc_point_contacts": (C.c_int, [C.c_int, D, D, I, C.c_int]),
+            "orc_point_cells": (C.c_int, [C.c_int, I, C.c_double, C.c_int, D, D, I, I]),
             "orc_diagnostics": (C.c_int, [P, D]),
             "orc_relaxation": (C.c_int, [P, D]),
             "orc_time": (C.c_long, [P]),
@@ -262,3 +264,26 @@ def lagrange_weights(x: float, npts: int = 4):
     w = np.empty(npts)
     base = lib().orc_lagrange_weights(float(x), int(npts), _dp(w))
     return int(base), w
+
+
+def point_contacts(X, R) -> np.ndarray:
+    """Brute-force contact pairs (i < j, sorted) of a bare point set."""
+    X = _f64(X, (-1, 3))
+    R = _f64(R)
+    n = lib().orc_point_contacts(len(R), _dp(X), _dp(R), None, 0)
+    buf = np.zeros(2 * max(n, 1), dtype=np.int32)
+    lib().orc_point_contacts(len(R), _dp(X), _dp(R), buf.ctypes.data_as(C.POINTER(C.c_int)), n)
+    return buf[: 2 * n].reshape(n, 2)
+
+
+def point_cells(dim, shape, cell_size, X, R):
+    """Cell of each point under the cell-grid definition shared with the library."""
+    X = _f64(X, (-1, 3))
+    R = _f64(R)
+    nl = np.asarray(shape, dtype=np.int32)
+    c = np.zeros(max(len(R), 1), dtype=np.int32)
+    nc = np.zeros(3, dtype=np.int32)
+    I = C.POINTER(C.c_int)
+    lib().orc_point_cells(dim, nl.ctypes.data_as(I), float(cell_size), len(R), _dp(X), _dp(R),
+                          c.ctypes.data_as(I), nc.ctypes.data_as(I))
+    return c[: len(R)], tuple(int(v) for v in nc)

@@ -415,7 +415,7 @@ static void cell_grid(const orc_sim* s, int nc[3], double inv[3]) {
     double rmax = 0.0;
     for (int p = 0; p < s->np; p++)
         if (s->R[p] > rmax) rmax = s->R[p];
-    double cmin = s->P.cell_size > 0.0 ? s->P.cell_size : 2.0 * rmax + 0.5;
+    double cmin = s->P.cell_size > 0.0 ? s->P.cell_size : 2.0 * rmax + 1.5;
     for (int a = 0; a < 3; a++) {
         nc[a] = 1;
         inv[a] = 1.0 / (double)s->n[a];
@@ -532,6 +532,52 @@ int orc_contacts_bruteforce(orc_sim* s, int* pairs, int cap) {
                 n++;
             }
     return n;
+}
+
+/* contact pairs and cells of a bare point set (same definitions, no lattice):
+ * brute force over all pairs i < j with |X_i - X_j|^2 < (R_i + R_j)^2 */
+int orc_point_contacts(int np, const double* X, const double* R, int* pairs, int cap) {
+    int n = 0;
+    for (int i = 0; i < np; i++)
+        for (int j = i + 1; j < np; j++) {
+            double dx = X[3 * j] - X[3 * i], dy = X[3 * j + 1] - X[3 * i + 1], dz = X[3 * j + 2] - X[3 * i + 2];
+            double d2 = dx * dx + dy * dy + dz * dz;
+            double sr = R[i] + R[j];
+            if (d2 < sr * sr) {
+                if (n < cap) {
+                    pairs[2 * n] = i;
+                    pairs[2 * n + 1] = j;
+                }
+                n++;
+            }
+        }
+    return n;
+}
+
+int orc_point_cells(int dim, const int* nlat, double cell_size, int np, const double* X, const double* R, int* cell,
+                    int* ncell) {
+    double rmax = 0.0;
+    for (int p = 0; p < np; p++)
+        if (R[p] > rmax) rmax = R[p];
+    double cmin = cell_size > 0.0 ? cell_size : 2.0 * rmax + 1.5;
+    int nc[3];
+    double inv[3];
+    for (int a = 0; a < 3; a++) {
+        nc[a] = 1;
+        inv[a] = 1.0 / (double)nlat[a];
+        if (a < dim) {
+            nc[a] = (int)floor((double)nlat[a] / cmin);
+            if (nc[a] < 1) nc[a] = 1;
+            inv[a] = (double)nc[a] / (double)nlat[a];
+        }
+    }
+    for (int p = 0; p < np; p++) {
+        int c[3];
+        for (int a = 0; a < 3; a++) c[a] = cell_coord(X[3 * p + a], inv[a], nc[a]);
+        cell[p] = (c[2] * nc[1] + c[1]) * nc[0] + c[0];
+    }
+    for (int a = 0; a < 3; a++) ncell[a] = nc[a];
+    return np;
 }
 
 /* Hertz normal force (text after Eq demgov) and Mindlin-Deresiewicz loading stiffness

@@ -42,7 +42,7 @@ typedef struct {
     double g_particle[3];    /* gravitational acceleration felt by particles */
     int dem_substeps;        /* DEM substeps per lattice step */
     double kappa_T;          /* prefactor of the thermal PIBM correction */
-    double cell_size;        /* minimum DEM cell side; <= 0: 2*R_max + 0.5 */
+    double cell_size;        /* minimum DEM cell side; <= 0: 2*R_max + 1.5 */
     double nu_dT;            /* T_hot - T_inf in the Nusselt number */
     int pibm;                /* 1: particles and fluid are coupled */
 } orc_params;
@@ -73,6 +73,9 @@ double   orc_nusselt(orc_sim* s);
 int      orc_contacts(orc_sim* s, int* pairs, int cap);
 int      orc_contacts_bruteforce(orc_sim* s, int* pairs, int cap);
 int      orc_cells(orc_sim* s, int* cell, int* ncell);
+int      orc_point_contacts(int np, const double* X, const double* R, int* pairs, int cap);
+int      orc_point_cells(int dim, const int* nlat, double cell_size, int np, const double* X, const double* R,
+                         int* cell, int* ncell);
 int      orc_diagnostics(orc_sim* s, double* out);
 int      orc_relaxation(orc_sim* s, double* out);
 long     orc_time(orc_sim* s);

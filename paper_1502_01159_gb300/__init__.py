@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) implementation of the thermal LBM-PIBM-DEM lattice step of
+Zhang et al., "Particulate immersed boundary method for complex
+fluid-particle interaction problems with heat transfer" (arXiv 1502.01159).
+
+The compute path is the C-ABI CUDA library ``libpibm.so`` (include/pibm.h);
+this package holds its sources (csrc/), its build (build.py) and the ctypes
+binding (_native.py).  There is no CPU fallback: without the library every
+call raises."""
+from ._native import (ADIABATIC, FIELDS, HERTZ_MD, ISOTHERMAL, PERIODIC, SPRING_DASHPOT, STORE_F32, STORE_F64,
+                      WALL, PibmError, Simulation, load)
+
+__all__ = ["Simulation", "PibmError", "load", "FIELDS", "PERIODIC", "WALL", "ADIABATIC", "ISOTHERMAL",
+           "SPRING_DASHPOT", "HERTZ_MD", "STORE_F32", "STORE_F64"]

@@ -1,0 +1,319 @@
+"""ctypes binding of libpibm.so (include/pibm.h).  Argument marshalling only:
+every step of the lattice update, the coupling and the DEM runs in the CUDA
+kernels of the library.  PyTorch provides the device memory (through the
+allocator hook of pibm_create) and the stream."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpibm.so")
+
+PIBM_OK, PIBM_ERR_ARG, PIBM_ERR_OOM, PIBM_ERR_CUDA, PIBM_ERR_STATE, PIBM_ERR_UNSTABLE, PIBM_ERR_TIMEOUT = range(7)
+PERIODIC, WALL = 0, 1
+ADIABATIC, ISOTHERMAL = 0, 1
+SPRING_DASHPOT, HERTZ_MD = 0, 1
+STORE_F32, STORE_F64 = 0, 1
+FIELDS = {"rho": 0, "ux": 1, "uy": 2, "uz": 3, "T": 4, "FBx": 5, "FBy": 6, "FBz": 7, "QB": 8}
+
+# every symbol include/pibm.h declares, with (restype, argtypes)
+_P, _D, _I32, _U8 = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_uint8)
+
+
+class pibm_desc(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("storage", C.c_int),
+        ("Ra", C.c_double), ("Pr", C.c_double), ("U_c", C.c_double), ("L_c", C.c_double),
+        ("T_ref", C.c_double), ("T_init", C.c_double),
+        ("buoyancy", C.c_int), ("gravity_axis", C.c_int),
+        ("body_force", C.c_double * 3), ("g_particle", C.c_double * 3),
+        ("dem_substeps", C.c_int), ("kappa_T", C.c_double), ("cell_size", C.c_double),
+        ("nu_dT", C.c_double), ("pibm", C.c_int),
+    ]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class pibm_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+SIGNATURES = {
+    "pibm_create": (C.c_int, [C.POINTER(pibm_desc), _P, C.POINTER(pibm_allocator), C.POINTER(_P)]),
+    "pibm_destroy": (C.c_int, [_P]),
+    "pibm_set_wall": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double]),
+    "pibm_set_contact_law": (C.c_int, [_P, C.c_int] + [C.c_double] * 7),
+    "pibm_set_particles": (C.c_int, [_P, C.c_int, _D, _D, _D, _D, _D, _D, _D, _U8]),
+    "pibm_set_markers": (C.c_int, [_P, C.c_int, _D, _D, _D]),
+    "pibm_set_populations": (C.c_int, [_P, _D, _D]),
+    "pibm_step": (C.c_int, [_P, C.c_int]),
+    "pibm_read_field": (C.c_int, [_P, C.c_int, _D, C.c_size_t]),
+    "pibm_read_populations": (C.c_int, [_P, _D, _D]),
+    "pibm_read_particles": (C.c_int, [_P, _D, _D, _D, _D]),
+    "pibm_read_particle_forces": (C.c_int, [_P, _D, _D, _D]),
+    "pibm_nusselt": (C.c_int, [_P, _D]),
+    "pibm_read_contacts": (C.c_int, [_P, _I32, C.c_int, C.POINTER(C.c_int)]),
+    "pibm_read_cells": (C.c_int, [_P, _I32, _I32]),
+    "pibm_diagnostics": (C.c_int, [_P, _D]),
+    "pibm_relaxation": (C.c_int, [_P, _D]),
+    "pibm_time": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "pibm_kernels_per_step": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "pibm_step_timed": (C.c_int, [_P, _D]),
+    "pibm_status_string": (C.c_char_p, [C.c_int]),
+    "pibm_last_error": (C.c_int, [_P, C.c_char_p, C.c_size_t]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpibm.so.  There is no fallback: a missing library is an error."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"{path} is missing: build the CUDA library first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class PibmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def _f64(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return a.reshape(shape) if shape is not None else a
+
+
+class TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator.  Each
+    allocation is a uint8 CUDA tensor kept alive until the library frees it."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.live = {}
+        self._alloc = ALLOC_FN(self._do_alloc)
+        self._free = FREE_FN(self._do_free)
+        self.struct = pibm_allocator(self._alloc, self._free, None)
+
+    def _do_alloc(self, nbytes, user):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+        except Exception:  # out of memory: the library reports PIBM_ERR_OOM
+            return None
+        ptr = t.data_ptr()
+        self.live[ptr] = t
+        return ptr
+
+    def _do_free(self, ptr, user):
+        self.live.pop(ptr, None)
+
+
+class Simulation:
+    """One library context built from a workload dict (see workloads.py).
+
+    Method names follow the C ABI without the ``pibm_`` prefix.  With
+    ``use_torch=True`` (default) device memory comes from PyTorch and the
+    work is ordered on a dedicated torch CUDA stream."""
+
+    def __init__(self, case: dict, use_torch: bool = True, device: int = 0):
+        self.L = load()
+        self.case = case
+        d = pibm_desc()
+        d.dim = case["dim"]
+        d.nx, d.ny, d.nz = case["shape"]
+        d.storage = STORE_F64 if case.get("storage", "f32") == "f64" else STORE_F32
+        d.Ra, d.Pr, d.U_c, d.L_c = case["Ra"], case["Pr"], case["U_c"], case["L_c"]
+        d.T_ref, d.T_init = case["T_ref"], case["T_init"]
+        d.buoyancy, d.gravity_axis = int(case["buoyancy"]), case["gravity_axis"]
+        d.body_force = (C.c_double * 3)(*case["body_force"])
+        d.g_particle = (C.c_double * 3)(*case["g_particle"])
+        d.dem_substeps = case["dem_substeps"]
+        d.kappa_T, d.cell_size, d.nu_dT = case["kappa_T"], case["cell_size"], case["nu_dT"]
+        d.pibm = int(case["pibm"])
+        self.desc = d
+        self.dim = d.dim
+        self.shape = (d.nz, d.ny, d.nx)
+        self.N = d.nx * d.ny * d.nz
+        self.Q, self.QG = (9, 5) if self.dim == 2 else (19, 7)
+        self.np = 0
+        self.allocator = None
+        self.stream = None
+        stream_ptr = None
+        alloc_ptr = None
+        if use_torch:
+            import torch
+            dev = torch.device("cuda", device)
+            self.stream = torch.cuda.Stream(device=dev)
+            stream_ptr = C.c_void_p(self.stream.cuda_stream)
+            self.allocator = TorchAllocator(dev)
+            alloc_ptr = C.byref(self.allocator.struct)
+        h = C.c_void_p()
+        st = self.L.pibm_create(C.byref(d), stream_ptr, alloc_ptr, C.byref(h))
+        if st != PIBM_OK:
+            buf = C.create_string_buffer(512)
+            self.L.pibm_last_error(None, buf, 512)
+            raise PibmError(st, "pibm_create: " + buf.value.decode())
+        self.h = h
+        for face, (kind, thermal, Tw) in enumerate(case["walls"]):
+            self.set_wall(face, kind, thermal, Tw)
+        law = case.get("contact")
+        if law is not None:
+            self.set_contact_law(law["law"], law["E"], law["poisson"], law["mu"], law["kn"], law["kt"],
+                                 law["gamma_n"], law["gamma_t"])
+        if case.get("particles") is not None:
+            self.set_particles(case["particles"])
+        if case.get("markers") is not None:
+            m = case["markers"]
+            self.set_markers(m["X"], m["A"], m["T"])
+
+    # ------------------------------------------------------------ plumbing
+    def _check(self, st, what):
+        if st != PIBM_OK:
+            buf = C.create_string_buffer(512)
+            self.L.pibm_last_error(self.h, buf, 512)
+            raise PibmError(st, f"{what}: {buf.value.decode()}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.pibm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ set-up
+    def set_wall(self, face, kind, thermal, T_w):
+        self._check(self.L.pibm_set_wall(self.h, face, kind, thermal, float(T_w)), "pibm_set_wall")
+
+    def set_contact_law(self, law, E, poisson, mu, kn, kt, gamma_n, gamma_t):
+        self._check(self.L.pibm_set_contact_law(self.h, law, E, poisson, mu, kn, kt, gamma_n, gamma_t),
+                    "pibm_set_contact_law")
+
+    def set_particles(self, parts: dict):
+        X = _f64(parts["X"], (-1, 3))
+        n = X.shape[0]
+        z3 = np.zeros((n, 3))
+        U = _f64(parts.get("U", z3), (-1, 3))
+        W = _f64(parts.get("W", z3), (-1, 3))
+        R, rho = _f64(parts["R"]), _f64(parts["rho_p"])
+        Tp = _f64(parts.get("T_p", np.zeros(n)))
+        Cp = _f64(parts.get("heat_cap"))
+        fixed = parts.get("fixed")
+        fx = None
+        if fixed is not None:
+            fixed = np.ascontiguousarray(np.asarray(fixed, dtype=np.uint8))
+            fx = fixed.ctypes.data_as(_U8)
+        st = self.L.pibm_set_particles(self.h, n, _dp(X), _dp(U), _dp(W), _dp(R), _dp(rho), _dp(Tp), _dp(Cp), fx)
+        self._check(st, "pibm_set_particles")
+        self.np = n
+
+    def set_markers(self, X, A, T):
+        X = _f64(X, (-1, 3))
+        A, T = _f64(A), _f64(T)
+        self._check(self.L.pibm_set_markers(self.h, len(A), _dp(X), _dp(A), _dp(T)), "pibm_set_markers")
+
+    def set_populations(self, f=None, g=None):
+        f, g = _f64(f), _f64(g)
+        self._check(self.L.pibm_set_populations(self.h, _dp(f), _dp(g)), "pibm_set_populations")
+
+    # ------------------------------------------------------------ stepping
+    def step(self, n: int = 1):
+        self._check(self.L.pibm_step(self.h, int(n)), "pibm_step")
+
+    def step_timed(self):
+        """One un-graphed step; returns per-kernel-group device times in ms:
+        collide-and-stream, DEM, coupling, whole step."""
+        ms = np.zeros(4)
+        self._check(self.L.pibm_step_timed(self.h, _dp(ms)), "pibm_step_timed")
+        return dict(zip(["stream_collide", "dem", "coupling", "step"], ms.tolist()))
+
+    # ------------------------------------------------------------ read-back
+    def read_field(self, name: str) -> np.ndarray:
+        out = np.empty(self.N)
+        self._check(self.L.pibm_read_field(self.h, FIELDS[name], _dp(out), self.N), "pibm_read_field")
+        return out.reshape(self.shape)
+
+    def read_populations(self):
+        f = np.empty(self.Q * self.N)
+        g = np.empty(self.QG * self.N)
+        self._check(self.L.pibm_read_populations(self.h, _dp(f), _dp(g)), "pibm_read_populations")
+        return f.reshape((self.Q,) + self.shape), g.reshape((self.QG,) + self.shape)
+
+    def read_particles(self):
+        n = self.np
+        X, U, W, T = np.empty((n, 3)), np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
+        self._check(self.L.pibm_read_particles(self.h, _dp(X), _dp(U), _dp(W), _dp(T)), "pibm_read_particles")
+        return {"X": X, "U": U, "W": W, "T_p": T}
+
+    def read_particle_forces(self):
+        n = self.np
+        F, T, H = np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
+        self._check(self.L.pibm_read_particle_forces(self.h, _dp(F), _dp(T), _dp(H)), "pibm_read_particle_forces")
+        return {"F": F, "T": T, "H": H}
+
+    def nusselt(self) -> float:
+        v = C.c_double()
+        self._check(self.L.pibm_nusselt(self.h, C.byref(v)), "pibm_nusselt")
+        return v.value
+
+    def read_contacts(self) -> np.ndarray:
+        n = C.c_int()
+        self._check(self.L.pibm_read_contacts(self.h, None, 0, C.byref(n)), "pibm_read_contacts")
+        buf = np.zeros(2 * max(n.value, 1), dtype=np.int32)
+        self._check(self.L.pibm_read_contacts(self.h, buf.ctypes.data_as(_I32), n.value, C.byref(n)),
+                    "pibm_read_contacts")
+        return buf[: 2 * n.value].reshape(-1, 2)
+
+    def read_cells(self):
+        c = np.zeros(max(self.np, 1), dtype=np.int32)
+        nc = np.zeros(3, dtype=np.int32)
+        self._check(self.L.pibm_read_cells(self.h, c.ctypes.data_as(_I32), nc.ctypes.data_as(_I32)),
+                    "pibm_read_cells")
+        return c[: self.np], tuple(int(v) for v in nc)
+
+    def diagnostics(self) -> dict:
+        out = np.empty(6)
+        self._check(self.L.pibm_diagnostics(self.h, _dp(out)), "pibm_diagnostics")
+        return dict(zip(["mass", "heat", "ke", "min_height", "umax", "nonfinite"], out.tolist()))
+
+    def relaxation(self) -> dict:
+        out = np.empty(5)
+        self._check(self.L.pibm_relaxation(self.h, _dp(out)), "pibm_relaxation")
+        return dict(zip(["nu", "alpha", "tau_f", "tau_g", "buoy"], out.tolist()))
+
+    @property
+    def t(self) -> int:
+        v = C.c_int64()
+        self._check(self.L.pibm_time(self.h, C.byref(v)), "pibm_time")
+        return v.value
+
+    def kernels_per_step(self) -> int:
+        v = C.c_int()
+        self._check(self.L.pibm_kernels_per_step(self.h, C.byref(v)), "pibm_kernels_per_step")
+        return v.value

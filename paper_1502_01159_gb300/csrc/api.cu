@@ -1,0 +1,763 @@
+// Host side of the C ABI declared in include/pibm.h: argument checks, device
+// memory through the caller's allocator, set-up of particles and static
+// markers, CUDA-graph capture of one lattice step per time parity, and the
+// read-back calls.  All arithmetic of the step runs in the kernels of
+// lattice.cu, coupling.cu and dem.cu.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "pibm_internal.cuh"
+
+using namespace pibm;
+
+struct pibm_ctx {
+    Ctx c;
+    std::vector<std::pair<void*, int>> allocs;  // (pointer, group): 0 lattice, 1 particles, 2 markers, 3 scratch
+};
+
+static std::string g_create_error;
+
+enum { GRP_LATTICE = 0, GRP_PARTICLES = 1, GRP_MARKERS = 2, GRP_SCRATCH = 3 };
+
+#define PCHECK(call)                                                                         \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            ctx->c.err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+            return e_ == cudaErrorMemoryAllocation ? PIBM_ERR_OOM : PIBM_ERR_CUDA;           \
+        }                                                                                    \
+    } while (0)
+
+static pibm_status fail(pibm_ctx* ctx, pibm_status s, const std::string& msg) {
+    if (ctx) ctx->c.err = msg;
+    return s;
+}
+
+static void* dalloc(pibm_ctx* ctx, size_t bytes, int group) {
+    Ctx& c = ctx->c;
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (c.alloc.alloc) {
+        p = c.alloc.alloc(bytes, c.alloc.user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        p = nullptr;
+    }
+    if (!p) return nullptr;
+    if (cudaMemsetAsync(p, 0, bytes, c.s0) != cudaSuccess) return nullptr;
+    ctx->allocs.push_back({p, group});
+    return p;
+}
+
+static void dfree_group(pibm_ctx* ctx, int group) {
+    Ctx& c = ctx->c;
+    cudaStreamSynchronize(c.s0);
+    std::vector<std::pair<void*, int>> keep;
+    for (auto& a : ctx->allocs) {
+        if (group >= 0 && a.second != group) {
+            keep.push_back(a);
+            continue;
+        }
+        if (c.alloc.free) c.alloc.free(a.first, c.alloc.user);
+        else cudaFree(a.first);
+    }
+    ctx->allocs.swap(keep);
+}
+
+static void drop_graphs(Ctx& c) {
+    for (int p = 0; p < 2; p++) {
+        if (c.graph_ok[p]) cudaGraphExecDestroy(c.graph[p]);
+        c.graph_ok[p] = 0;
+    }
+}
+
+// Device status words written by kernels (sticky until particles are reset).
+static pibm_status device_status(pibm_ctx* ctx) {
+    Ctx& c = ctx->c;
+    cudaError_t e = cudaStreamSynchronize(c.s0);
+    if (e != cudaSuccess) return fail(ctx, PIBM_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+    int st[2] = {0, 0};
+    e = cudaMemcpy(st, c.dstat, sizeof(st), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(ctx, PIBM_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+    if (st[0] != 0) {
+        const char* what = st[1] == 1   ? "more than 64 neighbour candidates for one particle"
+                           : st[1] == 2 ? "a particle moved more than half the neighbour skin in one lattice step"
+                           : st[1] == 3 ? "neighbour list capacity exceeded"
+                                        : "neighbour list inconsistent";
+        return fail(ctx, (pibm_status)st[0], std::string("device check failed: ") + what);
+    }
+    return PIBM_OK;
+}
+
+static pibm_status check_config(pibm_ctx* ctx) {
+    Ctx& c = ctx->c;
+    for (int a = 0; a < c.D; a++)
+        if ((c.walls_kind[2 * a] == PIBM_PERIODIC) != (c.walls_kind[2 * a + 1] == PIBM_PERIODIC))
+            return fail(ctx, PIBM_ERR_STATE, "both faces of an axis must be periodic or both walls");
+    if (c.np > 0)
+        for (int a = 0; a < c.D; a++)
+            if (c.walls_kind[2 * a] == PIBM_PERIODIC)
+                return fail(ctx, PIBM_ERR_STATE, "particles require walls on every axis");
+    return PIBM_OK;
+}
+
+static void update_geo(Ctx& c) {
+    for (int a = 0; a < 3; a++) c.G.per[a] = (a >= c.D) ? 1 : (c.walls_kind[2 * a] == PIBM_PERIODIC);
+    c.G.iso = 0;
+    for (int f = 0; f < 6; f++) {
+        if ((f < 2 * c.D) && c.walls_kind[f] == PIBM_WALL && c.walls_therm[f] == PIBM_ISOTHERMAL) c.G.iso |= 1 << f;
+        c.G.dTw[f] = c.walls_T[f] - c.desc.T_ref;
+    }
+    for (int a = 0; a < 3; a++) {
+        c.dem.walled[a] = a < c.D && c.walls_kind[2 * a] == PIBM_WALL;
+        int n = a == 0 ? c.G.nx : (a == 1 ? c.G.ny : c.G.nz);
+        c.dem.lo[a] = -0.5;
+        c.dem.hi[a] = n - 0.5;
+    }
+}
+
+static int parity(const Ctx& c) { return (int)(c.t & 1); }
+
+// Coupling of the current time (after any change of state outside a step).
+static pibm_status prime(pibm_ctx* ctx) {
+    Ctx& c = ctx->c;
+    PCHECK(launch_coupling(&c, c.s0, parity(c)));
+    PCHECK(cudaStreamSynchronize(c.s0));
+    return PIBM_OK;
+}
+
+extern "C" {
+
+const char* pibm_status_string(pibm_status s) {
+    switch (s) {
+        case PIBM_OK: return "ok";
+        case PIBM_ERR_ARG: return "invalid argument";
+        case PIBM_ERR_OOM: return "out of device memory";
+        case PIBM_ERR_CUDA: return "CUDA error";
+        case PIBM_ERR_STATE: return "invalid state";
+        case PIBM_ERR_UNSTABLE: return "non-finite values";
+        case PIBM_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+int pibm_last_error(pibm_ctx* ctx, char* buf, size_t n) {
+    const std::string& s = ctx ? ctx->c.err : g_create_error;
+    if (buf && n) {
+        size_t k = std::min(n - 1, s.size());
+        memcpy(buf, s.data(), k);
+        buf[k] = 0;
+    }
+    return (int)s.size();
+}
+
+pibm_status pibm_create(const pibm_desc* d, void* stream, const pibm_allocator* alloc, pibm_ctx** out) {
+    if (!d || !out) return g_create_error = "null argument", PIBM_ERR_ARG;
+    *out = nullptr;
+    if ((d->dim != 2 && d->dim != 3) || d->nx < 1 || d->ny < 1 || d->nz < 1 || (d->dim == 2 && d->nz != 1))
+        return g_create_error = "invalid lattice size", PIBM_ERR_ARG;
+    if (d->storage != PIBM_STORE_F32 && d->storage != PIBM_STORE_F64)
+        return g_create_error = "invalid storage", PIBM_ERR_ARG;
+    if (!(d->Ra > 0) || !(d->Pr > 0) || !(d->U_c > 0) || !(d->L_c > 0) || d->gravity_axis < 0 ||
+        d->gravity_axis >= d->dim || d->dem_substeps < 1 || d->nu_dT == 0.0)
+        return g_create_error = "invalid physical parameters", PIBM_ERR_ARG;
+    if ((long long)d->nx * d->ny * d->nz > (1LL << 31) - 1) return g_create_error = "lattice too large", PIBM_ERR_ARG;
+
+    pibm_ctx* ctx = new pibm_ctx();
+    Ctx& c = ctx->c;
+    memset((void*)&c.desc, 0, sizeof(c.desc));
+    c.desc = *d;
+    c.D = d->dim;
+    c.Q = c.D == 2 ? 9 : 19;
+    c.QG = c.D == 2 ? 5 : 7;
+    c.G.nx = d->nx, c.G.ny = d->ny, c.G.nz = d->nz;
+    c.G.N = (long long)d->nx * d->ny * d->nz;
+    c.G.ntx = (d->nx + 31) / 32;
+    c.es = d->storage == PIBM_STORE_F64 ? 8 : 4;
+    // Eq lbm2.6: nu = U_c L_c sqrt(Pr / Ra); Eq lbm2.7 with Pr = nu / alpha
+    c.nu = d->U_c * d->L_c * sqrt(d->Pr / d->Ra);
+    c.alpha = c.nu / d->Pr;
+    c.tau_f = 3.0 * c.nu + 0.5;
+    c.tau_g = c.alpha * (c.D == 2 ? 3.0 : 4.0) + 0.5;
+    c.buoy = d->U_c * d->U_c / d->L_c;
+    c.t = 0;
+    c.alloc = alloc ? *alloc : pibm_allocator{nullptr, nullptr, nullptr};
+    for (int f = 0; f < 6; f++) c.walls_kind[f] = PIBM_PERIODIC, c.walls_therm[f] = PIBM_ADIABATIC, c.walls_T[f] = 0.0;
+    c.graph_ok[0] = c.graph_ok[1] = 0;
+    c.np = 0;
+    c.nm = 0;
+
+    cudaError_t e;
+    if (stream) {
+        c.s0 = (cudaStream_t)stream;
+    } else if ((e = cudaStreamCreateWithFlags(&c.s0, cudaStreamNonBlocking)) != cudaSuccess) {
+        delete ctx;
+        return g_create_error = cudaGetErrorString(e), PIBM_ERR_CUDA;
+    }
+    c.own_s0 = stream ? 0 : 1;
+    if ((e = cudaStreamCreateWithFlags(&c.s1, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming)) != cudaSuccess) {
+        delete ctx;
+        return g_create_error = cudaGetErrorString(e), PIBM_ERR_CUDA;
+    }
+    long long N = c.G.N;
+    c.f = dalloc(ctx, (size_t)c.Q * N * c.es, GRP_LATTICE);
+    c.g = dalloc(ctx, (size_t)c.QG * N * c.es, GRP_LATTICE);
+    c.fb = dalloc(ctx, (size_t)N * 4 * c.es, GRP_LATTICE);
+    c.mk = dalloc(ctx, (size_t)N * 4 * c.es, GRP_LATTICE);
+    c.flags = (uint8_t*)dalloc(ctx, (size_t)c.G.ntx * d->ny * d->nz, GRP_LATTICE);
+    c.red = (double*)dalloc(ctx, sizeof(double) * (4 * 512 + 16), GRP_LATTICE);
+    c.dstat = (int*)dalloc(ctx, sizeof(int) * 4, GRP_LATTICE);
+    c.nu_val = (double*)dalloc(ctx, sizeof(double) * 2, GRP_LATTICE);
+    c.nb_cur = (int*)dalloc(ctx, sizeof(int) * 2, GRP_LATTICE);
+    c.plane = nullptr;
+    if (!c.f || !c.g || !c.fb || !c.mk || !c.flags || !c.red || !c.dstat || !c.nu_val || !c.nb_cur) {
+        g_create_error = "device allocation failed";
+        pibm_destroy(ctx);
+        return PIBM_ERR_OOM;
+    }
+    update_geo(c);
+    c.dem.n = 0;
+    c.dem.dim = c.D;
+    c.dem.nsub = d->dem_substeps;
+    c.dem.dt = 1.0 / d->dem_substeps;
+    c.dem.law = PIBM_SPRING_DASHPOT;
+    if ((e = launch_init_equilibrium(&c)) != cudaSuccess || (e = cudaStreamSynchronize(c.s0)) != cudaSuccess) {
+        g_create_error = cudaGetErrorString(e);
+        pibm_destroy(ctx);
+        return PIBM_ERR_CUDA;
+    }
+    c.kernels_per_step = 1;
+    *out = ctx;
+    return PIBM_OK;
+}
+
+pibm_status pibm_destroy(pibm_ctx* ctx) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (c.s0) cudaStreamSynchronize(c.s0);
+    if (c.s1) cudaStreamSynchronize(c.s1);
+    drop_graphs(c);
+    dfree_group(ctx, -1);
+    if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+    if (c.ev_join) cudaEventDestroy(c.ev_join);
+    if (c.s1) cudaStreamDestroy(c.s1);
+    if (c.own_s0 && c.s0) cudaStreamDestroy(c.s0);
+    delete ctx;
+    return PIBM_OK;
+}
+
+pibm_status pibm_set_wall(pibm_ctx* ctx, int face, int kind, int thermal, double T_w) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (face < 0 || face >= 2 * c.D || (kind != PIBM_PERIODIC && kind != PIBM_WALL) ||
+        (thermal != PIBM_ADIABATIC && thermal != PIBM_ISOTHERMAL) || !isfinite(T_w))
+        return fail(ctx, PIBM_ERR_ARG, "invalid wall");
+    c.walls_kind[face] = kind;
+    c.walls_therm[face] = thermal;
+    c.walls_T[face] = T_w;
+    update_geo(c);
+    drop_graphs(c);
+    return prime(ctx);
+}
+
+pibm_status pibm_set_contact_law(pibm_ctx* ctx, int law, double E, double poisson, double mu, double kn, double kt,
+                                 double gamma_n, double gamma_t) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    if ((law != PIBM_SPRING_DASHPOT && law != PIBM_HERTZ_MD) || mu < 0 || (law == PIBM_HERTZ_MD && !(E > 0)) ||
+        (law == PIBM_HERTZ_MD && !(poisson > -1 && poisson < 1)) || (law == PIBM_SPRING_DASHPOT && !(kn >= 0)))
+        return fail(ctx, PIBM_ERR_ARG, "invalid contact law");
+    c.dem.law = law;
+    // text after Eq demgov: 1/E* = (1 - nu^2)/E_1 + (1 - nu^2)/E_2, same for G*; equal materials
+    double Estar = law == PIBM_HERTZ_MD ? E / (2.0 * (1.0 - poisson * poisson)) : 0.0;
+    double G = law == PIBM_HERTZ_MD ? E / (2.0 * (1.0 + poisson)) : 0.0;
+    double Gstar = law == PIBM_HERTZ_MD ? G / (2.0 * (1.0 - poisson * poisson)) : 0.0;
+    c.dem.E_star = (float)Estar;
+    c.dem.G_star = (float)Gstar;
+    c.dem.mu = (float)mu;
+    c.dem.kn = (float)kn;
+    c.dem.kt = (float)kt;
+    c.dem.gn = (float)gamma_n;
+    c.dem.gt = (float)gamma_t;
+    drop_graphs(c);
+    return PIBM_OK;
+}
+
+pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const double* U, const double* W, const double* R,
+                               const double* rho_p, const double* T_p, const double* heat_cap, const uint8_t* fixed) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (n < 0 || (n > 0 && (!X || !R || !rho_p))) return fail(ctx, PIBM_ERR_ARG, "invalid particle arrays");
+    if (n > 0 && c.nm > 0) return fail(ctx, PIBM_ERR_STATE, "static markers and particles cannot be combined");
+    int nn[3] = {c.G.nx, c.G.ny, c.G.nz};
+    double rmax = 0.0;
+    for (int p = 0; p < n; p++) {
+        if (!(R[p] > 0) || !(rho_p[p] > 0)) return fail(ctx, PIBM_ERR_ARG, "particle radius and density must be positive");
+        for (int a = 0; a < c.D; a++)
+            if (!(X[3 * p + a] > -0.5 && X[3 * p + a] < nn[a] - 0.5))
+                return fail(ctx, PIBM_ERR_ARG, "particle centre outside the domain");
+        rmax = std::max(rmax, R[p]);
+    }
+    if (n > 0)
+        for (int a = 0; a < c.D; a++)
+            if (c.walls_kind[2 * a] == PIBM_PERIODIC || c.walls_kind[2 * a + 1] == PIBM_PERIODIC)
+                return fail(ctx, PIBM_ERR_STATE, "particles require walls on every axis");
+    double cmin = c.desc.cell_size > 0 ? c.desc.cell_size : 2.0 * rmax + 1.5;
+    if (n > 0 && cmin < 2.0 * rmax + 1.0)
+        return fail(ctx, PIBM_ERR_ARG, "cell size must be at least the largest diameter plus one node");
+
+    drop_graphs(c);
+    dfree_group(ctx, GRP_PARTICLES);
+    c.np = 0;
+    c.dem.n = 0;
+    PCHECK(cudaMemsetAsync(c.mk, 0, (size_t)c.G.N * 4 * c.es, c.s0));
+    PCHECK(cudaMemsetAsync(c.fb, 0, (size_t)c.G.N * 4 * c.es, c.s0));
+    PCHECK(cudaMemsetAsync(c.flags, 0, (size_t)c.G.ntx * c.G.ny * c.G.nz, c.s0));
+    PCHECK(cudaMemsetAsync(c.dstat, 0, sizeof(int) * 4, c.s0));
+    PCHECK(cudaMemsetAsync(c.nb_cur, 0, sizeof(int) * 2, c.s0));
+    if (n == 0) return prime(ctx);
+
+    // host-side derived quantities (FP64): mass, moment of inertia, buoyant weight factor
+    const double PI = 3.14159265358979323846;
+    std::vector<double> hX(3 * n), hU(3 * n, 0.0), hW(3 * n, 0.0), hR(n), hrho(n), hT(n, 0.0), hC(n, 0.0), hm(n), hI(n), hmg(n);
+    std::vector<uint8_t> hfix(n, 0);
+    std::vector<int> hbox(6 * n);
+    for (int p = 0; p < n; p++) {
+        for (int a = 0; a < 3; a++) {
+            hX[3 * p + a] = X[3 * p + a];
+            if (U) hU[3 * p + a] = U[3 * p + a];
+            if (W) hW[3 * p + a] = W[3 * p + a];
+        }
+        if (c.D == 2) {
+            hX[3 * p + 2] = 0.0;
+            hU[3 * p + 2] = 0.0;
+            hW[3 * p] = hW[3 * p + 1] = 0.0;
+        }
+        hR[p] = R[p];
+        hrho[p] = rho_p[p];
+        if (T_p) hT[p] = T_p[p];
+        if (heat_cap) hC[p] = heat_cap[p];
+        if (fixed) hfix[p] = fixed[p];
+        if (c.D == 2) {
+            hm[p] = hrho[p] * PI * R[p] * R[p];
+            hI[p] = 0.5 * hm[p] * R[p] * R[p];
+        } else {
+            hm[p] = hrho[p] * 4.0 / 3.0 * PI * R[p] * R[p] * R[p];
+            hI[p] = 0.4 * hm[p] * R[p] * R[p];
+        }
+        hmg[p] = hm[p] * (1.0 - 1.0 / hrho[p]);  // Eq demgov: m (1 - rho_f / rho_p), rho_f = 1
+        for (int a = 0; a < 3; a++) hbox[6 * p + a] = 0, hbox[6 * p + 3 + a] = -1;
+    }
+    // cell grid: nc_a = floor(n_a / cell_min), side n_a / nc_a >= cell_min >= 2 R_max + skin
+    DemCfg& C = c.dem;
+    C.n = n;
+    C.dim = c.D;
+    C.nsub = c.desc.dem_substeps;
+    C.dt = 1.0 / c.desc.dem_substeps;
+    for (int a = 0; a < 3; a++) C.g[a] = c.desc.g_particle[a];
+    C.ncell = 1;
+    for (int a = 0; a < 3; a++) {
+        C.nc[a] = 1;
+        C.inv[a] = 1.0 / (double)nn[a];
+        if (a < c.D) {
+            C.nc[a] = std::max(1, (int)floor((double)nn[a] / cmin));
+            C.inv[a] = (double)C.nc[a] / (double)nn[a];
+        }
+        C.ncell *= C.nc[a];
+    }
+    C.skin = cmin - 2.0 * rmax;
+    C.cap = std::max(64, 16 * n);
+    C.maxnb = 64;
+    c.adj_cap = 2 * C.cap;
+    update_geo(c);
+
+    size_t v3 = sizeof(double) * 3 * (n + 1), v1 = sizeof(double) * (n + 1);
+    auto A = [&](size_t b) { return dalloc(ctx, b, GRP_PARTICLES); };
+    c.X = (double*)A(v3), c.U = (double*)A(v3), c.W = (double*)A(v3), c.Xb = (double*)A(v3);
+    c.R = (double*)A(v1), c.rho = (double*)A(v1), c.Tp = (double*)A(v1), c.Cp = (double*)A(v1);
+    c.m = (double*)A(v1), c.I = (double*)A(v1), c.mg = (double*)A(v1);
+    c.fixed = (uint8_t*)A(n + 1);
+    c.Fh = (double*)A(v3), c.Th = (double*)A(v3), c.Hh = (double*)A(v1), c.Fc = (double*)A(v3), c.Tc = (double*)A(v3);
+    c.box = (int*)A(sizeof(int) * 6 * (n + 1));
+    c.cell_of = (int*)A(sizeof(int) * (n + 1));
+    c.cell_cnt = (int*)A(sizeof(int) * (C.ncell + 1));
+    c.cell_start = (int*)A(sizeof(int) * (C.ncell + 2));
+    c.cell_ids = (int*)A(sizeof(int) * (n + 1));
+    c.cnt_hi = (int*)A(sizeof(int) * (n + 1));
+    c.cnt_lo = (int*)A(sizeof(int) * (n + 1));
+    for (int b = 0; b < 2; b++) {
+        c.nb_start[b] = (int*)A(sizeof(int) * (n + 2));
+        c.nb_i[b] = (int*)A(sizeof(int) * C.cap);
+        c.nb_j[b] = (int*)A(sizeof(int) * C.cap);
+        c.nb_ft[b] = (float*)A(sizeof(float) * 3 * C.cap);
+    }
+    c.adj_start = (int*)A(sizeof(int) * (n + 2));
+    c.adj_nb = (int*)A(sizeof(int) * c.adj_cap);
+    c.adj_k = (int*)A(sizeof(int) * c.adj_cap);
+    c.pF = (float*)A(sizeof(float) * 3 * C.cap);
+    c.pTi = (float*)A(sizeof(float) * 3 * C.cap);
+    c.pTj = (float*)A(sizeof(float) * 3 * C.cap);
+    c.wall_ft = (float*)A(sizeof(float) * 18 * (n + 1));
+    c.wF = (float*)A(sizeof(float) * 3 * (n + 1));
+    c.wT = (float*)A(sizeof(float) * 3 * (n + 1));
+    c.contact_pairs = (int*)A(sizeof(int) * 2 * C.cap);
+    c.contact_scratch = (int*)A(sizeof(int) * (2 * n + 8));
+    void* need[] = {c.X, c.U, c.W, c.Xb, c.R, c.rho, c.Tp, c.Cp, c.m, c.I, c.mg, c.fixed, c.Fh, c.Th, c.Hh, c.Fc,
+                    c.Tc, c.box, c.cell_of, c.cell_cnt, c.cell_start, c.cell_ids, c.cnt_hi, c.cnt_lo, c.nb_start[0],
+                    c.nb_start[1], c.nb_i[0], c.nb_i[1], c.nb_j[0], c.nb_j[1], c.nb_ft[0], c.nb_ft[1], c.adj_start,
+                    c.adj_nb, c.adj_k, c.pF, c.pTi, c.pTj, c.wall_ft, c.wF, c.wT, c.contact_pairs, c.contact_scratch};
+    for (void* p : need)
+        if (!p) {
+            dfree_group(ctx, GRP_PARTICLES);
+            return fail(ctx, PIBM_ERR_OOM, "particle buffers: device allocation failed");
+        }
+    auto up = [&](void* dst, const void* src, size_t b) { return cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, c.s0); };
+    PCHECK(up(c.X, hX.data(), sizeof(double) * 3 * n));
+    PCHECK(up(c.U, hU.data(), sizeof(double) * 3 * n));
+    PCHECK(up(c.W, hW.data(), sizeof(double) * 3 * n));
+    PCHECK(up(c.R, hR.data(), sizeof(double) * n));
+    PCHECK(up(c.rho, hrho.data(), sizeof(double) * n));
+    PCHECK(up(c.Tp, hT.data(), sizeof(double) * n));
+    PCHECK(up(c.Cp, hC.data(), sizeof(double) * n));
+    PCHECK(up(c.m, hm.data(), sizeof(double) * n));
+    PCHECK(up(c.I, hI.data(), sizeof(double) * n));
+    PCHECK(up(c.mg, hmg.data(), sizeof(double) * n));
+    PCHECK(up(c.fixed, hfix.data(), n));
+    PCHECK(up(c.box, hbox.data(), sizeof(int) * 6 * n));
+    PCHECK(cudaStreamSynchronize(c.s0));  // host vectors go out of scope
+    c.np = n;
+    // neighbour list at the initial positions, then the coupling of the current time
+    PCHECK(launch_dem(&c, c.s0, 0));
+    pibm_status st = device_status(ctx);
+    if (st != PIBM_OK) return st;
+    return prime(ctx);
+}
+
+pibm_status pibm_set_markers(pibm_ctx* ctx, int n, const double* X, const double* A, const double* T_p) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (n < 0 || (n > 0 && (!X || !A || !T_p))) return fail(ctx, PIBM_ERR_ARG, "invalid marker arrays");
+    if (n > 0 && c.np > 0) return fail(ctx, PIBM_ERR_STATE, "static markers and particles cannot be combined");
+    int nn[3] = {c.G.nx, c.G.ny, c.G.nz};
+    for (int l = 0; l < n; l++)
+        for (int a = 0; a < c.D; a++) {
+            double x = X[3 * l + a];
+            if (!isfinite(x)) return fail(ctx, PIBM_ERR_ARG, "non-finite marker position");
+            bool per = c.walls_kind[2 * a] == PIBM_PERIODIC;
+            if (!per && (floor(x) - 1 < 0 || floor(x) + 2 > nn[a] - 1))
+                return fail(ctx, PIBM_ERR_ARG, "marker interpolation stencil leaves the lattice");
+        }
+    drop_graphs(c);
+    dfree_group(ctx, GRP_MARKERS);
+    c.nm = 0;
+    PCHECK(cudaMemsetAsync(c.fb, 0, (size_t)c.G.N * 4 * c.es, c.s0));
+    PCHECK(cudaMemsetAsync(c.flags, 0, (size_t)c.G.ntx * c.G.ny * c.G.nz, c.s0));
+    if (n == 0) return prime(ctx);
+    // node -> (marker, weight) lists for the spreading gather; delta_h of Eq lbm12
+    const double PI = 3.14159265358979323846;
+    auto dh = [&](double a) { return fabs(a) <= 2.0 ? 0.25 * (1.0 + cos(PI * a / 2.0)) : 0.0; };
+    struct E3 { long long node; int l; double w; };
+    std::vector<E3> ent;
+    for (int l = 0; l < n; l++) {
+        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        for (int a = 0; a < c.D; a++) lo[a] = (int)ceil(X[3 * l + a] - 2.0), hi[a] = (int)floor(X[3 * l + a] + 2.0);
+        for (int z = lo[2]; z <= hi[2]; z++)
+            for (int y = lo[1]; y <= hi[1]; y++)
+                for (int x = lo[0]; x <= hi[0]; x++) {
+                    int cc[3] = {x, y, z};
+                    bool skip = false;
+                    for (int a = 0; a < c.D; a++) {
+                        if (cc[a] < 0 || cc[a] >= nn[a]) {
+                            if (c.walls_kind[2 * a] != PIBM_PERIODIC) skip = true;
+                            cc[a] = ((cc[a] % nn[a]) + nn[a]) % nn[a];
+                        }
+                    }
+                    if (skip) continue;
+                    double w = dh(x - X[3 * l]) * dh(y - X[3 * l + 1]);
+                    if (c.D == 3) w *= dh(z - X[3 * l + 2]);
+                    if (w == 0.0) continue;
+                    ent.push_back({node_index(c.G, cc[0], cc[1], cc[2]), l, w});
+                }
+    }
+    std::stable_sort(ent.begin(), ent.end(), [](const E3& a, const E3& b) { return a.node < b.node; });
+    std::vector<long long> nodes;
+    std::vector<int> start, mk;
+    std::vector<double> wt;
+    for (size_t k = 0; k < ent.size(); k++) {
+        if (k == 0 || ent[k].node != ent[k - 1].node) {
+            nodes.push_back(ent[k].node);
+            start.push_back((int)k);
+        }
+        mk.push_back(ent[k].l);
+        wt.push_back(ent[k].w);
+    }
+    start.push_back((int)ent.size());
+    std::vector<uint8_t> hflags((size_t)c.G.ntx * c.G.ny * c.G.nz, 0);
+    for (long long nd : nodes) {
+        long long x = nd % c.G.nx, yz = nd / c.G.nx;
+        hflags[yz * c.G.ntx + (x >> 5)] = 1;
+    }
+    std::vector<double> hX(3 * n);
+    for (int l = 0; l < n; l++)
+        for (int a = 0; a < 3; a++) hX[3 * l + a] = a < c.D ? X[3 * l + a] : 0.0;
+    c.n_csr_nodes = (int)nodes.size();
+    auto Al = [&](size_t b) { return dalloc(ctx, b, GRP_MARKERS); };
+    c.MX = (double*)Al(sizeof(double) * 3 * n);
+    c.MA = (double*)Al(sizeof(double) * n);
+    c.MT = (double*)Al(sizeof(double) * n);
+    c.nu_part = (double*)Al(sizeof(double) * n);
+    c.Ml = Al((size_t)n * 4 * c.es);
+    c.csr_node = (long long*)Al(sizeof(long long) * nodes.size());
+    c.csr_start = (int*)Al(sizeof(int) * start.size());
+    c.csr_marker = (int*)Al(sizeof(int) * mk.size());
+    c.csr_w = (double*)Al(sizeof(double) * wt.size());
+    if (!c.MX || !c.MA || !c.MT || !c.nu_part || !c.Ml || !c.csr_node || !c.csr_start || !c.csr_marker || !c.csr_w) {
+        dfree_group(ctx, GRP_MARKERS);
+        return fail(ctx, PIBM_ERR_OOM, "marker buffers: device allocation failed");
+    }
+    PCHECK(cudaMemcpy(c.MX, hX.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
+    PCHECK(cudaMemcpy(c.MA, A, sizeof(double) * n, cudaMemcpyHostToDevice));
+    PCHECK(cudaMemcpy(c.MT, T_p, sizeof(double) * n, cudaMemcpyHostToDevice));
+    PCHECK(cudaMemcpy(c.csr_node, nodes.data(), sizeof(long long) * nodes.size(), cudaMemcpyHostToDevice));
+    PCHECK(cudaMemcpy(c.csr_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice));
+    PCHECK(cudaMemcpy(c.csr_marker, mk.data(), sizeof(int) * mk.size(), cudaMemcpyHostToDevice));
+    PCHECK(cudaMemcpy(c.csr_w, wt.data(), sizeof(double) * wt.size(), cudaMemcpyHostToDevice));
+    PCHECK(cudaMemcpy(c.flags, hflags.data(), hflags.size(), cudaMemcpyHostToDevice));
+    c.nm = n;
+    return prime(ctx);
+}
+
+static pibm_status ensure_plane(pibm_ctx* ctx) {
+    Ctx& c = ctx->c;
+    if (!c.plane) c.plane = (double*)dalloc(ctx, sizeof(double) * c.G.N, GRP_SCRATCH);
+    return c.plane ? PIBM_OK : fail(ctx, PIBM_ERR_OOM, "read buffer: device allocation failed");
+}
+
+pibm_status pibm_set_populations(pibm_ctx* ctx, const double* f, const double* g) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    pibm_status st = ensure_plane(ctx);
+    if (st != PIBM_OK) return st;
+    for (int which = 0; which < 2; which++) {
+        const double* src = which == 0 ? f : g;
+        if (!src) continue;
+        int nq = which == 0 ? c.Q : c.QG;
+        for (int q = 0; q < nq; q++) {
+            PCHECK(cudaMemcpyAsync(c.plane, src + (size_t)q * c.G.N, sizeof(double) * c.G.N, cudaMemcpyHostToDevice, c.s0));
+            PCHECK(launch_write_plane(&c, which, q, parity(c)));
+        }
+    }
+    return prime(ctx);
+}
+
+static pibm_status capture(pibm_ctx* ctx, int par) {
+    Ctx& c = ctx->c;
+    cudaGraph_t graph;
+    PCHECK(cudaStreamBeginCapture(c.s0, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    int kernels = 1;
+    auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    chk(cudaEventRecord(c.ev_fork, c.s0));
+    chk(cudaStreamWaitEvent(c.s1, c.ev_fork, 0));
+    chk(launch_stream_collide(&c, c.s0, par));        // collide + stream, t -> t+1
+    if (c.np > 0) {
+        chk(launch_dem(&c, c.s1, c.desc.dem_substeps));  // particles t -> t+1, concurrent
+        kernels++;
+    }
+    chk(cudaEventRecord(c.ev_join, c.s1));
+    chk(cudaStreamWaitEvent(c.s0, c.ev_join, 0));
+    chk(launch_coupling(&c, c.s0, par ^ 1));         // coupling of time t+1
+    kernels += coupling_kernel_count(&c);
+    cudaError_t e2 = cudaStreamEndCapture(c.s0, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (e2 == cudaSuccess) cudaGraphDestroy(graph);
+        return fail(ctx, PIBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&c.graph[par], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(ctx, PIBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    c.graph_ok[par] = 1;
+    c.kernels_per_step = kernels;
+    return PIBM_OK;
+}
+
+pibm_status pibm_step(pibm_ctx* ctx, int nsteps) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (nsteps < 0) return fail(ctx, PIBM_ERR_ARG, "negative step count");
+    pibm_status st = check_config(ctx);
+    if (st != PIBM_OK) return st;
+    for (int k = 0; k < nsteps; k++) {
+        int par = parity(c);
+        if (!c.graph_ok[par]) {
+            st = capture(ctx, par);
+            if (st != PIBM_OK) return st;
+        }
+        PCHECK(cudaGraphLaunch(c.graph[par], c.s0));
+        c.t++;
+    }
+    return PIBM_OK;
+}
+
+pibm_status pibm_step_timed(pibm_ctx* ctx, double* ms) {
+    if (!ctx || !ms) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    pibm_status st = check_config(ctx);
+    if (st != PIBM_OK) return st;
+    cudaEvent_t ev[8];
+    for (int k = 0; k < 8; k++) PCHECK(cudaEventCreate(&ev[k]));
+    int par = parity(c);
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    chk(cudaEventRecord(ev[0], c.s0));
+    chk(cudaStreamWaitEvent(c.s1, ev[0], 0));
+    chk(launch_stream_collide(&c, c.s0, par));
+    chk(cudaEventRecord(ev[1], c.s0));
+    chk(cudaEventRecord(ev[2], c.s1));
+    chk(launch_dem(&c, c.s1, c.desc.dem_substeps));
+    chk(cudaEventRecord(ev[3], c.s1));
+    chk(cudaStreamWaitEvent(c.s0, ev[3], 0));
+    chk(cudaEventRecord(ev[4], c.s0));
+    chk(launch_coupling(&c, c.s0, par ^ 1));
+    chk(cudaEventRecord(ev[5], c.s0));
+    chk(cudaEventSynchronize(ev[5]));
+    float t[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) {
+        chk(cudaEventElapsedTime(&t[0], ev[0], ev[1]));
+        chk(cudaEventElapsedTime(&t[1], ev[2], ev[3]));
+        chk(cudaEventElapsedTime(&t[2], ev[4], ev[5]));
+        chk(cudaEventElapsedTime(&t[3], ev[0], ev[5]));
+    }
+    for (int k = 0; k < 8; k++) cudaEventDestroy(ev[k]);
+    if (e != cudaSuccess) return fail(ctx, PIBM_ERR_CUDA, std::string("timed step: ") + cudaGetErrorString(e));
+    for (int k = 0; k < 4; k++) ms[k] = t[k];
+    c.t++;
+    return device_status(ctx);
+}
+
+pibm_status pibm_read_field(pibm_ctx* ctx, int field, double* dst, size_t n) {
+    if (!ctx || !dst) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (field < PIBM_RHO || field > PIBM_QB || n != (size_t)c.G.N) return fail(ctx, PIBM_ERR_ARG, "invalid field request");
+    pibm_status st = ensure_plane(ctx);
+    if (st != PIBM_OK) return st;
+    PCHECK(launch_macro(&c, field, parity(c)));
+    PCHECK(cudaMemcpyAsync(dst, c.plane, sizeof(double) * n, cudaMemcpyDeviceToHost, c.s0));
+    return device_status(ctx);
+}
+
+pibm_status pibm_read_populations(pibm_ctx* ctx, double* f, double* g) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    pibm_status st = ensure_plane(ctx);
+    if (st != PIBM_OK) return st;
+    for (int which = 0; which < 2; which++) {
+        double* dst = which == 0 ? f : g;
+        if (!dst) continue;
+        int nq = which == 0 ? c.Q : c.QG;
+        for (int q = 0; q < nq; q++) {
+            PCHECK(launch_read_plane(&c, which, q, parity(c)));
+            PCHECK(cudaMemcpyAsync(dst + (size_t)q * c.G.N, c.plane, sizeof(double) * c.G.N, cudaMemcpyDeviceToHost, c.s0));
+        }
+    }
+    return device_status(ctx);
+}
+
+pibm_status pibm_read_particles(pibm_ctx* ctx, double* X, double* U, double* W, double* T_p) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    int n = c.np;
+    if (n > 0) {
+        if (X) PCHECK(cudaMemcpyAsync(X, c.X, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c.s0));
+        if (U) PCHECK(cudaMemcpyAsync(U, c.U, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c.s0));
+        if (W) PCHECK(cudaMemcpyAsync(W, c.W, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c.s0));
+        if (T_p) PCHECK(cudaMemcpyAsync(T_p, c.Tp, sizeof(double) * n, cudaMemcpyDeviceToHost, c.s0));
+    }
+    return device_status(ctx);
+}
+
+pibm_status pibm_read_particle_forces(pibm_ctx* ctx, double* F, double* T, double* H) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    int n = c.np;
+    if (n > 0) {
+        if (F) PCHECK(cudaMemcpyAsync(F, c.Fh, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c.s0));
+        if (T) PCHECK(cudaMemcpyAsync(T, c.Th, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c.s0));
+        if (H) PCHECK(cudaMemcpyAsync(H, c.Hh, sizeof(double) * n, cudaMemcpyDeviceToHost, c.s0));
+    }
+    return device_status(ctx);
+}
+
+pibm_status pibm_nusselt(pibm_ctx* ctx, double* nu) {
+    if (!ctx || !nu) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    *nu = 0.0;
+    if (c.nm > 0) PCHECK(cudaMemcpyAsync(nu, c.nu_val, sizeof(double), cudaMemcpyDeviceToHost, c.s0));
+    return device_status(ctx);
+}
+
+pibm_status pibm_read_contacts(pibm_ctx* ctx, int32_t* pairs, int cap, int* n_out) {
+    if (!ctx || !n_out || cap < 0 || (cap > 0 && !pairs)) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    *n_out = 0;
+    if (c.np == 0) return device_status(ctx);
+    pibm_status st = device_status(ctx);
+    if (st != PIBM_OK) return st;
+    PCHECK(launch_contacts(&c, c.contact_pairs, c.dem.cap, c.contact_scratch));
+    int total = 0;
+    PCHECK(cudaMemcpyAsync(&total, c.contact_scratch, sizeof(int), cudaMemcpyDeviceToHost, c.s0));
+    PCHECK(cudaStreamSynchronize(c.s0));
+    *n_out = total;
+    int k = std::min(cap, total);
+    if (k > 0) PCHECK(cudaMemcpy(pairs, c.contact_pairs, sizeof(int) * 2 * k, cudaMemcpyDeviceToHost));
+    return device_status(ctx);
+}
+
+pibm_status pibm_read_cells(pibm_ctx* ctx, int32_t* cell, int32_t* ncell) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (ncell)
+        for (int a = 0; a < 3; a++) ncell[a] = c.np > 0 ? c.dem.nc[a] : 0;
+    if (c.np > 0 && cell) PCHECK(cudaMemcpyAsync(cell, c.cell_of, sizeof(int) * c.np, cudaMemcpyDeviceToHost, c.s0));
+    return device_status(ctx);
+}
+
+pibm_status pibm_diagnostics(pibm_ctx* ctx, double* out) {
+    if (!ctx || !out) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    PCHECK(launch_diagnostics(&c, parity(c)));
+    PCHECK(cudaMemcpyAsync(out, c.red + 4 * 512, sizeof(double) * 6, cudaMemcpyDeviceToHost, c.s0));
+    pibm_status st = device_status(ctx);
+    if (st != PIBM_OK) return st;
+    if (out[5] != 0.0) return fail(ctx, PIBM_ERR_UNSTABLE, "non-finite values in the lattice or particle state");
+    return PIBM_OK;
+}
+
+pibm_status pibm_relaxation(pibm_ctx* ctx, double* out) {
+    if (!ctx || !out) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    out[0] = c.nu, out[1] = c.alpha, out[2] = c.tau_f, out[3] = c.tau_g, out[4] = c.buoy;
+    return PIBM_OK;
+}
+
+pibm_status pibm_time(pibm_ctx* ctx, int64_t* t) {
+    if (!ctx || !t) return PIBM_ERR_ARG;
+    *t = ctx->c.t;
+    return PIBM_OK;
+}
+
+pibm_status pibm_kernels_per_step(pibm_ctx* ctx, int* n) {
+    if (!ctx || !n) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    *n = 1 + (c.np > 0 ? 1 : 0) + coupling_kernel_count(&c);
+    return PIBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,353 @@
+// PIBM coupling kernels (Section 2.2, Eqs lbm5-lbm13).
+//
+// Resolved particles: every lattice node a particle covers is a PIBM point of
+// area eps = clamp(R + 1/2 - |r - X|, 0, 1); a node shared by two footprints
+// belongs to the particle with the larger eps (ties: lower index).  At a node
+// the interpolation of Eqs lbm5/lbm5.5 is the identity, and Eqs lbm7 + lbm8
+// give the force density F_f = 2 (rho U_l - j); Eq lbm7.5 gives the heat
+// source Q = 2 kappa_T (T_p - T).  Three kernels, one CTA per particle, no
+// atomics:
+//   clear     : zero the marker field, F_B / Q_B and tile flags on the boxes
+//               recorded in the previous step;
+//   footprint : ownership test against the particle's neighbours, marker
+//               values eps (F_f, Q) for the nodes it owns, and the FP64 block
+//               reduction to force, torque and heat release (Eq lbm13);
+//   spread    : F_B(r) = sum_d W(d) M(r + d), W = product of delta_h weights
+//               1/2, 1/4, 1/4 (Eqs lbm10-lbm12, lbm12.6) over the footprint
+//               grown by one node; overlapping boxes write identical values.
+//
+// Static off-node markers (the cavity cylinder): one thread per marker does
+// the 4-point Lagrange interpolation (Eq lbm6) and forms A (F_f, Q); spreading
+// is a gather over a precomputed node -> marker list in marker order.
+#include "pibm_internal.cuh"
+
+namespace pibm {
+
+constexpr int CP_THREADS = 256;
+constexpr int CP_MAXNB = 64;
+
+__device__ __forceinline__ double eps_of(double x, double y, double z, const double* Xp, double Rp) {
+    double dx = __dsub_rn(x, Xp[0]), dy = __dsub_rn(y, Xp[1]), dz = __dsub_rn(z, Xp[2]);
+    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    double e = __dsub_rn(__dadd_rn(Rp, 0.5), __dsqrt_rn(d2));
+    return e > 1.0 ? 1.0 : e;
+}
+
+__device__ __forceinline__ void footprint_box(const Geo& G, int D, const double* X, double R, int* lo, int* hi) {
+    int n[3] = {G.nx, G.ny, G.nz};
+    for (int a = 0; a < 3; a++) {
+        if (a < D) {
+            lo[a] = (int)ceil(X[a] - R - 0.5);
+            hi[a] = (int)floor(X[a] + R + 0.5);
+            if (lo[a] < 0) lo[a] = 0;
+            if (hi[a] > n[a] - 1) hi[a] = n[a] - 1;
+        } else {
+            lo[a] = hi[a] = 0;
+        }
+    }
+}
+
+template <typename V>
+__device__ __forceinline__ V zero4();
+template <> __device__ __forceinline__ float4 zero4<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <> __device__ __forceinline__ double4_32a zero4<double4_32a>() { return make_double4_32a(0., 0., 0., 0.); }
+
+template <typename V>
+__global__ void __launch_bounds__(CP_THREADS) k_clear(Geo G, const int* __restrict__ box, V* mk, V* fb, uint8_t* flags) {
+    const int p = blockIdx.x;
+    int lo[3] = {box[6 * p], box[6 * p + 1], box[6 * p + 2]}, hi[3] = {box[6 * p + 3], box[6 * p + 4], box[6 * p + 5]};
+    if (hi[0] < lo[0]) return;
+    int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
+    long long cnt = (long long)ex * ey * ez;
+    for (long long q = threadIdx.x; q < cnt; q += blockDim.x) {
+        int x = lo[0] + (int)(q % ex), y = lo[1] + (int)((q / ex) % ey), z = lo[2] + (int)(q / ((long long)ex * ey));
+        long long n = node_index(G, x, y, z);
+        mk[n] = zero4<V>();
+        fb[n] = zero4<V>();
+        flags[((long long)z * G.ny + y) * G.ntx + (x >> 5)] = 0;
+    }
+}
+
+template <int D, typename S>
+__global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __restrict__ f, const S* __restrict__ g,
+                                                          typename Vec4<S>::T* __restrict__ mk,
+                                                          const double* __restrict__ X, const double* __restrict__ U,
+                                                          const double* __restrict__ W, const double* __restrict__ Rr,
+                                                          const double* __restrict__ Tp, const int* __restrict__ adj_start,
+                                                          const int* __restrict__ adj_nb, double kappa, double Tref,
+                                                          int parity, double* Fh, double* Th, double* Hh) {
+    using L = Lat<D>;
+    using R = S;
+    __shared__ double sh_nb[CP_MAXNB][4];
+    __shared__ int sh_id[CP_MAXNB];
+    __shared__ double red[7][CP_THREADS / 32];
+    const int p = blockIdx.x;
+    const double Xp[3] = {X[3 * p], X[3 * p + 1], X[3 * p + 2]};
+    const double Rp = Rr[p];
+    const int a0 = adj_start[p];
+    int nnb = adj_start[p + 1] - a0;
+    if (nnb > CP_MAXNB) nnb = CP_MAXNB;  // the neighbour build rejects more
+    for (int k = threadIdx.x; k < nnb; k += blockDim.x) {
+        int q = adj_nb[a0 + k];
+        sh_id[k] = q;
+        sh_nb[k][0] = X[3 * q];
+        sh_nb[k][1] = X[3 * q + 1];
+        sh_nb[k][2] = X[3 * q + 2];
+        sh_nb[k][3] = Rr[q];
+    }
+    __syncthreads();
+    int lo[3], hi[3];
+    footprint_box(G, D, Xp, Rp, lo, hi);
+    int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
+    long long cnt = (ex > 0 && ey > 0 && ez > 0) ? (long long)ex * ey * ez : 0;
+    const double Up[3] = {U[3 * p], U[3 * p + 1], U[3 * p + 2]};
+    const double Wp[3] = {W[3 * p], W[3 * p + 1], W[3 * p + 2]};
+    const double Tpp = Tp[p];
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (long long q = threadIdx.x; q < cnt; q += blockDim.x) {
+        int x = lo[0] + (int)(q % ex), y = lo[1] + (int)((q / ex) % ey), z = lo[2] + (int)(q / ((long long)ex * ey));
+        double eps = eps_of((double)x, (double)y, (double)z, Xp, Rp);
+        if (!(eps > 0.0)) continue;
+        bool own = true;
+        for (int k = 0; k < nnb; k++) {
+            double e2 = eps_of((double)x, (double)y, (double)z, sh_nb[k], sh_nb[k][3]);
+            if (e2 > eps || (e2 == eps && sh_id[k] < p)) {
+                own = false;
+                break;
+            }
+        }
+        if (!own) continue;
+        R s[L::Q], sg[L::QG];
+        load_node<D, S, R>(G, f, g, x, y, z, parity, s, sg);
+        R drho = 0, j[3] = {0, 0, 0}, dT = 0;
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) {
+            drho += s[i];
+            if (L::ex(i)) j[0] += L::ex(i) * s[i];
+            if (L::ey(i)) j[1] += L::ey(i) * s[i];
+            if (L::ez(i)) j[2] += L::ez(i) * s[i];
+        }
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) dT += sg[k];
+        const R rho = (R)1 + drho;
+        const double arm[3] = {x - Xp[0], y - Xp[1], z - Xp[2]};
+        // U_l = U_p + omega_p x (r - X_p)
+        const double Ul[3] = {Up[0] + (Wp[1] * arm[2] - Wp[2] * arm[1]), Up[1] + (Wp[2] * arm[0] - Wp[0] * arm[2]),
+                              Up[2] + (Wp[0] * arm[1] - Wp[1] * arm[0])};
+        const R e = (R)eps;
+        R M[4];
+#pragma unroll
+        for (int a = 0; a < 3; a++) M[a] = e * (R)2 * (rho * (R)Ul[a] - j[a]);      // eps F_f (Eqs lbm7, lbm8)
+        M[3] = e * (R)2 * (R)kappa * ((R)(Tpp - Tref) - dT);                       // eps Q (Eq lbm7.5)
+        if (D == 2) M[2] = 0;
+        typename Vec4<S>::T mv;
+        mv.x = M[0], mv.y = M[1], mv.z = M[2], mv.w = M[3];
+        mk[node_index(G, x, y, z)] = mv;
+        // Eq lbm13 and the torque about the centre, accumulated in FP64
+        double MF[3] = {(double)M[0], (double)M[1], (double)M[2]};
+        acc[0] -= MF[0];
+        acc[1] -= MF[1];
+        acc[2] -= MF[2];
+        acc[3] -= arm[1] * MF[2] - arm[2] * MF[1];
+        acc[4] -= arm[2] * MF[0] - arm[0] * MF[2];
+        acc[5] -= arm[0] * MF[1] - arm[1] * MF[0];
+        acc[6] += (double)M[3];
+    }
+    // FP64 block reduction: warp shuffles, then one value per warp in shared memory
+#pragma unroll
+    for (int a = 0; a < 7; a++) {
+        double v = acc[a];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        double v = 0;
+        for (int w = 0; w < CP_THREADS / 32; w++) v += red[threadIdx.x][w];
+        if (threadIdx.x < 3) Fh[3 * p + threadIdx.x] = v;
+        else if (threadIdx.x < 6) Th[3 * p + threadIdx.x - 3] = v;
+        else Hh[p] = v;
+    }
+}
+
+template <int D, typename V>
+__global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __restrict__ X, const double* __restrict__ Rr,
+                                                       const V* __restrict__ mk, V* __restrict__ fb, uint8_t* flags, int* box) {
+    const int p = blockIdx.x;
+    const double Xp[3] = {X[3 * p], X[3 * p + 1], X[3 * p + 2]};
+    int lo[3], hi[3];
+    footprint_box(G, D, Xp, Rr[p], lo, hi);
+    int n[3] = {G.nx, G.ny, G.nz};
+    for (int a = 0; a < D; a++) {
+        lo[a] = max(lo[a] - 1, 0);
+        hi[a] = min(hi[a] + 1, n[a] - 1);
+    }
+    if (threadIdx.x == 0) {
+        for (int a = 0; a < 3; a++) {
+            box[6 * p + a] = lo[a];
+            box[6 * p + 3 + a] = hi[a];
+        }
+    }
+    int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
+    if (ex <= 0 || ey <= 0 || ez <= 0) return;
+    long long cnt = (long long)ex * ey * ez;
+    for (long long q = threadIdx.x; q < cnt; q += blockDim.x) {
+        int x = lo[0] + (int)(q % ex), y = lo[1] + (int)((q / ex) % ey), z = lo[2] + (int)(q / ((long long)ex * ey));
+        decltype(V().x) s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); dz++) {
+            int zz = z + dz;
+            if (zz < 0 || zz >= G.nz) continue;
+            for (int dy = -1; dy <= 1; dy++) {
+                int yy = y + dy;
+                if (yy < 0 || yy >= G.ny) continue;
+                for (int dx = -1; dx <= 1; dx++) {
+                    int xx = x + dx;
+                    if (xx < 0 || xx >= G.nx) continue;
+                    // delta_h(0) = 1/2, delta_h(+-1) = 1/4 (Eq lbm12)
+                    decltype(V().x) w = (dx == 0 ? 0.5 : 0.25) * (dy == 0 ? 0.5 : 0.25);
+                    if (D == 3) w *= (dz == 0 ? 0.5 : 0.25);
+                    V m = mk[node_index(G, xx, yy, zz)];
+                    s0 += w * m.x;
+                    s1 += w * m.y;
+                    s2 += w * m.z;
+                    s3 += w * m.w;
+                }
+            }
+        }
+        V out;
+        out.x = s0, out.y = s1, out.z = s2, out.w = s3;
+        fb[node_index(G, x, y, z)] = out;
+        flags[((long long)z * G.ny + y) * G.ntx + (x >> 5)] = 1;
+    }
+}
+
+// ------------------------------------------------------- static markers
+template <int D, typename S>
+__global__ void __launch_bounds__(CP_THREADS) k_markers(Geo G, const S* __restrict__ f, const S* __restrict__ g,
+                                                        int nm, const double* __restrict__ MX, const double* __restrict__ MA,
+                                                        const double* __restrict__ MT, double kappa, double Tref, int parity,
+                                                        typename Vec4<S>::T* Ml, double* nu_part) {
+    using L = Lat<D>;
+    using R = S;
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nm) return;
+    double Xl[3] = {MX[3 * l], MX[3 * l + 1], MX[3 * l + 2]};
+    double Lw[3][4];
+    int base[3] = {0, 0, 0};
+    for (int a = 0; a < D; a++) {
+        base[a] = (int)floor(Xl[a]) - 1;
+        for (int k = 0; k < 4; k++) {  // Eq lbm6, four points per axis
+            double Lk = 1.0;
+            for (int mm = 0; mm < 4; mm++)
+                if (mm != k) Lk *= (Xl[a] - (base[a] + mm)) / (double)(k - mm);
+            Lw[a][k] = Lk;
+        }
+    }
+    R fl[L::Q], gl[L::QG];
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) fl[i] = 0;
+#pragma unroll
+    for (int k = 0; k < L::QG; k++) gl[k] = 0;
+    int nn[3] = {G.nx, G.ny, G.nz};
+    for (int kz = 0; kz < (D == 3 ? 4 : 1); kz++)
+        for (int ky = 0; ky < 4; ky++)
+            for (int kx = 0; kx < 4; kx++) {
+                int c[3] = {base[0] + kx, base[1] + ky, D == 3 ? base[2] + kz : 0};
+                for (int a = 0; a < D; a++) c[a] = ((c[a] % nn[a]) + nn[a]) % nn[a];
+                R wgt = (R)(Lw[0][kx] * Lw[1][ky] * (D == 3 ? Lw[2][kz] : 1.0));
+                R s[L::Q], sg[L::QG];
+                load_node<D, S, R>(G, f, g, c[0], c[1], c[2], parity, s, sg);
+#pragma unroll
+                for (int i = 0; i < L::Q; i++) fl[i] += wgt * s[i];
+#pragma unroll
+                for (int k = 0; k < L::QG; k++) gl[k] += wgt * sg[k];
+            }
+    R j[3] = {0, 0, 0}, dT = 0;
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+        if (L::ex(i)) j[0] += L::ex(i) * fl[i];
+        if (L::ey(i)) j[1] += L::ey(i) * fl[i];
+        if (L::ez(i)) j[2] += L::ez(i) * fl[i];
+    }
+#pragma unroll
+    for (int k = 0; k < L::QG; k++) dT += gl[k];
+    const R A = (R)MA[l];
+    const R dTp = (R)(MT[l] - Tref) - dT;  // T_p - T_l
+    typename Vec4<S>::T mv;
+    mv.x = A * (R)(-2) * j[0];  // static marker: U_l = 0, F_f = -2 j
+    mv.y = A * (R)(-2) * j[1];
+    mv.z = D == 3 ? A * (R)(-2) * j[2] : (R)0;
+    mv.w = A * (R)2 * (R)kappa * dTp;
+    Ml[l] = mv;
+    nu_part[l] = (double)A * (double)dTp;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(CP_THREADS) k_marker_spread(int nn, const long long* __restrict__ node, const int* __restrict__ start,
+                                                              const int* __restrict__ marker, const double* __restrict__ w,
+                                                              const V* __restrict__ Ml, V* fb) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nn) return;
+    decltype(V().x) s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    for (int k = start[q]; k < start[q + 1]; k++) {
+        V m = Ml[marker[k]];
+        decltype(V().x) wk = (decltype(V().x))w[k];
+        s0 += wk * m.x;
+        s1 += wk * m.y;
+        s2 += wk * m.z;
+        s3 += wk * m.w;
+    }
+    V out;
+    out.x = s0, out.y = s1, out.z = s2, out.w = s3;
+    fb[node[q]] = out;
+}
+
+__global__ void __launch_bounds__(CP_THREADS) k_nu_reduce(const double* part, int nm, double scale, double* out) {
+    __shared__ double sh[CP_THREADS];
+    double v = 0;
+    for (int l = threadIdx.x; l < nm; l += blockDim.x) v += part[l];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = CP_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0] * scale;
+}
+
+template <int D, typename S>
+static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
+    using V = typename Vec4<S>::T;
+    if (!c->desc.pibm) return cudaSuccess;
+    if (c->np > 0) {
+        k_clear<V><<<c->np, CP_THREADS, 0, s>>>(c->G, c->box, (V*)c->mk, (V*)c->fb, c->flags);
+        k_footprint<D, S><<<c->np, CP_THREADS, 0, s>>>(c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk, c->X, c->U, c->W,
+                                                       c->R, c->Tp, c->adj_start, c->adj_nb, c->desc.kappa_T,
+                                                       c->desc.T_ref, parity, c->Fh, c->Th, c->Hh);
+        k_spread<D, V><<<c->np, CP_THREADS, 0, s>>>(c->G, c->X, c->R, (const V*)c->mk, (V*)c->fb, c->flags, c->box);
+    }
+    if (c->nm > 0) {
+        int nb = (c->nm + CP_THREADS - 1) / CP_THREADS;
+        k_markers<D, S><<<nb, CP_THREADS, 0, s>>>(c->G, (const S*)c->f, (const S*)c->g, c->nm, c->MX, c->MA, c->MT,
+                                                  c->desc.kappa_T, c->desc.T_ref, parity, (V*)c->Ml, c->nu_part);
+        int nn = c->n_csr_nodes;
+        if (nn > 0)
+            k_marker_spread<V><<<(nn + CP_THREADS - 1) / CP_THREADS, CP_THREADS, 0, s>>>(nn, c->csr_node, c->csr_start, c->csr_marker,
+                                                                                   c->csr_w, (const V*)c->Ml, (V*)c->fb);
+        k_nu_reduce<<<1, CP_THREADS, 0, s>>>(c->nu_part, c->nm, 1.0 / (c->alpha * c->desc.nu_dT), c->nu_val);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coupling(Ctx* c, cudaStream_t s, int parity) {
+    bool dbl = c->desc.storage == PIBM_STORE_F64;
+    if (c->D == 2) return dbl ? coupling_impl<2, double>(c, s, parity) : coupling_impl<2, float>(c, s, parity);
+    return dbl ? coupling_impl<3, double>(c, s, parity) : coupling_impl<3, float>(c, s, parity);
+}
+
+int coupling_kernel_count(Ctx* c) {
+    if (!c->desc.pibm) return 0;
+    return (c->np > 0 ? 3 : 0) + (c->nm > 0 ? 3 : 0);
+}
+
+}  // namespace pibm

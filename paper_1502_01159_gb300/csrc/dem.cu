@@ -1,0 +1,578 @@
+// DEM kernels (Section 2.3, Eq demgov; Hertz normal law and
+// Mindlin-Deresiewicz loading stiffness, or a linear spring-dashpot law).
+//
+// One launch per lattice step runs as a thread-block cluster (up to 8 CTAs on
+// 8 SMs) and synchronises with the hardware cluster barrier, so all substeps
+// and the neighbour-list rebuild run without returning to the host:
+//   for each substep: half kick + drift (FP64), pair forces over the canonical
+//   neighbour list (pairs i < j, FP64 contact test, FP32 force law, tangential
+//   history per pair), per-particle sums in a fixed order over each particle's
+//   adjacency (so pair forces are applied with exactly opposite signs and no
+//   atomics), half kick;
+//   then the thermosensitive update C_p dT_p = -H_p and the rebuild at the new
+//   positions: cell ids (FP64, no contraction), counting sort stable by
+//   particle index, neighbour pairs within R_i + R_j + skin sorted by (i, j),
+//   tangential history carried over by binary search in the previous list.
+// The skin is the cell side minus the largest diameter; a particle that moves
+// more than half the skin within one lattice step raises a status word.
+#include <cooperative_groups.h>
+
+#include "pibm_internal.cuh"
+
+namespace pibm {
+
+constexpr int DEM_T = 256;
+constexpr int DEM_MAXNB = 64;
+
+struct DemState {
+    double *X, *U, *W, *Xb, *R, *m, *I, *mg, *Tp, *Cp, *Fh, *Th, *Hh, *Fc, *Tc;
+    const uint8_t* fixed;
+    int *cell_of, *cell_cnt, *cell_start, *cell_ids, *cnt_hi, *cnt_lo;
+    int *nb_start0, *nb_start1, *nb_i0, *nb_i1, *nb_j0, *nb_j1;
+    float *nb_ft0, *nb_ft1;
+    int* nb_cur;
+    int *adj_start, *adj_nb, *adj_k;
+    float *pF, *pTi, *pTj, *wall_ft, *wF, *wT;
+    int* dstat;
+    int* flag;  // cluster-wide overflow flag
+    int adj_cap;
+};
+
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void set_error(int* dstat, int detail) {
+    if (atomicCAS(dstat, 0, (int)PIBM_ERR_STATE) == 0) dstat[1] = detail;
+}
+
+// exclusive scan of in[0..M) into out[0..M] (out[M] = total) by one CTA
+__device__ void cta_scan(const int* in, int* out, int M, int* sh) {
+    const int T = blockDim.x, t = threadIdx.x;
+    const int chunk = (M + T - 1) / T;
+    const int b = min(M, t * chunk), e = min(M, b + chunk);
+    int s = 0;
+    for (int i = b; i < e; i++) s += in[i];
+    sh[t] = s;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {
+        int v = t >= off ? sh[t - off] : 0;
+        __syncthreads();
+        sh[t] += v;
+        __syncthreads();
+    }
+    int base = t ? sh[t - 1] : 0;
+    for (int i = b; i < e; i++) {
+        int v = in[i];
+        out[i] = base;
+        base += v;
+    }
+    if (t == T - 1) out[M] = sh[T - 1];
+    __syncthreads();
+}
+
+// FP64 squared distance with the oracle's operation order (no contraction)
+__device__ __forceinline__ double dist2(const double* Xi, const double* Xj) {
+    double dx = __dsub_rn(Xj[0], Xi[0]), dy = __dsub_rn(Xj[1], Xi[1]), dz = __dsub_rn(Xj[2], Xi[2]);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+__device__ __forceinline__ void ldX(const double* X, int p, double* o) {
+    o[0] = __ldcg(X + 3 * p);
+    o[1] = __ldcg(X + 3 * p + 1);
+    o[2] = __ldcg(X + 3 * p + 2);
+}
+
+__device__ __forceinline__ float3 f3(float a, float b, float c) { return make_float3(a, b, c); }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// Contact law in FP32: returns F_n and the tangential stiffness.
+__device__ __forceinline__ float normal_law(const DemCfg& C, float delta, float vn, float Rstar, float* kt_eff) {
+    if (C.law == PIBM_HERTZ_MD) {
+        *kt_eff = 8.0f * C.G_star * sqrtf(delta * Rstar);
+        return (4.0f / 3.0f) * C.E_star * sqrtf(Rstar) * delta * sqrtf(delta) + C.gn * vn;
+    }
+    *kt_eff = C.kt;
+    return C.kn * delta + C.gn * vn;
+}
+
+// Tangential force: history projected on the tangent plane, incremented by
+// -k_t v_t dt, capped at mu |F_n|; returns the total with tangential damping.
+__device__ __forceinline__ float3 tangential(const DemCfg& C, float* ft, float3 n, float3 vt, float kt_eff, float Fn, float dt) {
+    float3 h = f3(ft[0], ft[1], ft[2]);
+    float hn = h.x * n.x + h.y * n.y + h.z * n.z;
+    h = f3(h.x - hn * n.x - kt_eff * vt.x * dt, h.y - hn * n.y - kt_eff * vt.y * dt, h.z - hn * n.z - kt_eff * vt.z * dt);
+    float mag = sqrtf(h.x * h.x + h.y * h.y + h.z * h.z);
+    float cap = C.mu * fabsf(Fn);
+    if (mag > cap) {
+        float sc = mag > 0.f ? cap / mag : 0.f;
+        h = f3(h.x * sc, h.y * sc, h.z * sc);
+    }
+    ft[0] = h.x, ft[1] = h.y, ft[2] = h.z;
+    return f3(h.x - C.gt * vt.x, h.y - C.gt * vt.y, h.z - C.gt * vt.z);
+}
+
+__device__ __forceinline__ void kick(const DemCfg& C, const DemState& S, int p, double h) {
+    double m = S.m[p], I = S.I[p], mg = S.mg[p];
+    for (int a = 0; a < 3; a++) {
+        double F = S.Fc[3 * p + a] + S.Fh[3 * p + a] + mg * C.g[a];
+        S.U[3 * p + a] += h * F / m;
+        S.W[3 * p + a] += h * (S.Tc[3 * p + a] + S.Th[3 * p + a]) / I;
+    }
+    if (C.dim == 2) {
+        S.U[3 * p + 2] = 0.0;
+        S.W[3 * p] = 0.0;
+        S.W[3 * p + 1] = 0.0;
+    }
+}
+
+__device__ __forceinline__ void drift(const DemCfg& C, const DemState& S, int p, double dt, float half_skin2) {
+    double d2 = 0;
+    for (int a = 0; a < 3; a++) {
+        S.X[3 * p + a] += dt * S.U[3 * p + a];
+        double d = S.X[3 * p + a] - S.Xb[3 * p + a];
+        d2 += d * d;
+    }
+    if (d2 > (double)half_skin2) set_error(S.dstat, 2);
+}
+
+template <int D>
+__device__ void cell_coords(const DemCfg& C, const double* Xp, int* c) {
+    for (int a = 0; a < 3; a++) {
+        int v = 0;
+        if (a < D) {
+            v = (int)floor(__dmul_rn(__dadd_rn(Xp[a], 0.5), C.inv[a]));
+            if (v < 0) v = 0;
+            if (v > C.nc[a] - 1) v = C.nc[a] - 1;
+        }
+        c[a] = v;
+    }
+}
+
+// visit the particles of the 3^D cells around cell c
+template <int D, typename F>
+__device__ __forceinline__ void for_neighbours(const DemCfg& C, const DemState& S, const int* c, F&& fn) {
+    for (int z = c[2] - 1; z <= c[2] + 1; z++) {
+        if (z < 0 || z >= C.nc[2]) continue;
+        for (int y = c[1] - 1; y <= c[1] + 1; y++) {
+            if (y < 0 || y >= C.nc[1]) continue;
+            for (int x = c[0] - 1; x <= c[0] + 1; x++) {
+                if (x < 0 || x >= C.nc[0]) continue;
+                int cell = (z * C.nc[1] + y) * C.nc[0] + x;
+                int b = __ldcg(S.cell_start + cell), e = __ldcg(S.cell_start + cell + 1);
+                for (int k = b; k < e; k++) fn(__ldcg(S.cell_ids + k));
+            }
+        }
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, int advance) {
+    __shared__ int sh[DEM_T];
+    const int n = C.n;
+    const unsigned rank = cluster_rank();
+    const int gt = rank * blockDim.x + threadIdx.x, gs = cluster_size() * blockDim.x;
+    const int cur = __ldcg(S.nb_cur);
+    int* nb_start = cur ? S.nb_start1 : S.nb_start0;
+    int* nb_i = cur ? S.nb_i1 : S.nb_i0;
+    int* nb_j = cur ? S.nb_j1 : S.nb_j0;
+    float* nb_ft = cur ? S.nb_ft1 : S.nb_ft0;
+    const double dt = C.dt;
+    const float dtf = (float)dt;
+    const float half_skin2 = (float)(0.25 * C.skin * C.skin);
+
+    if (advance) {
+        for (int p = gt; p < n; p += gs)
+            if (!S.fixed[p]) {
+                kick(C, S, p, 0.5 * dt);
+                drift(C, S, p, dt, half_skin2);
+            }
+        cluster_barrier();
+        const int npairs = __ldcg(nb_start + n);
+        for (int sub = 0; sub < nsub; sub++) {
+            // pair forces at the drifted positions with the half-kicked velocities
+            for (int k = gt; k < npairs; k += gs) {
+                int i = __ldcg(nb_i + k), j = __ldcg(nb_j + k);
+                double Xi[3], Xj[3];
+                ldX(S.X, i, Xi);
+                ldX(S.X, j, Xj);
+                double d2 = dist2(Xi, Xj);
+                double Ssum = S.R[i] + S.R[j];
+                float* ft = nb_ft + 3 * k;
+                if (!(d2 < Ssum * Ssum)) {
+                    ft[0] = ft[1] = ft[2] = 0.f;
+                    S.pF[3 * k] = S.pF[3 * k + 1] = S.pF[3 * k + 2] = 0.f;
+                    S.pTi[3 * k] = S.pTi[3 * k + 1] = S.pTi[3 * k + 2] = 0.f;
+                    S.pTj[3 * k] = S.pTj[3 * k + 1] = S.pTj[3 * k + 2] = 0.f;
+                    continue;
+                }
+                float distf = sqrtf((float)d2);
+                float delta = (float)(Ssum * Ssum - d2) / ((float)Ssum + distf);
+                float3 nn = f3((float)(Xj[0] - Xi[0]) / distf, (float)(Xj[1] - Xi[1]) / distf, (float)(Xj[2] - Xi[2]) / distf);
+                float ai = (float)S.R[i] - 0.5f * delta, aj = (float)S.R[j] - 0.5f * delta;
+                float3 Ui = f3(__ldcg(S.U + 3 * i), __ldcg(S.U + 3 * i + 1), __ldcg(S.U + 3 * i + 2));
+                float3 Uj = f3(__ldcg(S.U + 3 * j), __ldcg(S.U + 3 * j + 1), __ldcg(S.U + 3 * j + 2));
+                float3 Wi = f3(__ldcg(S.W + 3 * i), __ldcg(S.W + 3 * i + 1), __ldcg(S.W + 3 * i + 2));
+                float3 Wj = f3(__ldcg(S.W + 3 * j), __ldcg(S.W + 3 * j + 1), __ldcg(S.W + 3 * j + 2));
+                float3 wi = cross3(Wi, f3(ai * nn.x, ai * nn.y, ai * nn.z));
+                float3 wj = cross3(Wj, f3(-aj * nn.x, -aj * nn.y, -aj * nn.z));
+                float3 vr = f3(Ui.x + wi.x - Uj.x - wj.x, Ui.y + wi.y - Uj.y - wj.y, Ui.z + wi.z - Uj.z - wj.z);
+                float vn = vr.x * nn.x + vr.y * nn.y + vr.z * nn.z;
+                float3 vt = f3(vr.x - vn * nn.x, vr.y - vn * nn.y, vr.z - vn * nn.z);
+                float Rstar = (float)(S.R[i] * S.R[j] / Ssum), kt_eff;
+                float Fn = normal_law(C, delta, vn, Rstar, &kt_eff);
+                float3 Ft = tangential(C, ft, nn, vt, kt_eff, Fn, dtf);
+                float3 Ti = cross3(f3(ai * nn.x, ai * nn.y, ai * nn.z), Ft);
+                float3 Tj = cross3(f3(aj * nn.x, aj * nn.y, aj * nn.z), Ft);
+                S.pF[3 * k] = -Fn * nn.x + Ft.x;
+                S.pF[3 * k + 1] = -Fn * nn.y + Ft.y;
+                S.pF[3 * k + 2] = -Fn * nn.z + Ft.z;
+                S.pTi[3 * k] = Ti.x, S.pTi[3 * k + 1] = Ti.y, S.pTi[3 * k + 2] = Ti.z;
+                S.pTj[3 * k] = Tj.x, S.pTj[3 * k + 1] = Tj.y, S.pTj[3 * k + 2] = Tj.z;
+            }
+            // particle-wall contacts: the same law with R_wall = infinity
+            for (int p = gt; p < n; p += gs) {
+                float3 F = f3(0, 0, 0), T = f3(0, 0, 0);
+                for (int face = 0; face < 2 * D; face++) {
+                    int a = face >> 1, hi = face & 1;
+                    float* ft = S.wall_ft + 3 * (6 * p + face);
+                    if (!C.walled[a]) continue;
+                    double Xa = __ldcg(S.X + 3 * p + a);
+                    double dist = hi ? C.hi[a] - Xa : Xa - C.lo[a];
+                    double dd = S.R[p] - dist;
+                    if (!(dd > 0.0)) {
+                        ft[0] = ft[1] = ft[2] = 0.f;
+                        continue;
+                    }
+                    float delta = (float)dd;
+                    float3 nn = f3(0, 0, 0);
+                    if (a == 0) nn.x = hi ? 1.f : -1.f;
+                    else if (a == 1) nn.y = hi ? 1.f : -1.f;
+                    else nn.z = hi ? 1.f : -1.f;
+                    float ai = (float)S.R[p] - 0.5f * delta;
+                    float3 Ui = f3(__ldcg(S.U + 3 * p), __ldcg(S.U + 3 * p + 1), __ldcg(S.U + 3 * p + 2));
+                    float3 Wi = f3(__ldcg(S.W + 3 * p), __ldcg(S.W + 3 * p + 1), __ldcg(S.W + 3 * p + 2));
+                    float3 ri = f3(ai * nn.x, ai * nn.y, ai * nn.z);
+                    float3 wi = cross3(Wi, ri);
+                    float3 vr = f3(Ui.x + wi.x, Ui.y + wi.y, Ui.z + wi.z);
+                    float vn = vr.x * nn.x + vr.y * nn.y + vr.z * nn.z;
+                    float3 vt = f3(vr.x - vn * nn.x, vr.y - vn * nn.y, vr.z - vn * nn.z);
+                    float kt_eff;
+                    float Fn = normal_law(C, delta, vn, (float)S.R[p], &kt_eff);
+                    float3 Ft = tangential(C, ft, nn, vt, kt_eff, Fn, dtf);
+                    float3 Ti = cross3(ri, Ft);
+                    F = f3(F.x - Fn * nn.x + Ft.x, F.y - Fn * nn.y + Ft.y, F.z - Fn * nn.z + Ft.z);
+                    T = f3(T.x + Ti.x, T.y + Ti.y, T.z + Ti.z);
+                }
+                S.wF[3 * p] = F.x, S.wF[3 * p + 1] = F.y, S.wF[3 * p + 2] = F.z;
+                S.wT[3 * p] = T.x, S.wT[3 * p + 1] = T.y, S.wT[3 * p + 2] = T.z;
+            }
+            cluster_barrier();
+            // per-particle sums over the adjacency in index order, then the kicks
+            for (int p = gt; p < n; p += gs) {
+                double F[3] = {S.wF[3 * p], S.wF[3 * p + 1], S.wF[3 * p + 2]};
+                double T[3] = {S.wT[3 * p], S.wT[3 * p + 1], S.wT[3 * p + 2]};
+                for (int e = S.adj_start[p]; e < S.adj_start[p + 1]; e++) {
+                    int k = S.adj_k[e];
+                    if (k >= 0) {
+                        for (int a = 0; a < 3; a++) {
+                            F[a] += (double)__ldcg(S.pF + 3 * k + a);
+                            T[a] += (double)__ldcg(S.pTi + 3 * k + a);
+                        }
+                    } else {
+                        k = ~k;
+                        for (int a = 0; a < 3; a++) {
+                            F[a] -= (double)__ldcg(S.pF + 3 * k + a);
+                            T[a] += (double)__ldcg(S.pTj + 3 * k + a);
+                        }
+                    }
+                }
+                for (int a = 0; a < 3; a++) {
+                    S.Fc[3 * p + a] = F[a];
+                    S.Tc[3 * p + a] = T[a];
+                }
+                if (S.fixed[p]) continue;
+                kick(C, S, p, 0.5 * dt);
+                if (sub + 1 < nsub) {
+                    kick(C, S, p, 0.5 * dt);
+                    drift(C, S, p, dt, half_skin2);
+                }
+            }
+            cluster_barrier();
+        }
+        // thermosensitive particles: C_p dT_p / dt = -H_p over one lattice step
+        for (int p = gt; p < n; p += gs)
+            if (S.Cp[p] > 0.0) S.Tp[p] -= S.Hh[p] / S.Cp[p];
+    }
+
+    // ------------------------------------------------ rebuild at new positions
+    for (int p = gt; p < n; p += gs) {
+        double Xp[3];
+        ldX(S.X, p, Xp);
+        int c[3];
+        cell_coords<D>(C, Xp, c);
+        S.cell_of[p] = (c[2] * C.nc[1] + c[1]) * C.nc[0] + c[0];
+        for (int a = 0; a < 3; a++) S.Xb[3 * p + a] = Xp[a];
+    }
+    for (int cidx = gt; cidx < C.ncell; cidx += gs) S.cell_cnt[cidx] = 0;
+    if (gt == 0) *S.flag = 0;
+    cluster_barrier();
+    for (int p = gt; p < n; p += gs) atomicAdd(S.cell_cnt + __ldcg(S.cell_of + p), 1);
+    cluster_barrier();
+    if (rank == 0) {
+        cta_scan(S.cell_cnt, S.cell_start, C.ncell, sh);
+        for (int cidx = threadIdx.x; cidx < C.ncell; cidx += blockDim.x) S.cell_cnt[cidx] = 0;
+    }
+    cluster_barrier();
+    for (int p = gt; p < n; p += gs) {
+        int cidx = __ldcg(S.cell_of + p);
+        int pos = atomicAdd(S.cell_cnt + cidx, 1);
+        S.cell_ids[__ldcg(S.cell_start + cidx) + pos] = p;
+    }
+    cluster_barrier();
+    for (int cidx = gt; cidx < C.ncell; cidx += gs) {  // stable order: by particle index
+        int b = __ldcg(S.cell_start + cidx), e = __ldcg(S.cell_start + cidx + 1);
+        for (int a = b + 1; a < e; a++) {
+            int v = __ldcg(S.cell_ids + a), q = a - 1;
+            while (q >= b && __ldcg(S.cell_ids + q) > v) {
+                S.cell_ids[q + 1] = __ldcg(S.cell_ids + q);
+                q--;
+            }
+            S.cell_ids[q + 1] = v;
+        }
+    }
+    cluster_barrier();
+    // neighbour counts (pairs within R_i + R_j + skin)
+    for (int i = gt; i < n; i += gs) {
+        double Xi[3];
+        ldX(S.X, i, Xi);
+        int c[3];
+        cell_coords<D>(C, Xi, c);
+        int hi = 0, lo = 0;
+        double Ri = S.R[i];
+        for_neighbours<D>(C, S, c, [&](int j) {
+            if (j == i) return;
+            double Xj[3];
+            ldX(S.X, j, Xj);
+            double cut = Ri + S.R[j] + C.skin;
+            if (dist2(Xi, Xj) < cut * cut) {
+                if (j > i) hi++;
+                else lo++;
+            }
+        });
+        S.cnt_hi[i] = hi;
+        S.cnt_lo[i] = lo;
+        if (hi + lo > DEM_MAXNB) {
+            set_error(S.dstat, 1);
+            atomicExch(S.flag, 1);
+        }
+    }
+    cluster_barrier();
+    int* nst = cur ? S.nb_start0 : S.nb_start1;
+    int* ni = cur ? S.nb_i0 : S.nb_i1;
+    int* nj = cur ? S.nb_j0 : S.nb_j1;
+    float* nft = cur ? S.nb_ft0 : S.nb_ft1;
+    if (rank == 0) {
+        cta_scan(S.cnt_hi, nst, n, sh);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) S.cnt_lo[i] += S.cnt_hi[i];
+        __syncthreads();
+        cta_scan(S.cnt_lo, S.adj_start, n, sh);
+        if (threadIdx.x == 0 && (nst[n] > C.cap || S.adj_start[n] > S.adj_cap)) {
+            set_error(S.dstat, 3);
+            *S.flag = 1;
+        }
+    }
+    cluster_barrier();
+    if (__ldcg(S.flag)) return;  // keep the previous list; the host reports the status
+    for (int i = gt; i < n; i += gs) {
+        double Xi[3];
+        ldX(S.X, i, Xi);
+        int c[3];
+        cell_coords<D>(C, Xi, c);
+        int cand[DEM_MAXNB], cnt = 0;
+        double Ri = S.R[i];
+        for_neighbours<D>(C, S, c, [&](int j) {
+            if (j <= i) return;
+            double Xj[3];
+            ldX(S.X, j, Xj);
+            double cut = Ri + S.R[j] + C.skin;
+            if (dist2(Xi, Xj) < cut * cut && cnt < DEM_MAXNB) cand[cnt++] = j;
+        });
+        for (int a = 1; a < cnt; a++) {
+            int v = cand[a], q = a - 1;
+            while (q >= 0 && cand[q] > v) {
+                cand[q + 1] = cand[q];
+                q--;
+            }
+            cand[q + 1] = v;
+        }
+        int o = __ldcg(nst + i);
+        int ob = nb_start[i], oe = nb_start[i + 1];
+        for (int r = 0; r < cnt; r++) {
+            int j = cand[r];
+            ni[o + r] = i;
+            nj[o + r] = j;
+            int L = ob, Hh = oe - 1, found = -1;
+            while (L <= Hh) {
+                int mid = (L + Hh) >> 1, v = nb_j[mid];
+                if (v == j) { found = mid; break; }
+                if (v < j) L = mid + 1;
+                else Hh = mid - 1;
+            }
+            for (int a = 0; a < 3; a++) nft[3 * (o + r) + a] = found >= 0 ? nb_ft[3 * found + a] : 0.f;
+        }
+    }
+    cluster_barrier();
+    // adjacency of each particle: partners j < i (pair found in j's segment), then j > i
+    for (int i = gt; i < n; i += gs) {
+        double Xi[3];
+        ldX(S.X, i, Xi);
+        int c[3];
+        cell_coords<D>(C, Xi, c);
+        int cand[DEM_MAXNB], cnt = 0;
+        double Ri = S.R[i];
+        for_neighbours<D>(C, S, c, [&](int j) {
+            if (j >= i) return;
+            double Xj[3];
+            ldX(S.X, j, Xj);
+            double cut = Ri + S.R[j] + C.skin;
+            if (dist2(Xi, Xj) < cut * cut && cnt < DEM_MAXNB) cand[cnt++] = j;
+        });
+        for (int a = 1; a < cnt; a++) {
+            int v = cand[a], q = a - 1;
+            while (q >= 0 && cand[q] > v) {
+                cand[q + 1] = cand[q];
+                q--;
+            }
+            cand[q + 1] = v;
+        }
+        int e0 = __ldcg(S.adj_start + i);
+        for (int r = 0; r < cnt; r++) {
+            int j = cand[r];
+            int L = __ldcg(nst + j), Hh = __ldcg(nst + j + 1) - 1, found = -1;
+            while (L <= Hh) {
+                int mid = (L + Hh) >> 1, v = __ldcg(nj + mid);
+                if (v == i) { found = mid; break; }
+                if (v < i) L = mid + 1;
+                else Hh = mid - 1;
+            }
+            if (found < 0) set_error(S.dstat, 4);
+            S.adj_nb[e0 + r] = j;
+            S.adj_k[e0 + r] = ~found;
+        }
+        int o = __ldcg(nst + i), oc = __ldcg(nst + i + 1) - o;
+        for (int r = 0; r < oc; r++) {
+            S.adj_nb[e0 + cnt + r] = __ldcg(nj + o + r);
+            S.adj_k[e0 + cnt + r] = o + r;
+        }
+    }
+    cluster_barrier();
+    if (gt == 0) *S.nb_cur = cur ^ 1;
+}
+
+int dem_cluster_size(Ctx* c) {
+    int cs = (c->np + 63) / 64;
+    return cs < 1 ? 1 : (cs > 8 ? 8 : cs);
+}
+
+static DemState dem_state(Ctx* c) {
+    DemState S;
+    S.X = c->X, S.U = c->U, S.W = c->W, S.Xb = c->Xb, S.R = c->R, S.m = c->m, S.I = c->I, S.mg = c->mg;
+    S.Tp = c->Tp, S.Cp = c->Cp, S.Fh = c->Fh, S.Th = c->Th, S.Hh = c->Hh, S.Fc = c->Fc, S.Tc = c->Tc;
+    S.fixed = c->fixed;
+    S.cell_of = c->cell_of, S.cell_cnt = c->cell_cnt, S.cell_start = c->cell_start, S.cell_ids = c->cell_ids;
+    S.cnt_hi = c->cnt_hi, S.cnt_lo = c->cnt_lo;
+    S.nb_start0 = c->nb_start[0], S.nb_start1 = c->nb_start[1];
+    S.nb_i0 = c->nb_i[0], S.nb_i1 = c->nb_i[1];
+    S.nb_j0 = c->nb_j[0], S.nb_j1 = c->nb_j[1];
+    S.nb_ft0 = c->nb_ft[0], S.nb_ft1 = c->nb_ft[1];
+    S.nb_cur = c->nb_cur;
+    S.adj_start = c->adj_start, S.adj_nb = c->adj_nb, S.adj_k = c->adj_k;
+    S.pF = c->pF, S.pTi = c->pTi, S.pTj = c->pTj, S.wall_ft = c->wall_ft, S.wF = c->wF, S.wT = c->wT;
+    S.dstat = c->dstat;
+    S.flag = c->dstat + 2;
+    S.adj_cap = c->adj_cap;
+    return S;
+}
+
+cudaError_t launch_dem(Ctx* c, cudaStream_t s, int nsub) {
+    if (c->np <= 0) return cudaSuccess;
+    int cs = dem_cluster_size(c);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(DEM_T, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    DemState S = dem_state(c);
+    int advance = nsub > 0 ? 1 : 0;
+    if (c->D == 2) return cudaLaunchKernelEx(&cfg, k_dem<2>, c->dem, S, nsub, advance);
+    return cudaLaunchKernelEx(&cfg, k_dem<3>, c->dem, S, nsub, advance);
+}
+
+// ---------------------------------------------------- contacts for read-back
+// Pairs of the current neighbour list with |X_i - X_j| < R_i + R_j (FP64, the
+// oracle's operation order), in list order, i.e. sorted by (i, j).
+__global__ void __launch_bounds__(DEM_T) k_contacts(int n, const double* X, const double* R, const int* nb_cur,
+                                                    const int* st0, const int* st1, const int* j0, const int* j1,
+                                                    int* cnt, int* pairs, int cap, int* total) {
+    __shared__ int sh[DEM_T];
+    const int cur = *nb_cur;
+    const int* st = cur ? st1 : st0;
+    const int* nj = cur ? j1 : j0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int c = 0;
+        for (int k = st[i]; k < st[i + 1]; k++) {
+            int j = nj[k];
+            double s = R[i] + R[j];
+            if (dist2(X + 3 * i, X + 3 * j) < s * s) c++;
+        }
+        cnt[i] = c;
+    }
+    __syncthreads();
+    cta_scan(cnt, cnt + n + 1, n, sh);
+    const int* off = cnt + n + 1;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int o = off[i];
+        for (int k = st[i]; k < st[i + 1]; k++) {
+            int j = nj[k];
+            double s = R[i] + R[j];
+            if (dist2(X + 3 * i, X + 3 * j) < s * s) {
+                if (o < cap) {
+                    pairs[2 * o] = i;
+                    pairs[2 * o + 1] = j;
+                }
+                o++;
+            }
+        }
+    }
+    if (threadIdx.x == 0) *total = off[n];
+}
+
+cudaError_t launch_contacts(Ctx* c, int* d_pairs, int cap, int* d_count) {
+    // scratch: cnt (n) + offsets (n + 1) in cnt_hi / cnt_lo region is not large
+    // enough in general; the caller passes d_count with room for 2n + 2 ints.
+    k_contacts<<<1, DEM_T, 0, c->s0>>>(c->np, c->X, c->R, c->nb_cur, c->nb_start[0], c->nb_start[1], c->nb_j[0],
+                                       c->nb_j[1], d_count + 1, d_pairs, cap, d_count);
+    return cudaGetLastError();
+}
+
+}  // namespace pibm

@@ -1,0 +1,421 @@
+// Lattice kernels: the fused collide-and-stream update of the flow (D2Q9 /
+// D3Q19) and thermal (D2Q5 / D3Q7) populations (Section 2.1), plus the
+// initialisation, read-back and diagnostic kernels of the lattice state.
+//
+// Storage: structure of arrays, one plane of nx*ny*nz values per direction,
+// x fastest.  Populations are kept as deviations s_i = f_i - w_i (density 1)
+// and s_gk = g_k - w_k T_ref, so that the small velocity-carrying part keeps
+// its relative precision in FP32.  Streaming follows the A-A pattern in place:
+// even steps read and write the node's own slots (the post-collision value of
+// direction i goes to the slot of its opposite), odd steps read from and write
+// to the neighbours, so one array serves both time levels.
+#include <float.h>
+
+#include "pibm_internal.cuh"
+
+namespace pibm {
+
+struct CollideParams {
+    double omf, omg;        // 1 / tau_f, 1 / tau_g
+    double cf, cg;          // 1 - 1/(2 tau_f), 1 - 1/(2 tau_g)
+    double buoy, Tref;      // U_c^2 / L_c, reference temperature
+    double body[3];
+    int gaxis, buoyancy;
+};
+
+// One node update: moments, forcing, BGK collision of f and g.
+//   rho = 1 + sum s_i, j = sum e_i s_i, T = T_ref + sum s_gk + Q_B / 2
+//   F = F_B + body + buoy (T - T_ref) e_up,  u = (j + F/2) / rho
+//   Eq lbm2 + lbm3 + lbm9 in deviation form:
+//     s_i* = s_i + (s_i^eq - s_i)/tau_f + (1 - 1/2tau_f) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . F
+//     s_i^eq = w_i (rho - 1 + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u^2))
+//   Eq lbm2.5 + lbm3.5 (linear, D2Q5 / D3Q7) + lbm12.5:
+//     s_gk* = s_gk + (w_k (T - T_ref + T e.u / cs_T^2) - s_gk)/tau_g + (1 - 1/2tau_g) w_k Q_B
+template <int D, typename R>
+__device__ __forceinline__ void collide_node(R* s, R* sg, R fbx, R fby, R fbz, R qb, const CollideParams& P) {
+    using L = Lat<D>;
+    R drho = 0, jx = 0, jy = 0, jz = 0, dT = 0;
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+        drho += s[i];
+        if (L::ex(i)) jx += L::ex(i) * s[i];
+        if (L::ey(i)) jy += L::ey(i) * s[i];
+        if (L::ez(i)) jz += L::ez(i) * s[i];
+    }
+#pragma unroll
+    for (int k = 0; k < L::QG; k++) dT += sg[k];
+    const R half = (R)0.5;
+    dT += half * qb;                        // T - T_ref
+    const R T = (R)P.Tref + dT;
+    R Fx = fbx + (R)P.body[0], Fy = fby + (R)P.body[1], Fz = fbz + (R)P.body[2];
+    if (P.buoyancy) {
+        R fbu = (R)P.buoy * dT;
+        if (P.gaxis == 0) Fx += fbu;
+        else if (P.gaxis == 1) Fy += fbu;
+        else Fz += fbu;
+    }
+    const R rho = (R)1 + drho;
+    const R inv_rho = (R)1 / rho;
+    const R ux = (jx + half * Fx) * inv_rho, uy = (jy + half * Fy) * inv_rho, uz = (jz + half * Fz) * inv_rho;
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R uF = ux * Fx + uy * Fy + uz * Fz;
+    const R omf = (R)P.omf, cf = (R)P.cf;
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+        const R wi = (R)L::w(i);
+        R eu = 0, eF = 0;
+        if (L::ex(i)) { eu += L::ex(i) * ux; eF += L::ex(i) * Fx; }
+        if (L::ey(i)) { eu += L::ey(i) * uy; eF += L::ey(i) * Fy; }
+        if (L::ez(i)) { eu += L::ez(i) * uz; eF += L::ez(i) * Fz; }
+        const R seq = wi * (drho + rho * ((R)3 * eu + (R)4.5 * eu * eu - (R)1.5 * uu));
+        const R Fi = cf * wi * ((R)3 * (eF - uF) + (R)9 * eu * eF);
+        s[i] = s[i] + omf * (seq - s[i]) + Fi;
+    }
+    const R omg = (R)P.omg, gq = (R)P.cg * qb;
+#pragma unroll
+    for (int k = 0; k < L::QG; k++) {
+        const R wk = (R)L::wg(k);
+        R eu = 0;
+        if (L::ex(k)) eu += L::ex(k) * ux;
+        if (L::ey(k)) eu += L::ey(k) * uy;
+        if (L::ez(k)) eu += L::ez(k) * uz;
+        const R sgeq = wk * (dT + T * eu * (R)L::inv_csT2);
+        sg[k] = sg[k] + omg * (sgeq - sg[k]) + wk * gq;
+    }
+}
+
+template <int D, typename S, int PARITY>
+__global__ void __launch_bounds__(256) k_stream_collide(Geo G, S* __restrict__ f, S* __restrict__ g,
+                                                        const typename Vec4<S>::T* __restrict__ fb,
+                                                        const uint8_t* __restrict__ flags, CollideParams P) {
+    using L = Lat<D>;
+    using R = S;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= G.nx) return;
+    const long long N = G.N;
+    const long long n = node_index(G, x, y, z);
+    const long long sy = G.nx, sz = (long long)G.nx * G.ny;
+    const bool interior = x > 0 && x < G.nx - 1 && y > 0 && y < G.ny - 1 && (D == 2 || (z > 0 && z < G.nz - 1));
+    R s[L::Q], sg[L::QG];
+    if (PARITY == 0) {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) s[i] = f[i * N + n];
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) sg[k] = g[k * N + n];
+    } else if (interior) {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) s[i] = f[L::opp(i) * N + n - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz)];
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) sg[k] = g[L::opp(k) * N + n - (L::ex(k) + L::ey(k) * sy + L::ez(k) * sz)];
+    } else {
+        load_node<D, S, R>(G, f, g, x, y, z, 1, s, sg);
+    }
+    R fbx = 0, fby = 0, fbz = 0, qb = 0;
+    if (flags[((long long)z * G.ny + y) * G.ntx + (x >> 5)]) {
+        const typename Vec4<S>::T v = fb[n];
+        fbx = v.x;
+        fby = v.y;
+        fbz = v.z;
+        qb = v.w;
+    }
+    collide_node<D, R>(s, sg, fbx, fby, fbz, qb, P);
+    if (PARITY == 0) {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) f[L::opp(i) * N + n] = s[i];
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) g[L::opp(k) * N + n] = sg[k];
+    } else if (interior) {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) f[i * N + n + (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz)] = s[i];
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) g[k * N + n + (L::ex(k) + L::ey(k) * sy + L::ez(k) * sz)] = sg[k];
+    } else {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) {
+            long long idx;
+            post_slot(G, x, y, z, L::ex(i), L::ey(i), L::ez(i), i, L::opp(i), 1, idx);
+            f[idx] = s[i];
+        }
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) {
+            long long idx;
+            int face = post_slot(G, x, y, z, L::ex(k), L::ey(k), L::ez(k), k, L::opp(k), 1, idx);
+            R v = sg[k];
+            if (face_iso(G, face)) v = (R)(2.0 * L::wg(k) * face_dTw(G, face)) - v;
+            g[idx] = v;
+        }
+    }
+}
+
+static CollideParams collide_params(const Ctx* c) {
+    CollideParams P;
+    P.omf = 1.0 / c->tau_f;
+    P.omg = 1.0 / c->tau_g;
+    P.cf = 1.0 - 0.5 / c->tau_f;
+    P.cg = 1.0 - 0.5 / c->tau_g;
+    P.buoy = c->buoy;
+    P.Tref = c->desc.T_ref;
+    for (int a = 0; a < 3; a++) P.body[a] = c->desc.body_force[a];
+    P.gaxis = c->desc.gravity_axis;
+    P.buoyancy = c->desc.buoyancy;
+    return P;
+}
+
+template <int D, typename S>
+static cudaError_t sc_launch(Ctx* c, cudaStream_t s, int parity) {
+    dim3 block(256), grid((c->G.nx + 255) / 256, c->G.ny, c->G.nz);
+    if (c->G.nx <= 128) block.x = 128, grid.x = (c->G.nx + 127) / 128;
+    CollideParams P = collide_params(c);
+    using V = typename Vec4<S>::T;
+    if (parity == 0)
+        k_stream_collide<D, S, 0><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb, c->flags, P);
+    else
+        k_stream_collide<D, S, 1><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb, c->flags, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_collide(Ctx* c, cudaStream_t s, int parity) {
+    bool dbl = c->desc.storage == PIBM_STORE_F64;
+    if (c->D == 2) return dbl ? sc_launch<2, double>(c, s, parity) : sc_launch<2, float>(c, s, parity);
+    return dbl ? sc_launch<3, double>(c, s, parity) : sc_launch<3, float>(c, s, parity);
+}
+
+// ----------------------------------------------------------- initialisation
+// Rest equilibrium at density 1 and temperature T_init: s_i = 0, s_gk = w_k (T_init - T_ref).
+template <int D, typename S>
+__global__ void k_init(long long N, S* f, S* g, double dT0) {
+    using L = Lat<D>;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) f[i * N + n] = (S)0;
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) g[k * N + n] = (S)(L::wg(k) * dT0);
+    }
+}
+
+cudaError_t launch_init_equilibrium(Ctx* c) {
+    double dT0 = c->desc.T_init - c->desc.T_ref;
+    int grid = 1024;
+    bool dbl = c->desc.storage == PIBM_STORE_F64;
+    if (c->D == 2) {
+        if (dbl) k_init<2, double><<<grid, 256, 0, c->s0>>>(c->G.N, (double*)c->f, (double*)c->g, dT0);
+        else k_init<2, float><<<grid, 256, 0, c->s0>>>(c->G.N, (float*)c->f, (float*)c->g, dT0);
+    } else {
+        if (dbl) k_init<3, double><<<grid, 256, 0, c->s0>>>(c->G.N, (double*)c->f, (double*)c->g, dT0);
+        else k_init<3, float><<<grid, 256, 0, c->s0>>>(c->G.N, (float*)c->f, (float*)c->g, dT0);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------- population read / write
+// One plane (direction q) of the populations of the current time, as doubles.
+template <int D, typename S>
+__global__ void k_read_plane(Geo G, const S* __restrict__ arr, int thermal, int q, int parity, double* out, double Tref) {
+    using L = Lat<D>;
+    long long N = G.N;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
+        int ex = 0, ey = 0, ez = 0, io = 0;
+        double w = 0;
+#pragma unroll
+        for (int i = 0; i < L::Q; i++)
+            if (i == q) { ex = L::ex(i); ey = L::ey(i); ez = L::ez(i); io = L::opp(i); w = thermal ? L::wg(i) : L::w(i); }
+        long long idx;
+        int face = pop_slot(G, x, y, z, ex, ey, ez, q, io, parity, idx);
+        double v = (double)arr[idx];
+        if (thermal && face_iso(G, face)) v = 2.0 * w * face_dTw(G, face) - v;
+        out[n] = v + (thermal ? w * Tref : w);
+    }
+}
+
+template <int D, typename S>
+__global__ void k_write_plane(Geo G, S* __restrict__ arr, int thermal, int q, int parity, const double* in, double Tref) {
+    using L = Lat<D>;
+    long long N = G.N;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
+        int ex = 0, ey = 0, ez = 0, io = 0;
+        double w = 0;
+#pragma unroll
+        for (int i = 0; i < L::Q; i++)
+            if (i == q) { ex = L::ex(i); ey = L::ey(i); ez = L::ez(i); io = L::opp(i); w = thermal ? L::wg(i) : L::w(i); }
+        long long idx;
+        int face = pop_slot(G, x, y, z, ex, ey, ez, q, io, parity, idx);
+        double v = in[n] - (thermal ? w * Tref : w);
+        if (thermal && face_iso(G, face)) v = 2.0 * w * face_dTw(G, face) - v;
+        arr[idx] = (S)v;
+    }
+}
+
+template <int D, typename S>
+static cudaError_t rw_plane(Ctx* c, int which, int q, int parity, bool write) {
+    const S* arr = (const S*)(which == 0 ? c->f : c->g);
+    if (write)
+        k_write_plane<D, S><<<1024, 256, 0, c->s0>>>(c->G, (S*)arr, which, q, parity, c->plane, c->desc.T_ref);
+    else
+        k_read_plane<D, S><<<1024, 256, 0, c->s0>>>(c->G, arr, which, q, parity, c->plane, c->desc.T_ref);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_read_plane(Ctx* c, int which, int q, int parity) {
+    bool dbl = c->desc.storage == PIBM_STORE_F64;
+    if (c->D == 2) return dbl ? rw_plane<2, double>(c, which, q, parity, false) : rw_plane<2, float>(c, which, q, parity, false);
+    return dbl ? rw_plane<3, double>(c, which, q, parity, false) : rw_plane<3, float>(c, which, q, parity, false);
+}
+
+cudaError_t launch_write_plane(Ctx* c, int which, int q, int parity) {
+    bool dbl = c->desc.storage == PIBM_STORE_F64;
+    if (c->D == 2) return dbl ? rw_plane<2, double>(c, which, q, parity, true) : rw_plane<2, float>(c, which, q, parity, true);
+    return dbl ? rw_plane<3, double>(c, which, q, parity, true) : rw_plane<3, float>(c, which, q, parity, true);
+}
+
+// ------------------------------------------------------ macroscopic fields
+template <int D, typename S>
+__device__ void node_macro(const Geo& G, const S* f, const S* g, const typename Vec4<S>::T* fb, const uint8_t* flags,
+                           const CollideParams& P, int x, int y, int z, int parity, double* out /*rho,ux,uy,uz,T,fbx,fby,fbz,qb,T0*/) {
+    using L = Lat<D>;
+    double s[L::Q], sg[L::QG];
+    load_node<D, S, double>(G, f, g, x, y, z, parity, s, sg);
+    long long n = node_index(G, x, y, z);
+    double fbv[4] = {0, 0, 0, 0};
+    if (flags[((long long)z * G.ny + y) * G.ntx + (x >> 5)]) {
+        typename Vec4<S>::T v = fb[n];
+        fbv[0] = v.x, fbv[1] = v.y, fbv[2] = v.z, fbv[3] = v.w;
+    }
+    double drho = 0, j[3] = {0, 0, 0}, dT = 0;
+    for (int i = 0; i < L::Q; i++) {
+        drho += s[i];
+        j[0] += L::ex(i) * s[i];
+        j[1] += L::ey(i) * s[i];
+        j[2] += L::ez(i) * s[i];
+    }
+    for (int k = 0; k < L::QG; k++) dT += sg[k];
+    double T0 = P.Tref + dT;
+    dT += 0.5 * fbv[3];
+    double F[3] = {fbv[0] + P.body[0], fbv[1] + P.body[1], fbv[2] + P.body[2]};
+    if (P.buoyancy) F[P.gaxis] += P.buoy * dT;
+    double rho = 1.0 + drho;
+    out[0] = rho;
+    for (int a = 0; a < 3; a++) out[1 + a] = (j[a] + 0.5 * F[a]) / rho;
+    out[4] = P.Tref + dT;
+    for (int a = 0; a < 4; a++) out[5 + a] = fbv[a];
+    out[9] = T0;
+}
+
+template <int D, typename S>
+__global__ void k_macro(Geo G, const S* f, const S* g, const typename Vec4<S>::T* fb, const uint8_t* flags,
+                        CollideParams P, int field, int parity, double* out) {
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < G.N; n += (long long)gridDim.x * blockDim.x) {
+        int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
+        double m[10];
+        node_macro<D, S>(G, f, g, fb, flags, P, x, y, z, parity, m);
+        out[n] = m[field];
+    }
+}
+
+template <int D, typename S>
+static cudaError_t macro_launch(Ctx* c, int field, int parity) {
+    using V = typename Vec4<S>::T;
+    k_macro<D, S><<<1024, 256, 0, c->s0>>>(c->G, (const S*)c->f, (const S*)c->g, (const V*)c->fb, c->flags,
+                                           collide_params(c), field, parity, c->plane);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro(Ctx* c, int field, int parity) {
+    bool dbl = c->desc.storage == PIBM_STORE_F64;
+    if (c->D == 2) return dbl ? macro_launch<2, double>(c, field, parity) : macro_launch<2, float>(c, field, parity);
+    return dbl ? macro_launch<3, double>(c, field, parity) : macro_launch<3, float>(c, field, parity);
+}
+
+// ------------------------------------------------------------ diagnostics
+// Deterministic two-level reduction: a fixed grid of 512 blocks writes
+// partials, one block combines them in a fixed order.
+constexpr int DIAG_BLOCKS = 512;
+
+template <int D, typename S>
+__global__ void __launch_bounds__(256) k_diag_lattice(Geo G, const S* f, const S* g, const typename Vec4<S>::T* fb,
+                                                      const uint8_t* flags, CollideParams P, int parity, double* part) {
+    __shared__ double sh[4][256];
+    double mass = 0, heat = 0, umax = 0, bad = 0;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < G.N; n += (long long)gridDim.x * blockDim.x) {
+        int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
+        double m[10];
+        node_macro<D, S>(G, f, g, fb, flags, P, x, y, z, parity, m);
+        mass += m[0];
+        heat += m[9];
+        double um = sqrt(m[1] * m[1] + m[2] * m[2] + m[3] * m[3]);
+        if (!(um <= umax)) umax = isfinite(um) ? um : umax;
+        if (!isfinite(m[0]) || !isfinite(m[9]) || !isfinite(um)) bad = 1;
+    }
+    int t = threadIdx.x;
+    sh[0][t] = mass, sh[1][t] = heat, sh[2][t] = umax, sh[3][t] = bad;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (t < s) {
+            sh[0][t] += sh[0][t + s];
+            sh[1][t] += sh[1][t + s];
+            sh[2][t] = fmax(sh[2][t], sh[2][t + s]);
+            sh[3][t] = fmax(sh[3][t], sh[3][t + s]);
+        }
+        __syncthreads();
+    }
+    if (t == 0)
+        for (int a = 0; a < 4; a++) part[4 * blockIdx.x + a] = sh[a][0];
+}
+
+__global__ void __launch_bounds__(256) k_diag_final(const double* part, int nblocks, const double* U, const double* W,
+                                                    const double* X, const double* m, const double* I, int np,
+                                                    int gaxis, double* out) {
+    __shared__ double sh[6][256];
+    int t = threadIdx.x;
+    double mass = 0, heat = 0, umax = 0, bad = 0, ke = 0, hmin = 1e300;
+    for (int b = t; b < nblocks; b += 256) {
+        mass += part[4 * b];
+        heat += part[4 * b + 1];
+        umax = fmax(umax, part[4 * b + 2]);
+        bad = fmax(bad, part[4 * b + 3]);
+    }
+    for (int p = t; p < np; p += 256) {
+        double v2 = U[3 * p] * U[3 * p] + U[3 * p + 1] * U[3 * p + 1] + U[3 * p + 2] * U[3 * p + 2];
+        double w2 = W[3 * p] * W[3 * p] + W[3 * p + 1] * W[3 * p + 1] + W[3 * p + 2] * W[3 * p + 2];
+        ke += 0.5 * m[p] * v2 + 0.5 * I[p] * w2;
+        hmin = fmin(hmin, X[3 * p + gaxis]);
+        if (!isfinite(v2) || !isfinite(w2)) bad = 1;
+    }
+    sh[0][t] = mass, sh[1][t] = heat, sh[2][t] = ke, sh[3][t] = hmin, sh[4][t] = umax, sh[5][t] = bad;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (t < s) {
+            sh[0][t] += sh[0][t + s];
+            sh[1][t] += sh[1][t + s];
+            sh[2][t] += sh[2][t + s];
+            sh[3][t] = fmin(sh[3][t], sh[3][t + s]);
+            sh[4][t] = fmax(sh[4][t], sh[4][t + s]);
+            sh[5][t] = fmax(sh[5][t], sh[5][t + s]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        for (int a = 0; a < 6; a++) out[a] = sh[a][0];
+        if (np == 0) out[3] = 0.0;
+    }
+}
+
+template <int D, typename S>
+static cudaError_t diag_launch(Ctx* c, int parity) {
+    using V = typename Vec4<S>::T;
+    k_diag_lattice<D, S><<<DIAG_BLOCKS, 256, 0, c->s0>>>(c->G, (const S*)c->f, (const S*)c->g, (const V*)c->fb,
+                                                         c->flags, collide_params(c), parity, c->red);
+    k_diag_final<<<1, 256, 0, c->s0>>>(c->red, DIAG_BLOCKS, c->U, c->W, c->X, c->m, c->I, c->np,
+                                       c->desc.gravity_axis, c->red + 4 * DIAG_BLOCKS);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(Ctx* c, int parity) {
+    bool dbl = c->desc.storage == PIBM_STORE_F64;
+    if (c->D == 2) return dbl ? diag_launch<2, double>(c, parity) : diag_launch<2, float>(c, parity);
+    return dbl ? diag_launch<3, double>(c, parity) : diag_launch<3, float>(c, parity);
+}
+
+}  // namespace pibm

@@ -1,0 +1,255 @@
+// Internal declarations of the GB300 LBM-PIBM-DEM library: device-side lattice
+// tables, the A-A population addressing shared by every kernel that touches
+// f and g, the context structure and the launch wrappers of each kernel file.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/pibm.h"
+
+namespace pibm {
+
+// ------------------------------------------------------------------ lattices
+// D2Q9 / D2Q5 and D3Q19 / D3Q7 in the direction order of pibm.h.  Functions of
+// a compile-time index fold to constants after unrolling.
+template <int D> struct Lat;
+template <> struct Lat<2> {
+    static constexpr int Q = 9, QG = 5;
+    __host__ __device__ static constexpr int ex(int i) { return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0); }
+    __host__ __device__ static constexpr int ey(int i) { return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0); }
+    __host__ __device__ static constexpr int ez(int) { return 0; }
+    __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 5 + 2) % 4) + 5); }
+    __host__ __device__ static constexpr double w(int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+    __host__ __device__ static constexpr double wg(int k) { return k == 0 ? 1.0 / 3.0 : 1.0 / 6.0; }
+    static constexpr double inv_csT2 = 3.0;  // D2Q5: cs_T^2 = 1/3
+};
+template <> struct Lat<3> {
+    static constexpr int Q = 19, QG = 7;
+    __host__ __device__ static constexpr int ex(int i) {
+        return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1 : ((i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int ey(int i) {
+        return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1 : ((i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int ez(int i) {
+        return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1 : ((i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+    __host__ __device__ static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+    __host__ __device__ static constexpr double wg(int k) { return k == 0 ? 0.25 : 0.125; }
+    static constexpr double inv_csT2 = 4.0;  // D3Q7: cs_T^2 = 1/4
+};
+
+template <typename S> struct Vec4;
+template <> struct Vec4<float> { using T = float4; };
+template <> struct Vec4<double> { using T = double4_32a; };
+
+// ------------------------------------------------------------ lattice state
+// Geometry and boundary data every lattice kernel needs (passed by value).
+struct Geo {
+    int nx, ny, nz;
+    long long N;      // nodes = plane stride
+    int ntx;          // 32-node tiles along x
+    int per[3];       // 1 if the axis is periodic
+    int iso;          // bit f set: face f is an isothermal wall
+    double dTw[6];    // T_w - T_ref per face
+};
+
+// Anti-bounce-back offset 2 w (T_w - T_ref) of face f, or -1 if face f is not
+// isothermal (constant indices only, so the struct stays in registers).
+__host__ __device__ __forceinline__ bool face_iso(const Geo& G, int f) { return f >= 0 && ((G.iso >> f) & 1); }
+__host__ __device__ __forceinline__ double face_dTw(const Geo& G, int f) {
+    switch (f) {
+        case 0: return G.dTw[0];
+        case 1: return G.dTw[1];
+        case 2: return G.dTw[2];
+        case 3: return G.dTw[3];
+        case 4: return G.dTw[4];
+        default: return G.dTw[5];
+    }
+}
+
+__host__ __device__ inline long long node_index(const Geo& G, int x, int y, int z) {
+    return ((long long)z * G.ny + y) * G.nx + x;
+}
+
+// Location of the population of direction i (opposite io) that node (x,y,z)
+// holds before collision at time parity p under the A-A pattern:
+//   even t: plane i at the node itself;
+//   odd t : plane io at node x - e_i, or -- when x - e_i lies beyond a wall --
+//           plane i at the node itself (halfway bounce-back of the value the
+//           node wrote in the previous step).
+// Returns the face crossed (>= 0) or -1.  The population value is the stored
+// value, except at a crossed isothermal face of the thermal lattice where it
+// is 2 w (T_w - T_ref) minus the stored value (anti-bounce-back).
+__device__ __forceinline__ int pop_slot(const Geo& G, int x, int y, int z, int exi, int eyi, int ezi, int i, int io,
+                                        int parity, long long& idx) {
+    long long n = node_index(G, x, y, z);
+    if (parity == 0) {
+        idx = (long long)i * G.N + n;
+        return -1;
+    }
+    int sx = x - exi, sy = y - eyi, sz = z - ezi, face = -1;
+    if (sx < 0) { if (G.per[0]) sx += G.nx; else face = 0; }
+    else if (sx >= G.nx) { if (G.per[0]) sx -= G.nx; else face = 1; }
+    if (sy < 0) { if (G.per[1]) sy += G.ny; else face = 2; }
+    else if (sy >= G.ny) { if (G.per[1]) sy -= G.ny; else face = 3; }
+    if (sz < 0) { if (G.per[2]) sz += G.nz; else face = 4; }
+    else if (sz >= G.nz) { if (G.per[2]) sz -= G.nz; else face = 5; }
+    if (face >= 0)
+        idx = (long long)i * G.N + n;
+    else
+        idx = (long long)io * G.N + node_index(G, sx, sy, sz);
+    return face;
+}
+
+// Destination of the post-collision population of direction i of node
+// (x,y,z) at time parity p (the inverse of pop_slot one step later):
+//   even t: plane io at the node;
+//   odd t : plane i at node x + e_i, or plane io at the node when x + e_i lies
+//           beyond a wall (bounce-back; anti-bounce-back at isothermal faces).
+__device__ __forceinline__ int post_slot(const Geo& G, int x, int y, int z, int exi, int eyi, int ezi, int i, int io,
+                                         int parity, long long& idx) {
+    long long n = node_index(G, x, y, z);
+    if (parity == 0) {
+        idx = (long long)io * G.N + n;
+        return -1;
+    }
+    int tx = x + exi, ty = y + eyi, tz = z + ezi, face = -1;
+    if (tx < 0) { if (G.per[0]) tx += G.nx; else face = 0; }
+    else if (tx >= G.nx) { if (G.per[0]) tx -= G.nx; else face = 1; }
+    if (ty < 0) { if (G.per[1]) ty += G.ny; else face = 2; }
+    else if (ty >= G.ny) { if (G.per[1]) ty -= G.ny; else face = 3; }
+    if (tz < 0) { if (G.per[2]) tz += G.nz; else face = 4; }
+    else if (tz >= G.nz) { if (G.per[2]) tz -= G.nz; else face = 5; }
+    if (face >= 0)
+        idx = (long long)io * G.N + n;
+    else
+        idx = (long long)i * G.N + node_index(G, tx, ty, tz);
+    return face;
+}
+
+// Load the pre-collision deviations s_i = f_i - w_i and s_gk = g_k - w_k T_ref
+// of one node at parity p (generic path: any node, any boundary).
+template <int D, typename S, typename R>
+__device__ __forceinline__ void load_node(const Geo& G, const S* __restrict__ f, const S* __restrict__ g, int x, int y,
+                                          int z, int parity, R* s, R* sg) {
+    using L = Lat<D>;
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+        long long idx;
+        pop_slot(G, x, y, z, L::ex(i), L::ey(i), L::ez(i), i, L::opp(i), parity, idx);
+        s[i] = (R)f[idx];
+    }
+#pragma unroll
+    for (int k = 0; k < L::QG; k++) {
+        long long idx;
+        int face = pop_slot(G, x, y, z, L::ex(k), L::ey(k), L::ez(k), k, L::opp(k), parity, idx);
+        R v = (R)g[idx];
+        if (face_iso(G, face)) v = (R)(2.0 * L::wg(k) * face_dTw(G, face)) - v;
+        sg[k] = v;
+    }
+}
+
+// ------------------------------------------------------------------ context
+struct DemCfg {
+    int n;            // particles
+    int dim;
+    int nsub;         // substeps per lattice step
+    double dt;        // 1 / nsub
+    int law;
+    float E_star, G_star, mu, kn, kt, gn, gt;
+    double g[3];      // particle gravity
+    double lo[3], hi[3];  // wall planes (-0.5, n - 0.5)
+    int walled[3];
+    int nc[3];        // cells per axis
+    double inv[3];    // nc / n per axis
+    int ncell;
+    double skin;      // neighbour-list margin
+    int cap;          // capacity of the canonical pair list
+    int maxnb;        // candidates per particle
+};
+
+struct Ctx {
+    pibm_desc desc;
+    int D, Q, QG;
+    Geo G;
+    int walls_kind[6];
+    int walls_therm[6];
+    double walls_T[6];
+    double nu, alpha, tau_f, tau_g, buoy;
+    long long t;
+    size_t es;  // bytes per stored population element
+
+    cudaStream_t s0;  // caller's stream
+    cudaStream_t s1;  // internal stream for the DEM branch
+    cudaEvent_t ev_fork, ev_join;
+    pibm_allocator alloc;
+    int own_s0;  // 1 if the library created s0
+
+    // lattice buffers
+    void* f;
+    void* g;
+    void* fb;         // F_B (xyz) and Q_B (w) per node, valid on flagged tiles
+    void* mk;         // marker field of covered nodes (eps * F_f, eps * Q)
+    uint8_t* flags;   // one byte per 32-node tile along x
+    double* plane;    // one plane of doubles (reads / writes through the API)
+    double* red;      // reduction scratch
+    int* dstat;       // device status words [code, detail]
+
+    // particles
+    int np;
+    double *X, *U, *W, *Xb, *R, *rho, *Tp, *Cp, *m, *I, *mg;
+    uint8_t* fixed;
+    double *Fh, *Th, *Hh, *Fc, *Tc;
+    int* box;         // spread box per particle (lo xyz, hi xyz); empty = hi < lo
+    DemCfg dem;
+    int *cell_of, *cell_cnt, *cell_start, *cell_ids, *cnt_hi, *cnt_lo;
+    int* nb_start[2];
+    int* nb_i[2];
+    int* nb_j[2];
+    float* nb_ft[2];
+    int* nb_cur;      // device int: which list is current
+    int *adj_start, *adj_nb, *adj_k;
+    float *pF, *pTi, *pTj, *wall_ft, *wF, *wT;
+    int adj_cap;
+    int* contact_pairs;   // 2 * dem.cap ints
+    int* contact_scratch; // 2 * np + 4 ints
+
+    // static markers
+    int nm;
+    double *MX, *MA, *MT, *nu_part, *nu_val;
+    void* Ml;         // per-marker (A F_f, A Q)
+    int n_csr_nodes;
+    long long* csr_node;
+    int *csr_start, *csr_marker;
+    double* csr_w;
+
+    // CUDA graphs: one lattice step starting at even / odd time
+    cudaGraphExec_t graph[2];
+    int graph_ok[2];
+    int kernels_per_step;
+
+    std::string err;
+};
+
+// ---------------------------------------------------------- launch wrappers
+// lattice.cu
+cudaError_t launch_init_equilibrium(Ctx* c);
+cudaError_t launch_stream_collide(Ctx* c, cudaStream_t s, int parity);
+cudaError_t launch_read_plane(Ctx* c, int which, int plane, int parity);    // which: 0 f, 1 g
+cudaError_t launch_write_plane(Ctx* c, int which, int plane, int parity);
+cudaError_t launch_macro(Ctx* c, int field, int parity);
+cudaError_t launch_diagnostics(Ctx* c, int parity);
+// coupling.cu
+cudaError_t launch_coupling(Ctx* c, cudaStream_t s, int parity);
+int coupling_kernel_count(Ctx* c);
+// dem.cu
+cudaError_t launch_dem(Ctx* c, cudaStream_t s, int nsub);
+cudaError_t launch_contacts(Ctx* c, int* d_pairs, int cap, int* d_count);
+int dem_cluster_size(Ctx* c);
+
+}  // namespace pibm

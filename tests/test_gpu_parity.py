@@ -1,0 +1,243 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on the
+same seeded inputs.
+
+Bars: cell ids and contact lists bit-exact; FP32 fields (rho, u, T) within
+relative L2 1e-5 after 100 steps; particle positions within 1e-6 lattice
+units over 100 steps.  FP64 storage (the cavity case) is held to 1e-10.
+Sizes span several 32-node tiles and ragged tails."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from _util import FIELD_RTOL, POS_ATOL, build_library, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build_library()
+
+
+def _sim(case):
+    from paper_1502_01159_gb300 import Simulation
+    return Simulation(case)
+
+
+def _compare_fields(sim, orc, rtol, dim):
+    errs = {}
+    for name in ("rho", "T"):
+        errs[name] = rel_l2(sim.read_field(name), orc.field(name))
+    comps = ("ux", "uy") + (("uz",) if dim == 3 else ())
+    errs["u"] = rel_l2(np.stack([sim.read_field(c) for c in comps]), np.stack([orc.field(c) for c in comps]))
+    fs, gs = sim.read_populations()
+    fo, go = orc.populations()
+    errs["f"] = rel_l2(fs, fo)
+    errs["g"] = rel_l2(gs, go)
+    for k, v in errs.items():
+        assert v < rtol, (k, v, errs)
+    return errs
+
+
+@pytest.mark.parametrize("dim,shape", [(2, (45, 37, 1)), (3, (37, 13, 11))])
+def test_periodic_box_random_state(dim, shape):
+    case = W.periodic_box(shape=shape, dim=dim, buoyancy=True, body=(2e-6, -1e-6, 0.0))
+    f, g = W.random_populations(case, amp=0.02)
+    sim, orc = _sim(case), oracle.Oracle(case)
+    sim.set_populations(f.ravel(), g.ravel())
+    orc.set_populations(f.ravel(), g.ravel())
+    sim.step(100)
+    orc.step(100)
+    assert sim.t == 100
+    _compare_fields(sim, orc, FIELD_RTOL, dim)
+
+
+@pytest.mark.parametrize("dim,shape", [(2, (70, 41, 1)), (3, (35, 19, 23))])
+def test_walled_box_mixed_thermal_walls(dim, shape):
+    case = W.periodic_box(shape=shape, dim=dim, buoyancy=True)
+    walls = [(1, 1, 0.0), (1, 0, 0.0), (1, 1, 1.0), (1, 1, 0.2)]
+    if dim == 3:
+        walls += [(1, 0, 0.0), (1, 1, 0.7)]
+    case["walls"] = walls
+    f, g = W.random_populations(case, amp=0.02, config_index=8)
+    sim, orc = _sim(case), oracle.Oracle(case)
+    sim.set_populations(f.ravel(), g.ravel())
+    orc.set_populations(f.ravel(), g.ravel())
+    for k in (1, 1, 98):  # odd and even parities, then the rest
+        sim.step(k)
+        orc.step(k)
+    _compare_fields(sim, orc, FIELD_RTOL, dim)
+
+
+def test_poiseuille_closed_form_on_gpu():
+    case = W.poiseuille(ny=16, nx=40)
+    sim = _sim(case)
+    sim.step(20000)
+    ux = sim.read_field("ux")[0, :, 5]
+    y = np.arange(16)
+    nu = sim.relaxation()["nu"]
+    exact = case["body_force"][0] / (2 * nu) * (y + 0.5) * (16 - 0.5 - y)
+    assert np.max(np.abs(ux - exact)) / exact.max() < 2e-5
+
+
+def test_degenerate_lattices():
+    # one-node-wide periodic axes and a 1x1 cross-section
+    for shape, walls in [((1, 9, 1), [(0, 0, 0.0), (0, 0, 0.0), (1, 1, 1.0), (1, 1, 0.0)]),
+                         ((1, 1, 1), [(0, 0, 0.0)] * 4)]:
+        case = W.periodic_box(shape=shape, dim=2, buoyancy=True)
+        case["walls"] = walls
+        sim, orc = _sim(case), oracle.Oracle(case)
+        sim.step(50)
+        orc.step(50)
+        for name in ("rho", "T", "uy"):
+            a, b = sim.read_field(name), orc.field(name)
+            assert np.max(np.abs(a - b)) < 1e-6 * max(1.0, np.abs(b).max()), (shape, name)
+
+
+def _small_sed2d(n_p=12, nx=96, ny=128, seed=1):
+    case = W.sed2d(nx=nx, ny=ny, n_p=n_p, d=10.0, config_index=seed)
+    case["g_particle"] = [0.0, -2e-4, 0.0]
+    return case
+
+
+def _small_sed3d(n_p=6, shape=(32, 32, 48), seed=2):
+    case = W.sed3d(nx=shape[0], ny=shape[1], nz=shape[2], n_p=n_p, d=8.0, config_index=seed)
+    case["g_particle"] = [0.0, 0.0, -2e-4]
+    return case
+
+
+@pytest.mark.parametrize("which", ["2d", "3d"])
+def test_sedimentation_parity_100_steps(which):
+    case = _small_sed2d() if which == "2d" else _small_sed3d()
+    sim, orc = _sim(case), oracle.Oracle(case)
+    # coupling of the initial state
+    Fs, Fo = sim.read_particle_forces(), orc.particle_forces()
+    assert np.max(np.abs(Fs["H"] - Fo["H"])) < 1e-5 * np.abs(Fo["H"]).max()
+    sim.step(100)
+    orc.step(100)
+    dim = case["dim"]
+    _compare_fields(sim, orc, FIELD_RTOL, dim)
+    ps, po = sim.read_particles(), orc.particles()
+    assert np.max(np.abs(ps["X"] - po["X"])) < POS_ATOL
+    moved = np.max(np.abs(po["X"] - np.asarray(case["particles"]["X"])))
+    assert moved > 1e-3  # the particles did move
+    Fs, Fo = sim.read_particle_forces(), orc.particle_forces()
+    scale = np.abs(Fo["F"]).max()
+    assert np.max(np.abs(Fs["F"] - Fo["F"])) < 1e-4 * scale
+    assert rel_l2(sim.read_field("FBx"), orc.field("FBx")) < 1e-4
+
+
+def test_colliding_particles_parity():
+    # dense 2-D cluster with contacts from the start (spring-dashpot with friction), no fluid coupling drift
+    gen = W.rng(41)
+    n = 24
+    X = W.rsa_positions(gen, n, 3.0, [10.0, 10.0], [50.0, 50.0], gap=-0.4)
+    parts = dict(X=X, U=gen.normal(size=(n, 3)) * 2e-3, R=np.full(n, 3.0), rho_p=np.full(n, 1.5),
+                 T_p=np.full(n, 0.8))
+    parts["U"][:, 2] = 0
+    case = W.sed2d(nx=64, ny=64, n_p=0)
+    case.update(particles=parts, contact=W.spring_dashpot(kn=20.0, kt=6.0, gamma_n=1.0, gamma_t=0.2, mu=0.4),
+                g_particle=[0.0, -1e-4, 0.0])
+    sim, orc = _sim(case), oracle.Oracle(case)
+    c0 = oracle.point_contacts(X, parts["R"])
+    assert len(c0) > 5
+    assert np.array_equal(sim.read_contacts(), c0)
+    sim.step(100)
+    orc.step(100)
+    ps, po = sim.read_particles(), orc.particles()
+    assert np.max(np.abs(ps["X"] - po["X"])) < POS_ATOL
+    assert np.max(np.abs(ps["W"] - po["W"])) < 1e-6
+    _compare_fields(sim, orc, FIELD_RTOL, 2)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_contacts_and_cells_bit_exact(dim):
+    gen = W.rng(51 + dim)
+    n = 200 if dim == 2 else 300
+    shape = (120, 100, 1) if dim == 2 else (40, 36, 44)
+    R = 2.0 + gen.random(n)
+    X = np.zeros((n, 3))
+    X[:, :dim] = 4.0 + gen.random((n, dim)) * (np.array(shape[:dim]) - 9.0)
+    case = W.periodic_box(shape=shape, dim=dim, buoyancy=False)
+    case.update(walls=[(1, 1, 0.0)] * (2 * dim), pibm=False, contact=W.hertz(),
+                particles=dict(X=X, R=R, rho_p=np.full(n, 1.2)))
+    sim = _sim(case)
+    bf = oracle.point_contacts(X, R)
+    assert len(bf) > 10
+    assert np.array_equal(sim.read_contacts(), bf)
+    cells, nc = sim.read_cells()
+    oc, onc = oracle.point_cells(dim, shape, 0.0, X, R)
+    assert nc == onc
+    assert np.array_equal(cells, oc)
+
+
+def test_empty_particle_set_and_no_contacts():
+    case = _small_sed2d(n_p=1)
+    sim = _sim(case)
+    assert len(sim.read_contacts()) == 0
+    sim.set_particles(dict(X=np.zeros((0, 3)), R=np.zeros(0), rho_p=np.zeros(0)))
+    sim.step(3)
+    assert sim.diagnostics()["nonfinite"] == 0
+
+
+def test_cavity_markers_fp64_parity():
+    case = W.cavity(n=48, Ar=2.5, storage="f64")
+    sim, orc = _sim(case), oracle.Oracle(case)
+    assert abs(sim.nusselt() - orc.nusselt()) < 1e-10 * abs(orc.nusselt())
+    sim.step(100)
+    orc.step(100)
+    _compare_fields(sim, orc, 1e-10, 2)
+    assert abs(sim.nusselt() - orc.nusselt()) < 1e-9 * abs(orc.nusselt())
+    assert rel_l2(sim.read_field("QB"), orc.field("QB")) < 1e-10
+
+
+def test_cavity_markers_fp32():
+    case = W.cavity(n=40, Ar=2.5, storage="f32")
+    sim, orc = _sim(case), oracle.Oracle(case)
+    sim.step(100)
+    orc.step(100)
+    _compare_fields(sim, orc, FIELD_RTOL, 2)
+    assert abs(sim.nusselt() - orc.nusselt()) < 1e-5 * abs(orc.nusselt())
+
+
+def test_thermosensitive_particles():
+    case = _small_sed3d(n_p=5)
+    gen = W.rng(61)
+    case["particles"]["T_p"] = gen.random(5)
+    case["particles"]["heat_cap"] = np.full(5, 50.0)
+    sim, orc = _sim(case), oracle.Oracle(case)
+    sim.step(100)
+    orc.step(100)
+    ts, to = sim.read_particles()["T_p"], orc.particles()["T_p"]
+    assert np.max(np.abs(ts - to)) < 1e-5
+    assert np.max(np.abs(to - case["particles"]["T_p"])) > 1e-3
+
+
+def test_full_size_sed2d_parity():
+    # the 2-D sedimentation workload at full size: 512 x 1024 lattice, 500 disks
+    case = W.sed2d()
+    sim, orc = _sim(case), oracle.Oracle(case)
+    sim.step(100)
+    orc.step(100)
+    _compare_fields(sim, orc, FIELD_RTOL, 2)
+    ps, po = sim.read_particles(), orc.particles()
+    assert np.max(np.abs(ps["X"] - po["X"])) < POS_ATOL
+
+
+def test_full_size_sed3d_properties():
+    # the 3-D sedimentation workload at full size (256 x 256 x 512, 2000 spheres):
+    # contacts and cells at the generated positions bit-exact, mass conserved
+    case = W.sed3d()
+    sim = _sim(case)
+    X, R = case["particles"]["X"], case["particles"]["R"]
+    assert np.array_equal(sim.read_contacts(), oracle.point_contacts(X, R))
+    cells, nc = sim.read_cells()
+    oc, onc = oracle.point_cells(3, case["shape"], 0.0, X, R)
+    assert nc == onc and np.array_equal(cells, oc)
+    d0 = sim.diagnostics()
+    sim.step(20)
+    d1 = sim.diagnostics()
+    assert d1["nonfinite"] == 0
+    assert abs(d1["mass"] - d0["mass"]) / d0["mass"] < 1e-6
+    assert d1["min_height"] < d0["min_height"]  # the spheres sink
