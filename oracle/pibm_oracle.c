@@ -92,6 +92,8 @@ struct orc_sim {
     double *X, *U, *W, *R, *rho, *Tp, *Cp, *m, *I;
     unsigned char* fixed;
     double *Fh, *Th, *Hh, *Fc, *Tc;
+    double *Fp, *Tq, *Hp; /* coupling of the previous time (force, torque, heat) */
+    int have_prev;
     double* wall_ft; /* [np][6][3] */
     contact* cont;
     int ncont;
@@ -693,15 +695,25 @@ static void contact_forces(orc_sim* s, double dt) {
         }
 }
 
+/* Hydrodynamic force, torque and heat felt by particle p over one lattice step:
+ * the mean of the coupling of time t and of time t-1.  Under the half-force
+ * velocity of the text after Eq lbm3.5 the fluid's physical momentum advances
+ * by the mean of consecutive forcing terms, so the particle receives the same
+ * mean; this removes the step-to-step sign flip that a bounce-back impulse
+ * (Eqs lbm7, lbm8) applied on every covered node imprints on the reaction. */
+static double hydro(const orc_sim* s, const double* cur, const double* prev, int k) {
+    return s->have_prev ? 0.5 * (cur[k] + prev[k]) : cur[k];
+}
+
 /* Eq demgov: m dU/dt = m (1 - rho_f/rho_p) g + F_fpi + sum F_c ; I domega/dt = tau_p + sum T_c */
 static void kick(orc_sim* s, double h) {
     for (int p = 0; p < s->np; p++) {
         if (s->fixed[p]) continue;
         double mg = s->m[p] * (1.0 - 1.0 / s->rho[p]);
         for (int a = 0; a < 3; a++) {
-            double F = s->Fc[3 * p + a] + s->Fh[3 * p + a] + mg * s->P.g_particle[a];
+            double F = s->Fc[3 * p + a] + hydro(s, s->Fh, s->Fp, 3 * p + a) + mg * s->P.g_particle[a];
             s->U[3 * p + a] += h * F / s->m[p];
-            s->W[3 * p + a] += h * (s->Tc[3 * p + a] + s->Th[3 * p + a]) / s->I[p];
+            s->W[3 * p + a] += h * (s->Tc[3 * p + a] + hydro(s, s->Th, s->Tq, 3 * p + a)) / s->I[p];
         }
         if (s->D == 2) {
             s->U[3 * p + 2] = 0.0;
@@ -771,7 +783,7 @@ orc_sim* orc_create(const orc_params* p) {
 
 static void free_particles(orc_sim* s) {
     double** arr[] = {&s->X, &s->U, &s->W, &s->R, &s->rho, &s->Tp, &s->Cp, &s->m, &s->I,
-                      &s->Fh, &s->Th, &s->Hh, &s->Fc, &s->Tc, &s->wall_ft};
+                      &s->Fh, &s->Th, &s->Hh, &s->Fc, &s->Tc, &s->Fp, &s->Tq, &s->Hp, &s->wall_ft};
     for (unsigned k = 0; k < sizeof(arr) / sizeof(arr[0]); k++) {
         free(*arr[k]);
         *arr[k] = NULL;
@@ -842,6 +854,10 @@ int orc_set_particles(orc_sim* s, int n, const double* X, const double* U, const
     s->Hh = (double*)calloc(n + 1, sizeof(double));
     s->Fc = (double*)calloc(3 * (n + 1), sizeof(double));
     s->Tc = (double*)calloc(3 * (n + 1), sizeof(double));
+    s->Fp = (double*)calloc(3 * (n + 1), sizeof(double));
+    s->Tq = (double*)calloc(3 * (n + 1), sizeof(double));
+    s->Hp = (double*)calloc(n + 1, sizeof(double));
+    s->have_prev = 0;
     s->wall_ft = (double*)calloc(18 * (n + 1), sizeof(double));
     s->fixed = (unsigned char*)calloc(n + 1, 1);
     for (int p = 0; p < n; p++) {
@@ -901,8 +917,14 @@ int orc_step(orc_sim* s, int nsteps) {
         lattice_step(s);
         dem(s);
         for (int p = 0; p < s->np; p++) /* thermosensitive particles: C_p dT_p = -H_p dt */
-            if (s->Cp[p] > 0.0) s->Tp[p] -= s->Hh[p] / s->Cp[p];
+            if (s->Cp[p] > 0.0) s->Tp[p] -= hydro(s, s->Hh, s->Hp, p) / s->Cp[p];
         s->t++;
+        if (s->np > 0) {
+            memcpy(s->Fp, s->Fh, sizeof(double) * 3 * s->np);
+            memcpy(s->Tq, s->Th, sizeof(double) * 3 * s->np);
+            memcpy(s->Hp, s->Hh, sizeof(double) * s->np);
+            s->have_prev = 1;
+        }
         coupling(s);
     }
     return 0;

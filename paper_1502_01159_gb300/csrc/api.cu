@@ -385,6 +385,9 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     c.m = (double*)A(v1), c.I = (double*)A(v1), c.mg = (double*)A(v1);
     c.fixed = (uint8_t*)A(n + 1);
     c.Fh = (double*)A(v3), c.Th = (double*)A(v3), c.Hh = (double*)A(v1), c.Fc = (double*)A(v3), c.Tc = (double*)A(v3);
+    c.Fh_prev = (double*)A(v3), c.Th_prev = (double*)A(v3), c.Hh_prev = (double*)A(v1);
+    c.have_prev = (int*)A(sizeof(int) * 2);
+    c.adj_start_new = (int*)A(sizeof(int) * (n + 2));
     c.box = (int*)A(sizeof(int) * 6 * (n + 1));
     c.cell_of = (int*)A(sizeof(int) * (n + 1));
     c.cell_cnt = (int*)A(sizeof(int) * (C.ncell + 1));
@@ -410,6 +413,7 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     c.contact_pairs = (int*)A(sizeof(int) * 2 * C.cap);
     c.contact_scratch = (int*)A(sizeof(int) * (2 * n + 8));
     void* need[] = {c.X, c.U, c.W, c.Xb, c.R, c.rho, c.Tp, c.Cp, c.m, c.I, c.mg, c.fixed, c.Fh, c.Th, c.Hh, c.Fc,
+                    c.Fh_prev, c.Th_prev, c.Hh_prev, c.have_prev, c.adj_start_new,
                     c.Tc, c.box, c.cell_of, c.cell_cnt, c.cell_start, c.cell_ids, c.cnt_hi, c.cnt_lo, c.nb_start[0],
                     c.nb_start[1], c.nb_i[0], c.nb_i[1], c.nb_j[0], c.nb_j[1], c.nb_ft[0], c.nb_ft[1], c.adj_start,
                     c.adj_nb, c.adj_k, c.pF, c.pTi, c.pTj, c.wall_ft, c.wF, c.wT, c.contact_pairs, c.contact_scratch};

@@ -26,6 +26,9 @@ constexpr int DEM_MAXNB = 64;
 
 struct DemState {
     double *X, *U, *W, *Xb, *R, *m, *I, *mg, *Tp, *Cp, *Fh, *Th, *Hh, *Fc, *Tc;
+    double *Fhp, *Thp, *Hhp;
+    int* have_prev;
+    int* adj_new;
     const uint8_t* fixed;
     int *cell_of, *cell_cnt, *cell_start, *cell_ids, *cnt_hi, *cnt_lo;
     int *nb_start0, *nb_start1, *nb_i0, *nb_i1, *nb_j0, *nb_j1;
@@ -124,12 +127,20 @@ __device__ __forceinline__ float3 tangential(const DemCfg& C, float* ft, float3 
     return f3(h.x - C.gt * vt.x, h.y - C.gt * vt.y, h.z - C.gt * vt.z);
 }
 
-__device__ __forceinline__ void kick(const DemCfg& C, const DemState& S, int p, double h) {
+// Hydrodynamic load over one lattice step: the mean of the couplings of time
+// t and t-1 (the half-force fluid momentum advances by the mean of consecutive
+// forcing terms; this also cancels the step-to-step sign flip of the
+// bounce-back impulse on covered nodes).
+__device__ __forceinline__ double hydro(const double* cur, const double* prev, int k, int hp) {
+    return hp ? 0.5 * (cur[k] + prev[k]) : cur[k];
+}
+
+__device__ __forceinline__ void kick(const DemCfg& C, const DemState& S, int p, double h, int hp) {
     double m = S.m[p], I = S.I[p], mg = S.mg[p];
     for (int a = 0; a < 3; a++) {
-        double F = S.Fc[3 * p + a] + S.Fh[3 * p + a] + mg * C.g[a];
+        double F = S.Fc[3 * p + a] + hydro(S.Fh, S.Fhp, 3 * p + a, hp) + mg * C.g[a];
         S.U[3 * p + a] += h * F / m;
-        S.W[3 * p + a] += h * (S.Tc[3 * p + a] + S.Th[3 * p + a]) / I;
+        S.W[3 * p + a] += h * (S.Tc[3 * p + a] + hydro(S.Th, S.Thp, 3 * p + a, hp)) / I;
     }
     if (C.dim == 2) {
         S.U[3 * p + 2] = 0.0;
@@ -194,9 +205,10 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
     const float half_skin2 = (float)(0.25 * C.skin * C.skin);
 
     if (advance) {
+        const int hp = __ldcg(S.have_prev);
         for (int p = gt; p < n; p += gs)
             if (!S.fixed[p]) {
-                kick(C, S, p, 0.5 * dt);
+                kick(C, S, p, 0.5 * dt, hp);
                 drift(C, S, p, dt, half_skin2);
             }
         cluster_barrier();
@@ -304,17 +316,25 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                     S.Tc[3 * p + a] = T[a];
                 }
                 if (S.fixed[p]) continue;
-                kick(C, S, p, 0.5 * dt);
+                kick(C, S, p, 0.5 * dt, hp);
                 if (sub + 1 < nsub) {
-                    kick(C, S, p, 0.5 * dt);
+                    kick(C, S, p, 0.5 * dt, hp);
                     drift(C, S, p, dt, half_skin2);
                 }
             }
             cluster_barrier();
         }
-        // thermosensitive particles: C_p dT_p / dt = -H_p over one lattice step
-        for (int p = gt; p < n; p += gs)
-            if (S.Cp[p] > 0.0) S.Tp[p] -= S.Hh[p] / S.Cp[p];
+        // thermosensitive particles: C_p dT_p / dt = -H_p over one lattice step;
+        // then keep this step's coupling as the previous one
+        for (int p = gt; p < n; p += gs) {
+            if (S.Cp[p] > 0.0) S.Tp[p] -= hydro(S.Hh, S.Hhp, p, hp) / S.Cp[p];
+            for (int a = 0; a < 3; a++) {
+                S.Fhp[3 * p + a] = S.Fh[3 * p + a];
+                S.Thp[3 * p + a] = S.Th[3 * p + a];
+            }
+            S.Hhp[p] = S.Hh[p];
+        }
+        if (gt == 0) *S.have_prev = 1;
     }
 
     // ------------------------------------------------ rebuild at new positions
@@ -388,14 +408,14 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
         cta_scan(S.cnt_hi, nst, n, sh);
         for (int i = threadIdx.x; i < n; i += blockDim.x) S.cnt_lo[i] += S.cnt_hi[i];
         __syncthreads();
-        cta_scan(S.cnt_lo, S.adj_start, n, sh);
-        if (threadIdx.x == 0 && (nst[n] > C.cap || S.adj_start[n] > S.adj_cap)) {
+        cta_scan(S.cnt_lo, S.adj_new, n, sh);
+        if (threadIdx.x == 0 && (nst[n] > C.cap || S.adj_new[n] > S.adj_cap)) {
             set_error(S.dstat, 3);
             *S.flag = 1;
         }
     }
     cluster_barrier();
-    if (__ldcg(S.flag)) return;  // keep the previous list; the host reports the status
+    if (__ldcg(S.flag)) return;  // keep the previous list and adjacency; the host reports the status
     for (int i = gt; i < n; i += gs) {
         double Xi[3];
         ldX(S.X, i, Xi);
@@ -458,7 +478,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             }
             cand[q + 1] = v;
         }
-        int e0 = __ldcg(S.adj_start + i);
+        int e0 = __ldcg(S.adj_new + i);
         for (int r = 0; r < cnt; r++) {
             int j = cand[r];
             int L = __ldcg(nst + j), Hh = __ldcg(nst + j + 1) - 1, found = -1;
@@ -479,6 +499,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
         }
     }
     cluster_barrier();
+    for (int i = gt; i <= n; i += gs) S.adj_start[i] = __ldcg(S.adj_new + i);
     if (gt == 0) *S.nb_cur = cur ^ 1;
 }
 
@@ -491,6 +512,8 @@ static DemState dem_state(Ctx* c) {
     DemState S;
     S.X = c->X, S.U = c->U, S.W = c->W, S.Xb = c->Xb, S.R = c->R, S.m = c->m, S.I = c->I, S.mg = c->mg;
     S.Tp = c->Tp, S.Cp = c->Cp, S.Fh = c->Fh, S.Th = c->Th, S.Hh = c->Hh, S.Fc = c->Fc, S.Tc = c->Tc;
+    S.Fhp = c->Fh_prev, S.Thp = c->Th_prev, S.Hhp = c->Hh_prev, S.have_prev = c->have_prev;
+    S.adj_new = c->adj_start_new;
     S.fixed = c->fixed;
     S.cell_of = c->cell_of, S.cell_cnt = c->cell_cnt, S.cell_start = c->cell_start, S.cell_ids = c->cell_ids;
     S.cnt_hi = c->cnt_hi, S.cnt_lo = c->cnt_lo;

@@ -205,6 +205,9 @@ struct Ctx {
     double *X, *U, *W, *Xb, *R, *rho, *Tp, *Cp, *m, *I, *mg;
     uint8_t* fixed;
     double *Fh, *Th, *Hh, *Fc, *Tc;
+    double *Fh_prev, *Th_prev, *Hh_prev;  // coupling of the previous time
+    int* have_prev;   // device int: 1 once a previous coupling exists
+    int* adj_start_new;  // scratch for the adjacency offsets of a rebuild
     int* box;         // spread box per particle (lo xyz, hi xyz); empty = hi < lo
     DemCfg dem;
     int *cell_of, *cell_cnt, *cell_start, *cell_ids, *cnt_hi, *cnt_lo;

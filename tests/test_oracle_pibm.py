@@ -164,3 +164,27 @@ def test_cavity_symmetry_about_vertical_bisector():
     # hot cylinder: the fluid above it rises
     uy = o.field("uy")[0]
     assert uy[24, 16] > 0 or uy[22, 15] > 0
+
+
+def test_sedimenting_disk_approaches_force_balance():
+    # A single disk settling in a closed box: the hydrodynamic force (Eq lbm13,
+    # applied as the mean of consecutive couplings) grows until it balances the
+    # buoyant weight m (1 - rho_f/rho_p) g of Eq demgov; the motion stays
+    # monotone and on the symmetry line (no step-to-step oscillation).
+    case = W.sed2d(nx=64, ny=160, n_p=0)
+    case["buoyancy"] = False
+    case["particles"] = dict(X=[[32.0, 120.0, 0.0]], R=[5.0], rho_p=[1.5], T_p=[0.5])
+    case["g_particle"] = [0.0, -2e-4, 0.0]
+    o = oracle.Oracle(case)
+    m = 1.5 * np.pi * 25.0
+    weight = m * (1 - 1 / 1.5) * 2e-4
+    speeds, ratios = [], []
+    for _ in range(8):
+        o.step(50)
+        speeds.append(-o.particles()["U"][0, 1])
+        ratios.append(o.particle_forces()["F"][0, 1] / weight)
+    assert all(b > a for a, b in zip(speeds, speeds[1:]))  # monotone acceleration
+    assert 0.0 < speeds[-1] < 0.01
+    assert all(b > a for a, b in zip(ratios, ratios[1:]))
+    assert 0.9 < ratios[-1] < 1.0
+    assert abs(o.particles()["X"][0, 0] - 32.0) < 1e-3
