@@ -50,6 +50,9 @@ def workload(name: str):
     elif name == "sed3d":
         case = W.sed3d()
         desc = "sed3d: 3-D sedimentation, 256x256x512 lattice, 2000 heated spheres d=8, D3Q19+D3Q7 FP32, Hertz, 10 DEM substeps"
+    elif name == "sed3d_mid":
+        case = W.sed3d(nx=128, ny=128, nz=256, n_p=250)
+        desc = "sed3d_mid: 3-D sedimentation, 128x128x256 lattice, 250 heated spheres d=8, D3Q19+D3Q7 FP32, Hertz, 10 DEM substeps (profiling size)"
     else:
         raise SystemExit(f"unknown workload {name}")
     return case, desc
@@ -344,7 +347,7 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sed2d", choices=["sed2d", "sed3d"])
+    ap.add_argument("--workload", default="sed2d", choices=["sed2d", "sed3d", "sed3d_mid"])
     ap.add_argument("--cpu-steps", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

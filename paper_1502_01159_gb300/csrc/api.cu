@@ -312,6 +312,7 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     double cmin = c.desc.cell_size > 0 ? c.desc.cell_size : 2.0 * rmax + 1.5;
     if (n > 0 && cmin < 2.0 * rmax + 1.0)
         return fail(ctx, PIBM_ERR_ARG, "cell size must be at least the largest diameter plus one node");
+    if (n > dem_max_particles()) return fail(ctx, PIBM_ERR_ARG, "too many particles for one DEM cluster");
 
     drop_graphs(c);
     dfree_group(ctx, GRP_PARTICLES);
@@ -399,24 +400,19 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
         c.nb_start[b] = (int*)A(sizeof(int) * (n + 2));
         c.nb_i[b] = (int*)A(sizeof(int) * C.cap);
         c.nb_j[b] = (int*)A(sizeof(int) * C.cap);
-        c.nb_ft[b] = (float*)A(sizeof(float) * 3 * C.cap);
+        c.nb_ft[b] = (float*)A(sizeof(float) * 2 * 3 * C.cap);  // two substep buffers
     }
     c.adj_start = (int*)A(sizeof(int) * (n + 2));
     c.adj_nb = (int*)A(sizeof(int) * c.adj_cap);
     c.adj_k = (int*)A(sizeof(int) * c.adj_cap);
-    c.pF = (float*)A(sizeof(float) * 3 * C.cap);
-    c.pTi = (float*)A(sizeof(float) * 3 * C.cap);
-    c.pTj = (float*)A(sizeof(float) * 3 * C.cap);
     c.wall_ft = (float*)A(sizeof(float) * 18 * (n + 1));
-    c.wF = (float*)A(sizeof(float) * 3 * (n + 1));
-    c.wT = (float*)A(sizeof(float) * 3 * (n + 1));
     c.contact_pairs = (int*)A(sizeof(int) * 2 * C.cap);
     c.contact_scratch = (int*)A(sizeof(int) * (2 * n + 8));
     void* need[] = {c.X, c.U, c.W, c.Xb, c.R, c.rho, c.Tp, c.Cp, c.m, c.I, c.mg, c.fixed, c.Fh, c.Th, c.Hh, c.Fc,
                     c.Fh_prev, c.Th_prev, c.Hh_prev, c.have_prev, c.adj_start_new,
                     c.Tc, c.box, c.cell_of, c.cell_cnt, c.cell_start, c.cell_ids, c.cnt_hi, c.cnt_lo, c.nb_start[0],
                     c.nb_start[1], c.nb_i[0], c.nb_i[1], c.nb_j[0], c.nb_j[1], c.nb_ft[0], c.nb_ft[1], c.adj_start,
-                    c.adj_nb, c.adj_k, c.pF, c.pTi, c.pTj, c.wall_ft, c.wF, c.wT, c.contact_pairs, c.contact_scratch};
+                    c.adj_nb, c.adj_k, c.wall_ft, c.contact_pairs, c.contact_scratch};
     for (void* p : need)
         if (!p) {
             dfree_group(ctx, GRP_PARTICLES);
@@ -437,6 +433,7 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     PCHECK(up(c.box, hbox.data(), sizeof(int) * 6 * n));
     PCHECK(cudaStreamSynchronize(c.s0));  // host vectors go out of scope
     c.np = n;
+    c.dem_cs = dem_cluster_size(&c);
     // neighbour list at the initial positions, then the coupling of the current time
     PCHECK(launch_dem(&c, c.s0, 0));
     pibm_status st = device_status(ctx);
@@ -729,7 +726,10 @@ pibm_status pibm_read_cells(pibm_ctx* ctx, int32_t* cell, int32_t* ncell) {
     Ctx& c = ctx->c;
     if (ncell)
         for (int a = 0; a < 3; a++) ncell[a] = c.np > 0 ? c.dem.nc[a] : 0;
-    if (c.np > 0 && cell) PCHECK(cudaMemcpyAsync(cell, c.cell_of, sizeof(int) * c.np, cudaMemcpyDeviceToHost, c.s0));
+    if (c.np > 0 && cell) {
+        PCHECK(launch_cells(&c, c.cell_of));
+        PCHECK(cudaMemcpyAsync(cell, c.cell_of, sizeof(int) * c.np, cudaMemcpyDeviceToHost, c.s0));
+    }
     return device_status(ctx);
 }
 

@@ -1,27 +1,36 @@
 // DEM kernels (Section 2.3, Eq demgov; Hertz normal law and
 // Mindlin-Deresiewicz loading stiffness, or a linear spring-dashpot law).
 //
-// One launch per lattice step runs as a thread-block cluster (up to 8 CTAs on
-// 8 SMs) and synchronises with the hardware cluster barrier, so all substeps
-// and the neighbour-list rebuild run without returning to the host:
-//   for each substep: half kick + drift (FP64), pair forces over the canonical
-//   neighbour list (pairs i < j, FP64 contact test, FP32 force law, tangential
-//   history per pair), per-particle sums in a fixed order over each particle's
-//   adjacency (so pair forces are applied with exactly opposite signs and no
-//   atomics), half kick;
-//   then the thermosensitive update C_p dT_p = -H_p and the rebuild at the new
-//   positions: cell ids (FP64, no contraction), counting sort stable by
-//   particle index, neighbour pairs within R_i + R_j + skin sorted by (i, j),
-//   tangential history carried over by binary search in the previous list.
-// The skin is the cell side minus the largest diameter; a particle that moves
-// more than half the skin within one lattice step raises a status word.
+// One launch per lattice step runs as one thread-block cluster (up to 16 CTAs
+// on 16 SMs).  Particle p belongs to CTA p / per.  Each CTA publishes the
+// positions (FP64) and velocities (FP32) of its particles in shared memory,
+// double-buffered by substep; every thread reads the published state of its
+// particles' neighbours directly from the owning CTA's shared memory
+// (distributed shared memory), so one hardware cluster barrier per substep
+// is the only synchronisation:
+//   substep: for each own particle, contact forces with every neighbour of
+//   the neighbour list -- each pair is evaluated in its canonical order
+//   (lower index first) by both partners with bit-identical inputs, so the two
+//   contributions are exactly opposite and no atomics are needed; the lower
+//   index writes the pair's tangential history into the other half of a
+//   double buffer -- plus wall contacts, then the velocity Verlet kicks and
+//   drift in FP64 and the publication of the new state.
+// After the substeps: the thermosensitive update C_p dT_p = -H_p, and -- only
+// when a particle has moved more than (skin - 1)/2 since the last build -- the
+// rebuild: FP64 cell ids (no contraction, the oracle's operation order),
+// counting sort stable by index, neighbour pairs within R_i + R_j + skin
+// sorted by (i, j), histories carried over by binary search.  A move larger
+// than half the skin within one lattice step raises a status word (contacts
+// could be missed).
 #include <cooperative_groups.h>
 
 #include "pibm_internal.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace pibm {
 
-constexpr int DEM_T = 256;
+constexpr int DEM_T = 128;
 constexpr int DEM_MAXNB = 64;
 
 struct DemState {
@@ -32,28 +41,20 @@ struct DemState {
     const uint8_t* fixed;
     int *cell_of, *cell_cnt, *cell_start, *cell_ids, *cnt_hi, *cnt_lo;
     int *nb_start0, *nb_start1, *nb_i0, *nb_i1, *nb_j0, *nb_j1;
-    float *nb_ft0, *nb_ft1;
-    int* nb_cur;
+    float *nb_ft0, *nb_ft1;  // per list: two substep buffers of 3 * cap floats
+    int* nb_cur;             // [0] current list, [1] current history buffer
     int *adj_start, *adj_nb, *adj_k;
-    float *pF, *pTi, *pTj, *wall_ft, *wF, *wT;
+    float* wall_ft;
     int* dstat;
     int* flag;  // cluster-wide overflow flag
     int adj_cap;
 };
 
-__device__ __forceinline__ void cluster_barrier() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
-__device__ __forceinline__ unsigned cluster_rank() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ unsigned cluster_size() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-    return r;
-}
+// state a CTA publishes for each of its particles
+struct Pub {
+    double x[3];
+    float u[3], w[3];
+};
 
 __device__ __forceinline__ void set_error(int* dstat, int detail) {
     if (atomicCAS(dstat, 0, (int)PIBM_ERR_STATE) == 0) dstat[1] = detail;
@@ -113,8 +114,7 @@ __device__ __forceinline__ float normal_law(const DemCfg& C, float delta, float 
 
 // Tangential force: history projected on the tangent plane, incremented by
 // -k_t v_t dt, capped at mu |F_n|; returns the total with tangential damping.
-__device__ __forceinline__ float3 tangential(const DemCfg& C, float* ft, float3 n, float3 vt, float kt_eff, float Fn, float dt) {
-    float3 h = f3(ft[0], ft[1], ft[2]);
+__device__ __forceinline__ float3 tangential(const DemCfg& C, float3& h, float3 n, float3 vt, float kt_eff, float Fn, float dt) {
     float hn = h.x * n.x + h.y * n.y + h.z * n.z;
     h = f3(h.x - hn * n.x - kt_eff * vt.x * dt, h.y - hn * n.y - kt_eff * vt.y * dt, h.z - hn * n.z - kt_eff * vt.z * dt);
     float mag = sqrtf(h.x * h.x + h.y * h.y + h.z * h.z);
@@ -123,8 +123,35 @@ __device__ __forceinline__ float3 tangential(const DemCfg& C, float* ft, float3 
         float sc = mag > 0.f ? cap / mag : 0.f;
         h = f3(h.x * sc, h.y * sc, h.z * sc);
     }
-    ft[0] = h.x, ft[1] = h.y, ft[2] = h.z;
     return f3(h.x - C.gt * vt.x, h.y - C.gt * vt.y, h.z - C.gt * vt.z);
+}
+
+// Pair (a < b) in canonical order: force on a, torques on a and b, new
+// history.  Both partners call this with the same inputs and get the same bits.
+__device__ __forceinline__ void pair_force(const DemCfg& C, const Pub& A, const Pub& B, double Ra, double Rb,
+                                           float3& h, float dtf, float3& Fa, float3& Ta, float3& Tb) {
+    double d2 = dist2(A.x, B.x);
+    double S = Ra + Rb;
+    if (!(d2 < S * S)) {
+        h = f3(0.f, 0.f, 0.f);
+        Fa = Ta = Tb = f3(0.f, 0.f, 0.f);
+        return;
+    }
+    float distf = sqrtf((float)d2);
+    float delta = (float)(S * S - d2) / ((float)S + distf);
+    float3 nn = f3((float)(B.x[0] - A.x[0]) / distf, (float)(B.x[1] - A.x[1]) / distf, (float)(B.x[2] - A.x[2]) / distf);
+    float ai = (float)Ra - 0.5f * delta, aj = (float)Rb - 0.5f * delta;
+    float3 wi = cross3(f3(A.w[0], A.w[1], A.w[2]), f3(ai * nn.x, ai * nn.y, ai * nn.z));
+    float3 wj = cross3(f3(B.w[0], B.w[1], B.w[2]), f3(-aj * nn.x, -aj * nn.y, -aj * nn.z));
+    float3 vr = f3(A.u[0] + wi.x - B.u[0] - wj.x, A.u[1] + wi.y - B.u[1] - wj.y, A.u[2] + wi.z - B.u[2] - wj.z);
+    float vn = vr.x * nn.x + vr.y * nn.y + vr.z * nn.z;
+    float3 vt = f3(vr.x - vn * nn.x, vr.y - vn * nn.y, vr.z - vn * nn.z);
+    float Rstar = (float)(Ra * Rb / S), kt_eff;
+    float Fn = normal_law(C, delta, vn, Rstar, &kt_eff);
+    float3 Ft = tangential(C, h, nn, vt, kt_eff, Fn, dtf);
+    Ta = cross3(f3(ai * nn.x, ai * nn.y, ai * nn.z), Ft);
+    Tb = cross3(f3(aj * nn.x, aj * nn.y, aj * nn.z), Ft);
+    Fa = f3(-Fn * nn.x + Ft.x, -Fn * nn.y + Ft.y, -Fn * nn.z + Ft.z);
 }
 
 // Hydrodynamic load over one lattice step: the mean of the couplings of time
@@ -149,14 +176,27 @@ __device__ __forceinline__ void kick(const DemCfg& C, const DemState& S, int p, 
     }
 }
 
-__device__ __forceinline__ void drift(const DemCfg& C, const DemState& S, int p, double dt, float half_skin2) {
+// drift and publish the particle's new state into pub
+__device__ __forceinline__ void drift_publish(const DemCfg& C, const DemState& S, int p, double dt, Pub& pub) {
     double d2 = 0;
     for (int a = 0; a < 3; a++) {
-        S.X[3 * p + a] += dt * S.U[3 * p + a];
-        double d = S.X[3 * p + a] - S.Xb[3 * p + a];
+        double x = S.X[3 * p + a] + dt * S.U[3 * p + a];
+        S.X[3 * p + a] = x;
+        pub.x[a] = x;
+        pub.u[a] = (float)S.U[3 * p + a];
+        pub.w[a] = (float)S.W[3 * p + a];
+        double d = x - S.Xb[3 * p + a];
         d2 += d * d;
     }
-    if (d2 > (double)half_skin2) set_error(S.dstat, 2);
+    if (d2 > 0.25 * C.skin * C.skin) set_error(S.dstat, 2);
+}
+
+__device__ __forceinline__ void publish(const DemState& S, int p, Pub& pub) {
+    for (int a = 0; a < 3; a++) {
+        pub.x[a] = S.X[3 * p + a];
+        pub.u[a] = (float)S.U[3 * p + a];
+        pub.w[a] = (float)S.W[3 * p + a];
+    }
 }
 
 template <int D>
@@ -189,152 +229,164 @@ __device__ __forceinline__ void for_neighbours(const DemCfg& C, const DemState& 
     }
 }
 
+// wall contacts of particle p (same law, R_wall = infinity, wall at rest)
+template <int D>
+__device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, int p, const Pub& me, double Rp, float dtf,
+                                            double* F, double* T) {
+    for (int face = 0; face < 2 * D; face++) {
+        int a = face >> 1, hi = face & 1;
+        if (!C.walled[a]) continue;
+        float* ftp = S.wall_ft + 3 * (6 * p + face);
+        double dist = hi ? C.hi[a] - me.x[a] : me.x[a] - C.lo[a];
+        double dd = Rp - dist;
+        if (!(dd > 0.0)) {
+            if (ftp[0] != 0.f || ftp[1] != 0.f || ftp[2] != 0.f) ftp[0] = ftp[1] = ftp[2] = 0.f;
+            continue;
+        }
+        float delta = (float)dd;
+        float3 nn = f3(0, 0, 0);
+        if (a == 0) nn.x = hi ? 1.f : -1.f;
+        else if (a == 1) nn.y = hi ? 1.f : -1.f;
+        else nn.z = hi ? 1.f : -1.f;
+        float ai = (float)Rp - 0.5f * delta;
+        float3 ri = f3(ai * nn.x, ai * nn.y, ai * nn.z);
+        float3 wi = cross3(f3(me.w[0], me.w[1], me.w[2]), ri);
+        float3 vr = f3(me.u[0] + wi.x, me.u[1] + wi.y, me.u[2] + wi.z);
+        float vn = vr.x * nn.x + vr.y * nn.y + vr.z * nn.z;
+        float3 vt = f3(vr.x - vn * nn.x, vr.y - vn * nn.y, vr.z - vn * nn.z);
+        float kt_eff;
+        float Fn = normal_law(C, delta, vn, (float)Rp, &kt_eff);
+        float3 h = f3(ftp[0], ftp[1], ftp[2]);
+        float3 Ft = tangential(C, h, nn, vt, kt_eff, Fn, dtf);
+        ftp[0] = h.x, ftp[1] = h.y, ftp[2] = h.z;
+        float3 Ti = cross3(ri, Ft);
+        F[0] += -Fn * nn.x + Ft.x, F[1] += -Fn * nn.y + Ft.y, F[2] += -Fn * nn.z + Ft.z;
+        T[0] += Ti.x, T[1] += Ti.y, T[2] += Ti.z;
+    }
+}
+
 template <int D>
 __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, int advance) {
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int sh[DEM_T];
+    __shared__ int need_flag;
+    cg::cluster_group cl = cg::this_cluster();
+    const int per = C.per;
+    Pub* pub = reinterpret_cast<Pub*>(smem);                   // [2][per]
+    double* Rsh = reinterpret_cast<double*>(pub + 2 * per);     // [per]
     const int n = C.n;
-    const unsigned rank = cluster_rank();
-    const int gt = rank * blockDim.x + threadIdx.x, gs = cluster_size() * blockDim.x;
+    const unsigned rank = cl.block_rank();
+    const unsigned csize = cl.num_blocks();
+    const int gt = rank * blockDim.x + threadIdx.x, gs = csize * blockDim.x;
+    const int base = rank * per;
+    const int nloc = max(0, min(per, n - base));
     const int cur = __ldcg(S.nb_cur);
-    int* nb_start = cur ? S.nb_start1 : S.nb_start0;
-    int* nb_i = cur ? S.nb_i1 : S.nb_i0;
-    int* nb_j = cur ? S.nb_j1 : S.nb_j0;
+    const int hcur = __ldcg(S.nb_cur + 1);
+    const int* nb_start = cur ? S.nb_start1 : S.nb_start0;
+    const int* nb_j = cur ? S.nb_j1 : S.nb_j0;
     float* nb_ft = cur ? S.nb_ft1 : S.nb_ft0;
     const double dt = C.dt;
     const float dtf = (float)dt;
-    const float half_skin2 = (float)(0.25 * C.skin * C.skin);
+    int hfinal = hcur;
+
+    for (int l = threadIdx.x; l < nloc; l += blockDim.x) Rsh[l] = S.R[base + l];
 
     if (advance) {
         const int hp = __ldcg(S.have_prev);
-        for (int p = gt; p < n; p += gs)
+        for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
+            int p = base + l;
             if (!S.fixed[p]) {
                 kick(C, S, p, 0.5 * dt, hp);
-                drift(C, S, p, dt, half_skin2);
+                drift_publish(C, S, p, dt, pub[l]);
+            } else {
+                publish(S, p, pub[l]);
             }
-        cluster_barrier();
-        const int npairs = __ldcg(nb_start + n);
+        }
+        cl.sync();
         for (int sub = 0; sub < nsub; sub++) {
-            // pair forces at the drifted positions with the half-kicked velocities
-            for (int k = gt; k < npairs; k += gs) {
-                int i = __ldcg(nb_i + k), j = __ldcg(nb_j + k);
-                double Xi[3], Xj[3];
-                ldX(S.X, i, Xi);
-                ldX(S.X, j, Xj);
-                double d2 = dist2(Xi, Xj);
-                double Ssum = S.R[i] + S.R[j];
-                float* ft = nb_ft + 3 * k;
-                if (!(d2 < Ssum * Ssum)) {
-                    ft[0] = ft[1] = ft[2] = 0.f;
-                    S.pF[3 * k] = S.pF[3 * k + 1] = S.pF[3 * k + 2] = 0.f;
-                    S.pTi[3 * k] = S.pTi[3 * k + 1] = S.pTi[3 * k + 2] = 0.f;
-                    S.pTj[3 * k] = S.pTj[3 * k + 1] = S.pTj[3 * k + 2] = 0.f;
-                    continue;
-                }
-                float distf = sqrtf((float)d2);
-                float delta = (float)(Ssum * Ssum - d2) / ((float)Ssum + distf);
-                float3 nn = f3((float)(Xj[0] - Xi[0]) / distf, (float)(Xj[1] - Xi[1]) / distf, (float)(Xj[2] - Xi[2]) / distf);
-                float ai = (float)S.R[i] - 0.5f * delta, aj = (float)S.R[j] - 0.5f * delta;
-                float3 Ui = f3(__ldcg(S.U + 3 * i), __ldcg(S.U + 3 * i + 1), __ldcg(S.U + 3 * i + 2));
-                float3 Uj = f3(__ldcg(S.U + 3 * j), __ldcg(S.U + 3 * j + 1), __ldcg(S.U + 3 * j + 2));
-                float3 Wi = f3(__ldcg(S.W + 3 * i), __ldcg(S.W + 3 * i + 1), __ldcg(S.W + 3 * i + 2));
-                float3 Wj = f3(__ldcg(S.W + 3 * j), __ldcg(S.W + 3 * j + 1), __ldcg(S.W + 3 * j + 2));
-                float3 wi = cross3(Wi, f3(ai * nn.x, ai * nn.y, ai * nn.z));
-                float3 wj = cross3(Wj, f3(-aj * nn.x, -aj * nn.y, -aj * nn.z));
-                float3 vr = f3(Ui.x + wi.x - Uj.x - wj.x, Ui.y + wi.y - Uj.y - wj.y, Ui.z + wi.z - Uj.z - wj.z);
-                float vn = vr.x * nn.x + vr.y * nn.y + vr.z * nn.z;
-                float3 vt = f3(vr.x - vn * nn.x, vr.y - vn * nn.y, vr.z - vn * nn.z);
-                float Rstar = (float)(S.R[i] * S.R[j] / Ssum), kt_eff;
-                float Fn = normal_law(C, delta, vn, Rstar, &kt_eff);
-                float3 Ft = tangential(C, ft, nn, vt, kt_eff, Fn, dtf);
-                float3 Ti = cross3(f3(ai * nn.x, ai * nn.y, ai * nn.z), Ft);
-                float3 Tj = cross3(f3(aj * nn.x, aj * nn.y, aj * nn.z), Ft);
-                S.pF[3 * k] = -Fn * nn.x + Ft.x;
-                S.pF[3 * k + 1] = -Fn * nn.y + Ft.y;
-                S.pF[3 * k + 2] = -Fn * nn.z + Ft.z;
-                S.pTi[3 * k] = Ti.x, S.pTi[3 * k + 1] = Ti.y, S.pTi[3 * k + 2] = Ti.z;
-                S.pTj[3 * k] = Tj.x, S.pTj[3 * k + 1] = Tj.y, S.pTj[3 * k + 2] = Tj.z;
-            }
-            // particle-wall contacts: the same law with R_wall = infinity
-            for (int p = gt; p < n; p += gs) {
-                float3 F = f3(0, 0, 0), T = f3(0, 0, 0);
-                for (int face = 0; face < 2 * D; face++) {
-                    int a = face >> 1, hi = face & 1;
-                    float* ft = S.wall_ft + 3 * (6 * p + face);
-                    if (!C.walled[a]) continue;
-                    double Xa = __ldcg(S.X + 3 * p + a);
-                    double dist = hi ? C.hi[a] - Xa : Xa - C.lo[a];
-                    double dd = S.R[p] - dist;
-                    if (!(dd > 0.0)) {
-                        ft[0] = ft[1] = ft[2] = 0.f;
-                        continue;
-                    }
-                    float delta = (float)dd;
-                    float3 nn = f3(0, 0, 0);
-                    if (a == 0) nn.x = hi ? 1.f : -1.f;
-                    else if (a == 1) nn.y = hi ? 1.f : -1.f;
-                    else nn.z = hi ? 1.f : -1.f;
-                    float ai = (float)S.R[p] - 0.5f * delta;
-                    float3 Ui = f3(__ldcg(S.U + 3 * p), __ldcg(S.U + 3 * p + 1), __ldcg(S.U + 3 * p + 2));
-                    float3 Wi = f3(__ldcg(S.W + 3 * p), __ldcg(S.W + 3 * p + 1), __ldcg(S.W + 3 * p + 2));
-                    float3 ri = f3(ai * nn.x, ai * nn.y, ai * nn.z);
-                    float3 wi = cross3(Wi, ri);
-                    float3 vr = f3(Ui.x + wi.x, Ui.y + wi.y, Ui.z + wi.z);
-                    float vn = vr.x * nn.x + vr.y * nn.y + vr.z * nn.z;
-                    float3 vt = f3(vr.x - vn * nn.x, vr.y - vn * nn.y, vr.z - vn * nn.z);
-                    float kt_eff;
-                    float Fn = normal_law(C, delta, vn, (float)S.R[p], &kt_eff);
-                    float3 Ft = tangential(C, ft, nn, vt, kt_eff, Fn, dtf);
-                    float3 Ti = cross3(ri, Ft);
-                    F = f3(F.x - Fn * nn.x + Ft.x, F.y - Fn * nn.y + Ft.y, F.z - Fn * nn.z + Ft.z);
-                    T = f3(T.x + Ti.x, T.y + Ti.y, T.z + Ti.z);
-                }
-                S.wF[3 * p] = F.x, S.wF[3 * p + 1] = F.y, S.wF[3 * p + 2] = F.z;
-                S.wT[3 * p] = T.x, S.wT[3 * p + 1] = T.y, S.wT[3 * p + 2] = T.z;
-            }
-            cluster_barrier();
-            // per-particle sums over the adjacency in index order, then the kicks
-            for (int p = gt; p < n; p += gs) {
-                double F[3] = {S.wF[3 * p], S.wF[3 * p + 1], S.wF[3 * p + 2]};
-                double T[3] = {S.wT[3 * p], S.wT[3 * p + 1], S.wT[3 * p + 2]};
-                for (int e = S.adj_start[p]; e < S.adj_start[p + 1]; e++) {
-                    int k = S.adj_k[e];
-                    if (k >= 0) {
-                        for (int a = 0; a < 3; a++) {
-                            F[a] += (double)__ldcg(S.pF + 3 * k + a);
-                            T[a] += (double)__ldcg(S.pTi + 3 * k + a);
-                        }
+            const int rb = sub & 1;                      // published buffer read this substep
+            const int hb = (hcur + sub) & 1;             // history buffer read this substep
+            float* hist_old = nb_ft + (size_t)hb * 3 * C.cap;
+            float* hist_new = nb_ft + (size_t)(hb ^ 1) * 3 * C.cap;
+            for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
+                const int p = base + l;
+                const Pub me = pub[rb * per + l];
+                const double Rp = Rsh[l];
+                double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+                wall_forces<D>(C, S, p, me, Rp, dtf, F, T);
+                const int e1 = S.adj_start[p + 1];
+                for (int e = S.adj_start[p]; e < e1; e++) {
+                    const int q = S.adj_nb[e];
+                    const int kk = S.adj_k[e];
+                    const bool first = kk >= 0;
+                    const int k = first ? kk : ~kk;
+                    const int rq = q / per, lq = q - rq * per;
+                    const Pub* rpub = cl.map_shared_rank(pub, rq);
+                    const double* rR = cl.map_shared_rank(Rsh, rq);
+                    const Pub other = rpub[rb * per + lq];
+                    const double Rq = rR[lq];
+                    const Pub& A = first ? me : other;
+                    const Pub& B = first ? other : me;
+                    const double Ra = first ? Rp : Rq, Rb = first ? Rq : Rp;
+                    float3 h = f3(0.f, 0.f, 0.f), Fa, Ta, Tb;
+                    double d2 = dist2(A.x, B.x), Ssum = Ra + Rb;
+                    if (d2 < Ssum * Ssum) h = f3(__ldcg(hist_old + 3 * k), __ldcg(hist_old + 3 * k + 1), __ldcg(hist_old + 3 * k + 2));
+                    pair_force(C, A, B, Ra, Rb, h, dtf, Fa, Ta, Tb);
+                    if (first) {
+                        float* hn = hist_new + 3 * k;
+                        hn[0] = h.x, hn[1] = h.y, hn[2] = h.z;
+                        F[0] += Fa.x, F[1] += Fa.y, F[2] += Fa.z;
+                        T[0] += Ta.x, T[1] += Ta.y, T[2] += Ta.z;
                     } else {
-                        k = ~k;
-                        for (int a = 0; a < 3; a++) {
-                            F[a] -= (double)__ldcg(S.pF + 3 * k + a);
-                            T[a] += (double)__ldcg(S.pTj + 3 * k + a);
-                        }
+                        F[0] -= Fa.x, F[1] -= Fa.y, F[2] -= Fa.z;
+                        T[0] += Tb.x, T[1] += Tb.y, T[2] += Tb.z;
                     }
                 }
                 for (int a = 0; a < 3; a++) {
                     S.Fc[3 * p + a] = F[a];
                     S.Tc[3 * p + a] = T[a];
                 }
-                if (S.fixed[p]) continue;
+                if (S.fixed[p]) {
+                    publish(S, p, pub[(rb ^ 1) * per + l]);
+                    continue;
+                }
                 kick(C, S, p, 0.5 * dt, hp);
                 if (sub + 1 < nsub) {
                     kick(C, S, p, 0.5 * dt, hp);
-                    drift(C, S, p, dt, half_skin2);
+                    drift_publish(C, S, p, dt, pub[(rb ^ 1) * per + l]);
                 }
             }
-            cluster_barrier();
+            cl.sync();
         }
+        hfinal = (hcur + nsub) & 1;
         // thermosensitive particles: C_p dT_p / dt = -H_p over one lattice step;
         // then keep this step's coupling as the previous one
-        for (int p = gt; p < n; p += gs) {
+        int moved = 0;
+        const double thr2 = 0.25 * (C.skin - 1.0) * (C.skin - 1.0);
+        for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
+            int p = base + l;
             if (S.Cp[p] > 0.0) S.Tp[p] -= hydro(S.Hh, S.Hhp, p, hp) / S.Cp[p];
+            double d2 = 0;
             for (int a = 0; a < 3; a++) {
                 S.Fhp[3 * p + a] = S.Fh[3 * p + a];
                 S.Thp[3 * p + a] = S.Th[3 * p + a];
+                double d = S.X[3 * p + a] - S.Xb[3 * p + a];
+                d2 += d * d;
             }
             S.Hhp[p] = S.Hh[p];
+            if (d2 > thr2) moved = 1;
         }
+        moved = __syncthreads_or(moved);
+        if (threadIdx.x == 0) need_flag = moved;
         if (gt == 0) *S.have_prev = 1;
+        cl.sync();
+        int need = 0;
+        for (unsigned r = 0; r < csize; r++) need |= *cl.map_shared_rank(&need_flag, r);
+        if (!need) {
+            cl.sync();  // no CTA may exit while others still read its shared memory
+            if (gt == 0) S.nb_cur[1] = hfinal;
+            return;
+        }
     }
 
     // ------------------------------------------------ rebuild at new positions
@@ -344,24 +396,23 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
         int c[3];
         cell_coords<D>(C, Xp, c);
         S.cell_of[p] = (c[2] * C.nc[1] + c[1]) * C.nc[0] + c[0];
-        for (int a = 0; a < 3; a++) S.Xb[3 * p + a] = Xp[a];
     }
     for (int cidx = gt; cidx < C.ncell; cidx += gs) S.cell_cnt[cidx] = 0;
     if (gt == 0) *S.flag = 0;
-    cluster_barrier();
+    cl.sync();
     for (int p = gt; p < n; p += gs) atomicAdd(S.cell_cnt + __ldcg(S.cell_of + p), 1);
-    cluster_barrier();
+    cl.sync();
     if (rank == 0) {
         cta_scan(S.cell_cnt, S.cell_start, C.ncell, sh);
         for (int cidx = threadIdx.x; cidx < C.ncell; cidx += blockDim.x) S.cell_cnt[cidx] = 0;
     }
-    cluster_barrier();
+    cl.sync();
     for (int p = gt; p < n; p += gs) {
         int cidx = __ldcg(S.cell_of + p);
         int pos = atomicAdd(S.cell_cnt + cidx, 1);
         S.cell_ids[__ldcg(S.cell_start + cidx) + pos] = p;
     }
-    cluster_barrier();
+    cl.sync();
     for (int cidx = gt; cidx < C.ncell; cidx += gs) {  // stable order: by particle index
         int b = __ldcg(S.cell_start + cidx), e = __ldcg(S.cell_start + cidx + 1);
         for (int a = b + 1; a < e; a++) {
@@ -373,7 +424,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             S.cell_ids[q + 1] = v;
         }
     }
-    cluster_barrier();
+    cl.sync();
     // neighbour counts (pairs within R_i + R_j + skin)
     for (int i = gt; i < n; i += gs) {
         double Xi[3];
@@ -399,11 +450,12 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             atomicExch(S.flag, 1);
         }
     }
-    cluster_barrier();
+    cl.sync();
     int* nst = cur ? S.nb_start0 : S.nb_start1;
     int* ni = cur ? S.nb_i0 : S.nb_i1;
     int* nj = cur ? S.nb_j0 : S.nb_j1;
-    float* nft = cur ? S.nb_ft0 : S.nb_ft1;
+    float* nft = cur ? S.nb_ft0 : S.nb_ft1;   // new history goes into buffer 0
+    const float* oft = nb_ft + (size_t)hfinal * 3 * C.cap;
     if (rank == 0) {
         cta_scan(S.cnt_hi, nst, n, sh);
         for (int i = threadIdx.x; i < n; i += blockDim.x) S.cnt_lo[i] += S.cnt_hi[i];
@@ -414,8 +466,11 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             *S.flag = 1;
         }
     }
-    cluster_barrier();
-    if (__ldcg(S.flag)) return;  // keep the previous list and adjacency; the host reports the status
+    cl.sync();
+    if (__ldcg(S.flag)) {  // keep the previous list and adjacency; the host reports the status
+        if (gt == 0) S.nb_cur[1] = hfinal;
+        return;
+    }
     for (int i = gt; i < n; i += gs) {
         double Xi[3];
         ldX(S.X, i, Xi);
@@ -451,10 +506,10 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 if (v < j) L = mid + 1;
                 else Hh = mid - 1;
             }
-            for (int a = 0; a < 3; a++) nft[3 * (o + r) + a] = found >= 0 ? nb_ft[3 * found + a] : 0.f;
+            for (int a = 0; a < 3; a++) nft[3 * (o + r) + a] = found >= 0 ? oft[3 * found + a] : 0.f;
         }
     }
-    cluster_barrier();
+    cl.sync();
     // adjacency of each particle: partners j < i (pair found in j's segment), then j > i
     for (int i = gt; i < n; i += gs) {
         double Xi[3];
@@ -497,16 +552,54 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             S.adj_nb[e0 + cnt + r] = __ldcg(nj + o + r);
             S.adj_k[e0 + cnt + r] = o + r;
         }
+        for (int a = 0; a < 3; a++) S.Xb[3 * i + a] = Xi[a];
     }
-    cluster_barrier();
+    cl.sync();
     for (int i = gt; i <= n; i += gs) S.adj_start[i] = __ldcg(S.adj_new + i);
-    if (gt == 0) *S.nb_cur = cur ^ 1;
+    if (gt == 0) {
+        S.nb_cur[0] = cur ^ 1;
+        S.nb_cur[1] = 0;
+    }
 }
 
+// cluster size: up to 16 CTAs of DEM_T threads, at most DEM_MAXPER particles per CTA
+constexpr int DEM_MAXPER = 2048;
+
+static size_t dem_smem(int per) { return (size_t)per * (2 * sizeof(Pub) + sizeof(double)); }
+
 int dem_cluster_size(Ctx* c) {
-    int cs = (c->np + 63) / 64;
-    return cs < 1 ? 1 : (cs > 8 ? 8 : cs);
+    int n = c->np;
+    int cs = (n + 63) / 64;
+    cs = cs < 1 ? 1 : (cs > 16 ? 16 : cs);
+    if (cs > 8) {
+        int max16 = 0;  // is a 16-CTA cluster with this much shared memory schedulable here?
+        {
+            auto kern = c->D == 2 ? k_dem<2> : k_dem<3>;
+            int per = (n + 15) / 16;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dem_smem(DEM_MAXPER)) == cudaSuccess) {
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(16, 1, 1);
+                cfg.blockDim = dim3(DEM_T, 1, 1);
+                cfg.dynamicSmemBytes = dem_smem(per);
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = 16;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                int clusters = 0;
+                if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters > 0) max16 = 1;
+            }
+            cudaGetLastError();
+        }
+        if (!max16) cs = 8;
+    }
+    return cs;
 }
+
+int dem_max_particles() { return 16 * DEM_MAXPER; }
 
 static DemState dem_state(Ctx* c) {
     DemState S;
@@ -523,7 +616,7 @@ static DemState dem_state(Ctx* c) {
     S.nb_ft0 = c->nb_ft[0], S.nb_ft1 = c->nb_ft[1];
     S.nb_cur = c->nb_cur;
     S.adj_start = c->adj_start, S.adj_nb = c->adj_nb, S.adj_k = c->adj_k;
-    S.pF = c->pF, S.pTi = c->pTi, S.pTj = c->pTj, S.wall_ft = c->wall_ft, S.wF = c->wF, S.wT = c->wT;
+    S.wall_ft = c->wall_ft;
     S.dstat = c->dstat;
     S.flag = c->dstat + 2;
     S.adj_cap = c->adj_cap;
@@ -532,11 +625,21 @@ static DemState dem_state(Ctx* c) {
 
 cudaError_t launch_dem(Ctx* c, cudaStream_t s, int nsub) {
     if (c->np <= 0) return cudaSuccess;
-    int cs = dem_cluster_size(c);
+    int cs = c->dem_cs;
+    DemCfg C = c->dem;
+    C.per = (c->np + cs - 1) / cs;
+    auto kern = c->D == 2 ? k_dem<2> : k_dem<3>;
+    size_t smem = dem_smem(C.per);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dem_smem(DEM_MAXPER));
+    if (e != cudaSuccess) return e;
+    if (cs > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);
     cfg.blockDim = dim3(DEM_T, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -547,8 +650,7 @@ cudaError_t launch_dem(Ctx* c, cudaStream_t s, int nsub) {
     cfg.numAttrs = 1;
     DemState S = dem_state(c);
     int advance = nsub > 0 ? 1 : 0;
-    if (c->D == 2) return cudaLaunchKernelEx(&cfg, k_dem<2>, c->dem, S, nsub, advance);
-    return cudaLaunchKernelEx(&cfg, k_dem<3>, c->dem, S, nsub, advance);
+    return cudaLaunchKernelEx(&cfg, kern, C, S, nsub, advance);
 }
 
 // ---------------------------------------------------- contacts for read-back
@@ -591,10 +693,28 @@ __global__ void __launch_bounds__(DEM_T) k_contacts(int n, const double* X, cons
 }
 
 cudaError_t launch_contacts(Ctx* c, int* d_pairs, int cap, int* d_count) {
-    // scratch: cnt (n) + offsets (n + 1) in cnt_hi / cnt_lo region is not large
-    // enough in general; the caller passes d_count with room for 2n + 2 ints.
+    // d_count: total, then per-particle counts (n) and their offsets (n + 1)
     k_contacts<<<1, DEM_T, 0, c->s0>>>(c->np, c->X, c->R, c->nb_cur, c->nb_start[0], c->nb_start[1], c->nb_j[0],
                                        c->nb_j[1], d_count + 1, d_pairs, cap, d_count);
+    return cudaGetLastError();
+}
+
+// cell of each particle at the current positions (same definition as the rebuild)
+template <int D>
+__global__ void k_cells(DemCfg C, const double* X, int n, int* cell) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        double Xp[3] = {X[3 * p], X[3 * p + 1], X[3 * p + 2]};
+        int c[3];
+        cell_coords<D>(C, Xp, c);
+        cell[p] = (c[2] * C.nc[1] + c[1]) * C.nc[0] + c[0];
+    }
+}
+
+cudaError_t launch_cells(Ctx* c, int* d_cell) {
+    if (c->np <= 0) return cudaSuccess;
+    int blocks = (c->np + 255) / 256;
+    if (c->D == 2) k_cells<2><<<blocks, 256, 0, c->s0>>>(c->dem, c->X, c->np, d_cell);
+    else k_cells<3><<<blocks, 256, 0, c->s0>>>(c->dem, c->X, c->np, d_cell);
     return cudaGetLastError();
 }
 

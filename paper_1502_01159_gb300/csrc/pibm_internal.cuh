@@ -171,6 +171,7 @@ struct DemCfg {
     double skin;      // neighbour-list margin
     int cap;          // capacity of the canonical pair list
     int maxnb;        // candidates per particle
+    int per;          // particles per CTA of the DEM cluster
 };
 
 struct Ctx {
@@ -215,10 +216,11 @@ struct Ctx {
     int* nb_i[2];
     int* nb_j[2];
     float* nb_ft[2];
-    int* nb_cur;      // device int: which list is current
+    int* nb_cur;      // device ints: current list, current history buffer
     int *adj_start, *adj_nb, *adj_k;
-    float *pF, *pTi, *pTj, *wall_ft, *wF, *wT;
+    float* wall_ft;
     int adj_cap;
+    int dem_cs;           // CTAs in the DEM cluster
     int* contact_pairs;   // 2 * dem.cap ints
     int* contact_scratch; // 2 * np + 4 ints
 
@@ -253,6 +255,8 @@ int coupling_kernel_count(Ctx* c);
 // dem.cu
 cudaError_t launch_dem(Ctx* c, cudaStream_t s, int nsub);
 cudaError_t launch_contacts(Ctx* c, int* d_pairs, int cap, int* d_count);
+cudaError_t launch_cells(Ctx* c, int* d_cell);
 int dem_cluster_size(Ctx* c);
+int dem_max_particles();
 
 }  // namespace pibm

@@ -131,8 +131,11 @@ def test_sedimentation_parity_100_steps(which):
 def test_colliding_particles_parity():
     # dense 2-D cluster with contacts from the start (spring-dashpot with friction), no fluid coupling drift
     gen = W.rng(41)
-    n = 24
-    X = W.rsa_positions(gen, n, 3.0, [10.0, 10.0], [50.0, 50.0], gap=-0.4)
+    n = 25  # 5 x 5 grid at spacing 5.8 < 2R, small seeded jitter: about 40 initial contacts
+    X = np.zeros((n, 3))
+    gx, gy = np.meshgrid(np.arange(5), np.arange(5))
+    X[:, 0] = 20.0 + 5.8 * gx.ravel() + 0.1 * (gen.random(n) - 0.5)
+    X[:, 1] = 20.0 + 5.8 * gy.ravel() + 0.1 * (gen.random(n) - 0.5)
     parts = dict(X=X, U=gen.normal(size=(n, 3)) * 2e-3, R=np.full(n, 3.0), rho_p=np.full(n, 1.5),
                  T_p=np.full(n, 0.8))
     parts["U"][:, 2] = 0
@@ -205,7 +208,8 @@ def test_thermosensitive_particles():
     case = _small_sed3d(n_p=5)
     gen = W.rng(61)
     case["particles"]["T_p"] = gen.random(5)
-    case["particles"]["heat_cap"] = np.full(5, 50.0)
+    # heat capacity rho_p V (specific heat ratio 1): about the heat content of the covered nodes
+    case["particles"]["heat_cap"] = np.full(5, 1.2 * 4.0 / 3.0 * np.pi * 4.0 ** 3)
     sim, orc = _sim(case), oracle.Oracle(case)
     sim.step(100)
     orc.step(100)
