@@ -434,6 +434,11 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     PCHECK(cudaStreamSynchronize(c.s0));  // host vectors go out of scope
     c.np = n;
     c.dem_cs = dem_cluster_size(&c);
+    if ((n + c.dem_cs - 1) / c.dem_cs > dem_max_per_cta()) {
+        c.np = 0;
+        dfree_group(ctx, GRP_PARTICLES);
+        return fail(ctx, PIBM_ERR_ARG, "too many particles for one DEM cluster on this device");
+    }
     // neighbour list at the initial positions, then the coupling of the current time
     PCHECK(launch_dem(&c, c.s0, 0));
     pibm_status st = device_status(ctx);

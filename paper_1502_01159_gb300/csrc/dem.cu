@@ -162,43 +162,6 @@ __device__ __forceinline__ double hydro(const double* cur, const double* prev, i
     return hp ? 0.5 * (cur[k] + prev[k]) : cur[k];
 }
 
-__device__ __forceinline__ void kick(const DemCfg& C, const DemState& S, int p, double h, int hp) {
-    double m = S.m[p], I = S.I[p], mg = S.mg[p];
-    for (int a = 0; a < 3; a++) {
-        double F = S.Fc[3 * p + a] + hydro(S.Fh, S.Fhp, 3 * p + a, hp) + mg * C.g[a];
-        S.U[3 * p + a] += h * F / m;
-        S.W[3 * p + a] += h * (S.Tc[3 * p + a] + hydro(S.Th, S.Thp, 3 * p + a, hp)) / I;
-    }
-    if (C.dim == 2) {
-        S.U[3 * p + 2] = 0.0;
-        S.W[3 * p] = 0.0;
-        S.W[3 * p + 1] = 0.0;
-    }
-}
-
-// drift and publish the particle's new state into pub
-__device__ __forceinline__ void drift_publish(const DemCfg& C, const DemState& S, int p, double dt, Pub& pub) {
-    double d2 = 0;
-    for (int a = 0; a < 3; a++) {
-        double x = S.X[3 * p + a] + dt * S.U[3 * p + a];
-        S.X[3 * p + a] = x;
-        pub.x[a] = x;
-        pub.u[a] = (float)S.U[3 * p + a];
-        pub.w[a] = (float)S.W[3 * p + a];
-        double d = x - S.Xb[3 * p + a];
-        d2 += d * d;
-    }
-    if (d2 > 0.25 * C.skin * C.skin) set_error(S.dstat, 2);
-}
-
-__device__ __forceinline__ void publish(const DemState& S, int p, Pub& pub) {
-    for (int a = 0; a < 3; a++) {
-        pub.x[a] = S.X[3 * p + a];
-        pub.u[a] = (float)S.U[3 * p + a];
-        pub.w[a] = (float)S.W[3 * p + a];
-    }
-}
-
 template <int D>
 __device__ void cell_coords(const DemCfg& C, const double* Xp, int* c) {
     for (int a = 0; a < 3; a++) {
@@ -229,10 +192,12 @@ __device__ __forceinline__ void for_neighbours(const DemCfg& C, const DemState& 
     }
 }
 
-// wall contacts of particle p (same law, R_wall = infinity, wall at rest)
+// wall contacts of particle p (same law, R_wall = infinity, wall at rest).
+// mask: bit f set while face f holds a non-zero tangential history, so faces
+// out of contact cost no memory traffic.
 template <int D>
 __device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, int p, const Pub& me, double Rp, float dtf,
-                                            double* F, double* T) {
+                                            double* F, double* T, int& mask) {
     for (int face = 0; face < 2 * D; face++) {
         int a = face >> 1, hi = face & 1;
         if (!C.walled[a]) continue;
@@ -240,7 +205,10 @@ __device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, 
         double dist = hi ? C.hi[a] - me.x[a] : me.x[a] - C.lo[a];
         double dd = Rp - dist;
         if (!(dd > 0.0)) {
-            if (ftp[0] != 0.f || ftp[1] != 0.f || ftp[2] != 0.f) ftp[0] = ftp[1] = ftp[2] = 0.f;
+            if (mask & (1 << face)) {
+                ftp[0] = ftp[1] = ftp[2] = 0.f;
+                mask &= ~(1 << face);
+            }
             continue;
         }
         float delta = (float)dd;
@@ -256,12 +224,51 @@ __device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, 
         float3 vt = f3(vr.x - vn * nn.x, vr.y - vn * nn.y, vr.z - vn * nn.z);
         float kt_eff;
         float Fn = normal_law(C, delta, vn, (float)Rp, &kt_eff);
-        float3 h = f3(ftp[0], ftp[1], ftp[2]);
+        float3 h = (mask & (1 << face)) ? f3(__ldcg(ftp), __ldcg(ftp + 1), __ldcg(ftp + 2)) : f3(0.f, 0.f, 0.f);
         float3 Ft = tangential(C, h, nn, vt, kt_eff, Fn, dtf);
         ftp[0] = h.x, ftp[1] = h.y, ftp[2] = h.z;
+        mask |= 1 << face;
         float3 Ti = cross3(ri, Ft);
         F[0] += -Fn * nn.x + Ft.x, F[1] += -Fn * nn.y + Ft.y, F[2] += -Fn * nn.z + Ft.z;
         T[0] += Ti.x, T[1] += Ti.y, T[2] += Ti.z;
+    }
+}
+
+// private state of a particle while its CTA runs the substeps (shared memory)
+struct Priv {
+    double X[3], U[3], W[3];
+    double a[3], al[3];      // external linear / angular acceleration: (hydro + buoyant weight)/m, hydro torque/I
+    double im, iI, R;        // 1/m, 1/I, radius
+    float Fc[3], Tc[3];      // contact force / torque of the last evaluation
+    int fixed, wall_mask;    // wall_mask: faces with a non-zero tangential history
+};
+
+// velocity Verlet half kick: U += h (F_c/m + a_ext), omega += h (T_c/I + alpha_ext)
+__device__ __forceinline__ void kick_s(Priv& P, double h, int dim) {
+    for (int a = 0; a < 3; a++) {
+        P.U[a] += h * ((double)P.Fc[a] * P.im + P.a[a]);
+        P.W[a] += h * ((double)P.Tc[a] * P.iI + P.al[a]);
+    }
+    if (dim == 2) {
+        P.U[2] = 0.0;
+        P.W[0] = P.W[1] = 0.0;
+    }
+}
+
+__device__ __forceinline__ void drift_s(Priv& P, double dt, Pub& pub) {
+    for (int a = 0; a < 3; a++) {
+        P.X[a] += dt * P.U[a];
+        pub.x[a] = P.X[a];
+        pub.u[a] = (float)P.U[a];
+        pub.w[a] = (float)P.W[a];
+    }
+}
+
+__device__ __forceinline__ void publish_s(const Priv& P, Pub& pub) {
+    for (int a = 0; a < 3; a++) {
+        pub.x[a] = P.X[a];
+        pub.u[a] = (float)P.U[a];
+        pub.w[a] = (float)P.W[a];
     }
 }
 
@@ -272,8 +279,8 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
     __shared__ int need_flag;
     cg::cluster_group cl = cg::this_cluster();
     const int per = C.per;
-    Pub* pub = reinterpret_cast<Pub*>(smem);                   // [2][per]
-    double* Rsh = reinterpret_cast<double*>(pub + 2 * per);     // [per]
+    Pub* pub = reinterpret_cast<Pub*>(smem);                     // [2][per]
+    Priv* prv = reinterpret_cast<Priv*>(pub + 2 * per);          // [per]
     const int n = C.n;
     const unsigned rank = cl.block_rank();
     const unsigned csize = cl.num_blocks();
@@ -289,49 +296,73 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
     const float dtf = (float)dt;
     int hfinal = hcur;
 
-    for (int l = threadIdx.x; l < nloc; l += blockDim.x) Rsh[l] = S.R[base + l];
-
     if (advance) {
         const int hp = __ldcg(S.have_prev);
+        // load the private state once; external accelerations are constant over the lattice step
         for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
-            int p = base + l;
-            if (!S.fixed[p]) {
-                kick(C, S, p, 0.5 * dt, hp);
-                drift_publish(C, S, p, dt, pub[l]);
+            const int p = base + l;
+            Priv& P = prv[l];
+            P.im = 1.0 / S.m[p];
+            P.iI = 1.0 / S.I[p];
+            P.R = S.R[p];
+            P.fixed = S.fixed[p];
+            P.wall_mask = 0;
+            for (int f = 0; f < 2 * D; f++) {
+                const float* w = S.wall_ft + 3 * (6 * p + f);
+                if (w[0] != 0.f || w[1] != 0.f || w[2] != 0.f) P.wall_mask |= 1 << f;
+            }
+            const double mg = S.mg[p];
+            for (int a = 0; a < 3; a++) {
+                P.X[a] = S.X[3 * p + a];
+                P.U[a] = S.U[3 * p + a];
+                P.W[a] = S.W[3 * p + a];
+                P.Fc[a] = (float)S.Fc[3 * p + a];
+                P.Tc[a] = (float)S.Tc[3 * p + a];
+                P.a[a] = (hydro(S.Fh, S.Fhp, 3 * p + a, hp) + mg * C.g[a]) * P.im;
+                P.al[a] = hydro(S.Th, S.Thp, 3 * p + a, hp) * P.iI;
+            }
+            if (!P.fixed) {
+                kick_s(P, 0.5 * dt, D);
+                drift_s(P, dt, pub[l]);
             } else {
-                publish(S, p, pub[l]);
+                publish_s(P, pub[l]);
             }
         }
         cl.sync();
         for (int sub = 0; sub < nsub; sub++) {
             const int rb = sub & 1;                      // published buffer read this substep
             const int hb = (hcur + sub) & 1;             // history buffer read this substep
-            float* hist_old = nb_ft + (size_t)hb * 3 * C.cap;
+            const float* hist_old = nb_ft + (size_t)hb * 3 * C.cap;
             float* hist_new = nb_ft + (size_t)(hb ^ 1) * 3 * C.cap;
             for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
                 const int p = base + l;
+                Priv& P = prv[l];
                 const Pub me = pub[rb * per + l];
-                const double Rp = Rsh[l];
+                const double Rp = P.R;
                 double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-                wall_forces<D>(C, S, p, me, Rp, dtf, F, T);
-                const int e1 = S.adj_start[p + 1];
-                for (int e = S.adj_start[p]; e < e1; e++) {
-                    const int q = S.adj_nb[e];
-                    const int kk = S.adj_k[e];
+                wall_forces<D>(C, S, p, me, Rp, dtf, F, T, P.wall_mask);
+                const int e1 = __ldg(S.adj_start + p + 1);
+                for (int e = __ldg(S.adj_start + p); e < e1; e++) {
+                    const int q = __ldg(S.adj_nb + e);
+                    const int kk = __ldg(S.adj_k + e);
                     const bool first = kk >= 0;
                     const int k = first ? kk : ~kk;
                     const int rq = q / per, lq = q - rq * per;
-                    const Pub* rpub = cl.map_shared_rank(pub, rq);
-                    const double* rR = cl.map_shared_rank(Rsh, rq);
-                    const Pub other = rpub[rb * per + lq];
-                    const double Rq = rR[lq];
+                    const Pub other = cl.map_shared_rank(pub, rq)[rb * per + lq];
+                    const double Rq = cl.map_shared_rank(prv, rq)[lq].R;
                     const Pub& A = first ? me : other;
                     const Pub& B = first ? other : me;
                     const double Ra = first ? Rp : Rq, Rb = first ? Rq : Rp;
-                    float3 h = f3(0.f, 0.f, 0.f), Fa, Ta, Tb;
-                    double d2 = dist2(A.x, B.x), Ssum = Ra + Rb;
-                    if (d2 < Ssum * Ssum) h = f3(__ldcg(hist_old + 3 * k), __ldcg(hist_old + 3 * k + 1), __ldcg(hist_old + 3 * k + 2));
-                    pair_force(C, A, B, Ra, Rb, h, dtf, Fa, Ta, Tb);
+                    // FP32 prefilter; the contact decision itself is the exact FP64 test
+                    const float dxf = (float)(B.x[0] - A.x[0]), dyf = (float)(B.x[1] - A.x[1]), dzf = (float)(B.x[2] - A.x[2]);
+                    const float sf = (float)(Ra + Rb) + 1e-3f;
+                    float3 Fa = f3(0.f, 0.f, 0.f), Ta = Fa, Tb = Fa, h = Fa;
+                    if (dxf * dxf + dyf * dyf + dzf * dzf < sf * sf) {
+                        double d2 = dist2(A.x, B.x), Ssum = Ra + Rb;
+                        if (d2 < Ssum * Ssum)
+                            h = f3(__ldcg(hist_old + 3 * k), __ldcg(hist_old + 3 * k + 1), __ldcg(hist_old + 3 * k + 2));
+                        pair_force(C, A, B, Ra, Rb, h, dtf, Fa, Ta, Tb);
+                    }
                     if (first) {
                         float* hn = hist_new + 3 * k;
                         hn[0] = h.x, hn[1] = h.y, hn[2] = h.z;
@@ -343,38 +374,46 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                     }
                 }
                 for (int a = 0; a < 3; a++) {
-                    S.Fc[3 * p + a] = F[a];
-                    S.Tc[3 * p + a] = T[a];
+                    P.Fc[a] = (float)F[a];
+                    P.Tc[a] = (float)T[a];
                 }
-                if (S.fixed[p]) {
-                    publish(S, p, pub[(rb ^ 1) * per + l]);
+                if (P.fixed) {
+                    publish_s(P, pub[(rb ^ 1) * per + l]);
                     continue;
                 }
-                kick(C, S, p, 0.5 * dt, hp);
+                kick_s(P, 0.5 * dt, D);
                 if (sub + 1 < nsub) {
-                    kick(C, S, p, 0.5 * dt, hp);
-                    drift_publish(C, S, p, dt, pub[(rb ^ 1) * per + l]);
+                    kick_s(P, 0.5 * dt, D);
+                    drift_s(P, dt, pub[(rb ^ 1) * per + l]);
                 }
             }
             cl.sync();
         }
         hfinal = (hcur + nsub) & 1;
-        // thermosensitive particles: C_p dT_p / dt = -H_p over one lattice step;
-        // then keep this step's coupling as the previous one
+        // write back; thermosensitive particles: C_p dT_p / dt = -H_p over one
+        // lattice step; keep this step's coupling as the previous one
         int moved = 0;
         const double thr2 = 0.25 * (C.skin - 1.0) * (C.skin - 1.0);
+        const double err2 = 0.25 * C.skin * C.skin;
         for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
-            int p = base + l;
+            const int p = base + l;
+            const Priv& P = prv[l];
             if (S.Cp[p] > 0.0) S.Tp[p] -= hydro(S.Hh, S.Hhp, p, hp) / S.Cp[p];
             double d2 = 0;
             for (int a = 0; a < 3; a++) {
+                S.X[3 * p + a] = P.X[a];
+                S.U[3 * p + a] = P.U[a];
+                S.W[3 * p + a] = P.W[a];
+                S.Fc[3 * p + a] = P.Fc[a];
+                S.Tc[3 * p + a] = P.Tc[a];
                 S.Fhp[3 * p + a] = S.Fh[3 * p + a];
                 S.Thp[3 * p + a] = S.Th[3 * p + a];
-                double d = S.X[3 * p + a] - S.Xb[3 * p + a];
-                d2 += d * d;
+                double dd = P.X[a] - S.Xb[3 * p + a];
+                d2 += dd * dd;
             }
             S.Hhp[p] = S.Hh[p];
             if (d2 > thr2) moved = 1;
+            if (d2 > err2) set_error(S.dstat, 2);
         }
         moved = __syncthreads_or(moved);
         if (threadIdx.x == 0) need_flag = moved;
@@ -563,9 +602,9 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
 }
 
 // cluster size: up to 16 CTAs of DEM_T threads, at most DEM_MAXPER particles per CTA
-constexpr int DEM_MAXPER = 2048;
+constexpr int DEM_MAXPER = 768;  // (2 * 48 + 176) B per particle: 204 KB of shared memory
 
-static size_t dem_smem(int per) { return (size_t)per * (2 * sizeof(Pub) + sizeof(double)); }
+static size_t dem_smem(int per) { return (size_t)per * (2 * sizeof(Pub) + sizeof(Priv)); }
 
 int dem_cluster_size(Ctx* c) {
     int n = c->np;
@@ -600,6 +639,7 @@ int dem_cluster_size(Ctx* c) {
 }
 
 int dem_max_particles() { return 16 * DEM_MAXPER; }
+int dem_max_per_cta() { return DEM_MAXPER; }
 
 static DemState dem_state(Ctx* c) {
     DemState S;

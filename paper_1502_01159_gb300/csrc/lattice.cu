@@ -84,6 +84,90 @@ __device__ __forceinline__ void collide_node(R* s, R* sg, R fbx, R fby, R fbz, R
     }
 }
 
+// Odd-step source of direction i for a node whose y/z neighbours are all
+// inside: only the x neighbour can leave the lattice.  Per-lane selects keep a
+// warp that holds an x-boundary node on this path (no divergence into the
+// generic boundary code).  Returns the flat index and sets bounce when the x
+// neighbour lies beyond a wall (then the node's own slot of direction i holds
+// the bounced value).
+template <int D, int I>
+__device__ __forceinline__ long long odd_src(const Geo& G, long long n, int x, long long sy, long long sz, bool& bounce) {
+    using L = Lat<D>;
+    constexpr int ex = L::ex(I);
+    long long off = (long long)L::ey(I) * sy + (long long)L::ez(I) * sz;
+    bounce = false;
+    if (ex == 0) return (long long)L::opp(I) * G.N + n - off;
+    int sx = x - ex;
+    long long dx = ex;
+    if (sx < 0 || sx >= G.nx) {
+        if (G.per[0]) dx = ex + (sx < 0 ? -G.nx : G.nx);  // wrap: source at sx +- nx
+        else bounce = true;
+    }
+    return bounce ? (long long)I * G.N + n : (long long)L::opp(I) * G.N + n - off - dx;
+}
+
+template <int D, int I>
+__device__ __forceinline__ long long odd_dst(const Geo& G, long long n, int x, long long sy, long long sz, bool& bounce) {
+    using L = Lat<D>;
+    constexpr int ex = L::ex(I);
+    long long off = (long long)L::ey(I) * sy + (long long)L::ez(I) * sz;
+    bounce = false;
+    if (ex == 0) return (long long)I * G.N + n + off;
+    int tx = x + ex;
+    long long dx = ex;
+    if (tx < 0 || tx >= G.nx) {
+        if (G.per[0]) dx = ex + (tx < 0 ? G.nx : -G.nx);
+        else bounce = true;
+    }
+    return bounce ? (long long)L::opp(I) * G.N + n : (long long)I * G.N + n + off + dx;
+}
+
+template <int D, typename R, int I>
+struct OddLoad {
+    static __device__ __forceinline__ void run(const Geo& G, const R* f, const R* g, long long n, int x, long long sy,
+                                               long long sz, R* s, R* sg) {
+        using L = Lat<D>;
+        bool b;
+        long long idx = odd_src<D, I>(G, n, x, sy, sz, b);
+        s[I] = f[idx];
+        if (I < L::QG) {
+            R v = g[idx];
+            if (b && face_iso(G, L::ex(I) > 0 ? 0 : 1)) v = (R)(2.0 * L::wg(I) * face_dTw(G, L::ex(I) > 0 ? 0 : 1)) - v;
+            sg[I < L::QG ? I : 0] = v;
+        }
+        OddLoad<D, R, I + 1>::run(G, f, g, n, x, sy, sz, s, sg);
+    }
+};
+template <typename R> struct OddLoad<2, R, 9> {
+    static __device__ __forceinline__ void run(const Geo&, const R*, const R*, long long, int, long long, long long, R*, R*) {}
+};
+template <typename R> struct OddLoad<3, R, 19> {
+    static __device__ __forceinline__ void run(const Geo&, const R*, const R*, long long, int, long long, long long, R*, R*) {}
+};
+
+template <int D, typename R, int I>
+struct OddStore {
+    static __device__ __forceinline__ void run(const Geo& G, R* f, R* g, long long n, int x, long long sy, long long sz,
+                                               const R* s, const R* sg) {
+        using L = Lat<D>;
+        bool b;
+        long long idx = odd_dst<D, I>(G, n, x, sy, sz, b);
+        f[idx] = s[I];
+        if (I < L::QG) {
+            R v = sg[I < L::QG ? I : 0];
+            if (b && face_iso(G, L::ex(I) > 0 ? 1 : 0)) v = (R)(2.0 * L::wg(I) * face_dTw(G, L::ex(I) > 0 ? 1 : 0)) - v;
+            g[idx] = v;
+        }
+        OddStore<D, R, I + 1>::run(G, f, g, n, x, sy, sz, s, sg);
+    }
+};
+template <typename R> struct OddStore<2, R, 9> {
+    static __device__ __forceinline__ void run(const Geo&, R*, R*, long long, int, long long, long long, const R*, const R*) {}
+};
+template <typename R> struct OddStore<3, R, 19> {
+    static __device__ __forceinline__ void run(const Geo&, R*, R*, long long, int, long long, long long, const R*, const R*) {}
+};
+
 template <int D, typename S, int PARITY>
 __global__ void __launch_bounds__(256) k_stream_collide(Geo G, S* __restrict__ f, S* __restrict__ g,
                                                         const typename Vec4<S>::T* __restrict__ fb,
@@ -96,18 +180,16 @@ __global__ void __launch_bounds__(256) k_stream_collide(Geo G, S* __restrict__ f
     const long long N = G.N;
     const long long n = node_index(G, x, y, z);
     const long long sy = G.nx, sz = (long long)G.nx * G.ny;
-    const bool interior = x > 0 && x < G.nx - 1 && y > 0 && y < G.ny - 1 && (D == 2 || (z > 0 && z < G.nz - 1));
+    // y and z are uniform across the block, so this test never splits a warp
+    const bool inner_yz = y > 0 && y < G.ny - 1 && (D == 2 || (z > 0 && z < G.nz - 1));
     R s[L::Q], sg[L::QG];
     if (PARITY == 0) {
 #pragma unroll
         for (int i = 0; i < L::Q; i++) s[i] = f[i * N + n];
 #pragma unroll
         for (int k = 0; k < L::QG; k++) sg[k] = g[k * N + n];
-    } else if (interior) {
-#pragma unroll
-        for (int i = 0; i < L::Q; i++) s[i] = f[L::opp(i) * N + n - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz)];
-#pragma unroll
-        for (int k = 0; k < L::QG; k++) sg[k] = g[L::opp(k) * N + n - (L::ex(k) + L::ey(k) * sy + L::ez(k) * sz)];
+    } else if (inner_yz) {
+        OddLoad<D, R, 0>::run(G, f, g, n, x, sy, sz, s, sg);
     } else {
         load_node<D, S, R>(G, f, g, x, y, z, 1, s, sg);
     }
@@ -125,11 +207,8 @@ __global__ void __launch_bounds__(256) k_stream_collide(Geo G, S* __restrict__ f
         for (int i = 0; i < L::Q; i++) f[L::opp(i) * N + n] = s[i];
 #pragma unroll
         for (int k = 0; k < L::QG; k++) g[L::opp(k) * N + n] = sg[k];
-    } else if (interior) {
-#pragma unroll
-        for (int i = 0; i < L::Q; i++) f[i * N + n + (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz)] = s[i];
-#pragma unroll
-        for (int k = 0; k < L::QG; k++) g[k * N + n + (L::ex(k) + L::ey(k) * sy + L::ez(k) * sz)] = sg[k];
+    } else if (inner_yz) {
+        OddStore<D, R, 0>::run(G, f, g, n, x, sy, sz, s, sg);
     } else {
 #pragma unroll
         for (int i = 0; i < L::Q; i++) {
