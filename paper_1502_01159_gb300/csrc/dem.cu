@@ -197,13 +197,16 @@ __device__ __forceinline__ void for_neighbours(const DemCfg& C, const DemState& 
 // out of contact cost no memory traffic.
 template <int D>
 __device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, int p, const Pub& me, double Rp, float dtf,
-                                            double* F, double* T, int& mask) {
+                                            float* F, float* T, int& mask) {
     for (int face = 0; face < 2 * D; face++) {
         int a = face >> 1, hi = face & 1;
         if (!C.walled[a]) continue;
         float* ftp = S.wall_ft + 3 * (6 * p + face);
-        double dist = hi ? C.hi[a] - me.x[a] : me.x[a] - C.lo[a];
-        double dd = Rp - dist;
+        // FP32 prefilter on the distance to the wall plane, exact FP64 test when close
+        const float xf = (float)me.x[a];
+        const float distf = hi ? (float)C.hi[a] - xf : xf - (float)C.lo[a];
+        double dd = -1.0;
+        if (distf < (float)Rp + 1e-3f) dd = Rp - (hi ? C.hi[a] - me.x[a] : me.x[a] - C.lo[a]);
         if (!(dd > 0.0)) {
             if (mask & (1 << face)) {
                 ftp[0] = ftp[1] = ftp[2] = 0.f;
@@ -339,7 +342,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 Priv& P = prv[l];
                 const Pub me = pub[rb * per + l];
                 const double Rp = P.R;
-                double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+                float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};  // contact sums (a few terms) in FP32
                 wall_forces<D>(C, S, p, me, Rp, dtf, F, T, P.wall_mask);
                 const int e1 = __ldg(S.adj_start + p + 1);
                 for (int e = __ldg(S.adj_start + p); e < e1; e++) {
@@ -374,17 +377,18 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                     }
                 }
                 for (int a = 0; a < 3; a++) {
-                    P.Fc[a] = (float)F[a];
-                    P.Tc[a] = (float)T[a];
+                    P.Fc[a] = F[a];
+                    P.Tc[a] = T[a];
                 }
                 if (P.fixed) {
                     publish_s(P, pub[(rb ^ 1) * per + l]);
                     continue;
                 }
-                kick_s(P, 0.5 * dt, D);
-                if (sub + 1 < nsub) {
-                    kick_s(P, 0.5 * dt, D);
+                if (sub + 1 < nsub) {  // closing half kick of this substep + opening half kick of the next
+                    kick_s(P, dt, D);
                     drift_s(P, dt, pub[(rb ^ 1) * per + l]);
+                } else {
+                    kick_s(P, 0.5 * dt, D);
                 }
             }
             cl.sync();
@@ -608,7 +612,7 @@ static size_t dem_smem(int per) { return (size_t)per * (2 * sizeof(Pub) + sizeof
 
 int dem_cluster_size(Ctx* c) {
     int n = c->np;
-    int cs = (n + 63) / 64;
+    int cs = (n + 31) / 32;
     cs = cs < 1 ? 1 : (cs > 16 ? 16 : cs);
     if (cs > 8) {
         int max16 = 0;  // is a 16-CTA cluster with this much shared memory schedulable here?

@@ -15,11 +15,15 @@
 
 namespace pibm {
 
+// Collision constants in the arithmetic type R (no per-thread conversions:
+// GB300's FP64 pipe is slow, and a double-to-float conversion runs on it).
+template <typename R>
 struct CollideParams {
-    double omf, omg;        // 1 / tau_f, 1 / tau_g
-    double cf, cg;          // 1 - 1/(2 tau_f), 1 - 1/(2 tau_g)
-    double buoy, Tref;      // U_c^2 / L_c, reference temperature
-    double body[3];
+    R omf, omg;        // 1 / tau_f, 1 / tau_g
+    R cf, cg;          // 1 - 1/(2 tau_f), 1 - 1/(2 tau_g)
+    R buoy, Tref;      // U_c^2 / L_c, reference temperature
+    R body[3];
+    R abb[6];          // anti-bounce-back offset 2 w (T_w - T_ref) per face (w of a non-rest thermal direction)
     int gaxis, buoyancy;
 };
 
@@ -32,7 +36,7 @@ struct CollideParams {
 //   Eq lbm2.5 + lbm3.5 (linear, D2Q5 / D3Q7) + lbm12.5:
 //     s_gk* = s_gk + (w_k (T - T_ref + T e.u / cs_T^2) - s_gk)/tau_g + (1 - 1/2tau_g) w_k Q_B
 template <int D, typename R>
-__device__ __forceinline__ void collide_node(R* s, R* sg, R fbx, R fby, R fbz, R qb, const CollideParams& P) {
+__device__ __forceinline__ void collide_node(R* s, R* sg, R fbx, R fby, R fbz, R qb, const CollideParams<R>& P) {
     using L = Lat<D>;
     R drho = 0, jx = 0, jy = 0, jz = 0, dT = 0;
 #pragma unroll
@@ -124,54 +128,60 @@ __device__ __forceinline__ long long odd_dst(const Geo& G, long long n, int x, l
 
 template <int D, typename R, int I>
 struct OddLoad {
-    static __device__ __forceinline__ void run(const Geo& G, const R* f, const R* g, long long n, int x, long long sy,
-                                               long long sz, R* s, R* sg) {
+    static __device__ __forceinline__ void run(const Geo& G, const CollideParams<R>& P, const R* f, const R* g, long long n,
+                                               int x, long long sy, long long sz, R* s, R* sg) {
         using L = Lat<D>;
         bool b;
         long long idx = odd_src<D, I>(G, n, x, sy, sz, b);
         s[I] = f[idx];
         if (I < L::QG) {
             R v = g[idx];
-            if (b && face_iso(G, L::ex(I) > 0 ? 0 : 1)) v = (R)(2.0 * L::wg(I) * face_dTw(G, L::ex(I) > 0 ? 0 : 1)) - v;
+            constexpr int face = L::ex(I) > 0 ? 0 : 1;  // face crossed by x - e_I
+            if (b && face_iso(G, face)) v = P.abb[face] - v;
             sg[I < L::QG ? I : 0] = v;
         }
-        OddLoad<D, R, I + 1>::run(G, f, g, n, x, sy, sz, s, sg);
+        OddLoad<D, R, I + 1>::run(G, P, f, g, n, x, sy, sz, s, sg);
     }
 };
 template <typename R> struct OddLoad<2, R, 9> {
-    static __device__ __forceinline__ void run(const Geo&, const R*, const R*, long long, int, long long, long long, R*, R*) {}
+    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, const R*, const R*, long long, int,
+                                               long long, long long, R*, R*) {}
 };
 template <typename R> struct OddLoad<3, R, 19> {
-    static __device__ __forceinline__ void run(const Geo&, const R*, const R*, long long, int, long long, long long, R*, R*) {}
+    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, const R*, const R*, long long, int,
+                                               long long, long long, R*, R*) {}
 };
 
 template <int D, typename R, int I>
 struct OddStore {
-    static __device__ __forceinline__ void run(const Geo& G, R* f, R* g, long long n, int x, long long sy, long long sz,
-                                               const R* s, const R* sg) {
+    static __device__ __forceinline__ void run(const Geo& G, const CollideParams<R>& P, R* f, R* g, long long n, int x,
+                                               long long sy, long long sz, const R* s, const R* sg) {
         using L = Lat<D>;
         bool b;
         long long idx = odd_dst<D, I>(G, n, x, sy, sz, b);
         f[idx] = s[I];
         if (I < L::QG) {
             R v = sg[I < L::QG ? I : 0];
-            if (b && face_iso(G, L::ex(I) > 0 ? 1 : 0)) v = (R)(2.0 * L::wg(I) * face_dTw(G, L::ex(I) > 0 ? 1 : 0)) - v;
+            constexpr int face = L::ex(I) > 0 ? 1 : 0;  // face crossed by x + e_I
+            if (b && face_iso(G, face)) v = P.abb[face] - v;
             g[idx] = v;
         }
-        OddStore<D, R, I + 1>::run(G, f, g, n, x, sy, sz, s, sg);
+        OddStore<D, R, I + 1>::run(G, P, f, g, n, x, sy, sz, s, sg);
     }
 };
 template <typename R> struct OddStore<2, R, 9> {
-    static __device__ __forceinline__ void run(const Geo&, R*, R*, long long, int, long long, long long, const R*, const R*) {}
+    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, R*, R*, long long, int, long long,
+                                               long long, const R*, const R*) {}
 };
 template <typename R> struct OddStore<3, R, 19> {
-    static __device__ __forceinline__ void run(const Geo&, R*, R*, long long, int, long long, long long, const R*, const R*) {}
+    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, R*, R*, long long, int, long long,
+                                               long long, const R*, const R*) {}
 };
 
 template <int D, typename S, int PARITY>
 __global__ void __launch_bounds__(256) k_stream_collide(Geo G, S* __restrict__ f, S* __restrict__ g,
                                                         const typename Vec4<S>::T* __restrict__ fb,
-                                                        const uint8_t* __restrict__ flags, CollideParams P) {
+                                                        const uint8_t* __restrict__ flags, CollideParams<S> P) {
     using L = Lat<D>;
     using R = S;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -189,7 +199,7 @@ __global__ void __launch_bounds__(256) k_stream_collide(Geo G, S* __restrict__ f
 #pragma unroll
         for (int k = 0; k < L::QG; k++) sg[k] = g[k * N + n];
     } else if (inner_yz) {
-        OddLoad<D, R, 0>::run(G, f, g, n, x, sy, sz, s, sg);
+        OddLoad<D, R, 0>::run(G, P, f, g, n, x, sy, sz, s, sg);
     } else {
         load_node<D, S, R>(G, f, g, x, y, z, 1, s, sg);
     }
@@ -208,7 +218,7 @@ __global__ void __launch_bounds__(256) k_stream_collide(Geo G, S* __restrict__ f
 #pragma unroll
         for (int k = 0; k < L::QG; k++) g[L::opp(k) * N + n] = sg[k];
     } else if (inner_yz) {
-        OddStore<D, R, 0>::run(G, f, g, n, x, sy, sz, s, sg);
+        OddStore<D, R, 0>::run(G, P, f, g, n, x, sy, sz, s, sg);
     } else {
 #pragma unroll
         for (int i = 0; i < L::Q; i++) {
@@ -227,15 +237,18 @@ __global__ void __launch_bounds__(256) k_stream_collide(Geo G, S* __restrict__ f
     }
 }
 
-static CollideParams collide_params(const Ctx* c) {
-    CollideParams P;
-    P.omf = 1.0 / c->tau_f;
-    P.omg = 1.0 / c->tau_g;
-    P.cf = 1.0 - 0.5 / c->tau_f;
-    P.cg = 1.0 - 0.5 / c->tau_g;
-    P.buoy = c->buoy;
-    P.Tref = c->desc.T_ref;
-    for (int a = 0; a < 3; a++) P.body[a] = c->desc.body_force[a];
+template <typename R>
+static CollideParams<R> collide_params(const Ctx* c) {
+    CollideParams<R> P;
+    P.omf = (R)(1.0 / c->tau_f);
+    P.omg = (R)(1.0 / c->tau_g);
+    P.cf = (R)(1.0 - 0.5 / c->tau_f);
+    P.cg = (R)(1.0 - 0.5 / c->tau_g);
+    P.buoy = (R)c->buoy;
+    P.Tref = (R)c->desc.T_ref;
+    for (int a = 0; a < 3; a++) P.body[a] = (R)c->desc.body_force[a];
+    double wgk = c->D == 2 ? Lat<2>::wg(1) : Lat<3>::wg(1);
+    for (int f = 0; f < 6; f++) P.abb[f] = (R)(2.0 * wgk * c->G.dTw[f]);
     P.gaxis = c->desc.gravity_axis;
     P.buoyancy = c->desc.buoyancy;
     return P;
@@ -245,7 +258,7 @@ template <int D, typename S>
 static cudaError_t sc_launch(Ctx* c, cudaStream_t s, int parity) {
     dim3 block(256), grid((c->G.nx + 255) / 256, c->G.ny, c->G.nz);
     if (c->G.nx <= 128) block.x = 128, grid.x = (c->G.nx + 127) / 128;
-    CollideParams P = collide_params(c);
+    CollideParams<S> P = collide_params<S>(c);
     using V = typename Vec4<S>::T;
     if (parity == 0)
         k_stream_collide<D, S, 0><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb, c->flags, P);
@@ -352,7 +365,7 @@ cudaError_t launch_write_plane(Ctx* c, int which, int q, int parity) {
 // ------------------------------------------------------ macroscopic fields
 template <int D, typename S>
 __device__ void node_macro(const Geo& G, const S* f, const S* g, const typename Vec4<S>::T* fb, const uint8_t* flags,
-                           const CollideParams& P, int x, int y, int z, int parity, double* out /*rho,ux,uy,uz,T,fbx,fby,fbz,qb,T0*/) {
+                           const CollideParams<double>& P, int x, int y, int z, int parity, double* out /*rho,ux,uy,uz,T,fbx,fby,fbz,qb,T0*/) {
     using L = Lat<D>;
     double s[L::Q], sg[L::QG];
     load_node<D, S, double>(G, f, g, x, y, z, parity, s, sg);
@@ -384,7 +397,7 @@ __device__ void node_macro(const Geo& G, const S* f, const S* g, const typename 
 
 template <int D, typename S>
 __global__ void k_macro(Geo G, const S* f, const S* g, const typename Vec4<S>::T* fb, const uint8_t* flags,
-                        CollideParams P, int field, int parity, double* out) {
+                        CollideParams<double> P, int field, int parity, double* out) {
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < G.N; n += (long long)gridDim.x * blockDim.x) {
         int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
         double m[10];
@@ -397,7 +410,7 @@ template <int D, typename S>
 static cudaError_t macro_launch(Ctx* c, int field, int parity) {
     using V = typename Vec4<S>::T;
     k_macro<D, S><<<1024, 256, 0, c->s0>>>(c->G, (const S*)c->f, (const S*)c->g, (const V*)c->fb, c->flags,
-                                           collide_params(c), field, parity, c->plane);
+                                           collide_params<double>(c), field, parity, c->plane);
     return cudaGetLastError();
 }
 
@@ -414,7 +427,7 @@ constexpr int DIAG_BLOCKS = 512;
 
 template <int D, typename S>
 __global__ void __launch_bounds__(256) k_diag_lattice(Geo G, const S* f, const S* g, const typename Vec4<S>::T* fb,
-                                                      const uint8_t* flags, CollideParams P, int parity, double* part) {
+                                                      const uint8_t* flags, CollideParams<double> P, int parity, double* part) {
     __shared__ double sh[4][256];
     double mass = 0, heat = 0, umax = 0, bad = 0;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < G.N; n += (long long)gridDim.x * blockDim.x) {
@@ -485,7 +498,7 @@ template <int D, typename S>
 static cudaError_t diag_launch(Ctx* c, int parity) {
     using V = typename Vec4<S>::T;
     k_diag_lattice<D, S><<<DIAG_BLOCKS, 256, 0, c->s0>>>(c->G, (const S*)c->f, (const S*)c->g, (const V*)c->fb,
-                                                         c->flags, collide_params(c), parity, c->red);
+                                                         c->flags, collide_params<double>(c), parity, c->red);
     k_diag_final<<<1, 256, 0, c->s0>>>(c->red, DIAG_BLOCKS, c->U, c->W, c->X, c->m, c->I, c->np,
                                        c->desc.gravity_axis, c->red + 4 * DIAG_BLOCKS);
     return cudaGetLastError();
