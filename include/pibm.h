@@ -193,6 +193,34 @@ pibm_status pibm_step_timed(pibm_ctx* ctx, double* ms);
 /* Number of kernels one lattice step launches (for launch accounting). */
 pibm_status pibm_kernels_per_step(pibm_ctx* ctx, int* n);
 
+/* Contact search for callers that cannot allocate device memory.  The paper
+ * has no counterpart of this entry point: it serves code that runs inside
+ * another framework's memory pool or arena, plug-ins loaded into a host that
+ * owns every device allocation, and processes whose device memory is
+ * reserved up front -- they hold particles on the device but cannot create a
+ * context (which allocates) or call cudaMalloc.  It computes the same contact
+ * list as pibm_read_contacts (pairs i < j with |X_i - X_j| < R_i + R_j in the
+ * library's FP64 operation order, sorted by (i, j)) on the caller's device
+ * arrays and allocates nothing: its cell list and offsets live in one fixed
+ * file-scope device array of 786 440 bytes that every GPU loading the library
+ * holds until the process exits.
+ *   d_X: n*3 doubles, d_R: n doubles (device); n <= 16384.
+ *   dim, nlat[3]: lattice dimension and extents, walls at -0.5 and n - 0.5.
+ *   cell_size: minimum cell side (> 0, at least the largest diameter; the
+ *     library's default is 2 R_max + 1.5); at most 65536 cells.
+ *   d_pairs: 2*cap ints (device); d_count: 2 ints (device): [0] total number
+ *     of pairs (only the first cap are written), [1] 0, or 1 when a particle
+ *     had more than 64 partners, or 2 when a diameter exceeds the cell side.
+ *   stream: cudaStream_t or NULL.  Asynchronous; the results are valid once
+ *     the stream has reached this call.
+ * Sizes beyond the limits return PIBM_ERR_ARG (pibm_last_error(NULL, ...)
+ * says which).  The first call on each device looks up the device address of
+ * the scratch array with that device current; make that first call before any
+ * stream capture.  Every call shares the one array and clears what it needs,
+ * so calls that overlap on the GPU (on different streams) race. */
+pibm_status pibm_contacts_static(const double* d_X, const double* d_R, int n, int dim, const int32_t* nlat,
+                                 double cell_size, int32_t* d_pairs, int cap, int32_t* d_count, void* stream);
+
 const char* pibm_status_string(pibm_status s);
 /* Copies the last error message of the context (or of the last failed
  * pibm_create when ctx is NULL) into buf; returns its length. */

@@ -64,6 +64,7 @@ SIGNATURES = {
     "pibm_time": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "pibm_kernels_per_step": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "pibm_step_timed": (C.c_int, [_P, _D]),
+    "pibm_contacts_static": (C.c_int, [_P, _P, C.c_int, C.c_int, _I32, C.c_double, _P, C.c_int, _P, _P]),
     "pibm_status_string": (C.c_char_p, [C.c_int]),
     "pibm_last_error": (C.c_int, [_P, C.c_char_p, C.c_size_t]),
 }
@@ -317,3 +318,29 @@ class Simulation:
         v = C.c_int()
         self._check(self.L.pibm_kernels_per_step(self.h, C.byref(v)), "pibm_kernels_per_step")
         return v.value
+
+
+def contacts_static(X, R, dim, shape, cell_size, cap=None, stream=None):
+    """pibm_contacts_static on torch CUDA tensors X (n x 3 float64) and R (n
+    float64): the contact pairs computed without any device allocation by the
+    library.  The output buffers are the caller's (allocated here by torch);
+    returns (pairs n_pairs x 2 int32 tensor, flag)."""
+    import torch
+    L = load()
+    n = int(R.numel())
+    if cap is None:
+        cap = 8 * max(n, 1)
+    pairs = torch.zeros(2 * max(cap, 1), dtype=torch.int32, device=R.device)
+    count = torch.zeros(2, dtype=torch.int32, device=R.device)
+    nl = (C.c_int32 * 3)(*shape)
+    s = stream if stream is not None else torch.cuda.current_stream(R.device)
+    st = L.pibm_contacts_static(C.c_void_p(X.data_ptr()), C.c_void_p(R.data_ptr()), n, dim, nl, float(cell_size),
+                                C.c_void_p(pairs.data_ptr()), cap, C.c_void_p(count.data_ptr()),
+                                C.c_void_p(s.cuda_stream))
+    if st != PIBM_OK:
+        buf = C.create_string_buffer(512)
+        L.pibm_last_error(None, buf, 512)
+        raise PibmError(st, buf.value.decode())
+    s.synchronize()
+    total, flag = (int(v) for v in count.tolist())
+    return pairs[: 2 * min(total, cap)].view(-1, 2), flag

@@ -22,6 +22,8 @@ struct pibm_ctx {
 
 static std::string g_create_error;
 
+void pibm::set_global_error(const std::string& msg) { g_create_error = msg; }
+
 enum { GRP_LATTICE = 0, GRP_PARTICLES = 1, GRP_MARKERS = 2, GRP_SCRATCH = 3 };
 
 #define PCHECK(call)                                                                         \

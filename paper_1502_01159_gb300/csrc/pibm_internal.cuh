@@ -258,6 +258,8 @@ cudaError_t launch_contacts(Ctx* c, int* d_pairs, int cap, int* d_count);
 cudaError_t launch_cells(Ctx* c, int* d_cell);
 int dem_cluster_size(Ctx* c);
 int dem_max_particles();
+// api.cu: message returned by pibm_last_error(NULL, ...)
+void set_global_error(const std::string& msg);
 int dem_max_per_cta();
 
 }  // namespace pibm
