@@ -190,6 +190,12 @@ pibm_status pibm_time(pibm_ctx* ctx, int64_t* t);
  * ms[2] PIBM coupling, ms[3] the whole step (fork to join).  Synchronises. */
 pibm_status pibm_step_timed(pibm_ctx* ctx, double* ms);
 
+/* Launch-shape tuning (used by autotuning sweeps; results do not depend on it).
+ * PIBM_TUNE_DEM_PARTICLES_PER_CTA: particles per CTA of the DEM cluster
+ * (0 = default 32; at most 16 CTAs and 640 particles per CTA). */
+enum { PIBM_TUNE_DEM_PARTICLES_PER_CTA = 0 };
+pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value);
+
 /* Number of kernels one lattice step launches (for launch accounting). */
 pibm_status pibm_kernels_per_step(pibm_ctx* ctx, int* n);
 

@@ -64,6 +64,7 @@ SIGNATURES = {
     "pibm_time": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "pibm_kernels_per_step": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "pibm_step_timed": (C.c_int, [_P, _D]),
+    "pibm_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
     "pibm_contacts_static": (C.c_int, [_P, _P, C.c_int, C.c_int, _I32, C.c_double, _P, C.c_int, _P, _P]),
     "pibm_status_string": (C.c_char_p, [C.c_int]),
     "pibm_last_error": (C.c_int, [_P, C.c_char_p, C.c_size_t]),
@@ -313,6 +314,9 @@ class Simulation:
         v = C.c_int64()
         self._check(self.L.pibm_time(self.h, C.byref(v)), "pibm_time")
         return v.value
+
+    def set_tuning(self, knob: int, value: int):
+        self._check(self.L.pibm_set_tuning(self.h, knob, value), "pibm_set_tuning")
 
     def kernels_per_step(self) -> int:
         v = C.c_int()

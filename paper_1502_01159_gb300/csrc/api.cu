@@ -764,6 +764,21 @@ pibm_status pibm_time(pibm_ctx* ctx, int64_t* t) {
     return PIBM_OK;
 }
 
+pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (knob != PIBM_TUNE_DEM_PARTICLES_PER_CTA || value < 0 || value > dem_max_per_cta())
+        return fail(ctx, PIBM_ERR_ARG, "invalid tuning knob or value");
+    c.tune_dem_particles_per_cta = value;
+    if (c.np > 0) {
+        int cs = dem_cluster_size(&c);
+        if ((c.np + cs - 1) / cs > dem_max_per_cta()) return fail(ctx, PIBM_ERR_ARG, "too many particles per CTA");
+        c.dem_cs = cs;
+    }
+    drop_graphs(c);
+    return PIBM_OK;
+}
+
 pibm_status pibm_kernels_per_step(pibm_ctx* ctx, int* n) {
     if (!ctx || !n) return PIBM_ERR_ARG;
     Ctx& c = ctx->c;

@@ -68,6 +68,42 @@ __global__ void __launch_bounds__(CP_THREADS) k_clear(Geo G, const int* __restri
     }
 }
 
+// Pre-collision deviations of a node whose neighbours are all inside the
+// lattice (no wall or wrap): direct A-A addressing; other nodes take the
+// generic path.
+template <int D, typename S, typename R>
+__device__ __forceinline__ void load_node_fast(const Geo& G, const S* __restrict__ f, const S* __restrict__ g, int x,
+                                               int y, int z, int parity, R* s, R* sg) {
+    using L = Lat<D>;
+    const bool inner = x > 0 && x < G.nx - 1 && y > 0 && y < G.ny - 1 && (D == 2 || (z > 0 && z < G.nz - 1));
+    if (!inner) {
+        load_node<D, S, R>(G, f, g, x, y, z, parity, s, sg);
+        return;
+    }
+    const long long n = node_index(G, x, y, z), sy = G.nx, sz = (long long)G.nx * G.ny;
+    if (parity == 0) {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) s[i] = (R)f[i * G.N + n];
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) sg[k] = (R)g[k * G.N + n];
+    } else {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) s[i] = (R)f[L::opp(i) * G.N + n - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz)];
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) sg[k] = (R)g[L::opp(k) * G.N + n - (L::ex(k) + L::ey(k) * sy + L::ez(k) * sz)];
+    }
+}
+
+// FP32 estimate of eps at integer offset (ix, iy, iz) from the particle's base
+// node, centre at fractional offset c (both relative to the base node); the
+// absolute error is below 1e-6 for radii up to a few hundred nodes.
+__device__ __forceinline__ float eps_f32(int ix, int iy, int iz, const float* c, float Rp) {
+    float dx = (float)ix - c[0], dy = (float)iy - c[1], dz = (float)iz - c[2];
+    return Rp + 0.5f - sqrtf(dx * dx + dy * dy + dz * dz);
+}
+
+constexpr float EPS_GUARD = 1e-5f;  // FP32 decisions within this margin are re-taken in FP64
+
 template <int D, typename S>
 __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __restrict__ f, const S* __restrict__ g,
                                                           typename Vec4<S>::T* __restrict__ mk,
@@ -79,38 +115,55 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
     using L = Lat<D>;
     using R = S;
     __shared__ double sh_nb[CP_MAXNB][4];
+    __shared__ float sh_nbf[CP_MAXNB][4];
     __shared__ int sh_id[CP_MAXNB];
     __shared__ double red[7][CP_THREADS / 32];
     const int p = blockIdx.x;
     const double Xp[3] = {X[3 * p], X[3 * p + 1], X[3 * p + 2]};
     const double Rp = Rr[p];
+    int base[3];
+    float cf[3];
+    for (int a = 0; a < 3; a++) {
+        base[a] = (a < D) ? (int)floor(Xp[a]) : 0;
+        cf[a] = (float)(Xp[a] - base[a]);
+    }
     const int a0 = adj_start[p];
     int nnb = adj_start[p + 1] - a0;
     if (nnb > CP_MAXNB) nnb = CP_MAXNB;  // the neighbour build rejects more
     for (int k = threadIdx.x; k < nnb; k += blockDim.x) {
         int q = adj_nb[a0 + k];
         sh_id[k] = q;
-        sh_nb[k][0] = X[3 * q];
-        sh_nb[k][1] = X[3 * q + 1];
-        sh_nb[k][2] = X[3 * q + 2];
+        for (int a = 0; a < 3; a++) {
+            sh_nb[k][a] = X[3 * q + a];
+            sh_nbf[k][a] = (float)(X[3 * q + a] - base[a]);  // neighbour centre relative to p's base node
+        }
         sh_nb[k][3] = Rr[q];
+        sh_nbf[k][3] = (float)Rr[q];
     }
     __syncthreads();
     int lo[3], hi[3];
     footprint_box(G, D, Xp, Rp, lo, hi);
     int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
     long long cnt = (ex > 0 && ey > 0 && ez > 0) ? (long long)ex * ey * ez : 0;
-    const double Up[3] = {U[3 * p], U[3 * p + 1], U[3 * p + 2]};
-    const double Wp[3] = {W[3 * p], W[3 * p + 1], W[3 * p + 2]};
-    const double Tpp = Tp[p];
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    const float Upf[3] = {(float)U[3 * p], (float)U[3 * p + 1], (float)U[3 * p + 2]};
+    const float Wpf[3] = {(float)W[3 * p], (float)W[3 * p + 1], (float)W[3 * p + 2]};
+    const R dTp = (R)(Tp[p] - Tref);
+    const R twok = (R)(2.0 * kappa);
+    const float Rpf = (float)Rp;
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // per-thread partials; the block sum is FP64
     for (long long q = threadIdx.x; q < cnt; q += blockDim.x) {
         int x = lo[0] + (int)(q % ex), y = lo[1] + (int)((q / ex) % ey), z = lo[2] + (int)(q / ((long long)ex * ey));
-        double eps = eps_of((double)x, (double)y, (double)z, Xp, Rp);
+        const int ix = x - base[0], iy = y - base[1], iz = z - base[2];
+        const float ef = eps_f32(ix, iy, iz, cf, Rpf);
+        if (ef <= -EPS_GUARD) continue;  // certainly not covered
+        // eps exactly as the FP64 definition: clamped to 1 deep inside, FP64 on the rim
+        double eps = ef >= 1.0f + EPS_GUARD ? 1.0 : eps_of((double)x, (double)y, (double)z, Xp, Rp);
         if (!(eps > 0.0)) continue;
         bool own = true;
         for (int k = 0; k < nnb; k++) {
-            double e2 = eps_of((double)x, (double)y, (double)z, sh_nb[k], sh_nb[k][3]);
+            const float e2f = eps_f32(ix, iy, iz, sh_nbf[k], sh_nbf[k][3]);
+            if (e2f < (float)eps - 2.0f * EPS_GUARD) continue;  // certainly smaller: no contest
+            double e2 = e2f >= 1.0f + EPS_GUARD ? 1.0 : eps_of((double)x, (double)y, (double)z, sh_nb[k], sh_nb[k][3]);
             if (e2 > eps || (e2 == eps && sh_id[k] < p)) {
                 own = false;
                 break;
@@ -118,7 +171,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
         }
         if (!own) continue;
         R s[L::Q], sg[L::QG];
-        load_node<D, S, R>(G, f, g, x, y, z, parity, s, sg);
+        load_node_fast<D, S, R>(G, f, g, x, y, z, parity, s, sg);
         R drho = 0, j[3] = {0, 0, 0}, dT = 0;
 #pragma unroll
         for (int i = 0; i < L::Q; i++) {
@@ -130,33 +183,33 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
 #pragma unroll
         for (int k = 0; k < L::QG; k++) dT += sg[k];
         const R rho = (R)1 + drho;
-        const double arm[3] = {x - Xp[0], y - Xp[1], z - Xp[2]};
+        const float arm[3] = {(float)ix - cf[0], (float)iy - cf[1], (float)iz - cf[2]};  // r - X_p
         // U_l = U_p + omega_p x (r - X_p)
-        const double Ul[3] = {Up[0] + (Wp[1] * arm[2] - Wp[2] * arm[1]), Up[1] + (Wp[2] * arm[0] - Wp[0] * arm[2]),
-                              Up[2] + (Wp[0] * arm[1] - Wp[1] * arm[0])};
+        const float Ul[3] = {Upf[0] + (Wpf[1] * arm[2] - Wpf[2] * arm[1]), Upf[1] + (Wpf[2] * arm[0] - Wpf[0] * arm[2]),
+                             Upf[2] + (Wpf[0] * arm[1] - Wpf[1] * arm[0])};
         const R e = (R)eps;
         R M[4];
 #pragma unroll
-        for (int a = 0; a < 3; a++) M[a] = e * (R)2 * (rho * (R)Ul[a] - j[a]);      // eps F_f (Eqs lbm7, lbm8)
-        M[3] = e * (R)2 * (R)kappa * ((R)(Tpp - Tref) - dT);                       // eps Q (Eq lbm7.5)
+        for (int a = 0; a < 3; a++) M[a] = e * (R)2 * (rho * (R)Ul[a] - j[a]);  // eps F_f (Eqs lbm7, lbm8)
+        M[3] = e * twok * (dTp - dT);                                             // eps Q (Eq lbm7.5)
         if (D == 2) M[2] = 0;
         typename Vec4<S>::T mv;
         mv.x = M[0], mv.y = M[1], mv.z = M[2], mv.w = M[3];
         mk[node_index(G, x, y, z)] = mv;
-        // Eq lbm13 and the torque about the centre, accumulated in FP64
-        double MF[3] = {(double)M[0], (double)M[1], (double)M[2]};
+        // Eq lbm13 and the torque about the centre
+        const float MF[3] = {(float)M[0], (float)M[1], (float)M[2]};
         acc[0] -= MF[0];
         acc[1] -= MF[1];
         acc[2] -= MF[2];
         acc[3] -= arm[1] * MF[2] - arm[2] * MF[1];
         acc[4] -= arm[2] * MF[0] - arm[0] * MF[2];
         acc[5] -= arm[0] * MF[1] - arm[1] * MF[0];
-        acc[6] += (double)M[3];
+        acc[6] += (float)M[3];
     }
     // FP64 block reduction: warp shuffles, then one value per warp in shared memory
 #pragma unroll
     for (int a = 0; a < 7; a++) {
-        double v = acc[a];
+        double v = (double)acc[a];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = v;
     }
@@ -170,17 +223,32 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
     }
 }
 
+// Spreading over the footprint grown by one node: the marker field of the
+// region grown by two nodes is staged in shared memory, then every output node
+// gathers its 3^D neighbours from there (Eqs lbm10-lbm12, lbm12.6).
+constexpr int SPREAD_SMEM = 48 * 1024;
+
 template <int D, typename V>
 __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __restrict__ X, const double* __restrict__ Rr,
                                                        const V* __restrict__ mk, V* __restrict__ fb, uint8_t* flags, int* box) {
+    extern __shared__ __align__(32) unsigned char sm_raw[];
+    V* tile = reinterpret_cast<V*>(sm_raw);
+    using T = decltype(V().x);
     const int p = blockIdx.x;
     const double Xp[3] = {X[3 * p], X[3 * p + 1], X[3 * p + 2]};
     int lo[3], hi[3];
     footprint_box(G, D, Xp, Rr[p], lo, hi);
     int n[3] = {G.nx, G.ny, G.nz};
-    for (int a = 0; a < D; a++) {
-        lo[a] = max(lo[a] - 1, 0);
-        hi[a] = min(hi[a] + 1, n[a] - 1);
+    int ilo[3], ihi[3];  // staged input region
+    for (int a = 0; a < 3; a++) {
+        if (a < D) {
+            lo[a] = max(lo[a] - 1, 0);
+            hi[a] = min(hi[a] + 1, n[a] - 1);
+            ilo[a] = max(lo[a] - 1, 0);
+            ihi[a] = min(hi[a] + 1, n[a] - 1);
+        } else {
+            ilo[a] = ihi[a] = lo[a];
+        }
     }
     if (threadIdx.x == 0) {
         for (int a = 0; a < 3; a++) {
@@ -190,10 +258,20 @@ __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __re
     }
     int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
     if (ex <= 0 || ey <= 0 || ez <= 0) return;
-    long long cnt = (long long)ex * ey * ez;
+    const int sx = ihi[0] - ilo[0] + 1, sy = ihi[1] - ilo[1] + 1, sz = ihi[2] - ilo[2] + 1;
+    const long long ns = (long long)sx * sy * sz;
+    const bool staged = ns * (long long)sizeof(V) <= SPREAD_SMEM;
+    if (staged) {
+        for (long long q = threadIdx.x; q < ns; q += blockDim.x) {
+            int x = ilo[0] + (int)(q % sx), y = ilo[1] + (int)((q / sx) % sy), z = ilo[2] + (int)(q / ((long long)sx * sy));
+            tile[q] = mk[node_index(G, x, y, z)];
+        }
+        __syncthreads();
+    }
+    const long long cnt = (long long)ex * ey * ez;
     for (long long q = threadIdx.x; q < cnt; q += blockDim.x) {
         int x = lo[0] + (int)(q % ex), y = lo[1] + (int)((q / ex) % ey), z = lo[2] + (int)(q / ((long long)ex * ey));
-        decltype(V().x) s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
         for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); dz++) {
             int zz = z + dz;
             if (zz < 0 || zz >= G.nz) continue;
@@ -204,9 +282,10 @@ __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __re
                     int xx = x + dx;
                     if (xx < 0 || xx >= G.nx) continue;
                     // delta_h(0) = 1/2, delta_h(+-1) = 1/4 (Eq lbm12)
-                    decltype(V().x) w = (dx == 0 ? 0.5 : 0.25) * (dy == 0 ? 0.5 : 0.25);
-                    if (D == 3) w *= (dz == 0 ? 0.5 : 0.25);
-                    V m = mk[node_index(G, xx, yy, zz)];
+                    T w = (T)((dx == 0 ? 0.5 : 0.25) * (dy == 0 ? 0.5 : 0.25));
+                    if (D == 3) w *= (T)(dz == 0 ? 0.5 : 0.25);
+                    V m = staged ? tile[((long long)(zz - ilo[2]) * sy + (yy - ilo[1])) * sx + (xx - ilo[0])]
+                                 : mk[node_index(G, xx, yy, zz)];
                     s0 += w * m.x;
                     s1 += w * m.y;
                     s2 += w * m.z;
@@ -324,7 +403,7 @@ static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
         k_footprint<D, S><<<c->np, CP_THREADS, 0, s>>>(c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk, c->X, c->U, c->W,
                                                        c->R, c->Tp, c->adj_start, c->adj_nb, c->desc.kappa_T,
                                                        c->desc.T_ref, parity, c->Fh, c->Th, c->Hh);
-        k_spread<D, V><<<c->np, CP_THREADS, 0, s>>>(c->G, c->X, c->R, (const V*)c->mk, (V*)c->fb, c->flags, c->box);
+        k_spread<D, V><<<c->np, CP_THREADS, SPREAD_SMEM, s>>>(c->G, c->X, c->R, (const V*)c->mk, (V*)c->fb, c->flags, c->box);
     }
     if (c->nm > 0) {
         int nb = (c->nm + CP_THREADS - 1) / CP_THREADS;

@@ -244,6 +244,7 @@ struct Priv {
     double im, iI, R;        // 1/m, 1/I, radius
     float Fc[3], Tc[3];      // contact force / torque of the last evaluation
     int fixed, wall_mask;    // wall_mask: faces with a non-zero tangential history
+    int nadj, pad;           // neighbours in the adjacency
 };
 
 // velocity Verlet half kick: U += h (F_c/m + a_ext), omega += h (T_c/I + alpha_ext)
@@ -275,6 +276,8 @@ __device__ __forceinline__ void publish_s(const Priv& P, Pub& pub) {
     }
 }
 
+constexpr int DEM_MAXA = 8;  // neighbours per particle staged in shared memory
+
 template <int D>
 __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, int advance) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -284,6 +287,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
     const int per = C.per;
     Pub* pub = reinterpret_cast<Pub*>(smem);                     // [2][per]
     Priv* prv = reinterpret_cast<Priv*>(pub + 2 * per);          // [per]
+    int2* adj = reinterpret_cast<int2*>(prv + per);              // [per][DEM_MAXA]: (neighbour, +-pair)
     const int n = C.n;
     const unsigned rank = cl.block_rank();
     const unsigned csize = cl.num_blocks();
@@ -330,6 +334,10 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             } else {
                 publish_s(P, pub[l]);
             }
+            // the adjacency is fixed during the lattice step: stage it (up to DEM_MAXA entries)
+            const int e0 = S.adj_start[p], ne = S.adj_start[p + 1] - e0;
+            P.nadj = ne;
+            for (int e = 0; e < ne && e < DEM_MAXA; e++) adj[l * DEM_MAXA + e] = make_int2(S.adj_nb[e0 + e], S.adj_k[e0 + e]);
         }
         cl.sync();
         for (int sub = 0; sub < nsub; sub++) {
@@ -344,10 +352,15 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 const double Rp = P.R;
                 float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};  // contact sums (a few terms) in FP32
                 wall_forces<D>(C, S, p, me, Rp, dtf, F, T, P.wall_mask);
-                const int e1 = __ldg(S.adj_start + p + 1);
-                for (int e = __ldg(S.adj_start + p); e < e1; e++) {
-                    const int q = __ldg(S.adj_nb + e);
-                    const int kk = __ldg(S.adj_k + e);
+                const int ne = P.nadj, e0 = ne > DEM_MAXA ? __ldcg(S.adj_start + p) : 0;
+                for (int e = 0; e < ne; e++) {
+                    int q, kk;
+                    if (ne <= DEM_MAXA) {
+                        const int2 a = adj[l * DEM_MAXA + e];
+                        q = a.x, kk = a.y;
+                    } else {
+                        q = __ldcg(S.adj_nb + e0 + e), kk = __ldcg(S.adj_k + e0 + e);
+                    }
                     const bool first = kk >= 0;
                     const int k = first ? kk : ~kk;
                     const int rq = q / per, lq = q - rq * per;
@@ -606,13 +619,14 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
 }
 
 // cluster size: up to 16 CTAs of DEM_T threads, at most DEM_MAXPER particles per CTA
-constexpr int DEM_MAXPER = 768;  // (2 * 48 + 176) B per particle: 204 KB of shared memory
+constexpr int DEM_MAXPER = 640;  // (2 * 48 + 184 + 64) B per particle: 220 KB of shared memory
 
-static size_t dem_smem(int per) { return (size_t)per * (2 * sizeof(Pub) + sizeof(Priv)); }
+static size_t dem_smem(int per) { return (size_t)per * (2 * sizeof(Pub) + sizeof(Priv) + DEM_MAXA * sizeof(int2)); }
 
 int dem_cluster_size(Ctx* c) {
     int n = c->np;
-    int cs = (n + 31) / 32;
+    int cs = c->tune_dem_particles_per_cta > 0 ? (n + c->tune_dem_particles_per_cta - 1) / c->tune_dem_particles_per_cta
+                                               : (n + 31) / 32;
     cs = cs < 1 ? 1 : (cs > 16 ? 16 : cs);
     if (cs > 8) {
         int max16 = 0;  // is a 16-CTA cluster with this much shared memory schedulable here?

@@ -178,26 +178,41 @@ template <typename R> struct OddStore<3, R, 19> {
                                                long long, const R*, const R*) {}
 };
 
+// Flat offsets of the A-A slots relative to the node index n, per direction
+// (uniform over the grid, computed once on the host): odd-step sources
+// plane opp(i) at n - e_i, odd-step destinations plane i at n + e_i, even-step
+// loads plane i at n and stores plane opp(i) at n.
+struct AAOffsets {
+    long long src[19], dst[19], ld[19], st[19];
+};
+
 template <int D, typename S, int PARITY>
 __global__ void __launch_bounds__(256) k_stream_collide(Geo G, S* __restrict__ f, S* __restrict__ g,
                                                         const typename Vec4<S>::T* __restrict__ fb,
-                                                        const uint8_t* __restrict__ flags, CollideParams<S> P) {
+                                                        const uint8_t* __restrict__ flags, CollideParams<S> P,
+                                                        AAOffsets O) {
     using L = Lat<D>;
     using R = S;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= G.nx) return;
-    const long long N = G.N;
     const long long n = node_index(G, x, y, z);
     const long long sy = G.nx, sz = (long long)G.nx * G.ny;
     // y and z are uniform across the block, so this test never splits a warp
     const bool inner_yz = y > 0 && y < G.ny - 1 && (D == 2 || (z > 0 && z < G.nz - 1));
     R s[L::Q], sg[L::QG];
+    // lanes on the x faces need the wrap / bounce fix-up (warp-divergent only there)
+    const bool xedge = x == 0 || x == G.nx - 1;
     if (PARITY == 0) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) s[i] = f[i * N + n];
+        for (int i = 0; i < L::Q; i++) s[i] = f[n + O.ld[i]];
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) sg[k] = g[k * N + n];
+        for (int k = 0; k < L::QG; k++) sg[k] = g[n + O.ld[k]];
+    } else if (inner_yz && !xedge) {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) s[i] = f[n + O.src[i]];
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) sg[k] = g[n + O.src[k]];
     } else if (inner_yz) {
         OddLoad<D, R, 0>::run(G, P, f, g, n, x, sy, sz, s, sg);
     } else {
@@ -214,9 +229,14 @@ __global__ void __launch_bounds__(256) k_stream_collide(Geo G, S* __restrict__ f
     collide_node<D, R>(s, sg, fbx, fby, fbz, qb, P);
     if (PARITY == 0) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) f[L::opp(i) * N + n] = s[i];
+        for (int i = 0; i < L::Q; i++) f[n + O.st[i]] = s[i];
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) g[L::opp(k) * N + n] = sg[k];
+        for (int k = 0; k < L::QG; k++) g[n + O.st[k]] = sg[k];
+    } else if (inner_yz && !xedge) {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) f[n + O.dst[i]] = s[i];
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) g[n + O.dst[k]] = sg[k];
     } else if (inner_yz) {
         OddStore<D, R, 0>::run(G, P, f, g, n, x, sy, sz, s, sg);
     } else {
@@ -254,16 +274,33 @@ static CollideParams<R> collide_params(const Ctx* c) {
     return P;
 }
 
+template <int D>
+static AAOffsets aa_offsets(const Geo& G) {
+    using L = Lat<D>;
+    AAOffsets O;
+    const long long sy = G.nx, sz = (long long)G.nx * G.ny;
+    for (int i = 0; i < 19; i++) O.src[i] = O.dst[i] = O.ld[i] = O.st[i] = 0;
+    for (int i = 0; i < L::Q; i++) {
+        long long off = L::ex(i) + L::ey(i) * sy + L::ez(i) * sz;
+        O.src[i] = (long long)L::opp(i) * G.N - off;
+        O.dst[i] = (long long)i * G.N + off;
+        O.ld[i] = (long long)i * G.N;
+        O.st[i] = (long long)L::opp(i) * G.N;
+    }
+    return O;
+}
+
 template <int D, typename S>
 static cudaError_t sc_launch(Ctx* c, cudaStream_t s, int parity) {
     dim3 block(256), grid((c->G.nx + 255) / 256, c->G.ny, c->G.nz);
     if (c->G.nx <= 128) block.x = 128, grid.x = (c->G.nx + 127) / 128;
     CollideParams<S> P = collide_params<S>(c);
+    AAOffsets O = aa_offsets<D>(c->G);
     using V = typename Vec4<S>::T;
     if (parity == 0)
-        k_stream_collide<D, S, 0><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb, c->flags, P);
+        k_stream_collide<D, S, 0><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb, c->flags, P, O);
     else
-        k_stream_collide<D, S, 1><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb, c->flags, P);
+        k_stream_collide<D, S, 1><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb, c->flags, P, O);
     return cudaGetLastError();
 }
 

@@ -221,6 +221,7 @@ struct Ctx {
     float* wall_ft;
     int adj_cap;
     int dem_cs;           // CTAs in the DEM cluster
+    int tune_dem_particles_per_cta;  // 0: default (32)
     int* contact_pairs;   // 2 * dem.cap ints
     int* contact_scratch; // 2 * np + 4 ints
 

@@ -245,3 +245,24 @@ def test_full_size_sed3d_properties():
     assert d1["nonfinite"] == 0
     assert abs(d1["mass"] - d0["mass"]) / d0["mass"] < 1e-6
     assert d1["min_height"] < d0["min_height"]  # the spheres sink
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_footprint_ownership_ties(dim):
+    # Particles placed mirror-symmetrically about the node plane x = 13: nodes on
+    # that plane have equal eps for both, and belong to the lower index.  A
+    # wrong tie rule moves whole nodes between particles and shows up in the
+    # per-particle force and heat at the 1e-2 level.
+    shape = (28, 22, 1) if dim == 2 else (28, 20, 20)
+    c = 10.0 if dim == 2 else 9.5
+    X = [[10.0, c, 0.0 if dim == 2 else c], [16.0, c, 0.0 if dim == 2 else c], [13.0, c + 6.0, 0.0 if dim == 2 else c]]
+    U = np.array([[0.01, 0.002, 0.0], [-0.01, 0.001, 0.0], [0.0, -0.01, 0.0]])
+    case = W.periodic_box(shape=shape, dim=dim, buoyancy=False)
+    case.update(walls=[(1, 1, 0.0)] * (2 * dim), pibm=True, contact=W.spring_dashpot(), T_init=0.3,
+                particles=dict(X=X, U=U, R=[3.2, 3.2, 3.2], rho_p=[1.5, 1.5, 1.5], T_p=[1.0, 0.8, 0.6]))
+    sim, orc = _sim(case), oracle.Oracle(case)
+    Fs, Fo = sim.read_particle_forces(), orc.particle_forces()
+    for key in ("F", "H"):
+        scale = np.abs(Fo[key]).max()
+        assert np.max(np.abs(Fs[key] - Fo[key])) < 1e-5 * scale, key
+    assert rel_l2(sim.read_field("FBx"), orc.field("FBx")) < 1e-5
