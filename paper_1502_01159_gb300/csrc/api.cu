@@ -402,7 +402,7 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
         c.nb_start[b] = (int*)A(sizeof(int) * (n + 2));
         c.nb_i[b] = (int*)A(sizeof(int) * C.cap);
         c.nb_j[b] = (int*)A(sizeof(int) * C.cap);
-        c.nb_ft[b] = (float*)A(sizeof(float) * 2 * 3 * C.cap);  // two substep buffers
+        c.nb_ft[b] = (float*)A(sizeof(float4) * 2 * C.cap);  // two substep buffers of (history, stamp)
     }
     c.adj_start = (int*)A(sizeof(int) * (n + 2));
     c.adj_nb = (int*)A(sizeof(int) * c.adj_cap);

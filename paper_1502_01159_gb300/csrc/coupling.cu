@@ -206,12 +206,12 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
         acc[5] -= arm[0] * MF[1] - arm[1] * MF[0];
         acc[6] += (float)M[3];
     }
-    // FP64 block reduction: warp shuffles, then one value per warp in shared memory
+    // warp sums in FP32 (32 partials), the per-particle total over the warps in FP64
 #pragma unroll
     for (int a = 0; a < 7; a++) {
-        double v = (double)acc[a];
+        float v = acc[a];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = v;
+        if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = (double)v;
     }
     __syncthreads();
     if (threadIdx.x < 7) {
@@ -282,8 +282,8 @@ __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __re
                     int xx = x + dx;
                     if (xx < 0 || xx >= G.nx) continue;
                     // delta_h(0) = 1/2, delta_h(+-1) = 1/4 (Eq lbm12)
-                    T w = (T)((dx == 0 ? 0.5 : 0.25) * (dy == 0 ? 0.5 : 0.25));
-                    if (D == 3) w *= (T)(dz == 0 ? 0.5 : 0.25);
+                    T w = (dx == 0 ? (T)0.5 : (T)0.25) * (dy == 0 ? (T)0.5 : (T)0.25);
+                    if (D == 3) w *= (dz == 0 ? (T)0.5 : (T)0.25);
                     V m = staged ? tile[((long long)(zz - ilo[2]) * sy + (yy - ilo[1])) * sx + (xx - ilo[0])]
                                  : mk[node_index(G, xx, yy, zz)];
                     s0 += w * m.x;

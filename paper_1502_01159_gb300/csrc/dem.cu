@@ -41,8 +41,8 @@ struct DemState {
     const uint8_t* fixed;
     int *cell_of, *cell_cnt, *cell_start, *cell_ids, *cnt_hi, *cnt_lo;
     int *nb_start0, *nb_start1, *nb_i0, *nb_i1, *nb_j0, *nb_j1;
-    float *nb_ft0, *nb_ft1;  // per list: two substep buffers of 3 * cap floats
-    int* nb_cur;             // [0] current list, [1] current history buffer
+    float4 *nb_ft0, *nb_ft1;  // per list: two substep buffers of cap entries (history xyz, substep stamp)
+    int* nb_cur;              // [0] current list, [1] global substep counter
     int *adj_start, *adj_nb, *adj_k;
     float* wall_ft;
     int* dstat;
@@ -295,13 +295,13 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
     const int base = rank * per;
     const int nloc = max(0, min(per, n - base));
     const int cur = __ldcg(S.nb_cur);
-    const int hcur = __ldcg(S.nb_cur + 1);
+    const int gbase = __ldcg(S.nb_cur + 1);  // global index of this launch's first substep
     const int* nb_start = cur ? S.nb_start1 : S.nb_start0;
     const int* nb_j = cur ? S.nb_j1 : S.nb_j0;
-    float* nb_ft = cur ? S.nb_ft1 : S.nb_ft0;
+    float4* nb_ft = cur ? S.nb_ft1 : S.nb_ft0;
     const double dt = C.dt;
     const float dtf = (float)dt;
-    int hfinal = hcur;
+    int gnow = gbase;  // global substep counter after this launch
 
     if (advance) {
         const int hp = __ldcg(S.have_prev);
@@ -342,9 +342,12 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
         cl.sync();
         for (int sub = 0; sub < nsub; sub++) {
             const int rb = sub & 1;                      // published buffer read this substep
-            const int hb = (hcur + sub) & 1;             // history buffer read this substep
-            const float* hist_old = nb_ft + (size_t)hb * 3 * C.cap;
-            float* hist_new = nb_ft + (size_t)(hb ^ 1) * 3 * C.cap;
+            // tangential history: entries carry the global substep that wrote them; a pair's
+            // history is valid only if written in the previous substep (it was in contact),
+            // so pairs out of contact cost no memory traffic
+            const int gsub = gbase + sub;
+            const float4* hist_old = nb_ft + (size_t)(gsub & 1) * C.cap;
+            float4* hist_new = nb_ft + (size_t)((gsub + 1) & 1) * C.cap;
             for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
                 const int p = base + l;
                 Priv& P = prv[l];
@@ -373,15 +376,18 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                     const float dxf = (float)(B.x[0] - A.x[0]), dyf = (float)(B.x[1] - A.x[1]), dzf = (float)(B.x[2] - A.x[2]);
                     const float sf = (float)(Ra + Rb) + 1e-3f;
                     float3 Fa = f3(0.f, 0.f, 0.f), Ta = Fa, Tb = Fa, h = Fa;
+                    bool contact = false;
                     if (dxf * dxf + dyf * dyf + dzf * dzf < sf * sf) {
                         double d2 = dist2(A.x, B.x), Ssum = Ra + Rb;
-                        if (d2 < Ssum * Ssum)
-                            h = f3(__ldcg(hist_old + 3 * k), __ldcg(hist_old + 3 * k + 1), __ldcg(hist_old + 3 * k + 2));
-                        pair_force(C, A, B, Ra, Rb, h, dtf, Fa, Ta, Tb);
+                        contact = d2 < Ssum * Ssum;
+                        if (contact) {
+                            const float4 hv = __ldcg(hist_old + k);
+                            if (__float_as_int(hv.w) == gsub - 1) h = f3(hv.x, hv.y, hv.z);
+                            pair_force(C, A, B, Ra, Rb, h, dtf, Fa, Ta, Tb);
+                        }
                     }
                     if (first) {
-                        float* hn = hist_new + 3 * k;
-                        hn[0] = h.x, hn[1] = h.y, hn[2] = h.z;
+                        if (contact) hist_new[k] = make_float4(h.x, h.y, h.z, __int_as_float(gsub));
                         F[0] += Fa.x, F[1] += Fa.y, F[2] += Fa.z;
                         T[0] += Ta.x, T[1] += Ta.y, T[2] += Ta.z;
                     } else {
@@ -406,7 +412,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             }
             cl.sync();
         }
-        hfinal = (hcur + nsub) & 1;
+        gnow = gbase + nsub;
         // write back; thermosensitive particles: C_p dT_p / dt = -H_p over one
         // lattice step; keep this step's coupling as the previous one
         int moved = 0;
@@ -440,7 +446,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
         for (unsigned r = 0; r < csize; r++) need |= *cl.map_shared_rank(&need_flag, r);
         if (!need) {
             cl.sync();  // no CTA may exit while others still read its shared memory
-            if (gt == 0) S.nb_cur[1] = hfinal;
+            if (gt == 0) S.nb_cur[1] = gnow;
             return;
         }
     }
@@ -510,8 +516,10 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
     int* nst = cur ? S.nb_start0 : S.nb_start1;
     int* ni = cur ? S.nb_i0 : S.nb_i1;
     int* nj = cur ? S.nb_j0 : S.nb_j1;
-    float* nft = cur ? S.nb_ft0 : S.nb_ft1;   // new history goes into buffer 0
-    const float* oft = nb_ft + (size_t)hfinal * 3 * C.cap;
+    // histories written in the last substep (stamp gnow - 1) live in buffer gnow & 1 of the
+    // old list; the new list gets them in the same buffer with the same stamp
+    float4* nft = (cur ? S.nb_ft0 : S.nb_ft1) + (size_t)(gnow & 1) * C.cap;
+    const float4* oft = nb_ft + (size_t)(gnow & 1) * C.cap;
     if (rank == 0) {
         cta_scan(S.cnt_hi, nst, n, sh);
         for (int i = threadIdx.x; i < n; i += blockDim.x) S.cnt_lo[i] += S.cnt_hi[i];
@@ -524,7 +532,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
     }
     cl.sync();
     if (__ldcg(S.flag)) {  // keep the previous list and adjacency; the host reports the status
-        if (gt == 0) S.nb_cur[1] = hfinal;
+        if (gt == 0) S.nb_cur[1] = gnow;
         return;
     }
     for (int i = gt; i < n; i += gs) {
@@ -562,7 +570,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 if (v < j) L = mid + 1;
                 else Hh = mid - 1;
             }
-            for (int a = 0; a < 3; a++) nft[3 * (o + r) + a] = found >= 0 ? oft[3 * found + a] : 0.f;
+            nft[o + r] = found >= 0 ? __ldcg(oft + found) : make_float4(0.f, 0.f, 0.f, __int_as_float(-2));
         }
     }
     cl.sync();
@@ -614,7 +622,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
     for (int i = gt; i <= n; i += gs) S.adj_start[i] = __ldcg(S.adj_new + i);
     if (gt == 0) {
         S.nb_cur[0] = cur ^ 1;
-        S.nb_cur[1] = 0;
+        S.nb_cur[1] = gnow;
     }
 }
 
@@ -671,7 +679,7 @@ static DemState dem_state(Ctx* c) {
     S.nb_start0 = c->nb_start[0], S.nb_start1 = c->nb_start[1];
     S.nb_i0 = c->nb_i[0], S.nb_i1 = c->nb_i[1];
     S.nb_j0 = c->nb_j[0], S.nb_j1 = c->nb_j[1];
-    S.nb_ft0 = c->nb_ft[0], S.nb_ft1 = c->nb_ft[1];
+    S.nb_ft0 = (float4*)c->nb_ft[0], S.nb_ft1 = (float4*)c->nb_ft[1];
     S.nb_cur = c->nb_cur;
     S.adj_start = c->adj_start, S.adj_nb = c->adj_nb, S.adj_k = c->adj_k;
     S.wall_ft = c->wall_ft;
