@@ -228,6 +228,54 @@ def e2e_run(case, steps, torch):
                     "then per step: step + particle state read-back; final temperature field read-back"}
 
 
+def precision_study(torch, flush):
+    """Reduced-precision storage (FP16 / BF16 deviations, FP32 arithmetic) against
+    the plain FP32 form: throughput of the fused lattice kernel and of the whole
+    step on the full sed3d workload, and the error against the FP64 oracle on a
+    40x40x64 sedimentation crop (8 spheres, 50 steps) with the same recipe."""
+    import numpy as np
+
+    import oracle
+    import workloads as W
+    from paper_1502_01159_gb300 import Simulation
+    out = {}
+    crop = W.sed3d(nx=40, ny=40, nz=64, n_p=8, config_index=2)
+    crop["g_particle"] = [0.0, 0.0, -2e-4]
+    orc = oracle.Oracle(crop)
+    orc.step(50)
+    ref = {k: orc.field(k) for k in ("rho", "T", "ux", "uy", "uz")}
+    refX = orc.particles()["X"]
+    orc.close()
+    nodes = 256 * 256 * 512
+    for storage in ("f32", "f16", "bf16"):
+        case = W.sed3d()
+        case["storage"] = storage
+        sim, ms = measure_gpu(case, 8, 3, torch, flush)
+        kt = kernel_times(sim, 5, torch, flush)
+        sim.close()
+        c2 = dict(crop)
+        c2["storage"] = storage
+        s2 = Simulation(c2)
+        s2.step(50)
+
+        def rl2(a, b):
+            return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        err = {"rho": rl2(s2.read_field("rho"), ref["rho"]), "T": rl2(s2.read_field("T"), ref["T"]),
+               "u": rl2(np.stack([s2.read_field(c) for c in ("ux", "uy", "uz")]),
+                        np.stack([ref[c] for c in ("ux", "uy", "uz")])),
+               "X_max_abs": float(np.max(np.abs(s2.read_particles()["X"] - refX)))}
+        s2.close()
+        step = statistics.mean(ms)
+        out[storage] = {"step_ms": round(step, 4), "MLUPS": round(nodes / (step * 1e-3) / 1e6, 1),
+                        "stream_collide_ms": round(kt["stream_collide"], 4),
+                        "error_vs_fp64_oracle_crop": {k: float(f"{v:.3g}") for k, v in err.items()}}
+    for storage in ("f16", "bf16"):
+        out[storage]["speedup_step_vs_f32"] = round(out["f32"]["step_ms"] / out[storage]["step_ms"], 3)
+        out[storage]["speedup_kernel_vs_f32"] = round(out["f32"]["stream_collide_ms"] / out[storage]["stream_collide_ms"], 3)
+    out["workload"] = "sed3d full size for speed; 40x40x64 crop, 8 spheres, 50 steps for the error"
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -316,6 +364,10 @@ def run_ours(args):
                                   "kernel": "k_stream_collide", "bytes_per_node": b3, "nodes_per_launch": n3}}
         sim3.close()
 
+    precision = None
+    if rank == 0 and world == 1 and args.workload == "sed2d" and not args.no_3d and not args.no_precision:
+        precision = precision_study(torch, flush)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -335,6 +387,8 @@ def run_ours(args):
         }
         if secondary:
             line["secondary"] = secondary
+        if precision:
+            line["precision"] = precision
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -352,6 +406,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -70,7 +70,10 @@ typedef enum {
 enum { PIBM_PERIODIC = 0, PIBM_WALL = 1 };           /* wall kind per face */
 enum { PIBM_ADIABATIC = 0, PIBM_ISOTHERMAL = 1 };    /* thermal condition per wall face */
 enum { PIBM_SPRING_DASHPOT = 0, PIBM_HERTZ_MD = 1 }; /* contact law */
-enum { PIBM_STORE_F32 = 0, PIBM_STORE_F64 = 1 };     /* population storage (deviation form) */
+/* population storage (deviation form f - w, g - w T_ref; arithmetic in FP32
+ * for F32 / F16 / BF16, FP64 for F64; F16 stores the deviations scaled by 2^10
+ * (flow) and 2^8 (thermal), BF16 unscaled) */
+enum { PIBM_STORE_F32 = 0, PIBM_STORE_F64 = 1, PIBM_STORE_F16 = 2, PIBM_STORE_BF16 = 3 };
 enum {                                                /* fields for pibm_read_field */
     PIBM_RHO = 0, PIBM_UX, PIBM_UY, PIBM_UZ, PIBM_T, PIBM_FBX, PIBM_FBY, PIBM_FBZ, PIBM_QB
 };
@@ -89,7 +92,7 @@ typedef struct {
 typedef struct {
     int dim;                /* 2 or 3 */
     int nx, ny, nz;         /* lattice size; nz = 1 in 2-D */
-    int storage;            /* PIBM_STORE_F32 or PIBM_STORE_F64 */
+    int storage;            /* PIBM_STORE_F32, _F64, _F16 or _BF16 */
     double Ra, Pr;          /* Rayleigh and Prandtl numbers */
     double U_c, L_c;        /* characteristic velocity (lattice units) and length (nodes) */
     double T_ref;           /* Boussinesq reference temperature */

@@ -16,7 +16,8 @@ PIBM_OK, PIBM_ERR_ARG, PIBM_ERR_OOM, PIBM_ERR_CUDA, PIBM_ERR_STATE, PIBM_ERR_UNS
 PERIODIC, WALL = 0, 1
 ADIABATIC, ISOTHERMAL = 0, 1
 SPRING_DASHPOT, HERTZ_MD = 0, 1
-STORE_F32, STORE_F64 = 0, 1
+STORE_F32, STORE_F64, STORE_F16, STORE_BF16 = 0, 1, 2, 3
+STORAGE = {"f32": STORE_F32, "f64": STORE_F64, "f16": STORE_F16, "bf16": STORE_BF16}
 FIELDS = {"rho": 0, "ux": 1, "uy": 2, "uz": 3, "T": 4, "FBx": 5, "FBy": 6, "FBz": 7, "QB": 8}
 
 # every symbol include/pibm.h declares, with (restype, argtypes)
@@ -146,7 +147,7 @@ class Simulation:
         d = pibm_desc()
         d.dim = case["dim"]
         d.nx, d.ny, d.nz = case["shape"]
-        d.storage = STORE_F64 if case.get("storage", "f32") == "f64" else STORE_F32
+        d.storage = STORAGE[case.get("storage", "f32")]
         d.Ra, d.Pr, d.U_c, d.L_c = case["Ra"], case["Pr"], case["U_c"], case["L_c"]
         d.T_ref, d.T_init = case["T_ref"], case["T_init"]
         d.buoyancy, d.gravity_axis = int(case["buoyancy"]), case["gravity_axis"]

@@ -163,7 +163,8 @@ pibm_status pibm_create(const pibm_desc* d, void* stream, const pibm_allocator* 
     *out = nullptr;
     if ((d->dim != 2 && d->dim != 3) || d->nx < 1 || d->ny < 1 || d->nz < 1 || (d->dim == 2 && d->nz != 1))
         return g_create_error = "invalid lattice size", PIBM_ERR_ARG;
-    if (d->storage != PIBM_STORE_F32 && d->storage != PIBM_STORE_F64)
+    if (d->storage != PIBM_STORE_F32 && d->storage != PIBM_STORE_F64 && d->storage != PIBM_STORE_F16 &&
+        d->storage != PIBM_STORE_BF16)
         return g_create_error = "invalid storage", PIBM_ERR_ARG;
     if (!(d->Ra > 0) || !(d->Pr > 0) || !(d->U_c > 0) || !(d->L_c > 0) || d->gravity_axis < 0 ||
         d->gravity_axis >= d->dim || d->dem_substeps < 1 || d->nu_dT == 0.0)
@@ -180,7 +181,8 @@ pibm_status pibm_create(const pibm_desc* d, void* stream, const pibm_allocator* 
     c.G.nx = d->nx, c.G.ny = d->ny, c.G.nz = d->nz;
     c.G.N = (long long)d->nx * d->ny * d->nz;
     c.G.ntx = (d->nx + 31) / 32;
-    c.es = d->storage == PIBM_STORE_F64 ? 8 : 4;
+    c.es = d->storage == PIBM_STORE_F64 ? 8 : (d->storage == PIBM_STORE_F32 ? 4 : 2);
+    c.v4 = d->storage == PIBM_STORE_F64 ? 32 : 16;  // F_B / Q_B and marker fields: double4 or float4
     // Eq lbm2.6: nu = U_c L_c sqrt(Pr / Ra); Eq lbm2.7 with Pr = nu / alpha
     c.nu = d->U_c * d->L_c * sqrt(d->Pr / d->Ra);
     c.alpha = c.nu / d->Pr;
@@ -211,8 +213,8 @@ pibm_status pibm_create(const pibm_desc* d, void* stream, const pibm_allocator* 
     long long N = c.G.N;
     c.f = dalloc(ctx, (size_t)c.Q * N * c.es, GRP_LATTICE);
     c.g = dalloc(ctx, (size_t)c.QG * N * c.es, GRP_LATTICE);
-    c.fb = dalloc(ctx, (size_t)N * 4 * c.es, GRP_LATTICE);
-    c.mk = dalloc(ctx, (size_t)N * 4 * c.es, GRP_LATTICE);
+    c.fb = dalloc(ctx, (size_t)N * c.v4, GRP_LATTICE);
+    c.mk = dalloc(ctx, (size_t)N * c.v4, GRP_LATTICE);
     c.flags = (uint8_t*)dalloc(ctx, (size_t)c.G.ntx * d->ny * d->nz, GRP_LATTICE);
     c.red = (double*)dalloc(ctx, sizeof(double) * (4 * 512 + 16), GRP_LATTICE);
     c.dstat = (int*)dalloc(ctx, sizeof(int) * 4, GRP_LATTICE);
@@ -320,8 +322,8 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     dfree_group(ctx, GRP_PARTICLES);
     c.np = 0;
     c.dem.n = 0;
-    PCHECK(cudaMemsetAsync(c.mk, 0, (size_t)c.G.N * 4 * c.es, c.s0));
-    PCHECK(cudaMemsetAsync(c.fb, 0, (size_t)c.G.N * 4 * c.es, c.s0));
+    PCHECK(cudaMemsetAsync(c.mk, 0, (size_t)c.G.N * c.v4, c.s0));
+    PCHECK(cudaMemsetAsync(c.fb, 0, (size_t)c.G.N * c.v4, c.s0));
     PCHECK(cudaMemsetAsync(c.flags, 0, (size_t)c.G.ntx * c.G.ny * c.G.nz, c.s0));
     PCHECK(cudaMemsetAsync(c.dstat, 0, sizeof(int) * 4, c.s0));
     PCHECK(cudaMemsetAsync(c.nb_cur, 0, sizeof(int) * 2, c.s0));
@@ -465,7 +467,7 @@ pibm_status pibm_set_markers(pibm_ctx* ctx, int n, const double* X, const double
     drop_graphs(c);
     dfree_group(ctx, GRP_MARKERS);
     c.nm = 0;
-    PCHECK(cudaMemsetAsync(c.fb, 0, (size_t)c.G.N * 4 * c.es, c.s0));
+    PCHECK(cudaMemsetAsync(c.fb, 0, (size_t)c.G.N * c.v4, c.s0));
     PCHECK(cudaMemsetAsync(c.flags, 0, (size_t)c.G.ntx * c.G.ny * c.G.nz, c.s0));
     if (n == 0) return prime(ctx);
     // node -> (marker, weight) lists for the spreading gather; delta_h of Eq lbm12
@@ -521,7 +523,7 @@ pibm_status pibm_set_markers(pibm_ctx* ctx, int n, const double* X, const double
     c.MA = (double*)Al(sizeof(double) * n);
     c.MT = (double*)Al(sizeof(double) * n);
     c.nu_part = (double*)Al(sizeof(double) * n);
-    c.Ml = Al((size_t)n * 4 * c.es);
+    c.Ml = Al((size_t)n * c.v4);
     c.csr_node = (long long*)Al(sizeof(long long) * nodes.size());
     c.csr_start = (int*)Al(sizeof(int) * start.size());
     c.csr_marker = (int*)Al(sizeof(int) * mk.size());

@@ -83,14 +83,14 @@ __device__ __forceinline__ void load_node_fast(const Geo& G, const S* __restrict
     const long long n = node_index(G, x, y, z), sy = G.nx, sz = (long long)G.nx * G.ny;
     if (parity == 0) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) s[i] = (R)f[i * G.N + n];
+        for (int i = 0; i < L::Q; i++) s[i] = (R)Store<S>::ldf(f[i * G.N + n]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) sg[k] = (R)g[k * G.N + n];
+        for (int k = 0; k < L::QG; k++) sg[k] = (R)Store<S>::ldg(g[k * G.N + n]);
     } else {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) s[i] = (R)f[L::opp(i) * G.N + n - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz)];
+        for (int i = 0; i < L::Q; i++) s[i] = (R)Store<S>::ldf(f[L::opp(i) * G.N + n - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz)]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) sg[k] = (R)g[L::opp(k) * G.N + n - (L::ex(k) + L::ey(k) * sy + L::ez(k) * sz)];
+        for (int k = 0; k < L::QG; k++) sg[k] = (R)Store<S>::ldg(g[L::opp(k) * G.N + n - (L::ex(k) + L::ey(k) * sy + L::ez(k) * sz)]);
     }
 }
 
@@ -106,30 +106,45 @@ constexpr float EPS_GUARD = 1e-5f;  // FP32 decisions within this margin are re-
 
 template <int D, typename S>
 __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __restrict__ f, const S* __restrict__ g,
-                                                          typename Vec4<S>::T* __restrict__ mk,
+                                                          typename Store<S>::V4* __restrict__ mk,
                                                           const double* __restrict__ X, const double* __restrict__ U,
                                                           const double* __restrict__ W, const double* __restrict__ Rr,
                                                           const double* __restrict__ Tp, const int* __restrict__ adj_start,
                                                           const int* __restrict__ adj_nb, double kappa, double Tref,
                                                           int parity, double* Fh, double* Th, double* Hh) {
     using L = Lat<D>;
-    using R = S;
+    using R = typename Store<S>::R;
     __shared__ double sh_nb[CP_MAXNB][4];
     __shared__ float sh_nbf[CP_MAXNB][4];
     __shared__ int sh_id[CP_MAXNB];
     __shared__ double red[7][CP_THREADS / 32];
+    // per-particle constants, computed once by thread 0 (FP64 is slow on this GPU)
+    __shared__ int s_box[6], s_base[3];
+    __shared__ float s_cf[3], s_U[3], s_W[3], s_misc[3];
     const int p = blockIdx.x;
     const double Xp[3] = {X[3 * p], X[3 * p + 1], X[3 * p + 2]};
     const double Rp = Rr[p];
-    int base[3];
-    float cf[3];
-    for (int a = 0; a < 3; a++) {
-        base[a] = (a < D) ? (int)floor(Xp[a]) : 0;
-        cf[a] = (float)(Xp[a] - base[a]);
+    if (threadIdx.x == 0) {
+        int lo[3], hi[3];
+        footprint_box(G, D, Xp, Rp, lo, hi);
+        for (int a = 0; a < 3; a++) {
+            s_box[a] = lo[a];
+            s_box[3 + a] = hi[a];
+            s_base[a] = (a < D) ? (int)floor(Xp[a]) : 0;
+            s_cf[a] = (float)(Xp[a] - s_base[a]);
+            s_U[a] = (float)U[3 * p + a];
+            s_W[a] = (float)W[3 * p + a];
+        }
+        s_misc[0] = (float)(Tp[p] - Tref);
+        s_misc[1] = (float)(2.0 * kappa);
+        s_misc[2] = (float)Rp;
     }
     const int a0 = adj_start[p];
     int nnb = adj_start[p + 1] - a0;
     if (nnb > CP_MAXNB) nnb = CP_MAXNB;  // the neighbour build rejects more
+    __syncthreads();
+    const int base[3] = {s_base[0], s_base[1], s_base[2]};
+    const float cf[3] = {s_cf[0], s_cf[1], s_cf[2]};
     for (int k = threadIdx.x; k < nnb; k += blockDim.x) {
         int q = adj_nb[a0 + k];
         sh_id[k] = q;
@@ -141,15 +156,14 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
         sh_nbf[k][3] = (float)Rr[q];
     }
     __syncthreads();
-    int lo[3], hi[3];
-    footprint_box(G, D, Xp, Rp, lo, hi);
+    const int lo[3] = {s_box[0], s_box[1], s_box[2]}, hi[3] = {s_box[3], s_box[4], s_box[5]};
     int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
     long long cnt = (ex > 0 && ey > 0 && ez > 0) ? (long long)ex * ey * ez : 0;
-    const float Upf[3] = {(float)U[3 * p], (float)U[3 * p + 1], (float)U[3 * p + 2]};
-    const float Wpf[3] = {(float)W[3 * p], (float)W[3 * p + 1], (float)W[3 * p + 2]};
-    const R dTp = (R)(Tp[p] - Tref);
-    const R twok = (R)(2.0 * kappa);
-    const float Rpf = (float)Rp;
+    const float Upf[3] = {s_U[0], s_U[1], s_U[2]};
+    const float Wpf[3] = {s_W[0], s_W[1], s_W[2]};
+    const R dTp = (R)s_misc[0];
+    const R twok = (R)s_misc[1];
+    const float Rpf = s_misc[2];
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // per-thread partials; the block sum is FP64
     for (long long q = threadIdx.x; q < cnt; q += blockDim.x) {
         int x = lo[0] + (int)(q % ex), y = lo[1] + (int)((q / ex) % ey), z = lo[2] + (int)(q / ((long long)ex * ey));
@@ -193,7 +207,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
         for (int a = 0; a < 3; a++) M[a] = e * (R)2 * (rho * (R)Ul[a] - j[a]);  // eps F_f (Eqs lbm7, lbm8)
         M[3] = e * twok * (dTp - dT);                                             // eps Q (Eq lbm7.5)
         if (D == 2) M[2] = 0;
-        typename Vec4<S>::T mv;
+        typename Store<S>::V4 mv;
         mv.x = M[0], mv.y = M[1], mv.z = M[2], mv.w = M[3];
         mk[node_index(G, x, y, z)] = mv;
         // Eq lbm13 and the torque about the centre
@@ -235,27 +249,28 @@ __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __re
     V* tile = reinterpret_cast<V*>(sm_raw);
     using T = decltype(V().x);
     const int p = blockIdx.x;
-    const double Xp[3] = {X[3 * p], X[3 * p + 1], X[3 * p + 2]};
-    int lo[3], hi[3];
-    footprint_box(G, D, Xp, Rr[p], lo, hi);
-    int n[3] = {G.nx, G.ny, G.nz};
-    int ilo[3], ihi[3];  // staged input region
-    for (int a = 0; a < 3; a++) {
-        if (a < D) {
-            lo[a] = max(lo[a] - 1, 0);
-            hi[a] = min(hi[a] + 1, n[a] - 1);
-            ilo[a] = max(lo[a] - 1, 0);
-            ihi[a] = min(hi[a] + 1, n[a] - 1);
-        } else {
-            ilo[a] = ihi[a] = lo[a];
-        }
-    }
+    __shared__ int s_b[12];  // output box lo/hi, staged box lo/hi, computed once
     if (threadIdx.x == 0) {
+        const double Xp[3] = {X[3 * p], X[3 * p + 1], X[3 * p + 2]};
+        int lo[3], hi[3];
+        footprint_box(G, D, Xp, Rr[p], lo, hi);
+        int n[3] = {G.nx, G.ny, G.nz};
         for (int a = 0; a < 3; a++) {
+            int ilo = lo[a], ihi = hi[a];
+            if (a < D) {
+                lo[a] = max(lo[a] - 1, 0);
+                hi[a] = min(hi[a] + 1, n[a] - 1);
+                ilo = max(lo[a] - 1, 0);
+                ihi = min(hi[a] + 1, n[a] - 1);
+            }
+            s_b[a] = lo[a], s_b[3 + a] = hi[a], s_b[6 + a] = ilo, s_b[9 + a] = ihi;
             box[6 * p + a] = lo[a];
             box[6 * p + 3 + a] = hi[a];
         }
     }
+    __syncthreads();
+    const int lo[3] = {s_b[0], s_b[1], s_b[2]}, hi[3] = {s_b[3], s_b[4], s_b[5]};
+    const int ilo[3] = {s_b[6], s_b[7], s_b[8]}, ihi[3] = {s_b[9], s_b[10], s_b[11]};
     int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
     if (ex <= 0 || ey <= 0 || ez <= 0) return;
     const int sx = ihi[0] - ilo[0] + 1, sy = ihi[1] - ilo[1] + 1, sz = ihi[2] - ilo[2] + 1;
@@ -305,9 +320,9 @@ template <int D, typename S>
 __global__ void __launch_bounds__(CP_THREADS) k_markers(Geo G, const S* __restrict__ f, const S* __restrict__ g,
                                                         int nm, const double* __restrict__ MX, const double* __restrict__ MA,
                                                         const double* __restrict__ MT, double kappa, double Tref, int parity,
-                                                        typename Vec4<S>::T* Ml, double* nu_part) {
+                                                        typename Store<S>::V4* Ml, double* nu_part) {
     using L = Lat<D>;
-    using R = S;
+    using R = typename Store<S>::R;
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= nm) return;
     double Xl[3] = {MX[3 * l], MX[3 * l + 1], MX[3 * l + 2]};
@@ -352,7 +367,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_markers(Geo G, const S* __restri
     for (int k = 0; k < L::QG; k++) dT += gl[k];
     const R A = (R)MA[l];
     const R dTp = (R)(MT[l] - Tref) - dT;  // T_p - T_l
-    typename Vec4<S>::T mv;
+    typename Store<S>::V4 mv;
     mv.x = A * (R)(-2) * j[0];  // static marker: U_l = 0, F_f = -2 j
     mv.y = A * (R)(-2) * j[1];
     mv.z = D == 3 ? A * (R)(-2) * j[2] : (R)0;
@@ -396,7 +411,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_nu_reduce(const double* part, in
 
 template <int D, typename S>
 static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
-    using V = typename Vec4<S>::T;
+    using V = typename Store<S>::V4;
     if (!c->desc.pibm) return cudaSuccess;
     if (c->np > 0) {
         k_clear<V><<<c->np, CP_THREADS, 0, s>>>(c->G, c->box, (V*)c->mk, (V*)c->fb, c->flags);
@@ -418,11 +433,7 @@ static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_coupling(Ctx* c, cudaStream_t s, int parity) {
-    bool dbl = c->desc.storage == PIBM_STORE_F64;
-    if (c->D == 2) return dbl ? coupling_impl<2, double>(c, s, parity) : coupling_impl<2, float>(c, s, parity);
-    return dbl ? coupling_impl<3, double>(c, s, parity) : coupling_impl<3, float>(c, s, parity);
-}
+cudaError_t launch_coupling(Ctx* c, cudaStream_t s, int parity) { PIBM_DISPATCH(c, coupling_impl, c, s, parity); }
 
 int coupling_kernel_count(Ctx* c) {
     if (!c->desc.pibm) return 0;

@@ -126,55 +126,61 @@ __device__ __forceinline__ long long odd_dst(const Geo& G, long long n, int x, l
     return bounce ? (long long)L::opp(I) * G.N + n : (long long)I * G.N + n + off + dx;
 }
 
-template <int D, typename R, int I>
+template <int D, typename S, int I>
 struct OddLoad {
-    static __device__ __forceinline__ void run(const Geo& G, const CollideParams<R>& P, const R* f, const R* g, long long n,
+    using R = typename Store<S>::R;
+    static __device__ __forceinline__ void run(const Geo& G, const CollideParams<R>& P, const S* f, const S* g, long long n,
                                                int x, long long sy, long long sz, R* s, R* sg) {
         using L = Lat<D>;
         bool b;
         long long idx = odd_src<D, I>(G, n, x, sy, sz, b);
-        s[I] = f[idx];
+        s[I] = Store<S>::ldf(f[idx]);
         if (I < L::QG) {
-            R v = g[idx];
+            R v = Store<S>::ldg(g[idx]);
             constexpr int face = L::ex(I) > 0 ? 0 : 1;  // face crossed by x - e_I
             if (b && face_iso(G, face)) v = P.abb[face] - v;
             sg[I < L::QG ? I : 0] = v;
         }
-        OddLoad<D, R, I + 1>::run(G, P, f, g, n, x, sy, sz, s, sg);
+        OddLoad<D, S, I + 1>::run(G, P, f, g, n, x, sy, sz, s, sg);
     }
 };
-template <typename R> struct OddLoad<2, R, 9> {
-    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, const R*, const R*, long long, int,
+template <typename S> struct OddLoad<2, S, 9> {
+    using R = typename Store<S>::R;
+    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, const S*, const S*, long long, int,
                                                long long, long long, R*, R*) {}
 };
-template <typename R> struct OddLoad<3, R, 19> {
-    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, const R*, const R*, long long, int,
+template <typename S> struct OddLoad<3, S, 19> {
+    using R = typename Store<S>::R;
+    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, const S*, const S*, long long, int,
                                                long long, long long, R*, R*) {}
 };
 
-template <int D, typename R, int I>
+template <int D, typename S, int I>
 struct OddStore {
-    static __device__ __forceinline__ void run(const Geo& G, const CollideParams<R>& P, R* f, R* g, long long n, int x,
+    using R = typename Store<S>::R;
+    static __device__ __forceinline__ void run(const Geo& G, const CollideParams<R>& P, S* f, S* g, long long n, int x,
                                                long long sy, long long sz, const R* s, const R* sg) {
         using L = Lat<D>;
         bool b;
         long long idx = odd_dst<D, I>(G, n, x, sy, sz, b);
-        f[idx] = s[I];
+        f[idx] = Store<S>::stf(s[I]);
         if (I < L::QG) {
             R v = sg[I < L::QG ? I : 0];
             constexpr int face = L::ex(I) > 0 ? 1 : 0;  // face crossed by x + e_I
             if (b && face_iso(G, face)) v = P.abb[face] - v;
-            g[idx] = v;
+            g[idx] = Store<S>::stg(v);
         }
-        OddStore<D, R, I + 1>::run(G, P, f, g, n, x, sy, sz, s, sg);
+        OddStore<D, S, I + 1>::run(G, P, f, g, n, x, sy, sz, s, sg);
     }
 };
-template <typename R> struct OddStore<2, R, 9> {
-    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, R*, R*, long long, int, long long,
+template <typename S> struct OddStore<2, S, 9> {
+    using R = typename Store<S>::R;
+    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, S*, S*, long long, int, long long,
                                                long long, const R*, const R*) {}
 };
-template <typename R> struct OddStore<3, R, 19> {
-    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, R*, R*, long long, int, long long,
+template <typename S> struct OddStore<3, S, 19> {
+    using R = typename Store<S>::R;
+    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, S*, S*, long long, int, long long,
                                                long long, const R*, const R*) {}
 };
 
@@ -188,11 +194,11 @@ struct AAOffsets {
 
 template <int D, typename S, int PARITY>
 __global__ void __launch_bounds__(256) k_stream_collide(Geo G, S* __restrict__ f, S* __restrict__ g,
-                                                        const typename Vec4<S>::T* __restrict__ fb,
-                                                        const uint8_t* __restrict__ flags, CollideParams<S> P,
-                                                        AAOffsets O) {
+                                                        const typename Store<S>::V4* __restrict__ fb,
+                                                        const uint8_t* __restrict__ flags,
+                                                        CollideParams<typename Store<S>::R> P, AAOffsets O) {
     using L = Lat<D>;
-    using R = S;
+    using R = typename Store<S>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= G.nx) return;
@@ -205,22 +211,22 @@ __global__ void __launch_bounds__(256) k_stream_collide(Geo G, S* __restrict__ f
     const bool xedge = x == 0 || x == G.nx - 1;
     if (PARITY == 0) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) s[i] = f[n + O.ld[i]];
+        for (int i = 0; i < L::Q; i++) s[i] = Store<S>::ldf(f[n + O.ld[i]]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) sg[k] = g[n + O.ld[k]];
+        for (int k = 0; k < L::QG; k++) sg[k] = Store<S>::ldg(g[n + O.ld[k]]);
     } else if (inner_yz && !xedge) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) s[i] = f[n + O.src[i]];
+        for (int i = 0; i < L::Q; i++) s[i] = Store<S>::ldf(f[n + O.src[i]]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) sg[k] = g[n + O.src[k]];
+        for (int k = 0; k < L::QG; k++) sg[k] = Store<S>::ldg(g[n + O.src[k]]);
     } else if (inner_yz) {
-        OddLoad<D, R, 0>::run(G, P, f, g, n, x, sy, sz, s, sg);
+        OddLoad<D, S, 0>::run(G, P, f, g, n, x, sy, sz, s, sg);
     } else {
         load_node<D, S, R>(G, f, g, x, y, z, 1, s, sg);
     }
     R fbx = 0, fby = 0, fbz = 0, qb = 0;
     if (flags[((long long)z * G.ny + y) * G.ntx + (x >> 5)]) {
-        const typename Vec4<S>::T v = fb[n];
+        const typename Store<S>::V4 v = fb[n];
         fbx = v.x;
         fby = v.y;
         fbz = v.z;
@@ -229,30 +235,30 @@ __global__ void __launch_bounds__(256) k_stream_collide(Geo G, S* __restrict__ f
     collide_node<D, R>(s, sg, fbx, fby, fbz, qb, P);
     if (PARITY == 0) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) f[n + O.st[i]] = s[i];
+        for (int i = 0; i < L::Q; i++) f[n + O.st[i]] = Store<S>::stf(s[i]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) g[n + O.st[k]] = sg[k];
+        for (int k = 0; k < L::QG; k++) g[n + O.st[k]] = Store<S>::stg(sg[k]);
     } else if (inner_yz && !xedge) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) f[n + O.dst[i]] = s[i];
+        for (int i = 0; i < L::Q; i++) f[n + O.dst[i]] = Store<S>::stf(s[i]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) g[n + O.dst[k]] = sg[k];
+        for (int k = 0; k < L::QG; k++) g[n + O.dst[k]] = Store<S>::stg(sg[k]);
     } else if (inner_yz) {
-        OddStore<D, R, 0>::run(G, P, f, g, n, x, sy, sz, s, sg);
+        OddStore<D, S, 0>::run(G, P, f, g, n, x, sy, sz, s, sg);
     } else {
 #pragma unroll
         for (int i = 0; i < L::Q; i++) {
             long long idx;
             post_slot(G, x, y, z, L::ex(i), L::ey(i), L::ez(i), i, L::opp(i), 1, idx);
-            f[idx] = s[i];
+            f[idx] = Store<S>::stf(s[i]);
         }
 #pragma unroll
         for (int k = 0; k < L::QG; k++) {
             long long idx;
             int face = post_slot(G, x, y, z, L::ex(k), L::ey(k), L::ez(k), k, L::opp(k), 1, idx);
             R v = sg[k];
-            if (face_iso(G, face)) v = (R)(2.0 * L::wg(k) * face_dTw(G, face)) - v;
-            g[idx] = v;
+            if (face_iso(G, face)) v = P.abb[face] - v;
+            g[idx] = Store<S>::stg(v);
         }
     }
 }
@@ -294,9 +300,10 @@ template <int D, typename S>
 static cudaError_t sc_launch(Ctx* c, cudaStream_t s, int parity) {
     dim3 block(256), grid((c->G.nx + 255) / 256, c->G.ny, c->G.nz);
     if (c->G.nx <= 128) block.x = 128, grid.x = (c->G.nx + 127) / 128;
-    CollideParams<S> P = collide_params<S>(c);
+    using R = typename Store<S>::R;
+    CollideParams<R> P = collide_params<R>(c);
     AAOffsets O = aa_offsets<D>(c->G);
-    using V = typename Vec4<S>::T;
+    using V = typename Store<S>::V4;
     if (parity == 0)
         k_stream_collide<D, S, 0><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb, c->flags, P, O);
     else
@@ -304,37 +311,31 @@ static cudaError_t sc_launch(Ctx* c, cudaStream_t s, int parity) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_stream_collide(Ctx* c, cudaStream_t s, int parity) {
-    bool dbl = c->desc.storage == PIBM_STORE_F64;
-    if (c->D == 2) return dbl ? sc_launch<2, double>(c, s, parity) : sc_launch<2, float>(c, s, parity);
-    return dbl ? sc_launch<3, double>(c, s, parity) : sc_launch<3, float>(c, s, parity);
-}
+cudaError_t launch_stream_collide(Ctx* c, cudaStream_t s, int parity) { PIBM_DISPATCH(c, sc_launch, c, s, parity); }
 
 // ----------------------------------------------------------- initialisation
 // Rest equilibrium at density 1 and temperature T_init: s_i = 0, s_gk = w_k (T_init - T_ref).
 template <int D, typename S>
 __global__ void k_init(long long N, S* f, S* g, double dT0) {
     using L = Lat<D>;
+    using R = typename Store<S>::R;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) f[i * N + n] = (S)0;
+        for (int i = 0; i < L::Q; i++) f[i * N + n] = Store<S>::stf((R)0);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) g[k * N + n] = (S)(L::wg(k) * dT0);
+        for (int k = 0; k < L::QG; k++) g[k * N + n] = Store<S>::stg((R)(L::wg(k) * dT0));
     }
+}
+
+template <int D, typename S>
+static cudaError_t init_launch(Ctx* c, double dT0) {
+    k_init<D, S><<<1024, 256, 0, c->s0>>>(c->G.N, (S*)c->f, (S*)c->g, dT0);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init_equilibrium(Ctx* c) {
     double dT0 = c->desc.T_init - c->desc.T_ref;
-    int grid = 1024;
-    bool dbl = c->desc.storage == PIBM_STORE_F64;
-    if (c->D == 2) {
-        if (dbl) k_init<2, double><<<grid, 256, 0, c->s0>>>(c->G.N, (double*)c->f, (double*)c->g, dT0);
-        else k_init<2, float><<<grid, 256, 0, c->s0>>>(c->G.N, (float*)c->f, (float*)c->g, dT0);
-    } else {
-        if (dbl) k_init<3, double><<<grid, 256, 0, c->s0>>>(c->G.N, (double*)c->f, (double*)c->g, dT0);
-        else k_init<3, float><<<grid, 256, 0, c->s0>>>(c->G.N, (float*)c->f, (float*)c->g, dT0);
-    }
-    return cudaGetLastError();
+    PIBM_DISPATCH(c, init_launch, c, dT0);
 }
 
 // ------------------------------------------------- population read / write
@@ -352,7 +353,7 @@ __global__ void k_read_plane(Geo G, const S* __restrict__ arr, int thermal, int 
             if (i == q) { ex = L::ex(i); ey = L::ey(i); ez = L::ez(i); io = L::opp(i); w = thermal ? L::wg(i) : L::w(i); }
         long long idx;
         int face = pop_slot(G, x, y, z, ex, ey, ez, q, io, parity, idx);
-        double v = (double)arr[idx];
+        double v = thermal ? (double)Store<S>::ldg(arr[idx]) : (double)Store<S>::ldf(arr[idx]);
         if (thermal && face_iso(G, face)) v = 2.0 * w * face_dTw(G, face) - v;
         out[n] = v + (thermal ? w * Tref : w);
     }
@@ -373,7 +374,8 @@ __global__ void k_write_plane(Geo G, S* __restrict__ arr, int thermal, int q, in
         int face = pop_slot(G, x, y, z, ex, ey, ez, q, io, parity, idx);
         double v = in[n] - (thermal ? w * Tref : w);
         if (thermal && face_iso(G, face)) v = 2.0 * w * face_dTw(G, face) - v;
-        arr[idx] = (S)v;
+        using R = typename Store<S>::R;
+        arr[idx] = thermal ? Store<S>::stg((R)v) : Store<S>::stf((R)v);
     }
 }
 
@@ -387,21 +389,13 @@ static cudaError_t rw_plane(Ctx* c, int which, int q, int parity, bool write) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_read_plane(Ctx* c, int which, int q, int parity) {
-    bool dbl = c->desc.storage == PIBM_STORE_F64;
-    if (c->D == 2) return dbl ? rw_plane<2, double>(c, which, q, parity, false) : rw_plane<2, float>(c, which, q, parity, false);
-    return dbl ? rw_plane<3, double>(c, which, q, parity, false) : rw_plane<3, float>(c, which, q, parity, false);
-}
+cudaError_t launch_read_plane(Ctx* c, int which, int q, int parity) { PIBM_DISPATCH(c, rw_plane, c, which, q, parity, false); }
 
-cudaError_t launch_write_plane(Ctx* c, int which, int q, int parity) {
-    bool dbl = c->desc.storage == PIBM_STORE_F64;
-    if (c->D == 2) return dbl ? rw_plane<2, double>(c, which, q, parity, true) : rw_plane<2, float>(c, which, q, parity, true);
-    return dbl ? rw_plane<3, double>(c, which, q, parity, true) : rw_plane<3, float>(c, which, q, parity, true);
-}
+cudaError_t launch_write_plane(Ctx* c, int which, int q, int parity) { PIBM_DISPATCH(c, rw_plane, c, which, q, parity, true); }
 
 // ------------------------------------------------------ macroscopic fields
 template <int D, typename S>
-__device__ void node_macro(const Geo& G, const S* f, const S* g, const typename Vec4<S>::T* fb, const uint8_t* flags,
+__device__ void node_macro(const Geo& G, const S* f, const S* g, const typename Store<S>::V4* fb, const uint8_t* flags,
                            const CollideParams<double>& P, int x, int y, int z, int parity, double* out /*rho,ux,uy,uz,T,fbx,fby,fbz,qb,T0*/) {
     using L = Lat<D>;
     double s[L::Q], sg[L::QG];
@@ -409,7 +403,7 @@ __device__ void node_macro(const Geo& G, const S* f, const S* g, const typename 
     long long n = node_index(G, x, y, z);
     double fbv[4] = {0, 0, 0, 0};
     if (flags[((long long)z * G.ny + y) * G.ntx + (x >> 5)]) {
-        typename Vec4<S>::T v = fb[n];
+        typename Store<S>::V4 v = fb[n];
         fbv[0] = v.x, fbv[1] = v.y, fbv[2] = v.z, fbv[3] = v.w;
     }
     double drho = 0, j[3] = {0, 0, 0}, dT = 0;
@@ -433,7 +427,7 @@ __device__ void node_macro(const Geo& G, const S* f, const S* g, const typename 
 }
 
 template <int D, typename S>
-__global__ void k_macro(Geo G, const S* f, const S* g, const typename Vec4<S>::T* fb, const uint8_t* flags,
+__global__ void k_macro(Geo G, const S* f, const S* g, const typename Store<S>::V4* fb, const uint8_t* flags,
                         CollideParams<double> P, int field, int parity, double* out) {
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < G.N; n += (long long)gridDim.x * blockDim.x) {
         int x = (int)(n % G.nx), y = (int)((n / G.nx) % G.ny), z = (int)(n / ((long long)G.nx * G.ny));
@@ -445,17 +439,13 @@ __global__ void k_macro(Geo G, const S* f, const S* g, const typename Vec4<S>::T
 
 template <int D, typename S>
 static cudaError_t macro_launch(Ctx* c, int field, int parity) {
-    using V = typename Vec4<S>::T;
+    using V = typename Store<S>::V4;
     k_macro<D, S><<<1024, 256, 0, c->s0>>>(c->G, (const S*)c->f, (const S*)c->g, (const V*)c->fb, c->flags,
                                            collide_params<double>(c), field, parity, c->plane);
     return cudaGetLastError();
 }
 
-cudaError_t launch_macro(Ctx* c, int field, int parity) {
-    bool dbl = c->desc.storage == PIBM_STORE_F64;
-    if (c->D == 2) return dbl ? macro_launch<2, double>(c, field, parity) : macro_launch<2, float>(c, field, parity);
-    return dbl ? macro_launch<3, double>(c, field, parity) : macro_launch<3, float>(c, field, parity);
-}
+cudaError_t launch_macro(Ctx* c, int field, int parity) { PIBM_DISPATCH(c, macro_launch, c, field, parity); }
 
 // ------------------------------------------------------------ diagnostics
 // Deterministic two-level reduction: a fixed grid of 512 blocks writes
@@ -463,7 +453,7 @@ cudaError_t launch_macro(Ctx* c, int field, int parity) {
 constexpr int DIAG_BLOCKS = 512;
 
 template <int D, typename S>
-__global__ void __launch_bounds__(256) k_diag_lattice(Geo G, const S* f, const S* g, const typename Vec4<S>::T* fb,
+__global__ void __launch_bounds__(256) k_diag_lattice(Geo G, const S* f, const S* g, const typename Store<S>::V4* fb,
                                                       const uint8_t* flags, CollideParams<double> P, int parity, double* part) {
     __shared__ double sh[4][256];
     double mass = 0, heat = 0, umax = 0, bad = 0;
@@ -533,7 +523,7 @@ __global__ void __launch_bounds__(256) k_diag_final(const double* part, int nblo
 
 template <int D, typename S>
 static cudaError_t diag_launch(Ctx* c, int parity) {
-    using V = typename Vec4<S>::T;
+    using V = typename Store<S>::V4;
     k_diag_lattice<D, S><<<DIAG_BLOCKS, 256, 0, c->s0>>>(c->G, (const S*)c->f, (const S*)c->g, (const V*)c->fb,
                                                          c->flags, collide_params<double>(c), parity, c->red);
     k_diag_final<<<1, 256, 0, c->s0>>>(c->red, DIAG_BLOCKS, c->U, c->W, c->X, c->m, c->I, c->np,
@@ -541,10 +531,6 @@ static cudaError_t diag_launch(Ctx* c, int parity) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_diagnostics(Ctx* c, int parity) {
-    bool dbl = c->desc.storage == PIBM_STORE_F64;
-    if (c->D == 2) return dbl ? diag_launch<2, double>(c, parity) : diag_launch<2, float>(c, parity);
-    return dbl ? diag_launch<3, double>(c, parity) : diag_launch<3, float>(c, parity);
-}
+cudaError_t launch_diagnostics(Ctx* c, int parity) { PIBM_DISPATCH(c, diag_launch, c, parity); }
 
 }  // namespace pibm

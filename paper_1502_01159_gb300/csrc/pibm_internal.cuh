@@ -3,6 +3,8 @@
 // f and g, the context structure and the launch wrappers of each kernel file.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -46,6 +48,52 @@ template <> struct Lat<3> {
 template <typename S> struct Vec4;
 template <> struct Vec4<float> { using T = float4; };
 template <> struct Vec4<double> { using T = double4_32a; };
+
+// Population storage: the type S kept in HBM, the arithmetic type R, the
+// per-node force / heat-source field type V4, and the conversions.  FP32 and
+// FP64 store the deviations as they are.  FP16 stores them scaled by a power
+// of two (exact), so that deviations of order 1e-4 .. 1e-1 sit in the normal
+// FP16 range (flow x 1024, thermal x 256); BF16 keeps FP32's exponent range
+// and needs no scale.  All collision arithmetic is in R = FP32 for both.
+template <typename S> struct Store {
+    using R = S;
+    using V4 = typename Vec4<S>::T;
+    static __host__ __device__ __forceinline__ R ldf(S v) { return v; }
+    static __host__ __device__ __forceinline__ R ldg(S v) { return v; }
+    static __host__ __device__ __forceinline__ S stf(R v) { return v; }
+    static __host__ __device__ __forceinline__ S stg(R v) { return v; }
+};
+template <> struct Store<__half> {
+    using R = float;
+    using V4 = float4;
+    static __device__ __forceinline__ float ldf(__half v) { return __half2float(v) * 0.0009765625f; }
+    static __device__ __forceinline__ float ldg(__half v) { return __half2float(v) * 0.00390625f; }
+    static __device__ __forceinline__ __half stf(float v) { return __float2half_rn(v * 1024.0f); }
+    static __device__ __forceinline__ __half stg(float v) { return __float2half_rn(v * 256.0f); }
+};
+template <> struct Store<__nv_bfloat16> {
+    using R = float;
+    using V4 = float4;
+    static __device__ __forceinline__ float ldf(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ float ldg(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 stf(float v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ __nv_bfloat16 stg(float v) { return __float2bfloat16_rn(v); }
+};
+
+// Run FN<D, S>(args...) for the context's dimension and storage type.
+#define PIBM_DISPATCH(c, FN, ...)                                                                       \
+    do {                                                                                                \
+        switch ((c)->desc.storage) {                                                                    \
+            case PIBM_STORE_F64:                                                                        \
+                return (c)->D == 2 ? FN<2, double>(__VA_ARGS__) : FN<3, double>(__VA_ARGS__);           \
+            case PIBM_STORE_F16:                                                                        \
+                return (c)->D == 2 ? FN<2, __half>(__VA_ARGS__) : FN<3, __half>(__VA_ARGS__);           \
+            case PIBM_STORE_BF16:                                                                       \
+                return (c)->D == 2 ? FN<2, __nv_bfloat16>(__VA_ARGS__) : FN<3, __nv_bfloat16>(__VA_ARGS__); \
+            default:                                                                                    \
+                return (c)->D == 2 ? FN<2, float>(__VA_ARGS__) : FN<3, float>(__VA_ARGS__);             \
+        }                                                                                               \
+    } while (0)
 
 // ------------------------------------------------------------ lattice state
 // Geometry and boundary data every lattice kernel needs (passed by value).
@@ -142,13 +190,13 @@ __device__ __forceinline__ void load_node(const Geo& G, const S* __restrict__ f,
     for (int i = 0; i < L::Q; i++) {
         long long idx;
         pop_slot(G, x, y, z, L::ex(i), L::ey(i), L::ez(i), i, L::opp(i), parity, idx);
-        s[i] = (R)f[idx];
+        s[i] = (R)Store<S>::ldf(f[idx]);
     }
 #pragma unroll
     for (int k = 0; k < L::QG; k++) {
         long long idx;
         int face = pop_slot(G, x, y, z, L::ex(k), L::ey(k), L::ez(k), k, L::opp(k), parity, idx);
-        R v = (R)g[idx];
+        R v = (R)Store<S>::ldg(g[idx]);
         if (face_iso(G, face)) v = (R)(2.0 * L::wg(k) * face_dTw(G, face)) - v;
         sg[k] = v;
     }
@@ -184,6 +232,7 @@ struct Ctx {
     double nu, alpha, tau_f, tau_g, buoy;
     long long t;
     size_t es;  // bytes per stored population element
+    size_t v4;  // bytes per node of the F_B / Q_B and marker fields
 
     cudaStream_t s0;  // caller's stream
     cudaStream_t s1;  // internal stream for the DEM branch

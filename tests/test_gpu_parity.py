@@ -266,3 +266,29 @@ def test_footprint_ownership_ties(dim):
         scale = np.abs(Fo[key]).max()
         assert np.max(np.abs(Fs[key] - Fo[key])) < 1e-5 * scale, key
     assert rel_l2(sim.read_field("FBx"), orc.field("FBx")) < 1e-5
+
+
+# Reduced-precision storage (FP16 / BF16 deviations, FP32 arithmetic): the
+# error against the FP64 oracle is stated per field, not held to the FP32 bar.
+REDUCED_BOUNDS = {"f16": {"rho": 1e-6, "T": 2e-4, "u": 5e-3, "X": 1e-4},
+                  "bf16": {"rho": 1e-5, "T": 5e-3, "u": 5e-2, "X": 1e-3}}
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("which", ["2d", "3d"])
+def test_reduced_precision_storage(storage, which):
+    case = _small_sed2d() if which == "2d" else _small_sed3d()
+    case["storage"] = storage
+    sim, orc = _sim(case), oracle.Oracle(case)
+    sim.step(100)
+    orc.step(100)
+    dim = case["dim"]
+    comps = ("ux", "uy") + (("uz",) if dim == 3 else ())
+    errs = {"rho": rel_l2(sim.read_field("rho"), orc.field("rho")),
+            "T": rel_l2(sim.read_field("T"), orc.field("T")),
+            "u": rel_l2(np.stack([sim.read_field(c) for c in comps]), np.stack([orc.field(c) for c in comps])),
+            "X": float(np.max(np.abs(sim.read_particles()["X"] - orc.particles()["X"])))}
+    print(storage, which, errs)
+    for k, v in errs.items():
+        assert v < REDUCED_BOUNDS[storage][k], (k, v, errs)
+    assert sim.diagnostics()["nonfinite"] == 0
