@@ -131,6 +131,20 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """Slowest rank's value (the job finishes when the last replica does)."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: float, ms_step: float) -> float:
+    """Whole-job throughput in millions of units per second: every rank runs an
+    independent replica of the same workload."""
+    return world * units_per_rank / (ms_step * 1e-3) / 1e6
+
+
 def oracle_run(case, steps, warmup):
     import oracle
     o = oracle.Oracle(case)
@@ -323,11 +337,9 @@ def run_ours(args):
     clocks = sampler.stop()
     ms_step = statistics.mean(ms)
     if world > 1:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+        ms_step = max_over_ranks(ms_step, dist, "cuda")
         dist.barrier()
-    value = world * nodes / (ms_step * 1e-3) / 1e6
+    value = job_throughput(world, nodes, ms_step)
     kps = sim.kernels_per_step()
 
     kt = kernel_times(sim, max(5, args.steps // 2), torch, flush)

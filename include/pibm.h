@@ -188,6 +188,15 @@ pibm_status pibm_relaxation(pibm_ctx* ctx, double* out);
 /* Current lattice time (number of steps taken). */
 pibm_status pibm_time(pibm_ctx* ctx, int64_t* t);
 
+/* Checkpoint: every device buffer that carries state between steps (f, g,
+ * coupling fields, particles, contact histories, neighbour lists, markers)
+ * and the time, written to a file.  pibm_load restores it into a context
+ * created with the same description, walls and contact law, and with the
+ * same number of particles or markers already set; stepping then continues
+ * bit-exactly as the saved run would have.  Both synchronise the stream. */
+pibm_status pibm_save(pibm_ctx* ctx, const char* path);
+pibm_status pibm_load(pibm_ctx* ctx, const char* path);
+
 /* One lattice step launched without a graph, with CUDA events around each
  * kernel group on the stream it runs on.  ms[0] collide-and-stream, ms[1] DEM,
  * ms[2] PIBM coupling, ms[3] the whole step (fork to join).  Synchronises. */

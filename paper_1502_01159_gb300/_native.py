@@ -66,6 +66,8 @@ SIGNATURES = {
     "pibm_kernels_per_step": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "pibm_step_timed": (C.c_int, [_P, _D]),
     "pibm_set_tuning": (C.c_int, [_P, C.c_int, C.c_int]),
+    "pibm_save": (C.c_int, [_P, C.c_char_p]),
+    "pibm_load": (C.c_int, [_P, C.c_char_p]),
     "pibm_contacts_static": (C.c_int, [_P, _P, C.c_int, C.c_int, _I32, C.c_double, _P, C.c_int, _P, _P]),
     "pibm_status_string": (C.c_char_p, [C.c_int]),
     "pibm_last_error": (C.c_int, [_P, C.c_char_p, C.c_size_t]),
@@ -315,6 +317,12 @@ class Simulation:
         v = C.c_int64()
         self._check(self.L.pibm_time(self.h, C.byref(v)), "pibm_time")
         return v.value
+
+    def save(self, path: str):
+        self._check(self.L.pibm_save(self.h, str(path).encode()), "pibm_save")
+
+    def load(self, path: str):
+        self._check(self.L.pibm_load(self.h, str(path).encode()), "pibm_load")
 
     def set_tuning(self, knob: int, value: int):
         self._check(self.L.pibm_set_tuning(self.h, knob, value), "pibm_set_tuning")

@@ -781,6 +781,129 @@ pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value) {
     return PIBM_OK;
 }
 
+// ------------------------------------------------------------- checkpoints
+// Every device buffer that carries state between steps, by name and size.
+struct BufRef {
+    const char* name;
+    void* ptr;
+    size_t bytes;
+};
+
+static std::vector<BufRef> state_buffers(Ctx& c) {
+    std::vector<BufRef> v;
+    long long N = c.G.N;
+    v.push_back({"f", c.f, (size_t)c.Q * N * c.es});
+    v.push_back({"g", c.g, (size_t)c.QG * N * c.es});
+    v.push_back({"fb", c.fb, (size_t)N * c.v4});
+    v.push_back({"mk", c.mk, (size_t)N * c.v4});
+    v.push_back({"flags", c.flags, (size_t)c.G.ntx * c.G.ny * c.G.nz});
+    v.push_back({"nu_val", c.nu_val, sizeof(double) * 2});
+    v.push_back({"nb_cur", c.nb_cur, sizeof(int) * 2});
+    int n = c.np;
+    if (n > 0) {
+        size_t v3 = sizeof(double) * 3 * n, v1 = sizeof(double) * n;
+        BufRef pv[] = {{"X", c.X, v3}, {"U", c.U, v3}, {"W", c.W, v3}, {"Xb", c.Xb, v3}, {"R", c.R, v1},
+                       {"rho", c.rho, v1}, {"Tp", c.Tp, v1}, {"Cp", c.Cp, v1}, {"m", c.m, v1}, {"I", c.I, v1},
+                       {"mg", c.mg, v1}, {"fixed", c.fixed, (size_t)n}, {"Fh", c.Fh, v3}, {"Th", c.Th, v3},
+                       {"Hh", c.Hh, v1}, {"Fc", c.Fc, v3}, {"Tc", c.Tc, v3}, {"Fh_prev", c.Fh_prev, v3},
+                       {"Th_prev", c.Th_prev, v3}, {"Hh_prev", c.Hh_prev, v1}, {"have_prev", c.have_prev, sizeof(int)},
+                       {"box", c.box, sizeof(int) * 6 * n}, {"wall_ft", c.wall_ft, sizeof(float) * 18 * n},
+                       {"nb_start0", c.nb_start[0], sizeof(int) * (n + 1)}, {"nb_start1", c.nb_start[1], sizeof(int) * (n + 1)},
+                       {"nb_i0", c.nb_i[0], sizeof(int) * c.dem.cap}, {"nb_i1", c.nb_i[1], sizeof(int) * c.dem.cap},
+                       {"nb_j0", c.nb_j[0], sizeof(int) * c.dem.cap}, {"nb_j1", c.nb_j[1], sizeof(int) * c.dem.cap},
+                       {"nb_ft0", c.nb_ft[0], sizeof(float4) * 2 * c.dem.cap}, {"nb_ft1", c.nb_ft[1], sizeof(float4) * 2 * c.dem.cap},
+                       {"adj_start", c.adj_start, sizeof(int) * (n + 1)}, {"adj_nb", c.adj_nb, sizeof(int) * c.adj_cap},
+                       {"adj_k", c.adj_k, sizeof(int) * c.adj_cap}};
+        for (auto& b : pv) v.push_back(b);
+    }
+    if (c.nm > 0) {
+        v.push_back({"Ml", c.Ml, (size_t)c.nm * c.v4});
+        v.push_back({"nu_part", c.nu_part, sizeof(double) * c.nm});
+    }
+    return v;
+}
+
+struct CkptHeader {
+    char magic[8];
+    int version, dim, nx, ny, nz, storage, np, nm, nbuf;
+    long long t;
+};
+
+pibm_status pibm_save(pibm_ctx* ctx, const char* path) {
+    if (!ctx || !path) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    pibm_status st = device_status(ctx);
+    if (st != PIBM_OK) return st;
+    FILE* fp = fopen(path, "wb");
+    if (!fp) return fail(ctx, PIBM_ERR_ARG, std::string("cannot open ") + path);
+    std::vector<BufRef> bufs = state_buffers(c);
+    CkptHeader h;
+    memcpy(h.magic, "PIBMCKP", 8);
+    h.version = 1, h.dim = c.D, h.nx = c.G.nx, h.ny = c.G.ny, h.nz = c.G.nz, h.storage = c.desc.storage;
+    h.np = c.np, h.nm = c.nm, h.nbuf = (int)bufs.size(), h.t = c.t;
+    bool ok = fwrite(&h, sizeof(h), 1, fp) == 1;
+    std::vector<char> host;
+    for (auto& b : bufs) {
+        char name[16] = {0};
+        strncpy(name, b.name, 15);
+        unsigned long long bytes = b.bytes;
+        host.resize(b.bytes);
+        if (cudaMemcpy(host.data(), b.ptr, b.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) ok = false;
+        ok = ok && fwrite(name, 16, 1, fp) == 1 && fwrite(&bytes, sizeof(bytes), 1, fp) == 1 &&
+             (b.bytes == 0 || fwrite(host.data(), b.bytes, 1, fp) == 1);
+    }
+    ok = (fclose(fp) == 0) && ok;
+    return ok ? PIBM_OK : fail(ctx, PIBM_ERR_CUDA, std::string("checkpoint write failed: ") + path);
+}
+
+pibm_status pibm_load(pibm_ctx* ctx, const char* path) {
+    if (!ctx || !path) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return fail(ctx, PIBM_ERR_ARG, std::string("cannot open ") + path);
+    CkptHeader h;
+    if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, "PIBMCKP", 8) != 0 || h.version != 1) {
+        fclose(fp);
+        return fail(ctx, PIBM_ERR_ARG, "not a checkpoint of this library");
+    }
+    if (h.dim != c.D || h.nx != c.G.nx || h.ny != c.G.ny || h.nz != c.G.nz || h.storage != c.desc.storage ||
+        h.np != c.np || h.nm != c.nm) {
+        fclose(fp);
+        return fail(ctx, PIBM_ERR_STATE, "checkpoint does not match this context (lattice, storage, particle or marker count)");
+    }
+    std::vector<BufRef> bufs = state_buffers(c);
+    std::vector<char> host;
+    pibm_status st = PIBM_OK;
+    for (int k = 0; k < h.nbuf && st == PIBM_OK; k++) {
+        char name[16];
+        unsigned long long bytes = 0;
+        if (fread(name, 16, 1, fp) != 1 || fread(&bytes, sizeof(bytes), 1, fp) != 1) {
+            st = fail(ctx, PIBM_ERR_ARG, "truncated checkpoint");
+            break;
+        }
+        name[15] = 0;
+        BufRef* dst = nullptr;
+        for (auto& b : bufs)
+            if (strcmp(b.name, name) == 0) dst = &b;
+        if (!dst || dst->bytes != bytes) {
+            st = fail(ctx, PIBM_ERR_STATE, std::string("checkpoint buffer does not match: ") + name);
+            break;
+        }
+        host.resize(bytes);
+        if (bytes && fread(host.data(), bytes, 1, fp) != 1) {
+            st = fail(ctx, PIBM_ERR_ARG, "truncated checkpoint");
+            break;
+        }
+        if (bytes && cudaMemcpy(dst->ptr, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+            st = fail(ctx, PIBM_ERR_CUDA, "checkpoint upload failed");
+    }
+    fclose(fp);
+    if (st != PIBM_OK) return st;
+    c.t = h.t;
+    drop_graphs(c);
+    return device_status(ctx);
+}
+
 pibm_status pibm_kernels_per_step(pibm_ctx* ctx, int* n) {
     if (!ctx || !n) return PIBM_ERR_ARG;
     Ctx& c = ctx->c;
