@@ -204,8 +204,11 @@ pibm_status pibm_step_timed(pibm_ctx* ctx, double* ms);
 
 /* Launch-shape tuning (used by autotuning sweeps; results do not depend on it).
  * PIBM_TUNE_DEM_PARTICLES_PER_CTA: particles per CTA of the DEM cluster
- * (0 = default 32; at most 16 CTAs and 640 particles per CTA). */
-enum { PIBM_TUNE_DEM_PARTICLES_PER_CTA = 0 };
+ * (0 = default 32; at most 16 CTAs and 640 particles per CTA).
+ * PIBM_TUNE_SCALAR_LATTICE: 1 = one node per thread also for FP16 / BF16
+ * storage (default 0: two nodes per thread with 32-bit accesses when nx is a
+ * multiple of 64). */
+enum { PIBM_TUNE_DEM_PARTICLES_PER_CTA = 0, PIBM_TUNE_SCALAR_LATTICE = 1 };
 pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value);
 
 /* Number of kernels one lattice step launches (for launch accounting). */

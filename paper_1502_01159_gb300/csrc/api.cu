@@ -120,6 +120,8 @@ static void update_geo(Ctx& c) {
         int n = a == 0 ? c.G.nx : (a == 1 ? c.G.ny : c.G.nz);
         c.dem.lo[a] = -0.5;
         c.dem.hi[a] = n - 0.5;
+        c.dem.lof[a] = -0.5f;
+        c.dem.hif[a] = (float)(n - 0.5);
     }
 }
 
@@ -128,6 +130,7 @@ static int parity(const Ctx& c) { return (int)(c.t & 1); }
 // Coupling of the current time (after any change of state outside a step).
 static pibm_status prime(pibm_ctx* ctx) {
     Ctx& c = ctx->c;
+    PCHECK(launch_coupling_clear(&c, c.s0, parity(c)));
     PCHECK(launch_coupling(&c, c.s0, parity(c)));
     PCHECK(cudaStreamSynchronize(c.s0));
     return PIBM_OK;
@@ -204,7 +207,10 @@ pibm_status pibm_create(const pibm_desc* d, void* stream, const pibm_allocator* 
         return g_create_error = cudaGetErrorString(e), PIBM_ERR_CUDA;
     }
     c.own_s0 = stream ? 0 : 1;
-    if ((e = cudaStreamCreateWithFlags(&c.s1, cudaStreamNonBlocking)) != cudaSuccess ||
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    // the DEM branch is latency-bound on a few SMs: give it the highest priority
+    if ((e = cudaStreamCreateWithPriority(&c.s1, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming)) != cudaSuccess) {
         delete ctx;
@@ -213,15 +219,18 @@ pibm_status pibm_create(const pibm_desc* d, void* stream, const pibm_allocator* 
     long long N = c.G.N;
     c.f = dalloc(ctx, (size_t)c.Q * N * c.es, GRP_LATTICE);
     c.g = dalloc(ctx, (size_t)c.QG * N * c.es, GRP_LATTICE);
-    c.fb = dalloc(ctx, (size_t)N * c.v4, GRP_LATTICE);
-    c.mk = dalloc(ctx, (size_t)N * c.v4, GRP_LATTICE);
-    c.flags = (uint8_t*)dalloc(ctx, (size_t)c.G.ntx * d->ny * d->nz, GRP_LATTICE);
+    for (int b = 0; b < 2; b++) {
+        c.fb[b] = dalloc(ctx, (size_t)N * c.v4, GRP_LATTICE);
+        c.mk[b] = dalloc(ctx, (size_t)N * c.v4, GRP_LATTICE);
+        c.flags[b] = (uint8_t*)dalloc(ctx, (size_t)c.G.ntx * d->ny * d->nz, GRP_LATTICE);
+    }
     c.red = (double*)dalloc(ctx, sizeof(double) * (4 * 512 + 16), GRP_LATTICE);
     c.dstat = (int*)dalloc(ctx, sizeof(int) * 4, GRP_LATTICE);
     c.nu_val = (double*)dalloc(ctx, sizeof(double) * 2, GRP_LATTICE);
     c.nb_cur = (int*)dalloc(ctx, sizeof(int) * 2, GRP_LATTICE);
     c.plane = nullptr;
-    if (!c.f || !c.g || !c.fb || !c.mk || !c.flags || !c.red || !c.dstat || !c.nu_val || !c.nb_cur) {
+    if (!c.f || !c.g || !c.fb[0] || !c.mk[0] || !c.flags[0] || !c.fb[1] || !c.mk[1] || !c.flags[1] || !c.red ||
+        !c.dstat || !c.nu_val || !c.nb_cur) {
         g_create_error = "device allocation failed";
         pibm_destroy(ctx);
         return PIBM_ERR_OOM;
@@ -322,9 +331,11 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     dfree_group(ctx, GRP_PARTICLES);
     c.np = 0;
     c.dem.n = 0;
-    PCHECK(cudaMemsetAsync(c.mk, 0, (size_t)c.G.N * c.v4, c.s0));
-    PCHECK(cudaMemsetAsync(c.fb, 0, (size_t)c.G.N * c.v4, c.s0));
-    PCHECK(cudaMemsetAsync(c.flags, 0, (size_t)c.G.ntx * c.G.ny * c.G.nz, c.s0));
+    for (int b = 0; b < 2; b++) {
+        PCHECK(cudaMemsetAsync(c.mk[b], 0, (size_t)c.G.N * c.v4, c.s0));
+        PCHECK(cudaMemsetAsync(c.fb[b], 0, (size_t)c.G.N * c.v4, c.s0));
+        PCHECK(cudaMemsetAsync(c.flags[b], 0, (size_t)c.G.ntx * c.G.ny * c.G.nz, c.s0));
+    }
     PCHECK(cudaMemsetAsync(c.dstat, 0, sizeof(int) * 4, c.s0));
     PCHECK(cudaMemsetAsync(c.nb_cur, 0, sizeof(int) * 2, c.s0));
     if (n == 0) return prime(ctx);
@@ -393,7 +404,8 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     c.Fh_prev = (double*)A(v3), c.Th_prev = (double*)A(v3), c.Hh_prev = (double*)A(v1);
     c.have_prev = (int*)A(sizeof(int) * 2);
     c.adj_start_new = (int*)A(sizeof(int) * (n + 2));
-    c.box = (int*)A(sizeof(int) * 6 * (n + 1));
+    c.box[0] = (int*)A(sizeof(int) * 6 * (n + 1));
+    c.box[1] = (int*)A(sizeof(int) * 6 * (n + 1));
     c.cell_of = (int*)A(sizeof(int) * (n + 1));
     c.cell_cnt = (int*)A(sizeof(int) * (C.ncell + 1));
     c.cell_start = (int*)A(sizeof(int) * (C.ncell + 2));
@@ -414,7 +426,7 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     c.contact_scratch = (int*)A(sizeof(int) * (2 * n + 8));
     void* need[] = {c.X, c.U, c.W, c.Xb, c.R, c.rho, c.Tp, c.Cp, c.m, c.I, c.mg, c.fixed, c.Fh, c.Th, c.Hh, c.Fc,
                     c.Fh_prev, c.Th_prev, c.Hh_prev, c.have_prev, c.adj_start_new,
-                    c.Tc, c.box, c.cell_of, c.cell_cnt, c.cell_start, c.cell_ids, c.cnt_hi, c.cnt_lo, c.nb_start[0],
+                    c.Tc, c.box[0], c.box[1], c.cell_of, c.cell_cnt, c.cell_start, c.cell_ids, c.cnt_hi, c.cnt_lo, c.nb_start[0],
                     c.nb_start[1], c.nb_i[0], c.nb_i[1], c.nb_j[0], c.nb_j[1], c.nb_ft[0], c.nb_ft[1], c.adj_start,
                     c.adj_nb, c.adj_k, c.wall_ft, c.contact_pairs, c.contact_scratch};
     for (void* p : need)
@@ -434,7 +446,8 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     PCHECK(up(c.I, hI.data(), sizeof(double) * n));
     PCHECK(up(c.mg, hmg.data(), sizeof(double) * n));
     PCHECK(up(c.fixed, hfix.data(), n));
-    PCHECK(up(c.box, hbox.data(), sizeof(int) * 6 * n));
+    PCHECK(up(c.box[0], hbox.data(), sizeof(int) * 6 * n));
+    PCHECK(up(c.box[1], hbox.data(), sizeof(int) * 6 * n));
     PCHECK(cudaStreamSynchronize(c.s0));  // host vectors go out of scope
     c.np = n;
     c.dem_cs = dem_cluster_size(&c);
@@ -467,8 +480,10 @@ pibm_status pibm_set_markers(pibm_ctx* ctx, int n, const double* X, const double
     drop_graphs(c);
     dfree_group(ctx, GRP_MARKERS);
     c.nm = 0;
-    PCHECK(cudaMemsetAsync(c.fb, 0, (size_t)c.G.N * c.v4, c.s0));
-    PCHECK(cudaMemsetAsync(c.flags, 0, (size_t)c.G.ntx * c.G.ny * c.G.nz, c.s0));
+    for (int b = 0; b < 2; b++) {
+        PCHECK(cudaMemsetAsync(c.fb[b], 0, (size_t)c.G.N * c.v4, c.s0));
+        PCHECK(cudaMemsetAsync(c.flags[b], 0, (size_t)c.G.ntx * c.G.ny * c.G.nz, c.s0));
+    }
     if (n == 0) return prime(ctx);
     // node -> (marker, weight) lists for the spreading gather; delta_h of Eq lbm12
     const double PI = 3.14159265358979323846;
@@ -539,7 +554,8 @@ pibm_status pibm_set_markers(pibm_ctx* ctx, int n, const double* X, const double
     PCHECK(cudaMemcpy(c.csr_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice));
     PCHECK(cudaMemcpy(c.csr_marker, mk.data(), sizeof(int) * mk.size(), cudaMemcpyHostToDevice));
     PCHECK(cudaMemcpy(c.csr_w, wt.data(), sizeof(double) * wt.size(), cudaMemcpyHostToDevice));
-    PCHECK(cudaMemcpy(c.flags, hflags.data(), hflags.size(), cudaMemcpyHostToDevice));
+    PCHECK(cudaMemcpy(c.flags[0], hflags.data(), hflags.size(), cudaMemcpyHostToDevice));  // static: both parities
+    PCHECK(cudaMemcpy(c.flags[1], hflags.data(), hflags.size(), cudaMemcpyHostToDevice));
     c.nm = n;
     return prime(ctx);
 }
@@ -576,11 +592,12 @@ static pibm_status capture(pibm_ctx* ctx, int par) {
     auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
     chk(cudaEventRecord(c.ev_fork, c.s0));
     chk(cudaStreamWaitEvent(c.s1, c.ev_fork, 0));
-    chk(launch_stream_collide(&c, c.s0, par));        // collide + stream, t -> t+1
     if (c.np > 0) {
-        chk(launch_dem(&c, c.s1, c.desc.dem_substeps));  // particles t -> t+1, concurrent
+        chk(launch_dem(&c, c.s1, c.desc.dem_substeps));  // particles t -> t+1, concurrent, launched first
+        chk(launch_coupling_clear(&c, c.s1, par ^ 1));  // free the other coupling set (read at t-1)
         kernels++;
     }
+    chk(launch_stream_collide(&c, c.s0, par));        // collide + stream, t -> t+1
     chk(cudaEventRecord(c.ev_join, c.s1));
     chk(cudaStreamWaitEvent(c.s0, c.ev_join, 0));
     chk(launch_coupling(&c, c.s0, par ^ 1));         // coupling of time t+1
@@ -628,11 +645,12 @@ pibm_status pibm_step_timed(pibm_ctx* ctx, double* ms) {
     auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
     chk(cudaEventRecord(ev[0], c.s0));
     chk(cudaStreamWaitEvent(c.s1, ev[0], 0));
-    chk(launch_stream_collide(&c, c.s0, par));
-    chk(cudaEventRecord(ev[1], c.s0));
     chk(cudaEventRecord(ev[2], c.s1));
     chk(launch_dem(&c, c.s1, c.desc.dem_substeps));
+    chk(launch_coupling_clear(&c, c.s1, par ^ 1));
     chk(cudaEventRecord(ev[3], c.s1));
+    chk(launch_stream_collide(&c, c.s0, par));
+    chk(cudaEventRecord(ev[1], c.s0));
     chk(cudaStreamWaitEvent(c.s0, ev[3], 0));
     chk(cudaEventRecord(ev[4], c.s0));
     chk(launch_coupling(&c, c.s0, par ^ 1));
@@ -769,6 +787,12 @@ pibm_status pibm_time(pibm_ctx* ctx, int64_t* t) {
 pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value) {
     if (!ctx) return PIBM_ERR_ARG;
     Ctx& c = ctx->c;
+    if (knob == PIBM_TUNE_SCALAR_LATTICE) {
+        if (value != 0 && value != 1) return fail(ctx, PIBM_ERR_ARG, "invalid tuning value");
+        c.tune_scalar_lattice = value;
+        drop_graphs(c);
+        return PIBM_OK;
+    }
     if (knob != PIBM_TUNE_DEM_PARTICLES_PER_CTA || value < 0 || value > dem_max_per_cta())
         return fail(ctx, PIBM_ERR_ARG, "invalid tuning knob or value");
     c.tune_dem_particles_per_cta = value;
@@ -794,9 +818,14 @@ static std::vector<BufRef> state_buffers(Ctx& c) {
     long long N = c.G.N;
     v.push_back({"f", c.f, (size_t)c.Q * N * c.es});
     v.push_back({"g", c.g, (size_t)c.QG * N * c.es});
-    v.push_back({"fb", c.fb, (size_t)N * c.v4});
-    v.push_back({"mk", c.mk, (size_t)N * c.v4});
-    v.push_back({"flags", c.flags, (size_t)c.G.ntx * c.G.ny * c.G.nz});
+    const char* fbn[2] = {"fb0", "fb1"};
+    const char* mkn[2] = {"mk0", "mk1"};
+    const char* fln[2] = {"flags0", "flags1"};
+    for (int b = 0; b < 2; b++) {
+        v.push_back({fbn[b], c.fb[b], (size_t)N * c.v4});
+        v.push_back({mkn[b], c.mk[b], (size_t)N * c.v4});
+        v.push_back({fln[b], c.flags[b], (size_t)c.G.ntx * c.G.ny * c.G.nz});
+    }
     v.push_back({"nu_val", c.nu_val, sizeof(double) * 2});
     v.push_back({"nb_cur", c.nb_cur, sizeof(int) * 2});
     int n = c.np;
@@ -807,7 +836,8 @@ static std::vector<BufRef> state_buffers(Ctx& c) {
                        {"mg", c.mg, v1}, {"fixed", c.fixed, (size_t)n}, {"Fh", c.Fh, v3}, {"Th", c.Th, v3},
                        {"Hh", c.Hh, v1}, {"Fc", c.Fc, v3}, {"Tc", c.Tc, v3}, {"Fh_prev", c.Fh_prev, v3},
                        {"Th_prev", c.Th_prev, v3}, {"Hh_prev", c.Hh_prev, v1}, {"have_prev", c.have_prev, sizeof(int)},
-                       {"box", c.box, sizeof(int) * 6 * n}, {"wall_ft", c.wall_ft, sizeof(float) * 18 * n},
+                       {"box0", c.box[0], sizeof(int) * 6 * n}, {"box1", c.box[1], sizeof(int) * 6 * n},
+                       {"wall_ft", c.wall_ft, sizeof(float) * 18 * n},
                        {"nb_start0", c.nb_start[0], sizeof(int) * (n + 1)}, {"nb_start1", c.nb_start[1], sizeof(int) * (n + 1)},
                        {"nb_i0", c.nb_i[0], sizeof(int) * c.dem.cap}, {"nb_i1", c.nb_i[1], sizeof(int) * c.dem.cap},
                        {"nb_j0", c.nb_j[0], sizeof(int) * c.dem.cap}, {"nb_j1", c.nb_j[1], sizeof(int) * c.dem.cap},

@@ -414,11 +414,11 @@ static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
     using V = typename Store<S>::V4;
     if (!c->desc.pibm) return cudaSuccess;
     if (c->np > 0) {
-        k_clear<V><<<c->np, CP_THREADS, 0, s>>>(c->G, c->box, (V*)c->mk, (V*)c->fb, c->flags);
-        k_footprint<D, S><<<c->np, CP_THREADS, 0, s>>>(c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk, c->X, c->U, c->W,
+        k_footprint<D, S><<<c->np, CP_THREADS, 0, s>>>(c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk[parity], c->X, c->U, c->W,
                                                        c->R, c->Tp, c->adj_start, c->adj_nb, c->desc.kappa_T,
                                                        c->desc.T_ref, parity, c->Fh, c->Th, c->Hh);
-        k_spread<D, V><<<c->np, CP_THREADS, SPREAD_SMEM, s>>>(c->G, c->X, c->R, (const V*)c->mk, (V*)c->fb, c->flags, c->box);
+        k_spread<D, V><<<c->np, CP_THREADS, SPREAD_SMEM, s>>>(c->G, c->X, c->R, (const V*)c->mk[parity], (V*)c->fb[parity],
+                                                              c->flags[parity], c->box[parity]);
     }
     if (c->nm > 0) {
         int nb = (c->nm + CP_THREADS - 1) / CP_THREADS;
@@ -427,7 +427,7 @@ static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
         int nn = c->n_csr_nodes;
         if (nn > 0)
             k_marker_spread<V><<<(nn + CP_THREADS - 1) / CP_THREADS, CP_THREADS, 0, s>>>(nn, c->csr_node, c->csr_start, c->csr_marker,
-                                                                                   c->csr_w, (const V*)c->Ml, (V*)c->fb);
+                                                                                   c->csr_w, (const V*)c->Ml, (V*)c->fb[parity]);
         k_nu_reduce<<<1, CP_THREADS, 0, s>>>(c->nu_part, c->nm, 1.0 / (c->alpha * c->desc.nu_dT), c->nu_val);
     }
     return cudaGetLastError();
@@ -435,9 +435,20 @@ static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
 
 cudaError_t launch_coupling(Ctx* c, cudaStream_t s, int parity) { PIBM_DISPATCH(c, coupling_impl, c, s, parity); }
 
+// Zero the coupling fields of one parity on the boxes its last spread recorded.
+template <int D, typename S>
+static cudaError_t clear_impl(Ctx* c, cudaStream_t s, int parity) {
+    using V = typename Store<S>::V4;
+    if (!c->desc.pibm || c->np <= 0) return cudaSuccess;
+    k_clear<V><<<c->np, CP_THREADS, 0, s>>>(c->G, c->box[parity], (V*)c->mk[parity], (V*)c->fb[parity], c->flags[parity]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coupling_clear(Ctx* c, cudaStream_t s, int parity) { PIBM_DISPATCH(c, clear_impl, c, s, parity); }
+
 int coupling_kernel_count(Ctx* c) {
     if (!c->desc.pibm) return 0;
-    return (c->np > 0 ? 3 : 0) + (c->nm > 0 ? 3 : 0);
+    return (c->np > 0 ? 3 : 0) + (c->nm > 0 ? 3 : 0);  // clear (on the DEM stream), footprint, spread
 }
 
 }  // namespace pibm

@@ -50,10 +50,12 @@ struct DemState {
     int adj_cap;
 };
 
-// state a CTA publishes for each of its particles
+// state a CTA publishes for each of its particles: FP64 position (exact
+// contact test), FP32 copy of it (prefilter), FP32 velocities (force law)
 struct Pub {
     double x[3];
     float u[3], w[3];
+    float xf[3], pad;
 };
 
 __device__ __forceinline__ void set_error(int* dstat, int detail) {
@@ -196,17 +198,16 @@ __device__ __forceinline__ void for_neighbours(const DemCfg& C, const DemState& 
 // mask: bit f set while face f holds a non-zero tangential history, so faces
 // out of contact cost no memory traffic.
 template <int D>
-__device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, int p, const Pub& me, double Rp, float dtf,
-                                            float* F, float* T, int& mask) {
+__device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, int p, const Pub& me, double Rp, float Rpf,
+                                            float dtf, float* F, float* T, int& mask) {
     for (int face = 0; face < 2 * D; face++) {
         int a = face >> 1, hi = face & 1;
         if (!C.walled[a]) continue;
         float* ftp = S.wall_ft + 3 * (6 * p + face);
         // FP32 prefilter on the distance to the wall plane, exact FP64 test when close
-        const float xf = (float)me.x[a];
-        const float distf = hi ? (float)C.hi[a] - xf : xf - (float)C.lo[a];
+        const float distf = hi ? C.hif[a] - me.xf[a] : me.xf[a] - C.lof[a];
         double dd = -1.0;
-        if (distf < (float)Rp + 1e-3f) dd = Rp - (hi ? C.hi[a] - me.x[a] : me.x[a] - C.lo[a]);
+        if (distf < Rpf + 1e-3f) dd = Rp - (hi ? C.hi[a] - me.x[a] : me.x[a] - C.lo[a]);
         if (!(dd > 0.0)) {
             if (mask & (1 << face)) {
                 ftp[0] = ftp[1] = ftp[2] = 0.f;
@@ -219,14 +220,14 @@ __device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, 
         if (a == 0) nn.x = hi ? 1.f : -1.f;
         else if (a == 1) nn.y = hi ? 1.f : -1.f;
         else nn.z = hi ? 1.f : -1.f;
-        float ai = (float)Rp - 0.5f * delta;
+        float ai = Rpf - 0.5f * delta;
         float3 ri = f3(ai * nn.x, ai * nn.y, ai * nn.z);
         float3 wi = cross3(f3(me.w[0], me.w[1], me.w[2]), ri);
         float3 vr = f3(me.u[0] + wi.x, me.u[1] + wi.y, me.u[2] + wi.z);
         float vn = vr.x * nn.x + vr.y * nn.y + vr.z * nn.z;
         float3 vt = f3(vr.x - vn * nn.x, vr.y - vn * nn.y, vr.z - vn * nn.z);
         float kt_eff;
-        float Fn = normal_law(C, delta, vn, (float)Rp, &kt_eff);
+        float Fn = normal_law(C, delta, vn, Rpf, &kt_eff);
         float3 h = (mask & (1 << face)) ? f3(__ldcg(ftp), __ldcg(ftp + 1), __ldcg(ftp + 2)) : f3(0.f, 0.f, 0.f);
         float3 Ft = tangential(C, h, nn, vt, kt_eff, Fn, dtf);
         ftp[0] = h.x, ftp[1] = h.y, ftp[2] = h.z;
@@ -240,8 +241,9 @@ __device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, 
 // private state of a particle while its CTA runs the substeps (shared memory)
 struct Priv {
     double X[3], U[3], W[3];
-    double a[3], al[3];      // external linear / angular acceleration: (hydro + buoyant weight)/m, hydro torque/I
+    float a[3], al[3];       // external linear / angular acceleration: (hydro + buoyant weight)/m, hydro torque/I
     double im, iI, R;        // 1/m, 1/I, radius
+    float Rf, pad2;          // radius in FP32 (prefilters)
     float Fc[3], Tc[3];      // contact force / torque of the last evaluation
     int fixed, wall_mask;    // wall_mask: faces with a non-zero tangential history
     int nadj, pad;           // neighbours in the adjacency
@@ -250,8 +252,8 @@ struct Priv {
 // velocity Verlet half kick: U += h (F_c/m + a_ext), omega += h (T_c/I + alpha_ext)
 __device__ __forceinline__ void kick_s(Priv& P, double h, int dim) {
     for (int a = 0; a < 3; a++) {
-        P.U[a] += h * ((double)P.Fc[a] * P.im + P.a[a]);
-        P.W[a] += h * ((double)P.Tc[a] * P.iI + P.al[a]);
+        P.U[a] += h * ((double)P.Fc[a] * P.im + (double)P.a[a]);
+        P.W[a] += h * ((double)P.Tc[a] * P.iI + (double)P.al[a]);
     }
     if (dim == 2) {
         P.U[2] = 0.0;
@@ -263,6 +265,7 @@ __device__ __forceinline__ void drift_s(Priv& P, double dt, Pub& pub) {
     for (int a = 0; a < 3; a++) {
         P.X[a] += dt * P.U[a];
         pub.x[a] = P.X[a];
+        pub.xf[a] = (float)P.X[a];
         pub.u[a] = (float)P.U[a];
         pub.w[a] = (float)P.W[a];
     }
@@ -271,12 +274,13 @@ __device__ __forceinline__ void drift_s(Priv& P, double dt, Pub& pub) {
 __device__ __forceinline__ void publish_s(const Priv& P, Pub& pub) {
     for (int a = 0; a < 3; a++) {
         pub.x[a] = P.X[a];
+        pub.xf[a] = (float)P.X[a];
         pub.u[a] = (float)P.U[a];
         pub.w[a] = (float)P.W[a];
     }
 }
 
-constexpr int DEM_MAXA = 8;  // neighbours per particle staged in shared memory
+constexpr int DEM_MAXA = 6;  // neighbours per particle staged in shared memory
 
 template <int D>
 __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, int advance) {
@@ -312,6 +316,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             P.im = 1.0 / S.m[p];
             P.iI = 1.0 / S.I[p];
             P.R = S.R[p];
+            P.Rf = (float)P.R;
             P.fixed = S.fixed[p];
             P.wall_mask = 0;
             for (int f = 0; f < 2 * D; f++) {
@@ -325,8 +330,8 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 P.W[a] = S.W[3 * p + a];
                 P.Fc[a] = (float)S.Fc[3 * p + a];
                 P.Tc[a] = (float)S.Tc[3 * p + a];
-                P.a[a] = (hydro(S.Fh, S.Fhp, 3 * p + a, hp) + mg * C.g[a]) * P.im;
-                P.al[a] = hydro(S.Th, S.Thp, 3 * p + a, hp) * P.iI;
+                P.a[a] = (float)((hydro(S.Fh, S.Fhp, 3 * p + a, hp) + mg * C.g[a]) * P.im);
+                P.al[a] = (float)(hydro(S.Th, S.Thp, 3 * p + a, hp) * P.iI);
             }
             if (!P.fixed) {
                 kick_s(P, 0.5 * dt, D);
@@ -353,8 +358,9 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 Priv& P = prv[l];
                 const Pub me = pub[rb * per + l];
                 const double Rp = P.R;
+                const float Rpf = P.Rf;
                 float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};  // contact sums (a few terms) in FP32
-                wall_forces<D>(C, S, p, me, Rp, dtf, F, T, P.wall_mask);
+                wall_forces<D>(C, S, p, me, Rp, Rpf, dtf, F, T, P.wall_mask);
                 const int ne = P.nadj, e0 = ne > DEM_MAXA ? __ldcg(S.adj_start + p) : 0;
                 for (int e = 0; e < ne; e++) {
                     int q, kk;
@@ -367,19 +373,21 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                     const bool first = kk >= 0;
                     const int k = first ? kk : ~kk;
                     const int rq = q / per, lq = q - rq * per;
-                    const Pub other = cl.map_shared_rank(pub, rq)[rb * per + lq];
-                    const double Rq = cl.map_shared_rank(prv, rq)[lq].R;
-                    const Pub& A = first ? me : other;
-                    const Pub& B = first ? other : me;
-                    const double Ra = first ? Rp : Rq, Rb = first ? Rq : Rp;
-                    // FP32 prefilter; the contact decision itself is the exact FP64 test
-                    const float dxf = (float)(B.x[0] - A.x[0]), dyf = (float)(B.x[1] - A.x[1]), dzf = (float)(B.x[2] - A.x[2]);
-                    const float sf = (float)(Ra + Rb) + 1e-3f;
+                    const Pub* rp = cl.map_shared_rank(pub, rq) + rb * per + lq;
+                    const Priv* rv = cl.map_shared_rank(prv, rq) + lq;
+                    // FP32 prefilter from the published FP32 positions (no FP64 for pairs apart)
+                    const float dxf = rp->xf[0] - me.xf[0], dyf = rp->xf[1] - me.xf[1], dzf = rp->xf[2] - me.xf[2];
+                    const float sf = Rpf + rv->Rf + 1e-3f;
                     float3 Fa = f3(0.f, 0.f, 0.f), Ta = Fa, Tb = Fa, h = Fa;
                     bool contact = false;
                     if (dxf * dxf + dyf * dyf + dzf * dzf < sf * sf) {
+                        const Pub other = *rp;
+                        const double Rq = rv->R;
+                        const Pub& A = first ? me : other;
+                        const Pub& B = first ? other : me;
+                        const double Ra = first ? Rp : Rq, Rb = first ? Rq : Rp;
                         double d2 = dist2(A.x, B.x), Ssum = Ra + Rb;
-                        contact = d2 < Ssum * Ssum;
+                        contact = d2 < Ssum * Ssum;  // the exact FP64 contact test
                         if (contact) {
                             const float4 hv = __ldcg(hist_old + k);
                             if (__float_as_int(hv.w) == gsub - 1) h = f3(hv.x, hv.y, hv.z);
@@ -627,7 +635,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
 }
 
 // cluster size: up to 16 CTAs of DEM_T threads, at most DEM_MAXPER particles per CTA
-constexpr int DEM_MAXPER = 640;  // (2 * 48 + 184 + 64) B per particle: 220 KB of shared memory
+constexpr int DEM_MAXPER = 640;  // (2 * 64 + 168 + 48) B per particle: 220 KB of shared memory
 
 static size_t dem_smem(int per) { return (size_t)per * (2 * sizeof(Pub) + sizeof(Priv) + DEM_MAXA * sizeof(int2)); }
 

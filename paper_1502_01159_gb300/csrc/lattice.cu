@@ -11,6 +11,8 @@
 // to the neighbours, so one array serves both time levels.
 #include <float.h>
 
+#include <type_traits>
+
 #include "pibm_internal.cuh"
 
 namespace pibm {
@@ -280,6 +282,188 @@ static CollideParams<R> collide_params(const Ctx* c) {
     return P;
 }
 
+// Generic odd-step store of one node's post-collision populations (any
+// boundary).  side = -1 or +1 restricts it to the directions that leave the
+// lattice through that x face (the rest were stored by the pair path).
+template <int D, typename S>
+__device__ __forceinline__ void store_node(const Geo& G, const CollideParams<typename Store<S>::R>& P, S* f, S* g, int x,
+                                           int y, int z, const typename Store<S>::R* s, const typename Store<S>::R* sg,
+                                           int side) {
+    using L = Lat<D>;
+    using R = typename Store<S>::R;
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+        if (side != 0 && L::ex(i) != side) continue;
+        long long idx;
+        post_slot(G, x, y, z, L::ex(i), L::ey(i), L::ez(i), i, L::opp(i), 1, idx);
+        f[idx] = Store<S>::stf(s[i]);
+    }
+#pragma unroll
+    for (int k = 0; k < L::QG; k++) {
+        if (side != 0 && L::ex(k) != side) continue;
+        long long idx;
+        int face = post_slot(G, x, y, z, L::ex(k), L::ey(k), L::ez(k), k, L::opp(k), 1, idx);
+        R v = sg[k];
+        if (face_iso(G, face)) v = P.abb[face] - v;
+        g[idx] = Store<S>::stg(v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 16-bit storage, two nodes per thread.  Populations of the pair (x0, x0+1)
+// move as one 32-bit half2 / bfloat162 word with a packed conversion.  In odd
+// steps a direction with e_x = +1 reads x-1 (the upper half of the left
+// neighbour lane's aligned pair, via a warp shuffle) and e_x = -1 reads x+1
+// (the lower half of the right lane's pair); the lanes at either end of the
+// warp fetch the one element beyond it with a scalar access.  Stores mirror
+// this.  Lanes holding a node on an x face run the generic path for that node
+// as well (wrap or bounce-back); accesses that would cross the row end are
+// skipped there.  Requires nx to be a multiple of 64 (whole warps per row).
+template <typename S> struct Pair;
+template <> struct Pair<__half> {
+    using T = __half2;
+    static __device__ __forceinline__ float2 ldf(T v) { float2 r = __half22float2(v); return make_float2(r.x * 0.0009765625f, r.y * 0.0009765625f); }
+    static __device__ __forceinline__ float2 ldg(T v) { float2 r = __half22float2(v); return make_float2(r.x * 0.00390625f, r.y * 0.00390625f); }
+    static __device__ __forceinline__ T stf(float a, float b) { return __floats2half2_rn(a * 1024.0f, b * 1024.0f); }
+    static __device__ __forceinline__ T stg(float a, float b) { return __floats2half2_rn(a * 256.0f, b * 256.0f); }
+};
+template <> struct Pair<__nv_bfloat16> {
+    using T = __nv_bfloat162;
+    static __device__ __forceinline__ float2 ldf(T v) { return __bfloat1622float2(v); }
+    static __device__ __forceinline__ float2 ldg(T v) { return __bfloat1622float2(v); }
+    static __device__ __forceinline__ T stf(float a, float b) { return __floats2bfloat162_rn(a, b); }
+    static __device__ __forceinline__ T stg(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+
+template <int D, typename S, int PARITY>
+__global__ void __launch_bounds__(256) k_stream_collide_pair(Geo G, S* __restrict__ f, S* __restrict__ g,
+                                                             const float4* __restrict__ fb, const uint8_t* __restrict__ flags,
+                                                             CollideParams<float> P, AAOffsets O) {
+    using L = Lat<D>;
+    using PT = typename Pair<S>::T;
+    using St = Store<S>;
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int lane = threadIdx.x & 31;
+    if (x0 >= G.nx) return;  // whole warps only: nx / 2 is a multiple of 32
+    const long long n0 = node_index(G, x0, y, z);
+    const bool inner_yz = y > 0 && y < G.ny - 1 && (D == 2 || (z > 0 && z < G.nz - 1));
+    const bool lo_edge = x0 == 0, hi_edge = x0 + 1 == G.nx - 1;
+    float s0[L::Q], s1[L::Q], g0[L::QG], g1[L::QG];
+    if (PARITY == 0) {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) {
+            float2 v = Pair<S>::ldf(*reinterpret_cast<const PT*>(f + n0 + O.ld[i]));
+            s0[i] = v.x, s1[i] = v.y;
+        }
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) {
+            float2 v = Pair<S>::ldg(*reinterpret_cast<const PT*>(g + n0 + O.ld[k]));
+            g0[k] = v.x, g1[k] = v.y;
+        }
+    } else if (inner_yz) {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) {
+            const int ex = L::ex(i);
+            const long long e = n0 + O.src[i];  // source element of node x0
+            if (ex == 0) {
+                float2 v = Pair<S>::ldf(*reinterpret_cast<const PT*>(f + e));
+                s0[i] = v.x, s1[i] = v.y;
+            } else if (ex == 1) {  // node x reads x-1: (x0-1, x0)
+                float2 v = Pair<S>::ldf(*reinterpret_cast<const PT*>(f + e + 1));
+                float left = __shfl_up_sync(0xffffffffu, v.y, 1);
+                if (lane == 0) left = lo_edge ? 0.f : St::ldf(f[e]);
+                s0[i] = left, s1[i] = v.x;
+            } else {  // node x reads x+1: (x0+1, x0+2)
+                float2 v = Pair<S>::ldf(*reinterpret_cast<const PT*>(f + e - 1));
+                float right = __shfl_down_sync(0xffffffffu, v.x, 1);
+                if (lane == 31) right = hi_edge ? 0.f : St::ldf(f[e + 1]);
+                s0[i] = v.y, s1[i] = right;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) {
+            const int ex = L::ex(k);
+            const long long e = n0 + O.src[k];
+            if (ex == 0) {
+                float2 v = Pair<S>::ldg(*reinterpret_cast<const PT*>(g + e));
+                g0[k] = v.x, g1[k] = v.y;
+            } else if (ex == 1) {
+                float2 v = Pair<S>::ldg(*reinterpret_cast<const PT*>(g + e + 1));
+                float left = __shfl_up_sync(0xffffffffu, v.y, 1);
+                if (lane == 0) left = lo_edge ? 0.f : St::ldg(g[e]);
+                g0[k] = left, g1[k] = v.x;
+            } else {
+                float2 v = Pair<S>::ldg(*reinterpret_cast<const PT*>(g + e - 1));
+                float right = __shfl_down_sync(0xffffffffu, v.x, 1);
+                if (lane == 31) right = hi_edge ? 0.f : St::ldg(g[e + 1]);
+                g0[k] = v.y, g1[k] = right;
+            }
+        }
+        if (lo_edge) load_node<D, S, float>(G, f, g, x0, y, z, 1, s0, g0);
+        if (hi_edge) load_node<D, S, float>(G, f, g, x0 + 1, y, z, 1, s1, g1);
+    } else {
+        load_node<D, S, float>(G, f, g, x0, y, z, 1, s0, g0);
+        load_node<D, S, float>(G, f, g, x0 + 1, y, z, 1, s1, g1);
+    }
+    float b0[4] = {0.f, 0.f, 0.f, 0.f}, b1[4] = {0.f, 0.f, 0.f, 0.f};
+    if (flags[((long long)z * G.ny + y) * G.ntx + (x0 >> 5)]) {  // x0 and x0+1 share a 32-node tile
+        const float4 v0 = fb[n0], v1 = fb[n0 + 1];
+        b0[0] = v0.x, b0[1] = v0.y, b0[2] = v0.z, b0[3] = v0.w;
+        b1[0] = v1.x, b1[1] = v1.y, b1[2] = v1.z, b1[3] = v1.w;
+    }
+    collide_node<D, float>(s0, g0, b0[0], b0[1], b0[2], b0[3], P);
+    collide_node<D, float>(s1, g1, b1[0], b1[1], b1[2], b1[3], P);
+    if (PARITY == 0) {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) *reinterpret_cast<PT*>(f + n0 + O.st[i]) = Pair<S>::stf(s0[i], s1[i]);
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) *reinterpret_cast<PT*>(g + n0 + O.st[k]) = Pair<S>::stg(g0[k], g1[k]);
+    } else if (inner_yz) {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) {
+            const int ex = L::ex(i);
+            const long long e = n0 + O.dst[i];  // destination element of node x0
+            if (ex == 0) {
+                *reinterpret_cast<PT*>(f + e) = Pair<S>::stf(s0[i], s1[i]);
+            } else if (ex == 1) {  // x0 -> x0+1, x0+1 -> x0+2: this lane owns the word (x0, x0+1)
+                float left = __shfl_up_sync(0xffffffffu, s1[i], 1);
+                if (lane > 0) *reinterpret_cast<PT*>(f + e - 1) = Pair<S>::stf(left, s0[i]);
+                else f[e] = St::stf(s0[i]);
+                if (lane == 31 && !hi_edge) f[e + 1] = St::stf(s1[i]);
+            } else {  // x0 -> x0-1, x0+1 -> x0: this lane owns the word (x0, x0+1)
+                float right = __shfl_down_sync(0xffffffffu, s0[i], 1);
+                if (lane < 31) *reinterpret_cast<PT*>(f + e + 1) = Pair<S>::stf(s1[i], right);
+                else f[e + 1] = St::stf(s1[i]);
+                if (lane == 0 && !lo_edge) f[e] = St::stf(s0[i]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) {
+            const int ex = L::ex(k);
+            const long long e = n0 + O.dst[k];
+            if (ex == 0) {
+                *reinterpret_cast<PT*>(g + e) = Pair<S>::stg(g0[k], g1[k]);
+            } else if (ex == 1) {
+                float left = __shfl_up_sync(0xffffffffu, g1[k], 1);
+                if (lane > 0) *reinterpret_cast<PT*>(g + e - 1) = Pair<S>::stg(left, g0[k]);
+                else g[e] = St::stg(g0[k]);
+                if (lane == 31 && !hi_edge) g[e + 1] = St::stg(g1[k]);
+            } else {
+                float right = __shfl_down_sync(0xffffffffu, g0[k], 1);
+                if (lane < 31) *reinterpret_cast<PT*>(g + e + 1) = Pair<S>::stg(g1[k], right);
+                else g[e + 1] = St::stg(g1[k]);
+                if (lane == 0 && !lo_edge) g[e] = St::stg(g0[k]);
+            }
+        }
+        if (lo_edge) store_node<D, S>(G, P, f, g, x0, y, z, s0, g0, -1);
+        if (hi_edge) store_node<D, S>(G, P, f, g, x0 + 1, y, z, s1, g1, +1);
+    } else {
+        store_node<D, S>(G, P, f, g, x0, y, z, s0, g0, 0);
+        store_node<D, S>(G, P, f, g, x0 + 1, y, z, s1, g1, 0);
+    }
+}
+
 template <int D>
 static AAOffsets aa_offsets(const Geo& G) {
     using L = Lat<D>;
@@ -297,7 +481,27 @@ static AAOffsets aa_offsets(const Geo& G) {
 }
 
 template <int D, typename S>
+static cudaError_t pair_launch(Ctx* c, cudaStream_t s, int parity) {
+    if constexpr (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value) {
+        const int pairs = c->G.nx / 2;
+        dim3 block(pairs < 256 ? pairs : 256), grid((pairs + 255) / 256, c->G.ny, c->G.nz);
+        CollideParams<float> P = collide_params<float>(c);
+        AAOffsets O = aa_offsets<D>(c->G);
+        if (parity == 0)
+            k_stream_collide_pair<D, S, 0><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const float4*)c->fb[parity],
+                                                                  c->flags[parity], P, O);
+        else
+            k_stream_collide_pair<D, S, 1><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const float4*)c->fb[parity],
+                                                                  c->flags[parity], P, O);
+        return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int D, typename S>
 static cudaError_t sc_launch(Ctx* c, cudaStream_t s, int parity) {
+    constexpr bool half = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
+    if (half && c->G.nx % 64 == 0 && !c->tune_scalar_lattice) return pair_launch<D, S>(c, s, parity);
     dim3 block(256), grid((c->G.nx + 255) / 256, c->G.ny, c->G.nz);
     if (c->G.nx <= 128) block.x = 128, grid.x = (c->G.nx + 127) / 128;
     using R = typename Store<S>::R;
@@ -305,9 +509,9 @@ static cudaError_t sc_launch(Ctx* c, cudaStream_t s, int parity) {
     AAOffsets O = aa_offsets<D>(c->G);
     using V = typename Store<S>::V4;
     if (parity == 0)
-        k_stream_collide<D, S, 0><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb, c->flags, P, O);
+        k_stream_collide<D, S, 0><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb[parity], c->flags[parity], P, O);
     else
-        k_stream_collide<D, S, 1><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb, c->flags, P, O);
+        k_stream_collide<D, S, 1><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb[parity], c->flags[parity], P, O);
     return cudaGetLastError();
 }
 
@@ -440,7 +644,7 @@ __global__ void k_macro(Geo G, const S* f, const S* g, const typename Store<S>::
 template <int D, typename S>
 static cudaError_t macro_launch(Ctx* c, int field, int parity) {
     using V = typename Store<S>::V4;
-    k_macro<D, S><<<1024, 256, 0, c->s0>>>(c->G, (const S*)c->f, (const S*)c->g, (const V*)c->fb, c->flags,
+    k_macro<D, S><<<1024, 256, 0, c->s0>>>(c->G, (const S*)c->f, (const S*)c->g, (const V*)c->fb[parity], c->flags[parity],
                                            collide_params<double>(c), field, parity, c->plane);
     return cudaGetLastError();
 }
@@ -524,8 +728,8 @@ __global__ void __launch_bounds__(256) k_diag_final(const double* part, int nblo
 template <int D, typename S>
 static cudaError_t diag_launch(Ctx* c, int parity) {
     using V = typename Store<S>::V4;
-    k_diag_lattice<D, S><<<DIAG_BLOCKS, 256, 0, c->s0>>>(c->G, (const S*)c->f, (const S*)c->g, (const V*)c->fb,
-                                                         c->flags, collide_params<double>(c), parity, c->red);
+    k_diag_lattice<D, S><<<DIAG_BLOCKS, 256, 0, c->s0>>>(c->G, (const S*)c->f, (const S*)c->g, (const V*)c->fb[parity],
+                                                         c->flags[parity], collide_params<double>(c), parity, c->red);
     k_diag_final<<<1, 256, 0, c->s0>>>(c->red, DIAG_BLOCKS, c->U, c->W, c->X, c->m, c->I, c->np,
                                        c->desc.gravity_axis, c->red + 4 * DIAG_BLOCKS);
     return cudaGetLastError();

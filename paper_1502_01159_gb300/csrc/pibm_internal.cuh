@@ -212,6 +212,7 @@ struct DemCfg {
     float E_star, G_star, mu, kn, kt, gn, gt;
     double g[3];      // particle gravity
     double lo[3], hi[3];  // wall planes (-0.5, n - 0.5)
+    float lof[3], hif[3]; // the same in FP32 (prefilters)
     int walled[3];
     int nc[3];        // cells per axis
     double inv[3];    // nc / n per axis
@@ -243,9 +244,12 @@ struct Ctx {
     // lattice buffers
     void* f;
     void* g;
-    void* fb;         // F_B (xyz) and Q_B (w) per node, valid on flagged tiles
-    void* mk;         // marker field of covered nodes (eps * F_f, eps * Q)
-    uint8_t* flags;   // one byte per 32-node tile along x
+    // coupling fields, double-buffered by time parity: the coupling of time t
+    // writes set t & 1, the lattice step of time t reads it, and the set of the
+    // other parity is cleared concurrently with that step
+    void* fb[2];      // F_B (xyz) and Q_B (w) per node, valid on flagged tiles
+    void* mk[2];      // marker field of covered nodes (eps * F_f, eps * Q)
+    uint8_t* flags[2];  // one byte per 32-node tile along x
     double* plane;    // one plane of doubles (reads / writes through the API)
     double* red;      // reduction scratch
     int* dstat;       // device status words [code, detail]
@@ -258,7 +262,7 @@ struct Ctx {
     double *Fh_prev, *Th_prev, *Hh_prev;  // coupling of the previous time
     int* have_prev;   // device int: 1 once a previous coupling exists
     int* adj_start_new;  // scratch for the adjacency offsets of a rebuild
-    int* box;         // spread box per particle (lo xyz, hi xyz); empty = hi < lo
+    int* box[2];      // spread box per particle and parity (lo xyz, hi xyz); empty = hi < lo
     DemCfg dem;
     int *cell_of, *cell_cnt, *cell_start, *cell_ids, *cnt_hi, *cnt_lo;
     int* nb_start[2];
@@ -271,6 +275,7 @@ struct Ctx {
     int adj_cap;
     int dem_cs;           // CTAs in the DEM cluster
     int tune_dem_particles_per_cta;  // 0: default (32)
+    int tune_scalar_lattice;         // 1: one node per thread also for 16-bit storage
     int* contact_pairs;   // 2 * dem.cap ints
     int* contact_scratch; // 2 * np + 4 ints
 
@@ -301,6 +306,7 @@ cudaError_t launch_macro(Ctx* c, int field, int parity);
 cudaError_t launch_diagnostics(Ctx* c, int parity);
 // coupling.cu
 cudaError_t launch_coupling(Ctx* c, cudaStream_t s, int parity);
+cudaError_t launch_coupling_clear(Ctx* c, cudaStream_t s, int parity);
 int coupling_kernel_count(Ctx* c);
 // dem.cu
 cudaError_t launch_dem(Ctx* c, cudaStream_t s, int nsub);

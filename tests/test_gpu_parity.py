@@ -275,9 +275,12 @@ REDUCED_BOUNDS = {"f16": {"rho": 1e-6, "T": 2e-4, "u": 5e-3, "X": 1e-4},
 
 
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
-@pytest.mark.parametrize("which", ["2d", "3d"])
+@pytest.mark.parametrize("which", ["2d", "3d", "2d_pair", "3d_pair"])
 def test_reduced_precision_storage(storage, which):
-    case = _small_sed2d() if which == "2d" else _small_sed3d()
+    # nx a multiple of 64 selects the two-nodes-per-thread kernel
+    case = {"2d": _small_sed2d, "3d": _small_sed3d,
+            "2d_pair": lambda: _small_sed2d(nx=128),
+            "3d_pair": lambda: _small_sed3d(shape=(64, 32, 48))}[which]()
     case["storage"] = storage
     sim, orc = _sim(case), oracle.Oracle(case)
     sim.step(100)
@@ -292,6 +295,55 @@ def test_reduced_precision_storage(storage, which):
     for k, v in errs.items():
         assert v < REDUCED_BOUNDS[storage][k], (k, v, errs)
     assert sim.diagnostics()["nonfinite"] == 0
+
+
+def _paired_cases():
+    mixed2 = [(1, 1, 0.0), (1, 0, 0.0), (1, 1, 1.0), (1, 1, 0.2)]
+    mixed3 = mixed2 + [(1, 0, 0.0), (1, 1, 0.7)]
+    out = []
+    for dim, shape, walls in [(2, (128, 37, 1), None), (2, (192, 41, 1), mixed2),
+                              (3, (64, 13, 11), None), (3, (128, 19, 9), mixed3)]:
+        case = W.periodic_box(shape=shape, dim=dim, buoyancy=True, body=(2e-6, -1e-6, 0.0))
+        if walls:
+            case["walls"] = walls
+        out.append(case)
+    return out
+
+
+def _deviation(f):
+    q = f.shape[0]
+    return f - f.reshape(q, -1).mean(axis=1).reshape((q,) + (1,) * (f.ndim - 1))
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("ci", range(4))
+def test_paired_16bit_kernel_matches_scalar(storage, ci):
+    from paper_1502_01159_gb300 import TUNE_SCALAR_LATTICE
+    # the two-nodes-per-thread kernel (packed 32-bit accesses, shuffles for the
+    # x-shifted odd-step directions, face nodes on the generic path) against
+    # the one-node-per-thread kernel, periodic and walled x faces
+    case = _paired_cases()[ci]
+    case["storage"] = storage
+    f, g = W.random_populations(case, amp=0.02, config_index=9)
+    sims = []
+    for scalar in (1, 0):
+        s = _sim(case)
+        s.set_tuning(TUNE_SCALAR_LATTICE, scalar)
+        s.set_populations(f.ravel(), g.ravel())
+        sims.append(s)
+    for k in (1, 1, 48):
+        for s in sims:
+            s.step(k)
+        fa, ga = sims[0].read_populations()
+        fb_, gb_ = sims[1].read_populations()
+        tol = 2e-3 if storage == "f16" else 2e-2
+        for a, b in ((fa, fb_), (ga, gb_)):
+            da = _deviation(a)
+            err = np.max(np.abs(a - b)) / np.max(np.abs(da))
+            print(storage, case["shape"], k, err, np.mean(a == b))
+            assert err < tol, (k, err)
+    for s in sims:
+        assert s.diagnostics()["nonfinite"] == 0
 
 
 def test_checkpoint_resume_bit_exact(tmp_path):
