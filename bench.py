@@ -28,6 +28,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The ensemble's graph has one branch per box; the default of 8 hardware work
+# queues would serialise branches beyond the eighth (process-local setting,
+# read when the CUDA context is created).
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "fluid+thermal MLUPS and particle-steps/s at 1 GB300; % HBM peak; speedup vs plain FP32 at error"
 FALLBACK_HBM_GBS = 6800.0
@@ -38,11 +42,11 @@ def bytes_per_node(case) -> int:
     """Algorithmic bytes of one node update of the fused kernel: every flow and
     thermal population read once and written once (A-A in place)."""
     q = (9 + 5) if case["dim"] == 2 else (19 + 7)
-    es = 8 if case.get("storage") == "f64" else 4
+    es = {"f64": 8, "f16": 2, "bf16": 2}.get(case.get("storage", "f32"), 4)
     return 2 * q * es
 
 
-def workload(name: str):
+def workload(name: str, storage: str = "f32"):
     import workloads as W
     if name == "sed2d":
         case = W.sed2d()
@@ -55,6 +59,9 @@ def workload(name: str):
         desc = "sed3d_mid: 3-D sedimentation, 128x128x256 lattice, 250 heated spheres d=8, D3Q19+D3Q7 FP32, Hertz, 10 DEM substeps (profiling size)"
     else:
         raise SystemExit(f"unknown workload {name}")
+    if storage != "f32":
+        case["storage"] = storage
+        desc = desc.replace("FP32", f"{storage.upper()}-deviation storage (FP32 arithmetic)")
     return case, desc
 
 
@@ -161,7 +168,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    case, desc = workload(args.workload)
+    case, desc = workload(args.workload, args.storage)
     mlups, psps, dt = oracle_run(case, args.steps, args.warmup)
     sample = f"{args.steps} lattice steps (after {args.warmup} untimed) of the full {args.workload} workload"
     line = {
@@ -246,14 +253,17 @@ def precision_study(torch, flush):
     """Reduced-precision storage (FP16 / BF16 deviations, FP32 arithmetic) against
     the plain FP32 form: throughput of the fused lattice kernel and of the whole
     step on the full sed3d workload, and the error against the FP64 oracle on a
-    40x40x64 sedimentation crop (8 spheres, 50 steps) with the same recipe."""
+    64x64x128 sedimentation crop (31 spheres, the full case's solid fraction;
+    50 steps) with the same recipe.  The 16-bit kernel's two-nodes-per-thread
+    form is timed beside the default one-node-per-thread form."""
     import numpy as np
 
     import oracle
     import workloads as W
     from paper_1502_01159_gb300 import Simulation
     out = {}
-    crop = W.sed3d(nx=40, ny=40, nz=64, n_p=8, config_index=2)
+    from paper_1502_01159_gb300 import TUNE_PAIR_LATTICE
+    crop = W.sed3d(nx=64, ny=64, nz=128, n_p=31, config_index=2)
     crop["g_particle"] = [0.0, 0.0, -2e-4]
     orc = oracle.Oracle(crop)
     orc.step(50)
@@ -266,6 +276,10 @@ def precision_study(torch, flush):
         case["storage"] = storage
         sim, ms = measure_gpu(case, 8, 3, torch, flush)
         kt = kernel_times(sim, 5, torch, flush)
+        kt_pair = None
+        if storage != "f32":
+            sim.set_tuning(TUNE_PAIR_LATTICE, 1)
+            kt_pair = kernel_times(sim, 5, torch, flush)["stream_collide"]
         sim.close()
         c2 = dict(crop)
         c2["storage"] = storage
@@ -280,14 +294,84 @@ def precision_study(torch, flush):
                "X_max_abs": float(np.max(np.abs(s2.read_particles()["X"] - refX)))}
         s2.close()
         step = statistics.mean(ms)
+        bpn = bytes_per_node(case)
         out[storage] = {"step_ms": round(step, 4), "MLUPS": round(nodes / (step * 1e-3) / 1e6, 1),
                         "stream_collide_ms": round(kt["stream_collide"], 4),
+                        "stream_collide_GBs": round(nodes * bpn / (kt["stream_collide"] * 1e-3) / 1e9, 1),
+                        "bytes_per_node": bpn,
                         "error_vs_fp64_oracle_crop": {k: float(f"{v:.3g}") for k, v in err.items()}}
+        if kt_pair is not None:
+            out[storage]["stream_collide_ms_two_nodes_per_thread"] = round(kt_pair, 4)
     for storage in ("f16", "bf16"):
         out[storage]["speedup_step_vs_f32"] = round(out["f32"]["step_ms"] / out[storage]["step_ms"], 3)
         out[storage]["speedup_kernel_vs_f32"] = round(out["f32"]["stream_collide_ms"] / out[storage]["stream_collide_ms"], 3)
-    out["workload"] = "sed3d full size for speed; 40x40x64 crop, 8 spheres, 50 steps for the error"
+    out["workload"] = "sed3d full size for speed; 64x64x128 crop, 31 spheres, 50 steps for the error"
     return out
+
+
+def ensemble_study(torch, flush, steps):
+    """Batched ensemble of 32 uneven thermosensitive sphere-sedimentation
+    boxes (edges 64..128, Ra log-uniform 1e3..1e5, 50-400 spheres), all
+    advanced by one graph launch per step; timed before and after the
+    autotuner, and against launching every box's own step graph in turn."""
+    import workloads as W
+    from paper_1502_01159_gb300 import Ensemble
+    cases = W.ensemble()
+    nodes = sum(c["shape"][0] * c["shape"][1] * c["shape"][2] for c in cases)
+    n_p = sum(len(c["particles"]["R"]) for c in cases)
+    ens = Ensemble(cases)
+    s = ens.stream
+
+    def timed(k, fn):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for i in range(k):
+            with torch.cuda.stream(s):
+                flush.fill_(i & 0xFF)
+            ev[i][0].record(s)
+            fn()
+            ev[i][1].record(s)
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+    ens.step(3)
+    torch.cuda.synchronize()
+    ms_default = timed(steps, lambda: ens.step(1))
+    t0 = time.perf_counter()
+    choice = ens.autotune(reps=2)
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    ens.step(3)
+    torch.cuda.synchronize()
+    ms_tuned = timed(steps, lambda: ens.step(1))
+    # the same boxes stepped one context at a time (each its own graph launch)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for _ in range(steps):
+        for b in ens.boxes:
+            b.step(1)
+    torch.cuda.synchronize()
+    ms_separate_wall = (time.perf_counter() - t1) * 1e3 / steps
+    t1 = time.perf_counter()
+    for _ in range(steps):
+        ens.step(1)
+    torch.cuda.synchronize()
+    ms_ensemble_wall = (time.perf_counter() - t1) * 1e3 / steps
+    kps = ens.kernels_per_step()
+    diag = [b.diagnostics()["nonfinite"] for b in ens.boxes]
+    ens.close()
+    lat = {}
+    for c_lat, c_dem in choice:
+        lat[str(c_lat)] = lat.get(str(c_lat), 0) + 1
+    return {"workload": f"{len(cases)} boxes, edges 64..128 (sum {nodes} nodes), {n_p} thermosensitive spheres d=8, "
+                        "Ra log-uniform 1e3..1e5, D3Q19+D3Q7 FP32, Hertz, 10 DEM substeps",
+            "MLUPS": round(nodes / (ms_tuned * 1e-3) / 1e6, 1), "ms_per_step": round(ms_tuned, 4),
+            "ms_per_step_untuned": round(ms_default, 4),
+            "particle_steps_per_s": round(n_p / (ms_tuned * 1e-3), 1),
+            "graph_launches_per_step": 1, "kernels_per_step": kps,
+            "wall_ms_per_step_one_graph": round(ms_ensemble_wall, 4),
+            "wall_ms_per_step_box_by_box": round(ms_separate_wall, 4),
+            "autotune": {"seconds": round(tune_s, 2), "lattice_threads_chosen": lat},
+            "nonfinite_boxes": int(sum(1 for d in diag if d))}
 
 
 def run_ours(args):
@@ -307,7 +391,7 @@ def run_ours(args):
         dist.barrier()
         __graft_entry__.build()
 
-    case, desc = workload(args.workload)
+    case, desc = workload(args.workload, args.storage)
     nodes = case["shape"][0] * case["shape"][1] * case["shape"][2]
     n_p = len(case["particles"]["R"]) if case.get("particles") else 0
 
@@ -346,7 +430,7 @@ def run_ours(args):
     peak, peak_kind = peaks()
     bpn = bytes_per_node(case)
     achieved = nodes * bpn / (kt["stream_collide"] * 1e-3) / 1e9
-    traffic = traffic_record("k_stream_collide", args.workload)
+    traffic = traffic_record("k_stream_collide", args.workload if args.storage == "f32" else f"{args.workload}_{args.storage}")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "kernel": "k_stream_collide", "bytes_per_node": bpn, "nodes_per_launch": nodes,
@@ -360,7 +444,7 @@ def run_ours(args):
         e2e = e2e_run(case, args.steps, torch)
 
     secondary = None
-    if rank == 0 and world == 1 and args.workload == "sed2d" and not args.no_3d:
+    if rank == 0 and world == 1 and args.workload == "sed2d" and args.storage == "f32" and not args.no_3d:
         c3, d3 = workload("sed3d")
         sim3, ms3 = measure_gpu(c3, max(5, args.steps // 2), 3, torch, flush)
         kt3 = kernel_times(sim3, 5, torch, flush)
@@ -376,8 +460,13 @@ def run_ours(args):
                                   "kernel": "k_stream_collide", "bytes_per_node": b3, "nodes_per_launch": n3}}
         sim3.close()
 
+    ensemble = None
+    if rank == 0 and world == 1 and args.workload == "sed2d" and args.storage == "f32" and not args.no_ensemble:
+        ensemble = ensemble_study(torch, flush, max(5, args.steps // 2))
+
     precision = None
-    if rank == 0 and world == 1 and args.workload == "sed2d" and not args.no_3d and not args.no_precision:
+    if (rank == 0 and world == 1 and args.workload == "sed2d" and args.storage == "f32" and not args.no_3d
+            and not args.no_precision):
         precision = precision_study(torch, flush)
 
     if rank == 0:
@@ -385,6 +474,7 @@ def run_ours(args):
             "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "storage": args.storage,
             "config": {"workload": desc, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "flushed before every timed step (256 MB write); per-step device time excludes the flush",
                        "wall_s_timed_region": round(t_wall, 3)},
@@ -401,6 +491,8 @@ def run_ours(args):
             line["secondary"] = secondary
         if precision:
             line["precision"] = precision
+        if ensemble:
+            line["ensemble"] = ensemble
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -414,11 +506,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sed2d", choices=["sed2d", "sed3d", "sed3d_mid"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="population storage (arithmetic is FP32 in every case)")
     ap.add_argument("--cpu-steps", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -205,10 +205,14 @@ pibm_status pibm_step_timed(pibm_ctx* ctx, double* ms);
 /* Launch-shape tuning (used by autotuning sweeps; results do not depend on it).
  * PIBM_TUNE_DEM_PARTICLES_PER_CTA: particles per CTA of the DEM cluster
  * (0 = default 32; at most 16 CTAs and 640 particles per CTA).
- * PIBM_TUNE_SCALAR_LATTICE: 1 = one node per thread also for FP16 / BF16
- * storage (default 0: two nodes per thread with 32-bit accesses when nx is a
- * multiple of 64). */
-enum { PIBM_TUNE_DEM_PARTICLES_PER_CTA = 0, PIBM_TUNE_SCALAR_LATTICE = 1 };
+ * PIBM_TUNE_PAIR_LATTICE: 1 = two nodes per thread with 32-bit accesses for
+ * FP16 / BF16 storage when nx is a multiple of 64 (default 0: one node per
+ * thread, the faster form on GB300).
+ * PIBM_TUNE_LATTICE_THREADS: threads per block of the collide-and-stream
+ * kernel, 0 (default shape) or a multiple of 32 in [32, 512]; a block spans
+ * min(threads, row width rounded up to 32) nodes of a row and as many rows as
+ * the remaining factor gives. */
+enum { PIBM_TUNE_DEM_PARTICLES_PER_CTA = 0, PIBM_TUNE_PAIR_LATTICE = 1, PIBM_TUNE_LATTICE_THREADS = 2 };
 pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value);
 
 /* Number of kernels one lattice step launches (for launch accounting). */
@@ -241,6 +245,45 @@ pibm_status pibm_kernels_per_step(pibm_ctx* ctx, int* n);
  * so calls that overlap on the GPU (on different streams) race. */
 pibm_status pibm_contacts_static(const double* d_X, const double* d_R, int n, int dim, const int32_t* nlat,
                                  double cell_size, int32_t* d_pairs, int cap, int32_t* d_count, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched ensemble (no counterpart in the paper, which runs one case at a
+ * time): n_boxes independent lattices -- sizes, Rayleigh numbers, particle
+ * sets and every other descriptor field may differ -- advanced together by
+ * one CUDA graph launch per lattice step on the ensemble stream.  Each box is
+ * an ordinary context, owned by the ensemble: set it up and read it back with
+ * the per-context calls on the handle pibm_ensemble_box returns (never
+ * pibm_destroy it).  Results of every box are identical to stepping it alone.
+ *   descs: n_boxes descriptors (copied).  stream: the ensemble's
+ *   cudaStream_t or NULL (one is created).  alloc: device memory hook shared
+ *   by all boxes, or NULL.
+ * Errors: as pibm_create for any box (the message names the box). */
+typedef struct pibm_ensemble pibm_ensemble;
+pibm_status pibm_ensemble_create(const pibm_desc* descs, int n_boxes, void* stream, const pibm_allocator* alloc,
+                                 pibm_ensemble** out);
+pibm_status pibm_ensemble_destroy(pibm_ensemble* e);
+/* The context of box b (0 <= b < n_boxes), owned by the ensemble. */
+pibm_status pibm_ensemble_box(pibm_ensemble* e, int b, pibm_ctx** out);
+/* nsteps lattice steps of every box, one graph launch each.  All boxes must
+ * be at the same time step (PIBM_ERR_STATE otherwise); a box whose set-up
+ * changed since the last call is re-captured automatically.  Ordered after
+ * work already queued on the boxes' streams; later per-box calls are ordered
+ * after it.  Device-side errors of a box are reported by the next call. */
+pibm_status pibm_ensemble_step(pibm_ensemble* e, int nsteps);
+/* Kernels one ensemble step launches (sum over the boxes). */
+pibm_status pibm_ensemble_kernels_per_step(pibm_ensemble* e, int* n);
+/* Autotuner: for each box in turn, time reps un-graphed steps (CUDA events)
+ * of each of five candidate launch shapes -- PIBM_TUNE_LATTICE_THREADS in
+ * {default, 64, 128, 256, 512} paired with PIBM_TUNE_DEM_PARTICLES_PER_CTA in
+ * {default, 16, 48, 64, 96} (shapes a box cannot take time the default) --
+ * and keep the fastest lattice and DEM shapes.  These are real steps: every
+ * box advances by 5*reps steps (launch shapes change no result).  choice:
+ * NULL or 2*n_boxes ints receiving (lattice threads, DEM particles per CTA)
+ * per box, 0 meaning the default. */
+pibm_status pibm_ensemble_autotune(pibm_ensemble* e, int reps, int32_t* choice);
+/* Last error message of the ensemble (or of a failed create when e is NULL:
+ * use pibm_last_error(NULL, ...)); returns its length. */
+int pibm_ensemble_last_error(pibm_ensemble* e, char* buf, size_t n);
 
 const char* pibm_status_string(pibm_status s);
 /* Copies the last error message of the context (or of the last failed

@@ -17,7 +17,7 @@ PERIODIC, WALL = 0, 1
 ADIABATIC, ISOTHERMAL = 0, 1
 SPRING_DASHPOT, HERTZ_MD = 0, 1
 STORE_F32, STORE_F64, STORE_F16, STORE_BF16 = 0, 1, 2, 3
-TUNE_DEM_PARTICLES_PER_CTA, TUNE_SCALAR_LATTICE = 0, 1
+TUNE_DEM_PARTICLES_PER_CTA, TUNE_PAIR_LATTICE, TUNE_LATTICE_THREADS = 0, 1, 2
 STORAGE = {"f32": STORE_F32, "f64": STORE_F64, "f16": STORE_F16, "bf16": STORE_BF16}
 FIELDS = {"rho": 0, "ux": 1, "uy": 2, "uz": 3, "T": 4, "FBx": 5, "FBy": 6, "FBz": 7, "QB": 8}
 
@@ -70,6 +70,13 @@ SIGNATURES = {
     "pibm_save": (C.c_int, [_P, C.c_char_p]),
     "pibm_load": (C.c_int, [_P, C.c_char_p]),
     "pibm_contacts_static": (C.c_int, [_P, _P, C.c_int, C.c_int, _I32, C.c_double, _P, C.c_int, _P, _P]),
+    "pibm_ensemble_create": (C.c_int, [C.POINTER(pibm_desc), C.c_int, _P, C.POINTER(pibm_allocator), C.POINTER(_P)]),
+    "pibm_ensemble_destroy": (C.c_int, [_P]),
+    "pibm_ensemble_box": (C.c_int, [_P, C.c_int, C.POINTER(_P)]),
+    "pibm_ensemble_step": (C.c_int, [_P, C.c_int]),
+    "pibm_ensemble_kernels_per_step": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "pibm_ensemble_autotune": (C.c_int, [_P, C.c_int, _I32]),
+    "pibm_ensemble_last_error": (C.c_int, [_P, C.c_char_p, C.c_size_t]),
     "pibm_status_string": (C.c_char_p, [C.c_int]),
     "pibm_last_error": (C.c_int, [_P, C.c_char_p, C.c_size_t]),
 }
@@ -111,6 +118,23 @@ def _f64(a, shape=None):
     return a.reshape(shape) if shape is not None else a
 
 
+def desc_from_case(case: dict) -> pibm_desc:
+    """The C descriptor of a workload dict (see workloads.py)."""
+    d = pibm_desc()
+    d.dim = case["dim"]
+    d.nx, d.ny, d.nz = case["shape"]
+    d.storage = STORAGE[case.get("storage", "f32")]
+    d.Ra, d.Pr, d.U_c, d.L_c = case["Ra"], case["Pr"], case["U_c"], case["L_c"]
+    d.T_ref, d.T_init = case["T_ref"], case["T_init"]
+    d.buoyancy, d.gravity_axis = int(case["buoyancy"]), case["gravity_axis"]
+    d.body_force = (C.c_double * 3)(*case["body_force"])
+    d.g_particle = (C.c_double * 3)(*case["g_particle"])
+    d.dem_substeps = case["dem_substeps"]
+    d.kappa_T, d.cell_size, d.nu_dT = case["kappa_T"], case["cell_size"], case["nu_dT"]
+    d.pibm = int(case["pibm"])
+    return d
+
+
 class TorchAllocator:
     """Device memory for the library from PyTorch's caching allocator.  Each
     allocation is a uint8 CUDA tensor kept alive until the library frees it."""
@@ -144,21 +168,10 @@ class Simulation:
     ``use_torch=True`` (default) device memory comes from PyTorch and the
     work is ordered on a dedicated torch CUDA stream."""
 
-    def __init__(self, case: dict, use_torch: bool = True, device: int = 0):
+    def __init__(self, case: dict, use_torch: bool = True, device: int = 0, _handle=None):
         self.L = load()
         self.case = case
-        d = pibm_desc()
-        d.dim = case["dim"]
-        d.nx, d.ny, d.nz = case["shape"]
-        d.storage = STORAGE[case.get("storage", "f32")]
-        d.Ra, d.Pr, d.U_c, d.L_c = case["Ra"], case["Pr"], case["U_c"], case["L_c"]
-        d.T_ref, d.T_init = case["T_ref"], case["T_init"]
-        d.buoyancy, d.gravity_axis = int(case["buoyancy"]), case["gravity_axis"]
-        d.body_force = (C.c_double * 3)(*case["body_force"])
-        d.g_particle = (C.c_double * 3)(*case["g_particle"])
-        d.dem_substeps = case["dem_substeps"]
-        d.kappa_T, d.cell_size, d.nu_dT = case["kappa_T"], case["cell_size"], case["nu_dT"]
-        d.pibm = int(case["pibm"])
+        d = desc_from_case(case)
         self.desc = d
         self.dim = d.dim
         self.shape = (d.nz, d.ny, d.nx)
@@ -167,22 +180,26 @@ class Simulation:
         self.np = 0
         self.allocator = None
         self.stream = None
-        stream_ptr = None
-        alloc_ptr = None
-        if use_torch:
-            import torch
-            dev = torch.device("cuda", device)
-            self.stream = torch.cuda.Stream(device=dev)
-            stream_ptr = C.c_void_p(self.stream.cuda_stream)
-            self.allocator = TorchAllocator(dev)
-            alloc_ptr = C.byref(self.allocator.struct)
-        h = C.c_void_p()
-        st = self.L.pibm_create(C.byref(d), stream_ptr, alloc_ptr, C.byref(h))
-        if st != PIBM_OK:
-            buf = C.create_string_buffer(512)
-            self.L.pibm_last_error(None, buf, 512)
-            raise PibmError(st, "pibm_create: " + buf.value.decode())
-        self.h = h
+        self._owned = _handle is None
+        if _handle is not None:  # a box of an ensemble: the ensemble owns the context
+            self.h = _handle
+        else:
+            stream_ptr = None
+            alloc_ptr = None
+            if use_torch:
+                import torch
+                dev = torch.device("cuda", device)
+                self.stream = torch.cuda.Stream(device=dev)
+                stream_ptr = C.c_void_p(self.stream.cuda_stream)
+                self.allocator = TorchAllocator(dev)
+                alloc_ptr = C.byref(self.allocator.struct)
+            h = C.c_void_p()
+            st = self.L.pibm_create(C.byref(d), stream_ptr, alloc_ptr, C.byref(h))
+            if st != PIBM_OK:
+                buf = C.create_string_buffer(512)
+                self.L.pibm_last_error(None, buf, 512)
+                raise PibmError(st, "pibm_create: " + buf.value.decode())
+            self.h = h
         for face, (kind, thermal, Tw) in enumerate(case["walls"]):
             self.set_wall(face, kind, thermal, Tw)
         law = case.get("contact")
@@ -204,7 +221,8 @@ class Simulation:
 
     def close(self):
         if getattr(self, "h", None):
-            self.L.pibm_destroy(self.h)
+            if self._owned:
+                self.L.pibm_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -358,3 +376,75 @@ def contacts_static(X, R, dim, shape, cell_size, cap=None, stream=None):
     s.synchronize()
     total, flag = (int(v) for v in count.tolist())
     return pairs[: 2 * min(total, cap)].view(-1, 2), flag
+
+
+class Ensemble:
+    """Independent boxes advanced together, one graph launch per step
+    (pibm_ensemble_*).  ``boxes[b]`` is a Simulation view of box b for set-up
+    and read-back; the ensemble owns the contexts."""
+
+    def __init__(self, cases, use_torch: bool = True, device: int = 0):
+        self.L = load()
+        n = len(cases)
+        descs = (pibm_desc * n)(*[desc_from_case(c) for c in cases])
+        self.allocator = None
+        self.stream = None
+        stream_ptr = alloc_ptr = None
+        if use_torch:
+            import torch
+            dev = torch.device("cuda", device)
+            self.stream = torch.cuda.Stream(device=dev)
+            stream_ptr = C.c_void_p(self.stream.cuda_stream)
+            self.allocator = TorchAllocator(dev)
+            alloc_ptr = C.byref(self.allocator.struct)
+        h = C.c_void_p()
+        st = self.L.pibm_ensemble_create(descs, n, stream_ptr, alloc_ptr, C.byref(h))
+        if st != PIBM_OK:
+            buf = C.create_string_buffer(512)
+            self.L.pibm_last_error(None, buf, 512)
+            raise PibmError(st, "pibm_ensemble_create: " + buf.value.decode())
+        self.h = h
+        self.boxes = []
+        for b, case in enumerate(cases):
+            bh = C.c_void_p()
+            self._check(self.L.pibm_ensemble_box(self.h, b, C.byref(bh)), "pibm_ensemble_box")
+            self.boxes.append(Simulation(case, _handle=bh))
+
+    def _check(self, st, what):
+        if st != PIBM_OK:
+            buf = C.create_string_buffer(512)
+            self.L.pibm_ensemble_last_error(self.h, buf, 512)
+            raise PibmError(st, f"{what}: {buf.value.decode()}")
+
+    def step(self, n: int = 1):
+        self._check(self.L.pibm_ensemble_step(self.h, int(n)), "pibm_ensemble_step")
+
+    def autotune(self, reps: int = 2):
+        """Per-box launch shapes chosen by timing; returns [(lattice threads,
+        DEM particles per CTA)] (0 = default).  Advances every box 5*reps steps."""
+        out = np.zeros(2 * len(self.boxes), dtype=np.int32)
+        self._check(self.L.pibm_ensemble_autotune(self.h, int(reps), out.ctypes.data_as(_I32)),
+                    "pibm_ensemble_autotune")
+        return [(int(out[2 * b]), int(out[2 * b + 1])) for b in range(len(self.boxes))]
+
+    def kernels_per_step(self) -> int:
+        n = C.c_int()
+        self._check(self.L.pibm_ensemble_kernels_per_step(self.h, C.byref(n)), "pibm_ensemble_kernels_per_step")
+        return n.value
+
+    @property
+    def t(self):
+        return self.boxes[0].t
+
+    def close(self):
+        if getattr(self, "h", None):
+            for b in self.boxes:
+                b.h = None
+            self.L.pibm_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -72,6 +72,7 @@ static void dfree_group(pibm_ctx* ctx, int group) {
 }
 
 static void drop_graphs(Ctx& c) {
+    c.gen++;  // graphs that captured this context (its own and any ensemble's) are stale
     for (int p = 0; p < 2; p++) {
         if (c.graph_ok[p]) cudaGraphExecDestroy(c.graph[p]);
         c.graph_ok[p] = 0;
@@ -135,6 +136,33 @@ static pibm_status prime(pibm_ctx* ctx) {
     PCHECK(cudaStreamSynchronize(c.s0));
     return PIBM_OK;
 }
+
+// The launches of one lattice step at parity par, ordered on s0 with the
+// DEM branch forked onto s1 and joined back (s0 may be capturing).
+cudaError_t pibm::record_step(Ctx* cp, int par, int* kernels_out) {
+    Ctx& c = *cp;
+    cudaError_t e = cudaSuccess;
+    int kernels = 1;
+    auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    chk(cudaEventRecord(c.ev_fork, c.s0));
+    chk(cudaStreamWaitEvent(c.s1, c.ev_fork, 0));
+    if (c.np > 0) {
+        chk(launch_dem(&c, c.s1, c.desc.dem_substeps));  // particles t -> t+1, concurrent, launched first
+        chk(launch_coupling_clear(&c, c.s1, par ^ 1));  // free the other coupling set (read at t-1)
+        kernels++;
+    }
+    chk(launch_stream_collide(&c, c.s0, par));        // collide + stream, t -> t+1
+    chk(cudaEventRecord(c.ev_join, c.s1));
+    chk(cudaStreamWaitEvent(c.s0, c.ev_join, 0));
+    chk(launch_coupling(&c, c.s0, par ^ 1));         // coupling of time t+1
+    kernels += coupling_kernel_count(&c);
+    if (kernels_out) *kernels_out = kernels;
+    return e;
+}
+
+pibm::Ctx* pibm::ctx_state(pibm_ctx* ctx) { return &ctx->c; }
+
+pibm_status pibm::ctx_ready(pibm_ctx* ctx) { return check_config(ctx); }
 
 extern "C" {
 
@@ -587,21 +615,8 @@ static pibm_status capture(pibm_ctx* ctx, int par) {
     Ctx& c = ctx->c;
     cudaGraph_t graph;
     PCHECK(cudaStreamBeginCapture(c.s0, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    int kernels = 1;
-    auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-    chk(cudaEventRecord(c.ev_fork, c.s0));
-    chk(cudaStreamWaitEvent(c.s1, c.ev_fork, 0));
-    if (c.np > 0) {
-        chk(launch_dem(&c, c.s1, c.desc.dem_substeps));  // particles t -> t+1, concurrent, launched first
-        chk(launch_coupling_clear(&c, c.s1, par ^ 1));  // free the other coupling set (read at t-1)
-        kernels++;
-    }
-    chk(launch_stream_collide(&c, c.s0, par));        // collide + stream, t -> t+1
-    chk(cudaEventRecord(c.ev_join, c.s1));
-    chk(cudaStreamWaitEvent(c.s0, c.ev_join, 0));
-    chk(launch_coupling(&c, c.s0, par ^ 1));         // coupling of time t+1
-    kernels += coupling_kernel_count(&c);
+    int kernels = 0;
+    cudaError_t e = record_step(&c, par, &kernels);
     cudaError_t e2 = cudaStreamEndCapture(c.s0, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (e2 == cudaSuccess) cudaGraphDestroy(graph);
@@ -787,9 +802,16 @@ pibm_status pibm_time(pibm_ctx* ctx, int64_t* t) {
 pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value) {
     if (!ctx) return PIBM_ERR_ARG;
     Ctx& c = ctx->c;
-    if (knob == PIBM_TUNE_SCALAR_LATTICE) {
+    if (knob == PIBM_TUNE_LATTICE_THREADS) {
+        if (value != 0 && (value < 32 || value > 512 || value % 32 != 0))
+            return fail(ctx, PIBM_ERR_ARG, "lattice threads per block: 0 or a multiple of 32 in [32, 512]");
+        c.tune_lattice_threads = value;
+        drop_graphs(c);
+        return PIBM_OK;
+    }
+    if (knob == PIBM_TUNE_PAIR_LATTICE) {
         if (value != 0 && value != 1) return fail(ctx, PIBM_ERR_ARG, "invalid tuning value");
-        c.tune_scalar_lattice = value;
+        c.tune_pair_lattice = value;
         drop_graphs(c);
         return PIBM_OK;
     }

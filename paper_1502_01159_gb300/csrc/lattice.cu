@@ -65,28 +65,55 @@ __device__ __forceinline__ void collide_node(R* s, R* sg, R fbx, R fby, R fbz, R
     const R ux = (jx + half * Fx) * inv_rho, uy = (jy + half * Fy) * inv_rho, uz = (jz + half * Fz) * inv_rho;
     const R uu = ux * ux + uy * uy + uz * uz;
     const R uF = ux * Fx + uy * Fy + uz * Fz;
-    const R omf = (R)P.omf, cf = (R)P.cf;
+    const R omf = (R)P.omf, cf = (R)P.cf, om1 = (R)1 - omf;
+    // Opposite directions i, i' share e.u and e.F up to sign, so equilibrium
+    // and forcing split into parts even and odd in e:
+    //   s_i^eq = w (p0 + 4.5 rho (e.u)^2) + w 3 rho e.u,  p0 = drho - 1.5 rho u^2
+    //   F_i    = w cf (9 (e.u)(e.F) - 3 u.F) + w 3 cf e.F
+    // and the update keeps the non-equilibrium form (small correction added to
+    // the equilibrium, no cancellation of two large terms):
+    //   s_i* = s_i^eq + F_i + (1 - 1/tau) (s_i - s_i^eq)
+    const R p0 = drho - (R)1.5 * rho * uu, q0 = (R)4.5 * rho, r0 = (R)3 * rho;
+    const R k0 = (R)-3 * cf * uF, c9 = (R)9 * cf, c3 = (R)3 * cf;
+    {
+        const R seq = (R)L::w(0) * p0;
+        s[0] = seq + (R)L::w(0) * k0 + om1 * (s[0] - seq);
+    }
 #pragma unroll
-    for (int i = 0; i < L::Q; i++) {
+    for (int i = 1; i < L::Q; i++) {
+        if (L::opp(i) < i) continue;
+        const int io = L::opp(i);
         const R wi = (R)L::w(i);
         R eu = 0, eF = 0;
         if (L::ex(i)) { eu += L::ex(i) * ux; eF += L::ex(i) * Fx; }
         if (L::ey(i)) { eu += L::ey(i) * uy; eF += L::ey(i) * Fy; }
         if (L::ez(i)) { eu += L::ez(i) * uz; eF += L::ez(i) * Fz; }
-        const R seq = wi * (drho + rho * ((R)3 * eu + (R)4.5 * eu * eu - (R)1.5 * uu));
-        const R Fi = cf * wi * ((R)3 * (eF - uF) + (R)9 * eu * eF);
-        s[i] = s[i] + omf * (seq - s[i]) + Fi;
+        const R es = wi * (p0 + q0 * eu * eu), ea = wi * r0 * eu;     // even / odd equilibrium parts
+        const R fs = wi * (k0 + c9 * eu * eF), fa = wi * c3 * eF;      // even / odd forcing parts
+        const R ni = s[i] - es - ea, no = s[io] - es + ea;             // non-equilibrium parts
+        s[i] = (es + fs) + (ea + fa) + om1 * ni;
+        s[io] = (es + fs) - (ea + fa) + om1 * no;
     }
-    const R omg = (R)P.omg, gq = (R)P.cg * qb;
+    // thermal, the same split: s_gk^eq = w_k dT + w_k (T / cs_T^2) e.u, source w_k cg Q_B
+    const R omg = (R)P.omg, om1g = (R)1 - omg;
+    const R gq = (R)P.cg * qb, kT = T * (R)L::inv_csT2;
+    {
+        const R seq = (R)L::wg(0) * dT;
+        sg[0] = seq + (R)L::wg(0) * gq + om1g * (sg[0] - seq);
+    }
 #pragma unroll
-    for (int k = 0; k < L::QG; k++) {
+    for (int k = 1; k < L::QG; k++) {
+        if (L::opp(k) < k) continue;
+        const int ko = L::opp(k);
         const R wk = (R)L::wg(k);
         R eu = 0;
         if (L::ex(k)) eu += L::ex(k) * ux;
         if (L::ey(k)) eu += L::ey(k) * uy;
         if (L::ez(k)) eu += L::ez(k) * uz;
-        const R sgeq = wk * (dT + T * eu * (R)L::inv_csT2);
-        sg[k] = sg[k] + omg * (sgeq - sg[k]) + wk * gq;
+        const R es = wk * dT, ea = wk * kT * eu, src = wk * gq;
+        const R ni = sg[k] - es - ea, no = sg[ko] - es + ea;
+        sg[k] = (es + src) + ea + om1g * ni;
+        sg[ko] = (es + src) - ea + om1g * no;
     }
 }
 
@@ -195,22 +222,26 @@ struct AAOffsets {
 };
 
 template <int D, typename S, int PARITY>
-__global__ void __launch_bounds__(256) k_stream_collide(Geo G, S* __restrict__ f, S* __restrict__ g,
+__global__ void __launch_bounds__(512) k_stream_collide(Geo G, S* __restrict__ f, S* __restrict__ g,
                                                         const typename Store<S>::V4* __restrict__ fb,
                                                         const uint8_t* __restrict__ flags,
                                                         CollideParams<typename Store<S>::R> P, AAOffsets O) {
     using L = Lat<D>;
     using R = typename Store<S>::R;
+    // block: blockDim.x nodes of a row (a multiple of 32) x blockDim.y rows
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= G.nx) return;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    if (x >= G.nx || y >= G.ny) return;
     const long long n = node_index(G, x, y, z);
     const long long sy = G.nx, sz = (long long)G.nx * G.ny;
-    // y and z are uniform across the block, so this test never splits a warp
+    // y and z are uniform across a warp, so this test never splits one
     const bool inner_yz = y > 0 && y < G.ny - 1 && (D == 2 || (z > 0 && z < G.nz - 1));
     R s[L::Q], sg[L::QG];
-    // lanes on the x faces need the wrap / bounce fix-up (warp-divergent only there)
-    const bool xedge = x == 0 || x == G.nx - 1;
+    // warps holding a node on an x face take the per-lane-select path as a
+    // whole (it is exact for interior lanes too), so no warp splits in two;
+    // blockDim.x is a multiple of 32, so x & ~31 is the warp's first node
+    const int xw = x & ~31;
+    const bool xedge = xw == 0 || xw + 31 >= G.nx - 1;
     if (PARITY == 0) {
 #pragma unroll
         for (int i = 0; i < L::Q; i++) s[i] = Store<S>::ldf(f[n + O.ld[i]]);
@@ -282,25 +313,20 @@ static CollideParams<R> collide_params(const Ctx* c) {
     return P;
 }
 
-// Generic odd-step store of one node's post-collision populations (any
-// boundary).  side = -1 or +1 restricts it to the directions that leave the
-// lattice through that x face (the rest were stored by the pair path).
+// Generic odd-step store of one node's post-collision populations (any boundary).
 template <int D, typename S>
 __device__ __forceinline__ void store_node(const Geo& G, const CollideParams<typename Store<S>::R>& P, S* f, S* g, int x,
-                                           int y, int z, const typename Store<S>::R* s, const typename Store<S>::R* sg,
-                                           int side) {
+                                           int y, int z, const typename Store<S>::R* s, const typename Store<S>::R* sg) {
     using L = Lat<D>;
     using R = typename Store<S>::R;
 #pragma unroll
     for (int i = 0; i < L::Q; i++) {
-        if (side != 0 && L::ex(i) != side) continue;
         long long idx;
         post_slot(G, x, y, z, L::ex(i), L::ey(i), L::ez(i), i, L::opp(i), 1, idx);
         f[idx] = Store<S>::stf(s[i]);
     }
 #pragma unroll
     for (int k = 0; k < L::QG; k++) {
-        if (side != 0 && L::ex(k) != side) continue;
         long long idx;
         int face = post_slot(G, x, y, z, L::ex(k), L::ey(k), L::ez(k), k, L::opp(k), 1, idx);
         R v = sg[k];
@@ -310,157 +336,166 @@ __device__ __forceinline__ void store_node(const Geo& G, const CollideParams<typ
 }
 
 // ---------------------------------------------------------------------------
-// 16-bit storage, two nodes per thread.  Populations of the pair (x0, x0+1)
-// move as one 32-bit half2 / bfloat162 word with a packed conversion.  In odd
-// steps a direction with e_x = +1 reads x-1 (the upper half of the left
-// neighbour lane's aligned pair, via a warp shuffle) and e_x = -1 reads x+1
-// (the lower half of the right lane's pair); the lanes at either end of the
-// warp fetch the one element beyond it with a scalar access.  Stores mirror
-// this.  Lanes holding a node on an x face run the generic path for that node
-// as well (wrap or bounce-back); accesses that would cross the row end are
-// skipped there.  Requires nx to be a multiple of 64 (whole warps per row).
-template <typename S> struct Pair;
-template <> struct Pair<__half> {
-    using T = __half2;
-    static __device__ __forceinline__ float2 ldf(T v) { float2 r = __half22float2(v); return make_float2(r.x * 0.0009765625f, r.y * 0.0009765625f); }
-    static __device__ __forceinline__ float2 ldg(T v) { float2 r = __half22float2(v); return make_float2(r.x * 0.00390625f, r.y * 0.00390625f); }
-    static __device__ __forceinline__ T stf(float a, float b) { return __floats2half2_rn(a * 1024.0f, b * 1024.0f); }
-    static __device__ __forceinline__ T stg(float a, float b) { return __floats2half2_rn(a * 256.0f, b * 256.0f); }
-};
-template <> struct Pair<__nv_bfloat16> {
-    using T = __nv_bfloat162;
-    static __device__ __forceinline__ float2 ldf(T v) { return __bfloat1622float2(v); }
-    static __device__ __forceinline__ float2 ldg(T v) { return __bfloat1622float2(v); }
-    static __device__ __forceinline__ T stf(float a, float b) { return __floats2bfloat162_rn(a, b); }
-    static __device__ __forceinline__ T stg(float a, float b) { return __floats2bfloat162_rn(a, b); }
-};
+// 16-bit storage, two nodes per thread.  The populations of the pair (x0, x0+1)
+// move as 32-bit words (low half node x0, high half node x0+1) and stay packed
+// in registers; the two nodes are collided one after the other (unpack to
+// FP32, collide, repack into the same words), so only one node's FP32 state is
+// live at a time.  In odd steps a direction with e_x = +1 reads x-1, the high
+// half of the left lane's word, through a warp shuffle; e_x = -1 reads x+1,
+// the low half of the right lane's word.  The element beyond the warp comes
+// from a 16-bit load that every lane issues at an in-row address (no branch,
+// and the sectors are the ones the word loads touch); at an x face that
+// address is the wrapped element or, at a wall, the node's own slot
+// (bounce-back; anti-bounce-back of the thermal populations is applied in
+// FP32 after unpacking and before repacking).  Stores mirror the loads.  Rows
+// on a y or z face take the generic path, one node at a time.  Requires nx to
+// be a multiple of 64 (whole warps per row).
+template <typename S> __device__ __forceinline__ S bits_to(uint32_t b);
+template <> __device__ __forceinline__ __half bits_to<__half>(uint32_t b) { return __ushort_as_half((unsigned short)b); }
+template <> __device__ __forceinline__ __nv_bfloat16 bits_to<__nv_bfloat16>(uint32_t b) {
+    return __ushort_as_bfloat16((unsigned short)b);
+}
+__device__ __forceinline__ uint32_t to_bits(__half v) { return __half_as_ushort(v); }
+__device__ __forceinline__ uint32_t to_bits(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
+__device__ __forceinline__ uint32_t ld32(const void* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ void st32(void* p, uint32_t v) { *reinterpret_cast<uint32_t*>(p) = v; }
+__device__ __forceinline__ uint32_t ld16(const void* p) { return *reinterpret_cast<const unsigned short*>(p); }
+__device__ __forceinline__ void st16(void* p, uint32_t v) { *reinterpret_cast<unsigned short*>(p) = (unsigned short)v; }
+
+// Odd-step word (x0's value low, x0+1's value high) of one direction.  e is
+// the source element of node x0; own_lo / own_hi are the bounce-back slots of
+// the two nodes (plane i at the node itself).
+template <typename S>
+__device__ __forceinline__ uint32_t odd_gather(const S* p, long long e, int ex, int lane, bool lo_edge, bool hi_edge,
+                                               bool per, int nx, long long own_lo, long long own_hi) {
+    if (ex == 0) return ld32(p + e);
+    if (ex > 0) {  // node x reads x-1
+        const uint32_t v = ld32(p + e + 1);                      // elements (x0, x0+1)
+        const uint32_t left = __shfl_up_sync(0xffffffffu, v, 1);  // (x0-2, x0-1)
+        const uint32_t xe = ld16(p + (lo_edge ? (per ? e + nx : own_lo) : e));
+        return (lane == 0 ? xe : (left >> 16)) | (v << 16);
+    }
+    const uint32_t v = ld32(p + e - 1);                            // node x reads x+1; elements (x0, x0+1)
+    const uint32_t right = __shfl_down_sync(0xffffffffu, v, 1);     // (x0+2, x0+3)
+    const uint32_t xe = ld16(p + (hi_edge ? (per ? e + 1 - nx : own_hi) : e + 1));
+    return (v >> 16) | ((lane == 31 ? xe : (right & 0xffffu)) << 16);
+}
+
+// Odd-step stores of one direction: node x0 -> x0 + e_x, node x0+1 -> x0+1+e_x.
+// e is the destination element of node x0; own_lo / own_hi the bounce-back
+// slots (plane opp(i) at the node).  Each lane writes the aligned word
+// (x0, x0+1) of the destination row; the end lanes add the single element
+// that belongs to the neighbouring warp's word or lies beyond an x face.
+template <typename S>
+__device__ __forceinline__ void odd_scatter(S* p, long long e, int ex, int lane, bool lo_edge, bool hi_edge, bool per,
+                                            int nx, long long own_lo, long long own_hi, uint32_t w) {
+    if (ex == 0) {
+        st32(p + e, w);
+    } else if (ex > 0) {  // word (x0, x0+1) = (x0-1's value from the left lane, x0's value)
+        const uint32_t left = __shfl_up_sync(0xffffffffu, w, 1);
+        if (lane > 0) st32(p + e - 1, (left >> 16) | (w << 16));
+        else st16(p + e, w);
+        if (lane == 31) st16(p + (hi_edge ? (per ? e + 1 - nx : own_hi) : e + 1), w >> 16);
+    } else {  // word (x0, x0+1) = (x0+1's value, x0+2's value from the right lane)
+        const uint32_t right = __shfl_down_sync(0xffffffffu, w, 1);
+        if (lane < 31) st32(p + e + 1, (w >> 16) | (right << 16));
+        else st16(p + e + 1, w >> 16);
+        if (lane == 0) st16(p + (lo_edge ? (per ? e + nx : own_lo) : e), w);
+    }
+}
 
 template <int D, typename S, int PARITY>
-__global__ void __launch_bounds__(256) k_stream_collide_pair(Geo G, S* __restrict__ f, S* __restrict__ g,
+__global__ void __launch_bounds__(512) k_stream_collide_pair(Geo G, S* __restrict__ f, S* __restrict__ g,
                                                              const float4* __restrict__ fb, const uint8_t* __restrict__ flags,
                                                              CollideParams<float> P, AAOffsets O) {
     using L = Lat<D>;
-    using PT = typename Pair<S>::T;
     using St = Store<S>;
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
     const int lane = threadIdx.x & 31;
-    if (x0 >= G.nx) return;  // whole warps only: nx / 2 is a multiple of 32
+    if (x0 >= G.nx || y >= G.ny) return;  // whole warps only: nx / 2 and blockDim.x are multiples of 32
     const long long n0 = node_index(G, x0, y, z);
+    const long long N = G.N;
     const bool inner_yz = y > 0 && y < G.ny - 1 && (D == 2 || (z > 0 && z < G.nz - 1));
-    const bool lo_edge = x0 == 0, hi_edge = x0 + 1 == G.nx - 1;
-    float s0[L::Q], s1[L::Q], g0[L::QG], g1[L::QG];
+    const bool tile = flags[((long long)z * G.ny + y) * G.ntx + (x0 >> 5)] != 0;  // x0, x0+1 share a tile
+    if (PARITY == 1 && !inner_yz) {  // a y or z face row: generic addressing, one node at a time
+#pragma unroll 1
+        for (int h = 0; h < 2; h++) {
+            float s[L::Q], sg[L::QG];
+            load_node<D, S, float>(G, f, g, x0 + h, y, z, 1, s, sg);
+            float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (tile) b = fb[n0 + h];
+            collide_node<D, float>(s, sg, b.x, b.y, b.z, b.w, P);
+            store_node<D, S>(G, P, f, g, x0 + h, y, z, s, sg);
+        }
+        return;
+    }
+    const bool lo_edge = x0 == 0, hi_edge = x0 + 1 == G.nx - 1, per = G.per[0] != 0;
+    uint32_t wf[L::Q], wt[L::QG];
     if (PARITY == 0) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) {
-            float2 v = Pair<S>::ldf(*reinterpret_cast<const PT*>(f + n0 + O.ld[i]));
-            s0[i] = v.x, s1[i] = v.y;
-        }
+        for (int i = 0; i < L::Q; i++) wf[i] = ld32(f + n0 + O.ld[i]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) {
-            float2 v = Pair<S>::ldg(*reinterpret_cast<const PT*>(g + n0 + O.ld[k]));
-            g0[k] = v.x, g1[k] = v.y;
-        }
-    } else if (inner_yz) {
-#pragma unroll
-        for (int i = 0; i < L::Q; i++) {
-            const int ex = L::ex(i);
-            const long long e = n0 + O.src[i];  // source element of node x0
-            if (ex == 0) {
-                float2 v = Pair<S>::ldf(*reinterpret_cast<const PT*>(f + e));
-                s0[i] = v.x, s1[i] = v.y;
-            } else if (ex == 1) {  // node x reads x-1: (x0-1, x0)
-                float2 v = Pair<S>::ldf(*reinterpret_cast<const PT*>(f + e + 1));
-                float left = __shfl_up_sync(0xffffffffu, v.y, 1);
-                if (lane == 0) left = lo_edge ? 0.f : St::ldf(f[e]);
-                s0[i] = left, s1[i] = v.x;
-            } else {  // node x reads x+1: (x0+1, x0+2)
-                float2 v = Pair<S>::ldf(*reinterpret_cast<const PT*>(f + e - 1));
-                float right = __shfl_down_sync(0xffffffffu, v.x, 1);
-                if (lane == 31) right = hi_edge ? 0.f : St::ldf(f[e + 1]);
-                s0[i] = v.y, s1[i] = right;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < L::QG; k++) {
-            const int ex = L::ex(k);
-            const long long e = n0 + O.src[k];
-            if (ex == 0) {
-                float2 v = Pair<S>::ldg(*reinterpret_cast<const PT*>(g + e));
-                g0[k] = v.x, g1[k] = v.y;
-            } else if (ex == 1) {
-                float2 v = Pair<S>::ldg(*reinterpret_cast<const PT*>(g + e + 1));
-                float left = __shfl_up_sync(0xffffffffu, v.y, 1);
-                if (lane == 0) left = lo_edge ? 0.f : St::ldg(g[e]);
-                g0[k] = left, g1[k] = v.x;
-            } else {
-                float2 v = Pair<S>::ldg(*reinterpret_cast<const PT*>(g + e - 1));
-                float right = __shfl_down_sync(0xffffffffu, v.x, 1);
-                if (lane == 31) right = hi_edge ? 0.f : St::ldg(g[e + 1]);
-                g0[k] = v.y, g1[k] = right;
-            }
-        }
-        if (lo_edge) load_node<D, S, float>(G, f, g, x0, y, z, 1, s0, g0);
-        if (hi_edge) load_node<D, S, float>(G, f, g, x0 + 1, y, z, 1, s1, g1);
+        for (int k = 0; k < L::QG; k++) wt[k] = ld32(g + n0 + O.ld[k]);
     } else {
-        load_node<D, S, float>(G, f, g, x0, y, z, 1, s0, g0);
-        load_node<D, S, float>(G, f, g, x0 + 1, y, z, 1, s1, g1);
+#pragma unroll
+        for (int i = 0; i < L::Q; i++)
+            wf[i] = odd_gather(f, n0 + O.src[i], L::ex(i), lane, lo_edge, hi_edge, per, G.nx, n0 + i * N, n0 + 1 + i * N);
+#pragma unroll
+        for (int k = 0; k < L::QG; k++)
+            wt[k] = odd_gather(g, n0 + O.src[k], L::ex(k), lane, lo_edge, hi_edge, per, G.nx, n0 + k * N, n0 + 1 + k * N);
     }
-    float b0[4] = {0.f, 0.f, 0.f, 0.f}, b1[4] = {0.f, 0.f, 0.f, 0.f};
-    if (flags[((long long)z * G.ny + y) * G.ntx + (x0 >> 5)]) {  // x0 and x0+1 share a 32-node tile
-        const float4 v0 = fb[n0], v1 = fb[n0 + 1];
-        b0[0] = v0.x, b0[1] = v0.y, b0[2] = v0.z, b0[3] = v0.w;
-        b1[0] = v1.x, b1[1] = v1.y, b1[2] = v1.z, b1[3] = v1.w;
+    // anti-bounce-back at an isothermal x wall (odd steps; face 0 for node x0, face 1 for node x0+1)
+    const bool abb_lo = PARITY == 1 && lo_edge && !per && face_iso(G, 0);
+    const bool abb_hi = PARITY == 1 && hi_edge && !per && face_iso(G, 1);
+#pragma unroll 1
+    for (int h = 0; h < 2; h++) {
+        const int sh = 16 * h;
+        const uint32_t keep = 0xffff0000u >> sh;
+        float s[L::Q], sg[L::QG];
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) s[i] = St::ldf(bits_to<S>(wf[i] >> sh));
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) {
+            float v = St::ldg(bits_to<S>(wt[k] >> sh));
+            // incoming across the low face (e_x > 0) for node x0, the high face (e_x < 0) for node x0+1
+            if (L::ex(k) > 0 && h == 0 && abb_lo) v = P.abb[0] - v;
+            if (L::ex(k) < 0 && h == 1 && abb_hi) v = P.abb[1] - v;
+            sg[k] = v;
+        }
+        float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (tile) b = fb[n0 + h];
+        collide_node<D, float>(s, sg, b.x, b.y, b.z, b.w, P);
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) wf[i] = (wf[i] & keep) | (to_bits(St::stf(s[i])) << sh);
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) {
+            float v = sg[k];
+            // outgoing across the low face (e_x < 0) for node x0, the high face (e_x > 0) for node x0+1
+            if (L::ex(k) < 0 && h == 0 && abb_lo) v = P.abb[0] - v;
+            if (L::ex(k) > 0 && h == 1 && abb_hi) v = P.abb[1] - v;
+            wt[k] = (wt[k] & keep) | (to_bits(St::stg(v)) << sh);
+        }
     }
-    collide_node<D, float>(s0, g0, b0[0], b0[1], b0[2], b0[3], P);
-    collide_node<D, float>(s1, g1, b1[0], b1[1], b1[2], b1[3], P);
+    // Recompute the store addresses from an opaque copy of the node index:
+    // otherwise the compiler keeps the 26 load addresses (the same slots, in
+    // even steps) live in registers across both collisions.
+    long long ns;
+    asm volatile("mov.b64 %0, %1;" : "=l"(ns) : "l"(n0));
     if (PARITY == 0) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) *reinterpret_cast<PT*>(f + n0 + O.st[i]) = Pair<S>::stf(s0[i], s1[i]);
+        for (int i = 0; i < L::Q; i++) st32(f + ns + O.st[i], wf[i]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) *reinterpret_cast<PT*>(g + n0 + O.st[k]) = Pair<S>::stg(g0[k], g1[k]);
-    } else if (inner_yz) {
-#pragma unroll
-        for (int i = 0; i < L::Q; i++) {
-            const int ex = L::ex(i);
-            const long long e = n0 + O.dst[i];  // destination element of node x0
-            if (ex == 0) {
-                *reinterpret_cast<PT*>(f + e) = Pair<S>::stf(s0[i], s1[i]);
-            } else if (ex == 1) {  // x0 -> x0+1, x0+1 -> x0+2: this lane owns the word (x0, x0+1)
-                float left = __shfl_up_sync(0xffffffffu, s1[i], 1);
-                if (lane > 0) *reinterpret_cast<PT*>(f + e - 1) = Pair<S>::stf(left, s0[i]);
-                else f[e] = St::stf(s0[i]);
-                if (lane == 31 && !hi_edge) f[e + 1] = St::stf(s1[i]);
-            } else {  // x0 -> x0-1, x0+1 -> x0: this lane owns the word (x0, x0+1)
-                float right = __shfl_down_sync(0xffffffffu, s0[i], 1);
-                if (lane < 31) *reinterpret_cast<PT*>(f + e + 1) = Pair<S>::stf(s1[i], right);
-                else f[e + 1] = St::stf(s1[i]);
-                if (lane == 0 && !lo_edge) f[e] = St::stf(s0[i]);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < L::QG; k++) {
-            const int ex = L::ex(k);
-            const long long e = n0 + O.dst[k];
-            if (ex == 0) {
-                *reinterpret_cast<PT*>(g + e) = Pair<S>::stg(g0[k], g1[k]);
-            } else if (ex == 1) {
-                float left = __shfl_up_sync(0xffffffffu, g1[k], 1);
-                if (lane > 0) *reinterpret_cast<PT*>(g + e - 1) = Pair<S>::stg(left, g0[k]);
-                else g[e] = St::stg(g0[k]);
-                if (lane == 31 && !hi_edge) g[e + 1] = St::stg(g1[k]);
-            } else {
-                float right = __shfl_down_sync(0xffffffffu, g0[k], 1);
-                if (lane < 31) *reinterpret_cast<PT*>(g + e + 1) = Pair<S>::stg(g1[k], right);
-                else g[e + 1] = St::stg(g1[k]);
-                if (lane == 0 && !lo_edge) g[e] = St::stg(g0[k]);
-            }
-        }
-        if (lo_edge) store_node<D, S>(G, P, f, g, x0, y, z, s0, g0, -1);
-        if (hi_edge) store_node<D, S>(G, P, f, g, x0 + 1, y, z, s1, g1, +1);
+        for (int k = 0; k < L::QG; k++) st32(g + ns + O.st[k], wt[k]);
     } else {
-        store_node<D, S>(G, P, f, g, x0, y, z, s0, g0, 0);
-        store_node<D, S>(G, P, f, g, x0 + 1, y, z, s1, g1, 0);
+#pragma unroll
+        for (int i = 0; i < L::Q; i++)
+            odd_scatter(f, ns + O.dst[i], L::ex(i), lane, lo_edge, hi_edge, per, G.nx, ns + L::opp(i) * N,
+                        ns + 1 + L::opp(i) * N, wf[i]);
+#pragma unroll
+        for (int k = 0; k < L::QG; k++)
+            odd_scatter(g, ns + O.dst[k], L::ex(k), lane, lo_edge, hi_edge, per, G.nx, ns + L::opp(k) * N,
+                        ns + 1 + L::opp(k) * N, wt[k]);
     }
 }
 
@@ -480,11 +515,25 @@ static AAOffsets aa_offsets(const Geo& G) {
     return O;
 }
 
+// Block shape of the lattice kernels for a row of `width` threads: bx threads
+// along x (a multiple of 32, at most 256) times by rows.  The default keeps
+// 256 threads per block for rows of 256 or more, 128 for shorter rows; the
+// tuning knob sets the threads per block (32 .. 512) and so the rows per block.
+static void lattice_shape(const Ctx* c, int width, dim3& block, dim3& grid) {
+    const int w32 = (width + 31) / 32 * 32;
+    const int threads = c->tune_lattice_threads > 0 ? c->tune_lattice_threads : (w32 >= 256 ? 256 : 128);
+    const int bx = w32 < threads ? w32 : (threads < 256 ? threads : 256);
+    const int by = threads / bx > 0 ? threads / bx : 1;
+    block = dim3(bx, by, 1);
+    grid = dim3((width + bx - 1) / bx, (c->G.ny + by - 1) / by, c->G.nz);
+}
+
 template <int D, typename S>
 static cudaError_t pair_launch(Ctx* c, cudaStream_t s, int parity) {
     if constexpr (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value) {
         const int pairs = c->G.nx / 2;
-        dim3 block(pairs < 256 ? pairs : 256), grid((pairs + 255) / 256, c->G.ny, c->G.nz);
+        dim3 block, grid;
+        lattice_shape(c, pairs, block, grid);
         CollideParams<float> P = collide_params<float>(c);
         AAOffsets O = aa_offsets<D>(c->G);
         if (parity == 0)
@@ -501,9 +550,9 @@ static cudaError_t pair_launch(Ctx* c, cudaStream_t s, int parity) {
 template <int D, typename S>
 static cudaError_t sc_launch(Ctx* c, cudaStream_t s, int parity) {
     constexpr bool half = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
-    if (half && c->G.nx % 64 == 0 && !c->tune_scalar_lattice) return pair_launch<D, S>(c, s, parity);
-    dim3 block(256), grid((c->G.nx + 255) / 256, c->G.ny, c->G.nz);
-    if (c->G.nx <= 128) block.x = 128, grid.x = (c->G.nx + 127) / 128;
+    if (half && c->G.nx % 64 == 0 && c->tune_pair_lattice) return pair_launch<D, S>(c, s, parity);
+    dim3 block, grid;
+    lattice_shape(c, c->G.nx, block, grid);
     using R = typename Store<S>::R;
     CollideParams<R> P = collide_params<R>(c);
     AAOffsets O = aa_offsets<D>(c->G);

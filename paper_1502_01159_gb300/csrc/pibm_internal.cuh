@@ -275,7 +275,9 @@ struct Ctx {
     int adj_cap;
     int dem_cs;           // CTAs in the DEM cluster
     int tune_dem_particles_per_cta;  // 0: default (32)
-    int tune_scalar_lattice;         // 1: one node per thread also for 16-bit storage
+    int tune_pair_lattice;           // 1: two nodes per thread for 16-bit storage (nx a multiple of 64)
+    int tune_lattice_threads;        // 0: default block shape; else threads per lattice block
+    unsigned gen;                    // bumped whenever the captured step graphs become stale
     int* contact_pairs;   // 2 * dem.cap ints
     int* contact_scratch; // 2 * np + 4 ints
 
@@ -317,5 +319,9 @@ int dem_max_particles();
 // api.cu: message returned by pibm_last_error(NULL, ...)
 void set_global_error(const std::string& msg);
 int dem_max_per_cta();
+// api.cu: for the ensemble (ensemble.cu)
+cudaError_t record_step(Ctx* c, int parity, int* kernels);
+Ctx* ctx_state(pibm_ctx* ctx);
+pibm_status ctx_ready(pibm_ctx* ctx);
 
 }  // namespace pibm

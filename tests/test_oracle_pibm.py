@@ -188,3 +188,26 @@ def test_sedimenting_disk_approaches_force_balance():
     assert all(b > a for a, b in zip(ratios, ratios[1:]))
     assert 0.9 < ratios[-1] < 1.0
     assert abs(o.particles()["X"][0, 0] - 32.0) < 1e-3
+
+
+def test_conduction_nusselt_equals_cylinder_shape_factor():
+    # Section 3.1 cavity case with the flow switched off (Ra -> 0): heat leaves
+    # the static-point cylinder by conduction only.  With Q_l = 2 kappa_T (T_p - T_l)
+    # the Nu sum (heat rate / (2 k dT)) equals half the conduction shape factor
+    # of a circular cylinder of diameter D centred in a square of side W with
+    # isothermal walls, S = 2 pi / ln(1.0787 W / D) per unit length (textbook
+    # shape-factor table, valid for W/D > 1.41; a finite-difference Laplace
+    # solve agrees to 0.3%).  At n = 48 the lattice result sits within 1%;
+    # dropping the factor 2 of the thermal correction or the sign of Q fails it.
+    case = W.cavity(n=48, Ar=2.5, storage="f64")
+    case["buoyancy"] = False
+    o = oracle.Oracle(case)
+    prev = None
+    for _ in range(40):
+        o.step(500)
+        nu = o.nusselt()
+        if prev is not None and abs(nu - prev) < 1e-7 * abs(nu):
+            break
+        prev = nu
+    shape = np.pi / np.log(1.0787 * 2.5)
+    assert abs(nu / shape - 1.0) < 0.01, (nu, shape)

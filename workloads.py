@@ -28,6 +28,11 @@ sed2d    : 2-D sedimentation of heated disks: n_p disks placed by random
            linear spring-dashpot contacts; 10 DEM substeps.
 sed3d    : 3-D sedimentation of heated spheres: random sequential addition in
            the upper 3/5; density ratio 1.2; Hertz / Mindlin-Deresiewicz.
+ensemble : batched thermosensitive 3-D sedimentation: cubic boxes with edge
+           drawn from {64, 72, ..., 128}, Ra log-uniform in [1e3, 1e5],
+           sphere count uniform in [50, 400] (capped at a 12% solid fraction
+           so random sequential addition over the whole box succeeds),
+           d = 8, T_p(0) uniform in [0, 1], heat capacity rho_p V_p, Hertz.
 poiseuille, conduction, periodic_box : closed-form and invariant checks.
 """
 from __future__ import annotations
@@ -142,6 +147,29 @@ def sed3d(nx=256, ny=256, nz=512, n_p=2000, d=8.0, rho_ratio=1.2, g=1e-4, config
         parts["heat_cap"] = np.full(n_p, heat_cap)
     return _base(3, (nx, ny, nz), particles=parts, contact=hertz(),
                  g_particle=[0.0, 0.0, -g], storage=storage, name=f"sed3d_{nx}x{ny}x{nz}_{n_p}p")
+
+
+def ensemble(n_boxes=32, edges=tuple(range(64, 129, 8)), n_range=(50, 400), Ra_range=(1e3, 1e5), d=8.0,
+             rho_ratio=1.2, g=1e-4, config_index=3, storage="f32"):
+    """Uneven boxes of thermosensitive sphere sedimentation, one dict per box."""
+    gen = rng(config_index)
+    R = d / 2
+    v_sphere = 4.0 / 3.0 * np.pi * R ** 3
+    cases = []
+    for b in range(n_boxes):
+        n = int(gen.choice(edges))
+        Ra = float(10.0 ** gen.uniform(np.log10(Ra_range[0]), np.log10(Ra_range[1])))
+        n_p = int(gen.integers(n_range[0], n_range[1] + 1))
+        n_p = min(n_p, int(0.12 * n ** 3 / v_sphere))
+        lo = [R + 1.0] * 3
+        hi = [n - 1.5 - R - 1.0] * 3
+        X = rsa_positions(gen, n_p, R, lo, hi)
+        Tp = gen.random(n_p)
+        parts = dict(X=X, R=np.full(n_p, R), rho_p=np.full(n_p, rho_ratio), T_p=Tp,
+                     heat_cap=np.full(n_p, rho_ratio * v_sphere))
+        cases.append(_base(3, (n, n, n), Ra=Ra, particles=parts, contact=hertz(), g_particle=[0.0, 0.0, -g],
+                           storage=storage, name=f"ens{b}_{n}^3_{n_p}p_Ra{Ra:.3g}"))
+    return cases
 
 
 def poiseuille(ny=16, nx=4, nu=np.sqrt(3.0 / 16.0) / 3.0, F=1e-6, dim=2, nz=1):
