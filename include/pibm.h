@@ -247,6 +247,60 @@ pibm_status pibm_contacts_static(const double* d_X, const double* d_R, int n, in
                                  double cell_size, int32_t* d_pairs, int cap, int32_t* d_count, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Learned coupling surrogate (no counterpart in the paper).  Eq demgov holds
+ * the PIBM hydrodynamic force and torque (Eq lbm13 and its torque analogue)
+ * fixed over the DEM substeps of a lattice step; a small network predicts how
+ * they change with the particle's own velocity and spin, and its secant
+ * Jacobian corrects the held load inside the step:
+ *   F = F_held + J_FU (U - U_step_start),  tau = tau_held + J_TW (omega - omega_step_start).
+ * Features (12 per particle, lattice units): over the nodes the particle
+ * covers (|r - X| < R + 1/2, where the coupling acts) the fluid velocity is
+ * fitted by a rigid motion V + Om x (r - X) (least squares); features are
+ * U - V (3), omega - Om (3), T_p - mean covered-fluid temperature (1), the
+ * solid fraction
+ * sum_{q != p, |X_q - X_p| < 4 R_p} (R_q / 4 R_p)^D (1) and the four smallest
+ * surface gaps capped at 2 R_p (4).  Targets: the force (3), torque (3) and
+ * heat flux (1) the particle feels over the next step, i.e. the mean of the
+ * PIBM couplings of t and t-1.  Network: 12 -> 64 -> 64 -> 64 -> 7, tanh hidden layers,
+ * FP32 parameters packed [W1 (64x12), b1, W2 (64x64), b2, W3, b3, W4 (7x64),
+ * b4], W[out][in] row-major (PIBM_SURROGATE_PARAMS floats); standardisation
+ * norm = [mu_x (12), sd_x (12), mu_y (7), sd_y (7)].  Inference runs on the
+ * tensor cores in BF16 with FP32 accumulation; training runs in FP32. */
+enum { PIBM_SURROGATE_PARAMS = 9607, PIBM_SURROGATE_NORM = 38 };
+/* The 12 features of every particle for the current state (n*12 doubles, host). */
+pibm_status pibm_read_features(pibm_ctx* ctx, double* out);
+/* Set / read the network (host arrays as above).  Scales must be positive. */
+pibm_status pibm_surrogate_set_params(pibm_ctx* ctx, const float* params, const float* norm);
+pibm_status pibm_surrogate_get_params(pibm_ctx* ctx, float* params, float* norm);
+/* Tensor-core inference of rows standardised inputs (rows x 16 floats, the
+ * last 4 columns ignored) into rows x 8 standardised outputs (column 7 is 0).
+ * PIBM_ERR_TIMEOUT if a bounded device wait gave up. */
+pibm_status pibm_surrogate_infer(pibm_ctx* ctx, const float* in, int rows, float* out);
+/* FP32 gradient (PIBM_SURROGATE_PARAMS floats) and loss of the mean squared
+ * standardised error on B rows (X: B x 12, Y: B x 7, standardised). */
+pibm_status pibm_surrogate_gradient(pibm_ctx* ctx, const float* X, const float* Y, int B, float* grad, double* loss);
+/* Train on n samples (feat: n x 12, targ: n x 7, raw units, host): the
+ * standardisation comes from the data, weights start Glorot-uniform from
+ * seed, then epochs of shuffled mini-batches of batch rows with Adam (lr).
+ * loss_per_epoch: NULL or epochs doubles (mean standardised loss). */
+pibm_status pibm_surrogate_train(pibm_ctx* ctx, const double* feat, const double* targ, int64_t n, int epochs, int batch,
+                                 double lr, uint64_t seed, double* loss_per_epoch);
+/* Put the surrogate in the step: after each step's coupling the features,
+ * inference, Jacobian and gate run on the device; the next step's DEM applies
+ * the Jacobian only when sum_p |F_net,p - F_held,p| / sum_p |F_held,p| <= bound
+ * for the current state (else the held PIBM load alone, the plain method).
+ * delta: secant step in standard deviations of each velocity / spin feature.
+ * on = 0 removes it.  A new particle set removes it. */
+pibm_status pibm_surrogate_enable(pibm_ctx* ctx, int on, double bound, double delta);
+/* [0] steps with the Jacobian applied, [1] steps that fell back, [2] the last relative force error. */
+pibm_status pibm_surrogate_stats(pibm_ctx* ctx, double* out);
+/* A caller-supplied Jacobian (n*18 doubles per particle: J_FU row-major, then
+ * J_TW), applied every step until replaced; NULL removes it. */
+pibm_status pibm_set_hydro_jacobian(pibm_ctx* ctx, const double* J);
+/* The Jacobian in use (n*18, host) and whether the next step applies it. */
+pibm_status pibm_read_hydro_jacobian(pibm_ctx* ctx, double* J, int* on);
+
+/* ------------------------------------------------------------------------
  * Batched ensemble (no counterpart in the paper, which runs one case at a
  * time): n_boxes independent lattices -- sizes, Rayleigh numbers, particle
  * sets and every other descriptor field may differ -- advanced together by

@@ -80,6 +80,7 @@ def lib():
             "orc_read_particles": (C.c_int, [P, D, D, D, D]),
             "orc_read_particle_forces": (C.c_int, [P, D, D, D]),
             "orc_read_contact_forces": (C.c_int, [P, D, D]),
+            "orc_set_hydro_jacobian": (C.c_int, [P, D]),
             "orc_nusselt": (C.c_double, [P]),
             "orc_contacts": (C.c_int, [P, I, C.c_int]),
             "orc_contacts_bruteforce": (C.c_int, [P, I, C.c_int]),
@@ -216,6 +217,15 @@ class Oracle:
         F, T, H = np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
         self.L.orc_read_particle_forces(self.h, _dp(F), _dp(T), _dp(H))
         return {"F": F, "T": T, "H": H}
+
+    def set_hydro_jacobian(self, J=None):
+        """n x 18 Jacobian (J_FU row-major, then J_TW) or None."""
+        if J is None:
+            self.L.orc_set_hydro_jacobian(self.h, None)
+            self._J = None
+        else:
+            self._J = _f64(J, (-1, 18))
+            self.L.orc_set_hydro_jacobian(self.h, _dp(self._J))
 
     def contact_forces(self):
         n = getattr(self, "np", 0)

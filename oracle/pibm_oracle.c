@@ -94,6 +94,7 @@ struct orc_sim {
     double *Fh, *Th, *Hh, *Fc, *Tc;
     double *Fp, *Tq, *Hp; /* coupling of the previous time (force, torque, heat) */
     int have_prev;
+    double *J, *U0, *W0;  /* optional hydrodynamic Jacobian [np][18] and the velocities at the step start */
     double* wall_ft; /* [np][6][3] */
     contact* cont;
     int ncont;
@@ -705,15 +706,27 @@ static double hydro(const orc_sim* s, const double* cur, const double* prev, int
     return s->have_prev ? 0.5 * (cur[k] + prev[k]) : cur[k];
 }
 
-/* Eq demgov: m dU/dt = m (1 - rho_f/rho_p) g + F_fpi + sum F_c ; I domega/dt = tau_p + sum T_c */
+/* Eq demgov: m dU/dt = m (1 - rho_f/rho_p) g + F_fpi + sum F_c ; I domega/dt = tau_p + sum T_c.
+ * With a hydrodynamic Jacobian J set (a learned estimate of dF_fpi/dU and
+ * dtau_p/domega), the held hydrodynamic load is corrected inside the step by
+ * J_FU (U - U_start) and J_TW (omega - omega_start). */
 static void kick(orc_sim* s, double h) {
     for (int p = 0; p < s->np; p++) {
         if (s->fixed[p]) continue;
         double mg = s->m[p] * (1.0 - 1.0 / s->rho[p]);
+        double dF[3] = {0, 0, 0}, dT[3] = {0, 0, 0};
+        if (s->J) {
+            const double* J = s->J + 18 * p;
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) {
+                    dF[a] += J[3 * a + b] * (s->U[3 * p + b] - s->U0[3 * p + b]);
+                    dT[a] += J[9 + 3 * a + b] * (s->W[3 * p + b] - s->W0[3 * p + b]);
+                }
+        }
         for (int a = 0; a < 3; a++) {
-            double F = s->Fc[3 * p + a] + hydro(s, s->Fh, s->Fp, 3 * p + a) + mg * s->P.g_particle[a];
+            double F = s->Fc[3 * p + a] + (hydro(s, s->Fh, s->Fp, 3 * p + a) + dF[a]) + mg * s->P.g_particle[a];
             s->U[3 * p + a] += h * F / s->m[p];
-            s->W[3 * p + a] += h * (s->Tc[3 * p + a] + hydro(s, s->Th, s->Tq, 3 * p + a)) / s->I[p];
+            s->W[3 * p + a] += h * (s->Tc[3 * p + a] + (hydro(s, s->Th, s->Tq, 3 * p + a) + dT[a])) / s->I[p];
         }
         if (s->D == 2) {
             s->U[3 * p + 2] = 0.0;
@@ -726,6 +739,10 @@ static void dem(orc_sim* s) {
     if (s->np == 0) return;
     int nsub = s->P.dem_substeps > 0 ? s->P.dem_substeps : 1;
     double dt = 1.0 / nsub;
+    if (s->J) {
+        memcpy(s->U0, s->U, sizeof(double) * 3 * s->np);
+        memcpy(s->W0, s->W, sizeof(double) * 3 * s->np);
+    }
     for (int sub = 0; sub < nsub; sub++) {
         kick(s, 0.5 * dt); /* velocity Verlet: half kick with the last contact force */
         for (int p = 0; p < s->np; p++) {
@@ -783,7 +800,8 @@ orc_sim* orc_create(const orc_params* p) {
 
 static void free_particles(orc_sim* s) {
     double** arr[] = {&s->X, &s->U, &s->W, &s->R, &s->rho, &s->Tp, &s->Cp, &s->m, &s->I,
-                      &s->Fh, &s->Th, &s->Hh, &s->Fc, &s->Tc, &s->Fp, &s->Tq, &s->Hp, &s->wall_ft};
+                      &s->Fh, &s->Th, &s->Hh, &s->Fc, &s->Tc, &s->Fp, &s->Tq, &s->Hp, &s->wall_ft,
+                      &s->J, &s->U0, &s->W0};
     for (unsigned k = 0; k < sizeof(arr) / sizeof(arr[0]); k++) {
         free(*arr[k]);
         *arr[k] = NULL;
@@ -969,6 +987,19 @@ int orc_read_particle_forces(orc_sim* s, double* F, double* T, double* H) {
     if (T) memcpy(T, s->Th, sizeof(double) * 3 * s->np);
     if (H) memcpy(H, s->Hh, sizeof(double) * s->np);
     return s->np;
+}
+
+int orc_set_hydro_jacobian(orc_sim* s, const double* J) {
+    free(s->J);
+    free(s->U0);
+    free(s->W0);
+    s->J = s->U0 = s->W0 = NULL;
+    if (!J || s->np == 0) return 0;
+    s->J = (double*)malloc(sizeof(double) * 18 * s->np);
+    s->U0 = (double*)malloc(sizeof(double) * 3 * s->np);
+    s->W0 = (double*)malloc(sizeof(double) * 3 * s->np);
+    memcpy(s->J, J, sizeof(double) * 18 * s->np);
+    return 0;
 }
 
 int orc_read_contact_forces(orc_sim* s, double* F, double* T) {

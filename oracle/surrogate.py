@@ -1,0 +1,263 @@
+"""Learned coupling surrogate: plain FP64 reference of everything the GPU
+surrogate computes -- the per-particle feature map, the MLP (forward, loss,
+backward, Adam), the BF16 inference arithmetic, the secant Jacobian used in
+the DEM substeps, and the gate that falls back to the plain PIBM load.
+
+TEST INFRASTRUCTURE ONLY: used by the tests and by nothing on the product
+path; it shares no code with the CUDA library.
+
+The surrogate is not in the paper.  It serves the momentum balance of Eq
+demgov: the hydrodynamic force, torque and heat flux of a particle (Eq lbm13
+and its torque / heat analogues) are computed once per lattice step by the
+PIBM coupling and are held fixed over the DEM substeps; the surrogate
+predicts how they change with the particle's own velocity and spin inside
+the step.  The coupling acts on the fluid the particle covers (Eqs lbm7,
+lbm8: F_f = 2 (rho U_l - j) on every covered node), so the velocity
+features are taken against that fluid.  Definitions (lattice units):
+
+  region S_p  the nodes the particle covers: r inside the lattice with
+              |r - X_p| < R_p + 1/2 (epsilon > 0)
+  raw fields  the moments before the coupling's correction, u = j / rho with
+              rho = sum f, j = sum e f, and T0 = sum g (see raw_fields): the
+              coupling acts on exactly these (F_f = 2 (rho U_l - j))
+  V_s, Om_s   rigid-motion fit of the raw fluid velocity over S_p about X_p:
+              minimise sum |u(r) - V - Om x d|^2, d = r - X_p; the normal
+              equations, with n nodes, D = sum d, M = sum (|d|^2 I - d d^T):
+                  n V - D x Om = sum u,   D x V + M Om = sum d x u
+              (2-D: unknowns V_x, V_y, Om_z); exact for any rigid field
+  T_s         mean raw fluid temperature T0 over S_p
+  features    U_p - V_s (3), omega_p - Om_s (3), T_p - T_s (1),
+              phi_p = sum_{q != p, |X_q - X_p| < 4 R_p} (R_q / 4 R_p)^D (1),
+              the four smallest surface gaps |X_q - X_p| - R_p - R_q, each
+              capped at 2 R_p and padded with 2 R_p (4)
+  targets     the PIBM coupling's force (3), torque (3) and heat flux (1) of
+              the state (Eq lbm13 and its analogues)
+  network     12 -> 64 -> 64 -> 64 -> 7, tanh on the hidden layers, inputs
+              and outputs standardised with the training set's mean and
+              standard deviation (a standard deviation below 1e-12 counts as 1)
+  loss        mean over rows and outputs of the squared standardised error
+  Jacobian    secant over delta standard deviations of each of the six
+              velocity / spin features: J_FU[a][b] = dF_a / dU_b and
+              J_TW[a][b] = dtau_a / domega_b of the coupling; the DEM holds
+              the mean of the couplings of t and t-1 and a velocity change
+              enters only the newer one, so it applies half of it
+              (applied_jacobian)
+  gate        e = sum_p |F_mlp,p - F_pibm,p| / sum_p |F_pibm,p|; the
+              Jacobian is applied in the next step only when e <= bound
+"""
+from __future__ import annotations
+
+import numpy as np
+
+N_FEAT, N_OUT, WIDTH = 12, 7, 64
+SIZES = [(N_FEAT, WIDTH), (WIDTH, WIDTH), (WIDTH, WIDTH), (WIDTH, N_OUT)]
+
+
+# ------------------------------------------------------------------ features
+_E2 = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (-1, 0, 0), (0, -1, 0), (1, 1, 0), (-1, 1, 0), (-1, -1, 0), (1, -1, 0)]
+_E3 = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+       (1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1),
+       (1, 0, -1), (-1, 0, 1), (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1)]
+
+
+def raw_fields(f, g, dim):
+    """rho = sum f, u = (sum e f) / rho, T = sum g from full populations
+    f [q][z][y][x] (D2Q9 / D3Q19 in the oracle's direction order) and g."""
+    E = np.asarray(_E2 if dim == 2 else _E3, dtype=np.float64)
+    rho = f.sum(axis=0)
+    j = np.einsum("qa,q...->a...", E, f)
+    return {"rho": rho, "ux": j[0] / rho, "uy": j[1] / rho, "uz": j[2] / rho, "T": g.sum(axis=0)}
+
+
+def region(X, R, shape_xyz, dim):
+    """Integer node coordinates (k, 3) of the covered nodes |r - X| < R + 1/2."""
+    lo = np.floor(np.asarray(X[:dim]) - R - 1).astype(int)
+    hi = np.ceil(np.asarray(X[:dim]) + R + 1).astype(int)
+    axes = [np.arange(max(lo[a], 0), min(hi[a], shape_xyz[a] - 1) + 1) for a in range(dim)]
+    grid = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, dim)
+    d = grid - np.asarray(X[:dim])[None, :]
+    r = np.sqrt(np.sum(d * d, axis=1))
+    sel = r < R + 0.5
+    out = np.zeros((int(sel.sum()), 3), dtype=np.int64)
+    out[:, :dim] = grid[sel]
+    return out
+
+
+def features(fields, X, U, W, R, Tp, dim):
+    """fields: dict with rho, ux, uy, uz (3-D), T as (nz, ny, nx) arrays."""
+    n = len(R)
+    nz, ny, nx = fields["T"].shape
+    out = np.zeros((n, N_FEAT))
+    uz = fields.get("uz", np.zeros_like(fields["T"]))
+    for p in range(n):
+        nodes = region(X[p], R[p], (nx, ny, nz), dim)
+        x, y, z = nodes[:, 0], nodes[:, 1], nodes[:, 2]
+        u = np.stack([fields["ux"][z, y, x], fields["uy"][z, y, x], uz[z, y, x]], axis=1)
+        Ts = fields["T"][z, y, x].mean()
+        d = nodes.astype(np.float64) - np.asarray(X[p])[None, :]
+        if dim == 2:
+            d[:, 2] = 0.0
+        m = len(nodes)
+        D = d.sum(axis=0)
+        su = u.sum(axis=0)
+        sdu = np.cross(d, u).sum(axis=0)
+        if dim == 3:
+            M = np.sum(d * d) * np.eye(3) - d.T @ d
+            Dx = np.array([[0, -D[2], D[1]], [D[2], 0, -D[0]], [-D[1], D[0], 0]])
+            A = np.block([[m * np.eye(3), -Dx], [Dx, M]])
+            sol = np.linalg.solve(A, np.concatenate([su, sdu]))
+            V, Om = sol[:3], sol[3:]
+        else:
+            A = np.array([[m, 0.0, -D[1]], [0.0, m, D[0]], [-D[1], D[0], np.sum(d * d)]])
+            sol = np.linalg.solve(A, np.array([su[0], su[1], sdu[2]]))
+            V, Om = np.array([sol[0], sol[1], 0.0]), np.array([0.0, 0.0, sol[2]])
+        out[p, 0:3] = np.asarray(U[p]) - V
+        out[p, 3:6] = np.asarray(W[p]) - Om
+        out[p, 6] = Tp[p] - Ts
+        dist = np.sqrt(np.sum((np.asarray(X) - np.asarray(X[p])[None, :]) ** 2, axis=1))
+        others = np.arange(n) != p
+        near = others & (dist < 4 * R[p])
+        out[p, 7] = np.sum((np.asarray(R)[near] / (4 * R[p])) ** dim)
+        gaps = np.sort(dist[others] - R[p] - np.asarray(R)[others])
+        cap = 2 * R[p]
+        g4 = np.full(4, cap)
+        k = min(4, len(gaps))
+        g4[:k] = np.minimum(gaps[:k], cap)
+        out[p, 8:12] = g4
+    return out
+
+
+def targets(F, T, H):
+    return np.concatenate([np.asarray(F), np.asarray(T), np.asarray(H)[:, None]], axis=1)
+
+
+# ---------------------------------------------------------------- the network
+def init_params(seed):
+    """Glorot-uniform weights, zero biases (W[l] is out x in)."""
+    gen = np.random.Generator(np.random.PCG64(seed))
+    params = []
+    for fi, fo in SIZES:
+        lim = np.sqrt(6.0 / (fi + fo))
+        params.append((gen.uniform(-lim, lim, size=(fo, fi)), np.zeros(fo)))
+    return params
+
+
+def flatten(params):
+    return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in params])
+
+
+def unflatten(vec):
+    params, k = [], 0
+    for fi, fo in SIZES:
+        W = np.asarray(vec[k:k + fo * fi], dtype=np.float64).reshape(fo, fi)
+        k += fo * fi
+        b = np.asarray(vec[k:k + fo], dtype=np.float64)
+        k += fo
+        params.append((W, b))
+    return params
+
+
+N_PARAMS = sum(fo * fi + fo for fi, fo in SIZES)
+
+
+def standardise(A):
+    mu = A.mean(axis=0)
+    sd = A.std(axis=0)
+    sd = np.where(sd < 1e-12, 1.0, sd)
+    return mu, sd
+
+
+def forward(params, Xn):
+    """Returns the list of layer outputs [x, a1, a2, a3, y] (FP64)."""
+    acts = [Xn]
+    a = Xn
+    for l, (W, b) in enumerate(params):
+        z = a @ W.T + b
+        a = np.tanh(z) if l < len(params) - 1 else z
+        acts.append(a)
+    return acts
+
+
+def loss_and_grads(params, Xn, Yn):
+    """Mean squared standardised error and its gradient (backpropagation)."""
+    acts = forward(params, Xn)
+    B = Xn.shape[0]
+    diff = acts[-1] - Yn
+    loss = float(np.mean(diff * diff))
+    delta = 2.0 * diff / (B * Yn.shape[1])          # dL/dy
+    grads = [None] * len(params)
+    for l in range(len(params) - 1, -1, -1):
+        W, _ = params[l]
+        grads[l] = (delta.T @ acts[l], delta.sum(axis=0))
+        if l > 0:
+            delta = (delta @ W) * (1.0 - acts[l] ** 2)  # through tanh of layer l-1's output
+    return loss, grads
+
+
+def adam(params, grads, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step (t counts from 1); returns new params, m, v."""
+    out_p, out_m, out_v = [], [], []
+    for (W, b), (gW, gb), (mW, mb), (vW, vb) in zip(params, grads, m, v):
+        new = []
+        for x, g, mm, vv in ((W, gW, mW, vW), (b, gb, mb, vb)):
+            mm = b1 * mm + (1 - b1) * g
+            vv = b2 * vv + (1 - b2) * g * g
+            mh = mm / (1 - b1 ** t)
+            vh = vv / (1 - b2 ** t)
+            new.append((x - lr * mh / (np.sqrt(vh) + eps), mm, vv))
+        out_p.append((new[0][0], new[1][0]))
+        out_m.append((new[0][1], new[1][1]))
+        out_v.append((new[0][2], new[1][2]))
+    return out_p, out_m, out_v
+
+
+# ------------------------------------------------------- BF16 inference model
+def to_bf16(a):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    a32 = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    bits = a32.view(np.uint32).astype(np.uint64)
+    bits = (bits + 0x7FFF + ((bits >> 16) & 1)) & 0xFFFF0000
+    return bits.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(params, Xn):
+    """The tensor-core inference arithmetic: BF16 inputs, weights and hidden
+    activations, wide accumulation, FP32 bias and tanh, FP32 output."""
+    a = to_bf16(Xn)
+    for l, (W, b) in enumerate(params):
+        z = a @ to_bf16(W).T + np.asarray(b, dtype=np.float32).astype(np.float64)
+        if l < len(params) - 1:
+            a = to_bf16(np.tanh(z))
+        else:
+            a = z
+    return a
+
+
+def jacobian(params, xmu, xsd, ymu, ysd, Xraw, delta=0.25, infer=forward):
+    """Secant Jacobian of (F, tau) in (U, omega) and the value row.
+    Returns (Y (n, 7) de-standardised, J (n, 18): J_FU row-major, J_TW row-major)."""
+    Xn = (Xraw - xmu) / xsd
+    n = Xn.shape[0]
+    rows = np.repeat(Xn, 7, axis=0)
+    for j in range(6):
+        rows[j + 1::7, j] += delta
+    Yn = infer(params, rows) if infer is not forward else forward(params, rows)[-1]
+    Y = Yn * ysd + ymu
+    Y = Y.reshape(n, 7, N_OUT)
+    base = Y[:, 0, :]
+    J = np.zeros((n, 18))
+    for b in range(3):
+        J[:, b:9:3] = (Y[:, 1 + b, 0:3] - base[:, 0:3]) / (delta * xsd[b])
+        J[:, 9 + b:18:3] = (Y[:, 4 + b, 3:6] - base[:, 3:6]) / (delta * xsd[3 + b])
+    return base, J
+
+
+def applied_jacobian(J):
+    """The Jacobian the DEM applies to the held load (half the coupling's)."""
+    return 0.5 * np.asarray(J)
+
+
+def gate_error(F_mlp, F_pibm):
+    num = np.sum(np.sqrt(np.sum((F_mlp - F_pibm) ** 2, axis=1)))
+    den = np.sum(np.sqrt(np.sum(F_pibm ** 2, axis=1)))
+    return float(num / den) if den > 0 else float("inf")

@@ -23,6 +23,8 @@ FIELDS = {"rho": 0, "ux": 1, "uy": 2, "uz": 3, "T": 4, "FBx": 5, "FBy": 6, "FBz"
 
 # every symbol include/pibm.h declares, with (restype, argtypes)
 _P, _D, _I32, _U8 = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_uint8)
+_F = C.POINTER(C.c_float)
+SURROGATE_PARAMS, SURROGATE_NORM = 9607, 38
 
 
 class pibm_desc(C.Structure):
@@ -70,6 +72,16 @@ SIGNATURES = {
     "pibm_save": (C.c_int, [_P, C.c_char_p]),
     "pibm_load": (C.c_int, [_P, C.c_char_p]),
     "pibm_contacts_static": (C.c_int, [_P, _P, C.c_int, C.c_int, _I32, C.c_double, _P, C.c_int, _P, _P]),
+    "pibm_read_features": (C.c_int, [_P, _D]),
+    "pibm_surrogate_set_params": (C.c_int, [_P, _F, _F]),
+    "pibm_surrogate_get_params": (C.c_int, [_P, _F, _F]),
+    "pibm_surrogate_infer": (C.c_int, [_P, _F, C.c_int, _F]),
+    "pibm_surrogate_gradient": (C.c_int, [_P, _F, _F, C.c_int, _F, _D]),
+    "pibm_surrogate_train": (C.c_int, [_P, _D, _D, C.c_int64, C.c_int, C.c_int, C.c_double, C.c_uint64, _D]),
+    "pibm_surrogate_enable": (C.c_int, [_P, C.c_int, C.c_double, C.c_double]),
+    "pibm_surrogate_stats": (C.c_int, [_P, _D]),
+    "pibm_set_hydro_jacobian": (C.c_int, [_P, _D]),
+    "pibm_read_hydro_jacobian": (C.c_int, [_P, _D, C.POINTER(C.c_int)]),
     "pibm_ensemble_create": (C.c_int, [C.POINTER(pibm_desc), C.c_int, _P, C.POINTER(pibm_allocator), C.POINTER(_P)]),
     "pibm_ensemble_destroy": (C.c_int, [_P]),
     "pibm_ensemble_box": (C.c_int, [_P, C.c_int, C.POINTER(_P)]),
@@ -345,6 +357,74 @@ class Simulation:
 
     def set_tuning(self, knob: int, value: int):
         self._check(self.L.pibm_set_tuning(self.h, knob, value), "pibm_set_tuning")
+
+    # ------------------------------------------------ learned surrogate
+    def read_features(self):
+        out = np.empty((self.np, 12))
+        self._check(self.L.pibm_read_features(self.h, _dp(out)), "pibm_read_features")
+        return out
+
+    def surrogate_set_params(self, params, norm):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        q = np.ascontiguousarray(norm, dtype=np.float32)
+        self._check(self.L.pibm_surrogate_set_params(self.h, p.ctypes.data_as(_F), q.ctypes.data_as(_F)),
+                    "pibm_surrogate_set_params")
+
+    def surrogate_get_params(self):
+        p = np.empty(SURROGATE_PARAMS, dtype=np.float32)
+        q = np.empty(SURROGATE_NORM, dtype=np.float32)
+        self._check(self.L.pibm_surrogate_get_params(self.h, p.ctypes.data_as(_F), q.ctypes.data_as(_F)),
+                    "pibm_surrogate_get_params")
+        return p, q
+
+    def surrogate_infer(self, Xn):
+        """Standardised inputs (rows x 12) -> standardised outputs (rows x 7), tensor cores."""
+        Xn = np.asarray(Xn, dtype=np.float32)
+        rows = Xn.shape[0]
+        inp = np.zeros((rows, 16), dtype=np.float32)
+        inp[:, :12] = Xn
+        out = np.empty((rows, 8), dtype=np.float32)
+        self._check(self.L.pibm_surrogate_infer(self.h, inp.ctypes.data_as(_F), rows, out.ctypes.data_as(_F)),
+                    "pibm_surrogate_infer")
+        return out[:, :7]
+
+    def surrogate_gradient(self, Xn, Yn):
+        X = np.ascontiguousarray(Xn, dtype=np.float32)
+        Y = np.ascontiguousarray(Yn, dtype=np.float32)
+        g = np.empty(SURROGATE_PARAMS, dtype=np.float32)
+        loss = C.c_double()
+        self._check(self.L.pibm_surrogate_gradient(self.h, X.ctypes.data_as(_F), Y.ctypes.data_as(_F), X.shape[0],
+                                                   g.ctypes.data_as(_F), C.byref(loss)), "pibm_surrogate_gradient")
+        return g, loss.value
+
+    def surrogate_train(self, feat, targ, epochs=10, batch=1024, lr=1e-3, seed=0):
+        F = np.ascontiguousarray(feat, dtype=np.float64)
+        T = np.ascontiguousarray(targ, dtype=np.float64)
+        losses = np.zeros(max(epochs, 1))
+        self._check(self.L.pibm_surrogate_train(self.h, _dp(F), _dp(T), F.shape[0], epochs, batch, lr, seed,
+                                                _dp(losses)), "pibm_surrogate_train")
+        return losses[:epochs]
+
+    def surrogate_enable(self, on=True, bound=0.01, delta=0.25):
+        self._check(self.L.pibm_surrogate_enable(self.h, int(on), float(bound), float(delta)), "pibm_surrogate_enable")
+
+    def surrogate_stats(self):
+        out = np.zeros(3)
+        self._check(self.L.pibm_surrogate_stats(self.h, _dp(out)), "pibm_surrogate_stats")
+        return {"on_steps": int(out[0]), "off_steps": int(out[1]), "last_error": float(out[2])}
+
+    def set_hydro_jacobian(self, J=None):
+        if J is None:
+            self._check(self.L.pibm_set_hydro_jacobian(self.h, None), "pibm_set_hydro_jacobian")
+        else:
+            J = np.ascontiguousarray(J, dtype=np.float64).reshape(-1, 18)
+            self._check(self.L.pibm_set_hydro_jacobian(self.h, _dp(J)), "pibm_set_hydro_jacobian")
+
+    def read_hydro_jacobian(self):
+        J = np.empty((self.np, 18))
+        on = C.c_int()
+        self._check(self.L.pibm_read_hydro_jacobian(self.h, _dp(J), C.byref(on)), "pibm_read_hydro_jacobian")
+        return J, bool(on.value)
 
     def kernels_per_step(self) -> int:
         v = C.c_int()

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpibm.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["lattice.cu", "coupling.cu", "dem.cu", "api.cu", "noalloc.cu", "ensemble.cu"]
+SOURCES = ["lattice.cu", "coupling.cu", "dem.cu", "api.cu", "noalloc.cu", "ensemble.cu", "surrogate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-Wall", "-Xcompiler", "-Wno-unused-function"]

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <random>
 #include <string>
 #include <vector>
 
@@ -24,7 +25,7 @@ static std::string g_create_error;
 
 void pibm::set_global_error(const std::string& msg) { g_create_error = msg; }
 
-enum { GRP_LATTICE = 0, GRP_PARTICLES = 1, GRP_MARKERS = 2, GRP_SCRATCH = 3 };
+enum { GRP_LATTICE = 0, GRP_PARTICLES = 1, GRP_MARKERS = 2, GRP_SCRATCH = 3, GRP_SURROGATE = 4, GRP_SG_PART = 5 };
 
 #define PCHECK(call)                                                                         \
     do {                                                                                     \
@@ -156,6 +157,10 @@ cudaError_t pibm::record_step(Ctx* cp, int par, int* kernels_out) {
     chk(cudaStreamWaitEvent(c.s0, c.ev_join, 0));
     chk(launch_coupling(&c, c.s0, par ^ 1));         // coupling of time t+1
     kernels += coupling_kernel_count(&c);
+    if (c.sg.enabled && c.np > 0) {                  // surrogate Jacobian for the next step's DEM, judged by t+1's coupling
+        chk(launch_surrogate(&c, c.s0, par ^ 1));
+        kernels += surrogate_kernel_count(&c);
+    }
     if (kernels_out) *kernels_out = kernels;
     return e;
 }
@@ -359,6 +364,11 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     dfree_group(ctx, GRP_PARTICLES);
     c.np = 0;
     c.dem.n = 0;
+    // a new particle set invalidates any hydrodynamic Jacobian (surrogate or fixed)
+    c.sg.enabled = 0;
+    c.sg.fixed = 0;
+    c.dem.J = nullptr;
+    c.dem.J_on = nullptr;
     for (int b = 0; b < 2; b++) {
         PCHECK(cudaMemsetAsync(c.mk[b], 0, (size_t)c.G.N * c.v4, c.s0));
         PCHECK(cudaMemsetAsync(c.fb[b], 0, (size_t)c.G.N * c.v4, c.s0));
@@ -954,6 +964,292 @@ pibm_status pibm_load(pibm_ctx* ctx, const char* path) {
     c.t = h.t;
     drop_graphs(c);
     return device_status(ctx);
+}
+
+// ------------------------------------------------------------ surrogate
+static pibm_status sg_ensure(pibm_ctx* ctx) {
+    Ctx& c = ctx->c;
+    if (!c.sg.params) {
+        c.sg.params = (float*)dalloc(ctx, sizeof(float) * SG_NPARAMS, GRP_SURROGATE);
+        c.sg.m = (float*)dalloc(ctx, sizeof(float) * SG_NPARAMS, GRP_SURROGATE);
+        c.sg.v = (float*)dalloc(ctx, sizeof(float) * SG_NPARAMS, GRP_SURROGATE);
+        c.sg.norm = (float*)dalloc(ctx, sizeof(float) * (2 * SG_NFEAT + 2 * SG_NOUT), GRP_SURROGATE);
+        c.sg.partial = (float*)dalloc(ctx, sizeof(float) * SG_NPARAMS * SG_TRAIN_BLOCKS, GRP_SURROGATE);
+        c.sg.lossp = (float*)dalloc(ctx, sizeof(float) * SG_TRAIN_BLOCKS, GRP_SURROGATE);
+        c.sg.J_on = (int*)dalloc(ctx, sizeof(int) * 2, GRP_SURROGATE);
+        c.sg.err = (int*)dalloc(ctx, sizeof(int) * 2, GRP_SURROGATE);
+        c.sg.stats = (double*)dalloc(ctx, sizeof(double) * 4, GRP_SURROGATE);
+        if (!c.sg.params || !c.sg.m || !c.sg.v || !c.sg.norm || !c.sg.partial || !c.sg.lossp || !c.sg.J_on ||
+            !c.sg.err || !c.sg.stats) {
+            c.sg.params = nullptr;
+            return fail(ctx, PIBM_ERR_OOM, "surrogate buffers");
+        }
+    }
+    if (c.np > c.sg.cap) {
+        dfree_group(ctx, GRP_SG_PART);
+        const size_t n = (size_t)c.np;
+        c.sg.feat = (double*)dalloc(ctx, sizeof(double) * 12 * n, GRP_SG_PART);
+        c.sg.rows = (float*)dalloc(ctx, sizeof(float) * 7 * 16 * n, GRP_SG_PART);
+        c.sg.yrows = (float*)dalloc(ctx, sizeof(float) * 7 * 8 * n, GRP_SG_PART);
+        c.sg.J = (float*)dalloc(ctx, sizeof(float) * 18 * n, GRP_SG_PART);
+        c.sg.part = (double*)dalloc(ctx, sizeof(double) * 2 * (n / 256 + 2), GRP_SG_PART);
+        if (!c.sg.feat || !c.sg.rows || !c.sg.yrows || !c.sg.J || !c.sg.part) {
+            c.sg.cap = 0;
+            return fail(ctx, PIBM_ERR_OOM, "surrogate particle buffers");
+        }
+        c.sg.cap = c.np;
+    }
+    return PIBM_OK;
+}
+
+pibm_status pibm_read_features(pibm_ctx* ctx, double* out) {
+    if (!ctx || !out) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (c.np == 0) return PIBM_OK;
+    pibm_status st = sg_ensure(ctx);
+    if (st != PIBM_OK) return st;
+    PCHECK(launch_features(&c, c.s0, parity(c), c.sg.feat));
+    PCHECK(cudaMemcpyAsync(out, c.sg.feat, sizeof(double) * 12 * c.np, cudaMemcpyDeviceToHost, c.s0));
+    PCHECK(cudaStreamSynchronize(c.s0));
+    return PIBM_OK;
+}
+
+pibm_status pibm_surrogate_set_params(pibm_ctx* ctx, const float* params, const float* norm) {
+    if (!ctx || !params || !norm) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    pibm_status st = sg_ensure(ctx);
+    if (st != PIBM_OK) return st;
+    for (int k = 0; k < SG_NFEAT; k++)
+        if (!(norm[SG_NFEAT + k] > 0)) return fail(ctx, PIBM_ERR_ARG, "feature scales must be positive");
+    for (int k = 0; k < SG_NOUT; k++)
+        if (!(norm[2 * SG_NFEAT + SG_NOUT + k] > 0)) return fail(ctx, PIBM_ERR_ARG, "target scales must be positive");
+    PCHECK(cudaMemcpyAsync(c.sg.params, params, sizeof(float) * SG_NPARAMS, cudaMemcpyHostToDevice, c.s0));
+    PCHECK(cudaMemcpyAsync(c.sg.norm, norm, sizeof(float) * (2 * SG_NFEAT + 2 * SG_NOUT), cudaMemcpyHostToDevice, c.s0));
+    PCHECK(cudaMemsetAsync(c.sg.m, 0, sizeof(float) * SG_NPARAMS, c.s0));
+    PCHECK(cudaMemsetAsync(c.sg.v, 0, sizeof(float) * SG_NPARAMS, c.s0));
+    PCHECK(cudaStreamSynchronize(c.s0));
+    c.sg.adam_t = 0;
+    c.sg.trained = 1;
+    return PIBM_OK;
+}
+
+pibm_status pibm_surrogate_get_params(pibm_ctx* ctx, float* params, float* norm) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!c.sg.trained) return fail(ctx, PIBM_ERR_STATE, "surrogate has no parameters yet");
+    if (params) PCHECK(cudaMemcpyAsync(params, c.sg.params, sizeof(float) * SG_NPARAMS, cudaMemcpyDeviceToHost, c.s0));
+    if (norm)
+        PCHECK(cudaMemcpyAsync(norm, c.sg.norm, sizeof(float) * (2 * SG_NFEAT + 2 * SG_NOUT), cudaMemcpyDeviceToHost, c.s0));
+    PCHECK(cudaStreamSynchronize(c.s0));
+    return PIBM_OK;
+}
+
+pibm_status pibm_surrogate_infer(pibm_ctx* ctx, const float* in, int rows, float* out) {
+    if (!ctx || rows < 0 || (rows > 0 && (!in || !out))) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!c.sg.trained) return fail(ctx, PIBM_ERR_STATE, "surrogate has no parameters yet");
+    if (rows == 0) return PIBM_OK;
+    float* din = (float*)dalloc(ctx, sizeof(float) * 16 * (size_t)rows, GRP_SCRATCH);
+    float* dout = (float*)dalloc(ctx, sizeof(float) * 8 * (size_t)rows, GRP_SCRATCH);
+    if (!din || !dout) {
+        dfree_group(ctx, GRP_SCRATCH);
+        return fail(ctx, PIBM_ERR_OOM, "inference buffers");
+    }
+    cudaError_t e = cudaMemcpyAsync(din, in, sizeof(float) * 16 * (size_t)rows, cudaMemcpyHostToDevice, c.s0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c.sg.err, 0, sizeof(int), c.s0);
+    if (e == cudaSuccess) e = launch_mlp(&c, c.s0, din, rows, dout);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof(float) * 8 * (size_t)rows, cudaMemcpyDeviceToHost, c.s0);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, c.sg.err, sizeof(int), cudaMemcpyDeviceToHost, c.s0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.s0);
+    dfree_group(ctx, GRP_SCRATCH);
+    if (e != cudaSuccess) return fail(ctx, PIBM_ERR_CUDA, std::string("inference: ") + cudaGetErrorString(e));
+    if (err) return fail(ctx, PIBM_ERR_TIMEOUT, "tensor-core wait gave up");
+    return PIBM_OK;
+}
+
+pibm_status pibm_surrogate_gradient(pibm_ctx* ctx, const float* X, const float* Y, int B, float* grad, double* loss) {
+    if (!ctx || !X || !Y || B < 1) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!c.sg.trained) return fail(ctx, PIBM_ERR_STATE, "surrogate has no parameters yet");
+    float* xb = (float*)dalloc(ctx, sizeof(float) * SG_NFEAT * (size_t)B, GRP_SCRATCH);
+    float* yb = (float*)dalloc(ctx, sizeof(float) * SG_NOUT * (size_t)B, GRP_SCRATCH);
+    float* g = (float*)dalloc(ctx, sizeof(float) * SG_NPARAMS, GRP_SCRATCH);
+    double* l = (double*)dalloc(ctx, sizeof(double), GRP_SCRATCH);
+    if (!xb || !yb || !g || !l) {
+        dfree_group(ctx, GRP_SCRATCH);
+        return fail(ctx, PIBM_ERR_OOM, "gradient buffers");
+    }
+    cudaError_t e = cudaMemcpyAsync(xb, X, sizeof(float) * SG_NFEAT * (size_t)B, cudaMemcpyHostToDevice, c.s0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(yb, Y, sizeof(float) * SG_NOUT * (size_t)B, cudaMemcpyHostToDevice, c.s0);
+    if (e == cudaSuccess) e = train_batch(&c, c.s0, xb, yb, B, 0.f, g, l);
+    if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, g, sizeof(float) * SG_NPARAMS, cudaMemcpyDeviceToHost, c.s0);
+    if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, l, sizeof(double), cudaMemcpyDeviceToHost, c.s0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.s0);
+    dfree_group(ctx, GRP_SCRATCH);
+    if (e != cudaSuccess) return fail(ctx, PIBM_ERR_CUDA, std::string("gradient: ") + cudaGetErrorString(e));
+    return PIBM_OK;
+}
+
+pibm_status pibm_surrogate_train(pibm_ctx* ctx, const double* feat, const double* targ, int64_t n, int epochs, int batch,
+                                 double lr, uint64_t seed, double* loss_per_epoch) {
+    if (!ctx || !feat || !targ || n < 2 || epochs < 0 || batch < 1 || !(lr > 0)) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    pibm_status st = sg_ensure(ctx);
+    if (st != PIBM_OK) return st;
+    // standardisation from the data (FP64, population standard deviation; below 1e-12 counts as 1)
+    std::vector<double> mu(SG_NFEAT + SG_NOUT, 0.0), sd(SG_NFEAT + SG_NOUT, 0.0);
+    for (int64_t i = 0; i < n; i++) {
+        for (int k = 0; k < SG_NFEAT; k++) mu[k] += feat[i * SG_NFEAT + k];
+        for (int k = 0; k < SG_NOUT; k++) mu[SG_NFEAT + k] += targ[i * SG_NOUT + k];
+    }
+    for (auto& v : mu) v /= (double)n;
+    for (int64_t i = 0; i < n; i++) {
+        for (int k = 0; k < SG_NFEAT; k++) sd[k] += (feat[i * SG_NFEAT + k] - mu[k]) * (feat[i * SG_NFEAT + k] - mu[k]);
+        for (int k = 0; k < SG_NOUT; k++)
+            sd[SG_NFEAT + k] += (targ[i * SG_NOUT + k] - mu[SG_NFEAT + k]) * (targ[i * SG_NOUT + k] - mu[SG_NFEAT + k]);
+    }
+    for (auto& v : sd) {
+        v = sqrt(v / (double)n);
+        if (v < 1e-12) v = 1.0;
+    }
+    std::vector<float> norm(2 * SG_NFEAT + 2 * SG_NOUT);
+    for (int k = 0; k < SG_NFEAT; k++) norm[k] = (float)mu[k], norm[SG_NFEAT + k] = (float)sd[k];
+    for (int k = 0; k < SG_NOUT; k++)
+        norm[2 * SG_NFEAT + k] = (float)mu[SG_NFEAT + k], norm[2 * SG_NFEAT + SG_NOUT + k] = (float)sd[SG_NFEAT + k];
+    std::vector<float> Xn((size_t)n * SG_NFEAT), Yn((size_t)n * SG_NOUT);
+    for (int64_t i = 0; i < n; i++) {
+        for (int k = 0; k < SG_NFEAT; k++) Xn[i * SG_NFEAT + k] = (float)((feat[i * SG_NFEAT + k] - mu[k]) / sd[k]);
+        for (int k = 0; k < SG_NOUT; k++)
+            Yn[i * SG_NOUT + k] = (float)((targ[i * SG_NOUT + k] - mu[SG_NFEAT + k]) / sd[SG_NFEAT + k]);
+    }
+    // Glorot-uniform initial weights, zero biases
+    std::mt19937_64 rng(seed);
+    std::vector<float> params(SG_NPARAMS, 0.f);
+    const int sizes[4][2] = {{SG_NFEAT, 64}, {64, 64}, {64, 64}, {64, SG_NOUT}};
+    for (int l = 0, off = 0; l < 4; l++) {
+        const int fi = sizes[l][0], fo = sizes[l][1];
+        std::uniform_real_distribution<double> U(-sqrt(6.0 / (fi + fo)), sqrt(6.0 / (fi + fo)));
+        for (int k = 0; k < fi * fo; k++) params[off + k] = (float)U(rng);
+        off += fi * fo + fo;
+    }
+    st = pibm_surrogate_set_params(ctx, params.data(), norm.data());
+    if (st != PIBM_OK) return st;
+    const int B = (int)std::min<int64_t>(batch, n);
+    float* dX = (float*)dalloc(ctx, sizeof(float) * Xn.size(), GRP_SCRATCH);
+    float* dY = (float*)dalloc(ctx, sizeof(float) * Yn.size(), GRP_SCRATCH);
+    int* didx = (int*)dalloc(ctx, sizeof(int) * (size_t)n, GRP_SCRATCH);
+    float* xb = (float*)dalloc(ctx, sizeof(float) * SG_NFEAT * (size_t)B, GRP_SCRATCH);
+    float* yb = (float*)dalloc(ctx, sizeof(float) * SG_NOUT * (size_t)B, GRP_SCRATCH);
+    double* dl = (double*)dalloc(ctx, sizeof(double) * 2, GRP_SCRATCH);
+    if (!dX || !dY || !didx || !xb || !yb || !dl) {
+        dfree_group(ctx, GRP_SCRATCH);
+        return fail(ctx, PIBM_ERR_OOM, "training buffers");
+    }
+    cudaError_t e = cudaMemcpyAsync(dX, Xn.data(), sizeof(float) * Xn.size(), cudaMemcpyHostToDevice, c.s0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dY, Yn.data(), sizeof(float) * Yn.size(), cudaMemcpyHostToDevice, c.s0);
+    std::vector<int> idx((size_t)n);
+    for (int64_t i = 0; i < n; i++) idx[i] = (int)i;
+    const int64_t nb = n / B;  // full batches per epoch
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ep++) {
+        std::shuffle(idx.begin(), idx.end(), rng);
+        e = cudaMemcpyAsync(didx, idx.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, c.s0);
+        double loss_sum = 0.0;
+        for (int64_t b = 0; b < nb && e == cudaSuccess; b++) {
+            e = launch_gather(c.s0, B, didx + b * B, dX, dY, xb, yb);
+            if (e == cudaSuccess) e = train_batch(&c, c.s0, xb, yb, B, (float)lr, nullptr, dl);
+            if (e == cudaSuccess && loss_per_epoch) {
+                double lv = 0.0;
+                e = cudaMemcpyAsync(&lv, dl, sizeof(double), cudaMemcpyDeviceToHost, c.s0);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(c.s0);
+                loss_sum += lv;
+            }
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.s0);
+        if (loss_per_epoch) loss_per_epoch[ep] = nb > 0 ? loss_sum / (double)nb : 0.0;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.s0);
+    dfree_group(ctx, GRP_SCRATCH);
+    if (e != cudaSuccess) return fail(ctx, PIBM_ERR_CUDA, std::string("training: ") + cudaGetErrorString(e));
+    drop_graphs(c);
+    return PIBM_OK;
+}
+
+pibm_status pibm_surrogate_enable(pibm_ctx* ctx, int on, double bound, double delta) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    drop_graphs(c);
+    if (!on) {
+        c.sg.enabled = 0;
+        if (!c.sg.fixed) c.dem.J = nullptr, c.dem.J_on = nullptr;
+        return PIBM_OK;
+    }
+    if (!c.sg.trained) return fail(ctx, PIBM_ERR_STATE, "surrogate has no parameters yet");
+    if (c.np == 0) return fail(ctx, PIBM_ERR_STATE, "no particles");
+    if (!(bound >= 0) || !(delta > 0)) return fail(ctx, PIBM_ERR_ARG, "bound must be >= 0 and delta > 0");
+    pibm_status st = sg_ensure(ctx);
+    if (st != PIBM_OK) return st;
+    c.sg.enabled = 1;
+    c.sg.fixed = 0;
+    c.sg.bound = bound;
+    c.sg.delta = delta;
+    c.dem.J = c.sg.J;
+    c.dem.J_on = c.sg.J_on;
+    PCHECK(cudaMemsetAsync(c.sg.stats, 0, sizeof(double) * 4, c.s0));
+    PCHECK(cudaMemsetAsync(c.sg.err, 0, sizeof(int), c.s0));
+    PCHECK(launch_surrogate(&c, c.s0, parity(c)));  // Jacobian and gate of the current state for the next step
+    PCHECK(cudaStreamSynchronize(c.s0));
+    return PIBM_OK;
+}
+
+pibm_status pibm_surrogate_stats(pibm_ctx* ctx, double* out) {
+    if (!ctx || !out) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    out[0] = out[1] = out[2] = 0.0;
+    if (!c.sg.stats) return PIBM_OK;
+    PCHECK(cudaMemcpyAsync(out, c.sg.stats, sizeof(double) * 3, cudaMemcpyDeviceToHost, c.s0));
+    PCHECK(cudaStreamSynchronize(c.s0));
+    return PIBM_OK;
+}
+
+pibm_status pibm_read_hydro_jacobian(pibm_ctx* ctx, double* J, int* on) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!c.dem.J) return fail(ctx, PIBM_ERR_STATE, "no hydrodynamic Jacobian in use");
+    std::vector<float> h((size_t)18 * c.np);
+    int o = 0;
+    PCHECK(cudaMemcpyAsync(h.data(), c.dem.J, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, c.s0));
+    PCHECK(cudaMemcpyAsync(&o, c.dem.J_on, sizeof(int), cudaMemcpyDeviceToHost, c.s0));
+    PCHECK(cudaStreamSynchronize(c.s0));
+    if (J)
+        for (size_t k = 0; k < h.size(); k++) J[k] = h[k];
+    if (on) *on = o;
+    return PIBM_OK;
+}
+
+pibm_status pibm_set_hydro_jacobian(pibm_ctx* ctx, const double* J) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    drop_graphs(c);
+    if (!J) {
+        c.sg.fixed = 0;
+        if (!c.sg.enabled) c.dem.J = nullptr, c.dem.J_on = nullptr;
+        return PIBM_OK;
+    }
+    if (c.np == 0) return fail(ctx, PIBM_ERR_STATE, "no particles");
+    pibm_status st = sg_ensure(ctx);
+    if (st != PIBM_OK) return st;
+    std::vector<float> h((size_t)18 * c.np);
+    for (size_t k = 0; k < h.size(); k++) h[k] = (float)J[k];
+    const int one = 1;
+    PCHECK(cudaMemcpyAsync(c.sg.J, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, c.s0));
+    PCHECK(cudaMemcpyAsync(c.sg.J_on, &one, sizeof(int), cudaMemcpyHostToDevice, c.s0));
+    PCHECK(cudaStreamSynchronize(c.s0));
+    c.sg.enabled = 0;
+    c.sg.fixed = 1;
+    c.dem.J = c.sg.J;
+    c.dem.J_on = c.sg.J_on;
+    return PIBM_OK;
 }
 
 pibm_status pibm_kernels_per_step(pibm_ctx* ctx, int* n) {

@@ -250,10 +250,25 @@ struct Priv {
 };
 
 // velocity Verlet half kick: U += h (F_c/m + a_ext), omega += h (T_c/I + alpha_ext)
-__device__ __forceinline__ void kick_s(Priv& P, double h, int dim) {
+// Velocity Verlet half or full kick.  J (optional, per particle: J_FU then
+// J_TW, row-major) is a learned estimate of d(hydrodynamic force)/dU and
+// d(hydrodynamic torque)/domega; the held hydrodynamic load is then corrected
+// by J_FU (U - U0) and J_TW (omega - omega0), with U0, omega0 the velocities
+// at the start of the lattice step.
+__device__ __forceinline__ void kick_s(Priv& P, double h, int dim, const float* J, const double* U0, const double* W0) {
+    double dF[3] = {0.0, 0.0, 0.0}, dT[3] = {0.0, 0.0, 0.0};
+    if (J) {
+        double du[3], dw[3];
+        for (int b = 0; b < 3; b++) du[b] = P.U[b] - U0[b], dw[b] = P.W[b] - W0[b];
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) {
+                dF[a] += (double)J[3 * a + b] * du[b];
+                dT[a] += (double)J[9 + 3 * a + b] * dw[b];
+            }
+    }
     for (int a = 0; a < 3; a++) {
-        P.U[a] += h * ((double)P.Fc[a] * P.im + (double)P.a[a]);
-        P.W[a] += h * ((double)P.Tc[a] * P.iI + (double)P.al[a]);
+        P.U[a] += h * ((double)P.Fc[a] * P.im + (double)P.a[a] + dF[a] * P.im);
+        P.W[a] += h * ((double)P.Tc[a] * P.iI + (double)P.al[a] + dT[a] * P.iI);
     }
     if (dim == 2) {
         P.U[2] = 0.0;
@@ -307,6 +322,8 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
     const float dtf = (float)dt;
     int gnow = gbase;  // global substep counter after this launch
 
+    // the learned hydrodynamic Jacobian, when set and passed by its gate
+    const bool useJ = C.J != nullptr && __ldcg(C.J_on) != 0;
     if (advance) {
         const int hp = __ldcg(S.have_prev);
         // load the private state once; external accelerations are constant over the lattice step
@@ -334,7 +351,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 P.al[a] = (float)(hydro(S.Th, S.Thp, 3 * p + a, hp) * P.iI);
             }
             if (!P.fixed) {
-                kick_s(P, 0.5 * dt, D);
+                kick_s(P, 0.5 * dt, D, useJ ? C.J + 18 * p : nullptr, S.U + 3 * p, S.W + 3 * p);
                 drift_s(P, dt, pub[l]);
             } else {
                 publish_s(P, pub[l]);
@@ -411,11 +428,12 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                     publish_s(P, pub[(rb ^ 1) * per + l]);
                     continue;
                 }
+                const float* Jp = useJ ? C.J + 18 * p : nullptr;
                 if (sub + 1 < nsub) {  // closing half kick of this substep + opening half kick of the next
-                    kick_s(P, dt, D);
+                    kick_s(P, dt, D, Jp, S.U + 3 * p, S.W + 3 * p);
                     drift_s(P, dt, pub[(rb ^ 1) * per + l]);
                 } else {
-                    kick_s(P, 0.5 * dt, D);
+                    kick_s(P, 0.5 * dt, D, Jp, S.U + 3 * p, S.W + 3 * p);
                 }
             }
             cl.sync();

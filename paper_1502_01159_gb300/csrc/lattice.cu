@@ -700,6 +700,200 @@ static cudaError_t macro_launch(Ctx* c, int field, int parity) {
 
 cudaError_t launch_macro(Ctx* c, int field, int parity) { PIBM_DISPATCH(c, macro_launch, c, field, parity); }
 
+// --------------------------------------------------- surrogate features
+// Per-particle features of the learned coupling surrogate (one CTA per
+// particle).  Region S_p = the nodes the particle covers, |r - X_p| < R_p + 1/2
+// (distance in FP64 without contraction, as the reference computes it); over
+// S_p the raw fluid velocity j / rho (the moments before the coupling's
+// correction) is fitted by a rigid motion V + Om x d about X_p (least
+// squares, d = r - X_p):  n V - D x Om = sum u,  D x V + M Om = sum d x u,
+// D = sum d, M = sum (|d|^2 I - d d^T)  (2-D: unknowns V_x, V_y, Om_z).
+// Features: U_p - V (3), omega_p - Om (3), T_p - mean raw T over S_p (1), the
+// solid fraction sum_{q != p, |X_q - X_p| < 4 R_p} (R_q / 4 R_p)^D (1), and
+// the four smallest surface gaps |X_q - X_p| - R_p - R_q capped at 2 R_p (4).
+constexpr int FEAT_T = 128;
+
+// Gaussian elimination with partial pivoting on an m x m system (m <= 6).
+__device__ void solve_small(double* A, double* b, int m) {
+    for (int k = 0; k < m; k++) {
+        int piv = k;
+        for (int i = k + 1; i < m; i++)
+            if (fabs(A[i * 6 + k]) > fabs(A[piv * 6 + k])) piv = i;
+        if (piv != k) {
+            for (int j = 0; j < m; j++) {
+                double t = A[k * 6 + j];
+                A[k * 6 + j] = A[piv * 6 + j];
+                A[piv * 6 + j] = t;
+            }
+            double t = b[k];
+            b[k] = b[piv];
+            b[piv] = t;
+        }
+        const double inv = 1.0 / A[k * 6 + k];
+        for (int i = k + 1; i < m; i++) {
+            const double l = A[i * 6 + k] * inv;
+            for (int j = k; j < m; j++) A[i * 6 + j] -= l * A[k * 6 + j];
+            b[i] -= l * b[k];
+        }
+    }
+    for (int k = m - 1; k >= 0; k--) {
+        double s = b[k];
+        for (int j = k + 1; j < m; j++) s -= A[k * 6 + j] * b[j];
+        b[k] = s / A[k * 6 + k];
+    }
+}
+
+template <int D, typename S>
+__global__ void __launch_bounds__(FEAT_T) k_features(Geo G, const S* f, const S* g, const typename Store<S>::V4* fb,
+                                                     const uint8_t* flags, CollideParams<double> P, int parity, int n,
+                                                     const double* X, const double* U, const double* W, const double* R,
+                                                     const double* Tp, double* out) {
+    __shared__ double red[18][FEAT_T];
+    __shared__ double gaps_sh[4 * FEAT_T];
+    const int p = blockIdx.x;
+    const double xp = X[3 * p], yp = X[3 * p + 1], zp = D == 3 ? X[3 * p + 2] : 0.0;
+    const double Rp = R[p];
+    const int nl[3] = {G.nx, G.ny, G.nz};
+    const double xc[3] = {xp, yp, zp};
+    int lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
+    for (int a = 0; a < D; a++) {
+        int l0 = (int)floor(xc[a] - Rp - 1.0), h0 = (int)ceil(xc[a] + Rp + 1.0);
+        l0 = l0 < 0 ? 0 : l0;
+        h0 = h0 > nl[a] - 1 ? nl[a] - 1 : h0;
+        lo[a] = l0;
+        ext[a] = h0 >= l0 ? h0 - l0 + 1 : 0;
+    }
+    double acc[17];
+    for (int k = 0; k < 17; k++) acc[k] = 0.0;
+    const long long total = (long long)ext[0] * ext[1] * ext[2];
+    for (long long k = threadIdx.x; k < total; k += FEAT_T) {
+        const int x = lo[0] + (int)(k % ext[0]);
+        const int y = lo[1] + (int)((k / ext[0]) % ext[1]);
+        const int z = lo[2] + (int)(k / ((long long)ext[0] * ext[1]));
+        const double dx = (double)x - xp, dy = (double)y - yp, dz = D == 3 ? (double)z - zp : 0.0;
+        double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+        if (D == 3) d2 = __dadd_rn(d2, __dmul_rn(dz, dz));
+        const double r = sqrt(d2);
+        if (!(r < Rp + 0.5)) continue;
+        // raw moments (before the coupling's correction): the coupling acts on
+        // exactly these, F_f = 2 (rho U_l - j) (Eq lbm8 as read), Q = 2 kappa (T_p - T0)
+        using L = Lat<D>;
+        double s[L::Q], sg[L::QG];
+        load_node<D, S, double>(G, f, g, x, y, z, parity, s, sg);
+        double drho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0, dT = 0.0;
+        for (int i = 0; i < L::Q; i++) {
+            drho += s[i];
+            jx += L::ex(i) * s[i], jy += L::ey(i) * s[i], jz += L::ez(i) * s[i];
+        }
+        for (int k = 0; k < L::QG; k++) dT += sg[k];
+        const double rho = 1.0 + drho;
+        const double ux = jx / rho, uy = jy / rho, uz = D == 3 ? jz / rho : 0.0;
+        const double T0 = P.Tref + dT;
+        acc[0] += 1.0;
+        acc[1] += dx, acc[2] += dy, acc[3] += dz;
+        acc[4] += dx * dx, acc[5] += dy * dy, acc[6] += dz * dz;
+        acc[7] += dx * dy, acc[8] += dx * dz, acc[9] += dy * dz;
+        acc[10] += ux, acc[11] += uy, acc[12] += uz;
+        acc[13] += dy * uz - dz * uy, acc[14] += dz * ux - dx * uz, acc[15] += dx * uy - dy * ux;
+        acc[16] += T0;
+    }
+    // neighbours: solid fraction and the four smallest gaps
+    double phi = 0.0;
+    double gd4[4] = {1e300, 1e300, 1e300, 1e300};
+    for (int q = threadIdx.x; q < n; q += FEAT_T) {
+        if (q == p) continue;
+        const double ex = X[3 * q] - xp, ey = X[3 * q + 1] - yp, ez = X[3 * q + 2] - X[3 * p + 2];
+        const double dist = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
+        const double Rq = R[q];
+        if (dist < 4.0 * Rp) {
+            const double s = Rq / (4.0 * Rp);
+            phi += D == 3 ? s * s * s : s * s;
+        }
+        double gap = (dist - Rp) - Rq;
+        for (int k = 0; k < 4; k++)  // insert into the sorted four
+            if (gap < gd4[k]) {
+                double t = gd4[k];
+                gd4[k] = gap;
+                gap = t;
+            }
+    }
+    for (int k = 0; k < 17; k++) red[k][threadIdx.x] = acc[k];
+    red[17][threadIdx.x] = phi;
+    for (int k = 0; k < 4; k++) gaps_sh[4 * threadIdx.x + k] = gd4[k];
+    __syncthreads();
+    // thread 0 combines in thread order (deterministic) and merges the gaps
+    if (threadIdx.x == 0) {
+        double s[18];
+        for (int k = 0; k < 18; k++) {
+            double v = 0.0;
+            for (int t = 0; t < FEAT_T; t++) v += red[k][t];
+            s[k] = v;
+        }
+        double best[4] = {1e300, 1e300, 1e300, 1e300};
+        for (int t = 0; t < 4 * FEAT_T; t++) {
+            double gap = gaps_sh[t];
+            for (int k = 0; k < 4; k++)
+                if (gap < best[k]) {
+                    double tt = best[k];
+                    best[k] = gap;
+                    gap = tt;
+                }
+        }
+        double V[3] = {0, 0, 0}, Om[3] = {0, 0, 0};
+        const double m = s[0];
+        if (m > 0) {
+            double A[36], b[6];
+            if (D == 3) {
+                const double Dd[3] = {s[1], s[2], s[3]};
+                const double trace = s[4] + s[5] + s[6];
+                const double M[9] = {trace - s[4], -s[7], -s[8], -s[7], trace - s[5], -s[9], -s[8], -s[9], trace - s[6]};
+                // [D]x: cross-product matrix of D
+                const double Dx[9] = {0, -Dd[2], Dd[1], Dd[2], 0, -Dd[0], -Dd[1], Dd[0], 0};
+                for (int i = 0; i < 3; i++)
+                    for (int j = 0; j < 3; j++) {
+                        A[i * 6 + j] = i == j ? m : 0.0;
+                        A[i * 6 + 3 + j] = -Dx[i * 3 + j];
+                        A[(3 + i) * 6 + j] = Dx[i * 3 + j];
+                        A[(3 + i) * 6 + 3 + j] = M[i * 3 + j];
+                    }
+                b[0] = s[10], b[1] = s[11], b[2] = s[12], b[3] = s[13], b[4] = s[14], b[5] = s[15];
+                solve_small(A, b, 6);
+                V[0] = b[0], V[1] = b[1], V[2] = b[2], Om[0] = b[3], Om[1] = b[4], Om[2] = b[5];
+            } else {
+                A[0] = m, A[1] = 0.0, A[2] = -s[2];
+                A[6] = 0.0, A[7] = m, A[8] = s[1];
+                A[12] = -s[2], A[13] = s[1], A[14] = s[4] + s[5];
+                b[0] = s[10], b[1] = s[11], b[2] = s[15];
+                solve_small(A, b, 3);
+                V[0] = b[0], V[1] = b[1], Om[2] = b[2];
+            }
+        }
+        double* o = out + 12 * (long long)p;
+        for (int a = 0; a < 3; a++) {
+            o[a] = U[3 * p + a] - V[a];
+            o[3 + a] = W[3 * p + a] - Om[a];
+        }
+        o[6] = Tp[p] - (m > 0 ? s[16] / m : 0.0);
+        o[7] = s[17];
+        const double cap = 2.0 * Rp;
+        for (int k = 0; k < 4; k++) o[8 + k] = best[k] < cap ? best[k] : cap;
+    }
+}
+
+template <int D, typename S>
+static cudaError_t features_launch(Ctx* c, cudaStream_t s, int parity, double* out) {
+    if (c->np == 0) return cudaSuccess;
+    using V = typename Store<S>::V4;
+    k_features<D, S><<<c->np, FEAT_T, 0, s>>>(c->G, (const S*)c->f, (const S*)c->g, (const V*)c->fb[parity],
+                                              c->flags[parity], collide_params<double>(c), parity, c->np, c->X, c->U,
+                                              c->W, c->R, c->Tp, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_features(Ctx* c, cudaStream_t s, int parity, double* out) {
+    PIBM_DISPATCH(c, features_launch, c, s, parity, out);
+}
+
 // ------------------------------------------------------------ diagnostics
 // Deterministic two-level reduction: a fixed grid of 512 blocks writes
 // partials, one block combines them in a fixed order.

@@ -221,6 +221,28 @@ struct DemCfg {
     int cap;          // capacity of the canonical pair list
     int maxnb;        // candidates per particle
     int per;          // particles per CTA of the DEM cluster
+    const float* J;   // learned hydrodynamic Jacobian [n][18] or null
+    const int* J_on;  // device gate: apply J this step when non-zero
+};
+
+// learned coupling surrogate (surrogate.cu)
+constexpr int SG_NFEAT = 12, SG_NOUT = 7;
+constexpr int SG_NPARAMS = 64 * 12 + 64 + 2 * (64 * 64 + 64) + 7 * 64 + 7;
+constexpr int SG_TRAIN_BLOCKS = 152;
+struct Surrogate {
+    float *params, *m, *v, *norm;   // FP32 master parameters, Adam moments, standardisation (38)
+    float *partial, *lossp;          // training reduction scratch
+    int adam_t;
+    int trained;                     // parameters set or trained
+    int enabled;                     // Jacobian pipeline in the step graph
+    int fixed;                       // a caller-supplied Jacobian is in use
+    double bound, delta;
+    int cap;                         // particles the per-particle buffers hold
+    double* feat;                    // [n][12]
+    float *rows, *yrows, *J;         // [7n][16], [7n][8], [n][18]
+    double* part;                    // gate partial sums
+    int *J_on, *err;                 // device gate flag, tensor-core wait status
+    double* stats;                   // [on steps, off steps, last relative error]
 };
 
 struct Ctx {
@@ -277,6 +299,7 @@ struct Ctx {
     int tune_dem_particles_per_cta;  // 0: default (32)
     int tune_pair_lattice;           // 1: two nodes per thread for 16-bit storage (nx a multiple of 64)
     int tune_lattice_threads;        // 0: default block shape; else threads per lattice block
+    Surrogate sg;
     unsigned gen;                    // bumped whenever the captured step graphs become stale
     int* contact_pairs;   // 2 * dem.cap ints
     int* contact_scratch; // 2 * np + 4 ints
@@ -306,6 +329,7 @@ cudaError_t launch_read_plane(Ctx* c, int which, int plane, int parity);    // w
 cudaError_t launch_write_plane(Ctx* c, int which, int plane, int parity);
 cudaError_t launch_macro(Ctx* c, int field, int parity);
 cudaError_t launch_diagnostics(Ctx* c, int parity);
+cudaError_t launch_features(Ctx* c, cudaStream_t s, int parity, double* out);  // n x 12 surrogate features
 // coupling.cu
 cudaError_t launch_coupling(Ctx* c, cudaStream_t s, int parity);
 cudaError_t launch_coupling_clear(Ctx* c, cudaStream_t s, int parity);
@@ -321,6 +345,13 @@ void set_global_error(const std::string& msg);
 int dem_max_per_cta();
 // api.cu: for the ensemble (ensemble.cu)
 cudaError_t record_step(Ctx* c, int parity, int* kernels);
+// surrogate.cu
+cudaError_t launch_mlp(Ctx* c, cudaStream_t s, const float* in, int rows, float* out);
+cudaError_t launch_surrogate(Ctx* c, cudaStream_t s, int parity);
+int surrogate_kernel_count(Ctx* c);
+cudaError_t train_batch(Ctx* c, cudaStream_t s, const float* xb, const float* yb, int B, float lr, float* grad_out,
+                        double* loss_out);
+cudaError_t launch_gather(cudaStream_t s, int B, const int* idx, const float* X, const float* Y, float* xb, float* yb);
 Ctx* ctx_state(pibm_ctx* ctx);
 pibm_status ctx_ready(pibm_ctx* ctx);
 

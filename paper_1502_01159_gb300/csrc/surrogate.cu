@@ -1,0 +1,490 @@
+// Learned coupling surrogate: a 12 -> 64 -> 64 -> 64 -> 7 MLP (tanh hidden
+// layers) that maps per-particle features (relative velocity and spin against
+// the fluid the particle covers, temperature difference, local solid
+// fraction, four nearest surface gaps) to the PIBM coupling's force, torque and
+// heat flux.  Inside the DEM substeps half its secant Jacobian in the
+// particle's velocity and spin corrects the hydrodynamic load held over the
+// lattice step (Eq demgov; the held load is the mean of two couplings, and a
+// velocity change enters the newer one); the PIBM coupling computed every
+// step is the judge, and the correction is switched off for the next step
+// whenever the network's force differs from it by more than the bound.
+//
+//   inference  k_mlp_tc: tcgen05 BF16 tensor-core MMAs (M = 128 rows per CTA,
+//              N = 64 / 16, K = 16 / 64), FP32 accumulators in tensor memory,
+//              bias + tanh epilogue from tcgen05.ld, activations re-staged
+//              as BF16 in shared memory for the next layer
+//   training   k_train_partial / k_train_adam: FP32 forward and backward on
+//              CUDA cores, deterministic two-level gradient reduction, Adam
+//
+// Parameters are FP32, packed [W1 (64x12), b1, W2 (64x64), b2, W3, b3,
+// W4 (7x64), b4] with W[out][in]; standardisation: x_n = (x - mu_x) / sd_x,
+// y = y_n sd_y + mu_y (38 floats: mu_x, sd_x, mu_y, sd_y).
+#include <string.h>
+
+#include <random>
+#include <string>
+#include <vector>
+
+#include "pibm_internal.cuh"
+
+namespace pibm {
+
+constexpr int NF = SG_NFEAT, NO = SG_NOUT, HW = 64;
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + HW * NF, OFF_W2 = OFF_B1 + HW, OFF_B2 = OFF_W2 + HW * HW;
+constexpr int OFF_W3 = OFF_B2 + HW, OFF_B3 = OFF_W3 + HW * HW, OFF_W4 = OFF_B3 + HW, OFF_B4 = OFF_W4 + NO * HW;
+static_assert(OFF_B4 + NO == SG_NPARAMS, "parameter layout");
+
+// ------------------------------------------------------------- tcgen05 MLP
+constexpr int MLP_M = 128;      // rows per CTA (tensor-memory lanes)
+constexpr int MLP_T = 128;      // 4 warps: warp w owns rows / lanes 32w .. 32w + 31
+// shared-memory layout (bytes); operands in the no-swizzle K-major core-matrix
+// layout: element (r, k) at (r / 8) * SBO + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2
+constexpr int SM_X = 0;                       // 128 x 16 bf16   (SBO 256)
+constexpr int SM_H = SM_X + 128 * 16 * 2;     // 128 x 64 bf16   (SBO 1024)
+constexpr int SM_W1 = SM_H + 128 * 64 * 2;    // 64 x 16 bf16    (SBO 256)
+constexpr int SM_W2 = SM_W1 + 64 * 16 * 2;    // 64 x 64 bf16    (SBO 1024)
+constexpr int SM_W3 = SM_W2 + 64 * 64 * 2;
+constexpr int SM_W4 = SM_W3 + 64 * 64 * 2;    // 16 x 64 bf16 (rows 7..15 zero)
+constexpr int SM_BIAS = SM_W4 + 16 * 64 * 2;  // 64 * 3 + 16 floats
+constexpr int SM_BAR = SM_BIAS + (64 * 3 + 16) * 4;
+constexpr int SM_TMEM = SM_BAR + 8;
+constexpr int MLP_SMEM = SM_TMEM + 8 + 1024;  // + alignment slack
+constexpr uint32_t TMEM_COLS = 64;
+
+__device__ __forceinline__ uint32_t core_off(int r, int k, int sbo) {
+    return (uint32_t)((r >> 3) * sbo + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Shared-memory matrix descriptor: start >> 4 (bits 0-13), leading byte
+// offset >> 4 (16-29: the step between core matrices along K), stride byte
+// offset >> 4 (32-45: between 8-row groups), version 1 (bit 46), no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
+// and B (7-9 = 1, 10-12 = 1), both K-major, N >> 3 at 17-22, M >> 4 at 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// bounded wait on an mbarrier phase; false when the limit ran out
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+        "[%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// rows x 16 FP32 standardised inputs (columns 12..15 ignored) -> rows x 8
+// FP32 standardised outputs (columns 7 ignored).  err: set to 1 when a bounded
+// wait gave up (the CTA then skips the rest of its work).
+__global__ void __launch_bounds__(MLP_T) k_mlp_tc(const float* __restrict__ params, const float* __restrict__ in, int rows,
+                                                  float* __restrict__ out, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row0 = blockIdx.x * MLP_M;
+    float* bias = reinterpret_cast<float*>(sm + SM_BIAS);
+    const uint32_t bar = sbase + SM_BAR;
+
+    // weights -> BF16 core-matrix layout; biases; this tile's inputs
+    for (int e = tid; e < 64 * 16; e += MLP_T) {
+        const int n = e >> 4, k = e & 15;
+        reinterpret_cast<__nv_bfloat16*>(sm + SM_W1 + core_off(n, k, 256))[0] =
+            __float2bfloat16_rn(k < NF ? params[OFF_W1 + n * NF + k] : 0.f);
+    }
+    for (int e = tid; e < 64 * 64; e += MLP_T) {
+        const int n = e >> 6, k = e & 63;
+        reinterpret_cast<__nv_bfloat16*>(sm + SM_W2 + core_off(n, k, 1024))[0] = __float2bfloat16_rn(params[OFF_W2 + e]);
+        reinterpret_cast<__nv_bfloat16*>(sm + SM_W3 + core_off(n, k, 1024))[0] = __float2bfloat16_rn(params[OFF_W3 + e]);
+    }
+    for (int e = tid; e < 16 * 64; e += MLP_T) {
+        const int n = e >> 6, k = e & 63;
+        reinterpret_cast<__nv_bfloat16*>(sm + SM_W4 + core_off(n, k, 1024))[0] =
+            __float2bfloat16_rn(n < NO ? params[OFF_W4 + n * HW + k] : 0.f);
+    }
+    for (int e = tid; e < 64; e += MLP_T) {
+        bias[e] = params[OFF_B1 + e];
+        bias[64 + e] = params[OFF_B2 + e];
+        bias[128 + e] = params[OFF_B3 + e];
+    }
+    if (tid < 16) bias[192 + tid] = tid < NO ? params[OFF_B4 + tid] : 0.f;
+    {
+        const int r = tid;  // one input row per thread
+        const int gr = row0 + r;
+        float x[16];
+        for (int k = 0; k < 16; k++) x[k] = (gr < rows && k < NF) ? in[(long long)gr * 16 + k] : 0.f;
+        for (int c = 0; c < 2; c++) {
+            uint4 v = make_uint4(pack_bf16(x[8 * c], x[8 * c + 1]), pack_bf16(x[8 * c + 2], x[8 * c + 3]),
+                                 pack_bf16(x[8 * c + 4], x[8 * c + 5]), pack_bf16(x[8 * c + 6], x[8 * c + 7]));
+            *reinterpret_cast<uint4*>(sm + SM_X + core_off(r, 8 * c, 256)) = v;
+        }
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {  // tensor memory: 64 columns x 128 lanes of FP32 accumulators
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sbase + SM_TMEM),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic smem writes -> tensor-core reads
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + SM_TMEM);
+
+    bool ok = true;
+    for (int layer = 0; layer < 4 && ok; layer++) {
+        const int K = layer == 0 ? 16 : 64, N = layer == 3 ? 16 : 64;
+        const uint32_t a0 = sbase + (layer == 0 ? SM_X : SM_H);
+        const uint32_t b0 = sbase + (layer == 0 ? SM_W1 : layer == 1 ? SM_W2 : layer == 2 ? SM_W3 : SM_W4);
+        const uint32_t sbo = K == 16 ? 256 : 1024;
+        if (tid == 0) {
+            for (int kk = 0; kk < K / 16; kk++)  // K = 16 per MMA: two core matrices along K (256 B)
+                mma_bf16(tmem, smem_desc(a0 + kk * 256, 128, sbo), smem_desc(b0 + kk * 256, 128, sbo),
+                         idesc_bf16(MLP_M, N), kk > 0);
+            mma_commit(bar);
+        }
+        const bool mine = bar_wait(bar, (uint32_t)(layer & 1));
+        ok = __syncthreads_and(mine ? 1 : 0) != 0;  // one block-wide decision (no split barrier below)
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) break;
+        const int r = 32 * warp + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+        if (layer < 3) {
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                float v[16];
+                tmem_ld16(taddr + c0, v);
+                for (int k = 0; k < 16; k++) v[k] = tanhf(v[k] + bias[64 * layer + c0 + k]);
+                for (int h = 0; h < 2; h++) {
+                    const int c = c0 + 8 * h;
+                    uint4 w = make_uint4(pack_bf16(v[8 * h], v[8 * h + 1]), pack_bf16(v[8 * h + 2], v[8 * h + 3]),
+                                         pack_bf16(v[8 * h + 4], v[8 * h + 5]), pack_bf16(v[8 * h + 6], v[8 * h + 7]));
+                    *reinterpret_cast<uint4*>(sm + SM_H + core_off(r, c, 1024)) = w;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        } else {
+            float v[16];
+            tmem_ld16(taddr, v);
+            const int gr = row0 + r;
+            if (gr < rows)
+                for (int k = 0; k < 8; k++) out[(long long)gr * 8 + k] = k < NO ? v[k] + bias[192 + k] : 0.f;
+        }
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
+}
+
+// --------------------------------------------------------- surrogate rows
+// Per particle seven rows: the standardised features, then the same with
+// delta added to each of the six velocity / spin features.
+__global__ void k_sg_rows(int n, const double* __restrict__ feat, const float* __restrict__ norm, float delta,
+                          float* __restrict__ rows) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    float x[NF];
+    for (int k = 0; k < NF; k++) x[k] = (float)((feat[12 * (long long)p + k] - (double)norm[k]) / (double)norm[NF + k]);
+    for (int j = 0; j < 7; j++) {
+        float* r = rows + (7 * (long long)p + j) * 16;
+        for (int k = 0; k < 16; k++) r[k] = k < NF ? x[k] + (j > 0 && k == j - 1 ? delta : 0.f) : 0.f;
+    }
+}
+
+// Jacobian and gate partial sums: J_FU[a][b] = (F_a(row 1+b) - F_a(row 0)) / (delta sd_x[b]),
+// J_TW[a][b] = (tau_a(row 4+b) - tau_a(row 0)) / (delta sd_x[3+b]); partial sums of
+// |F_mlp - F_pibm| and |F_pibm| per block.
+constexpr int GATE_T = 256;
+__global__ void __launch_bounds__(GATE_T) k_sg_jacobian(int n, const float* __restrict__ yrows, const float* __restrict__ norm,
+                                                        float delta, const double* __restrict__ Fh, float* __restrict__ J,
+                                                        double* __restrict__ part) {
+    __shared__ double s0[GATE_T], s1[GATE_T];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0, f = 0.0;
+    if (p < n) {
+        const float* ymu = norm + 2 * NF;
+        const float* ysd = norm + 2 * NF + NO;
+        const float* xsd = norm + NF;
+        float Y[7][NO];
+        for (int j = 0; j < 7; j++)
+            for (int k = 0; k < NO; k++) Y[j][k] = yrows[(7 * (long long)p + j) * 8 + k] * ysd[k] + ymu[k];
+        // The DEM holds the mean of the couplings of t and t-1; a velocity change
+        // enters only the newer of the two, so the held load's sensitivity is
+        // half the coupling's: J = (1/2) secant of the network.
+        float* Jp = J + 18 * (long long)p;
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) {
+                Jp[3 * a + b] = 0.5f * (Y[1 + b][a] - Y[0][a]) / (delta * xsd[b]);
+                Jp[9 + 3 * a + b] = 0.5f * (Y[4 + b][3 + a] - Y[0][3 + a]) / (delta * xsd[3 + b]);
+            }
+        double d2 = 0.0, f2 = 0.0;
+        for (int a = 0; a < 3; a++) {
+            const double fp = Fh[3 * (long long)p + a];
+            d2 += ((double)Y[0][a] - fp) * ((double)Y[0][a] - fp);
+            f2 += fp * fp;
+        }
+        e = sqrt(d2);
+        f = sqrt(f2);
+    }
+    s0[threadIdx.x] = e;
+    s1[threadIdx.x] = f;
+    __syncthreads();
+    for (int w = GATE_T / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            s0[threadIdx.x] += s0[threadIdx.x + w];
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = s0[0];
+        part[2 * blockIdx.x + 1] = s1[0];
+    }
+}
+
+// stats: [0] steps with the Jacobian on, [1] steps off, [2] last relative error
+__global__ void k_sg_gate(int nblocks, const double* part, double bound, const int* mlp_err, int* J_on, double* stats) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double e = 0.0, f = 0.0;
+    for (int b = 0; b < nblocks; b++) e += part[2 * b], f += part[2 * b + 1];
+    const double rel = f > 0.0 ? e / f : (e > 0.0 ? 1e300 : 0.0);
+    const int on = (rel <= bound && *mlp_err == 0) ? 1 : 0;
+    *J_on = on;
+    stats[on ? 0 : 1] += 1.0;
+    stats[2] = rel;
+}
+
+// ------------------------------------------------------------- training
+// One CTA accumulates the loss gradient of its share of the batch rows in
+// shared memory (rows in chunks of TR), then writes it to its partial slot.
+constexpr int TRAIN_T = 256, TR = 16;
+constexpr int TRAIN_SMEM = (SG_NPARAMS * 2 + TR * (NF + NO + 3 * HW + 3 * HW + NO)) * 4;
+
+__global__ void __launch_bounds__(TRAIN_T) k_train_partial(const float* __restrict__ params, const float* __restrict__ X,
+                                                           const float* __restrict__ Y, int B, float* __restrict__ partial,
+                                                           float* __restrict__ lossp) {
+    extern __shared__ float sh[];
+    float* w = sh;                          // parameters
+    float* gacc = w + SG_NPARAMS;           // gradient accumulator
+    float* x = gacc + SG_NPARAMS;           // [TR][NF]
+    float* y = x + TR * NF;                 // [TR][NO]
+    float* a = y + TR * NO;                 // [3][TR][HW] hidden outputs
+    float* dl = a + 3 * TR * HW;            // [3][TR][HW] hidden deltas
+    float* d4 = dl + 3 * TR * HW;           // [TR][NO] output deltas
+    const int tid = threadIdx.x;
+    for (int k = tid; k < SG_NPARAMS; k += TRAIN_T) w[k] = params[k], gacc[k] = 0.f;
+    const int per = (B + gridDim.x - 1) / gridDim.x;
+    const int r0 = blockIdx.x * per, r1 = min(B, r0 + per);
+    const float scale = 2.f / ((float)B * NO);
+    float lsum = 0.f;
+    __syncthreads();
+    for (int c0 = r0; c0 < r1; c0 += TR) {
+        const int nr = min(TR, r1 - c0);
+        for (int e = tid; e < TR * NF; e += TRAIN_T) x[e] = (e / NF) < nr ? X[(long long)(c0 + e / NF) * NF + e % NF] : 0.f;
+        for (int e = tid; e < TR * NO; e += TRAIN_T) y[e] = (e / NO) < nr ? Y[(long long)(c0 + e / NO) * NO + e % NO] : 0.f;
+        __syncthreads();
+        // forward
+        for (int l = 0; l < 3; l++) {
+            const float* W = w + (l == 0 ? OFF_W1 : l == 1 ? OFF_W2 : OFF_W3);
+            const float* bb = w + (l == 0 ? OFF_B1 : l == 1 ? OFF_B2 : OFF_B3);
+            const float* in = l == 0 ? x : a + (l - 1) * TR * HW;
+            const int nin = l == 0 ? NF : HW;
+            for (int e = tid; e < TR * HW; e += TRAIN_T) {
+                const int r = e / HW, o = e % HW;
+                float z = bb[o];
+                for (int i = 0; i < nin; i++) z += W[o * nin + i] * in[r * nin + i];
+                a[l * TR * HW + e] = tanhf(z);
+            }
+            __syncthreads();
+        }
+        for (int e = tid; e < TR * NO; e += TRAIN_T) {
+            const int r = e / NO, o = e % NO;
+            float z = w[OFF_B4 + o];
+            for (int i = 0; i < HW; i++) z += w[OFF_W4 + o * HW + i] * a[2 * TR * HW + r * HW + i];
+            const float diff = r < nr ? z - y[e] : 0.f;
+            d4[e] = scale * diff;
+            lsum += diff * diff;
+        }
+        __syncthreads();
+        // backward through the hidden layers: delta_l = (delta_{l+1} W_{l+1}) * (1 - a_l^2)
+        for (int l = 2; l >= 0; l--) {
+            const float* Wn = w + (l == 2 ? OFF_W4 : l == 1 ? OFF_W3 : OFF_W2);
+            const int nout = l == 2 ? NO : HW;
+            const float* dn = l == 2 ? d4 : dl + (l + 1) * TR * HW;
+            for (int e = tid; e < TR * HW; e += TRAIN_T) {
+                const int r = e / HW, i = e % HW;
+                float s = 0.f;
+                for (int o = 0; o < nout; o++) s += dn[r * nout + o] * Wn[o * HW + i];
+                const float av = a[l * TR * HW + e];
+                dl[l * TR * HW + e] = s * (1.f - av * av);
+            }
+            __syncthreads();
+        }
+        // gradient accumulation: dW_l[o][i] += sum_r delta_l[r][o] in_l[r][i]; db_l[o] += sum_r delta_l[r][o]
+        for (int k = tid; k < SG_NPARAMS; k += TRAIN_T) {
+            int l, o, i, nin;
+            bool isb;
+            if (k < OFF_B1) l = 0, isb = false, o = k / NF, i = k % NF, nin = NF;
+            else if (k < OFF_W2) l = 0, isb = true, o = k - OFF_B1, i = 0, nin = NF;
+            else if (k < OFF_B2) l = 1, isb = false, o = (k - OFF_W2) / HW, i = (k - OFF_W2) % HW, nin = HW;
+            else if (k < OFF_W3) l = 1, isb = true, o = k - OFF_B2, i = 0, nin = HW;
+            else if (k < OFF_B3) l = 2, isb = false, o = (k - OFF_W3) / HW, i = (k - OFF_W3) % HW, nin = HW;
+            else if (k < OFF_W4) l = 2, isb = true, o = k - OFF_B3, i = 0, nin = HW;
+            else if (k < OFF_B4) l = 3, isb = false, o = (k - OFF_W4) / HW, i = (k - OFF_W4) % HW, nin = HW;
+            else l = 3, isb = true, o = k - OFF_B4, i = 0, nin = HW;
+            const float* dlt = l == 3 ? d4 : dl + l * TR * HW;
+            const int nout = l == 3 ? NO : HW;
+            const float* in = l == 0 ? x : a + (l - 1) * TR * HW;
+            float s = 0.f;
+            for (int r = 0; r < nr; r++) s += dlt[r * nout + o] * (isb ? 1.f : in[r * nin + i]);
+            gacc[k] += s;
+        }
+        __syncthreads();
+    }
+    for (int k = tid; k < SG_NPARAMS; k += TRAIN_T) partial[(long long)blockIdx.x * SG_NPARAMS + k] = gacc[k];
+    // loss partial (deterministic: fixed-order block reduction)
+    __shared__ float lred[TRAIN_T];
+    lred[tid] = lsum;
+    __syncthreads();
+    if (tid == 0) {
+        float s = 0.f;
+        for (int t = 0; t < TRAIN_T; t++) s += lred[t];
+        lossp[blockIdx.x] = s;
+    }
+}
+
+// Sum the partials in block order; optional Adam step (lr > 0); optional gradient copy.
+__global__ void k_train_adam(int G, const float* __restrict__ partial, const float* __restrict__ lossp, float* params,
+                             float* m, float* v, int t, float lr, float* grad_out, double* loss_out, int B) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0 && loss_out) {
+        double s = 0.0;
+        for (int g = 0; g < G; g++) s += lossp[g];
+        *loss_out = s / ((double)B * NO);
+    }
+    if (k >= SG_NPARAMS) return;
+    float gsum = 0.f;
+    for (int g = 0; g < G; g++) gsum += partial[(long long)g * SG_NPARAMS + k];
+    if (grad_out) grad_out[k] = gsum;
+    if (lr > 0.f) {
+        const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+        const float mm = b1 * m[k] + (1.f - b1) * gsum;
+        const float vv = b2 * v[k] + (1.f - b2) * gsum * gsum;
+        m[k] = mm;
+        v[k] = vv;
+        const float mh = mm / (1.f - powf(b1, (float)t)), vh = vv / (1.f - powf(b2, (float)t));
+        params[k] -= lr * mh / (sqrtf(vh) + eps);
+    }
+}
+
+__global__ void k_gather_rows(int B, const int* __restrict__ idx, const float* __restrict__ X, const float* __restrict__ Y,
+                              float* __restrict__ xb, float* __restrict__ yb) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= B) return;
+    const long long s = idx[e];
+    for (int k = 0; k < NF; k++) xb[(long long)e * NF + k] = X[s * NF + k];
+    for (int k = 0; k < NO; k++) yb[(long long)e * NO + k] = Y[s * NO + k];
+}
+
+// ------------------------------------------------------------- launchers
+cudaError_t launch_mlp(Ctx* c, cudaStream_t s, const float* in, int rows, float* out) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, MLP_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (rows <= 0) return cudaSuccess;
+    k_mlp_tc<<<(rows + MLP_M - 1) / MLP_M, MLP_T, MLP_SMEM, s>>>(c->sg.params, in, rows, out, c->sg.err);
+    return cudaGetLastError();
+}
+
+// features of the current state -> rows -> MLP -> Jacobian and gate (step graph, stream s)
+cudaError_t launch_surrogate(Ctx* c, cudaStream_t s, int parity) {
+    if (c->np == 0) return cudaSuccess;
+    cudaError_t e = launch_features(c, s, parity, c->sg.feat);
+    if (e != cudaSuccess) return e;
+    k_sg_rows<<<(c->np + 127) / 128, 128, 0, s>>>(c->np, c->sg.feat, c->sg.norm, (float)c->sg.delta, c->sg.rows);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_mlp(c, s, c->sg.rows, 7 * c->np, c->sg.yrows)) != cudaSuccess) return e;
+    const int nb = (c->np + GATE_T - 1) / GATE_T;
+    k_sg_jacobian<<<nb, GATE_T, 0, s>>>(c->np, c->sg.yrows, c->sg.norm, (float)c->sg.delta, c->Fh, c->sg.J, c->sg.part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_sg_gate<<<1, 32, 0, s>>>(nb, c->sg.part, c->sg.bound, c->sg.err, c->sg.J_on, c->sg.stats);
+    return cudaGetLastError();
+}
+
+int surrogate_kernel_count(Ctx* c) { return (c->sg.enabled && c->np > 0) ? 5 : 0; }
+
+// Gradient (and optionally an Adam step) of one batch already on the device.
+cudaError_t train_batch(Ctx* c, cudaStream_t s, const float* xb, const float* yb, int B, float lr, float* grad_out,
+                        double* loss_out) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_train_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, TRAIN_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int G = (B + 63) / 64 < SG_TRAIN_BLOCKS ? (B + 63) / 64 : SG_TRAIN_BLOCKS;
+    k_train_partial<<<G, TRAIN_T, TRAIN_SMEM, s>>>(c->sg.params, xb, yb, B, c->sg.partial, c->sg.lossp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (lr > 0.f) c->sg.adam_t++;
+    k_train_adam<<<(SG_NPARAMS + 255) / 256, 256, 0, s>>>(G, c->sg.partial, c->sg.lossp, c->sg.params, c->sg.m, c->sg.v,
+                                                         c->sg.adam_t, lr, grad_out, loss_out, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(cudaStream_t s, int B, const int* idx, const float* X, const float* Y, float* xb, float* yb) {
+    k_gather_rows<<<(B + 255) / 256, 256, 0, s>>>(B, idx, X, Y, xb, yb);
+    return cudaGetLastError();
+}
+
+}  // namespace pibm

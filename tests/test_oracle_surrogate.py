@@ -1,0 +1,142 @@
+"""Pins of the surrogate's reference (oracle/surrogate.py) against closed forms:
+region statistics of uniform and rigidly rotating fields, gaps of a known
+arrangement, backpropagation against central differences, the first Adam step,
+BF16 rounding, and the secant Jacobian of a network whose answer is known."""
+import numpy as np
+import pytest
+
+from oracle import surrogate as S
+
+
+def _fields(shape_zyx, fn):
+    nz, ny, nx = shape_zyx
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ux, uy, uz, T = fn(x.astype(float), y.astype(float), z.astype(float))
+    return {"rho": np.ones(shape_zyx), "ux": ux, "uy": uy, "uz": uz, "T": T}
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_region_statistics_of_uniform_flow_and_rigid_rotation(dim):
+    # a uniform stream plus a rigid rotation about the particle centre: the
+    # rigid-motion fit returns both exactly on any (asymmetric) region, so a
+    # particle moving with the stream and spinning with the fluid has zero
+    # relative velocity and spin
+    Xc = np.array([10.3, 11.7, 9.4 if dim == 3 else 0.0])
+    U0 = np.array([0.01, -0.02, 0.005 if dim == 3 else 0.0])
+    Om = np.array([0.003, -0.001, 0.002]) if dim == 3 else np.array([0.0, 0.0, 0.002])
+    shape = (21, 23, 22) if dim == 3 else (1, 23, 22)
+
+    def fn(x, y, z):
+        d = np.stack([x - Xc[0], y - Xc[1], (z - Xc[2]) if dim == 3 else 0 * z], axis=-1)
+        u = U0 + np.cross(Om, d)
+        return u[..., 0], u[..., 1], u[..., 2], 0.7 + 0 * x
+
+    f = _fields(shape, fn)
+    feat = S.features(f, np.array([Xc]), np.array([U0]), np.array([Om]), np.array([3.2]), np.array([1.0]), dim)
+    assert np.max(np.abs(feat[0, 0:6])) < 1e-15
+    assert abs(feat[0, 6] - 0.3) < 1e-14
+    # moving particle: the relative velocity is U_p minus the stream
+    feat = S.features(f, np.array([Xc]), np.array([U0 + 0.1]), np.array([Om]), np.array([3.2]), np.array([1.0]), dim)
+    assert np.allclose(feat[0, 0:dim], 0.1, atol=1e-14)
+
+
+def test_region_is_the_covered_disk():
+    nodes = S.region(np.array([5.0, 5.0, 0.0]), 2.0, (11, 11, 1), 2)
+    r = np.hypot(nodes[:, 0] - 5.0, nodes[:, 1] - 5.0)
+    # x^2 + y^2 < 6.25: r^2 in {0, 1, 2, 4, 5}: 1 + 4 + 4 + 4 + 8 points
+    assert np.all(r < 2.5) and len(nodes) == 21
+
+
+def test_gaps_and_solid_fraction_of_a_row():
+    # equal spheres on a line at spacing 2R + g: gaps of the middle one are g, g,
+    # 2R + 2g capped at 2R, ...; phi counts the neighbours closer than 4R
+    R, g = 2.0, 0.5
+    n = 5
+    X = np.zeros((n, 3))
+    X[:, 0] = 10 + np.arange(n) * (2 * R + g)
+    f = _fields((20, 20, 40), lambda x, y, z: (0 * x, 0 * x, 0 * x, 0 * x))
+    feat = S.features(f, X + np.array([0, 10, 10]), np.zeros((n, 3)), np.zeros((n, 3)), np.full(n, R), np.zeros(n), 3)
+    mid = feat[2]
+    assert np.allclose(mid[8:12], [g, g, 2 * R, 2 * R])
+    # centres within 4R = 8 of the middle one: the two at 4.5 (the next at 9 is out)
+    assert abs(mid[7] - 2 * (R / (4 * R)) ** 3) < 1e-15
+    end = feat[0]
+    assert np.allclose(end[8:12], [g, 2 * R, 2 * R, 2 * R])
+
+
+def test_backprop_matches_central_differences():
+    gen = np.random.default_rng(3)
+    params = S.init_params(11)
+    params = [(W, gen.normal(size=b.shape) * 0.1) for W, b in params]
+    X = gen.normal(size=(9, S.N_FEAT))
+    Y = gen.normal(size=(9, S.N_OUT))
+    loss, grads = S.loss_and_grads(params, X, Y)
+    flat = S.flatten(params)
+    gflat = S.flatten(grads)
+    h = 1e-6
+    for k in gen.choice(len(flat), 40, replace=False):
+        e = np.zeros_like(flat)
+        e[k] = h
+        lp, _ = S.loss_and_grads(S.unflatten(flat + e), X, Y)
+        lm, _ = S.loss_and_grads(S.unflatten(flat - e), X, Y)
+        assert abs((lp - lm) / (2 * h) - gflat[k]) < 1e-7 * max(1.0, abs(gflat[k])), k
+    assert len(flat) == S.N_PARAMS
+
+
+def test_first_adam_step_is_signed_learning_rate():
+    params = S.init_params(1)
+    grads = [(np.full_like(W, 3.0), np.full_like(b, -2.0)) for W, b in params]
+    zeros = [(np.zeros_like(W), np.zeros_like(b)) for W, b in params]
+    new, m, v = S.adam(params, grads, zeros, zeros, 1, 1e-3)
+    for (W0, b0), (W1, b1) in zip(params, new):
+        assert np.allclose(W1 - W0, -1e-3 * 3 / (3 + 1e-8)) and np.allclose(b1 - b0, 1e-3 * 2 / (2 + 1e-8))
+
+
+def test_bf16_rounding():
+    vals = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -8 + 2 ** -20, -2.5, 3.0e38])
+    exp = np.array([1.0, 1.0, 1.0 + 2 ** -6, 1.0 + 2 ** -7, -2.5, 2.9980e38])
+    got = S.to_bf16(vals)
+    assert np.array_equal(got[:5], exp[:5])
+    assert abs(got[5] / 3.0e38 - 1) < 2 ** -8
+
+
+def test_secant_jacobian_of_a_linear_network():
+    # a network with tiny first-layer weights is linear to first order; make it
+    # exactly linear by checking the secant against forward differences of the
+    # same network and the de-standardisation by a known scale
+    params = S.init_params(5)
+    gen = np.random.default_rng(2)
+    Xraw = gen.normal(size=(4, S.N_FEAT))
+    xmu, xsd = np.zeros(S.N_FEAT), np.full(S.N_FEAT, 2.0)
+    ymu, ysd = np.zeros(S.N_OUT), np.full(S.N_OUT, 3.0)
+    Y, J = S.jacobian(params, xmu, xsd, ymu, ysd, Xraw, delta=1e-6)
+    # analytical derivative of the FP64 network by forward differences on the raw input
+    for b in range(3):
+        Xp = Xraw.copy()
+        Xp[:, b] += 1e-6 * 2.0
+        Yp = S.forward(params, (Xp - xmu) / xsd)[-1] * ysd + ymu
+        assert np.allclose(J[:, b:9:3], (Yp[:, 0:3] - Y[:, 0:3]) / (1e-6 * 2.0), rtol=1e-6, atol=1e-8)
+    assert np.allclose(Y, S.forward(params, (Xraw - xmu) / xsd)[-1] * ysd + ymu)
+    assert S.gate_error(Y[:, 0:3], Y[:, 0:3]) == 0.0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_raw_fields_of_linear_equilibrium(dim):
+    # first-order equilibrium populations f_i = w_i rho (1 + 3 e_i.u) carry
+    # exactly the momentum rho u; g_k = w_k T sums to T
+    gen = np.random.default_rng(8)
+    E = np.asarray(S._E2 if dim == 2 else S._E3, dtype=float)
+    w = (np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4) if dim == 2
+         else np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12))
+    shape = (1, 5, 6) if dim == 2 else (4, 5, 6)
+    rho = 1 + 0.01 * gen.random(shape)
+    u = 0.01 * gen.normal(size=(3,) + shape)
+    if dim == 2:
+        u[2] = 0
+    f = w[:, None, None, None] * rho[None] * (1 + 3 * np.einsum("qa,a...->q...", E, u))
+    T = gen.random(shape)
+    g = np.stack([T * wk for wk in ([1 / 3] + [1 / 6] * 4 if dim == 2 else [1 / 4] + [1 / 8] * 6)])
+    r = S.raw_fields(f, g, dim)
+    assert np.allclose(r["rho"], rho, rtol=1e-14) and np.allclose(r["T"], T, rtol=1e-14)
+    for a, k in enumerate(("ux", "uy", "uz")):
+        assert np.allclose(r[k], u[a], atol=1e-16)
