@@ -989,11 +989,12 @@ static pibm_status sg_ensure(pibm_ctx* ctx) {
         dfree_group(ctx, GRP_SG_PART);
         const size_t n = (size_t)c.np;
         c.sg.feat = (double*)dalloc(ctx, sizeof(double) * 12 * n, GRP_SG_PART);
+        c.sg.xr = (float4*)dalloc(ctx, sizeof(float4) * n, GRP_SG_PART);
         c.sg.rows = (float*)dalloc(ctx, sizeof(float) * 7 * 16 * n, GRP_SG_PART);
         c.sg.yrows = (float*)dalloc(ctx, sizeof(float) * 7 * 8 * n, GRP_SG_PART);
         c.sg.J = (float*)dalloc(ctx, sizeof(float) * 18 * n, GRP_SG_PART);
         c.sg.part = (double*)dalloc(ctx, sizeof(double) * 2 * (n / 256 + 2), GRP_SG_PART);
-        if (!c.sg.feat || !c.sg.rows || !c.sg.yrows || !c.sg.J || !c.sg.part) {
+        if (!c.sg.feat || !c.sg.xr || !c.sg.rows || !c.sg.yrows || !c.sg.J || !c.sg.part) {
             c.sg.cap = 0;
             return fail(ctx, PIBM_ERR_OOM, "surrogate particle buffers");
         }

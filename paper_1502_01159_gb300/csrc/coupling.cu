@@ -170,15 +170,34 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
         const int ix = x - base[0], iy = y - base[1], iz = z - base[2];
         const float ef = eps_f32(ix, iy, iz, cf, Rpf);
         if (ef <= -EPS_GUARD) continue;  // certainly not covered
-        // eps exactly as the FP64 definition: clamped to 1 deep inside, FP64 on the rim
-        double eps = ef >= 1.0f + EPS_GUARD ? 1.0 : eps_of((double)x, (double)y, (double)z, Xp, Rp);
-        if (!(eps > 0.0)) continue;
+        // eps: 1 deep inside (exact), the FP32 value in the open band, FP64 within
+        // the guard of the clamp points 0 and 1 (there the decision must be exact)
+        float eps;
+        double eps64 = -1.0;  // the FP64 value once computed
+        if (ef >= 1.0f + EPS_GUARD) {
+            eps = 1.0f;
+            eps64 = 1.0;
+        } else if (ef > EPS_GUARD && ef < 1.0f - EPS_GUARD) {
+            eps = ef;
+        } else {
+            eps64 = eps_of((double)x, (double)y, (double)z, Xp, Rp);
+            if (!(eps64 > 0.0)) continue;
+            eps = (float)eps64;
+        }
+        // ownership: the larger eps, ties to the lower index; FP32 decides
+        // unless the two values are within the guard of each other
         bool own = true;
         for (int k = 0; k < nnb; k++) {
-            const float e2f = eps_f32(ix, iy, iz, sh_nbf[k], sh_nbf[k][3]);
-            if (e2f < (float)eps - 2.0f * EPS_GUARD) continue;  // certainly smaller: no contest
-            double e2 = e2f >= 1.0f + EPS_GUARD ? 1.0 : eps_of((double)x, (double)y, (double)z, sh_nb[k], sh_nb[k][3]);
-            if (e2 > eps || (e2 == eps && sh_id[k] < p)) {
+            const float e2r = eps_f32(ix, iy, iz, sh_nbf[k], sh_nbf[k][3]);
+            const float e2f = e2r >= 1.0f + EPS_GUARD ? 1.0f : e2r;
+            if (e2f < eps - 2.0f * EPS_GUARD) continue;  // certainly smaller: no contest
+            if (!(eps == 1.0f && e2f == 1.0f) && e2f > eps + 2.0f * EPS_GUARD) {  // certainly larger
+                own = false;
+                break;
+            }
+            if (eps64 < 0.0) eps64 = eps_of((double)x, (double)y, (double)z, Xp, Rp);
+            const double e2 = e2r >= 1.0f + EPS_GUARD ? 1.0 : eps_of((double)x, (double)y, (double)z, sh_nb[k], sh_nb[k][3]);
+            if (e2 > eps64 || (e2 == eps64 && sh_id[k] < p)) {
                 own = false;
                 break;
             }
@@ -201,7 +220,13 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
         // U_l = U_p + omega_p x (r - X_p)
         const float Ul[3] = {Upf[0] + (Wpf[1] * arm[2] - Wpf[2] * arm[1]), Upf[1] + (Wpf[2] * arm[0] - Wpf[0] * arm[2]),
                              Upf[2] + (Wpf[0] * arm[1] - Wpf[1] * arm[0])};
-        const R e = (R)eps;
+        R e;
+        if constexpr (sizeof(R) == 8) {  // FP64 storage: the exact value
+            if (eps64 < 0.0) eps64 = eps_of((double)x, (double)y, (double)z, Xp, Rp);
+            e = (R)eps64;
+        } else {
+            e = (R)eps;  // FP32 away from the clamp points (error ~1e-7 of eps)
+        }
         R M[4];
 #pragma unroll
         for (int a = 0; a < 3; a++) M[a] = e * (R)2 * (rho * (R)Ul[a] - j[a]);  // eps F_f (Eqs lbm7, lbm8)

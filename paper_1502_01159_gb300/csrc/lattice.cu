@@ -708,9 +708,10 @@ cudaError_t launch_macro(Ctx* c, int field, int parity) { PIBM_DISPATCH(c, macro
 // correction) is fitted by a rigid motion V + Om x d about X_p (least
 // squares, d = r - X_p):  n V - D x Om = sum u,  D x V + M Om = sum d x u,
 // D = sum d, M = sum (|d|^2 I - d d^T)  (2-D: unknowns V_x, V_y, Om_z).
-// Features: U_p - V (3), omega_p - Om (3), T_p - mean raw T over S_p (1), the
-// solid fraction sum_{q != p, |X_q - X_p| < 4 R_p} (R_q / 4 R_p)^D (1), and
-// the four smallest surface gaps |X_q - X_p| - R_p - R_q capped at 2 R_p (4).
+// Features: U_p - V (3), omega_p - Om (3), T_p - mean raw T over S_p (1) here;
+// the solid fraction sum_{q != p, |X_q - X_p| < 4 R_p} (R_q / 4 R_p)^D (1) and
+// the four smallest surface gaps |X_q - X_p| - R_p - R_q capped at 2 R_p (4)
+// in k_neighbour_features.
 constexpr int FEAT_T = 128;
 
 // Gaussian elimination with partial pivoting on an m x m system (m <= 6).
@@ -748,8 +749,7 @@ __global__ void __launch_bounds__(FEAT_T) k_features(Geo G, const S* f, const S*
                                                      const uint8_t* flags, CollideParams<double> P, int parity, int n,
                                                      const double* X, const double* U, const double* W, const double* R,
                                                      const double* Tp, double* out) {
-    __shared__ double red[18][FEAT_T];
-    __shared__ double gaps_sh[4 * FEAT_T];
+    __shared__ double red[17][FEAT_T / 32];
     const int p = blockIdx.x;
     const double xp = X[3 * p], yp = X[3 * p + 1], zp = D == 3 ? X[3 * p + 2] : 0.0;
     const double Rp = R[p];
@@ -797,48 +797,20 @@ __global__ void __launch_bounds__(FEAT_T) k_features(Geo G, const S* f, const S*
         acc[13] += dy * uz - dz * uy, acc[14] += dz * ux - dx * uz, acc[15] += dx * uy - dy * ux;
         acc[16] += T0;
     }
-    // neighbours: solid fraction and the four smallest gaps
-    double phi = 0.0;
-    double gd4[4] = {1e300, 1e300, 1e300, 1e300};
-    for (int q = threadIdx.x; q < n; q += FEAT_T) {
-        if (q == p) continue;
-        const double ex = X[3 * q] - xp, ey = X[3 * q + 1] - yp, ez = X[3 * q + 2] - X[3 * p + 2];
-        const double dist = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
-        const double Rq = R[q];
-        if (dist < 4.0 * Rp) {
-            const double s = Rq / (4.0 * Rp);
-            phi += D == 3 ? s * s * s : s * s;
-        }
-        double gap = (dist - Rp) - Rq;
-        for (int k = 0; k < 4; k++)  // insert into the sorted four
-            if (gap < gd4[k]) {
-                double t = gd4[k];
-                gd4[k] = gap;
-                gap = t;
-            }
+    // fixed-order tree reduction: warp shuffles, then the four warp sums in
+    // order (a serial FP64 chain over 128 threads would cost ~2000 dependent
+    // FP64 additions)
+    for (int k = 0; k < 17; k++) {
+        double v = acc[k];
+        for (int w = 16; w > 0; w >>= 1) v += __shfl_down_sync(0xffffffffu, v, w);
+        acc[k] = v;
     }
-    for (int k = 0; k < 17; k++) red[k][threadIdx.x] = acc[k];
-    red[17][threadIdx.x] = phi;
-    for (int k = 0; k < 4; k++) gaps_sh[4 * threadIdx.x + k] = gd4[k];
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 17; k++) red[k][threadIdx.x >> 5] = acc[k];
     __syncthreads();
-    // thread 0 combines in thread order (deterministic) and merges the gaps
     if (threadIdx.x == 0) {
-        double s[18];
-        for (int k = 0; k < 18; k++) {
-            double v = 0.0;
-            for (int t = 0; t < FEAT_T; t++) v += red[k][t];
-            s[k] = v;
-        }
-        double best[4] = {1e300, 1e300, 1e300, 1e300};
-        for (int t = 0; t < 4 * FEAT_T; t++) {
-            double gap = gaps_sh[t];
-            for (int k = 0; k < 4; k++)
-                if (gap < best[k]) {
-                    double tt = best[k];
-                    best[k] = gap;
-                    gap = tt;
-                }
-        }
+        double s[17];
+        for (int k = 0; k < 17; k++) s[k] = (red[k][0] + red[k][1]) + (red[k][2] + red[k][3]);
         double V[3] = {0, 0, 0}, Om[3] = {0, 0, 0};
         const double m = s[0];
         if (m > 0) {
@@ -874,19 +846,76 @@ __global__ void __launch_bounds__(FEAT_T) k_features(Geo G, const S* f, const S*
             o[3 + a] = W[3 * p + a] - Om[a];
         }
         o[6] = Tp[p] - (m > 0 ? s[16] / m : 0.0);
-        o[7] = s[17];
-        const double cap = 2.0 * Rp;
-        for (int k = 0; k < 4; k++) o[8 + k] = best[k] < cap ? best[k] : cap;
     }
+}
+
+// Neighbour features (solid fraction and the four smallest gaps), n-body
+// style: one thread per particle, the other particles staged through shared
+// memory in tiles of NB_T as FP32 (x, y, z, R).  The FP32 prefilter keeps the
+// exact FP64 distance to the particles that can matter: centres closer than
+// max(4 R_p, 3 R_p + R_q) (a larger gap is capped at 2 R_p anyway).
+constexpr int NB_T = 128;
+template <int D>
+__global__ void __launch_bounds__(NB_T) k_neighbour_features(int n, const double* __restrict__ X, const double* __restrict__ R,
+                                                             const float4* __restrict__ xr, double* __restrict__ out) {
+    __shared__ float4 tile[NB_T];
+    const int p = blockIdx.x * NB_T + threadIdx.x;
+    const bool live = p < n;
+    const float4 me = live ? xr[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+    double xp = 0.0, yp = 0.0, zp = 0.0, Rp = 1.0;
+    if (live) xp = X[3 * p], yp = X[3 * p + 1], zp = X[3 * p + 2], Rp = R[p];
+    double phi = 0.0;
+    double gd4[4] = {1e300, 1e300, 1e300, 1e300};
+    for (int t0 = 0; t0 < n; t0 += NB_T) {
+        __syncthreads();
+        if (t0 + threadIdx.x < n) tile[threadIdx.x] = xr[t0 + threadIdx.x];
+        __syncthreads();
+        const int m = n - t0 < NB_T ? n - t0 : NB_T;
+        if (!live) continue;
+        for (int j = 0; j < m; j++) {
+            const int q = t0 + j;
+            if (q == p) continue;
+            const float4 o = tile[j];
+            const float fx = o.x - me.x, fy = o.y - me.y, fz = o.z - me.z;
+            const float lim = fmaxf(4.f * me.w, 3.f * me.w + o.w) + 0.01f;
+            if (fx * fx + fy * fy + fz * fz >= lim * lim) continue;
+            const double ex = X[3 * q] - xp, ey = X[3 * q + 1] - yp, ez = X[3 * q + 2] - zp;
+            const double dist = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
+            const double Rq = R[q];
+            if (dist < 4.0 * Rp) {
+                const double sr = Rq / (4.0 * Rp);
+                phi += D == 3 ? sr * sr * sr : sr * sr;
+            }
+            double gap = (dist - Rp) - Rq;
+            for (int k = 0; k < 4; k++)  // insert into the sorted four
+                if (gap < gd4[k]) {
+                    const double tt = gd4[k];
+                    gd4[k] = gap;
+                    gap = tt;
+                }
+        }
+    }
+    if (!live) return;
+    double* o = out + 12 * (long long)p;
+    o[7] = phi;
+    const double cap = 2.0 * Rp;
+    for (int k = 0; k < 4; k++) o[8 + k] = gd4[k] < cap ? gd4[k] : cap;
+}
+
+__global__ void k_pos_f32(int n, const double* X, const double* R, float4* xr) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) xr[p] = make_float4((float)X[3 * p], (float)X[3 * p + 1], (float)X[3 * p + 2], (float)R[p]);
 }
 
 template <int D, typename S>
 static cudaError_t features_launch(Ctx* c, cudaStream_t s, int parity, double* out) {
     if (c->np == 0) return cudaSuccess;
     using V = typename Store<S>::V4;
+    k_pos_f32<<<(c->np + 255) / 256, 256, 0, s>>>(c->np, c->X, c->R, c->sg.xr);
     k_features<D, S><<<c->np, FEAT_T, 0, s>>>(c->G, (const S*)c->f, (const S*)c->g, (const V*)c->fb[parity],
                                               c->flags[parity], collide_params<double>(c), parity, c->np, c->X, c->U,
                                               c->W, c->R, c->Tp, out);
+    k_neighbour_features<D><<<(c->np + NB_T - 1) / NB_T, NB_T, 0, s>>>(c->np, c->X, c->R, c->sg.xr, out);
     return cudaGetLastError();
 }
 

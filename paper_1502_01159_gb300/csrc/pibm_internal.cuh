@@ -239,6 +239,7 @@ struct Surrogate {
     double bound, delta;
     int cap;                         // particles the per-particle buffers hold
     double* feat;                    // [n][12]
+    float4* xr;                      // [n] FP32 positions and radii (neighbour prefilter)
     float *rows, *yrows, *J;         // [7n][16], [7n][8], [n][18]
     double* part;                    // gate partial sums
     int *J_on, *err;                 // device gate flag, tensor-core wait status

@@ -400,3 +400,22 @@ def test_cavity_nusselt_table1(Ra, Ar):
     print("cavity", Ra, Ar, sim.t, nu, paper)
     assert abs(nu - prev) < 1e-6 * abs(nu), "not steady"
     assert abs(nu / paper - 1.0) < 0.03, (nu, paper)
+
+
+@pytest.mark.parametrize("Ra,Ar", [(1e4, 5.0), (1e4, 2.5), (1e4, 1.67), (1e5, 5.0), (1e5, 2.5), (1e5, 1.67),
+                                   (1e6, 5.0), (1e6, 2.5), (1e6, 1.67)])
+def test_cavity_nusselt_table1_paper_lattice(Ra, Ar):
+    # Section 3.1, Table 1, every row, on the paper's own 250^2 lattice (FP64):
+    # steady Nu within 3% of the paper's value
+    paper = _table1()[(Ra, Ar)]
+    sim = _sim(W.cavity(n=250, Ra=Ra, Ar=Ar, storage="f64"))
+    prev, nu = None, None
+    for _ in range(400):
+        sim.step(2000)
+        nu = sim.nusselt()
+        if prev is not None and abs(nu - prev) < 2e-6 * abs(nu):
+            break
+        prev = nu
+    print("cavity250", Ra, Ar, sim.t, nu, paper, nu / paper - 1)
+    assert np.isfinite(nu) and abs(nu - prev) < 2e-6 * abs(nu), "not steady"
+    assert abs(nu / paper - 1.0) < 0.03, (nu, paper)
