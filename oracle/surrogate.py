@@ -15,8 +15,10 @@ the step.  The coupling acts on the fluid the particle covers (Eqs lbm7,
 lbm8: F_f = 2 (rho U_l - j) on every covered node), so the velocity
 features are taken against that fluid.  Definitions (lattice units):
 
-  region S_p  the nodes the particle covers: r inside the lattice with
-              |r - X_p| < R_p + 1/2 (epsilon > 0)
+  region S_p  the nodes particle p owns in the coupling: r inside the lattice
+              with epsilon_p(r) = min(R_p + 1/2 - |r - X_p|, 1) > 0, and no
+              other particle with a larger epsilon there (equal: the lower
+              index owns it)
   raw fields  the moments before the coupling's correction, u = j / rho with
               rho = sum f, j = sum e f, and T0 = sum g (see raw_fields): the
               coupling acts on exactly these (F_f = 2 (rho U_l - j))
@@ -83,6 +85,24 @@ def region(X, R, shape_xyz, dim):
     return out
 
 
+def _eps(nodes, Xq, Rq, dim):
+    d = nodes[:, :dim].astype(np.float64) - np.asarray(Xq[:dim])[None, :]
+    e = (Rq + 0.5) - np.sqrt(np.sum(d * d, axis=1))
+    return np.minimum(e, 1.0)
+
+
+def owned(nodes, p, X, R, dim):
+    """The rows of nodes (covered by p) that p owns against the other particles."""
+    ep = _eps(nodes, X[p], R[p], dim)
+    keep = ep > 0
+    for q in range(len(R)):
+        if q == p or np.linalg.norm(np.asarray(X[q][:dim]) - np.asarray(X[p][:dim])) >= R[p] + R[q] + 2:
+            continue
+        eq = _eps(nodes, X[q], R[q], dim)
+        keep &= ~((eq > ep) | ((eq == ep) & (q < p)))
+    return nodes[keep]
+
+
 def features(fields, X, U, W, R, Tp, dim):
     """fields: dict with rho, ux, uy, uz (3-D), T as (nz, ny, nx) arrays."""
     n = len(R)
@@ -90,7 +110,7 @@ def features(fields, X, U, W, R, Tp, dim):
     out = np.zeros((n, N_FEAT))
     uz = fields.get("uz", np.zeros_like(fields["T"]))
     for p in range(n):
-        nodes = region(X[p], R[p], (nx, ny, nz), dim)
+        nodes = owned(region(X[p], R[p], (nx, ny, nz), dim), p, X, R, dim)
         x, y, z = nodes[:, 0], nodes[:, 1], nodes[:, 2]
         u = np.stack([fields["ux"][z, y, x], fields["uy"][z, y, x], uz[z, y, x]], axis=1)
         Ts = fields["T"][z, y, x].mean()

@@ -158,7 +158,7 @@ cudaError_t pibm::record_step(Ctx* cp, int par, int* kernels_out) {
     chk(launch_coupling(&c, c.s0, par ^ 1));         // coupling of time t+1
     kernels += coupling_kernel_count(&c);
     if (c.sg.enabled && c.np > 0) {                  // surrogate Jacobian for the next step's DEM, judged by t+1's coupling
-        chk(launch_surrogate(&c, c.s0, par ^ 1));
+        chk(launch_surrogate(&c, c.s0, par ^ 1, false));  // the coupling left the feature sums
         kernels += surrogate_kernel_count(&c);
     }
     if (kernels_out) *kernels_out = kernels;
@@ -989,12 +989,14 @@ static pibm_status sg_ensure(pibm_ctx* ctx) {
         dfree_group(ctx, GRP_SG_PART);
         const size_t n = (size_t)c.np;
         c.sg.feat = (double*)dalloc(ctx, sizeof(double) * 12 * n, GRP_SG_PART);
+        c.sg.fsum = (double*)dalloc(ctx, sizeof(double) * 17 * n, GRP_SG_PART);
         c.sg.xr = (float4*)dalloc(ctx, sizeof(float4) * n, GRP_SG_PART);
+        c.sg.nbpart = (double*)dalloc(ctx, sizeof(double) * 5 * SG_NB_SLICES * n, GRP_SG_PART);
         c.sg.rows = (float*)dalloc(ctx, sizeof(float) * 7 * 16 * n, GRP_SG_PART);
         c.sg.yrows = (float*)dalloc(ctx, sizeof(float) * 7 * 8 * n, GRP_SG_PART);
         c.sg.J = (float*)dalloc(ctx, sizeof(float) * 18 * n, GRP_SG_PART);
         c.sg.part = (double*)dalloc(ctx, sizeof(double) * 2 * (n / 256 + 2), GRP_SG_PART);
-        if (!c.sg.feat || !c.sg.xr || !c.sg.rows || !c.sg.yrows || !c.sg.J || !c.sg.part) {
+        if (!c.sg.feat || !c.sg.fsum || !c.sg.xr || !c.sg.nbpart || !c.sg.rows || !c.sg.yrows || !c.sg.J || !c.sg.part) {
             c.sg.cap = 0;
             return fail(ctx, PIBM_ERR_OOM, "surrogate particle buffers");
         }
@@ -1009,6 +1011,7 @@ pibm_status pibm_read_features(pibm_ctx* ctx, double* out) {
     if (c.np == 0) return PIBM_OK;
     pibm_status st = sg_ensure(ctx);
     if (st != PIBM_OK) return st;
+    PCHECK(launch_footprint_sums(&c, c.s0, parity(c)));
     PCHECK(launch_features(&c, c.s0, parity(c), c.sg.feat));
     PCHECK(cudaMemcpyAsync(out, c.sg.feat, sizeof(double) * 12 * c.np, cudaMemcpyDeviceToHost, c.s0));
     PCHECK(cudaStreamSynchronize(c.s0));
@@ -1198,7 +1201,7 @@ pibm_status pibm_surrogate_enable(pibm_ctx* ctx, int on, double bound, double de
     c.dem.J_on = c.sg.J_on;
     PCHECK(cudaMemsetAsync(c.sg.stats, 0, sizeof(double) * 4, c.s0));
     PCHECK(cudaMemsetAsync(c.sg.err, 0, sizeof(int), c.s0));
-    PCHECK(launch_surrogate(&c, c.s0, parity(c)));  // Jacobian and gate of the current state for the next step
+    PCHECK(launch_surrogate(&c, c.s0, parity(c), true));  // Jacobian and gate of the current state for the next step
     PCHECK(cudaStreamSynchronize(c.s0));
     return PIBM_OK;
 }

@@ -104,20 +104,26 @@ __device__ __forceinline__ float eps_f32(int ix, int iy, int iz, const float* c,
 
 constexpr float EPS_GUARD = 1e-5f;  // FP32 decisions within this margin are re-taken in FP64
 
-template <int D, typename S>
+// FEAT: also accumulate, over the particle's owned nodes, the sums the learned
+// surrogate's features need (count, sum d, sum d d^T, sum u, sum d x u, sum
+// dT with d = r - X_p, u = j / rho the raw velocity, dT = T0 - T_ref) into
+// fsum[p][17].
+template <int D, typename S, bool FEAT>
 __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __restrict__ f, const S* __restrict__ g,
                                                           typename Store<S>::V4* __restrict__ mk,
                                                           const double* __restrict__ X, const double* __restrict__ U,
                                                           const double* __restrict__ W, const double* __restrict__ Rr,
                                                           const double* __restrict__ Tp, const int* __restrict__ adj_start,
                                                           const int* __restrict__ adj_nb, double kappa, double Tref,
-                                                          int parity, double* Fh, double* Th, double* Hh) {
+                                                          int parity, double* Fh, double* Th, double* Hh, double* fsum) {
     using L = Lat<D>;
     using R = typename Store<S>::R;
     __shared__ double sh_nb[CP_MAXNB][4];
     __shared__ float sh_nbf[CP_MAXNB][4];
     __shared__ int sh_id[CP_MAXNB];
-    __shared__ double red[7][CP_THREADS / 32];
+    __shared__ double red[FEAT ? 24 : 7][CP_THREADS / 32];
+    float fa[FEAT ? 17 : 1];
+    for (int k = 0; k < (FEAT ? 17 : 1); k++) fa[k] = 0.f;
     // per-particle constants, computed once by thread 0 (FP64 is slow on this GPU)
     __shared__ int s_box[6], s_base[3];
     __shared__ float s_cf[3], s_U[3], s_W[3], s_misc[3];
@@ -244,6 +250,18 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
         acc[4] -= arm[2] * MF[0] - arm[0] * MF[2];
         acc[5] -= arm[0] * MF[1] - arm[1] * MF[0];
         acc[6] += (float)M[3];
+        if constexpr (FEAT) {
+            const float inv = 1.f / (float)rho;
+            const float u[3] = {(float)j[0] * inv, (float)j[1] * inv, D == 3 ? (float)j[2] * inv : 0.f};
+            const float dz = D == 3 ? arm[2] : 0.f;
+            fa[0] += 1.f;
+            fa[1] += arm[0], fa[2] += arm[1], fa[3] += dz;
+            fa[4] += arm[0] * arm[0], fa[5] += arm[1] * arm[1], fa[6] += dz * dz;
+            fa[7] += arm[0] * arm[1], fa[8] += arm[0] * dz, fa[9] += arm[1] * dz;
+            fa[10] += u[0], fa[11] += u[1], fa[12] += u[2];
+            fa[13] += arm[1] * u[2] - dz * u[1], fa[14] += dz * u[0] - arm[0] * u[2], fa[15] += arm[0] * u[1] - arm[1] * u[0];
+            fa[16] += (float)dT;
+        }
     }
     // warp sums in FP32 (32 partials), the per-particle total over the warps in FP64
 #pragma unroll
@@ -252,13 +270,22 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = (double)v;
     }
+    if constexpr (FEAT) {
+#pragma unroll
+        for (int a = 0; a < 17; a++) {
+            float v = fa[a];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) red[7 + a][threadIdx.x >> 5] = (double)v;
+        }
+    }
     __syncthreads();
-    if (threadIdx.x < 7) {
+    if (threadIdx.x < (FEAT ? 24 : 7)) {
         double v = 0;
         for (int w = 0; w < CP_THREADS / 32; w++) v += red[threadIdx.x][w];
         if (threadIdx.x < 3) Fh[3 * p + threadIdx.x] = v;
         else if (threadIdx.x < 6) Th[3 * p + threadIdx.x - 3] = v;
-        else Hh[p] = v;
+        else if (threadIdx.x == 6) Hh[p] = v;
+        else fsum[17 * (long long)p + threadIdx.x - 7] = v;
     }
 }
 
@@ -439,9 +466,14 @@ static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
     using V = typename Store<S>::V4;
     if (!c->desc.pibm) return cudaSuccess;
     if (c->np > 0) {
-        k_footprint<D, S><<<c->np, CP_THREADS, 0, s>>>(c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk[parity], c->X, c->U, c->W,
-                                                       c->R, c->Tp, c->adj_start, c->adj_nb, c->desc.kappa_T,
-                                                       c->desc.T_ref, parity, c->Fh, c->Th, c->Hh);
+        if (c->sg.enabled)  // the surrogate's feature sums ride along
+            k_footprint<D, S, true><<<c->np, CP_THREADS, 0, s>>>(
+                c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk[parity], c->X, c->U, c->W, c->R, c->Tp, c->adj_start,
+                c->adj_nb, c->desc.kappa_T, c->desc.T_ref, parity, c->Fh, c->Th, c->Hh, c->sg.fsum);
+        else
+            k_footprint<D, S, false><<<c->np, CP_THREADS, 0, s>>>(
+                c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk[parity], c->X, c->U, c->W, c->R, c->Tp, c->adj_start,
+                c->adj_nb, c->desc.kappa_T, c->desc.T_ref, parity, c->Fh, c->Th, c->Hh, nullptr);
         k_spread<D, V><<<c->np, CP_THREADS, SPREAD_SMEM, s>>>(c->G, c->X, c->R, (const V*)c->mk[parity], (V*)c->fb[parity],
                                                               c->flags[parity], c->box[parity]);
     }
@@ -459,6 +491,22 @@ static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
 }
 
 cudaError_t launch_coupling(Ctx* c, cudaStream_t s, int parity) { PIBM_DISPATCH(c, coupling_impl, c, s, parity); }
+
+// The footprint pass alone with the feature sums (rewrites the same marker
+// field and particle loads: the pass is deterministic).
+template <int D, typename S>
+static cudaError_t footprint_sums_impl(Ctx* c, cudaStream_t s, int parity) {
+    using V = typename Store<S>::V4;
+    if (!c->desc.pibm || c->np <= 0) return cudaSuccess;
+    k_footprint<D, S, true><<<c->np, CP_THREADS, 0, s>>>(c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk[parity], c->X,
+                                                         c->U, c->W, c->R, c->Tp, c->adj_start, c->adj_nb, c->desc.kappa_T,
+                                                         c->desc.T_ref, parity, c->Fh, c->Th, c->Hh, c->sg.fsum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_footprint_sums(Ctx* c, cudaStream_t s, int parity) {
+    PIBM_DISPATCH(c, footprint_sums_impl, c, s, parity);
+}
 
 // Zero the coupling fields of one parity on the boxes its last spread recorded.
 template <int D, typename S>

@@ -243,13 +243,13 @@ struct Priv {
     double X[3], U[3], W[3];
     float a[3], al[3];       // external linear / angular acceleration: (hydro + buoyant weight)/m, hydro torque/I
     double im, iI, R;        // 1/m, 1/I, radius
-    float Rf, pad2;          // radius in FP32 (prefilters)
+    float Rf, imf;           // radius and 1/m in FP32
     float Fc[3], Tc[3];      // contact force / torque of the last evaluation
     int fixed, wall_mask;    // wall_mask: faces with a non-zero tangential history
-    int nadj, pad;           // neighbours in the adjacency
+    int nadj;                // neighbours in the adjacency
+    float iIf;               // 1/I in FP32
 };
 
-// velocity Verlet half kick: U += h (F_c/m + a_ext), omega += h (T_c/I + alpha_ext)
 // Velocity Verlet half or full kick.  J (optional, per particle: J_FU then
 // J_TW, row-major) is a learned estimate of d(hydrodynamic force)/dU and
 // d(hydrodynamic torque)/domega; the held hydrodynamic load is then corrected
@@ -266,10 +266,19 @@ __device__ __forceinline__ void kick_s(Priv& P, double h, int dim, const float* 
                 dT[a] += (double)J[9 + 3 * a + b] * dw[b];
             }
     }
+    // the increment h (F_c/m + a_ext) is formed in FP32 (relative error ~1e-7 of
+    // a per-substep change) and added to the FP64 velocity in one operation:
+    // FP64 latency is long on this GPU and these chains are the substep's tail
+    const float hf = (float)h;
     for (int a = 0; a < 3; a++) {
-        P.U[a] += h * ((double)P.Fc[a] * P.im + (double)P.a[a] + dF[a] * P.im);
-        P.W[a] += h * ((double)P.Tc[a] * P.iI + (double)P.al[a] + dT[a] * P.iI);
+        P.U[a] += (double)(hf * (P.Fc[a] * P.imf + P.a[a]));
+        P.W[a] += (double)(hf * (P.Tc[a] * P.iIf + P.al[a]));
     }
+    if (J)
+        for (int a = 0; a < 3; a++) {
+            P.U[a] += h * dF[a] * P.im;
+            P.W[a] += h * dT[a] * P.iI;
+        }
     if (dim == 2) {
         P.U[2] = 0.0;
         P.W[0] = P.W[1] = 0.0;
@@ -332,6 +341,8 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             Priv& P = prv[l];
             P.im = 1.0 / S.m[p];
             P.iI = 1.0 / S.I[p];
+            P.imf = (float)P.im;
+            P.iIf = (float)P.iI;
             P.R = S.R[p];
             P.Rf = (float)P.R;
             P.fixed = S.fixed[p];
@@ -370,56 +381,80 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             const int gsub = gbase + sub;
             const float4* hist_old = nb_ft + (size_t)(gsub & 1) * C.cap;
             float4* hist_new = nb_ft + (size_t)((gsub + 1) & 1) * C.cap;
-            for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
-                const int p = base + l;
-                Priv& P = prv[l];
-                const Pub me = pub[rb * per + l];
-                const double Rp = P.R;
-                const float Rpf = P.Rf;
+            // tpp threads per particle (4 when a CTA holds at most 32 particles,
+            // 2 up to 64, else 1): consecutive lanes, each taking every tpp-th
+            // neighbour (the first also the walls); warp-uniform loop so the
+            // shuffles below always see the whole warp
+            const int tpp = per <= 32 ? 4 : (per <= 64 ? 2 : 1), ltpp = tpp == 4 ? 2 : tpp == 2 ? 1 : 0;
+            const int lane = threadIdx.x & 31, sl = lane & (tpp - 1);
+            for (int l0 = (threadIdx.x >> 5) * (32 >> ltpp); l0 < nloc; l0 += (int)blockDim.x >> ltpp) {
+                const int l = l0 + (lane >> ltpp);
+                const bool active = l < nloc;
                 float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};  // contact sums (a few terms) in FP32
-                wall_forces<D>(C, S, p, me, Rp, Rpf, dtf, F, T, P.wall_mask);
-                const int ne = P.nadj, e0 = ne > DEM_MAXA ? __ldcg(S.adj_start + p) : 0;
-                for (int e = 0; e < ne; e++) {
-                    int q, kk;
-                    if (ne <= DEM_MAXA) {
-                        const int2 a = adj[l * DEM_MAXA + e];
-                        q = a.x, kk = a.y;
-                    } else {
-                        q = __ldcg(S.adj_nb + e0 + e), kk = __ldcg(S.adj_k + e0 + e);
-                    }
-                    const bool first = kk >= 0;
-                    const int k = first ? kk : ~kk;
-                    const int rq = q / per, lq = q - rq * per;
-                    const Pub* rp = cl.map_shared_rank(pub, rq) + rb * per + lq;
-                    const Priv* rv = cl.map_shared_rank(prv, rq) + lq;
-                    // FP32 prefilter from the published FP32 positions (no FP64 for pairs apart)
-                    const float dxf = rp->xf[0] - me.xf[0], dyf = rp->xf[1] - me.xf[1], dzf = rp->xf[2] - me.xf[2];
-                    const float sf = Rpf + rv->Rf + 1e-3f;
-                    float3 Fa = f3(0.f, 0.f, 0.f), Ta = Fa, Tb = Fa, h = Fa;
-                    bool contact = false;
-                    if (dxf * dxf + dyf * dyf + dzf * dzf < sf * sf) {
-                        const Pub other = *rp;
-                        const double Rq = rv->R;
-                        const Pub& A = first ? me : other;
-                        const Pub& B = first ? other : me;
-                        const double Ra = first ? Rp : Rq, Rb = first ? Rq : Rp;
-                        double d2 = dist2(A.x, B.x), Ssum = Ra + Rb;
-                        contact = d2 < Ssum * Ssum;  // the exact FP64 contact test
-                        if (contact) {
-                            const float4 hv = __ldcg(hist_old + k);
-                            if (__float_as_int(hv.w) == gsub - 1) h = f3(hv.x, hv.y, hv.z);
-                            pair_force(C, A, B, Ra, Rb, h, dtf, Fa, Ta, Tb);
+                if (active) {
+                    const int p = base + l;
+                    Priv& P = prv[l];
+                    const Pub me = pub[rb * per + l];
+                    const double Rp = P.R;
+                    const float Rpf = P.Rf;
+                    if (sl == 0) wall_forces<D>(C, S, p, me, Rp, Rpf, dtf, F, T, P.wall_mask);
+                    const int ne = P.nadj, e0 = ne > DEM_MAXA ? __ldcg(S.adj_start + p) : 0;
+                    for (int e = sl; e < ne; e += tpp) {
+                        int q, kk;
+                        if (ne <= DEM_MAXA) {
+                            const int2 a = adj[l * DEM_MAXA + e];
+                            q = a.x, kk = a.y;
+                        } else {
+                            q = __ldcg(S.adj_nb + e0 + e), kk = __ldcg(S.adj_k + e0 + e);
+                        }
+                        const bool first = kk >= 0;
+                        const int k = first ? kk : ~kk;
+                        const int rq = q / per, lq = q - rq * per;
+                        const Pub* rp = cl.map_shared_rank(pub, rq) + rb * per + lq;
+                        const Priv* rv = cl.map_shared_rank(prv, rq) + lq;
+                        // FP32 prefilter from the published FP32 positions (no FP64 for pairs apart)
+                        const float dxf = rp->xf[0] - me.xf[0], dyf = rp->xf[1] - me.xf[1], dzf = rp->xf[2] - me.xf[2];
+                        const float sf = Rpf + rv->Rf + 1e-3f;
+                        float3 Fa = f3(0.f, 0.f, 0.f), Ta = Fa, Tb = Fa, h = Fa;
+                        bool contact = false;
+                        if (dxf * dxf + dyf * dyf + dzf * dzf < sf * sf) {
+                            const Pub other = *rp;
+                            const double Rq = rv->R;
+                            const Pub& A = first ? me : other;
+                            const Pub& B = first ? other : me;
+                            const double Ra = first ? Rp : Rq, Rb = first ? Rq : Rp;
+                            double d2 = dist2(A.x, B.x), Ssum = Ra + Rb;
+                            contact = d2 < Ssum * Ssum;  // the exact FP64 contact test
+                            if (contact) {
+                                const float4 hv = __ldcg(hist_old + k);
+                                if (__float_as_int(hv.w) == gsub - 1) h = f3(hv.x, hv.y, hv.z);
+                                pair_force(C, A, B, Ra, Rb, h, dtf, Fa, Ta, Tb);
+                            }
+                        }
+                        if (first) {
+                            if (contact) hist_new[k] = make_float4(h.x, h.y, h.z, __int_as_float(gsub));
+                            F[0] += Fa.x, F[1] += Fa.y, F[2] += Fa.z;
+                            T[0] += Ta.x, T[1] += Ta.y, T[2] += Ta.z;
+                        } else {
+                            F[0] -= Fa.x, F[1] -= Fa.y, F[2] -= Fa.z;
+                            T[0] += Tb.x, T[1] += Tb.y, T[2] += Tb.z;
                         }
                     }
-                    if (first) {
-                        if (contact) hist_new[k] = make_float4(h.x, h.y, h.z, __int_as_float(gsub));
-                        F[0] += Fa.x, F[1] += Fa.y, F[2] += Fa.z;
-                        T[0] += Ta.x, T[1] += Ta.y, T[2] += Ta.z;
-                    } else {
-                        F[0] -= Fa.x, F[1] -= Fa.y, F[2] -= Fa.z;
-                        T[0] += Tb.x, T[1] += Tb.y, T[2] += Tb.z;
-                    }
                 }
+                // the tpp partial sums, in a fixed order: (0 + 1) + (2 + 3)
+                if (tpp > 1)
+                    for (int a = 0; a < 3; a++) {
+                        F[a] += __shfl_xor_sync(0xffffffffu, F[a], 1);
+                        T[a] += __shfl_xor_sync(0xffffffffu, T[a], 1);
+                    }
+                if (tpp > 2)
+                    for (int a = 0; a < 3; a++) {
+                        F[a] += __shfl_xor_sync(0xffffffffu, F[a], 2);
+                        T[a] += __shfl_xor_sync(0xffffffffu, T[a], 2);
+                    }
+                if (!active || sl != 0) continue;
+                const int p = base + l;
+                Priv& P = prv[l];
                 for (int a = 0; a < 3; a++) {
                     P.Fc[a] = F[a];
                     P.Tc[a] = T[a];

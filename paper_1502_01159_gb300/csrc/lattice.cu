@@ -11,6 +11,7 @@
 // to the neighbours, so one array serves both time levels.
 #include <float.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "pibm_internal.cuh"
@@ -701,18 +702,18 @@ static cudaError_t macro_launch(Ctx* c, int field, int parity) {
 cudaError_t launch_macro(Ctx* c, int field, int parity) { PIBM_DISPATCH(c, macro_launch, c, field, parity); }
 
 // --------------------------------------------------- surrogate features
-// Per-particle features of the learned coupling surrogate (one CTA per
-// particle).  Region S_p = the nodes the particle covers, |r - X_p| < R_p + 1/2
-// (distance in FP64 without contraction, as the reference computes it); over
-// S_p the raw fluid velocity j / rho (the moments before the coupling's
-// correction) is fitted by a rigid motion V + Om x d about X_p (least
-// squares, d = r - X_p):  n V - D x Om = sum u,  D x V + M Om = sum d x u,
-// D = sum d, M = sum (|d|^2 I - d d^T)  (2-D: unknowns V_x, V_y, Om_z).
-// Features: U_p - V (3), omega_p - Om (3), T_p - mean raw T over S_p (1) here;
+// Per-particle features of the learned coupling surrogate.  Region S_p = the
+// nodes particle p owns in the coupling (epsilon > 0, the larger epsilon, ties
+// to the lower index): the footprint pass accumulates the sums over S_p of
+// d = r - X_p, d d^T, the raw fluid velocity u = j / rho (moments before the
+// coupling's correction), d x u and T0 - T_ref; here the velocity is fitted by
+// a rigid motion V + Om x d about X_p (least squares):
+//   n V - D x Om = sum u,  D x V + M Om = sum d x u,
+//   D = sum d, M = sum (|d|^2 I - d d^T)   (2-D: unknowns V_x, V_y, Om_z).
+// Features: U_p - V (3), omega_p - Om (3), T_p - mean T0 over S_p (1) here;
 // the solid fraction sum_{q != p, |X_q - X_p| < 4 R_p} (R_q / 4 R_p)^D (1) and
 // the four smallest surface gaps |X_q - X_p| - R_p - R_q capped at 2 R_p (4)
 // in k_neighbour_features.
-constexpr int FEAT_T = 128;
 
 // Gaussian elimination with partial pivoting on an m x m system (m <= 6).
 __device__ void solve_small(double* A, double* b, int m) {
@@ -744,109 +745,51 @@ __device__ void solve_small(double* A, double* b, int m) {
     }
 }
 
-template <int D, typename S>
-__global__ void __launch_bounds__(FEAT_T) k_features(Geo G, const S* f, const S* g, const typename Store<S>::V4* fb,
-                                                     const uint8_t* flags, CollideParams<double> P, int parity, int n,
-                                                     const double* X, const double* U, const double* W, const double* R,
-                                                     const double* Tp, double* out) {
-    __shared__ double red[17][FEAT_T / 32];
-    const int p = blockIdx.x;
-    const double xp = X[3 * p], yp = X[3 * p + 1], zp = D == 3 ? X[3 * p + 2] : 0.0;
-    const double Rp = R[p];
-    const int nl[3] = {G.nx, G.ny, G.nz};
-    const double xc[3] = {xp, yp, zp};
-    int lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
-    for (int a = 0; a < D; a++) {
-        int l0 = (int)floor(xc[a] - Rp - 1.0), h0 = (int)ceil(xc[a] + Rp + 1.0);
-        l0 = l0 < 0 ? 0 : l0;
-        h0 = h0 > nl[a] - 1 ? nl[a] - 1 : h0;
-        lo[a] = l0;
-        ext[a] = h0 >= l0 ? h0 - l0 + 1 : 0;
-    }
-    double acc[17];
-    for (int k = 0; k < 17; k++) acc[k] = 0.0;
-    const long long total = (long long)ext[0] * ext[1] * ext[2];
-    for (long long k = threadIdx.x; k < total; k += FEAT_T) {
-        const int x = lo[0] + (int)(k % ext[0]);
-        const int y = lo[1] + (int)((k / ext[0]) % ext[1]);
-        const int z = lo[2] + (int)(k / ((long long)ext[0] * ext[1]));
-        const double dx = (double)x - xp, dy = (double)y - yp, dz = D == 3 ? (double)z - zp : 0.0;
-        double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-        if (D == 3) d2 = __dadd_rn(d2, __dmul_rn(dz, dz));
-        const double r = sqrt(d2);
-        if (!(r < Rp + 0.5)) continue;
-        // raw moments (before the coupling's correction): the coupling acts on
-        // exactly these, F_f = 2 (rho U_l - j) (Eq lbm8 as read), Q = 2 kappa (T_p - T0)
-        using L = Lat<D>;
-        double s[L::Q], sg[L::QG];
-        load_node<D, S, double>(G, f, g, x, y, z, parity, s, sg);
-        double drho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0, dT = 0.0;
-        for (int i = 0; i < L::Q; i++) {
-            drho += s[i];
-            jx += L::ex(i) * s[i], jy += L::ey(i) * s[i], jz += L::ez(i) * s[i];
+// Features 0-6 from the sums the footprint pass accumulates over the
+// particle's owned nodes (fsum[p]: count, sum d (3), sum d d^T (xx, yy, zz,
+// xy, xz, yz), sum u (3), sum d x u (3), sum dT): one thread per particle.
+template <int D>
+__global__ void k_feature_solve(int n, const double* __restrict__ fsum, const double* __restrict__ U,
+                                const double* __restrict__ W, const double* __restrict__ Tp, double Tref,
+                                double* __restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double s[17];
+    for (int k = 0; k < 17; k++) s[k] = fsum[17 * (long long)p + k];
+    double V[3] = {0, 0, 0}, Om[3] = {0, 0, 0};
+    const double m = s[0];
+    if (m > 0) {
+        double A[36], b[6];
+        if (D == 3) {
+            const double Dd[3] = {s[1], s[2], s[3]};
+            const double trace = s[4] + s[5] + s[6];
+            const double M[9] = {trace - s[4], -s[7], -s[8], -s[7], trace - s[5], -s[9], -s[8], -s[9], trace - s[6]};
+            const double Dx[9] = {0, -Dd[2], Dd[1], Dd[2], 0, -Dd[0], -Dd[1], Dd[0], 0};  // D x (cross-product matrix)
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) {
+                    A[i * 6 + j] = i == j ? m : 0.0;
+                    A[i * 6 + 3 + j] = -Dx[i * 3 + j];
+                    A[(3 + i) * 6 + j] = Dx[i * 3 + j];
+                    A[(3 + i) * 6 + 3 + j] = M[i * 3 + j];
+                }
+            b[0] = s[10], b[1] = s[11], b[2] = s[12], b[3] = s[13], b[4] = s[14], b[5] = s[15];
+            solve_small(A, b, 6);
+            V[0] = b[0], V[1] = b[1], V[2] = b[2], Om[0] = b[3], Om[1] = b[4], Om[2] = b[5];
+        } else {
+            A[0] = m, A[1] = 0.0, A[2] = -s[2];
+            A[6] = 0.0, A[7] = m, A[8] = s[1];
+            A[12] = -s[2], A[13] = s[1], A[14] = s[4] + s[5];
+            b[0] = s[10], b[1] = s[11], b[2] = s[15];
+            solve_small(A, b, 3);
+            V[0] = b[0], V[1] = b[1], Om[2] = b[2];
         }
-        for (int k = 0; k < L::QG; k++) dT += sg[k];
-        const double rho = 1.0 + drho;
-        const double ux = jx / rho, uy = jy / rho, uz = D == 3 ? jz / rho : 0.0;
-        const double T0 = P.Tref + dT;
-        acc[0] += 1.0;
-        acc[1] += dx, acc[2] += dy, acc[3] += dz;
-        acc[4] += dx * dx, acc[5] += dy * dy, acc[6] += dz * dz;
-        acc[7] += dx * dy, acc[8] += dx * dz, acc[9] += dy * dz;
-        acc[10] += ux, acc[11] += uy, acc[12] += uz;
-        acc[13] += dy * uz - dz * uy, acc[14] += dz * ux - dx * uz, acc[15] += dx * uy - dy * ux;
-        acc[16] += T0;
     }
-    // fixed-order tree reduction: warp shuffles, then the four warp sums in
-    // order (a serial FP64 chain over 128 threads would cost ~2000 dependent
-    // FP64 additions)
-    for (int k = 0; k < 17; k++) {
-        double v = acc[k];
-        for (int w = 16; w > 0; w >>= 1) v += __shfl_down_sync(0xffffffffu, v, w);
-        acc[k] = v;
+    double* o = out + 12 * (long long)p;
+    for (int a = 0; a < 3; a++) {
+        o[a] = U[3 * p + a] - V[a];
+        o[3 + a] = W[3 * p + a] - Om[a];
     }
-    if ((threadIdx.x & 31) == 0)
-        for (int k = 0; k < 17; k++) red[k][threadIdx.x >> 5] = acc[k];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s[17];
-        for (int k = 0; k < 17; k++) s[k] = (red[k][0] + red[k][1]) + (red[k][2] + red[k][3]);
-        double V[3] = {0, 0, 0}, Om[3] = {0, 0, 0};
-        const double m = s[0];
-        if (m > 0) {
-            double A[36], b[6];
-            if (D == 3) {
-                const double Dd[3] = {s[1], s[2], s[3]};
-                const double trace = s[4] + s[5] + s[6];
-                const double M[9] = {trace - s[4], -s[7], -s[8], -s[7], trace - s[5], -s[9], -s[8], -s[9], trace - s[6]};
-                // [D]x: cross-product matrix of D
-                const double Dx[9] = {0, -Dd[2], Dd[1], Dd[2], 0, -Dd[0], -Dd[1], Dd[0], 0};
-                for (int i = 0; i < 3; i++)
-                    for (int j = 0; j < 3; j++) {
-                        A[i * 6 + j] = i == j ? m : 0.0;
-                        A[i * 6 + 3 + j] = -Dx[i * 3 + j];
-                        A[(3 + i) * 6 + j] = Dx[i * 3 + j];
-                        A[(3 + i) * 6 + 3 + j] = M[i * 3 + j];
-                    }
-                b[0] = s[10], b[1] = s[11], b[2] = s[12], b[3] = s[13], b[4] = s[14], b[5] = s[15];
-                solve_small(A, b, 6);
-                V[0] = b[0], V[1] = b[1], V[2] = b[2], Om[0] = b[3], Om[1] = b[4], Om[2] = b[5];
-            } else {
-                A[0] = m, A[1] = 0.0, A[2] = -s[2];
-                A[6] = 0.0, A[7] = m, A[8] = s[1];
-                A[12] = -s[2], A[13] = s[1], A[14] = s[4] + s[5];
-                b[0] = s[10], b[1] = s[11], b[2] = s[15];
-                solve_small(A, b, 3);
-                V[0] = b[0], V[1] = b[1], Om[2] = b[2];
-            }
-        }
-        double* o = out + 12 * (long long)p;
-        for (int a = 0; a < 3; a++) {
-            o[a] = U[3 * p + a] - V[a];
-            o[3 + a] = W[3 * p + a] - Om[a];
-        }
-        o[6] = Tp[p] - (m > 0 ? s[16] / m : 0.0);
-    }
+    o[6] = Tp[p] - (m > 0 ? Tref + s[16] / m : 0.0);
 }
 
 // Neighbour features (solid fraction and the four smallest gaps), n-body
@@ -856,21 +799,24 @@ __global__ void __launch_bounds__(FEAT_T) k_features(Geo G, const S* f, const S*
 // max(4 R_p, 3 R_p + R_q) (a larger gap is capped at 2 R_p anyway).
 constexpr int NB_T = 128;
 template <int D>
-__global__ void __launch_bounds__(NB_T) k_neighbour_features(int n, const double* __restrict__ X, const double* __restrict__ R,
-                                                             const float4* __restrict__ xr, double* __restrict__ out) {
+__global__ void __launch_bounds__(NB_T) k_neighbour_features(int n, int slice_len, const double* __restrict__ X,
+                                                             const double* __restrict__ R, const float4* __restrict__ xr,
+                                                             double* __restrict__ part) {
+    // blockIdx.y: slice of the other particles [q0, q1); part[slice][p][5]: phi, four gaps
     __shared__ float4 tile[NB_T];
     const int p = blockIdx.x * NB_T + threadIdx.x;
     const bool live = p < n;
+    const int q0 = blockIdx.y * slice_len, q1 = min(n, q0 + slice_len);
     const float4 me = live ? xr[p] : make_float4(0.f, 0.f, 0.f, 0.f);
     double xp = 0.0, yp = 0.0, zp = 0.0, Rp = 1.0;
     if (live) xp = X[3 * p], yp = X[3 * p + 1], zp = X[3 * p + 2], Rp = R[p];
     double phi = 0.0;
     double gd4[4] = {1e300, 1e300, 1e300, 1e300};
-    for (int t0 = 0; t0 < n; t0 += NB_T) {
+    for (int t0 = q0; t0 < q1; t0 += NB_T) {
         __syncthreads();
-        if (t0 + threadIdx.x < n) tile[threadIdx.x] = xr[t0 + threadIdx.x];
+        if (t0 + threadIdx.x < q1) tile[threadIdx.x] = xr[t0 + threadIdx.x];
         __syncthreads();
-        const int m = n - t0 < NB_T ? n - t0 : NB_T;
+        const int m = q1 - t0 < NB_T ? q1 - t0 : NB_T;
         if (!live) continue;
         for (int j = 0; j < m; j++) {
             const int q = t0 + j;
@@ -896,10 +842,34 @@ __global__ void __launch_bounds__(NB_T) k_neighbour_features(int n, const double
         }
     }
     if (!live) return;
-    double* o = out + 12 * (long long)p;
-    o[7] = phi;
-    const double cap = 2.0 * Rp;
-    for (int k = 0; k < 4; k++) o[8 + k] = gd4[k] < cap ? gd4[k] : cap;
+    double* o = part + ((long long)blockIdx.y * n + p) * 5;
+    o[0] = phi;
+    for (int k = 0; k < 4; k++) o[1 + k] = gd4[k];
+}
+
+// slices combined in slice order (deterministic): phi summed, the four smallest gaps merged
+__global__ void k_neighbour_merge(int n, int nslice, const double* __restrict__ R, const double* __restrict__ part,
+                                  double* __restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double phi = 0.0, best[4] = {1e300, 1e300, 1e300, 1e300};
+    for (int s = 0; s < nslice; s++) {
+        const double* o = part + ((long long)s * n + p) * 5;
+        phi += o[0];
+        for (int j = 1; j < 5; j++) {
+            double gap = o[j];
+            for (int k = 0; k < 4; k++)
+                if (gap < best[k]) {
+                    const double tt = best[k];
+                    best[k] = gap;
+                    gap = tt;
+                }
+        }
+    }
+    double* out_p = out + 12 * (long long)p;
+    out_p[7] = phi;
+    const double cap = 2.0 * R[p];
+    for (int k = 0; k < 4; k++) out_p[8 + k] = best[k] < cap ? best[k] : cap;
 }
 
 __global__ void k_pos_f32(int n, const double* X, const double* R, float4* xr) {
@@ -910,12 +880,14 @@ __global__ void k_pos_f32(int n, const double* X, const double* R, float4* xr) {
 template <int D, typename S>
 static cudaError_t features_launch(Ctx* c, cudaStream_t s, int parity, double* out) {
     if (c->np == 0) return cudaSuccess;
-    using V = typename Store<S>::V4;
     k_pos_f32<<<(c->np + 255) / 256, 256, 0, s>>>(c->np, c->X, c->R, c->sg.xr);
-    k_features<D, S><<<c->np, FEAT_T, 0, s>>>(c->G, (const S*)c->f, (const S*)c->g, (const V*)c->fb[parity],
-                                              c->flags[parity], collide_params<double>(c), parity, c->np, c->X, c->U,
-                                              c->W, c->R, c->Tp, out);
-    k_neighbour_features<D><<<(c->np + NB_T - 1) / NB_T, NB_T, 0, s>>>(c->np, c->X, c->R, c->sg.xr, out);
+    k_feature_solve<D><<<(c->np + 127) / 128, 128, 0, s>>>(c->np, c->sg.fsum, c->U, c->W, c->Tp, c->desc.T_ref, out);
+    // the other particles in slices of at least 1024, so that large sets fill the GPU
+    const int nslice = std::min(SG_NB_SLICES, std::max(1, (c->np + 1023) / 1024));
+    const int slice_len = (c->np + nslice - 1) / nslice;
+    k_neighbour_features<D><<<dim3((c->np + NB_T - 1) / NB_T, nslice), NB_T, 0, s>>>(c->np, slice_len, c->X, c->R,
+                                                                                    c->sg.xr, c->sg.nbpart);
+    k_neighbour_merge<<<(c->np + 127) / 128, 128, 0, s>>>(c->np, nslice, c->R, c->sg.nbpart, out);
     return cudaGetLastError();
 }
 

@@ -229,6 +229,7 @@ struct DemCfg {
 constexpr int SG_NFEAT = 12, SG_NOUT = 7;
 constexpr int SG_NPARAMS = 64 * 12 + 64 + 2 * (64 * 64 + 64) + 7 * 64 + 7;
 constexpr int SG_TRAIN_BLOCKS = 152;
+constexpr int SG_NB_SLICES = 16;  // neighbour-feature slices of the particle set
 struct Surrogate {
     float *params, *m, *v, *norm;   // FP32 master parameters, Adam moments, standardisation (38)
     float *partial, *lossp;          // training reduction scratch
@@ -239,7 +240,9 @@ struct Surrogate {
     double bound, delta;
     int cap;                         // particles the per-particle buffers hold
     double* feat;                    // [n][12]
+    double* fsum;                    // [n][17] feature sums of the footprint pass
     float4* xr;                      // [n] FP32 positions and radii (neighbour prefilter)
+    double* nbpart;                  // [slices][n][5] neighbour-feature partials
     float *rows, *yrows, *J;         // [7n][16], [7n][8], [n][18]
     double* part;                    // gate partial sums
     int *J_on, *err;                 // device gate flag, tensor-core wait status
@@ -334,6 +337,7 @@ cudaError_t launch_features(Ctx* c, cudaStream_t s, int parity, double* out);  /
 // coupling.cu
 cudaError_t launch_coupling(Ctx* c, cudaStream_t s, int parity);
 cudaError_t launch_coupling_clear(Ctx* c, cudaStream_t s, int parity);
+cudaError_t launch_footprint_sums(Ctx* c, cudaStream_t s, int parity);  // surrogate feature sums of the state
 int coupling_kernel_count(Ctx* c);
 // dem.cu
 cudaError_t launch_dem(Ctx* c, cudaStream_t s, int nsub);
@@ -348,7 +352,7 @@ int dem_max_per_cta();
 cudaError_t record_step(Ctx* c, int parity, int* kernels);
 // surrogate.cu
 cudaError_t launch_mlp(Ctx* c, cudaStream_t s, const float* in, int rows, float* out);
-cudaError_t launch_surrogate(Ctx* c, cudaStream_t s, int parity);
+cudaError_t launch_surrogate(Ctx* c, cudaStream_t s, int parity, bool need_sums);
 int surrogate_kernel_count(Ctx* c);
 cudaError_t train_batch(Ctx* c, cudaStream_t s, const float* xb, const float* yb, int B, float lr, float* grad_out,
                         double* loss_out);

@@ -447,9 +447,10 @@ cudaError_t launch_mlp(Ctx* c, cudaStream_t s, const float* in, int rows, float*
 }
 
 // features of the current state -> rows -> MLP -> Jacobian and gate (step graph, stream s)
-cudaError_t launch_surrogate(Ctx* c, cudaStream_t s, int parity) {
+cudaError_t launch_surrogate(Ctx* c, cudaStream_t s, int parity, bool need_sums) {
     if (c->np == 0) return cudaSuccess;
-    cudaError_t e = launch_features(c, s, parity, c->sg.feat);
+    cudaError_t e = need_sums ? launch_footprint_sums(c, s, parity) : cudaSuccess;
+    if (e == cudaSuccess) e = launch_features(c, s, parity, c->sg.feat);
     if (e != cudaSuccess) return e;
     k_sg_rows<<<(c->np + 127) / 128, 128, 0, s>>>(c->np, c->sg.feat, c->sg.norm, (float)c->sg.delta, c->sg.rows);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -461,7 +462,7 @@ cudaError_t launch_surrogate(Ctx* c, cudaStream_t s, int parity) {
     return cudaGetLastError();
 }
 
-int surrogate_kernel_count(Ctx* c) { return (c->sg.enabled && c->np > 0) ? 5 : 0; }
+int surrogate_kernel_count(Ctx* c) { return (c->sg.enabled && c->np > 0) ? 8 : 0; }
 
 // Gradient (and optionally an Adam step) of one batch already on the device.
 cudaError_t train_batch(Ctx* c, cudaStream_t s, const float* xb, const float* yb, int B, float lr, float* grad_out,

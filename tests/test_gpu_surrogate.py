@@ -50,9 +50,12 @@ def test_features_match_reference(dim):
     orc.step(30)
     fg = sim.read_features()
     fo = _oracle_features(orc, dim)
+    # columns 0-6 come from FP32 node arithmetic on the raw moments: the
+    # velocity differences (~1e-6) carry ~1e-10 absolute from FP32 moments of
+    # ~1e-3; the neighbour columns 7-11 are FP64 from the positions
     for k in range(12):
         scale = max(np.max(np.abs(fo[:, k])), 1e-12)
-        tol = 1e-5 * scale + (1e-6 if k >= 7 else 1e-12)
+        tol = 1e-4 * scale + 1e-9 if k < 7 else 1e-5 * scale + 1e-6
         assert np.max(np.abs(fg[:, k] - fo[:, k])) <= tol, (k, np.max(np.abs(fg[:, k] - fo[:, k])), scale)
     assert np.max(np.abs(fo[:, 0:3])) > 0  # the particles move relative to the fluid
 

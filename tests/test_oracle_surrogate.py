@@ -140,3 +140,22 @@ def test_raw_fields_of_linear_equilibrium(dim):
     assert np.allclose(r["rho"], rho, rtol=1e-14) and np.allclose(r["T"], T, rtol=1e-14)
     for a, k in enumerate(("ux", "uy", "uz")):
         assert np.allclose(r[k], u[a], atol=1e-16)
+
+
+def test_owned_regions_partition_overlapping_footprints():
+    # two overlapping disks: the owned node sets are disjoint, their union is
+    # every node either covers, and a node goes to the disk with the larger
+    # covered fraction (the lower index on a tie)
+    X = np.array([[10.2, 10.0, 0.0], [14.0, 10.3, 0.0]])
+    R = np.array([3.0, 2.5])
+    a = S.owned(S.region(X[0], R[0], (30, 30, 1), 2), 0, X, R, 2)
+    b = S.owned(S.region(X[1], R[1], (30, 30, 1), 2), 1, X, R, 2)
+    sa, sb = {tuple(v) for v in a}, {tuple(v) for v in b}
+    assert not (sa & sb)
+    ua = {tuple(v) for v in S.region(X[0], R[0], (30, 30, 1), 2)}
+    ub = {tuple(v) for v in S.region(X[1], R[1], (30, 30, 1), 2)}
+    assert sa | sb == ua | ub and (ua & ub)
+    for v in ua & ub:
+        n = np.array([v])
+        e0, e1 = S._eps(n, X[0], R[0], 2)[0], S._eps(n, X[1], R[1], 2)[0]
+        assert (v in sa) == (e0 >= e1)
