@@ -202,6 +202,21 @@ pibm_status pibm_load(pibm_ctx* ctx, const char* path);
  * ms[2] PIBM coupling, ms[3] the whole step (fork to join).  Synchronises. */
 pibm_status pibm_step_timed(pibm_ctx* ctx, double* ms);
 
+/* Particle model, set before pibm_set_particles:
+ *   PIBM_PARTICLES_RESOLVED (default): a particle is the set of lattice nodes
+ *     it covers, each a PIBM point with covered fraction epsilon (for
+ *     particles several nodes across);
+ *   PIBM_PARTICLES_POINT: one PIBM point per particle at its centre (Section
+ *     2.2's own regime, d_p <= h): Eq lbm6 with four points per axis (shifted
+ *     inside at walls), Eqs lbm7, lbm8, lbm7.5 with A_p = pi d_p^2 / 4, Eq lbm13,
+ *     delta_h spreading (Eqs lbm10-lbm12); no hydrodynamic torque.  Radii
+ *     above 1/2 and lattices with fewer than 4 nodes on an axis are rejected
+ *     by pibm_set_particles.  The spreading adds overlapping supports with
+ *     atomics, so the last bits of F_B can differ between runs.
+ * PIBM_ERR_STATE if particles are already set. */
+enum { PIBM_PARTICLES_RESOLVED = 0, PIBM_PARTICLES_POINT = 1 };
+pibm_status pibm_set_particle_model(pibm_ctx* ctx, int model);
+
 /* Launch-shape tuning (used by autotuning sweeps; results do not depend on it).
  * PIBM_TUNE_DEM_PARTICLES_PER_CTA: particles per CTA of the DEM cluster
  * (0 = default 32; at most 16 CTAs and 640 particles per CTA).

@@ -81,6 +81,7 @@ def lib():
             "orc_read_particle_forces": (C.c_int, [P, D, D, D]),
             "orc_read_contact_forces": (C.c_int, [P, D, D]),
             "orc_set_hydro_jacobian": (C.c_int, [P, D]),
+            "orc_set_particle_model": (C.c_int, [P, C.c_int]),
             "orc_nusselt": (C.c_double, [P]),
             "orc_contacts": (C.c_int, [P, I, C.c_int]),
             "orc_contacts_bruteforce": (C.c_int, [P, I, C.c_int]),
@@ -146,6 +147,8 @@ class Oracle:
         if law is not None:
             self.L.orc_set_contact_law(self.h, law["law"], law["E"], law["poisson"], law["mu"],
                                        law["kn"], law["kt"], law["gamma_n"], law["gamma_t"])
+        if case.get("particle_model", "resolved") == "point":
+            self.L.orc_set_particle_model(self.h, 1)
         if case.get("particles") is not None:
             self.set_particles(case["particles"])
         if case.get("markers") is not None:

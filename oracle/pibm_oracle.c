@@ -95,6 +95,7 @@ struct orc_sim {
     double *Fp, *Tq, *Hp; /* coupling of the previous time (force, torque, heat) */
     int have_prev;
     double *J, *U0, *W0;  /* optional hydrodynamic Jacobian [np][18] and the velocities at the step start */
+    int point;            /* particle model: 1 = one PIBM point per particle, d_p <= h (the paper's own regime) */
     double* wall_ft; /* [np][6][3] */
     contact* cont;
     int ncont;
@@ -297,8 +298,74 @@ static void coupling(orc_sim* s) {
     s->nu_sum = 0.0;
     if (!s->P.pibm) return;
 
+    /* sub-grid particles (d_p <= h): one PIBM point each at the particle centre,
+     * moving with it (Eqs lbm5-lbm8 at the point, Eqs lbm10-lbm12 for the spreading) */
+    if (s->np > 0 && s->point) {
+        for (int p = 0; p < s->np; p++) {
+            const double* Xl = &s->X[3 * p];
+            double L[3][4];
+            int base[3] = {0, 0, 0};
+            for (int a = 0; a < 3; a++) {
+                if (a < s->D) {
+                    /* Eq lbm6, four points per axis; at a wall the stencil is shifted inside */
+                    int b = (int)floor(Xl[a]) - 1;
+                    if (b > s->n[a] - 4) b = s->n[a] - 4;
+                    if (b < 0) b = 0;
+                    base[a] = b;
+                    for (int k = 0; k < 4; k++) {
+                        double Lk = 1.0;
+                        for (int m = 0; m < 4; m++)
+                            if (m != k) Lk *= (Xl[a] - (b + m)) / (double)(k - m);
+                        L[a][k] = Lk;
+                    }
+                } else {
+                    L[a][0] = 1.0;
+                }
+            }
+            int nz4 = (s->D == 3) ? 4 : 1;
+            double fl[19], gl[7];
+            for (int i = 0; i < s->Q; i++) fl[i] = 0.0;
+            for (int k = 0; k < s->QG; k++) gl[k] = 0.0;
+            for (int kz = 0; kz < nz4; kz++)
+                for (int ky = 0; ky < 4; ky++)
+                    for (int kx = 0; kx < 4; kx++) {
+                        long r = nidx(s, base[0] + kx, base[1] + ky, (s->D == 3) ? base[2] + kz : 0);
+                        double Lw = L[0][kx] * L[1][ky] * (s->D == 3 ? L[2][kz] : 1.0);
+                        for (int i = 0; i < s->Q; i++) fl[i] += Lw * s->f[(long)i * s->N + r];
+                        for (int k = 0; k < s->QG; k++) gl[k] += Lw * s->g[(long)k * s->N + r];
+                    }
+            double rho = 0, j[3] = {0, 0, 0}, Tl = 0;
+            for (int i = 0; i < s->Q; i++) {
+                rho += fl[i];
+                for (int a = 0; a < 3; a++) j[a] += s->e[i][a] * fl[i];
+            }
+            for (int k = 0; k < s->QG; k++) Tl += gl[k];
+            /* Eqs lbm7 + lbm8 with A_p = pi d_p^2 / 4; Eq lbm7.5 */
+            const double A = PI * s->R[p] * s->R[p];
+            double MF[3], MQ;
+            for (int a = 0; a < 3; a++) MF[a] = A * 2.0 * (rho * s->U[3 * p + a] - j[a]);
+            if (s->D == 2) MF[2] = 0.0;
+            MQ = A * 2.0 * s->P.kappa_T * (s->Tp[p] - Tl);
+            for (int a = 0; a < 3; a++) s->Fh[3 * p + a] = -MF[a]; /* Eq lbm13 */
+            s->Hh[p] = MQ;
+            int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+            for (int a = 0; a < s->D; a++) {
+                lo[a] = (int)ceil(Xl[a] - 2.0);
+                hi[a] = (int)floor(Xl[a] + 2.0);
+            }
+            for (int z = lo[2]; z <= hi[2]; z++)
+                for (int y = lo[1]; y <= hi[1]; y++)
+                    for (int x = lo[0]; x <= hi[0]; x++) {
+                        double Wk = orc_delta_h(x - Xl[0]) * orc_delta_h(y - Xl[1]);
+                        if (s->D == 3) Wk *= orc_delta_h(z - Xl[2]);
+                        int c[3] = {x, y, z};
+                        spread_to(s, c, Wk, MF, MQ);
+                    }
+        }
+    }
+
     /* resolved particles: covered nodes are the PIBM points */
-    if (s->np > 0) {
+    if (s->np > 0 && !s->point) {
         int* owner = (int*)malloc(sizeof(int) * s->N);
         double* best = (double*)calloc(s->N, sizeof(double));
         for (long r = 0; r < s->N; r++) owner[r] = -1;
@@ -876,6 +943,9 @@ int orc_set_particles(orc_sim* s, int n, const double* X, const double* U, const
     s->Tq = (double*)calloc(3 * (n + 1), sizeof(double));
     s->Hp = (double*)calloc(n + 1, sizeof(double));
     s->have_prev = 0;
+    if (s->point)
+        for (int p = 0; p < n; p++)
+            if (R[p] > 0.5) return -1; /* a point particle has d_p <= h */
     s->wall_ft = (double*)calloc(18 * (n + 1), sizeof(double));
     s->fixed = (unsigned char*)calloc(n + 1, 1);
     for (int p = 0; p < n; p++) {
@@ -987,6 +1057,12 @@ int orc_read_particle_forces(orc_sim* s, double* F, double* T, double* H) {
     if (T) memcpy(T, s->Th, sizeof(double) * 3 * s->np);
     if (H) memcpy(H, s->Hh, sizeof(double) * s->np);
     return s->np;
+}
+
+int orc_set_particle_model(orc_sim* s, int point) {
+    if (point != 0 && point != 1) return -1;
+    s->point = point;
+    return 0;
 }
 
 int orc_set_hydro_jacobian(orc_sim* s, const double* J) {

@@ -73,6 +73,10 @@ int      orc_read_contact_forces(orc_sim* s, double* F, double* T);
  * row-major, dF_a/dU_b) then J_TW (dtau_a/domega_b); NULL removes it.  Kept
  * until replaced or until the particles are reset. */
 int      orc_set_hydro_jacobian(orc_sim* s, const double* J);
+/* Particle model for the next orc_set_particles: 0 resolved (the covered
+ * nodes are the PIBM points), 1 one PIBM point per particle at its centre
+ * (d_p <= h, the paper's own regime; radii above 1/2 are rejected). */
+int      orc_set_particle_model(orc_sim* s, int point);
 double   orc_nusselt(orc_sim* s);
 int      orc_contacts(orc_sim* s, int* pairs, int cap);
 int      orc_contacts_bruteforce(orc_sim* s, int* pairs, int cap);

@@ -72,6 +72,7 @@ SIGNATURES = {
     "pibm_save": (C.c_int, [_P, C.c_char_p]),
     "pibm_load": (C.c_int, [_P, C.c_char_p]),
     "pibm_contacts_static": (C.c_int, [_P, _P, C.c_int, C.c_int, _I32, C.c_double, _P, C.c_int, _P, _P]),
+    "pibm_set_particle_model": (C.c_int, [_P, C.c_int]),
     "pibm_read_features": (C.c_int, [_P, _D]),
     "pibm_surrogate_set_params": (C.c_int, [_P, _F, _F]),
     "pibm_surrogate_get_params": (C.c_int, [_P, _F, _F]),
@@ -214,6 +215,8 @@ class Simulation:
             self.h = h
         for face, (kind, thermal, Tw) in enumerate(case["walls"]):
             self.set_wall(face, kind, thermal, Tw)
+        if case.get("particle_model", "resolved") == "point":
+            self._check(self.L.pibm_set_particle_model(self.h, 1), "pibm_set_particle_model")
         law = case.get("contact")
         if law is not None:
             self.set_contact_law(law["law"], law["E"], law["poisson"], law["mu"], law["kn"], law["kt"],

@@ -359,6 +359,13 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     if (n > 0 && cmin < 2.0 * rmax + 1.0)
         return fail(ctx, PIBM_ERR_ARG, "cell size must be at least the largest diameter plus one node");
     if (n > dem_max_particles()) return fail(ctx, PIBM_ERR_ARG, "too many particles for one DEM cluster");
+    if (c.point)
+        for (int p = 0; p < n; p++)
+            if (R[p] > 0.5) return fail(ctx, PIBM_ERR_ARG, "point particles need a diameter of at most one node");
+    if (c.point && n > 0)
+        for (int a = 0; a < c.D; a++)
+            if ((a == 0 ? c.G.nx : a == 1 ? c.G.ny : c.G.nz) < 4)
+                return fail(ctx, PIBM_ERR_ARG, "point particles need at least 4 nodes per axis");
 
     drop_graphs(c);
     dfree_group(ctx, GRP_PARTICLES);
@@ -1190,6 +1197,7 @@ pibm_status pibm_surrogate_enable(pibm_ctx* ctx, int on, double bound, double de
     }
     if (!c.sg.trained) return fail(ctx, PIBM_ERR_STATE, "surrogate has no parameters yet");
     if (c.np == 0) return fail(ctx, PIBM_ERR_STATE, "no particles");
+    if (c.point) return fail(ctx, PIBM_ERR_STATE, "the surrogate's features need resolved particles");
     if (!(bound >= 0) || !(delta > 0)) return fail(ctx, PIBM_ERR_ARG, "bound must be >= 0 and delta > 0");
     pibm_status st = sg_ensure(ctx);
     if (st != PIBM_OK) return st;
@@ -1253,6 +1261,17 @@ pibm_status pibm_set_hydro_jacobian(pibm_ctx* ctx, const double* J) {
     c.sg.fixed = 1;
     c.dem.J = c.sg.J;
     c.dem.J_on = c.sg.J_on;
+    return PIBM_OK;
+}
+
+pibm_status pibm_set_particle_model(pibm_ctx* ctx, int model) {
+    if (!ctx) return PIBM_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (model != PIBM_PARTICLES_RESOLVED && model != PIBM_PARTICLES_POINT)
+        return fail(ctx, PIBM_ERR_ARG, "unknown particle model");
+    if (c.np > 0) return fail(ctx, PIBM_ERR_STATE, "set the particle model before the particles");
+    c.point = model == PIBM_PARTICLES_POINT;
+    drop_graphs(c);
     return PIBM_OK;
 }
 

@@ -461,11 +461,116 @@ __global__ void __launch_bounds__(CP_THREADS) k_nu_reduce(const double* part, in
     if (threadIdx.x == 0) out[0] = sh[0] * scale;
 }
 
+// Sub-grid particles (d_p <= h, the paper's own regime): one PIBM point per
+// particle at its centre, moving with it.  One thread per particle:
+// Eq lbm6 with four points per axis (at a wall the stencil is shifted inside),
+// Eqs lbm7, lbm8, lbm7.5 with A_p = pi d_p^2 / 4, Eq lbm13 for the particle, and
+// the delta_h spreading of Eqs lbm10-lbm12 over the 4^D support by atomic
+// additions (supports of nearby particles overlap; the order of the additions,
+// and so the last bits of F_B, can differ between runs).  The support box is
+// recorded for the next clear.
+__device__ __forceinline__ double delta_h_dev(double a) { return fabs(a) <= 2.0 ? 0.25 * (1.0 + cospi(0.5 * a)) : 0.0; }
+
+template <typename V> __device__ __forceinline__ void atomic_add4(V* p, double a, double b, double c, double d);
+template <> __device__ __forceinline__ void atomic_add4<float4>(float4* p, double a, double b, double c, double d) {
+    atomicAdd(&p->x, (float)a), atomicAdd(&p->y, (float)b), atomicAdd(&p->z, (float)c), atomicAdd(&p->w, (float)d);
+}
+template <> __device__ __forceinline__ void atomic_add4<double4_32a>(double4_32a* p, double a, double b, double c, double d) {
+    atomicAdd(&p->x, a), atomicAdd(&p->y, b), atomicAdd(&p->z, c), atomicAdd(&p->w, d);
+}
+
+template <int D, typename S>
+__global__ void __launch_bounds__(CP_THREADS) k_points(Geo G, const S* __restrict__ f, const S* __restrict__ g, int np,
+                                                       const double* __restrict__ X, const double* __restrict__ U,
+                                                       const double* __restrict__ Rr, const double* __restrict__ Tp,
+                                                       double kappa, double Tref, int parity, typename Store<S>::V4* fb,
+                                                       uint8_t* flags, int* box, double* Fh, double* Th, double* Hh) {
+    using L = Lat<D>;
+    using R = typename Store<S>::R;
+    using V = typename Store<S>::V4;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const double Xl[3] = {X[3 * p], X[3 * p + 1], D == 3 ? X[3 * p + 2] : 0.0};
+    const int nn[3] = {G.nx, G.ny, G.nz};
+    double Lw[3][4];
+    int base[3] = {0, 0, 0};
+    for (int a = 0; a < D; a++) {
+        int b = (int)floor(Xl[a]) - 1;
+        b = b > nn[a] - 4 ? nn[a] - 4 : b;
+        b = b < 0 ? 0 : b;
+        base[a] = b;
+        for (int k = 0; k < 4; k++) {
+            double Lk = 1.0;
+            for (int m = 0; m < 4; m++)
+                if (m != k) Lk *= (Xl[a] - (b + m)) / (double)(k - m);
+            Lw[a][k] = Lk;
+        }
+    }
+    R fl[L::Q], gl[L::QG];
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) fl[i] = 0;
+#pragma unroll
+    for (int k = 0; k < L::QG; k++) gl[k] = 0;
+    for (int kz = 0; kz < (D == 3 ? 4 : 1); kz++)
+        for (int ky = 0; ky < 4; ky++)
+            for (int kx = 0; kx < 4; kx++) {
+                const R w = (R)(Lw[0][kx] * Lw[1][ky] * (D == 3 ? Lw[2][kz] : 1.0));
+                R s[L::Q], sg[L::QG];
+                load_node<D, S, R>(G, f, g, base[0] + kx, base[1] + ky, D == 3 ? base[2] + kz : 0, parity, s, sg);
+#pragma unroll
+                for (int i = 0; i < L::Q; i++) fl[i] += w * s[i];
+#pragma unroll
+                for (int k = 0; k < L::QG; k++) gl[k] += w * sg[k];
+            }
+    R drho = 0, j[3] = {0, 0, 0}, dT = 0;
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+        drho += fl[i];
+        if (L::ex(i)) j[0] += L::ex(i) * fl[i];
+        if (L::ey(i)) j[1] += L::ey(i) * fl[i];
+        if (L::ez(i)) j[2] += L::ez(i) * fl[i];
+    }
+#pragma unroll
+    for (int k = 0; k < L::QG; k++) dT += gl[k];
+    const double rho = 1.0 + (double)drho;
+    const double A = 3.14159265358979323846 * Rr[p] * Rr[p];
+    double MF[3];
+    for (int a = 0; a < 3; a++) MF[a] = A * 2.0 * (rho * U[3 * p + a] - (double)j[a]);
+    if (D == 2) MF[2] = 0.0;
+    const double MQ = A * 2.0 * kappa * ((Tp[p] - Tref) - (double)dT);
+    for (int a = 0; a < 3; a++) {
+        Fh[3 * p + a] = -MF[a];
+        Th[3 * p + a] = 0.0;
+    }
+    Hh[p] = MQ;
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int a = 0; a < D; a++) {
+        lo[a] = (int)ceil(Xl[a] - 2.0);
+        hi[a] = (int)floor(Xl[a] + 2.0);
+        lo[a] = lo[a] < 0 ? 0 : lo[a];
+        hi[a] = hi[a] > nn[a] - 1 ? nn[a] - 1 : hi[a];
+    }
+    for (int a = 0; a < 3; a++) box[6 * p + a] = lo[a], box[6 * p + 3 + a] = hi[a];
+    for (int z = lo[2]; z <= hi[2]; z++)
+        for (int y = lo[1]; y <= hi[1]; y++)
+            for (int x = lo[0]; x <= hi[0]; x++) {
+                double w = delta_h_dev(x - Xl[0]) * delta_h_dev(y - Xl[1]);
+                if (D == 3) w *= delta_h_dev(z - Xl[2]);
+                const long long n = node_index(G, x, y, z);
+                atomic_add4<V>(fb + n, w * MF[0], w * MF[1], w * MF[2], w * MQ);
+                flags[((long long)z * G.ny + y) * G.ntx + (x >> 5)] = 1;
+            }
+}
+
 template <int D, typename S>
 static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
     using V = typename Store<S>::V4;
     if (!c->desc.pibm) return cudaSuccess;
-    if (c->np > 0) {
+    if (c->np > 0 && c->point) {
+        k_points<D, S><<<(c->np + CP_THREADS - 1) / CP_THREADS, CP_THREADS, 0, s>>>(
+            c->G, (const S*)c->f, (const S*)c->g, c->np, c->X, c->U, c->R, c->Tp, c->desc.kappa_T, c->desc.T_ref, parity,
+            (V*)c->fb[parity], c->flags[parity], c->box[parity], c->Fh, c->Th, c->Hh);
+    } else if (c->np > 0) {
         if (c->sg.enabled)  // the surrogate's feature sums ride along
             k_footprint<D, S, true><<<c->np, CP_THREADS, 0, s>>>(
                 c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk[parity], c->X, c->U, c->W, c->R, c->Tp, c->adj_start,
@@ -521,7 +626,8 @@ cudaError_t launch_coupling_clear(Ctx* c, cudaStream_t s, int parity) { PIBM_DIS
 
 int coupling_kernel_count(Ctx* c) {
     if (!c->desc.pibm) return 0;
-    return (c->np > 0 ? 3 : 0) + (c->nm > 0 ? 3 : 0);  // clear (on the DEM stream), footprint, spread
+    // clear (on the DEM stream), footprint, spread; point particles: clear, k_points
+    return (c->np > 0 ? (c->point ? 2 : 3) : 0) + (c->nm > 0 ? 3 : 0);
 }
 
 }  // namespace pibm

@@ -223,7 +223,7 @@ struct AAOffsets {
 };
 
 template <int D, typename S, int PARITY>
-__global__ void __launch_bounds__(512) k_stream_collide(Geo G, S* __restrict__ f, S* __restrict__ g,
+__global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) k_stream_collide(Geo G, S* __restrict__ f, S* __restrict__ g,
                                                         const typename Store<S>::V4* __restrict__ fb,
                                                         const uint8_t* __restrict__ flags,
                                                         CollideParams<typename Store<S>::R> P, AAOffsets O) {

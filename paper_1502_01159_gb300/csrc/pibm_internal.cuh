@@ -304,6 +304,7 @@ struct Ctx {
     int tune_pair_lattice;           // 1: two nodes per thread for 16-bit storage (nx a multiple of 64)
     int tune_lattice_threads;        // 0: default block shape; else threads per lattice block
     Surrogate sg;
+    int point;                       // particle model: 1 = one PIBM point per particle (d_p <= h)
     unsigned gen;                    // bumped whenever the captured step graphs become stale
     int* contact_pairs;   // 2 * dem.cap ints
     int* contact_scratch; // 2 * np + 4 ints

@@ -419,3 +419,21 @@ def test_cavity_nusselt_table1_paper_lattice(Ra, Ar):
     print("cavity250", Ra, Ar, sim.t, nu, paper, nu / paper - 1)
     assert np.isfinite(nu) and abs(nu - prev) < 2e-6 * abs(nu), "not steady"
     assert abs(nu / paper - 1.0) < 0.03, (nu, paper)
+
+
+@pytest.mark.parametrize("dim,shape,n_p", [(2, (96, 128, 1), 200), (3, (32, 36, 48), 150)])
+def test_point_particles_parity(dim, shape, n_p):
+    # the paper's own regime: sub-grid particles (d = 0.5 < h), one PIBM point
+    # each, settling and colliding; 100 steps against the oracle
+    case = W.points(dim=dim, shape=shape, n_p=n_p)
+    sim, orc = _sim(case), oracle.Oracle(case)
+    Fs, Fo = sim.read_particle_forces(), orc.particle_forces()
+    assert np.max(np.abs(Fs["F"] - Fo["F"])) <= 1e-6 * max(np.abs(Fo["F"]).max(), 1e-12)
+    sim.step(100)
+    orc.step(100)
+    ps, po = sim.read_particles(), orc.particles()
+    dX = np.max(np.abs(ps["X"] - po["X"]))
+    moved = np.max(np.abs(po["X"] - np.asarray(case["particles"]["X"])))
+    print("points", dim, dX, moved)
+    assert dX < POS_ATOL and moved > 1e-3
+    _compare_fields(sim, orc, FIELD_RTOL, dim)

@@ -211,3 +211,49 @@ def test_conduction_nusselt_equals_cylinder_shape_factor():
         prev = nu
     shape = np.pi / np.log(1.0787 * 2.5)
     assert abs(nu / shape - 1.0) < 0.01, (nu, shape)
+
+
+def _point_case(X, U, shape=(40, 30, 1), dim=2):
+    case = W.periodic_box(shape=shape, dim=dim, buoyancy=False)
+    case["walls"] = [(1, 0, 0.0)] * (2 * dim)
+    n = len(X)
+    case["particles"] = dict(X=np.asarray(X, float), U=np.asarray(U, float), R=np.full(n, 0.4),
+                             rho_p=np.full(n, 2.0), T_p=np.full(n, 0.5))
+    case["pibm"] = True
+    case["particle_model"] = "point"
+    return case
+
+
+def test_point_particle_in_fluid_at_rest():
+    # sub-grid particle (d_p <= h, the paper's own regime): one PIBM point with
+    # A_p = pi d_p^2 / 4; in fluid at rest (rho = 1, j = 0) Eq lbm8 gives
+    # F_f = 2 U_p, the particle feels -A_p F_f, and the delta_h spreading hands
+    # the fluid exactly the opposite momentum (away from walls)
+    U = [[0.01, -0.02, 0.0]]
+    o = oracle.Oracle(_point_case([[20.3, 14.6, 0.0]], U))
+    F = o.particle_forces()["F"][0]
+    A = np.pi * 0.4 ** 2
+    assert np.allclose(F[:2], -2 * A * np.array(U[0][:2]), rtol=1e-13, atol=0)
+    fb = np.stack([o.field("FBx"), o.field("FBy")])
+    assert np.allclose(fb.reshape(2, -1).sum(axis=1), -F[:2], rtol=1e-12)
+
+
+def test_point_particle_interpolation_near_a_wall_is_exact_for_linear_flow():
+    # Eq lbm6 with four points reproduces linear fields; next to a wall the
+    # stencil is shifted inside and still does.  Equilibrium populations of a
+    # shear u_x = a (y - 3): a resting point at height y_p feels
+    # F_x = -A_p 2 (0 - rho u_x(y_p)) = 2 A_p a (y_p - 3)
+    case = _point_case([[20.0, 0.7, 0.0]], [[0.0, 0.0, 0.0]])
+    o = oracle.Oracle(case)
+    nz, ny, nx = 1, 30, 40
+    a = 1e-3
+    y = np.arange(ny)[None, :, None] * np.ones((nz, ny, nx))
+    ux = a * (y - 3.0)
+    E = np.array(W.D2Q9_E, float)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    f = w[:, None, None, None] * (1 + 3 * E[:, 0, None, None, None] * ux[None])  # first-order equilibrium, rho = 1
+    g = np.array([1 / 3] + [1 / 6] * 4)[:, None, None, None] * 0.5 * np.ones((5, nz, ny, nx))
+    o.set_populations(f.ravel(), g.ravel())
+    F = o.particle_forces()["F"][0]
+    A = np.pi * 0.4 ** 2
+    assert abs(F[0] - 2 * A * a * (0.7 - 3.0)) < 1e-15 and abs(F[1]) < 1e-15
