@@ -40,7 +40,7 @@ class _Params(C.Structure):
         ("buoyancy", C.c_int), ("gravity_axis", C.c_int),
         ("body_force", C.c_double * 3), ("g_particle", C.c_double * 3),
         ("dem_substeps", C.c_int), ("kappa_T", C.c_double), ("cell_size", C.c_double),
-        ("nu_dT", C.c_double), ("pibm", C.c_int),
+        ("nu_dT", C.c_double), ("pibm", C.c_int), ("flow_q", C.c_int),
     ]
 
 
@@ -133,6 +133,7 @@ class Oracle:
         p.dem_substeps = case["dem_substeps"]
         p.kappa_T, p.cell_size, p.nu_dT = case["kappa_T"], case["cell_size"], case["nu_dT"]
         p.pibm = int(case["pibm"])
+        p.flow_q = int(case.get("flow_q", 0))
         self.L = lib()
         self.h = self.L.orc_create(C.byref(p))
         if not self.h:
@@ -140,7 +141,7 @@ class Oracle:
         self.dim = p.dim
         self.shape = (p.nz, p.ny, p.nx)
         self.N = p.nx * p.ny * p.nz
-        self.Q, self.QG = (9, 5) if self.dim == 2 else (19, 7)
+        self.Q, self.QG = (9, 5) if self.dim == 2 else ((15, 7) if p.flow_q == 15 else (19, 7))
         for face, (kind, thermal, Tw) in enumerate(case["walls"]):
             self.L.orc_set_wall(self.h, face, kind, thermal, Tw)
         law = case.get("contact")

@@ -64,6 +64,13 @@ static const double W3Q19[19] = {1.0 / 3,  1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 1
                                  1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36,
                                  1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 static const double W3Q7[7] = {1.0 / 4, 1.0 / 8, 1.0 / 8, 1.0 / 8, 1.0 / 8, 1.0 / 8, 1.0 / 8};
+/* D3Q15 (Section 2.1): rest, six axis links, eight cube diagonals; c_s^2 = 1/3 */
+static const int E15[15][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},
+                               {0, 0, 1},  {0, 0, -1},  {1, 1, 1},   {-1, -1, -1}, {1, 1, -1},
+                               {-1, -1, 1}, {1, -1, 1}, {-1, 1, -1}, {-1, 1, 1},  {1, -1, -1}};
+static const double W3Q15[15] = {2.0 / 9,  1.0 / 9,  1.0 / 9,  1.0 / 9,  1.0 / 9,
+                                 1.0 / 9,  1.0 / 9,  1.0 / 72, 1.0 / 72, 1.0 / 72,
+                                 1.0 / 72, 1.0 / 72, 1.0 / 72, 1.0 / 72, 1.0 / 72};
 
 static const double PI = 3.14159265358979323846;
 
@@ -825,6 +832,8 @@ static void dem(orc_sim* s) {
 orc_sim* orc_create(const orc_params* p) {
     if (!p || (p->dim != 2 && p->dim != 3) || p->nx < 1 || p->ny < 1 || p->nz < 1) return NULL;
     if (p->dim == 2 && p->nz != 1) return NULL;
+    if (p->flow_q != 0 && !(p->dim == 3 && (p->flow_q == 15 || p->flow_q == 19)) && !(p->dim == 2 && p->flow_q == 9))
+        return NULL;
     orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
     s->P = *p;
     s->D = p->dim;
@@ -835,6 +844,13 @@ orc_sim* orc_create(const orc_params* p) {
         s->w = W2Q9;
         s->wg = W2Q5;
         s->csT2 = 1.0 / 3.0;
+    } else if (p->flow_q == 15) {
+        s->Q = 15;
+        s->QG = 7;
+        s->e = E15;
+        s->w = W3Q15;
+        s->wg = W3Q7;
+        s->csT2 = 1.0 / 4.0;
     } else {
         s->Q = 19;
         s->QG = 7;

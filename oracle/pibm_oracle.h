@@ -45,6 +45,7 @@ typedef struct {
     double cell_size;        /* minimum DEM cell side; <= 0: 2*R_max + 1.5 */
     double nu_dT;            /* T_hot - T_inf in the Nusselt number */
     int pibm;                /* 1: particles and fluid are coupled */
+    int flow_q;              /* 3-D flow lattice: 0 or 19 D3Q19, 15 D3Q15 (Section 2.1's own); 2-D: D2Q9 */
 } orc_params;
 
 enum { ORC_PERIODIC = 0, ORC_WALL = 1 };

@@ -13,8 +13,14 @@ import oracle
 import workloads as W
 
 
-def _poiseuille_err(ny, nu, steps, dim=2):
+E15 = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1), (1, 1, 1), (-1, -1, -1),
+       (1, 1, -1), (-1, -1, 1), (1, -1, 1), (-1, 1, -1), (-1, 1, 1), (1, -1, -1)]
+W15 = [2 / 9] + [1 / 9] * 6 + [1 / 72] * 8
+
+
+def _poiseuille_err(ny, nu, steps, dim=2, flow_q=0):
     case = W.poiseuille(ny=ny, nu=nu, dim=dim, nz=3 if dim == 3 else 1)
+    case["flow_q"] = flow_q
     o = oracle.Oracle(case)
     o.step(steps)
     ux = o.field("ux")[0, :, 0]
@@ -24,11 +30,12 @@ def _poiseuille_err(ny, nu, steps, dim=2):
     return np.max(np.abs(ux - exact)) / exact.max(), o
 
 
-@pytest.mark.parametrize("dim", [2, 3])
-def test_poiseuille_exact_at_magic_tau(dim):
+@pytest.mark.parametrize("dim,flow_q", [(2, 0), (3, 0), (3, 15)])
+def test_poiseuille_exact_at_magic_tau(dim, flow_q):
     # Halfway bounce-back + BGK reproduces the parabola exactly when
-    # tau_f = 1/2 + sqrt(3/16): walls at y = -1/2 and ny - 1/2.
-    err, o = _poiseuille_err(16, np.sqrt(3.0 / 16.0) / 3.0, 20000, dim)
+    # tau_f = 1/2 + sqrt(3/16): walls at y = -1/2 and ny - 1/2 (D2Q9, D3Q19
+    # and the paper's D3Q15)
+    err, o = _poiseuille_err(16, np.sqrt(3.0 / 16.0) / 3.0, 20000, dim, flow_q)
     assert abs(o.relaxation()["tau_f"] - (0.5 + np.sqrt(3.0 / 16.0))) < 1e-15
     assert err < 1e-9
     if dim == 3:
@@ -55,15 +62,16 @@ def test_conduction_linear_profile(dim):
 
 def _totals(o):
     f, g = o.populations()
-    E = np.array(W.D2Q9_E if o.dim == 2 else W.D3Q19_E, dtype=np.float64)
+    E = np.array(W.D2Q9_E if o.dim == 2 else (E15 if o.Q == 15 else W.D3Q19_E), dtype=np.float64)
     mass = f.sum()
     mom = E.T @ f.reshape(f.shape[0], -1).sum(axis=1)
     return mass, mom, g.sum()
 
 
-@pytest.mark.parametrize("dim,shape", [(2, (16, 12, 1)), (3, (6, 5, 4))])
-def test_periodic_box_invariants(dim, shape):
+@pytest.mark.parametrize("dim,shape,flow_q", [(2, (16, 12, 1), 0), (3, (6, 5, 4), 0), (3, (6, 5, 4), 15)])
+def test_periodic_box_invariants(dim, shape, flow_q):
     case = W.periodic_box(shape=shape, dim=dim, buoyancy=True)
+    case["flow_q"] = flow_q
     o = oracle.Oracle(case)
     f, g = W.random_populations(case)
     o.set_populations(f.ravel(), g.ravel())
@@ -139,6 +147,29 @@ def test_thermal_diffusivity(dim):
     a2 = np.sum((o.field("T")[0, 0, :] - 0.5) * np.sin(k * x))
     rate = -np.log(a2 / a1) / 600
     assert abs(rate / (alpha * k * k) - 1) < 5e-3
+
+
+def test_shear_wave_viscosity_d3q15():
+    # the paper's 3-D lattice: u_x = A sin(k z) decays as exp(-nu k^2 t) with
+    # nu = (tau_f - 1/2) / 3 (c_s^2 = 1/3 on D3Q15 as on D3Q19)
+    nz = 48
+    case = W.periodic_box(shape=(3, 3, nz), dim=3, buoyancy=False)
+    case.update(Ra=1e4, Pr=0.71, U_c=0.1, L_c=64.0, flow_q=15)
+    o = oracle.Oracle(case)
+    nu = o.relaxation()["nu"]
+    k = 2 * np.pi / nz
+    z = np.arange(nz)
+    ux = 1e-4 * np.sin(k * z)
+    E = np.array(E15, dtype=float)
+    f = np.array(W15)[:, None, None, None] * (1 + 3 * E[:, 0, None, None, None] * ux[None, :, None, None])
+    f = np.broadcast_to(f, (15, nz, 3, 3)).copy()
+    o.set_populations(f.ravel(), None)
+    o.step(100)
+    a1 = np.sum(o.field("ux")[:, 0, 0] * np.sin(k * z))
+    o.step(600)
+    a2 = np.sum(o.field("ux")[:, 0, 0] * np.sin(k * z))
+    rate = -np.log(a2 / a1) / 600
+    assert abs(rate / (nu * k * k) - 1) < 5e-3
 
 
 def test_rest_state_is_stationary():

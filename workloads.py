@@ -9,7 +9,8 @@ Case dict keys
 --------------
 dim, shape=(nx, ny, nz), Ra, Pr, U_c, L_c, T_ref, T_init, buoyancy,
 gravity_axis, body_force[3], g_particle[3], dem_substeps, kappa_T, cell_size,
-nu_dT, pibm, walls = 2*dim entries (kind, thermal, T_w) ordered
+nu_dT, pibm, flow_q (0 default; 15 selects D3Q15 in 3-D), particle_model
+("resolved" or "point"), walls = 2*dim entries (kind, thermal, T_w) ordered
 x-lo, x-hi, y-lo, y-hi, z-lo, z-hi (kind 0 periodic / 1 wall; thermal 0
 adiabatic / 1 isothermal), contact = contact-law dict, particles = dict of
 arrays (X n*3, U, W, R, rho_p, T_p, heat_cap, fixed) or None, markers =
@@ -225,6 +226,9 @@ def random_populations(case, config_index=7, amp=0.01):
     if dim == 2:
         w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
         wg = np.array([1 / 3] + [1 / 6] * 4)
+    elif case.get("flow_q", 0) == 15:
+        w = np.array([2 / 9] + [1 / 9] * 6 + [1 / 72] * 8)
+        wg = np.array([1 / 4] + [1 / 8] * 6)
     else:
         w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
         wg = np.array([1 / 4] + [1 / 8] * 6)
