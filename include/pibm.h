@@ -106,6 +106,9 @@ typedef struct {
     double cell_size;       /* minimum DEM cell side; <= 0 selects 2 R_max + 1.5 */
     double nu_dT;           /* T_hot - T_inf in the Nusselt number */
     int pibm;               /* 1: couple fluid and particles */
+    int flow_q;             /* 3-D flow lattice: 0 or 19 D3Q19, 15 D3Q15 (Section 2.1's own 3-D
+                               lattice: rest 2/9, six axis links 1/9, eight cube diagonals 1/72);
+                               2-D: 0 or 9 (D2Q9).  The thermal lattice is D2Q5 / D3Q7. */
 } pibm_desc;
 
 /* Create a context: allocates the lattice (f and g initialised to the rest

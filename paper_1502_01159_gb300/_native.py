@@ -35,7 +35,7 @@ class pibm_desc(C.Structure):
         ("buoyancy", C.c_int), ("gravity_axis", C.c_int),
         ("body_force", C.c_double * 3), ("g_particle", C.c_double * 3),
         ("dem_substeps", C.c_int), ("kappa_T", C.c_double), ("cell_size", C.c_double),
-        ("nu_dT", C.c_double), ("pibm", C.c_int),
+        ("nu_dT", C.c_double), ("pibm", C.c_int), ("flow_q", C.c_int),
     ]
 
 
@@ -145,6 +145,7 @@ def desc_from_case(case: dict) -> pibm_desc:
     d.dem_substeps = case["dem_substeps"]
     d.kappa_T, d.cell_size, d.nu_dT = case["kappa_T"], case["cell_size"], case["nu_dT"]
     d.pibm = int(case["pibm"])
+    d.flow_q = int(case.get("flow_q", 0))
     return d
 
 
@@ -189,7 +190,7 @@ class Simulation:
         self.dim = d.dim
         self.shape = (d.nz, d.ny, d.nx)
         self.N = d.nx * d.ny * d.nz
-        self.Q, self.QG = (9, 5) if self.dim == 2 else (19, 7)
+        self.Q, self.QG = (9, 5) if self.dim == 2 else ((15, 7) if d.flow_q == 15 else (19, 7))
         self.np = 0
         self.allocator = None
         self.stream = None

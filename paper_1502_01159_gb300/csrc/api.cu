@@ -206,13 +206,16 @@ pibm_status pibm_create(const pibm_desc* d, void* stream, const pibm_allocator* 
         d->gravity_axis >= d->dim || d->dem_substeps < 1 || d->nu_dT == 0.0)
         return g_create_error = "invalid physical parameters", PIBM_ERR_ARG;
     if ((long long)d->nx * d->ny * d->nz > (1LL << 31) - 1) return g_create_error = "lattice too large", PIBM_ERR_ARG;
+    if (d->flow_q != 0 && !(d->dim == 2 && d->flow_q == 9) && !(d->dim == 3 && (d->flow_q == 19 || d->flow_q == 15)))
+        return g_create_error = "flow lattice: 9 in 2-D, 19 or 15 in 3-D (0 = default)", PIBM_ERR_ARG;
 
     pibm_ctx* ctx = new pibm_ctx();
     Ctx& c = ctx->c;
     memset((void*)&c.desc, 0, sizeof(c.desc));
     c.desc = *d;
     c.D = d->dim;
-    c.Q = c.D == 2 ? 9 : 19;
+    c.lat = c.D == 2 ? 2 : (d->flow_q == 15 ? 4 : 3);
+    c.Q = c.D == 2 ? 9 : (c.lat == 4 ? 15 : 19);
     c.QG = c.D == 2 ? 5 : 7;
     c.G.nx = d->nx, c.G.ny = d->ny, c.G.nz = d->nz;
     c.G.N = (long long)d->nx * d->ny * d->nz;

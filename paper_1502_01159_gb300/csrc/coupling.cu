@@ -33,10 +33,10 @@ __device__ __forceinline__ double eps_of(double x, double y, double z, const dou
     return e > 1.0 ? 1.0 : e;
 }
 
-__device__ __forceinline__ void footprint_box(const Geo& G, int D, const double* X, double R, int* lo, int* hi) {
+__device__ __forceinline__ void footprint_box(const Geo& G, int dim, const double* X, double R, int* lo, int* hi) {
     int n[3] = {G.nx, G.ny, G.nz};
     for (int a = 0; a < 3; a++) {
-        if (a < D) {
+        if (a < dim) {
             lo[a] = (int)ceil(X[a] - R - 0.5);
             hi[a] = (int)floor(X[a] + R + 0.5);
             if (lo[a] < 0) lo[a] = 0;
@@ -132,11 +132,11 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
     const double Rp = Rr[p];
     if (threadIdx.x == 0) {
         int lo[3], hi[3];
-        footprint_box(G, D, Xp, Rp, lo, hi);
+        footprint_box(G, Lat<D>::dim, Xp, Rp, lo, hi);
         for (int a = 0; a < 3; a++) {
             s_box[a] = lo[a];
             s_box[3 + a] = hi[a];
-            s_base[a] = (a < D) ? (int)floor(Xp[a]) : 0;
+            s_base[a] = (a < Lat<D>::dim) ? (int)floor(Xp[a]) : 0;
             s_cf[a] = (float)(Xp[a] - s_base[a]);
             s_U[a] = (float)U[3 * p + a];
             s_W[a] = (float)W[3 * p + a];
@@ -252,8 +252,8 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
         acc[6] += (float)M[3];
         if constexpr (FEAT) {
             const float inv = 1.f / (float)rho;
-            const float u[3] = {(float)j[0] * inv, (float)j[1] * inv, D == 3 ? (float)j[2] * inv : 0.f};
-            const float dz = D == 3 ? arm[2] : 0.f;
+            const float u[3] = {(float)j[0] * inv, (float)j[1] * inv, Lat<D>::dim == 3 ? (float)j[2] * inv : 0.f};
+            const float dz = Lat<D>::dim == 3 ? arm[2] : 0.f;
             fa[0] += 1.f;
             fa[1] += arm[0], fa[2] += arm[1], fa[3] += dz;
             fa[4] += arm[0] * arm[0], fa[5] += arm[1] * arm[1], fa[6] += dz * dz;
@@ -305,11 +305,11 @@ __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __re
     if (threadIdx.x == 0) {
         const double Xp[3] = {X[3 * p], X[3 * p + 1], X[3 * p + 2]};
         int lo[3], hi[3];
-        footprint_box(G, D, Xp, Rr[p], lo, hi);
+        footprint_box(G, Lat<D>::dim, Xp, Rr[p], lo, hi);
         int n[3] = {G.nx, G.ny, G.nz};
         for (int a = 0; a < 3; a++) {
             int ilo = lo[a], ihi = hi[a];
-            if (a < D) {
+            if (a < Lat<D>::dim) {
                 lo[a] = max(lo[a] - 1, 0);
                 hi[a] = min(hi[a] + 1, n[a] - 1);
                 ilo = max(lo[a] - 1, 0);
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __re
     for (long long q = threadIdx.x; q < cnt; q += blockDim.x) {
         int x = lo[0] + (int)(q % ex), y = lo[1] + (int)((q / ex) % ey), z = lo[2] + (int)(q / ((long long)ex * ey));
         T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-        for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); dz++) {
+        for (int dz = (Lat<D>::dim == 3 ? -1 : 0); dz <= (Lat<D>::dim == 3 ? 1 : 0); dz++) {
             int zz = z + dz;
             if (zz < 0 || zz >= G.nz) continue;
             for (int dy = -1; dy <= 1; dy++) {
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __re
                     if (xx < 0 || xx >= G.nx) continue;
                     // delta_h(0) = 1/2, delta_h(+-1) = 1/4 (Eq lbm12)
                     T w = (dx == 0 ? (T)0.5 : (T)0.25) * (dy == 0 ? (T)0.5 : (T)0.25);
-                    if (D == 3) w *= (dz == 0 ? (T)0.5 : (T)0.25);
+                    if (Lat<D>::dim == 3) w *= (dz == 0 ? (T)0.5 : (T)0.25);
                     V m = staged ? tile[((long long)(zz - ilo[2]) * sy + (yy - ilo[1])) * sx + (xx - ilo[0])]
                                  : mk[node_index(G, xx, yy, zz)];
                     s0 += w * m.x;
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_markers(Geo G, const S* __restri
     double Xl[3] = {MX[3 * l], MX[3 * l + 1], MX[3 * l + 2]};
     double Lw[3][4];
     int base[3] = {0, 0, 0};
-    for (int a = 0; a < D; a++) {
+    for (int a = 0; a < Lat<D>::dim; a++) {
         base[a] = (int)floor(Xl[a]) - 1;
         for (int k = 0; k < 4; k++) {  // Eq lbm6, four points per axis
             double Lk = 1.0;
@@ -395,12 +395,12 @@ __global__ void __launch_bounds__(CP_THREADS) k_markers(Geo G, const S* __restri
 #pragma unroll
     for (int k = 0; k < L::QG; k++) gl[k] = 0;
     int nn[3] = {G.nx, G.ny, G.nz};
-    for (int kz = 0; kz < (D == 3 ? 4 : 1); kz++)
+    for (int kz = 0; kz < (Lat<D>::dim == 3 ? 4 : 1); kz++)
         for (int ky = 0; ky < 4; ky++)
             for (int kx = 0; kx < 4; kx++) {
-                int c[3] = {base[0] + kx, base[1] + ky, D == 3 ? base[2] + kz : 0};
-                for (int a = 0; a < D; a++) c[a] = ((c[a] % nn[a]) + nn[a]) % nn[a];
-                R wgt = (R)(Lw[0][kx] * Lw[1][ky] * (D == 3 ? Lw[2][kz] : 1.0));
+                int c[3] = {base[0] + kx, base[1] + ky, Lat<D>::dim == 3 ? base[2] + kz : 0};
+                for (int a = 0; a < Lat<D>::dim; a++) c[a] = ((c[a] % nn[a]) + nn[a]) % nn[a];
+                R wgt = (R)(Lw[0][kx] * Lw[1][ky] * (Lat<D>::dim == 3 ? Lw[2][kz] : 1.0));
                 R s[L::Q], sg[L::QG];
                 load_node<D, S, R>(G, f, g, c[0], c[1], c[2], parity, s, sg);
 #pragma unroll
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_markers(Geo G, const S* __restri
     typename Store<S>::V4 mv;
     mv.x = A * (R)(-2) * j[0];  // static marker: U_l = 0, F_f = -2 j
     mv.y = A * (R)(-2) * j[1];
-    mv.z = D == 3 ? A * (R)(-2) * j[2] : (R)0;
+    mv.z = Lat<D>::dim == 3 ? A * (R)(-2) * j[2] : (R)0;
     mv.w = A * (R)2 * (R)kappa * dTp;
     Ml[l] = mv;
     nu_part[l] = (double)A * (double)dTp;
@@ -490,11 +490,11 @@ __global__ void __launch_bounds__(CP_THREADS) k_points(Geo G, const S* __restric
     using V = typename Store<S>::V4;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
-    const double Xl[3] = {X[3 * p], X[3 * p + 1], D == 3 ? X[3 * p + 2] : 0.0};
+    const double Xl[3] = {X[3 * p], X[3 * p + 1], Lat<D>::dim == 3 ? X[3 * p + 2] : 0.0};
     const int nn[3] = {G.nx, G.ny, G.nz};
     double Lw[3][4];
     int base[3] = {0, 0, 0};
-    for (int a = 0; a < D; a++) {
+    for (int a = 0; a < Lat<D>::dim; a++) {
         int b = (int)floor(Xl[a]) - 1;
         b = b > nn[a] - 4 ? nn[a] - 4 : b;
         b = b < 0 ? 0 : b;
@@ -511,12 +511,12 @@ __global__ void __launch_bounds__(CP_THREADS) k_points(Geo G, const S* __restric
     for (int i = 0; i < L::Q; i++) fl[i] = 0;
 #pragma unroll
     for (int k = 0; k < L::QG; k++) gl[k] = 0;
-    for (int kz = 0; kz < (D == 3 ? 4 : 1); kz++)
+    for (int kz = 0; kz < (Lat<D>::dim == 3 ? 4 : 1); kz++)
         for (int ky = 0; ky < 4; ky++)
             for (int kx = 0; kx < 4; kx++) {
-                const R w = (R)(Lw[0][kx] * Lw[1][ky] * (D == 3 ? Lw[2][kz] : 1.0));
+                const R w = (R)(Lw[0][kx] * Lw[1][ky] * (Lat<D>::dim == 3 ? Lw[2][kz] : 1.0));
                 R s[L::Q], sg[L::QG];
-                load_node<D, S, R>(G, f, g, base[0] + kx, base[1] + ky, D == 3 ? base[2] + kz : 0, parity, s, sg);
+                load_node<D, S, R>(G, f, g, base[0] + kx, base[1] + ky, Lat<D>::dim == 3 ? base[2] + kz : 0, parity, s, sg);
 #pragma unroll
                 for (int i = 0; i < L::Q; i++) fl[i] += w * s[i];
 #pragma unroll
@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_points(Geo G, const S* __restric
     }
     Hh[p] = MQ;
     int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-    for (int a = 0; a < D; a++) {
+    for (int a = 0; a < Lat<D>::dim; a++) {
         lo[a] = (int)ceil(Xl[a] - 2.0);
         hi[a] = (int)floor(Xl[a] + 2.0);
         lo[a] = lo[a] < 0 ? 0 : lo[a];
@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_points(Geo G, const S* __restric
         for (int y = lo[1]; y <= hi[1]; y++)
             for (int x = lo[0]; x <= hi[0]; x++) {
                 double w = delta_h_dev(x - Xl[0]) * delta_h_dev(y - Xl[1]);
-                if (D == 3) w *= delta_h_dev(z - Xl[2]);
+                if (Lat<D>::dim == 3) w *= delta_h_dev(z - Xl[2]);
                 const long long n = node_index(G, x, y, z);
                 atomic_add4<V>(fb + n, w * MF[0], w * MF[1], w * MF[2], w * MQ);
                 flags[((long long)z * G.ny + y) * G.ntx + (x >> 5)] = 1;

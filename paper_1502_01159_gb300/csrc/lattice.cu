@@ -179,6 +179,11 @@ template <typename S> struct OddLoad<2, S, 9> {
     static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, const S*, const S*, long long, int,
                                                long long, long long, R*, R*) {}
 };
+template <typename S> struct OddLoad<4, S, 15> {
+    using R = typename Store<S>::R;
+    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, const S*, const S*, long long, int,
+                                               long long, long long, R*, R*) {}
+};
 template <typename S> struct OddLoad<3, S, 19> {
     using R = typename Store<S>::R;
     static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, const S*, const S*, long long, int,
@@ -204,6 +209,11 @@ struct OddStore {
     }
 };
 template <typename S> struct OddStore<2, S, 9> {
+    using R = typename Store<S>::R;
+    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, S*, S*, long long, int, long long,
+                                               long long, const R*, const R*) {}
+};
+template <typename S> struct OddStore<4, S, 15> {
     using R = typename Store<S>::R;
     static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, S*, S*, long long, int, long long,
                                                long long, const R*, const R*) {}
@@ -760,7 +770,7 @@ __global__ void k_feature_solve(int n, const double* __restrict__ fsum, const do
     const double m = s[0];
     if (m > 0) {
         double A[36], b[6];
-        if (D == 3) {
+        if (Lat<D>::dim == 3) {
             const double Dd[3] = {s[1], s[2], s[3]};
             const double trace = s[4] + s[5] + s[6];
             const double M[9] = {trace - s[4], -s[7], -s[8], -s[7], trace - s[5], -s[9], -s[8], -s[9], trace - s[6]};
@@ -830,7 +840,7 @@ __global__ void __launch_bounds__(NB_T) k_neighbour_features(int n, int slice_le
             const double Rq = R[q];
             if (dist < 4.0 * Rp) {
                 const double sr = Rq / (4.0 * Rp);
-                phi += D == 3 ? sr * sr * sr : sr * sr;
+                phi += Lat<D>::dim == 3 ? sr * sr * sr : sr * sr;
             }
             double gap = (dist - Rp) - Rq;
             for (int k = 0; k < 4; k++)  // insert into the sorted four

@@ -19,7 +19,7 @@ namespace pibm {
 // a compile-time index fold to constants after unrolling.
 template <int D> struct Lat;
 template <> struct Lat<2> {
-    static constexpr int Q = 9, QG = 5;
+    static constexpr int Q = 9, QG = 5, dim = 2;
     __host__ __device__ static constexpr int ex(int i) { return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0); }
     __host__ __device__ static constexpr int ey(int i) { return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0); }
     __host__ __device__ static constexpr int ez(int) { return 0; }
@@ -29,7 +29,7 @@ template <> struct Lat<2> {
     static constexpr double inv_csT2 = 3.0;  // D2Q5: cs_T^2 = 1/3
 };
 template <> struct Lat<3> {
-    static constexpr int Q = 19, QG = 7;
+    static constexpr int Q = 19, QG = 7, dim = 3;
     __host__ __device__ static constexpr int ex(int i) {
         return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1 : ((i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0);
     }
@@ -41,6 +41,26 @@ template <> struct Lat<3> {
     }
     __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
     __host__ __device__ static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+    __host__ __device__ static constexpr double wg(int k) { return k == 0 ? 0.25 : 0.125; }
+    static constexpr double inv_csT2 = 4.0;  // D3Q7: cs_T^2 = 1/4
+};
+
+// D3Q15 (Section 2.1's own 3-D lattice) with the D3Q7 thermal lattice: rest,
+// six axis links (1/9), eight cube diagonals (1/72); c_s^2 = 1/3.  Lattice id
+// 4 in the kernels' first template argument (2: D2Q9, 3: D3Q19).
+template <> struct Lat<4> {
+    static constexpr int Q = 15, QG = 7, dim = 3;
+    __host__ __device__ static constexpr int ex(int i) {
+        return (i == 1 || i == 7 || i == 9 || i == 11 || i == 14) ? 1 : ((i == 2 || i == 8 || i == 10 || i == 12 || i == 13) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int ey(int i) {
+        return (i == 3 || i == 7 || i == 9 || i == 12 || i == 13) ? 1 : ((i == 4 || i == 8 || i == 10 || i == 11 || i == 14) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int ez(int i) {
+        return (i == 5 || i == 7 || i == 10 || i == 11 || i == 13) ? 1 : ((i == 6 || i == 8 || i == 9 || i == 12 || i == 14) ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+    __host__ __device__ static constexpr double w(int i) { return i == 0 ? 2.0 / 9.0 : (i <= 6 ? 1.0 / 9.0 : 1.0 / 72.0); }
     __host__ __device__ static constexpr double wg(int k) { return k == 0 ? 0.25 : 0.125; }
     static constexpr double inv_csT2 = 4.0;  // D3Q7: cs_T^2 = 1/4
 };
@@ -85,13 +105,13 @@ template <> struct Store<__nv_bfloat16> {
     do {                                                                                                \
         switch ((c)->desc.storage) {                                                                    \
             case PIBM_STORE_F64:                                                                        \
-                return (c)->D == 2 ? FN<2, double>(__VA_ARGS__) : FN<3, double>(__VA_ARGS__);           \
+                return (c)->D == 2 ? FN<2, double>(__VA_ARGS__) : ((c)->lat == 4 ? FN<4, double>(__VA_ARGS__) : FN<3, double>(__VA_ARGS__));           \
             case PIBM_STORE_F16:                                                                        \
-                return (c)->D == 2 ? FN<2, __half>(__VA_ARGS__) : FN<3, __half>(__VA_ARGS__);           \
+                return (c)->D == 2 ? FN<2, __half>(__VA_ARGS__) : ((c)->lat == 4 ? FN<4, __half>(__VA_ARGS__) : FN<3, __half>(__VA_ARGS__));           \
             case PIBM_STORE_BF16:                                                                       \
-                return (c)->D == 2 ? FN<2, __nv_bfloat16>(__VA_ARGS__) : FN<3, __nv_bfloat16>(__VA_ARGS__); \
+                return (c)->D == 2 ? FN<2, __nv_bfloat16>(__VA_ARGS__) : ((c)->lat == 4 ? FN<4, __nv_bfloat16>(__VA_ARGS__) : FN<3, __nv_bfloat16>(__VA_ARGS__)); \
             default:                                                                                    \
-                return (c)->D == 2 ? FN<2, float>(__VA_ARGS__) : FN<3, float>(__VA_ARGS__);             \
+                return (c)->D == 2 ? FN<2, float>(__VA_ARGS__) : ((c)->lat == 4 ? FN<4, float>(__VA_ARGS__) : FN<3, float>(__VA_ARGS__));             \
         }                                                                                               \
     } while (0)
 
@@ -304,6 +324,7 @@ struct Ctx {
     int tune_pair_lattice;           // 1: two nodes per thread for 16-bit storage (nx a multiple of 64)
     int tune_lattice_threads;        // 0: default block shape; else threads per lattice block
     Surrogate sg;
+    int lat;                         // lattice id: 2 D2Q9, 3 D3Q19, 4 D3Q15 (all with D2Q5 / D3Q7 thermal)
     int point;                       // particle model: 1 = one PIBM point per particle (d_p <= h)
     unsigned gen;                    // bumped whenever the captured step graphs become stale
     int* contact_pairs;   // 2 * dem.cap ints

@@ -437,3 +437,45 @@ def test_point_particles_parity(dim, shape, n_p):
     print("points", dim, dX, moved)
     assert dX < POS_ATOL and moved > 1e-3
     _compare_fields(sim, orc, FIELD_RTOL, dim)
+
+
+@pytest.mark.parametrize("kind", ["periodic", "walled", "sedimentation", "periodic_f16"])
+def test_d3q15_parity(kind):
+    # the paper's own 3-D flow lattice (D3Q15) with the D3Q7 thermal lattice
+    if kind.startswith("periodic"):
+        case = W.periodic_box(shape=(37, 13, 11), dim=3, buoyancy=True, body=(2e-6, -1e-6, 0.0))
+    elif kind == "walled":
+        case = W.periodic_box(shape=(35, 19, 23), dim=3, buoyancy=True)
+        case["walls"] = [(1, 1, 0.0), (1, 0, 0.0), (1, 1, 1.0), (1, 1, 0.2), (1, 0, 0.0), (1, 1, 0.7)]
+    else:
+        case = _small_sed3d()
+    case["flow_q"] = 15
+    if kind.endswith("f16"):
+        case["storage"] = "f16"
+    sim, orc = _sim(case), oracle.Oracle(case)
+    if kind != "sedimentation":
+        f, g = W.random_populations(case, amp=0.02, config_index=8)
+        sim.set_populations(f.ravel(), g.ravel())
+        orc.set_populations(f.ravel(), g.ravel())
+    for k in (1, 1, 98):
+        sim.step(k)
+        orc.step(k)
+    if kind.endswith("f16"):
+        errs = {n: rel_l2(sim.read_field(n), orc.field(n)) for n in ("rho", "T")}
+        assert errs["rho"] < REDUCED_BOUNDS["f16"]["rho"] and errs["T"] < REDUCED_BOUNDS["f16"]["T"], errs
+        return
+    _compare_fields(sim, orc, FIELD_RTOL, 3)
+    if kind == "sedimentation":
+        assert np.max(np.abs(sim.read_particles()["X"] - orc.particles()["X"])) < POS_ATOL
+
+
+def test_d3q15_poiseuille_closed_form_on_gpu():
+    case = W.poiseuille(ny=16, nx=4, dim=3, nz=3)
+    case["flow_q"] = 15
+    sim = _sim(case)
+    sim.step(20000)
+    ux = sim.read_field("ux")[1, :, 2]
+    y = np.arange(16)
+    nu = sim.relaxation()["nu"]
+    exact = case["body_force"][0] / (2 * nu) * (y + 0.5) * (16 - 0.5 - y)
+    assert np.max(np.abs(ux - exact)) / exact.max() < 2e-5
