@@ -447,6 +447,7 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     c.X = (double*)A(v3), c.U = (double*)A(v3), c.W = (double*)A(v3), c.Xb = (double*)A(v3);
     c.R = (double*)A(v1), c.rho = (double*)A(v1), c.Tp = (double*)A(v1), c.Cp = (double*)A(v1);
     c.m = (double*)A(v1), c.I = (double*)A(v1), c.mg = (double*)A(v1);
+    c.im = (double*)A(v1), c.iI = (double*)A(v1);
     c.fixed = (uint8_t*)A(n + 1);
     c.Fh = (double*)A(v3), c.Th = (double*)A(v3), c.Hh = (double*)A(v1), c.Fc = (double*)A(v3), c.Tc = (double*)A(v3);
     c.Fh_prev = (double*)A(v3), c.Th_prev = (double*)A(v3), c.Hh_prev = (double*)A(v1);
@@ -472,7 +473,7 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     c.wall_ft = (float*)A(sizeof(float) * 18 * (n + 1));
     c.contact_pairs = (int*)A(sizeof(int) * 2 * C.cap);
     c.contact_scratch = (int*)A(sizeof(int) * (2 * n + 8));
-    void* need[] = {c.X, c.U, c.W, c.Xb, c.R, c.rho, c.Tp, c.Cp, c.m, c.I, c.mg, c.fixed, c.Fh, c.Th, c.Hh, c.Fc,
+    void* need[] = {c.X, c.U, c.W, c.Xb, c.R, c.rho, c.Tp, c.Cp, c.m, c.I, c.mg, c.im, c.iI, c.fixed, c.Fh, c.Th, c.Hh, c.Fc,
                     c.Fh_prev, c.Th_prev, c.Hh_prev, c.have_prev, c.adj_start_new,
                     c.Tc, c.box[0], c.box[1], c.cell_of, c.cell_cnt, c.cell_start, c.cell_ids, c.cnt_hi, c.cnt_lo, c.nb_start[0],
                     c.nb_start[1], c.nb_i[0], c.nb_i[1], c.nb_j[0], c.nb_j[1], c.nb_ft[0], c.nb_ft[1], c.adj_start,
@@ -491,6 +492,12 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     PCHECK(up(c.Tp, hT.data(), sizeof(double) * n));
     PCHECK(up(c.Cp, hC.data(), sizeof(double) * n));
     PCHECK(up(c.m, hm.data(), sizeof(double) * n));
+    {
+        std::vector<double> him(n), hiI(n);
+        for (int p = 0; p < n; p++) him[p] = 1.0 / hm[p], hiI[p] = 1.0 / hI[p];
+        PCHECK(up(c.im, him.data(), sizeof(double) * n));
+        PCHECK(up(c.iI, hiI.data(), sizeof(double) * n));
+    }
     PCHECK(up(c.I, hI.data(), sizeof(double) * n));
     PCHECK(up(c.mg, hmg.data(), sizeof(double) * n));
     PCHECK(up(c.fixed, hfix.data(), n));
@@ -874,7 +881,7 @@ static std::vector<BufRef> state_buffers(Ctx& c) {
     if (n > 0) {
         size_t v3 = sizeof(double) * 3 * n, v1 = sizeof(double) * n;
         BufRef pv[] = {{"X", c.X, v3}, {"U", c.U, v3}, {"W", c.W, v3}, {"Xb", c.Xb, v3}, {"R", c.R, v1},
-                       {"rho", c.rho, v1}, {"Tp", c.Tp, v1}, {"Cp", c.Cp, v1}, {"m", c.m, v1}, {"I", c.I, v1},
+                       {"rho", c.rho, v1}, {"Tp", c.Tp, v1}, {"Cp", c.Cp, v1}, {"m", c.m, v1}, {"I", c.I, v1}, {"im", c.im, v1}, {"iI", c.iI, v1},
                        {"mg", c.mg, v1}, {"fixed", c.fixed, (size_t)n}, {"Fh", c.Fh, v3}, {"Th", c.Th, v3},
                        {"Hh", c.Hh, v1}, {"Fc", c.Fc, v3}, {"Tc", c.Tc, v3}, {"Fh_prev", c.Fh_prev, v3},
                        {"Th_prev", c.Th_prev, v3}, {"Hh_prev", c.Hh_prev, v1}, {"have_prev", c.have_prev, sizeof(int)},

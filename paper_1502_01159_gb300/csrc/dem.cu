@@ -34,7 +34,7 @@ constexpr int DEM_T = 128;
 constexpr int DEM_MAXNB = 64;
 
 struct DemState {
-    double *X, *U, *W, *Xb, *R, *m, *I, *mg, *Tp, *Cp, *Fh, *Th, *Hh, *Fc, *Tc;
+    double *X, *U, *W, *Xb, *R, *m, *I, *im, *iI, *mg, *Tp, *Cp, *Fh, *Th, *Hh, *Fc, *Tc;
     double *Fhp, *Thp, *Hhp;
     int* have_prev;
     int* adj_new;
@@ -55,7 +55,7 @@ struct DemState {
 struct Pub {
     double x[3];
     float u[3], w[3];
-    float xf[3], pad;
+    float xf[3], rf;  // FP32 position and radius: one 16-byte load for the prefilter
 };
 
 __device__ __forceinline__ void set_error(int* dstat, int detail) {
@@ -293,6 +293,7 @@ __device__ __forceinline__ void drift_s(Priv& P, double dt, Pub& pub) {
         pub.u[a] = (float)P.U[a];
         pub.w[a] = (float)P.W[a];
     }
+    pub.rf = P.Rf;
 }
 
 __device__ __forceinline__ void publish_s(const Priv& P, Pub& pub) {
@@ -302,6 +303,7 @@ __device__ __forceinline__ void publish_s(const Priv& P, Pub& pub) {
         pub.u[a] = (float)P.U[a];
         pub.w[a] = (float)P.W[a];
     }
+    pub.rf = P.Rf;
 }
 
 constexpr int DEM_MAXA = 6;  // neighbours per particle staged in shared memory
@@ -339,8 +341,8 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
         for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
             const int p = base + l;
             Priv& P = prv[l];
-            P.im = 1.0 / S.m[p];
-            P.iI = 1.0 / S.I[p];
+            P.im = S.im[p];
+            P.iI = S.iI[p];
             P.imf = (float)P.im;
             P.iIf = (float)P.iI;
             P.R = S.R[p];
@@ -412,9 +414,10 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                         const int rq = q / per, lq = q - rq * per;
                         const Pub* rp = cl.map_shared_rank(pub, rq) + rb * per + lq;
                         const Priv* rv = cl.map_shared_rank(prv, rq) + lq;
-                        // FP32 prefilter from the published FP32 positions (no FP64 for pairs apart)
-                        const float dxf = rp->xf[0] - me.xf[0], dyf = rp->xf[1] - me.xf[1], dzf = rp->xf[2] - me.xf[2];
-                        const float sf = Rpf + rv->Rf + 1e-3f;
+                        // FP32 prefilter from the published FP32 position and radius (one load)
+                        const float4 pf = *reinterpret_cast<const float4*>(rp->xf);
+                        const float dxf = pf.x - me.xf[0], dyf = pf.y - me.xf[1], dzf = pf.z - me.xf[2];
+                        const float sf = Rpf + pf.w + 1e-3f;
                         float3 Fa = f3(0.f, 0.f, 0.f), Ta = Fa, Tb = Fa, h = Fa;
                         bool contact = false;
                         if (dxf * dxf + dyf * dyf + dzf * dzf < sf * sf) {
@@ -731,6 +734,7 @@ int dem_max_per_cta() { return DEM_MAXPER; }
 static DemState dem_state(Ctx* c) {
     DemState S;
     S.X = c->X, S.U = c->U, S.W = c->W, S.Xb = c->Xb, S.R = c->R, S.m = c->m, S.I = c->I, S.mg = c->mg;
+    S.im = c->im, S.iI = c->iI;
     S.Tp = c->Tp, S.Cp = c->Cp, S.Fh = c->Fh, S.Th = c->Th, S.Hh = c->Hh, S.Fc = c->Fc, S.Tc = c->Tc;
     S.Fhp = c->Fh_prev, S.Thp = c->Th_prev, S.Hhp = c->Hh_prev, S.have_prev = c->have_prev;
     S.adj_new = c->adj_start_new;

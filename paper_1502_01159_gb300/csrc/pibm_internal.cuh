@@ -303,6 +303,7 @@ struct Ctx {
     // particles
     int np;
     double *X, *U, *W, *Xb, *R, *rho, *Tp, *Cp, *m, *I, *mg;
+    double *im, *iI;                 // 1/m, 1/I (computed on the host: no FP64 division on the device)
     uint8_t* fixed;
     double *Fh, *Th, *Hh, *Fc, *Tc;
     double *Fh_prev, *Th_prev, *Hh_prev;  // coupling of the previous time
