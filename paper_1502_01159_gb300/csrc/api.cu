@@ -139,7 +139,11 @@ static pibm_status prime(pibm_ctx* ctx) {
 }
 
 // The launches of one lattice step at parity par, ordered on s0 with the
-// DEM branch forked onto s1 and joined back (s0 may be capturing).
+// DEM branch forked onto s1 and the clear of the other coupling set onto s2,
+// both joined back before the coupling (s0 may be capturing).  The three
+// branches touch disjoint data, so the DEM's latency-bound substeps, the
+// clear and the bandwidth-bound lattice kernel overlap; the step's critical
+// path is max(DEM, lattice) + coupling.
 cudaError_t pibm::record_step(Ctx* cp, int par, int* kernels_out) {
     Ctx& c = *cp;
     cudaError_t e = cudaSuccess;
@@ -149,12 +153,15 @@ cudaError_t pibm::record_step(Ctx* cp, int par, int* kernels_out) {
     chk(cudaStreamWaitEvent(c.s1, c.ev_fork, 0));
     if (c.np > 0) {
         chk(launch_dem(&c, c.s1, c.desc.dem_substeps));  // particles t -> t+1, concurrent, launched first
-        chk(launch_coupling_clear(&c, c.s1, par ^ 1));  // free the other coupling set (read at t-1)
+        chk(cudaStreamWaitEvent(c.s2, c.ev_fork, 0));
+        chk(launch_coupling_clear(&c, c.s2, par ^ 1));  // free the other coupling set (read at t-1)
+        chk(cudaEventRecord(c.ev_join2, c.s2));
         kernels++;
     }
     chk(launch_stream_collide(&c, c.s0, par));        // collide + stream, t -> t+1
     chk(cudaEventRecord(c.ev_join, c.s1));
     chk(cudaStreamWaitEvent(c.s0, c.ev_join, 0));
+    if (c.np > 0) chk(cudaStreamWaitEvent(c.s0, c.ev_join2, 0));
     chk(launch_coupling(&c, c.s0, par ^ 1));         // coupling of time t+1
     kernels += coupling_kernel_count(&c);
     if (c.sg.enabled && c.np > 0) {                  // surrogate Jacobian for the next step's DEM, judged by t+1's coupling
@@ -247,8 +254,10 @@ pibm_status pibm_create(const pibm_desc* d, void* stream, const pibm_allocator* 
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     // the DEM branch is latency-bound on a few SMs: give it the highest priority
     if ((e = cudaStreamCreateWithPriority(&c.s1, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
+        (e = cudaStreamCreateWithPriority(&c.s2, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming)) != cudaSuccess) {
+        (e = cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c.ev_join2, cudaEventDisableTiming)) != cudaSuccess) {
         delete ctx;
         return g_create_error = cudaGetErrorString(e), PIBM_ERR_CUDA;
     }
@@ -292,11 +301,14 @@ pibm_status pibm_destroy(pibm_ctx* ctx) {
     Ctx& c = ctx->c;
     if (c.s0) cudaStreamSynchronize(c.s0);
     if (c.s1) cudaStreamSynchronize(c.s1);
+    if (c.s2) cudaStreamSynchronize(c.s2);
     drop_graphs(c);
     dfree_group(ctx, -1);
     if (c.ev_fork) cudaEventDestroy(c.ev_fork);
     if (c.ev_join) cudaEventDestroy(c.ev_join);
+    if (c.ev_join2) cudaEventDestroy(c.ev_join2);
     if (c.s1) cudaStreamDestroy(c.s1);
+    if (c.s2) cudaStreamDestroy(c.s2);
     if (c.own_s0 && c.s0) cudaStreamDestroy(c.s0);
     delete ctx;
     return PIBM_OK;
@@ -442,14 +454,14 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     c.adj_cap = 2 * C.cap;
     update_geo(c);
 
-    size_t v3 = sizeof(double) * 3 * (n + 1), v1 = sizeof(double) * (n + 1);
+    size_t v3 = sizeof(double) * 3 * (n + 1), v1 = sizeof(double) * (n + 1), v3f = sizeof(float) * 3 * (n + 1);
     auto A = [&](size_t b) { return dalloc(ctx, b, GRP_PARTICLES); };
     c.X = (double*)A(v3), c.U = (double*)A(v3), c.W = (double*)A(v3), c.Xb = (double*)A(v3);
     c.R = (double*)A(v1), c.rho = (double*)A(v1), c.Tp = (double*)A(v1), c.Cp = (double*)A(v1);
     c.m = (double*)A(v1), c.I = (double*)A(v1), c.mg = (double*)A(v1);
     c.im = (double*)A(v1), c.iI = (double*)A(v1);
     c.fixed = (uint8_t*)A(n + 1);
-    c.Fh = (double*)A(v3), c.Th = (double*)A(v3), c.Hh = (double*)A(v1), c.Fc = (double*)A(v3), c.Tc = (double*)A(v3);
+    c.Fh = (double*)A(v3), c.Th = (double*)A(v3), c.Hh = (double*)A(v1), c.Fc = (float*)A(v3f), c.Tc = (float*)A(v3f);
     c.Fh_prev = (double*)A(v3), c.Th_prev = (double*)A(v3), c.Hh_prev = (double*)A(v1);
     c.have_prev = (int*)A(sizeof(int) * 2);
     c.adj_start_new = (int*)A(sizeof(int) * (n + 2));
@@ -689,11 +701,14 @@ pibm_status pibm_step_timed(pibm_ctx* ctx, double* ms) {
     chk(cudaStreamWaitEvent(c.s1, ev[0], 0));
     chk(cudaEventRecord(ev[2], c.s1));
     chk(launch_dem(&c, c.s1, c.desc.dem_substeps));
-    chk(launch_coupling_clear(&c, c.s1, par ^ 1));
     chk(cudaEventRecord(ev[3], c.s1));
+    chk(cudaStreamWaitEvent(c.s2, ev[0], 0));
+    chk(launch_coupling_clear(&c, c.s2, par ^ 1));
+    chk(cudaEventRecord(ev[6], c.s2));
     chk(launch_stream_collide(&c, c.s0, par));
     chk(cudaEventRecord(ev[1], c.s0));
     chk(cudaStreamWaitEvent(c.s0, ev[3], 0));
+    chk(cudaStreamWaitEvent(c.s0, ev[6], 0));
     chk(cudaEventRecord(ev[4], c.s0));
     chk(launch_coupling(&c, c.s0, par ^ 1));
     chk(cudaEventRecord(ev[5], c.s0));
@@ -883,7 +898,7 @@ static std::vector<BufRef> state_buffers(Ctx& c) {
         BufRef pv[] = {{"X", c.X, v3}, {"U", c.U, v3}, {"W", c.W, v3}, {"Xb", c.Xb, v3}, {"R", c.R, v1},
                        {"rho", c.rho, v1}, {"Tp", c.Tp, v1}, {"Cp", c.Cp, v1}, {"m", c.m, v1}, {"I", c.I, v1}, {"im", c.im, v1}, {"iI", c.iI, v1},
                        {"mg", c.mg, v1}, {"fixed", c.fixed, (size_t)n}, {"Fh", c.Fh, v3}, {"Th", c.Th, v3},
-                       {"Hh", c.Hh, v1}, {"Fc", c.Fc, v3}, {"Tc", c.Tc, v3}, {"Fh_prev", c.Fh_prev, v3},
+                       {"Hh", c.Hh, v1}, {"Fc", c.Fc, sizeof(float) * 3 * n}, {"Tc", c.Tc, sizeof(float) * 3 * n}, {"Fh_prev", c.Fh_prev, v3},
                        {"Th_prev", c.Th_prev, v3}, {"Hh_prev", c.Hh_prev, v1}, {"have_prev", c.have_prev, sizeof(int)},
                        {"box0", c.box[0], sizeof(int) * 6 * n}, {"box1", c.box[1], sizeof(int) * 6 * n},
                        {"wall_ft", c.wall_ft, sizeof(float) * 18 * n},

@@ -33,18 +33,21 @@ __device__ __forceinline__ double eps_of(double x, double y, double z, const dou
     return e > 1.0 ? 1.0 : e;
 }
 
-__device__ __forceinline__ void footprint_box(const Geo& G, int dim, const double* X, double R, int* lo, int* hi) {
-    int n[3] = {G.nx, G.ny, G.nz};
-    for (int a = 0; a < 3; a++) {
-        if (a < dim) {
-            lo[a] = (int)ceil(X[a] - R - 0.5);
-            hi[a] = (int)floor(X[a] + R + 0.5);
-            if (lo[a] < 0) lo[a] = 0;
-            if (hi[a] > n[a] - 1) hi[a] = n[a] - 1;
-        } else {
-            lo[a] = hi[a] = 0;
-        }
-    }
+// One axis of the footprint box (ceil(X - R - 1/2), floor(X + R + 1/2),
+// clamped to the lattice) and the base node floor(X), exactly as the FP64
+// expressions give them.  FP64 issues slowly on this GPU, so the integers come
+// from FP32 estimates (error below 2.5e-7 (|X| + R + 1)) whenever these lie
+// more than 1e-6 (|X| + R + 1) from an integer, and from FP64 otherwise.
+__device__ __forceinline__ void axis_box(double X, float xf, double R, float Rf, int n, int* lo, int* hi, int* base) {
+    const float g = 1e-6f * (fabsf(xf) + Rf + 1.f);
+    const float tl = xf - (Rf + 0.5f), th = xf + (Rf + 0.5f);
+    float cl = ceilf(tl), fh = floorf(th), fb = floorf(xf);
+    if (cl - tl < g || tl - (cl - 1.f) < g) cl = (float)ceil(X - R - 0.5);
+    if (th - fh < g || (fh + 1.f) - th < g) fh = (float)floor(X + R + 0.5);
+    if (xf - fb < g || (fb + 1.f) - xf < g) fb = (float)floor(X);
+    *lo = max((int)cl, 0);
+    *hi = min((int)fh, n - 1);
+    *base = (int)fb;
 }
 
 template <typename V>
@@ -109,7 +112,7 @@ constexpr float EPS_GUARD = 1e-5f;  // FP32 decisions within this margin are re-
 // dT with d = r - X_p, u = j / rho the raw velocity, dT = T0 - T_ref) into
 // fsum[p][17].
 template <int D, typename S, bool FEAT>
-__global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __restrict__ f, const S* __restrict__ g,
+__global__ void __launch_bounds__(CP_THREADS, (Lat<D>::dim == 2 && !FEAT) ? 4 : (FEAT ? 2 : 3)) k_footprint(Geo G, const S* __restrict__ f, const S* __restrict__ g,
                                                           typename Store<S>::V4* __restrict__ mk,
                                                           const double* __restrict__ X, const double* __restrict__ U,
                                                           const double* __restrict__ W, const double* __restrict__ Rr,
@@ -124,26 +127,40 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
     __shared__ double red[FEAT ? 24 : 7][CP_THREADS / 32];
     float fa[FEAT ? 17 : 1];
     for (int k = 0; k < (FEAT ? 17 : 1); k++) fa[k] = 0.f;
-    // per-particle constants, computed once by thread 0 (FP64 is slow on this GPU)
+    // per-particle constants, computed once by the first warp with one value per
+    // lane, so that each FP64 operation (slow on this GPU) is one warp instruction:
+    // lanes 0-2 the position axes, 3-5 U, 6-8 omega, 9 T_p - T_ref, 10 2 kappa, 11 R
     __shared__ int s_box[6], s_base[3];
     __shared__ float s_cf[3], s_U[3], s_W[3], s_misc[3];
     const int p = blockIdx.x;
     const double Xp[3] = {X[3 * p], X[3 * p + 1], X[3 * p + 2]};
     const double Rp = Rr[p];
-    if (threadIdx.x == 0) {
-        int lo[3], hi[3];
-        footprint_box(G, Lat<D>::dim, Xp, Rp, lo, hi);
-        for (int a = 0; a < 3; a++) {
-            s_box[a] = lo[a];
-            s_box[3 + a] = hi[a];
-            s_base[a] = (a < Lat<D>::dim) ? (int)floor(Xp[a]) : 0;
-            s_cf[a] = (float)(Xp[a] - s_base[a]);
-            s_U[a] = (float)U[3 * p + a];
-            s_W[a] = (float)W[3 * p + a];
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double v = 0.0;
+        if (lane < 3) v = Xp[lane];
+        else if (lane < 6) v = U[3 * p + lane - 3];
+        else if (lane < 9) v = W[3 * p + lane - 6];
+        else if (lane == 9) v = Tp[p] - Tref;
+        else if (lane == 10) v = 2.0 * kappa;
+        else if (lane == 11) v = Rp;
+        const float vf = (float)v;
+        const float Rf = __shfl_sync(0xffffffffu, vf, 11);
+        if (lane < 3) {
+            int lo = 0, hi = 0, base = 0;
+            const int n = lane == 0 ? G.nx : (lane == 1 ? G.ny : G.nz);
+            if (lane < Lat<D>::dim) axis_box(v, vf, Rp, Rf, n, &lo, &hi, &base);
+            s_box[lane] = lo;
+            s_box[3 + lane] = hi;
+            s_base[lane] = base;
+            s_cf[lane] = (float)(v - (double)base);
+        } else if (lane < 6) {
+            s_U[lane - 3] = vf;
+        } else if (lane < 9) {
+            s_W[lane - 6] = vf;
+        } else if (lane < 12) {
+            s_misc[lane == 9 ? 0 : (lane == 10 ? 1 : 2)] = vf;
         }
-        s_misc[0] = (float)(Tp[p] - Tref);
-        s_misc[1] = (float)(2.0 * kappa);
-        s_misc[2] = (float)Rp;
     }
     const int a0 = adj_start[p];
     int nnb = adj_start[p + 1] - a0;
@@ -151,15 +168,15 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
     __syncthreads();
     const int base[3] = {s_base[0], s_base[1], s_base[2]};
     const float cf[3] = {s_cf[0], s_cf[1], s_cf[2]};
-    for (int k = threadIdx.x; k < nnb; k += blockDim.x) {
-        int q = adj_nb[a0 + k];
-        sh_id[k] = q;
-        for (int a = 0; a < 3; a++) {
-            sh_nb[k][a] = X[3 * q + a];
-            sh_nbf[k][a] = (float)(X[3 * q + a] - base[a]);  // neighbour centre relative to p's base node
-        }
-        sh_nb[k][3] = Rr[q];
-        sh_nbf[k][3] = (float)Rr[q];
+    // neighbour centres relative to p's base node and radii: one (neighbour, axis
+    // or radius) per thread
+    for (int t = threadIdx.x; t < 4 * nnb; t += blockDim.x) {
+        const int k = t >> 2, a = t & 3;
+        const int q = adj_nb[a0 + k];
+        if (a == 0) sh_id[k] = q;
+        const double v = a < 3 ? X[3 * q + a] : Rr[q];
+        sh_nb[k][a] = v;
+        sh_nbf[k][a] = (float)(a < 3 ? v - (double)base[a] : v);
     }
     __syncthreads();
     const int lo[3] = {s_box[0], s_box[1], s_box[2]}, hi[3] = {s_box[3], s_box[4], s_box[5]};
@@ -263,21 +280,26 @@ __global__ void __launch_bounds__(CP_THREADS) k_footprint(Geo G, const S* __rest
             fa[16] += (float)dT;
         }
     }
-    // warp sums in FP32 (32 partials), the per-particle total over the warps in FP64
+    // warp sums in FP32 (32 partials, a butterfly: every lane gets the sum); lane
+    // a keeps quantity a and the warp converts them all in one FP64 instruction;
+    // the per-particle total over the warps is FP64
+    const int lane = threadIdx.x & 31;
+    float mine = 0.f;
 #pragma unroll
     for (int a = 0; a < 7; a++) {
         float v = acc[a];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = (double)v;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == a) mine = v;
     }
     if constexpr (FEAT) {
 #pragma unroll
         for (int a = 0; a < 17; a++) {
             float v = fa[a];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if ((threadIdx.x & 31) == 0) red[7 + a][threadIdx.x >> 5] = (double)v;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 7 + a) mine = v;
         }
     }
+    if (lane < (FEAT ? 24 : 7)) red[lane][threadIdx.x >> 5] = (double)mine;
     __syncthreads();
     if (threadIdx.x < (FEAT ? 24 : 7)) {
         double v = 0;
@@ -301,24 +323,23 @@ __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __re
     V* tile = reinterpret_cast<V*>(sm_raw);
     using T = decltype(V().x);
     const int p = blockIdx.x;
-    __shared__ int s_b[12];  // output box lo/hi, staged box lo/hi, computed once
-    if (threadIdx.x == 0) {
-        const double Xp[3] = {X[3 * p], X[3 * p + 1], X[3 * p + 2]};
-        int lo[3], hi[3];
-        footprint_box(G, Lat<D>::dim, Xp, Rr[p], lo, hi);
-        int n[3] = {G.nx, G.ny, G.nz};
-        for (int a = 0; a < 3; a++) {
-            int ilo = lo[a], ihi = hi[a];
-            if (a < Lat<D>::dim) {
-                lo[a] = max(lo[a] - 1, 0);
-                hi[a] = min(hi[a] + 1, n[a] - 1);
-                ilo = max(lo[a] - 1, 0);
-                ihi = min(hi[a] + 1, n[a] - 1);
-            }
-            s_b[a] = lo[a], s_b[3 + a] = hi[a], s_b[6 + a] = ilo, s_b[9 + a] = ihi;
-            box[6 * p + a] = lo[a];
-            box[6 * p + 3 + a] = hi[a];
+    __shared__ int s_b[12];  // output box lo/hi, staged box lo/hi, computed once (lane a: axis a)
+    if (threadIdx.x < 3) {
+        const int a = threadIdx.x;
+        const double Xa = X[3 * p + a], R = Rr[p];
+        const int n = a == 0 ? G.nx : (a == 1 ? G.ny : G.nz);
+        int lo = 0, hi = 0, base = 0;
+        if (a < Lat<D>::dim) axis_box(Xa, (float)Xa, R, (float)R, n, &lo, &hi, &base);
+        int ilo = lo, ihi = hi;
+        if (a < Lat<D>::dim) {
+            lo = max(lo - 1, 0);
+            hi = min(hi + 1, n - 1);
+            ilo = max(lo - 1, 0);
+            ihi = min(hi + 1, n - 1);
         }
+        s_b[a] = lo, s_b[3 + a] = hi, s_b[6 + a] = ilo, s_b[9 + a] = ihi;
+        box[6 * p + a] = lo;
+        box[6 * p + 3 + a] = hi;
     }
     __syncthreads();
     const int lo[3] = {s_b[0], s_b[1], s_b[2]}, hi[3] = {s_b[3], s_b[4], s_b[5]};

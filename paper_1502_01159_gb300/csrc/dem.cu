@@ -34,7 +34,8 @@ constexpr int DEM_T = 128;
 constexpr int DEM_MAXNB = 64;
 
 struct DemState {
-    double *X, *U, *W, *Xb, *R, *m, *I, *im, *iI, *mg, *Tp, *Cp, *Fh, *Th, *Hh, *Fc, *Tc;
+    double *X, *U, *W, *Xb, *R, *m, *I, *im, *iI, *mg, *Tp, *Cp, *Fh, *Th, *Hh;
+    float *Fc, *Tc;  // contact force and torque of the last evaluation (FP32, as the substeps form them)
     double *Fhp, *Thp, *Hhp;
     int* have_prev;
     int* adj_new;
@@ -128,27 +129,25 @@ __device__ __forceinline__ float3 tangential(const DemCfg& C, float3& h, float3 
     return f3(h.x - C.gt * vt.x, h.y - C.gt * vt.y, h.z - C.gt * vt.z);
 }
 
-// Pair (a < b) in canonical order: force on a, torques on a and b, new
-// history.  Both partners call this with the same inputs and get the same bits.
-__device__ __forceinline__ void pair_force(const DemCfg& C, const Pub& A, const Pub& B, double Ra, double Rb,
-                                           float3& h, float dtf, float3& Fa, float3& Ta, float3& Tb) {
-    double d2 = dist2(A.x, B.x);
-    double S = Ra + Rb;
-    if (!(d2 < S * S)) {
-        h = f3(0.f, 0.f, 0.f);
-        Fa = Ta = Tb = f3(0.f, 0.f, 0.f);
-        return;
-    }
+// Pair (a < b) in canonical order, in contact (d2 < SS): force on a, torques
+// on a and b, new history.  d = X_b - X_a and d2 = |d|^2, SS = (R_a + R_b)^2
+// come from the caller's exact FP64 contact test; the only FP64 operation left
+// is the overlap S^2 - d^2, which cancels.  Both partners call this with the
+// same inputs and get the same bits.
+__device__ __forceinline__ void pair_force(const DemCfg& C, const Pub& A, const Pub& B, const double* d, double d2,
+                                           double SS, float Raf, float Rbf, float3& h, float dtf, float3& Fa, float3& Ta,
+                                           float3& Tb) {
     float distf = sqrtf((float)d2);
-    float delta = (float)(S * S - d2) / ((float)S + distf);
-    float3 nn = f3((float)(B.x[0] - A.x[0]) / distf, (float)(B.x[1] - A.x[1]) / distf, (float)(B.x[2] - A.x[2]) / distf);
-    float ai = (float)Ra - 0.5f * delta, aj = (float)Rb - 0.5f * delta;
+    const float Sf = Raf + Rbf;
+    float delta = (float)(SS - d2) / (Sf + distf);
+    float3 nn = f3((float)d[0] / distf, (float)d[1] / distf, (float)d[2] / distf);
+    float ai = Raf - 0.5f * delta, aj = Rbf - 0.5f * delta;
     float3 wi = cross3(f3(A.w[0], A.w[1], A.w[2]), f3(ai * nn.x, ai * nn.y, ai * nn.z));
     float3 wj = cross3(f3(B.w[0], B.w[1], B.w[2]), f3(-aj * nn.x, -aj * nn.y, -aj * nn.z));
     float3 vr = f3(A.u[0] + wi.x - B.u[0] - wj.x, A.u[1] + wi.y - B.u[1] - wj.y, A.u[2] + wi.z - B.u[2] - wj.z);
     float vn = vr.x * nn.x + vr.y * nn.y + vr.z * nn.z;
     float3 vt = f3(vr.x - vn * nn.x, vr.y - vn * nn.y, vr.z - vn * nn.z);
-    float Rstar = (float)(Ra * Rb / S), kt_eff;
+    float Rstar = Raf * Rbf / Sf, kt_eff;
     float Fn = normal_law(C, delta, vn, Rstar, &kt_eff);
     float3 Ft = tangential(C, h, nn, vt, kt_eff, Fn, dtf);
     Ta = cross3(f3(ai * nn.x, ai * nn.y, ai * nn.z), Ft);
@@ -255,43 +254,61 @@ struct Priv {
 // d(hydrodynamic torque)/domega; the held hydrodynamic load is then corrected
 // by J_FU (U - U0) and J_TW (omega - omega0), with U0, omega0 the velocities
 // at the start of the lattice step.
-__device__ __forceinline__ void kick_s(Priv& P, double h, int dim, const float* J, const double* U0, const double* W0) {
+//
+// FP64 on this GPU issues at a small fraction of the FP32 rate, and every
+// warp-wide FP64 instruction holds its scheduler for many cycles, so the
+// substep does FP64 work only where the result needs it: the velocity and
+// position sums.  The increment h (F_c/m + a_ext) is formed in FP32 (relative
+// error ~1e-7 of a per-substep change) and added to the FP64 velocity in one
+// operation.  In 2-D only U_x, U_y and omega_z can change: U_z, omega_x and
+// omega_y are zero from the load on, and their FP64 operations are skipped.
+template <int D>
+__device__ __forceinline__ void kick_s(Priv& P, double h, float hf, const float* J, const double* U0, const double* W0) {
+    constexpr int NU = D == 3 ? 3 : 2;  // velocity components that can change
+    constexpr int W_LO = D == 3 ? 0 : 2;  // first spin component that can change
+    // held hydrodynamic load corrected by J_FU (U - U0), J_TW (omega - omega0),
+    // with the velocities before this kick
     double dF[3] = {0.0, 0.0, 0.0}, dT[3] = {0.0, 0.0, 0.0};
     if (J) {
         double du[3], dw[3];
         for (int b = 0; b < 3; b++) du[b] = P.U[b] - U0[b], dw[b] = P.W[b] - W0[b];
-        for (int a = 0; a < 3; a++)
-            for (int b = 0; b < 3; b++) {
-                dF[a] += (double)J[3 * a + b] * du[b];
-                dT[a] += (double)J[9 + 3 * a + b] * dw[b];
-            }
+        for (int a = 0; a < NU; a++)
+            for (int b = 0; b < NU; b++) dF[a] += (double)J[3 * a + b] * du[b];
+        for (int a = W_LO; a < 3; a++)
+            for (int b = W_LO; b < 3; b++) dT[a] += (double)J[9 + 3 * a + b] * dw[b];
     }
-    // the increment h (F_c/m + a_ext) is formed in FP32 (relative error ~1e-7 of
-    // a per-substep change) and added to the FP64 velocity in one operation:
-    // FP64 latency is long on this GPU and these chains are the substep's tail
-    const float hf = (float)h;
-    for (int a = 0; a < 3; a++) {
-        P.U[a] += (double)(hf * (P.Fc[a] * P.imf + P.a[a]));
-        P.W[a] += (double)(hf * (P.Tc[a] * P.iIf + P.al[a]));
-    }
-    if (J)
-        for (int a = 0; a < 3; a++) {
-            P.U[a] += h * dF[a] * P.im;
-            P.W[a] += h * dT[a] * P.iI;
-        }
-    if (dim == 2) {
-        P.U[2] = 0.0;
-        P.W[0] = P.W[1] = 0.0;
+    for (int a = 0; a < NU; a++) P.U[a] += (double)(hf * (P.Fc[a] * P.imf + P.a[a]));
+    for (int a = W_LO; a < 3; a++) P.W[a] += (double)(hf * (P.Tc[a] * P.iIf + P.al[a]));
+    if (J) {
+        for (int a = 0; a < NU; a++) P.U[a] += h * dF[a] * P.im;
+        for (int a = W_LO; a < 3; a++) P.W[a] += h * dT[a] * P.iI;
     }
 }
 
+// drift and publication of the fields that change (the others were published
+// into both buffers at the load)
+template <int D>
 __device__ __forceinline__ void drift_s(Priv& P, double dt, Pub& pub) {
-    for (int a = 0; a < 3; a++) {
+    constexpr int NU = D == 3 ? 3 : 2;
+    constexpr int W_LO = D == 3 ? 0 : 2;
+    for (int a = 0; a < NU; a++) {
         P.X[a] += dt * P.U[a];
         pub.x[a] = P.X[a];
         pub.xf[a] = (float)P.X[a];
         pub.u[a] = (float)P.U[a];
-        pub.w[a] = (float)P.W[a];
+    }
+    for (int a = W_LO; a < 3; a++) pub.w[a] = (float)P.W[a];
+}
+
+// the published fields a free particle's substeps never change: in 2-D the
+// out-of-plane position, velocity and in-plane spin; the radius
+template <int D>
+__device__ __forceinline__ void publish_const(const Priv& P, Pub& pub) {
+    if (D == 2) {
+        pub.x[2] = P.X[2];
+        pub.xf[2] = (float)P.X[2];
+        pub.u[2] = 0.f;
+        pub.w[0] = pub.w[1] = 0.f;
     }
     pub.rf = P.Rf;
 }
@@ -337,42 +354,73 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
     const bool useJ = C.J != nullptr && __ldcg(C.J_on) != 0;
     if (advance) {
         const int hp = __ldcg(S.have_prev);
-        // load the private state once; external accelerations are constant over the lattice step
+        // load the private state once; external accelerations are constant over the lattice step.
+        // Every global load of a particle is issued before the first store: the stores go to
+        // shared memory through pointers the compiler cannot separate from the global ones, so
+        // interleaving them would expose one load latency per value.
         for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
             const int p = base + l;
-            Priv& P = prv[l];
-            P.im = S.im[p];
-            P.iI = S.iI[p];
-            P.imf = (float)P.im;
-            P.iIf = (float)P.iI;
-            P.R = S.R[p];
-            P.Rf = (float)P.R;
-            P.fixed = S.fixed[p];
-            P.wall_mask = 0;
-            for (int f = 0; f < 2 * D; f++) {
-                const float* w = S.wall_ft + 3 * (6 * p + f);
-                if (w[0] != 0.f || w[1] != 0.f || w[2] != 0.f) P.wall_mask |= 1 << f;
-            }
-            const double mg = S.mg[p];
+            double x[3], u[3], w[3], fh[3], th[3], fhp[3], thp[3];
+            float fc[3], tc[3];
             for (int a = 0; a < 3; a++) {
-                P.X[a] = S.X[3 * p + a];
-                P.U[a] = S.U[3 * p + a];
-                P.W[a] = S.W[3 * p + a];
-                P.Fc[a] = (float)S.Fc[3 * p + a];
-                P.Tc[a] = (float)S.Tc[3 * p + a];
-                P.a[a] = (float)((hydro(S.Fh, S.Fhp, 3 * p + a, hp) + mg * C.g[a]) * P.im);
-                P.al[a] = (float)(hydro(S.Th, S.Thp, 3 * p + a, hp) * P.iI);
+                x[a] = __ldcg(S.X + 3 * p + a);
+                u[a] = __ldcg(S.U + 3 * p + a);
+                w[a] = __ldcg(S.W + 3 * p + a);
+                fc[a] = __ldcg(S.Fc + 3 * p + a);
+                tc[a] = __ldcg(S.Tc + 3 * p + a);
+                fh[a] = __ldcg(S.Fh + 3 * p + a);
+                th[a] = __ldcg(S.Th + 3 * p + a);
+                fhp[a] = __ldcg(S.Fhp + 3 * p + a);
+                thp[a] = __ldcg(S.Thp + 3 * p + a);
             }
-            if (!P.fixed) {
-                kick_s(P, 0.5 * dt, D, useJ ? C.J + 18 * p : nullptr, S.U + 3 * p, S.W + 3 * p);
-                drift_s(P, dt, pub[l]);
+            const double im = __ldcg(S.im + p), iI = __ldcg(S.iI + p), R = __ldcg(S.R + p), mg = __ldcg(S.mg + p);
+            const int fixed = S.fixed[p];
+            float wft[6][3];
+            for (int f = 0; f < 2 * D; f++)
+                for (int a = 0; a < 3; a++) wft[f][a] = __ldcg(S.wall_ft + 3 * (6 * p + f) + a);
+            // the adjacency is fixed during the lattice step: stage it (up to DEM_MAXA entries)
+            const int e0 = __ldcg(S.adj_start + p), ne = __ldcg(S.adj_start + p + 1) - e0;
+            int2 ad[DEM_MAXA];
+            for (int e = 0; e < DEM_MAXA; e++)
+                ad[e] = e < ne ? make_int2(__ldcg(S.adj_nb + e0 + e), __ldcg(S.adj_k + e0 + e)) : make_int2(0, 0);
+            Priv& P = prv[l];
+            P.im = im;
+            P.iI = iI;
+            P.imf = (float)im;
+            P.iIf = (float)iI;
+            P.R = R;
+            P.Rf = (float)R;
+            P.fixed = fixed;
+            P.wall_mask = 0;
+            for (int f = 0; f < 2 * D; f++)
+                if (wft[f][0] != 0.f || wft[f][1] != 0.f || wft[f][2] != 0.f) P.wall_mask |= 1 << f;
+            for (int a = 0; a < 3; a++) {
+                P.X[a] = x[a];
+                P.U[a] = u[a];
+                P.W[a] = w[a];
+                P.Fc[a] = fc[a];
+                P.Tc[a] = tc[a];
+                P.a[a] = 0.f;
+                P.al[a] = 0.f;
+            }
+            if (D == 2) {  // the components a 2-D particle cannot have
+                P.U[2] = 0.0;
+                P.W[0] = P.W[1] = 0.0;
+            }
+            for (int a = 0; a < (D == 3 ? 3 : 2); a++)
+                P.a[a] = (float)(((hp ? 0.5 * (fh[a] + fhp[a]) : fh[a]) + mg * C.g[a]) * im);
+            for (int a = (D == 3 ? 0 : 2); a < 3; a++) P.al[a] = (float)((hp ? 0.5 * (th[a] + thp[a]) : th[a]) * iI);
+            P.nadj = ne;
+            for (int e = 0; e < ne && e < DEM_MAXA; e++) adj[l * DEM_MAXA + e] = ad[e];
+            // both buffers get every field; the substeps rewrite only those that change
+            if (!fixed) {
+                kick_s<D>(P, 0.5 * dt, (float)(0.5 * dt), useJ ? C.J + 18 * p : nullptr, S.U + 3 * p, S.W + 3 * p);
+                publish_const<D>(P, pub[l]);
+                drift_s<D>(P, dt, pub[l]);
             } else {
                 publish_s(P, pub[l]);
             }
-            // the adjacency is fixed during the lattice step: stage it (up to DEM_MAXA entries)
-            const int e0 = S.adj_start[p], ne = S.adj_start[p + 1] - e0;
-            P.nadj = ne;
-            for (int e = 0; e < ne && e < DEM_MAXA; e++) adj[l * DEM_MAXA + e] = make_int2(S.adj_nb[e0 + e], S.adj_k[e0 + e]);
+            pub[per + l] = pub[l];
         }
         cl.sync();
         for (int sub = 0; sub < nsub; sub++) {
@@ -425,13 +473,18 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                             const double Rq = rv->R;
                             const Pub& A = first ? me : other;
                             const Pub& B = first ? other : me;
-                            const double Ra = first ? Rp : Rq, Rb = first ? Rq : Rp;
-                            double d2 = dist2(A.x, B.x), Ssum = Ra + Rb;
-                            contact = d2 < Ssum * Ssum;  // the exact FP64 contact test
+                            const double Ssum = first ? Rp + Rq : Rq + Rp;
+                            // the exact FP64 contact test, in the oracle's operation order
+                            const double d[3] = {__dsub_rn(B.x[0], A.x[0]), __dsub_rn(B.x[1], A.x[1]),
+                                                 __dsub_rn(B.x[2], A.x[2])};
+                            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])),
+                                                        __dmul_rn(d[2], d[2]));
+                            const double SS = Ssum * Ssum;
+                            contact = d2 < SS;
                             if (contact) {
                                 const float4 hv = __ldcg(hist_old + k);
                                 if (__float_as_int(hv.w) == gsub - 1) h = f3(hv.x, hv.y, hv.z);
-                                pair_force(C, A, B, Ra, Rb, h, dtf, Fa, Ta, Tb);
+                                pair_force(C, A, B, d, d2, SS, first ? Rpf : pf.w, first ? pf.w : Rpf, h, dtf, Fa, Ta, Tb);
                             }
                         }
                         if (first) {
@@ -462,16 +515,13 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                     P.Fc[a] = F[a];
                     P.Tc[a] = T[a];
                 }
-                if (P.fixed) {
-                    publish_s(P, pub[(rb ^ 1) * per + l]);
-                    continue;
-                }
+                if (P.fixed) continue;  // published into both buffers at the load
                 const float* Jp = useJ ? C.J + 18 * p : nullptr;
                 if (sub + 1 < nsub) {  // closing half kick of this substep + opening half kick of the next
-                    kick_s(P, dt, D, Jp, S.U + 3 * p, S.W + 3 * p);
-                    drift_s(P, dt, pub[(rb ^ 1) * per + l]);
+                    kick_s<D>(P, dt, dtf, Jp, S.U + 3 * p, S.W + 3 * p);
+                    drift_s<D>(P, dt, pub[(rb ^ 1) * per + l]);
                 } else {
-                    kick_s(P, 0.5 * dt, D, Jp, S.U + 3 * p, S.W + 3 * p);
+                    kick_s<D>(P, 0.5 * dt, (float)(0.5 * dt), Jp, S.U + 3 * p, S.W + 3 * p);
                 }
             }
             cl.sync();
@@ -485,7 +535,16 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
         for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
             const int p = base + l;
             const Priv& P = prv[l];
-            if (S.Cp[p] > 0.0) S.Tp[p] -= hydro(S.Hh, S.Hhp, p, hp) / S.Cp[p];
+            // loads first (the stores below may alias them as far as the compiler knows)
+            const double cp = __ldcg(S.Cp + p), tp = __ldcg(S.Tp + p), hh = __ldcg(S.Hh + p);
+            const double hhp = hp ? __ldcg(S.Hhp + p) : 0.0;
+            double fh[3], th[3], xb[3];
+            for (int a = 0; a < 3; a++) {
+                fh[a] = __ldcg(S.Fh + 3 * p + a);
+                th[a] = __ldcg(S.Th + 3 * p + a);
+                xb[a] = __ldcg(S.Xb + 3 * p + a);
+            }
+            if (cp > 0.0) S.Tp[p] = tp - (hp ? 0.5 * (hh + hhp) : hh) / cp;
             double d2 = 0;
             for (int a = 0; a < 3; a++) {
                 S.X[3 * p + a] = P.X[a];
@@ -493,12 +552,14 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 S.W[3 * p + a] = P.W[a];
                 S.Fc[3 * p + a] = P.Fc[a];
                 S.Tc[3 * p + a] = P.Tc[a];
-                S.Fhp[3 * p + a] = S.Fh[3 * p + a];
-                S.Thp[3 * p + a] = S.Th[3 * p + a];
-                double dd = P.X[a] - S.Xb[3 * p + a];
+                S.Fhp[3 * p + a] = fh[a];
+                S.Thp[3 * p + a] = th[a];
+            }
+            for (int a = 0; a < (D == 3 ? 3 : 2); a++) {  // a 2-D particle does not move out of plane
+                double dd = P.X[a] - xb[a];
                 d2 += dd * dd;
             }
-            S.Hhp[p] = S.Hh[p];
+            S.Hhp[p] = hh;
             if (d2 > thr2) moved = 1;
             if (d2 > err2) set_error(S.dstat, 2);
         }

@@ -283,7 +283,8 @@ struct Ctx {
 
     cudaStream_t s0;  // caller's stream
     cudaStream_t s1;  // internal stream for the DEM branch
-    cudaEvent_t ev_fork, ev_join;
+    cudaStream_t s2;  // internal stream for the clear of the previous coupling set
+    cudaEvent_t ev_fork, ev_join, ev_join2;
     pibm_allocator alloc;
     int own_s0;  // 1 if the library created s0
 
@@ -305,7 +306,8 @@ struct Ctx {
     double *X, *U, *W, *Xb, *R, *rho, *Tp, *Cp, *m, *I, *mg;
     double *im, *iI;                 // 1/m, 1/I (computed on the host: no FP64 division on the device)
     uint8_t* fixed;
-    double *Fh, *Th, *Hh, *Fc, *Tc;
+    double *Fh, *Th, *Hh;
+    float *Fc, *Tc;  // contact force / torque of the last DEM evaluation (FP32, as the substeps form them)
     double *Fh_prev, *Th_prev, *Hh_prev;  // coupling of the previous time
     int* have_prev;   // device int: 1 once a previous coupling exists
     int* adj_start_new;  // scratch for the adjacency offsets of a rebuild
