@@ -508,20 +508,54 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                         F[a] += __shfl_xor_sync(0xffffffffu, F[a], 2);
                         T[a] += __shfl_xor_sync(0xffffffffu, T[a], 2);
                     }
-                if (!active || sl != 0) continue;
+                if (!active) continue;
                 const int p = base + l;
                 Priv& P = prv[l];
-                for (int a = 0; a < 3; a++) {
-                    P.Fc[a] = F[a];
-                    P.Tc[a] = T[a];
-                }
+                if (sl == 0)
+                    for (int a = 0; a < 3; a++) {
+                        P.Fc[a] = F[a];
+                        P.Tc[a] = T[a];
+                    }
                 if (P.fixed) continue;  // published into both buffers at the load
-                const float* Jp = useJ ? C.J + 18 * p : nullptr;
-                if (sub + 1 < nsub) {  // closing half kick of this substep + opening half kick of the next
-                    kick_s<D>(P, dt, dtf, Jp, S.U + 3 * p, S.W + 3 * p);
-                    drift_s<D>(P, dt, pub[(rb ^ 1) * per + l]);
-                } else {
-                    kick_s<D>(P, 0.5 * dt, (float)(0.5 * dt), Jp, S.U + 3 * p, S.W + 3 * p);
+                const bool last = sub + 1 == nsub;  // closing half kick only; else also the next opening one
+                if (useJ) {  // the learned Jacobian couples the components: one thread per particle
+                    if (sl != 0) continue;
+                    const float* Jp = C.J + 18 * p;
+                    if (!last) {
+                        kick_s<D>(P, dt, dtf, Jp, S.U + 3 * p, S.W + 3 * p);
+                        drift_s<D>(P, dt, pub[(rb ^ 1) * per + l]);
+                    } else {
+                        kick_s<D>(P, 0.5 * dt, (float)(0.5 * dt), Jp, S.U + 3 * p, S.W + 3 * p);
+                    }
+                    continue;
+                }
+                // one velocity component per thread of the particle: the same operations as
+                // kick_s and drift_s, with the FP64 chain split over the tpp threads (2-D: U_x,
+                // U_y, omega_z; 3-D: U then omega)
+                const float hf = last ? (float)(0.5 * dt) : dtf;
+                Pub& out = pub[(rb ^ 1) * per + l];
+                constexpr int NU = D == 3 ? 3 : 2, NC = D == 3 ? 6 : 3;
+                for (int c = sl; c < NC; c += tpp) {
+                    const bool lin = c < NU;
+                    const int a = lin ? c : (D == 3 ? c - 3 : 2);
+                    const float Fa_ = a == 0 ? F[0] : (a == 1 ? F[1] : F[2]);
+                    const float Ta_ = a == 0 ? T[0] : (a == 1 ? T[1] : T[2]);
+                    const float inc = lin ? hf * (Fa_ * P.imf + P.a[a]) : hf * (Ta_ * P.iIf + P.al[a]);
+                    double& V = lin ? P.U[a] : P.W[a];
+                    const double v = V + (double)inc;
+                    V = v;
+                    if (!last) {
+                        const float vf = (float)v;
+                        if (lin) {
+                            const double xn = P.X[a] + dt * v;
+                            P.X[a] = xn;
+                            out.x[a] = xn;
+                            out.xf[a] = (float)xn;
+                            out.u[a] = vf;
+                        } else {
+                            out.w[a] = vf;
+                        }
+                    }
                 }
             }
             cl.sync();

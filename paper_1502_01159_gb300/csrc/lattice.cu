@@ -118,112 +118,6 @@ __device__ __forceinline__ void collide_node(R* s, R* sg, R fbx, R fby, R fbz, R
     }
 }
 
-// Odd-step source of direction i for a node whose y/z neighbours are all
-// inside: only the x neighbour can leave the lattice.  Per-lane selects keep a
-// warp that holds an x-boundary node on this path (no divergence into the
-// generic boundary code).  Returns the flat index and sets bounce when the x
-// neighbour lies beyond a wall (then the node's own slot of direction i holds
-// the bounced value).
-template <int D, int I>
-__device__ __forceinline__ long long odd_src(const Geo& G, long long n, int x, long long sy, long long sz, bool& bounce) {
-    using L = Lat<D>;
-    constexpr int ex = L::ex(I);
-    long long off = (long long)L::ey(I) * sy + (long long)L::ez(I) * sz;
-    bounce = false;
-    if (ex == 0) return (long long)L::opp(I) * G.N + n - off;
-    int sx = x - ex;
-    long long dx = ex;
-    if (sx < 0 || sx >= G.nx) {
-        if (G.per[0]) dx = ex + (sx < 0 ? -G.nx : G.nx);  // wrap: source at sx +- nx
-        else bounce = true;
-    }
-    return bounce ? (long long)I * G.N + n : (long long)L::opp(I) * G.N + n - off - dx;
-}
-
-template <int D, int I>
-__device__ __forceinline__ long long odd_dst(const Geo& G, long long n, int x, long long sy, long long sz, bool& bounce) {
-    using L = Lat<D>;
-    constexpr int ex = L::ex(I);
-    long long off = (long long)L::ey(I) * sy + (long long)L::ez(I) * sz;
-    bounce = false;
-    if (ex == 0) return (long long)I * G.N + n + off;
-    int tx = x + ex;
-    long long dx = ex;
-    if (tx < 0 || tx >= G.nx) {
-        if (G.per[0]) dx = ex + (tx < 0 ? G.nx : -G.nx);
-        else bounce = true;
-    }
-    return bounce ? (long long)L::opp(I) * G.N + n : (long long)I * G.N + n + off + dx;
-}
-
-template <int D, typename S, int I>
-struct OddLoad {
-    using R = typename Store<S>::R;
-    static __device__ __forceinline__ void run(const Geo& G, const CollideParams<R>& P, const S* f, const S* g, long long n,
-                                               int x, long long sy, long long sz, R* s, R* sg) {
-        using L = Lat<D>;
-        bool b;
-        long long idx = odd_src<D, I>(G, n, x, sy, sz, b);
-        s[I] = Store<S>::ldf(f[idx]);
-        if (I < L::QG) {
-            R v = Store<S>::ldg(g[idx]);
-            constexpr int face = L::ex(I) > 0 ? 0 : 1;  // face crossed by x - e_I
-            if (b && face_iso(G, face)) v = P.abb[face] - v;
-            sg[I < L::QG ? I : 0] = v;
-        }
-        OddLoad<D, S, I + 1>::run(G, P, f, g, n, x, sy, sz, s, sg);
-    }
-};
-template <typename S> struct OddLoad<2, S, 9> {
-    using R = typename Store<S>::R;
-    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, const S*, const S*, long long, int,
-                                               long long, long long, R*, R*) {}
-};
-template <typename S> struct OddLoad<4, S, 15> {
-    using R = typename Store<S>::R;
-    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, const S*, const S*, long long, int,
-                                               long long, long long, R*, R*) {}
-};
-template <typename S> struct OddLoad<3, S, 19> {
-    using R = typename Store<S>::R;
-    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, const S*, const S*, long long, int,
-                                               long long, long long, R*, R*) {}
-};
-
-template <int D, typename S, int I>
-struct OddStore {
-    using R = typename Store<S>::R;
-    static __device__ __forceinline__ void run(const Geo& G, const CollideParams<R>& P, S* f, S* g, long long n, int x,
-                                               long long sy, long long sz, const R* s, const R* sg) {
-        using L = Lat<D>;
-        bool b;
-        long long idx = odd_dst<D, I>(G, n, x, sy, sz, b);
-        f[idx] = Store<S>::stf(s[I]);
-        if (I < L::QG) {
-            R v = sg[I < L::QG ? I : 0];
-            constexpr int face = L::ex(I) > 0 ? 1 : 0;  // face crossed by x + e_I
-            if (b && face_iso(G, face)) v = P.abb[face] - v;
-            g[idx] = Store<S>::stg(v);
-        }
-        OddStore<D, S, I + 1>::run(G, P, f, g, n, x, sy, sz, s, sg);
-    }
-};
-template <typename S> struct OddStore<2, S, 9> {
-    using R = typename Store<S>::R;
-    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, S*, S*, long long, int, long long,
-                                               long long, const R*, const R*) {}
-};
-template <typename S> struct OddStore<4, S, 15> {
-    using R = typename Store<S>::R;
-    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, S*, S*, long long, int, long long,
-                                               long long, const R*, const R*) {}
-};
-template <typename S> struct OddStore<3, S, 19> {
-    using R = typename Store<S>::R;
-    static __device__ __forceinline__ void run(const Geo&, const CollideParams<R>&, S*, S*, long long, int, long long,
-                                               long long, const R*, const R*) {}
-};
-
 // Flat offsets of the A-A slots relative to the node index n, per direction
 // (uniform over the grid, computed once on the host): odd-step sources
 // plane opp(i) at n - e_i, odd-step destinations plane i at n + e_i, even-step
@@ -231,6 +125,62 @@ template <typename S> struct OddStore<3, S, 19> {
 struct AAOffsets {
     long long src[19], dst[19], ld[19], st[19];
 };
+
+// Odd-step loads and stores of a warp that holds an x-face node, for rows whose
+// y/z neighbours are all inside: only the x neighbour can leave the lattice.
+// Every lane takes the interior slot (the fast path's offset); a lane whose x
+// neighbour in direction i lies beyond the face takes, by a select, the
+// periodic image (the interior slot shifted by nx) or, at a wall, its own
+// slot of direction i (loads) / opp(i) (stores), where bounce-back left or
+// leaves the value.  Interior lanes get the fast path's indices exactly, and
+// no lane diverges.
+template <int D, typename S>
+__device__ __forceinline__ void odd_load_xface(const Geo& G, const CollideParams<typename Store<S>::R>& P, const S* f,
+                                               const S* g, long long n, int x, const AAOffsets& O,
+                                               typename Store<S>::R* s, typename Store<S>::R* sg) {
+    using L = Lat<D>;
+    using R = typename Store<S>::R;
+    const bool lo = x == 0, hi = x == G.nx - 1, per = G.per[0] != 0;
+    const long long nx = G.nx;
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+        const int ex = L::ex(i);
+        const bool out = (ex > 0 && lo) || (ex < 0 && hi);  // x - e_i beyond a face
+        long long idx = n + O.src[i];
+        if (out) idx = per ? idx + ex * nx : n + O.ld[i];
+        s[i] = Store<S>::ldf(f[idx]);
+        if (i < L::QG) {
+            R v = Store<S>::ldg(g[idx]);
+            const int face = ex > 0 ? 0 : 1;  // face crossed by x - e_i
+            if (out && !per && face_iso(G, face)) v = P.abb[face] - v;
+            sg[i < L::QG ? i : 0] = v;
+        }
+    }
+}
+
+template <int D, typename S>
+__device__ __forceinline__ void odd_store_xface(const Geo& G, const CollideParams<typename Store<S>::R>& P, S* f, S* g,
+                                                long long n, int x, const AAOffsets& O, const typename Store<S>::R* s,
+                                                const typename Store<S>::R* sg) {
+    using L = Lat<D>;
+    using R = typename Store<S>::R;
+    const bool lo = x == 0, hi = x == G.nx - 1, per = G.per[0] != 0;
+    const long long nx = G.nx;
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+        const int ex = L::ex(i);
+        const bool out = (ex > 0 && hi) || (ex < 0 && lo);  // x + e_i beyond a face
+        long long idx = n + O.dst[i];
+        if (out) idx = per ? idx - ex * nx : n + O.st[i];
+        f[idx] = Store<S>::stf(s[i]);
+        if (i < L::QG) {
+            R v = sg[i < L::QG ? i : 0];
+            const int face = ex > 0 ? 1 : 0;  // face crossed by x + e_i
+            if (out && !per && face_iso(G, face)) v = P.abb[face] - v;
+            g[idx] = Store<S>::stg(v);
+        }
+    }
+}
 
 template <int D, typename S, int PARITY>
 __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) k_stream_collide(Geo G, S* __restrict__ f, S* __restrict__ g,
@@ -244,7 +194,6 @@ __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) 
     const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
     if (x >= G.nx || y >= G.ny) return;
     const long long n = node_index(G, x, y, z);
-    const long long sy = G.nx, sz = (long long)G.nx * G.ny;
     // y and z are uniform across a warp, so this test never splits one
     const bool inner_yz = y > 0 && y < G.ny - 1 && (D == 2 || (z > 0 && z < G.nz - 1));
     R s[L::Q], sg[L::QG];
@@ -264,7 +213,7 @@ __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) 
 #pragma unroll
         for (int k = 0; k < L::QG; k++) sg[k] = Store<S>::ldg(g[n + O.src[k]]);
     } else if (inner_yz) {
-        OddLoad<D, S, 0>::run(G, P, f, g, n, x, sy, sz, s, sg);
+        odd_load_xface<D, S>(G, P, f, g, n, x, O, s, sg);
     } else {
         load_node<D, S, R>(G, f, g, x, y, z, 1, s, sg);
     }
@@ -288,7 +237,7 @@ __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) 
 #pragma unroll
         for (int k = 0; k < L::QG; k++) g[n + O.dst[k]] = Store<S>::stg(sg[k]);
     } else if (inner_yz) {
-        OddStore<D, S, 0>::run(G, P, f, g, n, x, sy, sz, s, sg);
+        odd_store_xface<D, S>(G, P, f, g, n, x, O, s, sg);
     } else {
 #pragma unroll
         for (int i = 0; i < L::Q; i++) {
