@@ -195,10 +195,11 @@ __device__ __forceinline__ void for_neighbours(const DemCfg& C, const DemState& 
 
 // wall contacts of particle p (same law, R_wall = infinity, wall at rest).
 // mask: bit f set while face f holds a non-zero tangential history, so faces
-// out of contact cost no memory traffic.
+// out of contact cost no memory traffic; hpre (or null): those histories,
+// loaded ahead by the caller.
 template <int D>
 __device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, int p, const Pub& me, double Rp, float Rpf,
-                                            float dtf, float* F, float* T, int& mask) {
+                                            float dtf, float* F, float* T, int& mask, const float* hpre) {
     for (int face = 0; face < 2 * D; face++) {
         int a = face >> 1, hi = face & 1;
         if (!C.walled[a]) continue;
@@ -227,7 +228,9 @@ __device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, 
         float3 vt = f3(vr.x - vn * nn.x, vr.y - vn * nn.y, vr.z - vn * nn.z);
         float kt_eff;
         float Fn = normal_law(C, delta, vn, Rpf, &kt_eff);
-        float3 h = (mask & (1 << face)) ? f3(__ldcg(ftp), __ldcg(ftp + 1), __ldcg(ftp + 2)) : f3(0.f, 0.f, 0.f);
+        float3 h = f3(0.f, 0.f, 0.f);
+        if (mask & (1 << face))
+            h = hpre ? f3(hpre[3 * face], hpre[3 * face + 1], hpre[3 * face + 2]) : f3(__ldcg(ftp), __ldcg(ftp + 1), __ldcg(ftp + 2));
         float3 Ft = tangential(C, h, nn, vt, kt_eff, Fn, dtf);
         ftp[0] = h.x, ftp[1] = h.y, ftp[2] = h.z;
         mask |= 1 << face;
@@ -358,9 +361,25 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
         // Every global load of a particle is issued before the first store: the stores go to
         // shared memory through pointers the compiler cannot separate from the global ones, so
         // interleaving them would expose one load latency per value.
+        // Two passes: one thread per particle for the scalar state, then one thread per
+        // (velocity component, particle) for the FP64 arithmetic of the opening half kick
+        // and drift, so the FP64 chain is split over the warps as in the substeps.  The
+        // second pass's loads are issued before the first pass (registers), so both
+        // passes wait on memory once.
+        constexpr int NU = D == 3 ? 3 : 2, NC = D == 3 ? 6 : 3;
+        const int items = NC * nloc;
+        double pre[3] = {0.0, 0.0, 0.0};  // hydrodynamic load now / before, m g (or 0) of item threadIdx.x
+        if (threadIdx.x < items) {
+            const int c = threadIdx.x / nloc, l = threadIdx.x - c * nloc, p = base + l;
+            const bool lin = c < NU;
+            const int a = lin ? c : (D == 3 ? c - 3 : 2);
+            pre[0] = __ldcg((lin ? S.Fh : S.Th) + 3 * p + a);
+            pre[1] = __ldcg((lin ? S.Fhp : S.Thp) + 3 * p + a);
+            pre[2] = lin ? __ldcg(S.mg + p) : 0.0;
+        }
         for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
             const int p = base + l;
-            double x[3], u[3], w[3], fh[3], th[3], fhp[3], thp[3];
+            double x[3], u[3], w[3];
             float fc[3], tc[3];
             for (int a = 0; a < 3; a++) {
                 x[a] = __ldcg(S.X + 3 * p + a);
@@ -368,12 +387,8 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 w[a] = __ldcg(S.W + 3 * p + a);
                 fc[a] = __ldcg(S.Fc + 3 * p + a);
                 tc[a] = __ldcg(S.Tc + 3 * p + a);
-                fh[a] = __ldcg(S.Fh + 3 * p + a);
-                th[a] = __ldcg(S.Th + 3 * p + a);
-                fhp[a] = __ldcg(S.Fhp + 3 * p + a);
-                thp[a] = __ldcg(S.Thp + 3 * p + a);
             }
-            const double im = __ldcg(S.im + p), iI = __ldcg(S.iI + p), R = __ldcg(S.R + p), mg = __ldcg(S.mg + p);
+            const double im = __ldcg(S.im + p), iI = __ldcg(S.iI + p), R = __ldcg(S.R + p);
             const int fixed = S.fixed[p];
             float wft[6][3];
             for (int f = 0; f < 2 * D; f++)
@@ -407,21 +422,53 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 P.U[2] = 0.0;
                 P.W[0] = P.W[1] = 0.0;
             }
-            for (int a = 0; a < (D == 3 ? 3 : 2); a++)
-                P.a[a] = (float)(((hp ? 0.5 * (fh[a] + fhp[a]) : fh[a]) + mg * C.g[a]) * im);
-            for (int a = (D == 3 ? 0 : 2); a < 3; a++) P.al[a] = (float)((hp ? 0.5 * (th[a] + thp[a]) : th[a]) * iI);
             P.nadj = ne;
             for (int e = 0; e < ne && e < DEM_MAXA; e++) adj[l * DEM_MAXA + e] = ad[e];
-            // both buffers get every field; the substeps rewrite only those that change
-            if (!fixed) {
-                kick_s<D>(P, 0.5 * dt, (float)(0.5 * dt), useJ ? C.J + 18 * p : nullptr, S.U + 3 * p, S.W + 3 * p);
-                publish_const<D>(P, pub[l]);
-                drift_s<D>(P, dt, pub[l]);
-            } else {
-                publish_s(P, pub[l]);
-            }
-            pub[per + l] = pub[l];
+            // every published field; for a free particle the second pass rewrites those that move
+            publish_s(P, pub[l]);
         }
+        __syncthreads();
+        // Accelerations and the opening half kick + drift, one (component, particle) per
+        // thread.  The learned Jacobian's correction is zero here (U = U0 at the start of
+        // the lattice step), so the kick is the plain one.
+        const float hf0 = (float)(0.5 * dt);
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            const int c = it / nloc, l = it - c * nloc, p = base + l;
+            const bool lin = c < NU;
+            const int a = lin ? c : (D == 3 ? c - 3 : 2);
+            if (it != threadIdx.x) {  // items beyond the first pass load here
+                pre[0] = __ldcg((lin ? S.Fh : S.Th) + 3 * p + a);
+                pre[1] = __ldcg((lin ? S.Fhp : S.Thp) + 3 * p + a);
+                pre[2] = lin ? __ldcg(S.mg + p) : 0.0;
+            }
+            Priv& P = prv[l];
+            const double hyd = hp ? 0.5 * (pre[0] + pre[1]) : pre[0];
+            float acc;
+            if (lin) {
+                acc = (float)((hyd + pre[2] * C.g[a]) * P.im);
+                P.a[a] = acc;
+            } else {
+                acc = (float)(hyd * P.iI);
+                P.al[a] = acc;
+            }
+            if (P.fixed) continue;
+            const float inc = lin ? hf0 * (P.Fc[a] * P.imf + acc) : hf0 * (P.Tc[a] * P.iIf + acc);
+            double& V = lin ? P.U[a] : P.W[a];
+            const double v = V + (double)inc;
+            V = v;
+            Pub& out = pub[l];
+            if (lin) {
+                const double xn = P.X[a] + dt * v;
+                P.X[a] = xn;
+                out.x[a] = xn;
+                out.xf[a] = (float)xn;
+                out.u[a] = (float)v;
+            } else {
+                out.w[a] = (float)v;
+            }
+        }
+        __syncthreads();
+        for (int l = threadIdx.x; l < nloc; l += blockDim.x) pub[per + l] = pub[l];  // both buffers
         cl.sync();
         for (int sub = 0; sub < nsub; sub++) {
             const int rb = sub & 1;                      // published buffer read this substep
@@ -433,8 +480,8 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             float4* hist_new = nb_ft + (size_t)((gsub + 1) & 1) * C.cap;
             // tpp threads per particle (4 when a CTA holds at most 32 particles,
             // 2 up to 64, else 1): consecutive lanes, each taking every tpp-th
-            // neighbour (the first also the walls); warp-uniform loop so the
-            // shuffles below always see the whole warp
+            // neighbour (the first also the walls, after the pairs); warp-uniform
+            // loop so the shuffles below always see the whole warp
             const int tpp = per <= 32 ? 4 : (per <= 64 ? 2 : 1), ltpp = tpp == 4 ? 2 : tpp == 2 ? 1 : 0;
             const int lane = threadIdx.x & 31, sl = lane & (tpp - 1);
             for (int l0 = (threadIdx.x >> 5) * (32 >> ltpp); l0 < nloc; l0 += (int)blockDim.x >> ltpp) {
@@ -447,7 +494,16 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                     const Pub me = pub[rb * per + l];
                     const double Rp = P.R;
                     const float Rpf = P.Rf;
-                    if (sl == 0) wall_forces<D>(C, S, p, me, Rp, Rpf, dtf, F, T, P.wall_mask);
+                    // 3-D: the wall histories are loaded now and used after the pairs (their
+                    // latency hides behind the pair loop; in 2-D the extra registers cost more)
+                    float hpre[D == 3 ? 18 : 1];
+                    if (D == 3 && sl == 0) {
+                        const float* wf = S.wall_ft + 18 * p;
+#pragma unroll
+                        for (int f = 0; f < 2 * D; f++)
+#pragma unroll
+                            for (int a = 0; a < 3; a++) hpre[3 * f + a] = (P.wall_mask >> f & 1) ? __ldcg(wf + 3 * f + a) : 0.f;
+                    }
                     const int ne = P.nadj, e0 = ne > DEM_MAXA ? __ldcg(S.adj_start + p) : 0;
                     for (int e = sl; e < ne; e += tpp) {
                         int q, kk;
@@ -460,17 +516,18 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                         const bool first = kk >= 0;
                         const int k = first ? kk : ~kk;
                         const int rq = q / per, lq = q - rq * per;
-                        const Pub* rp = cl.map_shared_rank(pub, rq) + rb * per + lq;
-                        const Priv* rv = cl.map_shared_rank(prv, rq) + lq;
-                        // FP32 prefilter from the published FP32 position and radius (one load)
-                        const float4 pf = *reinterpret_cast<const float4*>(rp->xf);
-                        const float dxf = pf.x - me.xf[0], dyf = pf.y - me.xf[1], dzf = pf.z - me.xf[2];
-                        const float sf = Rpf + pf.w + 1e-3f;
+                        // every load of the slot at once: the neighbour's published state and
+                        // radius (distributed shared memory) and the pair's tangential history
+                        // (global; used only in contact), so their latencies overlap
+                        const float4 hv = __ldcg(hist_old + k);
+                        const Pub other = cl.map_shared_rank(pub, rq)[rb * per + lq];
+                        const double Rq = cl.map_shared_rank(prv, rq)[lq].R;
+                        // FP32 prefilter from the published FP32 position and radius
+                        const float dxf = other.xf[0] - me.xf[0], dyf = other.xf[1] - me.xf[1], dzf = other.xf[2] - me.xf[2];
+                        const float sf = Rpf + other.rf + 1e-3f;
                         float3 Fa = f3(0.f, 0.f, 0.f), Ta = Fa, Tb = Fa, h = Fa;
                         bool contact = false;
                         if (dxf * dxf + dyf * dyf + dzf * dzf < sf * sf) {
-                            const Pub other = *rp;
-                            const double Rq = rv->R;
                             const Pub& A = first ? me : other;
                             const Pub& B = first ? other : me;
                             const double Ssum = first ? Rp + Rq : Rq + Rp;
@@ -482,9 +539,8 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                             const double SS = Ssum * Ssum;
                             contact = d2 < SS;
                             if (contact) {
-                                const float4 hv = __ldcg(hist_old + k);
                                 if (__float_as_int(hv.w) == gsub - 1) h = f3(hv.x, hv.y, hv.z);
-                                pair_force(C, A, B, d, d2, SS, first ? Rpf : pf.w, first ? pf.w : Rpf, h, dtf, Fa, Ta, Tb);
+                                pair_force(C, A, B, d, d2, SS, first ? Rpf : other.rf, first ? other.rf : Rpf, h, dtf, Fa, Ta, Tb);
                             }
                         }
                         if (first) {
@@ -496,6 +552,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                             T[0] += Tb.x, T[1] += Tb.y, T[2] += Tb.z;
                         }
                     }
+                    if (sl == 0) wall_forces<D>(C, S, p, me, Rp, Rpf, dtf, F, T, P.wall_mask, D == 3 ? hpre : nullptr);
                 }
                 // the tpp partial sums, in a fixed order: (0 + 1) + (2 + 3)
                 if (tpp > 1)
