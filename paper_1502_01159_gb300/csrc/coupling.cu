@@ -135,6 +135,9 @@ __global__ void __launch_bounds__(CP_THREADS, (Lat<D>::dim == 2 && !FEAT) ? 4 : 
     const int p = blockIdx.x;
     const double Xp[3] = {X[3 * p], X[3 * p + 1], X[3 * p + 2]};
     const double Rp = Rr[p];
+    const int a0 = adj_start[p];
+    int nnb = adj_start[p + 1] - a0;
+    if (nnb > CP_MAXNB) nnb = CP_MAXNB;  // the neighbour build rejects more
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         double v = 0.0;
@@ -162,20 +165,21 @@ __global__ void __launch_bounds__(CP_THREADS, (Lat<D>::dim == 2 && !FEAT) ? 4 : 
             s_misc[lane == 9 ? 0 : (lane == 10 ? 1 : 2)] = vf;
         }
     }
-    const int a0 = adj_start[p];
-    int nnb = adj_start[p + 1] - a0;
-    if (nnb > CP_MAXNB) nnb = CP_MAXNB;  // the neighbour build rejects more
-    __syncthreads();
-    const int base[3] = {s_base[0], s_base[1], s_base[2]};
-    const float cf[3] = {s_cf[0], s_cf[1], s_cf[2]};
-    // neighbour centres relative to p's base node and radii: one (neighbour, axis
-    // or radius) per thread
-    for (int t = threadIdx.x; t < 4 * nnb; t += blockDim.x) {
+    // the neighbours' centres and radii, staged by the other warps while the first
+    // sets up the particle: one (neighbour, axis or radius) per thread
+    for (int t = (int)threadIdx.x - 32; t >= 0 && t < 4 * nnb; t += (int)blockDim.x - 32) {
         const int k = t >> 2, a = t & 3;
         const int q = adj_nb[a0 + k];
         if (a == 0) sh_id[k] = q;
-        const double v = a < 3 ? X[3 * q + a] : Rr[q];
-        sh_nb[k][a] = v;
+        sh_nb[k][a] = a < 3 ? X[3 * q + a] : Rr[q];
+    }
+    __syncthreads();
+    const int base[3] = {s_base[0], s_base[1], s_base[2]};
+    const float cf[3] = {s_cf[0], s_cf[1], s_cf[2]};
+    // neighbour centres relative to p's base node (FP32 for the ownership estimates)
+    for (int t = threadIdx.x; t < 4 * nnb; t += blockDim.x) {
+        const int k = t >> 2, a = t & 3;
+        const double v = sh_nb[k][a];
         sh_nbf[k][a] = (float)(a < 3 ? v - (double)base[a] : v);
     }
     __syncthreads();
@@ -349,6 +353,10 @@ __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __re
     const int sx = ihi[0] - ilo[0] + 1, sy = ihi[1] - ilo[1] + 1, sz = ihi[2] - ilo[2] + 1;
     const long long ns = (long long)sx * sy * sz;
     const bool staged = ns * (long long)sizeof(V) <= SPREAD_SMEM;
+    // launched as a programmatic dependent of the footprint kernel: everything above
+    // overlaps its tail; the marker field is read only once that grid has completed
+    // and its writes are visible (a no-op when launched without the dependency)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (staged) {
         for (long long q = threadIdx.x; q < ns; q += blockDim.x) {
             int x = ilo[0] + (int)(q % sx), y = ilo[1] + (int)((q / sx) % sy), z = ilo[2] + (int)(q / ((long long)sx * sy));
@@ -600,8 +608,21 @@ static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
             k_footprint<D, S, false><<<c->np, CP_THREADS, 0, s>>>(
                 c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk[parity], c->X, c->U, c->W, c->R, c->Tp, c->adj_start,
                 c->adj_nb, c->desc.kappa_T, c->desc.T_ref, parity, c->Fh, c->Th, c->Hh, nullptr);
-        k_spread<D, V><<<c->np, CP_THREADS, SPREAD_SMEM, s>>>(c->G, c->X, c->R, (const V*)c->mk[parity], (V*)c->fb[parity],
-                                                              c->flags[parity], c->box[parity]);
+        // programmatic dependent launch: the spread's CTAs start (and set up their boxes)
+        // as the footprint's CTAs finish, then wait for the whole footprint grid
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c->np, 1, 1);
+        cfg.blockDim = dim3(CP_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = SPREAD_SMEM;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k_spread<D, V>, c->G, (const double*)c->X, (const double*)c->R,
+                                           (const V*)c->mk[parity], (V*)c->fb[parity], c->flags[parity], c->box[parity]);
+        if (e != cudaSuccess) return e;
     }
     if (c->nm > 0) {
         int nb = (c->nm + CP_THREADS - 1) / CP_THREADS;
