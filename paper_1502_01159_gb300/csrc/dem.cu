@@ -30,7 +30,7 @@ namespace cg = cooperative_groups;
 
 namespace pibm {
 
-constexpr int DEM_T = 128;
+constexpr int DEM_T = 256;
 constexpr int DEM_MAXNB = 64;
 
 struct DemState {
@@ -478,11 +478,12 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             const int gsub = gbase + sub;
             const float4* hist_old = nb_ft + (size_t)(gsub & 1) * C.cap;
             float4* hist_new = nb_ft + (size_t)((gsub + 1) & 1) * C.cap;
-            // tpp threads per particle (4 when a CTA holds at most 32 particles,
-            // 2 up to 64, else 1): consecutive lanes, each taking every tpp-th
-            // neighbour (the first also the walls, after the pairs); warp-uniform
-            // loop so the shuffles below always see the whole warp
-            const int tpp = per <= 32 ? 4 : (per <= 64 ? 2 : 1), ltpp = tpp == 4 ? 2 : tpp == 2 ? 1 : 0;
+            // tpp threads per particle (4 up to 64 particles per CTA, 2 up to 128, else
+            // 1; 8 measured slower than 4 on 2-D beds): consecutive lanes, each taking
+            // every tpp-th neighbour (the first also the walls, after the pairs);
+            // warp-uniform loop so the shuffles below always see the whole warp
+            const int tpp = per <= 64 ? 4 : (per <= 128 ? 2 : 1);
+            const int ltpp = tpp == 8 ? 3 : (tpp == 4 ? 2 : (tpp == 2 ? 1 : 0));
             const int lane = threadIdx.x & 31, sl = lane & (tpp - 1);
             for (int l0 = (threadIdx.x >> 5) * (32 >> ltpp); l0 < nloc; l0 += (int)blockDim.x >> ltpp) {
                 const int l = l0 + (lane >> ltpp);
@@ -554,7 +555,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                     }
                     if (sl == 0) wall_forces<D>(C, S, p, me, Rp, Rpf, dtf, F, T, P.wall_mask, D == 3 ? hpre : nullptr);
                 }
-                // the tpp partial sums, in a fixed order: (0 + 1) + (2 + 3)
+                // the tpp partial sums, in a fixed butterfly order: ((0 + 1) + (2 + 3)) + ...
                 if (tpp > 1)
                     for (int a = 0; a < 3; a++) {
                         F[a] += __shfl_xor_sync(0xffffffffu, F[a], 1);
@@ -564,6 +565,11 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                     for (int a = 0; a < 3; a++) {
                         F[a] += __shfl_xor_sync(0xffffffffu, F[a], 2);
                         T[a] += __shfl_xor_sync(0xffffffffu, T[a], 2);
+                    }
+                if (tpp > 4)
+                    for (int a = 0; a < 3; a++) {
+                        F[a] += __shfl_xor_sync(0xffffffffu, F[a], 4);
+                        T[a] += __shfl_xor_sync(0xffffffffu, T[a], 4);
                     }
                 if (!active) continue;
                 const int p = base + l;
@@ -615,8 +621,23 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                     }
                 }
             }
-            cl.sync();
+            if (sub + 1 < nsub) cl.sync();
         }
+        // After the last substep no CTA changes anything another reads (the last kick
+        // publishes nothing), so a CTA barrier suffices; the write-back's loads are
+        // issued before it.
+        double wb[13];  // write-back inputs of this thread's first particle (C_p, T_p, H, H_prev, F_h, tau_h, X_build)
+        if ((int)threadIdx.x < nloc) {
+            const int p = base + threadIdx.x;
+            wb[0] = __ldcg(S.Cp + p), wb[1] = __ldcg(S.Tp + p), wb[2] = __ldcg(S.Hh + p);
+            wb[3] = __ldcg(S.Hhp + p);
+            for (int a = 0; a < 3; a++) {
+                wb[4 + a] = __ldcg(S.Fh + 3 * p + a);
+                wb[7 + a] = __ldcg(S.Th + 3 * p + a);
+                wb[10 + a] = __ldcg(S.Xb + 3 * p + a);
+            }
+        }
+        __syncthreads();
         gnow = gbase + nsub;
         // write back; thermosensitive particles: C_p dT_p / dt = -H_p over one
         // lattice step; keep this step's coupling as the previous one
@@ -626,15 +647,19 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
         for (int l = threadIdx.x; l < nloc; l += blockDim.x) {
             const int p = base + l;
             const Priv& P = prv[l];
-            // loads first (the stores below may alias them as far as the compiler knows)
-            const double cp = __ldcg(S.Cp + p), tp = __ldcg(S.Tp + p), hh = __ldcg(S.Hh + p);
-            const double hhp = hp ? __ldcg(S.Hhp + p) : 0.0;
-            double fh[3], th[3], xb[3];
-            for (int a = 0; a < 3; a++) {
-                fh[a] = __ldcg(S.Fh + 3 * p + a);
-                th[a] = __ldcg(S.Th + 3 * p + a);
-                xb[a] = __ldcg(S.Xb + 3 * p + a);
+            // loads first (the stores below may alias them as far as the compiler knows);
+            // the first particle of each thread was loaded before the barrier
+            if (l != (int)threadIdx.x) {
+                wb[0] = __ldcg(S.Cp + p), wb[1] = __ldcg(S.Tp + p), wb[2] = __ldcg(S.Hh + p);
+                wb[3] = __ldcg(S.Hhp + p);
+                for (int a = 0; a < 3; a++) {
+                    wb[4 + a] = __ldcg(S.Fh + 3 * p + a);
+                    wb[7 + a] = __ldcg(S.Th + 3 * p + a);
+                    wb[10 + a] = __ldcg(S.Xb + 3 * p + a);
+                }
             }
+            const double cp = wb[0], tp = wb[1], hh = wb[2], hhp = hp ? wb[3] : 0.0;
+            const double fh[3] = {wb[4], wb[5], wb[6]}, th[3] = {wb[7], wb[8], wb[9]}, xb[3] = {wb[10], wb[11], wb[12]};
             if (cp > 0.0) S.Tp[p] = tp - (hp ? 0.5 * (hh + hhp) : hh) / cp;
             double d2 = 0;
             for (int a = 0; a < 3; a++) {
