@@ -229,8 +229,12 @@ pibm_status pibm_set_particle_model(pibm_ctx* ctx, int model);
  * PIBM_TUNE_LATTICE_THREADS: threads per block of the collide-and-stream
  * kernel, 0 (default shape) or a multiple of 32 in [32, 512]; a block spans
  * min(threads, row width rounded up to 32) nodes of a row and as many rows as
- * the remaining factor gives. */
-enum { PIBM_TUNE_DEM_PARTICLES_PER_CTA = 0, PIBM_TUNE_PAIR_LATTICE = 1, PIBM_TUNE_LATTICE_THREADS = 2 };
+ * the remaining factor gives.
+ * PIBM_TUNE_WIDE_INDEX: 1 = 64-bit slot offsets in the collide-and-stream
+ * kernel even where 32-bit ones suffice (default 0: 32-bit offsets whenever
+ * Q N < 2^31 elements, 64-bit beyond; the two give identical results). */
+enum { PIBM_TUNE_DEM_PARTICLES_PER_CTA = 0, PIBM_TUNE_PAIR_LATTICE = 1, PIBM_TUNE_LATTICE_THREADS = 2,
+       PIBM_TUNE_WIDE_INDEX = 3 };
 pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value);
 
 /* Number of kernels one lattice step launches (for launch accounting). */

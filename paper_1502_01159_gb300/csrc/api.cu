@@ -857,6 +857,12 @@ pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value) {
         drop_graphs(c);
         return PIBM_OK;
     }
+    if (knob == PIBM_TUNE_WIDE_INDEX) {
+        if (value != 0 && value != 1) return fail(ctx, PIBM_ERR_ARG, "invalid tuning value");
+        c.tune_wide_index = value;
+        drop_graphs(c);
+        return PIBM_OK;
+    }
     if (knob != PIBM_TUNE_DEM_PARTICLES_PER_CTA || value < 0 || value > dem_max_per_cta())
         return fail(ctx, PIBM_ERR_ARG, "invalid tuning knob or value");
     c.tune_dem_particles_per_cta = value;

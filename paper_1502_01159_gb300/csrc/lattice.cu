@@ -121,9 +121,13 @@ __device__ __forceinline__ void collide_node(R* s, R* sg, R fbx, R fby, R fbz, R
 // Flat offsets of the A-A slots relative to the node index n, per direction
 // (uniform over the grid, computed once on the host): odd-step sources
 // plane opp(i) at n - e_i, odd-step destinations plane i at n + e_i, even-step
-// loads plane i at n and stores plane opp(i) at n.
+// loads plane i at n and stores plane opp(i) at n.  IX = int when every offset
+// fits in 32 bits (Q N < 2^31 elements): then each access is the thread's node
+// pointer plus a 32-bit offset, one multiply-add, which matters to the 16-bit
+// kernels (their time goes to issuing instructions, not to HBM).
+template <typename IX>
 struct AAOffsets {
-    long long src[19], dst[19], ld[19], st[19];
+    IX src[19], dst[19], ld[19], st[19];
 };
 
 // Odd-step loads and stores of a warp that holds an x-face node, for rows whose
@@ -134,23 +138,23 @@ struct AAOffsets {
 // slot of direction i (loads) / opp(i) (stores), where bounce-back left or
 // leaves the value.  Interior lanes get the fast path's indices exactly, and
 // no lane diverges.
-template <int D, typename S>
-__device__ __forceinline__ void odd_load_xface(const Geo& G, const CollideParams<typename Store<S>::R>& P, const S* f,
-                                               const S* g, long long n, int x, const AAOffsets& O,
-                                               typename Store<S>::R* s, typename Store<S>::R* sg) {
+template <int D, typename S, typename IX>
+__device__ __forceinline__ void odd_load_xface(const Geo& G, const CollideParams<typename Store<S>::R>& P, const S* fn,
+                                               const S* gn, int x, const AAOffsets<IX>& O, typename Store<S>::R* s,
+                                               typename Store<S>::R* sg) {
     using L = Lat<D>;
     using R = typename Store<S>::R;
     const bool lo = x == 0, hi = x == G.nx - 1, per = G.per[0] != 0;
-    const long long nx = G.nx;
+    const IX nx = G.nx;
 #pragma unroll
     for (int i = 0; i < L::Q; i++) {
         const int ex = L::ex(i);
         const bool out = (ex > 0 && lo) || (ex < 0 && hi);  // x - e_i beyond a face
-        long long idx = n + O.src[i];
-        if (out) idx = per ? idx + ex * nx : n + O.ld[i];
-        s[i] = Store<S>::ldf(f[idx]);
+        IX idx = O.src[i];
+        if (out) idx = per ? idx + ex * nx : O.ld[i];
+        s[i] = Store<S>::ldf(fn[idx]);
         if (i < L::QG) {
-            R v = Store<S>::ldg(g[idx]);
+            R v = Store<S>::ldg(gn[idx]);
             const int face = ex > 0 ? 0 : 1;  // face crossed by x - e_i
             if (out && !per && face_iso(G, face)) v = P.abb[face] - v;
             sg[i < L::QG ? i : 0] = v;
@@ -158,35 +162,35 @@ __device__ __forceinline__ void odd_load_xface(const Geo& G, const CollideParams
     }
 }
 
-template <int D, typename S>
-__device__ __forceinline__ void odd_store_xface(const Geo& G, const CollideParams<typename Store<S>::R>& P, S* f, S* g,
-                                                long long n, int x, const AAOffsets& O, const typename Store<S>::R* s,
+template <int D, typename S, typename IX>
+__device__ __forceinline__ void odd_store_xface(const Geo& G, const CollideParams<typename Store<S>::R>& P, S* fn, S* gn,
+                                                int x, const AAOffsets<IX>& O, const typename Store<S>::R* s,
                                                 const typename Store<S>::R* sg) {
     using L = Lat<D>;
     using R = typename Store<S>::R;
     const bool lo = x == 0, hi = x == G.nx - 1, per = G.per[0] != 0;
-    const long long nx = G.nx;
+    const IX nx = G.nx;
 #pragma unroll
     for (int i = 0; i < L::Q; i++) {
         const int ex = L::ex(i);
         const bool out = (ex > 0 && hi) || (ex < 0 && lo);  // x + e_i beyond a face
-        long long idx = n + O.dst[i];
-        if (out) idx = per ? idx - ex * nx : n + O.st[i];
-        f[idx] = Store<S>::stf(s[i]);
+        IX idx = O.dst[i];
+        if (out) idx = per ? idx - ex * nx : O.st[i];
+        fn[idx] = Store<S>::stf(s[i]);
         if (i < L::QG) {
             R v = sg[i < L::QG ? i : 0];
             const int face = ex > 0 ? 1 : 0;  // face crossed by x + e_i
             if (out && !per && face_iso(G, face)) v = P.abb[face] - v;
-            g[idx] = Store<S>::stg(v);
+            gn[idx] = Store<S>::stg(v);
         }
     }
 }
 
-template <int D, typename S, int PARITY>
+template <int D, typename S, int PARITY, typename IX>
 __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) k_stream_collide(Geo G, S* __restrict__ f, S* __restrict__ g,
                                                         const typename Store<S>::V4* __restrict__ fb,
                                                         const uint8_t* __restrict__ flags,
-                                                        CollideParams<typename Store<S>::R> P, AAOffsets O) {
+                                                        CollideParams<typename Store<S>::R> P, AAOffsets<IX> O) {
     using L = Lat<D>;
     using R = typename Store<S>::R;
     // block: blockDim.x nodes of a row (a multiple of 32) x blockDim.y rows
@@ -194,6 +198,8 @@ __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) 
     const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
     if (x >= G.nx || y >= G.ny) return;
     const long long n = node_index(G, x, y, z);
+    S* const fn = f + n;  // this node's slot in plane 0 of f and g: every fast-path access is one offset from here
+    S* const gn = g + n;
     // y and z are uniform across a warp, so this test never splits one
     const bool inner_yz = y > 0 && y < G.ny - 1 && (D == 2 || (z > 0 && z < G.nz - 1));
     R s[L::Q], sg[L::QG];
@@ -204,16 +210,16 @@ __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) 
     const bool xedge = xw == 0 || xw + 31 >= G.nx - 1;
     if (PARITY == 0) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) s[i] = Store<S>::ldf(f[n + O.ld[i]]);
+        for (int i = 0; i < L::Q; i++) s[i] = Store<S>::ldf(fn[O.ld[i]]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) sg[k] = Store<S>::ldg(g[n + O.ld[k]]);
+        for (int k = 0; k < L::QG; k++) sg[k] = Store<S>::ldg(gn[O.ld[k]]);
     } else if (inner_yz && !xedge) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) s[i] = Store<S>::ldf(f[n + O.src[i]]);
+        for (int i = 0; i < L::Q; i++) s[i] = Store<S>::ldf(fn[O.src[i]]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) sg[k] = Store<S>::ldg(g[n + O.src[k]]);
+        for (int k = 0; k < L::QG; k++) sg[k] = Store<S>::ldg(gn[O.src[k]]);
     } else if (inner_yz) {
-        odd_load_xface<D, S>(G, P, f, g, n, x, O, s, sg);
+        odd_load_xface<D, S, IX>(G, P, fn, gn, x, O, s, sg);
     } else {
         load_node<D, S, R>(G, f, g, x, y, z, 1, s, sg);
     }
@@ -228,16 +234,16 @@ __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) 
     collide_node<D, R>(s, sg, fbx, fby, fbz, qb, P);
     if (PARITY == 0) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) f[n + O.st[i]] = Store<S>::stf(s[i]);
+        for (int i = 0; i < L::Q; i++) fn[O.st[i]] = Store<S>::stf(s[i]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) g[n + O.st[k]] = Store<S>::stg(sg[k]);
+        for (int k = 0; k < L::QG; k++) gn[O.st[k]] = Store<S>::stg(sg[k]);
     } else if (inner_yz && !xedge) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) f[n + O.dst[i]] = Store<S>::stf(s[i]);
+        for (int i = 0; i < L::Q; i++) fn[O.dst[i]] = Store<S>::stf(s[i]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) g[n + O.dst[k]] = Store<S>::stg(sg[k]);
+        for (int k = 0; k < L::QG; k++) gn[O.dst[k]] = Store<S>::stg(sg[k]);
     } else if (inner_yz) {
-        odd_store_xface<D, S>(G, P, f, g, n, x, O, s, sg);
+        odd_store_xface<D, S, IX>(G, P, fn, gn, x, O, s, sg);
     } else {
 #pragma unroll
         for (int i = 0; i < L::Q; i++) {
@@ -367,7 +373,7 @@ __device__ __forceinline__ void odd_scatter(S* p, long long e, int ex, int lane,
 template <int D, typename S, int PARITY>
 __global__ void __launch_bounds__(512) k_stream_collide_pair(Geo G, S* __restrict__ f, S* __restrict__ g,
                                                              const float4* __restrict__ fb, const uint8_t* __restrict__ flags,
-                                                             CollideParams<float> P, AAOffsets O) {
+                                                             CollideParams<float> P, AAOffsets<long long> O) {
     using L = Lat<D>;
     using St = Store<S>;
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -459,20 +465,27 @@ __global__ void __launch_bounds__(512) k_stream_collide_pair(Geo G, S* __restric
     }
 }
 
-template <int D>
-static AAOffsets aa_offsets(const Geo& G) {
+template <int D, typename IX>
+static AAOffsets<IX> aa_offsets(const Geo& G) {
     using L = Lat<D>;
-    AAOffsets O;
+    AAOffsets<IX> O;
     const long long sy = G.nx, sz = (long long)G.nx * G.ny;
     for (int i = 0; i < 19; i++) O.src[i] = O.dst[i] = O.ld[i] = O.st[i] = 0;
     for (int i = 0; i < L::Q; i++) {
         long long off = L::ex(i) + L::ey(i) * sy + L::ez(i) * sz;
-        O.src[i] = (long long)L::opp(i) * G.N - off;
-        O.dst[i] = (long long)i * G.N + off;
-        O.ld[i] = (long long)i * G.N;
-        O.st[i] = (long long)L::opp(i) * G.N;
+        O.src[i] = (IX)((long long)L::opp(i) * G.N - off);
+        O.dst[i] = (IX)((long long)i * G.N + off);
+        O.ld[i] = (IX)((long long)i * G.N);
+        O.st[i] = (IX)((long long)L::opp(i) * G.N);
     }
     return O;
+}
+
+// 32-bit offsets hold when every slot of f (the larger array) is within 2^31 - 1
+// elements of plane 0's node, with room for the periodic x shift
+template <int D>
+static bool narrow_offsets(const Geo& G) {
+    return (long long)Lat<D>::Q * G.N + 2LL * G.nx < (1LL << 31) - 1;
 }
 
 // Block shape of the lattice kernels for a row of `width` threads: bx threads
@@ -495,7 +508,7 @@ static cudaError_t pair_launch(Ctx* c, cudaStream_t s, int parity) {
         dim3 block, grid;
         lattice_shape(c, pairs, block, grid);
         CollideParams<float> P = collide_params<float>(c);
-        AAOffsets O = aa_offsets<D>(c->G);
+        AAOffsets<long long> O = aa_offsets<D, long long>(c->G);
         if (parity == 0)
             k_stream_collide_pair<D, S, 0><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const float4*)c->fb[parity],
                                                                   c->flags[parity], P, O);
@@ -515,12 +528,20 @@ static cudaError_t sc_launch(Ctx* c, cudaStream_t s, int parity) {
     lattice_shape(c, c->G.nx, block, grid);
     using R = typename Store<S>::R;
     CollideParams<R> P = collide_params<R>(c);
-    AAOffsets O = aa_offsets<D>(c->G);
     using V = typename Store<S>::V4;
-    if (parity == 0)
-        k_stream_collide<D, S, 0><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb[parity], c->flags[parity], P, O);
-    else
-        k_stream_collide<D, S, 1><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb[parity], c->flags[parity], P, O);
+    if (narrow_offsets<D>(c->G) && !c->tune_wide_index) {
+        const AAOffsets<int> O = aa_offsets<D, int>(c->G);
+        if (parity == 0)
+            k_stream_collide<D, S, 0, int><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb[parity], c->flags[parity], P, O);
+        else
+            k_stream_collide<D, S, 1, int><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb[parity], c->flags[parity], P, O);
+    } else {
+        const AAOffsets<long long> O = aa_offsets<D, long long>(c->G);
+        if (parity == 0)
+            k_stream_collide<D, S, 0, long long><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb[parity], c->flags[parity], P, O);
+        else
+            k_stream_collide<D, S, 1, long long><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb[parity], c->flags[parity], P, O);
+    }
     return cudaGetLastError();
 }
 
