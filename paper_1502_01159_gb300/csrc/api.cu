@@ -705,6 +705,9 @@ pibm_status pibm_step_timed(pibm_ctx* ctx, double* ms) {
     chk(cudaStreamWaitEvent(c.s2, ev[0], 0));
     chk(launch_coupling_clear(&c, c.s2, par ^ 1));
     chk(cudaEventRecord(ev[6], c.s2));
+    // the lattice kernel's own interval starts here, after the other branches were
+    // launched (host launch time is not the kernel's)
+    chk(cudaEventRecord(ev[7], c.s0));
     chk(launch_stream_collide(&c, c.s0, par));
     chk(cudaEventRecord(ev[1], c.s0));
     chk(cudaStreamWaitEvent(c.s0, ev[3], 0));
@@ -715,7 +718,7 @@ pibm_status pibm_step_timed(pibm_ctx* ctx, double* ms) {
     chk(cudaEventSynchronize(ev[5]));
     float t[4] = {0, 0, 0, 0};
     if (e == cudaSuccess) {
-        chk(cudaEventElapsedTime(&t[0], ev[0], ev[1]));
+        chk(cudaEventElapsedTime(&t[0], ev[7], ev[1]));
         chk(cudaEventElapsedTime(&t[1], ev[2], ev[3]));
         chk(cudaEventElapsedTime(&t[2], ev[4], ev[5]));
         chk(cudaEventElapsedTime(&t[3], ev[0], ev[5]));

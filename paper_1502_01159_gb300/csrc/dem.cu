@@ -938,11 +938,12 @@ cudaError_t launch_dem(Ctx* c, cudaStream_t s, int nsub) {
     C.per = (c->np + cs - 1) / cs;
     auto kern = c->D == 2 ? k_dem<2> : k_dem<3>;
     size_t smem = dem_smem(C.per);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dem_smem(DEM_MAXPER));
-    if (e != cudaSuccess) return e;
-    if (cs > 8) {
+    if (!c->dem_attr_ok) {  // once per context: these are host calls, not needed per launch
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dem_smem(DEM_MAXPER));
+        if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
+        c->dem_attr_ok = 1;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);

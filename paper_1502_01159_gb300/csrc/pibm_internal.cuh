@@ -327,6 +327,7 @@ struct Ctx {
     int tune_pair_lattice;           // 1: two nodes per thread for 16-bit storage (nx a multiple of 64)
     int tune_lattice_threads;        // 0: default block shape; else threads per lattice block
     int tune_wide_index;             // 1: 64-bit slot offsets in the lattice kernel even where 32-bit suffice
+    int dem_attr_ok;                 // the DEM kernel's launch attributes are set
     Surrogate sg;
     int lat;                         // lattice id: 2 D2Q9, 3 D3Q19, 4 D3Q15 (all with D2Q5 / D3Q7 thermal)
     int point;                       // particle model: 1 = one PIBM point per particle (d_p <= h)
