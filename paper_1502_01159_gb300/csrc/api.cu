@@ -19,7 +19,25 @@ using namespace pibm;
 struct pibm_ctx {
     Ctx c;
     std::vector<std::pair<void*, int>> allocs;  // (pointer, group): 0 lattice, 1 particles, 2 markers, 3 scratch
+    double* hstage = nullptr;                   // pinned host staging for the per-step read-backs
+    size_t hstage_n = 0;                        // its size in doubles
 };
+
+// Pinned host buffer of at least n doubles (grown on demand; null if the host
+// cannot pin memory, and the caller then copies directly).
+static double* host_stage(pibm_ctx* ctx, size_t n) {
+    if (ctx->hstage_n >= n) return ctx->hstage;
+    if (ctx->hstage) cudaFreeHost(ctx->hstage);
+    ctx->hstage = nullptr;
+    ctx->hstage_n = 0;
+    if (cudaMallocHost((void**)&ctx->hstage, sizeof(double) * n) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->hstage = nullptr;
+        return nullptr;
+    }
+    ctx->hstage_n = n;
+    return ctx->hstage;
+}
 
 static std::string g_create_error;
 
@@ -81,6 +99,8 @@ static void drop_graphs(Ctx& c) {
 }
 
 // Device status words written by kernels (sticky until particles are reset).
+static pibm_status status_word(pibm_ctx* ctx, const int* st);
+
 static pibm_status device_status(pibm_ctx* ctx) {
     Ctx& c = ctx->c;
     cudaError_t e = cudaStreamSynchronize(c.s0);
@@ -88,6 +108,11 @@ static pibm_status device_status(pibm_ctx* ctx) {
     int st[2] = {0, 0};
     e = cudaMemcpy(st, c.dstat, sizeof(st), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return fail(ctx, PIBM_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+    return status_word(ctx, st);
+}
+
+// the device status word (code, detail) as a status and message
+static pibm_status status_word(pibm_ctx* ctx, const int* st) {
     if (st[0] != 0) {
         const char* what = st[1] == 1   ? "more than 64 neighbour candidates for one particle"
                            : st[1] == 2 ? "a particle moved more than half the neighbour skin in one lattice step"
@@ -304,6 +329,7 @@ pibm_status pibm_destroy(pibm_ctx* ctx) {
     if (c.s2) cudaStreamSynchronize(c.s2);
     drop_graphs(c);
     dfree_group(ctx, -1);
+    if (ctx->hstage) cudaFreeHost(ctx->hstage);
     if (c.ev_fork) cudaEventDestroy(c.ev_fork);
     if (c.ev_join) cudaEventDestroy(c.ev_join);
     if (c.ev_join2) cudaEventDestroy(c.ev_join2);
@@ -449,6 +475,7 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
         C.ncell *= C.nc[a];
     }
     C.skin = cmin - 2.0 * rmax;
+    c.spread_smem = spread_smem_bytes(c.D, rmax, c.v4);
     C.cap = std::max(64, 16 * n);
     C.maxnb = 64;
     c.adj_cap = 2 * C.cap;
@@ -762,6 +789,25 @@ pibm_status pibm_read_particles(pibm_ctx* ctx, double* X, double* U, double* W, 
     if (!ctx) return PIBM_ERR_ARG;
     Ctx& c = ctx->c;
     int n = c.np;
+    // per-step read-back path: the state and the device status word go into one
+    // pinned buffer with asynchronous copies, one synchronisation, then host copies
+    double* h = n > 0 ? host_stage(ctx, (size_t)10 * n + 1) : nullptr;
+    if (h) {
+        PCHECK(cudaMemcpyAsync(h, c.X, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c.s0));
+        PCHECK(cudaMemcpyAsync(h + 3 * n, c.U, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c.s0));
+        PCHECK(cudaMemcpyAsync(h + 6 * n, c.W, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c.s0));
+        PCHECK(cudaMemcpyAsync(h + 9 * n, c.Tp, sizeof(double) * n, cudaMemcpyDeviceToHost, c.s0));
+        PCHECK(cudaMemcpyAsync(h + 10 * n, c.dstat, sizeof(int) * 2, cudaMemcpyDeviceToHost, c.s0));
+        cudaError_t e = cudaStreamSynchronize(c.s0);
+        if (e != cudaSuccess) return fail(ctx, PIBM_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+        if (X) memcpy(X, h, sizeof(double) * 3 * n);
+        if (U) memcpy(U, h + 3 * n, sizeof(double) * 3 * n);
+        if (W) memcpy(W, h + 6 * n, sizeof(double) * 3 * n);
+        if (T_p) memcpy(T_p, h + 9 * n, sizeof(double) * n);
+        int st[2];
+        memcpy(st, h + 10 * n, sizeof(st));
+        return status_word(ctx, st);
+    }
     if (n > 0) {
         if (X) PCHECK(cudaMemcpyAsync(X, c.X, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c.s0));
         if (U) PCHECK(cudaMemcpyAsync(U, c.U, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c.s0));

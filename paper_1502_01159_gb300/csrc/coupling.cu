@@ -320,9 +320,21 @@ __global__ void __launch_bounds__(CP_THREADS, (Lat<D>::dim == 2 && !FEAT) ? 4 : 
 // gathers its 3^D neighbours from there (Eqs lbm10-lbm12, lbm12.6).
 constexpr int SPREAD_SMEM = 46 * 1024;  // plus a few static bytes: under the 48 KB default per CTA
 
+// Shared memory the spread reserves per CTA: the staged region of the largest
+// particle (at most floor(2 R_max) + 6 nodes per axis: the footprint, grown by one
+// node for the output and one more for the stencil), capped at SPREAD_SMEM; a
+// smaller reservation lets more CTAs share an SM.
+int spread_smem_bytes(int dim, double rmax, size_t v4) {
+    const long long e = (long long)floor(2.0 * rmax) + 6;
+    long long b = (long long)v4;
+    for (int a = 0; a < dim; a++) b *= e;
+    return (int)(b < SPREAD_SMEM ? b : SPREAD_SMEM);
+}
+
 template <int D, typename V>
 __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __restrict__ X, const double* __restrict__ Rr,
-                                                       const V* __restrict__ mk, V* __restrict__ fb, uint8_t* flags, int* box) {
+                                                       const V* __restrict__ mk, V* __restrict__ fb, uint8_t* flags, int* box,
+                                                       int smem_bytes) {
     extern __shared__ __align__(32) unsigned char sm_raw[];
     V* tile = reinterpret_cast<V*>(sm_raw);
     using T = decltype(V().x);
@@ -352,7 +364,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __re
     if (ex <= 0 || ey <= 0 || ez <= 0) return;
     const int sx = ihi[0] - ilo[0] + 1, sy = ihi[1] - ilo[1] + 1, sz = ihi[2] - ilo[2] + 1;
     const long long ns = (long long)sx * sy * sz;
-    const bool staged = ns * (long long)sizeof(V) <= SPREAD_SMEM;
+    const bool staged = ns * (long long)sizeof(V) <= smem_bytes;
     // launched as a programmatic dependent of the footprint kernel: everything above
     // overlaps its tail; the marker field is read only once that grid has completed
     // and its writes are visible (a no-op when launched without the dependency)
@@ -613,7 +625,7 @@ static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(c->np, 1, 1);
         cfg.blockDim = dim3(CP_THREADS, 1, 1);
-        cfg.dynamicSmemBytes = SPREAD_SMEM;
+        cfg.dynamicSmemBytes = c->spread_smem;
         cfg.stream = s;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -621,7 +633,8 @@ static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
         cfg.attrs = at;
         cfg.numAttrs = 1;
         cudaError_t e = cudaLaunchKernelEx(&cfg, k_spread<D, V>, c->G, (const double*)c->X, (const double*)c->R,
-                                           (const V*)c->mk[parity], (V*)c->fb[parity], c->flags[parity], c->box[parity]);
+                                           (const V*)c->mk[parity], (V*)c->fb[parity], c->flags[parity], c->box[parity],
+                                           c->spread_smem);
         if (e != cudaSuccess) return e;
     }
     if (c->nm > 0) {

@@ -328,6 +328,7 @@ struct Ctx {
     int tune_lattice_threads;        // 0: default block shape; else threads per lattice block
     int tune_wide_index;             // 1: 64-bit slot offsets in the lattice kernel even where 32-bit suffice
     int dem_attr_ok;                 // the DEM kernel's launch attributes are set
+    int spread_smem;                 // shared memory per CTA of the spread kernel (from the largest radius)
     Surrogate sg;
     int lat;                         // lattice id: 2 D2Q9, 3 D3Q19, 4 D3Q15 (all with D2Q5 / D3Q7 thermal)
     int point;                       // particle model: 1 = one PIBM point per particle (d_p <= h)
@@ -364,6 +365,7 @@ cudaError_t launch_features(Ctx* c, cudaStream_t s, int parity, double* out);  /
 // coupling.cu
 cudaError_t launch_coupling(Ctx* c, cudaStream_t s, int parity);
 cudaError_t launch_coupling_clear(Ctx* c, cudaStream_t s, int parity);
+int spread_smem_bytes(int dim, double rmax, size_t v4);
 cudaError_t launch_footprint_sums(Ctx* c, cudaStream_t s, int parity);  // surrogate feature sums of the state
 int coupling_kernel_count(Ctx* c);
 // dem.cu
