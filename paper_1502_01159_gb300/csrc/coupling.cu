@@ -320,14 +320,14 @@ __global__ void __launch_bounds__(CP_THREADS, (Lat<D>::dim == 2 && !FEAT) ? 4 : 
 // gathers its 3^D neighbours from there (Eqs lbm10-lbm12, lbm12.6).
 constexpr int SPREAD_SMEM = 46 * 1024;  // plus a few static bytes: under the 48 KB default per CTA
 
-// Shared memory the spread reserves per CTA: the staged region of the largest
-// particle (at most floor(2 R_max) + 6 nodes per axis: the footprint, grown by one
-// node for the output and one more for the stencil), capped at SPREAD_SMEM; a
-// smaller reservation lets more CTAs share an SM.
+// Shared memory the spread reserves per CTA: the x-summed buffer of the largest
+// particle (the output x range, at most floor(2 R_max) + 4 nodes: the footprint
+// grown by one node; the y/z ranges one node wider on each side), capped at
+// SPREAD_SMEM; a smaller reservation lets more CTAs share an SM.
 int spread_smem_bytes(int dim, double rmax, size_t v4) {
-    const long long e = (long long)floor(2.0 * rmax) + 6;
-    long long b = (long long)v4;
-    for (int a = 0; a < dim; a++) b *= e;
+    const long long e = (long long)floor(2.0 * rmax) + 4;
+    long long b = (long long)v4 * e;
+    for (int a = 1; a < dim; a++) b *= e + 2;
     return (int)(b < SPREAD_SMEM ? b : SPREAD_SMEM);
 }
 
@@ -362,17 +362,36 @@ __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __re
     const int ilo[3] = {s_b[6], s_b[7], s_b[8]}, ihi[3] = {s_b[9], s_b[10], s_b[11]};
     int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
     if (ex <= 0 || ey <= 0 || ez <= 0) return;
-    const int sx = ihi[0] - ilo[0] + 1, sy = ihi[1] - ilo[1] + 1, sz = ihi[2] - ilo[2] + 1;
-    const long long ns = (long long)sx * sy * sz;
-    const bool staged = ns * (long long)sizeof(V) <= smem_bytes;
+    const int sy = ihi[1] - ilo[1] + 1, sz = ihi[2] - ilo[2] + 1;
+    // delta_h weights are separable (1/2 at 0, 1/4 at +-1 per axis, Eq lbm12):
+    // pass 1 sums along x, from the marker field into shared memory, over the
+    // output x range and the y/z range grown by one; pass 2 sums the 3 (2-D) or
+    // 3x3 (3-D) y/z neighbours from there.  Every node's value is formed from the
+    // same inputs in the same order by whichever CTA computes it, so overlapping
+    // boxes still write identical values.
+    const long long na = (long long)ex * sy * sz;
+    const bool staged = na * (long long)sizeof(V) <= smem_bytes;
     // launched as a programmatic dependent of the footprint kernel: everything above
     // overlaps its tail; the marker field is read only once that grid has completed
     // and its writes are visible (a no-op when launched without the dependency)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     if (staged) {
-        for (long long q = threadIdx.x; q < ns; q += blockDim.x) {
-            int x = ilo[0] + (int)(q % sx), y = ilo[1] + (int)((q / sx) % sy), z = ilo[2] + (int)(q / ((long long)sx * sy));
-            tile[q] = mk[node_index(G, x, y, z)];
+        for (long long q = threadIdx.x; q < na; q += blockDim.x) {
+            const int x = lo[0] + (int)(q % ex), y = ilo[1] + (int)((q / ex) % sy), z = ilo[2] + (int)(q / ((long long)ex * sy));
+            const long long n0 = node_index(G, x, y, z);
+            const V c = mk[n0];
+            T a0 = (T)0.5 * c.x, a1 = (T)0.5 * c.y, a2 = (T)0.5 * c.z, a3 = (T)0.5 * c.w;
+            if (x > 0) {
+                const V m = mk[n0 - 1];
+                a0 += (T)0.25 * m.x, a1 += (T)0.25 * m.y, a2 += (T)0.25 * m.z, a3 += (T)0.25 * m.w;
+            }
+            if (x < G.nx - 1) {
+                const V m = mk[n0 + 1];
+                a0 += (T)0.25 * m.x, a1 += (T)0.25 * m.y, a2 += (T)0.25 * m.z, a3 += (T)0.25 * m.w;
+            }
+            V a;
+            a.x = a0, a.y = a1, a.z = a2, a.w = a3;
+            tile[q] = a;
         }
         __syncthreads();
     }
@@ -380,24 +399,40 @@ __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __re
     for (long long q = threadIdx.x; q < cnt; q += blockDim.x) {
         int x = lo[0] + (int)(q % ex), y = lo[1] + (int)((q / ex) % ey), z = lo[2] + (int)(q / ((long long)ex * ey));
         T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-        for (int dz = (Lat<D>::dim == 3 ? -1 : 0); dz <= (Lat<D>::dim == 3 ? 1 : 0); dz++) {
-            int zz = z + dz;
-            if (zz < 0 || zz >= G.nz) continue;
-            for (int dy = -1; dy <= 1; dy++) {
-                int yy = y + dy;
-                if (yy < 0 || yy >= G.ny) continue;
-                for (int dx = -1; dx <= 1; dx++) {
-                    int xx = x + dx;
-                    if (xx < 0 || xx >= G.nx) continue;
-                    // delta_h(0) = 1/2, delta_h(+-1) = 1/4 (Eq lbm12)
-                    T w = (dx == 0 ? (T)0.5 : (T)0.25) * (dy == 0 ? (T)0.5 : (T)0.25);
-                    if (Lat<D>::dim == 3) w *= (dz == 0 ? (T)0.5 : (T)0.25);
-                    V m = staged ? tile[((long long)(zz - ilo[2]) * sy + (yy - ilo[1])) * sx + (xx - ilo[0])]
-                                 : mk[node_index(G, xx, yy, zz)];
-                    s0 += w * m.x;
-                    s1 += w * m.y;
-                    s2 += w * m.z;
-                    s3 += w * m.w;
+        if (staged) {
+            for (int dz = (Lat<D>::dim == 3 ? -1 : 0); dz <= (Lat<D>::dim == 3 ? 1 : 0); dz++) {
+                const int zz = z + dz;
+                if (zz < 0 || zz >= G.nz) continue;
+                const T wz = Lat<D>::dim == 3 ? (dz == 0 ? (T)0.5 : (T)0.25) : (T)1;
+                for (int dy = -1; dy <= 1; dy++) {
+                    const int yy = y + dy;
+                    if (yy < 0 || yy >= G.ny) continue;
+                    const T w = wz * (dy == 0 ? (T)0.5 : (T)0.25);
+                    const V a = tile[((long long)(zz - ilo[2]) * sy + (yy - ilo[1])) * ex + (x - lo[0])];
+                    s0 += w * a.x;
+                    s1 += w * a.y;
+                    s2 += w * a.z;
+                    s3 += w * a.w;
+                }
+            }
+        } else {  // a region beyond the reserved shared memory: the 27-point gather from global memory
+            for (int dz = (Lat<D>::dim == 3 ? -1 : 0); dz <= (Lat<D>::dim == 3 ? 1 : 0); dz++) {
+                int zz = z + dz;
+                if (zz < 0 || zz >= G.nz) continue;
+                for (int dy = -1; dy <= 1; dy++) {
+                    int yy = y + dy;
+                    if (yy < 0 || yy >= G.ny) continue;
+                    for (int dx = -1; dx <= 1; dx++) {
+                        int xx = x + dx;
+                        if (xx < 0 || xx >= G.nx) continue;
+                        T w = (dx == 0 ? (T)0.5 : (T)0.25) * (dy == 0 ? (T)0.5 : (T)0.25);
+                        if (Lat<D>::dim == 3) w *= (dz == 0 ? (T)0.5 : (T)0.25);
+                        V m = mk[node_index(G, xx, yy, zz)];
+                        s0 += w * m.x;
+                        s1 += w * m.y;
+                        s2 += w * m.z;
+                        s3 += w * m.w;
+                    }
                 }
             }
         }
