@@ -387,6 +387,7 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     double rmax = 0.0;
     for (int p = 0; p < n; p++) {
         if (!(R[p] > 0) || !(rho_p[p] > 0)) return fail(ctx, PIBM_ERR_ARG, "particle radius and density must be positive");
+        if (R[p] > 600.0) return fail(ctx, PIBM_ERR_ARG, "particle radius above 600 nodes");
         for (int a = 0; a < c.D; a++)
             if (!(X[3 * p + a] > -0.5 && X[3 * p + a] < nn[a] - 0.5))
                 return fail(ctx, PIBM_ERR_ARG, "particle centre outside the domain");

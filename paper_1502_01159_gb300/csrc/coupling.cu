@@ -61,9 +61,10 @@ __global__ void __launch_bounds__(CP_THREADS) k_clear(Geo G, const int* __restri
     int lo[3] = {box[6 * p], box[6 * p + 1], box[6 * p + 2]}, hi[3] = {box[6 * p + 3], box[6 * p + 4], box[6 * p + 5]};
     if (hi[0] < lo[0]) return;
     int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
-    long long cnt = (long long)ex * ey * ez;
-    for (long long q = threadIdx.x; q < cnt; q += blockDim.x) {
-        int x = lo[0] + (int)(q % ex), y = lo[1] + (int)((q / ex) % ey), z = lo[2] + (int)(q / ((long long)ex * ey));
+    const int cnt = ex * ey * ez;  // boxes span at most 2 R + 6 nodes per axis (R <= 600): 32-bit
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const int qy = q / ex, qz = qy / ey;
+        const int x = lo[0] + (q - qy * ex), y = lo[1] + (qy - qz * ey), z = lo[2] + qz;
         long long n = node_index(G, x, y, z);
         mk[n] = zero4<V>();
         fb[n] = zero4<V>();
@@ -185,15 +186,16 @@ __global__ void __launch_bounds__(CP_THREADS, (Lat<D>::dim == 2 && !FEAT) ? 4 : 
     __syncthreads();
     const int lo[3] = {s_box[0], s_box[1], s_box[2]}, hi[3] = {s_box[3], s_box[4], s_box[5]};
     int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
-    long long cnt = (ex > 0 && ey > 0 && ez > 0) ? (long long)ex * ey * ez : 0;
+    const int cnt = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;  // 32-bit: boxes of R <= 600
     const float Upf[3] = {s_U[0], s_U[1], s_U[2]};
     const float Wpf[3] = {s_W[0], s_W[1], s_W[2]};
     const R dTp = (R)s_misc[0];
     const R twok = (R)s_misc[1];
     const float Rpf = s_misc[2];
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // per-thread partials; the block sum is FP64
-    for (long long q = threadIdx.x; q < cnt; q += blockDim.x) {
-        int x = lo[0] + (int)(q % ex), y = lo[1] + (int)((q / ex) % ey), z = lo[2] + (int)(q / ((long long)ex * ey));
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const int qy = q / ex, qz = qy / ey;
+        const int x = lo[0] + (q - qy * ex), y = lo[1] + (qy - qz * ey), z = lo[2] + qz;
         const int ix = x - base[0], iy = y - base[1], iz = z - base[2];
         const float ef = eps_f32(ix, iy, iz, cf, Rpf);
         if (ef <= -EPS_GUARD) continue;  // certainly not covered
@@ -369,15 +371,16 @@ __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __re
     // 3x3 (3-D) y/z neighbours from there.  Every node's value is formed from the
     // same inputs in the same order by whichever CTA computes it, so overlapping
     // boxes still write identical values.
-    const long long na = (long long)ex * sy * sz;
-    const bool staged = na * (long long)sizeof(V) <= smem_bytes;
+    const int na = ex * sy * sz;  // 32-bit: boxes of R <= 600
+    const bool staged = (long long)na * (long long)sizeof(V) <= smem_bytes;
     // launched as a programmatic dependent of the footprint kernel: everything above
     // overlaps its tail; the marker field is read only once that grid has completed
     // and its writes are visible (a no-op when launched without the dependency)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     if (staged) {
-        for (long long q = threadIdx.x; q < na; q += blockDim.x) {
-            const int x = lo[0] + (int)(q % ex), y = ilo[1] + (int)((q / ex) % sy), z = ilo[2] + (int)(q / ((long long)ex * sy));
+        for (int q = threadIdx.x; q < na; q += blockDim.x) {
+            const int qy = q / ex, qz = qy / sy;
+            const int x = lo[0] + (q - qy * ex), y = ilo[1] + (qy - qz * sy), z = ilo[2] + qz;
             const long long n0 = node_index(G, x, y, z);
             const V c = mk[n0];
             T a0 = (T)0.5 * c.x, a1 = (T)0.5 * c.y, a2 = (T)0.5 * c.z, a3 = (T)0.5 * c.w;
@@ -395,9 +398,10 @@ __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __re
         }
         __syncthreads();
     }
-    const long long cnt = (long long)ex * ey * ez;
-    for (long long q = threadIdx.x; q < cnt; q += blockDim.x) {
-        int x = lo[0] + (int)(q % ex), y = lo[1] + (int)((q / ex) % ey), z = lo[2] + (int)(q / ((long long)ex * ey));
+    const int cnt = ex * ey * ez;
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const int qy = q / ex, qz = qy / ey;
+        const int x = lo[0] + (q - qy * ex), y = lo[1] + (qy - qz * ey), z = lo[2] + qz;
         T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
         if (staged) {
             for (int dz = (Lat<D>::dim == 3 ? -1 : 0); dz <= (Lat<D>::dim == 3 ? 1 : 0); dz++) {
