@@ -423,7 +423,11 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 P.W[0] = P.W[1] = 0.0;
             }
             P.nadj = ne;
-            for (int e = 0; e < ne && e < DEM_MAXA; e++) adj[l * DEM_MAXA + e] = ad[e];
+            // staged as (owning CTA << 16 | slot in it, pair): the substeps need no division
+            for (int e = 0; e < ne && e < DEM_MAXA; e++) {
+                const int q = ad[e].x, rq = q / per;
+                adj[l * DEM_MAXA + e] = make_int2((rq << 16) | (q - rq * per), ad[e].y);
+            }
             // every published field; for a free particle the second pass rewrites those that move
             publish_s(P, pub[l]);
         }
@@ -507,16 +511,17 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                     }
                     const int ne = P.nadj, e0 = ne > DEM_MAXA ? __ldcg(S.adj_start + p) : 0;
                     for (int e = sl; e < ne; e += tpp) {
-                        int q, kk;
+                        int rq, lq, kk;
                         if (ne <= DEM_MAXA) {
                             const int2 a = adj[l * DEM_MAXA + e];
-                            q = a.x, kk = a.y;
+                            rq = a.x >> 16, lq = a.x & 0xffff, kk = a.y;
                         } else {
-                            q = __ldcg(S.adj_nb + e0 + e), kk = __ldcg(S.adj_k + e0 + e);
+                            const int q = __ldcg(S.adj_nb + e0 + e);
+                            kk = __ldcg(S.adj_k + e0 + e);
+                            rq = q / per, lq = q - rq * per;
                         }
                         const bool first = kk >= 0;
                         const int k = first ? kk : ~kk;
-                        const int rq = q / per, lq = q - rq * per;
                         // every load of the slot at once: the neighbour's published state and
                         // radius (distributed shared memory) and the pair's tangential history
                         // (global; used only in contact), so their latencies overlap
