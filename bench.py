@@ -200,7 +200,8 @@ def measure_gpu(case, steps, warmup, torch, flush):
 
 
 def kernel_times(sim, steps, torch, flush):
-    """Per-kernel-group device times of un-graphed steps (CUDA events on each launching stream)."""
+    """Per-kernel-group device times: step-graph replays with CUDA event-record nodes around each
+    kernel group on its own stream (pibm_step_timed)."""
     out = []
     for k in range(steps):
         with torch.cuda.stream(sim.stream):

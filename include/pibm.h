@@ -201,9 +201,10 @@ pibm_status pibm_time(pibm_ctx* ctx, int64_t* t);
 pibm_status pibm_save(pibm_ctx* ctx, const char* path);
 pibm_status pibm_load(pibm_ctx* ctx, const char* path);
 
-/* One lattice step launched without a graph, with CUDA events around each
- * kernel group on the stream it runs on.  ms[0] collide-and-stream, ms[1] DEM,
- * ms[2] PIBM coupling, ms[3] the whole step (fork to join).  Synchronises. */
+/* One lattice step as a replay of the step graph with CUDA event-record nodes
+ * around each kernel group, on the stream the group runs on (the same kernels,
+ * streams and dependencies as pibm_step).  ms[0] collide-and-stream, ms[1] DEM,
+ * ms[2] PIBM coupling, ms[3] the whole step.  Synchronises. */
 pibm_status pibm_step_timed(pibm_ctx* ctx, double* ms);
 
 /* Particle model, set before pibm_set_particles:
@@ -349,7 +350,7 @@ pibm_status pibm_ensemble_box(pibm_ensemble* e, int b, pibm_ctx** out);
 pibm_status pibm_ensemble_step(pibm_ensemble* e, int nsteps);
 /* Kernels one ensemble step launches (sum over the boxes). */
 pibm_status pibm_ensemble_kernels_per_step(pibm_ensemble* e, int* n);
-/* Autotuner: for each box in turn, time reps un-graphed steps (CUDA events)
+/* Autotuner: for each box in turn, time reps steps (pibm_step_timed: graph replays with CUDA events)
  * of each of five candidate launch shapes -- PIBM_TUNE_LATTICE_THREADS in
  * {default, 64, 128, 256, 512} paired with PIBM_TUNE_DEM_PARTICLES_PER_CTA in
  * {default, 16, 48, 64, 96} (shapes a box cannot take time the default) --

@@ -287,7 +287,7 @@ class Simulation:
         self._check(self.L.pibm_step(self.h, int(n)), "pibm_step")
 
     def step_timed(self):
-        """One un-graphed step; returns per-kernel-group device times in ms:
+        """One step (a replay of the step graph with event-record nodes); returns per-kernel-group device times in ms:
         collide-and-stream, DEM, coupling, whole step."""
         ms = np.zeros(4)
         self._check(self.L.pibm_step_timed(self.h, _dp(ms)), "pibm_step_timed")

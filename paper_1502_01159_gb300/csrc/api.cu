@@ -95,6 +95,8 @@ static void drop_graphs(Ctx& c) {
     for (int p = 0; p < 2; p++) {
         if (c.graph_ok[p]) cudaGraphExecDestroy(c.graph[p]);
         c.graph_ok[p] = 0;
+        if (c.tgraph_ok[p]) cudaGraphExecDestroy(c.tgraph[p]);
+        c.tgraph_ok[p] = 0;
     }
 }
 
@@ -169,13 +171,17 @@ static pibm_status prime(pibm_ctx* ctx) {
 // branches touch disjoint data, so the DEM's latency-bound substeps, the
 // clear and the bandwidth-bound lattice kernel overlap; the step's critical
 // path is max(DEM, lattice) + coupling.
-cudaError_t pibm::record_step(Ctx* cp, int par, int* kernels_out) {
+cudaError_t pibm::record_step(Ctx* cp, int par, int* kernels_out, const cudaEvent_t* tev) {
     Ctx& c = *cp;
     cudaError_t e = cudaSuccess;
     int kernels = 1;
     auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    // tev (timing graph only): event-record nodes around each kernel group
+    auto mark = [&](int k, cudaStream_t s) { if (tev) chk(cudaEventRecordWithFlags(tev[k], s, cudaEventRecordExternal)); };
+    mark(0, c.s0);
     chk(cudaEventRecord(c.ev_fork, c.s0));
     chk(cudaStreamWaitEvent(c.s1, c.ev_fork, 0));
+    mark(2, c.s1);
     if (c.np > 0) {
         chk(launch_dem(&c, c.s1, c.desc.dem_substeps));  // particles t -> t+1, concurrent, launched first
         chk(cudaStreamWaitEvent(c.s2, c.ev_fork, 0));
@@ -183,16 +189,22 @@ cudaError_t pibm::record_step(Ctx* cp, int par, int* kernels_out) {
         chk(cudaEventRecord(c.ev_join2, c.s2));
         kernels++;
     }
+    mark(3, c.s1);
+    mark(7, c.s0);
     chk(launch_stream_collide(&c, c.s0, par));        // collide + stream, t -> t+1
+    mark(1, c.s0);
     chk(cudaEventRecord(c.ev_join, c.s1));
     chk(cudaStreamWaitEvent(c.s0, c.ev_join, 0));
     if (c.np > 0) chk(cudaStreamWaitEvent(c.s0, c.ev_join2, 0));
+    mark(4, c.s0);
     chk(launch_coupling(&c, c.s0, par ^ 1));         // coupling of time t+1
+    mark(5, c.s0);
     kernels += coupling_kernel_count(&c);
     if (c.sg.enabled && c.np > 0) {                  // surrogate Jacobian for the next step's DEM, judged by t+1's coupling
         chk(launch_surrogate(&c, c.s0, par ^ 1, false));  // the coupling left the feature sums
         kernels += surrogate_kernel_count(&c);
     }
+    mark(6, c.s0);
     if (kernels_out) *kernels_out = kernels;
     return e;
 }
@@ -333,6 +345,8 @@ pibm_status pibm_destroy(pibm_ctx* ctx) {
     if (c.ev_fork) cudaEventDestroy(c.ev_fork);
     if (c.ev_join) cudaEventDestroy(c.ev_join);
     if (c.ev_join2) cudaEventDestroy(c.ev_join2);
+    if (c.tev_ok)
+        for (int k = 0; k < 8; k++) cudaEventDestroy(c.tev[k]);
     if (c.s1) cudaStreamDestroy(c.s1);
     if (c.s2) cudaStreamDestroy(c.s2);
     if (c.own_s0 && c.s0) cudaStreamDestroy(c.s0);
@@ -678,22 +692,26 @@ pibm_status pibm_set_populations(pibm_ctx* ctx, const double* f, const double* g
     return prime(ctx);
 }
 
-static pibm_status capture(pibm_ctx* ctx, int par) {
+static pibm_status capture(pibm_ctx* ctx, int par, bool timed = false) {
     Ctx& c = ctx->c;
     cudaGraph_t graph;
     PCHECK(cudaStreamBeginCapture(c.s0, cudaStreamCaptureModeThreadLocal));
     int kernels = 0;
-    cudaError_t e = record_step(&c, par, &kernels);
+    cudaError_t e = record_step(&c, par, &kernels, timed ? c.tev : nullptr);
     cudaError_t e2 = cudaStreamEndCapture(c.s0, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (e2 == cudaSuccess) cudaGraphDestroy(graph);
         return fail(ctx, PIBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    e = cudaGraphInstantiate(&c.graph[par], graph, 0);
+    e = cudaGraphInstantiate(timed ? &c.tgraph[par] : &c.graph[par], graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(ctx, PIBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-    c.graph_ok[par] = 1;
-    c.kernels_per_step = kernels;
+    if (timed) {
+        c.tgraph_ok[par] = 1;
+    } else {
+        c.graph_ok[par] = 1;
+        c.kernels_per_step = kernels;
+    }
     return PIBM_OK;
 }
 
@@ -720,39 +738,22 @@ pibm_status pibm_step_timed(pibm_ctx* ctx, double* ms) {
     Ctx& c = ctx->c;
     pibm_status st = check_config(ctx);
     if (st != PIBM_OK) return st;
-    cudaEvent_t ev[8];
-    for (int k = 0; k < 8; k++) PCHECK(cudaEventCreate(&ev[k]));
-    int par = parity(c);
-    cudaError_t e = cudaSuccess;
-    auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-    chk(cudaEventRecord(ev[0], c.s0));
-    chk(cudaStreamWaitEvent(c.s1, ev[0], 0));
-    chk(cudaEventRecord(ev[2], c.s1));
-    chk(launch_dem(&c, c.s1, c.desc.dem_substeps));
-    chk(cudaEventRecord(ev[3], c.s1));
-    chk(cudaStreamWaitEvent(c.s2, ev[0], 0));
-    chk(launch_coupling_clear(&c, c.s2, par ^ 1));
-    chk(cudaEventRecord(ev[6], c.s2));
-    // the lattice kernel's own interval starts here, after the other branches were
-    // launched (host launch time is not the kernel's)
-    chk(cudaEventRecord(ev[7], c.s0));
-    chk(launch_stream_collide(&c, c.s0, par));
-    chk(cudaEventRecord(ev[1], c.s0));
-    chk(cudaStreamWaitEvent(c.s0, ev[3], 0));
-    chk(cudaStreamWaitEvent(c.s0, ev[6], 0));
-    chk(cudaEventRecord(ev[4], c.s0));
-    chk(launch_coupling(&c, c.s0, par ^ 1));
-    chk(cudaEventRecord(ev[5], c.s0));
-    chk(cudaEventSynchronize(ev[5]));
-    float t[4] = {0, 0, 0, 0};
-    if (e == cudaSuccess) {
-        chk(cudaEventElapsedTime(&t[0], ev[7], ev[1]));
-        chk(cudaEventElapsedTime(&t[1], ev[2], ev[3]));
-        chk(cudaEventElapsedTime(&t[2], ev[4], ev[5]));
-        chk(cudaEventElapsedTime(&t[3], ev[0], ev[5]));
+    if (!c.tev_ok) {
+        for (int k = 0; k < 8; k++) PCHECK(cudaEventCreate(&c.tev[k]));
+        c.tev_ok = 1;
     }
-    for (int k = 0; k < 8; k++) cudaEventDestroy(ev[k]);
-    if (e != cudaSuccess) return fail(ctx, PIBM_ERR_CUDA, std::string("timed step: ") + cudaGetErrorString(e));
+    const int par = parity(c);
+    if (!c.tgraph_ok[par]) {
+        st = capture(ctx, par, true);
+        if (st != PIBM_OK) return st;
+    }
+    PCHECK(cudaGraphLaunch(c.tgraph[par], c.s0));
+    PCHECK(cudaEventSynchronize(c.tev[6]));
+    float t[4] = {0, 0, 0, 0};
+    PCHECK(cudaEventElapsedTime(&t[0], c.tev[7], c.tev[1]));  // collide-and-stream
+    PCHECK(cudaEventElapsedTime(&t[1], c.tev[2], c.tev[3]));  // DEM
+    PCHECK(cudaEventElapsedTime(&t[2], c.tev[4], c.tev[5]));  // coupling
+    PCHECK(cudaEventElapsedTime(&t[3], c.tev[0], c.tev[6]));  // whole step
     for (int k = 0; k < 4; k++) ms[k] = t[k];
     c.t++;
     return device_status(ctx);

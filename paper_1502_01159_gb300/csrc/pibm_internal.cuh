@@ -348,6 +348,10 @@ struct Ctx {
     // CUDA graphs: one lattice step starting at even / odd time
     cudaGraphExec_t graph[2];
     int graph_ok[2];
+    cudaGraphExec_t tgraph[2];  // the step graph with event-record nodes around each kernel group (pibm_step_timed)
+    int tgraph_ok[2];
+    cudaEvent_t tev[8];         // its timing events (created on first use)
+    int tev_ok;
     int kernels_per_step;
 
     std::string err;
@@ -378,7 +382,7 @@ int dem_max_particles();
 void set_global_error(const std::string& msg);
 int dem_max_per_cta();
 // api.cu: for the ensemble (ensemble.cu)
-cudaError_t record_step(Ctx* c, int parity, int* kernels);
+cudaError_t record_step(Ctx* c, int parity, int* kernels, const cudaEvent_t* tev = nullptr);
 // surrogate.cu
 cudaError_t launch_mlp(Ctx* c, cudaStream_t s, const float* in, int rows, float* out);
 cudaError_t launch_surrogate(Ctx* c, cudaStream_t s, int parity, bool need_sums);
