@@ -491,6 +491,7 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
     }
     C.skin = cmin - 2.0 * rmax;
     c.spread_smem = spread_smem_bytes(c.D, rmax, c.v4);
+    c.rmax = rmax;
     C.cap = std::max(64, 16 * n);
     C.maxnb = 64;
     c.adj_cap = 2 * C.cap;

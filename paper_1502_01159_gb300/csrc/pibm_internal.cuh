@@ -329,6 +329,7 @@ struct Ctx {
     int tune_wide_index;             // 1: 64-bit slot offsets in the lattice kernel even where 32-bit suffice
     int dem_attr_ok;                 // the DEM kernel's launch attributes are set
     int spread_smem;                 // shared memory per CTA of the spread kernel (from the largest radius)
+    double rmax;                     // largest particle radius
     Surrogate sg;
     int lat;                         // lattice id: 2 D2Q9, 3 D3Q19, 4 D3Q15 (all with D2Q5 / D3Q7 thermal)
     int point;                       // particle model: 1 = one PIBM point per particle (d_p <= h)
