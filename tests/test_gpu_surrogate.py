@@ -60,6 +60,23 @@ def test_features_match_reference(dim):
     assert np.max(np.abs(fo[:, 0:3])) > 0  # the particles move relative to the fluid
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_features_with_one_cell_match_reference(dim):
+    # a cell as large as the box: the neighbour features take the all-pairs
+    # kernels instead of the cell scan (and the DEM's neighbour list holds every
+    # pair); the result is the same reference
+    case = _case(dim, seed=27)
+    case["cell_size"] = 1000.0
+    sim, orc = _sim(case), oracle.Oracle(case)
+    sim.step(10)
+    orc.step(10)
+    fg = sim.read_features()
+    fo = _oracle_features(orc, dim)
+    for k in range(7, 12):
+        scale = max(np.max(np.abs(fo[:, k])), 1e-12)
+        assert np.max(np.abs(fg[:, k] - fo[:, k])) <= 1e-5 * scale + 1e-6, (k, np.max(np.abs(fg[:, k] - fo[:, k])))
+
+
 def test_training_gradient_matches_fp64_backprop():
     sim = _sim(_case(3))
     gen = np.random.default_rng(5)
