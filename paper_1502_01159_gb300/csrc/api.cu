@@ -182,17 +182,32 @@ cudaError_t pibm::record_step(Ctx* cp, int par, int* kernels_out, const cudaEven
     chk(cudaEventRecord(c.ev_fork, c.s0));
     chk(cudaStreamWaitEvent(c.s1, c.ev_fork, 0));
     mark(2, c.s1);
+    // The clear of the other coupling set runs beside the lattice kernel when that kernel is the
+    // longer branch (it then costs nothing), and after it when the DEM is the longer branch (the
+    // lattice kernel then runs without the clear's CTAs in the way and the clear still ends
+    // before the DEM): estimated from the lattice kernel's bytes at 6.5 TB/s against ~2 us per
+    // DEM substep.
+    const double lattice_us = (double)c.G.N * 2.0 * (c.Q + c.QG) * (double)c.es / 6.5e6;
+    const bool clear_after = c.np > 0 && lattice_us < 2.0 * c.desc.dem_substeps;
     if (c.np > 0) {
         chk(launch_dem(&c, c.s1, c.desc.dem_substeps));  // particles t -> t+1, concurrent, launched first
-        chk(cudaStreamWaitEvent(c.s2, c.ev_fork, 0));
-        chk(launch_coupling_clear(&c, c.s2, par ^ 1));  // free the other coupling set (read at t-1)
-        chk(cudaEventRecord(c.ev_join2, c.s2));
+        if (!clear_after) {
+            chk(cudaStreamWaitEvent(c.s2, c.ev_fork, 0));
+            chk(launch_coupling_clear(&c, c.s2, par ^ 1));  // free the other coupling set (read at t-1)
+            chk(cudaEventRecord(c.ev_join2, c.s2));
+        }
         kernels++;
     }
     mark(3, c.s1);
     mark(7, c.s0);
     chk(launch_stream_collide(&c, c.s0, par));        // collide + stream, t -> t+1
     mark(1, c.s0);
+    if (clear_after) {
+        chk(cudaEventRecord(c.ev_k1, c.s0));
+        chk(cudaStreamWaitEvent(c.s2, c.ev_k1, 0));
+        chk(launch_coupling_clear(&c, c.s2, par ^ 1));
+        chk(cudaEventRecord(c.ev_join2, c.s2));
+    }
     chk(cudaEventRecord(c.ev_join, c.s1));
     chk(cudaStreamWaitEvent(c.s0, c.ev_join, 0));
     if (c.np > 0) chk(cudaStreamWaitEvent(c.s0, c.ev_join2, 0));
@@ -294,7 +309,8 @@ pibm_status pibm_create(const pibm_desc* d, void* stream, const pibm_allocator* 
         (e = cudaStreamCreateWithPriority(&c.s2, cudaStreamNonBlocking, prio_hi)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&c.ev_join2, cudaEventDisableTiming)) != cudaSuccess) {
+        (e = cudaEventCreateWithFlags(&c.ev_join2, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c.ev_k1, cudaEventDisableTiming)) != cudaSuccess) {
         delete ctx;
         return g_create_error = cudaGetErrorString(e), PIBM_ERR_CUDA;
     }
@@ -345,6 +361,7 @@ pibm_status pibm_destroy(pibm_ctx* ctx) {
     if (c.ev_fork) cudaEventDestroy(c.ev_fork);
     if (c.ev_join) cudaEventDestroy(c.ev_join);
     if (c.ev_join2) cudaEventDestroy(c.ev_join2);
+    if (c.ev_k1) cudaEventDestroy(c.ev_k1);
     if (c.tev_ok)
         for (int k = 0; k < 8; k++) cudaEventDestroy(c.tev[k]);
     if (c.s1) cudaStreamDestroy(c.s1);

@@ -284,7 +284,7 @@ struct Ctx {
     cudaStream_t s0;  // caller's stream
     cudaStream_t s1;  // internal stream for the DEM branch
     cudaStream_t s2;  // internal stream for the clear of the previous coupling set
-    cudaEvent_t ev_fork, ev_join, ev_join2;
+    cudaEvent_t ev_fork, ev_join, ev_join2, ev_k1;
     pibm_allocator alloc;
     int own_s0;  // 1 if the library created s0
 
