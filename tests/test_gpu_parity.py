@@ -375,6 +375,23 @@ def test_wide_and_narrow_slot_offsets_agree(storage, ci):
         assert np.array_equal(fa, fb_) and np.array_equal(ga, gb_), (storage, case["shape"], k)
 
 
+def test_timed_steps_match_plain_steps():
+    # pibm_step_timed replays a copy of the step graph with event-record nodes:
+    # the same kernels, so the same state bit for bit, and positive group times
+    case = _small_sed2d()
+    a, b = _sim(case), _sim(case)
+    for _ in range(7):
+        a.step(1)
+        t = b.step_timed()
+        assert all(t[k] > 0 for k in ("stream_collide", "dem", "coupling", "step")), t
+        assert t["step"] >= t["stream_collide"] and t["step"] >= t["coupling"], t
+    fa, ga = a.read_populations()
+    fb_, gb_ = b.read_populations()
+    assert np.array_equal(fa, fb_) and np.array_equal(ga, gb_)
+    pa, pb = a.read_particles(), b.read_particles()
+    assert all(np.array_equal(pa[k], pb[k]) for k in pa)
+
+
 def test_checkpoint_resume_bit_exact(tmp_path):
     # 50 steps, save, 50 more; a fresh context loaded from the checkpoint and
     # stepped 50 times reaches exactly the same state
