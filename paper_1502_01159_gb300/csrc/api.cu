@@ -215,7 +215,7 @@ cudaError_t pibm::record_step(Ctx* cp, int par, int* kernels_out, const cudaEven
     chk(launch_coupling(&c, c.s0, par ^ 1));         // coupling of time t+1
     mark(5, c.s0);
     kernels += coupling_kernel_count(&c);
-    if (c.sg.enabled && c.np > 0) {                  // surrogate Jacobian for the next step's DEM, judged by t+1's coupling
+    if (c.sg.enabled && c.np > 0) {                  // surrogate Jacobian for the next step's DEM, checked against t+1's coupling
         chk(launch_surrogate(&c, c.s0, par ^ 1, false));  // the coupling left the feature sums
         kernels += surrogate_kernel_count(&c);
     }

@@ -6,8 +6,9 @@
 // particle's velocity and spin corrects the hydrodynamic load held over the
 // lattice step (Eq demgov; the held load is the mean of two couplings, and a
 // velocity change enters the newer one); the PIBM coupling computed every
-// step is the judge, and the correction is switched off for the next step
-// whenever the network's force differs from it by more than the bound.
+// step is the reference it is checked against, and the correction is switched
+// off for the next step whenever the network's force differs from it by more
+// than the bound.
 //
 //   inference  k_mlp_tc: tcgen05 BF16 tensor-core MMAs (M = 128 rows per CTA,
 //              N = 64 / 16, K = 16 / 64), FP32 accumulators in tensor memory,
