@@ -167,23 +167,29 @@ __global__ void __launch_bounds__(CP_THREADS, (Lat<D>::dim == 2 && !FEAT) ? 4 : 
         }
     }
     // the neighbours' centres and radii, staged by the other warps while the first
-    // sets up the particle: one (neighbour, axis or radius) per thread
+    // sets up the particle: one (neighbour, axis or radius) per thread, with the
+    // centre relative to p's base node floor(X_p) (each thread forms that axis's
+    // base by the same exact rule as the set-up)
     for (int t = (int)threadIdx.x - 32; t >= 0 && t < 4 * nnb; t += (int)blockDim.x - 32) {
         const int k = t >> 2, a = t & 3;
         const int q = adj_nb[a0 + k];
         if (a == 0) sh_id[k] = q;
-        sh_nb[k][a] = a < 3 ? X[3 * q + a] : Rr[q];
+        const double v = a < 3 ? X[3 * q + a] : Rr[q];
+        sh_nb[k][a] = v;
+        if (a < 3) {
+            int blo = 0, bhi = 0, b = 0;
+            if (a < Lat<D>::dim) {
+                const int n = a == 0 ? G.nx : (a == 1 ? G.ny : G.nz);
+                axis_box(Xp[a], (float)Xp[a], Rp, (float)Rp, n, &blo, &bhi, &b);
+            }
+            sh_nbf[k][a] = (float)(v - (double)b);
+        } else {
+            sh_nbf[k][3] = (float)v;
+        }
     }
     __syncthreads();
     const int base[3] = {s_base[0], s_base[1], s_base[2]};
     const float cf[3] = {s_cf[0], s_cf[1], s_cf[2]};
-    // neighbour centres relative to p's base node (FP32 for the ownership estimates)
-    for (int t = threadIdx.x; t < 4 * nnb; t += blockDim.x) {
-        const int k = t >> 2, a = t & 3;
-        const double v = sh_nb[k][a];
-        sh_nbf[k][a] = (float)(a < 3 ? v - (double)base[a] : v);
-    }
-    __syncthreads();
     const int lo[3] = {s_box[0], s_box[1], s_box[2]}, hi[3] = {s_box[3], s_box[4], s_box[5]};
     int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
     const int cnt = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;  // 32-bit: boxes of R <= 600

@@ -428,8 +428,10 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 const int q = ad[e].x, rq = q / per;
                 adj[l * DEM_MAXA + e] = make_int2((rq << 16) | (q - rq * per), ad[e].y);
             }
-            // every published field; for a free particle the second pass rewrites those that move
+            // every published field, in both buffers; for a free particle the second pass
+            // rewrites those that move
             publish_s(P, pub[l]);
+            publish_s(P, pub[per + l]);
         }
         __syncthreads();
         // Accelerations and the opening half kick + drift, one (component, particle) per
@@ -461,18 +463,17 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             const double v = V + (double)inc;
             V = v;
             Pub& out = pub[l];
+            Pub& out2 = pub[per + l];  // both buffers: substep 0 reads one, its drift writes the other
             if (lin) {
                 const double xn = P.X[a] + dt * v;
                 P.X[a] = xn;
-                out.x[a] = xn;
-                out.xf[a] = (float)xn;
-                out.u[a] = (float)v;
+                out.x[a] = out2.x[a] = xn;
+                out.xf[a] = out2.xf[a] = (float)xn;
+                out.u[a] = out2.u[a] = (float)v;
             } else {
-                out.w[a] = (float)v;
+                out.w[a] = out2.w[a] = (float)v;
             }
         }
-        __syncthreads();
-        for (int l = threadIdx.x; l < nloc; l += blockDim.x) pub[per + l] = pub[l];  // both buffers
         cl.sync();
         for (int sub = 0; sub < nsub; sub++) {
             const int rb = sub & 1;                      // published buffer read this substep
