@@ -689,8 +689,8 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
         if (threadIdx.x == 0) need_flag = moved;
         if (gt == 0) *S.have_prev = 1;
         cl.sync();
-        int need = 0;
-        for (unsigned r = 0; r < csize; r++) need |= *cl.map_shared_rank(&need_flag, r);
+        // thread r reads CTA r's flag (16 remote loads per CTA, not one per thread and CTA)
+        const int need = __syncthreads_or(threadIdx.x < csize ? *cl.map_shared_rank(&need_flag, threadIdx.x) : 0);
         if (!need) {
             cl.sync();  // no CTA may exit while others still read its shared memory
             if (gt == 0) S.nb_cur[1] = gnow;
