@@ -580,13 +580,15 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 if (!active) continue;
                 const int p = base + l;
                 Priv& P = prv[l];
-                if (sl == 0)
+                const bool last = sub + 1 == nsub;  // closing half kick only; else also the next opening one
+                // the contact sums are read from shared memory only by the write-back (and by
+                // the learned-Jacobian kick below); the per-component kick takes the registers
+                if (sl == 0 && (last || useJ))
                     for (int a = 0; a < 3; a++) {
                         P.Fc[a] = F[a];
                         P.Tc[a] = T[a];
                     }
                 if (P.fixed) continue;  // published into both buffers at the load
-                const bool last = sub + 1 == nsub;  // closing half kick only; else also the next opening one
                 if (useJ) {  // the learned Jacobian couples the components: one thread per particle
                     if (sl != 0) continue;
                     const float* Jp = C.J + 18 * p;
