@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(CP_THREADS, (Lat<D>::dim == 2 && !FEAT) ? 4 : 
     __syncthreads();
     if (threadIdx.x < (FEAT ? 24 : 7)) {
         double v = 0;
-        for (int w = 0; w < CP_THREADS / 32; w++) v += red[threadIdx.x][w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[threadIdx.x][w];
         if (threadIdx.x < 3) Fh[3 * p + threadIdx.x] = v;
         else if (threadIdx.x < 6) Th[3 * p + threadIdx.x - 3] = v;
         else if (threadIdx.x == 6) Hh[p] = v;
@@ -648,6 +648,18 @@ __global__ void __launch_bounds__(CP_THREADS) k_points(Geo G, const S* __restric
             }
 }
 
+// Threads per footprint CTA: in 2-D a box of the largest particle holds at most
+// (floor(2 R_max) + 2)^2 nodes, so a block of that many threads (rounded up to
+// whole warps, at least two: the set-up warp and a staging warp) covers it in one
+// pass without idle warps in the barriers and the block reduction; 3-D boxes take
+// several nodes per thread in blocks of CP_THREADS.
+static int footprint_threads(const Ctx* c) {
+    if (c->D != 2) return CP_THREADS;
+    const long long e = (long long)floor(2.0 * c->rmax) + 2;
+    const long long t = (e * e + 31) / 32 * 32;
+    return (int)(t < 64 ? 64 : (t > CP_THREADS ? CP_THREADS : t));
+}
+
 template <int D, typename S>
 static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
     using V = typename Store<S>::V4;
@@ -658,11 +670,11 @@ static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
             (V*)c->fb[parity], c->flags[parity], c->box[parity], c->Fh, c->Th, c->Hh);
     } else if (c->np > 0) {
         if (c->sg.enabled)  // the surrogate's feature sums ride along
-            k_footprint<D, S, true><<<c->np, CP_THREADS, 0, s>>>(
+            k_footprint<D, S, true><<<c->np, footprint_threads(c), 0, s>>>(
                 c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk[parity], c->X, c->U, c->W, c->R, c->Tp, c->adj_start,
                 c->adj_nb, c->desc.kappa_T, c->desc.T_ref, parity, c->Fh, c->Th, c->Hh, c->sg.fsum);
         else
-            k_footprint<D, S, false><<<c->np, CP_THREADS, 0, s>>>(
+            k_footprint<D, S, false><<<c->np, footprint_threads(c), 0, s>>>(
                 c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk[parity], c->X, c->U, c->W, c->R, c->Tp, c->adj_start,
                 c->adj_nb, c->desc.kappa_T, c->desc.T_ref, parity, c->Fh, c->Th, c->Hh, nullptr);
         // programmatic dependent launch: the spread's CTAs start (and set up their boxes)
@@ -703,7 +715,7 @@ template <int D, typename S>
 static cudaError_t footprint_sums_impl(Ctx* c, cudaStream_t s, int parity) {
     using V = typename Store<S>::V4;
     if (!c->desc.pibm || c->np <= 0) return cudaSuccess;
-    k_footprint<D, S, true><<<c->np, CP_THREADS, 0, s>>>(c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk[parity], c->X,
+    k_footprint<D, S, true><<<c->np, footprint_threads(c), 0, s>>>(c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk[parity], c->X,
                                                          c->U, c->W, c->R, c->Tp, c->adj_start, c->adj_nb, c->desc.kappa_T,
                                                          c->desc.T_ref, parity, c->Fh, c->Th, c->Hh, c->sg.fsum);
     return cudaGetLastError();
