@@ -1,19 +1,23 @@
 #!/usr/bin/env python3
 """Throughput of the fused LBM-PIBM-DEM lattice step on one GB300 per rank.
 
-Default workload: 2-D sedimentation of 500 heated disks (diameter 10 lattice
-units) in a 512 x 1024 cavity, D2Q9 + D2Q5, FP32 storage, spring-dashpot DEM
-with 10 substeps per lattice step.  One "step" = one lattice step: fused
-collide-and-stream, DEM substeps (concurrent branch), PIBM coupling.  The
-metric is fluid+thermal lattice-node updates per second (MLUPS), plus
-particle-steps/s; the 29 MB state fits in L2, so L2 is flushed (256 MB write)
-between timed steps and each step is timed on its own with CUDA events.
+Default workload: 3-D thermosensitive sedimentation of 10 000 spheres
+(diameter 6 lattice units) in a 384^3 walled box, D3Q19 + D3Q7 with FP32
+population storage, Hertz / Mindlin-Deresiewicz DEM with 10 substeps per
+lattice step (the largest single-GPU configuration).  One "step" = one
+lattice step: fused collide-and-stream, DEM substeps (concurrent branch),
+PIBM coupling.  The metric is fluid+thermal lattice-node updates per second
+(MLUPS), plus particle-steps/s; L2 is flushed (256 MB write) before every
+timed step and each step is timed on its own with CUDA events.  The 16-bit
+storage forms, the 256x256x512 and 2-D cases, the batched ensemble and the
+learned surrogate are reported as extra keys of the same line.
 
 Under torchrun each rank runs an independent replica on its own GPU (the
 method does not shard here: replicas only); value = all ranks' node updates /
 the slowest rank's time.
 
---impl reference times the FP64 CPU oracle on the same workload (rank 0 only).
+--impl reference times the FP64 CPU oracle on the workload's bounded sample
+(the 64^3 crop of the 384^3 case at its number density; rank 0 only).
 """
 from __future__ import annotations
 
@@ -26,6 +30,8 @@ import subprocess
 import sys
 import tempfile
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -43,23 +49,71 @@ def bytes_per_node(case) -> int:
     return 2 * q * es
 
 
+HEAT_CAP_D6 = 1.2 * 4.0 / 3.0 * np.pi * 27.0  # rho_p V_p of a sphere of diameter 6 (specific heat ratio 1)
+STORAGE_NAME = {"f32": "FP32", "f16": "FP16-deviation storage (FP32 arithmetic)",
+                "bf16": "BF16-deviation storage (FP32 arithmetic)", "f64": "FP64"}
+
+
 def workload(name: str, storage: str = "f32"):
+    """(case dict, description) of a named workload; every placement is seeded."""
     import workloads as W
-    if name == "sed2d":
+    st = STORAGE_NAME[storage]
+    if name == "sed3d384":
+        case = W.sed3d(nx=384, ny=384, nz=384, n_p=10000, d=6.0, config_index=4, heat_cap=HEAT_CAP_D6,
+                       T_p_random=True)
+        desc = (f"sed3d384: 3-D thermosensitive sedimentation, 384^3 lattice, 10000 spheres d=6, "
+                f"D3Q19+D3Q7 {st}, Hertz/Mindlin, 10 DEM substeps")
+    elif name == "sed3d384_crop":
+        case = W.sed3d(nx=64, ny=64, nz=64, n_p=46, d=6.0, config_index=4, heat_cap=HEAT_CAP_D6, T_p_random=True)
+        desc = (f"sed3d384 crop: 64^3 lattice, 46 spheres d=6 (the 384^3 case's number density), thermosensitive, "
+                f"D3Q19+D3Q7 {st}, Hertz/Mindlin, 10 DEM substeps")
+    elif name == "sed2d":
         case = W.sed2d()
-        desc = "sed2d: 2-D sedimentation, 512x1024 lattice, 500 heated disks d=10, D2Q9+D2Q5 FP32, spring-dashpot, 10 DEM substeps"
+        desc = f"sed2d: 2-D sedimentation, 512x1024 lattice, 500 heated disks d=10, D2Q9+D2Q5 {st}, spring-dashpot, 10 DEM substeps"
     elif name == "sed3d":
         case = W.sed3d()
-        desc = "sed3d: 3-D sedimentation, 256x256x512 lattice, 2000 heated spheres d=8, D3Q19+D3Q7 FP32, Hertz, 10 DEM substeps"
+        desc = f"sed3d: 3-D sedimentation, 256x256x512 lattice, 2000 heated spheres d=8, D3Q19+D3Q7 {st}, Hertz/Mindlin, 10 DEM substeps"
+    elif name == "sed3d_crop":
+        case = W.sed3d(nx=64, ny=64, nz=128, n_p=62, config_index=2)
+        desc = f"sed3d crop: 64x64x128 lattice, 62 heated spheres d=8 (the 256x256x512 case's number density), D3Q19+D3Q7 {st}, Hertz/Mindlin"
     elif name == "sed3d_mid":
         case = W.sed3d(nx=128, ny=128, nz=256, n_p=250)
-        desc = "sed3d_mid: 3-D sedimentation, 128x128x256 lattice, 250 heated spheres d=8, D3Q19+D3Q7 FP32, Hertz, 10 DEM substeps (profiling size)"
+        desc = f"sed3d_mid: 3-D sedimentation, 128x128x256 lattice, 250 heated spheres d=8, D3Q19+D3Q7 {st}, Hertz/Mindlin (profiling size)"
+    elif name == "sed3d384_mid":
+        case = W.sed3d(nx=192, ny=192, nz=192, n_p=1250, d=6.0, config_index=4, heat_cap=HEAT_CAP_D6, T_p_random=True)
+        desc = f"sed3d384_mid: 192^3 lattice, 1250 thermosensitive spheres d=6, D3Q19+D3Q7 {st} (profiling size)"
     else:
         raise SystemExit(f"unknown workload {name}")
-    if storage != "f32":
-        case["storage"] = storage
-        desc = desc.replace("FP32", f"{storage.upper()}-deviation storage (FP32 arithmetic)")
+    case["storage"] = storage
     return case, desc
+
+
+# bounded CPU sample of each workload (the oracle runs FP64 on one core)
+CROP = {"sed3d384": "sed3d384_crop", "sed3d": "sed3d_crop", "sed3d384_mid": "sed3d384_crop",
+        "sed3d_mid": "sed3d_crop", "sed2d": "sed2d"}
+
+
+def cpu_info() -> dict:
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"cpu_model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count(),
+            "machine": platform.machine()}
 
 
 def peaks():
@@ -156,9 +210,33 @@ def oracle_run(case, steps, warmup):
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
+    o.close()
     nodes = case["shape"][0] * case["shape"][1] * case["shape"][2]
     n_p = len(case["particles"]["R"]) if case.get("particles") else 0
     return nodes * steps / dt / 1e6, n_p * steps / dt, dt
+
+
+def oracle_baselines() -> dict:
+    """The FP64 single-threaded oracle on the bounded CPU samples of every
+    workload family: the cavity in full (2000 steps), 200 steps of the 2-D
+    sedimentation case, the 64x64x128 crop of the 3-D case (100 steps), one
+    64^3 box of the ensemble (100 steps) and the 64^3 crop of the 384^3 case
+    (100 steps).  Run in its own process beside the GPU measurements."""
+    import workloads as W
+    runs = []
+    cav = W.cavity(n=128, Ar=2.5, storage="f64")
+    runs.append(("cavity 128^2 (Ra 1e4, Ar 2.5, 8235 static points), in full", cav, 2000))
+    runs.append(("sed2d 512x1024, 500 disks", workload("sed2d")[0], 200))
+    runs.append(("sed3d crop 64x64x128, 62 spheres", workload("sed3d_crop")[0], 100))
+    box = next(c for c in W.ensemble() if c["shape"][0] == 64)
+    runs.append((f"ensemble box {box['name']}", box, 100))
+    runs.append(("sed3d384 crop 64^3, 46 thermosensitive spheres", workload("sed3d384_crop")[0], 100))
+    out = []
+    for what, case, steps in runs:
+        mlups, psps, dt = oracle_run(case, steps, 1)
+        out.append({"case": what, "steps": steps, "MLUPS": round(mlups, 4), "particle_steps_per_s": round(psps, 1),
+                    "seconds": round(dt, 2)})
+    return {"cores": 1, "kind": "oracle", "precision": "f64", **cpu_info(), "runs": out}
 
 
 def run_reference(args):
@@ -166,16 +244,19 @@ def run_reference(args):
     if rank != 0:
         return
     case, desc = workload(args.workload, args.storage)
-    mlups, psps, dt = oracle_run(case, args.steps, args.warmup)
-    sample = f"{args.steps} lattice steps (after {args.warmup} untimed) of the full {args.workload} workload"
+    crop, crop_desc = workload(CROP[args.workload], args.storage)
+    mlups, psps, dt = oracle_run(crop, args.steps, args.warmup)
+    sample = (f"{args.steps} lattice steps (after {args.warmup} untimed) of {crop_desc}, the bounded CPU sample of "
+              f"{args.workload}")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": desc, "implementation": "FP64 single-threaded C oracle on the host"},
+        "config": {"workload": desc, "implementation": "FP64 single-threaded C oracle on the host", "sample": crop_desc},
         "particle_steps_per_s": round(psps, 2),
-        "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample,
+                         **cpu_info()},
         "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -212,22 +293,23 @@ def kernel_times(sim, steps, torch, flush):
 
 
 def e2e_run(case, steps, torch):
-    """Whole job through the public API with host buffers: create, upload the
-    initial populations from pinned host memory, then per step: step + read
-    the particle state back; finally read the temperature field."""
-    import numpy as np
-
-    import workloads as W
+    """Whole job through the public API with host buffers: create the context
+    (lattice at rest equilibrium, walls, contact law) and upload the particle
+    set from pinned host memory; then per step: one lattice step and a
+    read-back of the particle state (positions, velocities, spins,
+    temperatures); finally the temperature field."""
     from paper_1502_01159_gb300 import Simulation
-    f0, g0 = W.random_populations(case, amp=0.0)
-    fp = torch.empty(f0.size, dtype=torch.float64, pin_memory=True).numpy()
-    gp = torch.empty(g0.size, dtype=torch.float64, pin_memory=True).numpy()
-    fp[:] = f0.ravel()
-    gp[:] = g0.ravel()
+    parts = {}
+    for k, v in case["particles"].items():
+        a = np.ascontiguousarray(np.asarray(v, dtype=np.uint8 if k == "fixed" else np.float64))
+        pin = torch.empty(a.shape, dtype=torch.uint8 if k == "fixed" else torch.float64, pin_memory=True).numpy()
+        pin[...] = a
+        parts[k] = pin
+    c2 = dict(case)
+    c2["particles"] = parts
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim = Simulation(case)
-    sim.set_populations(fp, gp)
+    sim = Simulation(c2)
     n_p = sim.np
     d2h = 0
     for _ in range(steps):
@@ -238,72 +320,91 @@ def e2e_run(case, steps, torch):
     d2h += T.nbytes
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    h2d = fp.nbytes + gp.nbytes + n_p * 8 * 14
+    h2d = sum(v.nbytes for v in parts.values())
     nodes = case["shape"][0] * case["shape"][1] * case["shape"][2]
     sim.close()
-    return {"value": round(nodes * steps / dt / 1e6, 3), "unit": "MLUPS",
-            "h2d_bytes_per_step": int(h2d // steps), "d2h_bytes_per_step": int(d2h // steps),
-            "what": "create + upload of the initial populations and particles from host memory, "
-                    "then per step: step + particle state read-back; final temperature field read-back"}
+    return {"value": round(nodes * steps / dt / 1e6, 3), "unit": "MLUPS", "steps": steps, "seconds": round(dt, 4),
+            "particles": n_p, "h2d_bytes_per_step": int(h2d // steps), "d2h_bytes_per_step": int(d2h // steps),
+            "what": "create (device allocation, lattice at rest equilibrium) + upload of the particle set from pinned "
+                    "host memory, then per step: pibm_step + particle state read-back; final temperature field "
+                    "read-back"}
 
 
-def precision_study(torch, flush):
-    """Reduced-precision storage (FP16 / BF16 deviations, FP32 arithmetic) against
-    the plain FP32 form: throughput of the fused lattice kernel and of the whole
-    step on the full sed3d workload, and the error against the FP64 oracle on a
-    64x64x128 sedimentation crop (31 spheres, the full case's solid fraction;
-    50 steps) with the same recipe.  The 16-bit kernel's two-nodes-per-thread
-    form is timed beside the default one-node-per-thread form."""
-    import numpy as np
-
+def _crop_errors(crop, storages, steps=50):
+    """Relative L2 error per field and largest particle offset of the GPU path
+    in each storage form against the FP64 oracle after `steps` steps."""
     import oracle
-    import workloads as W
     from paper_1502_01159_gb300 import Simulation
-    out = {}
-    from paper_1502_01159_gb300 import TUNE_PAIR_LATTICE
-    crop = W.sed3d(nx=64, ny=64, nz=128, n_p=31, config_index=2)
-    crop["g_particle"] = [0.0, 0.0, -2e-4]
     orc = oracle.Oracle(crop)
-    orc.step(50)
+    orc.step(steps)
     ref = {k: orc.field(k) for k in ("rho", "T", "ux", "uy", "uz")}
-    refX = orc.particles()["X"]
+    refP = orc.particles()
     orc.close()
-    nodes = 256 * 256 * 512
-    for storage in ("f32", "f16", "bf16"):
-        case = W.sed3d()
-        case["storage"] = storage
-        sim, ms = measure_gpu(case, 8, 3, torch, flush)
-        kt = kernel_times(sim, 5, torch, flush)
-        kt_pair = None
-        if storage != "f32":
-            sim.set_tuning(TUNE_PAIR_LATTICE, 1)
-            kt_pair = kernel_times(sim, 5, torch, flush)["stream_collide"]
-        sim.close()
+
+    def rl2(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    out = {}
+    for storage in storages:
         c2 = dict(crop)
         c2["storage"] = storage
         s2 = Simulation(c2)
-        s2.step(50)
-
-        def rl2(a, b):
-            return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        s2.step(steps)
+        p = s2.read_particles()
         err = {"rho": rl2(s2.read_field("rho"), ref["rho"]), "T": rl2(s2.read_field("T"), ref["T"]),
                "u": rl2(np.stack([s2.read_field(c) for c in ("ux", "uy", "uz")]),
                         np.stack([ref[c] for c in ("ux", "uy", "uz")])),
-               "X_max_abs": float(np.max(np.abs(s2.read_particles()["X"] - refX)))}
+               "X_max_abs": float(np.max(np.abs(p["X"] - refP["X"]))),
+               "T_p_max_abs": float(np.max(np.abs(p["T_p"] - refP["T_p"])))}
         s2.close()
-        step = statistics.mean(ms)
-        bpn = bytes_per_node(case)
-        out[storage] = {"step_ms": round(step, 4), "MLUPS": round(nodes / (step * 1e-3) / 1e6, 1),
-                        "stream_collide_ms": round(kt["stream_collide"], 4),
-                        "stream_collide_GBs": round(nodes * bpn / (kt["stream_collide"] * 1e-3) / 1e9, 1),
-                        "bytes_per_node": bpn,
-                        "error_vs_fp64_oracle_crop": {k: float(f"{v:.3g}") for k, v in err.items()}}
-        if kt_pair is not None:
-            out[storage]["stream_collide_ms_two_nodes_per_thread"] = round(kt_pair, 4)
-    for storage in ("f16", "bf16"):
-        out[storage]["speedup_step_vs_f32"] = round(out["f32"]["step_ms"] / out[storage]["step_ms"], 3)
-        out[storage]["speedup_kernel_vs_f32"] = round(out["f32"]["stream_collide_ms"] / out[storage]["stream_collide_ms"], 3)
-    out["workload"] = "sed3d full size for speed; 64x64x128 crop, 31 spheres, 50 steps for the error"
+        out[storage] = {k: float(f"{v:.3g}") for k, v in err.items()}
+    return out
+
+
+def precision_study(torch, flush, head=None):
+    """Reduced-precision storage (FP16 / BF16 deviations, FP32 arithmetic) against
+    the plain FP32 form: step and lattice-kernel throughput on the full 384^3
+    case (whose FP32 numbers are the headline's) and on the 256x256x512 case,
+    and the error against the FP64 oracle on each case's crop (64^3 with 46
+    spheres; 64x64x128 with 31 spheres) after 50 steps with the same recipe."""
+    from paper_1502_01159_gb300 import TUNE_LATTICE_ROW_TILES
+    out = {}
+    for wl, crop_name in (("sed3d384", "sed3d384_crop"), ("sed3d", "sed3d_crop")):
+        res = {}
+        nodes = None
+        for storage in ("f32", "f16", "bf16"):
+            if storage == "f32" and wl == "sed3d384" and head is not None:
+                res["f32"] = dict(head)
+                continue
+            case, _ = workload(wl, storage)
+            nodes = case["shape"][0] * case["shape"][1] * case["shape"][2]
+            sim, ms = measure_gpu(case, 8, 3, torch, flush)
+            kt = kernel_times(sim, 6, torch, flush)
+            # the same kernel with blocks that divide the row, for comparison
+            sim.set_tuning(TUNE_LATTICE_ROW_TILES, 1)
+            kt_np = kernel_times(sim, 6, torch, flush)["stream_collide"]
+            sim.close()
+            step = statistics.mean(ms)
+            bpn = bytes_per_node(case)
+            res[storage] = {"step_ms": round(step, 4), "MLUPS": round(nodes / (step * 1e-3) / 1e6, 1),
+                            "stream_collide_ms": round(kt["stream_collide"], 4),
+                            "stream_collide_GBs": round(nodes * bpn / (kt["stream_collide"] * 1e-3) / 1e9, 1),
+                            "bytes_per_node": bpn}
+            res[storage]["stream_collide_ms_row_tiles"] = round(kt_np, 4)
+        crop, _ = workload(crop_name)
+        if crop_name == "sed3d_crop":
+            import workloads as W
+            crop = W.sed3d(nx=64, ny=64, nz=128, n_p=31, config_index=2)
+        crop["g_particle"] = [0.0, 0.0, -2e-4]
+        errs = _crop_errors(crop, ("f32", "f16", "bf16"))
+        for storage in ("f32", "f16", "bf16"):
+            res[storage]["error_vs_fp64_oracle_crop"] = errs[storage]
+        for storage in ("f16", "bf16"):
+            res[storage]["speedup_step_vs_f32"] = round(res["f32"]["step_ms"] / res[storage]["step_ms"], 3)
+            res[storage]["speedup_kernel_vs_f32"] = round(res["f32"]["stream_collide_ms"] /
+                                                          res[storage]["stream_collide_ms"], 3)
+        res["error_sample"] = (f"{crop['shape'][0]}x{crop['shape'][1]}x{crop['shape'][2]} crop, "
+                               f"{len(crop['particles']['R'])} spheres, 50 steps, against the FP64 oracle")
+        out[wl] = res
     return out
 
 
@@ -382,10 +483,8 @@ def surrogate_study(torch, flush, steps):
     and the gate's verdict at a 1% force-error bound is reported."""
     import numpy as np
 
-    import workloads as W
     from paper_1502_01159_gb300 import Simulation
-    case = W.sed3d(nx=384, ny=384, nz=384, n_p=10000, d=6.0, storage="bf16", config_index=4,
-                   heat_cap=1.2 * 4.0 / 3.0 * np.pi * 27.0, T_p_random=True)
+    case, _ = workload("sed3d384", "bf16")
     nodes = 384 ** 3
     sim = Simulation(case)
 
@@ -443,6 +542,12 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    solo = rank == 0 and world == 1
+    # the oracle baselines run in a process of their own (started before the first GPU call)
+    bg = None
+    if solo and not args.no_oracle_baselines:
+        bg = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-baselines-json"],
+                              stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -457,13 +562,15 @@ def run_ours(args):
     nodes = case["shape"][0] * case["shape"][1] * case["shape"][2]
     n_p = len(case["particles"]["R"]) if case.get("particles") else 0
 
-    # CPU baseline first (before the first GPU call of the timed part), rank 0 at N = 1 only
+    # CPU baseline: the oracle on the workload's bounded sample, rank 0 at N = 1 only
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if solo and not args.no_cpu_baseline:
+        crop, crop_desc = workload(CROP[args.workload], args.storage)
         cs = max(1, args.cpu_steps)
-        mlups, psps, dt = oracle_run(case, cs, 1)
+        mlups, psps, dt = oracle_run(crop, cs, 1)
         cpu = {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"{cs} lattice steps of the full {args.workload} workload ({dt:.1f} s, FP64, 1 thread)"}
+               "sample": f"{cs} lattice steps of {crop_desc} ({dt:.1f} s, FP64, 1 thread)",
+               "particle_steps_per_s": round(psps, 1), **cpu_info()}
 
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     uuid = None
@@ -480,6 +587,7 @@ def run_ours(args):
     sim, ms = measure_gpu(case, args.steps, args.warmup, torch, flush)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
+    kt = kernel_times(sim, max(6, args.steps // 2), torch, flush)
     clocks = sampler.stop()
     ms_step = statistics.mean(ms)
     if world > 1:
@@ -488,16 +596,24 @@ def run_ours(args):
     value = job_throughput(world, nodes, ms_step)
     kps = sim.kernels_per_step()
 
-    kt = kernel_times(sim, max(5, args.steps // 2), torch, flush)
     peak, peak_kind = peaks()
     bpn = bytes_per_node(case)
     achieved = nodes * bpn / (kt["stream_collide"] * 1e-3) / 1e9
-    traffic = traffic_record("k_stream_collide", args.workload if args.storage == "f32" else f"{args.workload}_{args.storage}")
+    tkey = args.workload if args.storage == "f32" else f"{args.workload}_{args.storage}"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "frac": round(achieved / peak, 4), "traffic": traffic_record("k_stream_collide", tkey),
                 "kernel": "k_stream_collide", "bytes_per_node": bpn, "nodes_per_launch": nodes,
-                "kernel_ms": round(kt["stream_collide"], 4), "peak_source": f"{peak_kind} hbm_gbs (copy, burst)"}
+                "kernel_ms": round(kt["stream_collide"], 4),
+                "peak_source": f"{peak_kind} hbm_gbs (copy, burst)",
+                "timing": "mean over even and odd launches, CUDA events around the kernel inside the step graph"}
     diag = sim.diagnostics()
+    head = {"step_ms": round(ms_step, 4), "MLUPS": round(nodes / (ms_step * 1e-3) / 1e6, 1),
+            "stream_collide_ms": round(kt["stream_collide"], 4), "stream_collide_GBs": round(achieved, 1),
+            "bytes_per_node": bpn}
+    if solo:  # the same kernel with blocks that divide the row, for comparison
+        from paper_1502_01159_gb300 import TUNE_LATTICE_ROW_TILES
+        sim.set_tuning(TUNE_LATTICE_ROW_TILES, 1)
+        head["stream_collide_ms_row_tiles"] = round(kernel_times(sim, 6, torch, flush)["stream_collide"], 4)
     sim.close()
     del sim
 
@@ -505,41 +621,46 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = e2e_run(case, args.steps, torch)
 
-    secondary = None
-    if rank == 0 and world == 1 and args.workload == "sed2d" and args.storage == "f32" and not args.no_3d:
-        c3, d3 = workload("sed3d")
-        sim3, ms3 = measure_gpu(c3, max(5, args.steps // 2), 3, torch, flush)
-        kt3 = kernel_times(sim3, 5, torch, flush)
-        n3 = c3["shape"][0] * c3["shape"][1] * c3["shape"][2]
-        b3 = bytes_per_node(c3)
-        a3 = n3 * b3 / (kt3["stream_collide"] * 1e-3) / 1e9
-        secondary = {"workload": d3, "value": round(n3 / (statistics.mean(ms3) * 1e-3) / 1e6, 1), "unit": "MLUPS",
-                     "ms_per_step": round(statistics.mean(ms3), 4),
-                     "particle_steps_per_s": round(2000 / (statistics.mean(ms3) * 1e-3), 1),
-                     "kernel_ms": {k: round(v, 4) for k, v in kt3.items()},
-                     "roofline": {"bound": "hbm", "achieved": round(a3, 1), "peak": peak, "unit": "GB/s",
-                                  "frac": round(a3 / peak, 4), "traffic": traffic_record("k_stream_collide", "sed3d"),
-                                  "kernel": "k_stream_collide", "bytes_per_node": b3, "nodes_per_launch": n3}}
-        sim3.close()
+    extras = {}
+    if solo and not args.no_extras:
+        for wl in ("sed3d", "sed2d"):
+            if wl == args.workload:
+                continue
+            c3, d3 = workload(wl)
+            sim3, ms3 = measure_gpu(c3, max(6, args.steps // 2), 3, torch, flush)
+            kt3 = kernel_times(sim3, 6, torch, flush)
+            n3 = c3["shape"][0] * c3["shape"][1] * c3["shape"][2]
+            np3 = len(c3["particles"]["R"])
+            b3 = bytes_per_node(c3)
+            a3 = n3 * b3 / (kt3["stream_collide"] * 1e-3) / 1e9
+            m3 = statistics.mean(ms3)
+            extras[wl] = {"workload": d3, "value": round(n3 / (m3 * 1e-3) / 1e6, 1), "unit": "MLUPS",
+                          "ms_per_step": round(m3, 4), "particle_steps_per_s": round(np3 / (m3 * 1e-3), 1),
+                          "kernel_ms": {k: round(v, 4) for k, v in kt3.items()},
+                          "roofline": {"bound": "hbm", "achieved": round(a3, 1), "peak": peak, "unit": "GB/s",
+                                       "frac": round(a3 / peak, 4), "traffic": traffic_record("k_stream_collide", wl),
+                                       "kernel": "k_stream_collide", "bytes_per_node": b3, "nodes_per_launch": n3}}
+            if wl == "sed2d":
+                extras[wl]["note"] = "29 MB state: L2-resident, L2 flushed before every timed step"
+            sim3.close()
+        if args.workload == "sed3d384" and args.storage == "f32":
+            extras["precision"] = precision_study(torch, flush, head)
+        extras["ensemble"] = ensemble_study(torch, flush, max(6, args.steps // 2))
+        extras["surrogate"] = surrogate_study(torch, flush, max(6, args.steps // 2))
 
-    ensemble = None
-    if rank == 0 and world == 1 and args.workload == "sed2d" and args.storage == "f32" and not args.no_ensemble:
-        ensemble = ensemble_study(torch, flush, max(5, args.steps // 2))
-
-    surrogate = None
-    if rank == 0 and world == 1 and args.workload == "sed2d" and args.storage == "f32" and not args.no_surrogate:
-        surrogate = surrogate_study(torch, flush, max(5, args.steps // 2))
-
-    precision = None
-    if (rank == 0 and world == 1 and args.workload == "sed2d" and args.storage == "f32" and not args.no_3d
-            and not args.no_precision):
-        precision = precision_study(torch, flush)
+    baselines = None
+    if bg is not None:
+        out, err = bg.communicate()
+        try:
+            baselines = json.loads(out.strip().splitlines()[-1])
+        except Exception:
+            baselines = {"error": (err or out)[-300:]}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
             "storage": args.storage,
             "config": {"workload": desc, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "flushed before every timed step (256 MB write); per-step device time excludes the flush",
@@ -553,14 +674,9 @@ def run_ours(args):
             "clocks": clocks,
             "diagnostics_after": {k: diag[k] for k in ("mass", "min_height", "umax", "nonfinite")},
         }
-        if secondary:
-            line["secondary"] = secondary
-        if precision:
-            line["precision"] = precision
-        if ensemble:
-            line["ensemble"] = ensemble
-        if surrogate:
-            line["surrogate"] = surrogate
+        line.update(extras)
+        if baselines is not None:
+            line["oracle_baselines"] = baselines
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -573,19 +689,21 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sed2d", choices=["sed2d", "sed3d", "sed3d_mid"])
+    ap.add_argument("--workload", default="sed3d384", choices=["sed3d384", "sed3d", "sed2d", "sed3d_mid",
+                                                                "sed3d384_mid"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="population storage (arithmetic is FP32 in every case)")
-    ap.add_argument("--cpu-steps", type=int, default=60)
+    ap.add_argument("--cpu-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-3d", action="store_true")
-    ap.add_argument("--no-precision", action="store_true")
-    ap.add_argument("--no-ensemble", action="store_true")
-    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="headline only (no other workloads or studies)")
+    ap.add_argument("--no-oracle-baselines", action="store_true")
+    ap.add_argument("--oracle-baselines-json", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
-    if args.impl == "reference":
+    if args.oracle_baselines_json:
+        print(json.dumps(oracle_baselines()), flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

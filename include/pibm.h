@@ -225,17 +225,18 @@ pibm_status pibm_set_particle_model(pibm_ctx* ctx, int model);
 /* Launch-shape tuning (used by autotuning sweeps; results do not depend on it).
  * PIBM_TUNE_DEM_PARTICLES_PER_CTA: particles per CTA of the DEM cluster
  * (0 = default 32; at most 16 CTAs and 640 particles per CTA).
- * PIBM_TUNE_PAIR_LATTICE: 1 = two nodes per thread with 32-bit accesses for
- * FP16 / BF16 storage when nx is a multiple of 64 (default 0: one node per
- * thread, the faster form on GB300).
+ * PIBM_TUNE_LATTICE_ROW_TILES: 1 = collide-and-stream blocks span the largest
+ * multiple of 32 nodes (at most 256) that divides the row rounded up to 32, so
+ * no block straddles a row end with idle warps; 0 (default) = blocks span
+ * min(256, row rounded up to 32) nodes.  Identical results either way.
  * PIBM_TUNE_LATTICE_THREADS: threads per block of the collide-and-stream
  * kernel, 0 (default shape) or a multiple of 32 in [32, 512]; a block spans
- * min(threads, row width rounded up to 32) nodes of a row and as many rows as
- * the remaining factor gives.
+ * min(threads, row width rounded up to 32) nodes of a row (or the row-dividing
+ * width above) and as many rows as the remaining factor gives.
  * PIBM_TUNE_WIDE_INDEX: 1 = 64-bit slot offsets in the collide-and-stream
  * kernel even where 32-bit ones suffice (default 0: 32-bit offsets whenever
  * Q N < 2^31 elements, 64-bit beyond; the two give identical results). */
-enum { PIBM_TUNE_DEM_PARTICLES_PER_CTA = 0, PIBM_TUNE_PAIR_LATTICE = 1, PIBM_TUNE_LATTICE_THREADS = 2,
+enum { PIBM_TUNE_DEM_PARTICLES_PER_CTA = 0, PIBM_TUNE_LATTICE_ROW_TILES = 1, PIBM_TUNE_LATTICE_THREADS = 2,
        PIBM_TUNE_WIDE_INDEX = 3 };
 pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value);
 

@@ -920,9 +920,9 @@ pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value) {
         drop_graphs(c);
         return PIBM_OK;
     }
-    if (knob == PIBM_TUNE_PAIR_LATTICE) {
+    if (knob == PIBM_TUNE_LATTICE_ROW_TILES) {
         if (value != 0 && value != 1) return fail(ctx, PIBM_ERR_ARG, "invalid tuning value");
-        c.tune_pair_lattice = value;
+        c.tune_lattice_row_tiles = value;
         drop_graphs(c);
         return PIBM_OK;
     }

@@ -9,6 +9,10 @@
 // even steps read and write the node's own slots (the post-collision value of
 // direction i goes to the slot of its opposite), odd steps read from and write
 // to the neighbours, so one array serves both time levels.
+//
+// One node per thread.  The collision is written with explicitly rounded
+// operations, so its result does not depend on how the compiler schedules or
+// fuses them.
 #include <float.h>
 
 #include <algorithm>
@@ -22,13 +26,33 @@ namespace pibm {
 // GB300's FP64 pipe is slow, and a double-to-float conversion runs on it).
 template <typename R>
 struct CollideParams {
-    R omf, omg;        // 1 / tau_f, 1 / tau_g
-    R cf, cg;          // 1 - 1/(2 tau_f), 1 - 1/(2 tau_g)
+    R om1f, om1g;      // 1 - 1/tau_f, 1 - 1/tau_g
+    R c9f, c3f, m3f;   // 9 (1 - 1/(2 tau_f)), 3 (1 - 1/(2 tau_f)), -3 (1 - 1/(2 tau_f))
+    R cg;              // 1 - 1/(2 tau_g)
     R buoy, Tref;      // U_c^2 / L_c, reference temperature
     R body[3];
     R abb[6];          // anti-bounce-back offset 2 w (T_w - T_ref) per face (w of a non-rest thermal direction)
     int gaxis, buoyancy;
 };
+
+// ------------------------------------------------------ collision arithmetic
+// Every add, subtract, multiply and fused multiply-add of the collision is
+// written out with its rounding (float, or double for FP64 storage), so the
+// compiler contracts nothing and the result is fixed by the source alone.
+__device__ __forceinline__ float op_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float op_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float op_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float op_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float op_rcp(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double op_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double op_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double op_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double op_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double op_rcp(double a) { return __drcp_rn(a); }
+// a constant of the arithmetic type T
+template <typename T> struct Bc;
+template <> struct Bc<float> { static __device__ __forceinline__ float of(float v) { return v; } };
+template <> struct Bc<double> { static __device__ __forceinline__ double of(double v) { return v; } };
 
 // One node update: moments, forcing, BGK collision of f and g.
 //   rho = 1 + sum s_i, j = sum e_i s_i, T = T_ref + sum s_gk + Q_B / 2
@@ -38,35 +62,42 @@ struct CollideParams {
 //     s_i^eq = w_i (rho - 1 + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u^2))
 //   Eq lbm2.5 + lbm3.5 (linear, D2Q5 / D3Q7) + lbm12.5:
 //     s_gk* = s_gk + (w_k (T - T_ref + T e.u / cs_T^2) - s_gk)/tau_g + (1 - 1/2tau_g) w_k Q_B
-template <int D, typename R>
-__device__ __forceinline__ void collide_node(R* s, R* sg, R fbx, R fby, R fbz, R qb, const CollideParams<R>& P) {
+template <int D, typename T, typename R>
+__device__ __forceinline__ void collide_node(T* s, T* sg, T fbx, T fby, T fbz, T qb, const CollideParams<R>& P) {
     using L = Lat<D>;
-    R drho = 0, jx = 0, jy = 0, jz = 0, dT = 0;
+    using B = Bc<T>;
+    T drho = s[0], jx = B::of(0), jy = B::of(0), jz = B::of(0);
 #pragma unroll
-    for (int i = 0; i < L::Q; i++) {
-        drho += s[i];
-        if (L::ex(i)) jx += L::ex(i) * s[i];
-        if (L::ey(i)) jy += L::ey(i) * s[i];
-        if (L::ez(i)) jz += L::ez(i) * s[i];
+    for (int i = 1; i < L::Q; i++) {
+        drho = op_add(drho, s[i]);
+        if (L::ex(i) > 0) jx = op_add(jx, s[i]);
+        if (L::ex(i) < 0) jx = op_sub(jx, s[i]);
+        if (L::ey(i) > 0) jy = op_add(jy, s[i]);
+        if (L::ey(i) < 0) jy = op_sub(jy, s[i]);
+        if (L::ez(i) > 0) jz = op_add(jz, s[i]);
+        if (L::ez(i) < 0) jz = op_sub(jz, s[i]);
     }
+    T dT = sg[0];
 #pragma unroll
-    for (int k = 0; k < L::QG; k++) dT += sg[k];
-    const R half = (R)0.5;
-    dT += half * qb;                        // T - T_ref
-    const R T = (R)P.Tref + dT;
-    R Fx = fbx + (R)P.body[0], Fy = fby + (R)P.body[1], Fz = fbz + (R)P.body[2];
+    for (int k = 1; k < L::QG; k++) dT = op_add(dT, sg[k]);
+    const T half = B::of(0.5);
+    dT = op_fma(half, qb, dT);  // T - T_ref
+    const T Tt = op_add(B::of(P.Tref), dT);
+    T Fx = op_add(fbx, B::of(P.body[0])), Fy = op_add(fby, B::of(P.body[1])), Fz = op_add(fbz, B::of(P.body[2]));
     if (P.buoyancy) {
-        R fbu = (R)P.buoy * dT;
-        if (P.gaxis == 0) Fx += fbu;
-        else if (P.gaxis == 1) Fy += fbu;
-        else Fz += fbu;
+        const T fbu = op_mul(B::of(P.buoy), dT);
+        if (P.gaxis == 0) Fx = op_add(Fx, fbu);
+        else if (P.gaxis == 1) Fy = op_add(Fy, fbu);
+        else Fz = op_add(Fz, fbu);
     }
-    const R rho = (R)1 + drho;
-    const R inv_rho = (R)1 / rho;
-    const R ux = (jx + half * Fx) * inv_rho, uy = (jy + half * Fy) * inv_rho, uz = (jz + half * Fz) * inv_rho;
-    const R uu = ux * ux + uy * uy + uz * uz;
-    const R uF = ux * Fx + uy * Fy + uz * Fz;
-    const R omf = (R)P.omf, cf = (R)P.cf, om1 = (R)1 - omf;
+    const T rho = op_add(B::of(1), drho);
+    const T inv_rho = op_rcp(rho);
+    const T ux = op_mul(op_fma(half, Fx, jx), inv_rho);
+    const T uy = op_mul(op_fma(half, Fy, jy), inv_rho);
+    const T uz = op_mul(op_fma(half, Fz, jz), inv_rho);
+    const T uu = op_fma(uz, uz, op_fma(uy, uy, op_mul(ux, ux)));
+    const T uF = op_fma(uz, Fz, op_fma(uy, Fy, op_mul(ux, Fx)));
+    const T om1 = B::of(P.om1f);
     // Opposite directions i, i' share e.u and e.F up to sign, so equilibrium
     // and forcing split into parts even and odd in e:
     //   s_i^eq = w (p0 + 4.5 rho (e.u)^2) + w 3 rho e.u,  p0 = drho - 1.5 rho u^2
@@ -74,47 +105,62 @@ __device__ __forceinline__ void collide_node(R* s, R* sg, R fbx, R fby, R fbz, R
     // and the update keeps the non-equilibrium form (small correction added to
     // the equilibrium, no cancellation of two large terms):
     //   s_i* = s_i^eq + F_i + (1 - 1/tau) (s_i - s_i^eq)
-    const R p0 = drho - (R)1.5 * rho * uu, q0 = (R)4.5 * rho, r0 = (R)3 * rho;
-    const R k0 = (R)-3 * cf * uF, c9 = (R)9 * cf, c3 = (R)3 * cf;
+    const T p0 = op_fma(B::of(-1.5), op_mul(rho, uu), drho);
+    const T q0 = op_mul(B::of(4.5), rho), r0 = op_mul(B::of(3), rho);
+    const T k0 = op_mul(B::of(P.m3f), uF), c9 = B::of(P.c9f), c3 = B::of(P.c3f);
     {
-        const R seq = (R)L::w(0) * p0;
-        s[0] = seq + (R)L::w(0) * k0 + om1 * (s[0] - seq);
+        const T w0 = B::of(L::w(0));
+        const T seq = op_mul(w0, p0);
+        s[0] = op_fma(om1, op_sub(s[0], seq), op_fma(w0, k0, seq));
     }
 #pragma unroll
     for (int i = 1; i < L::Q; i++) {
         if (L::opp(i) < i) continue;
         const int io = L::opp(i);
-        const R wi = (R)L::w(i);
-        R eu = 0, eF = 0;
-        if (L::ex(i)) { eu += L::ex(i) * ux; eF += L::ex(i) * Fx; }
-        if (L::ey(i)) { eu += L::ey(i) * uy; eF += L::ey(i) * Fy; }
-        if (L::ez(i)) { eu += L::ez(i) * uz; eF += L::ez(i) * Fz; }
-        const R es = wi * (p0 + q0 * eu * eu), ea = wi * r0 * eu;     // even / odd equilibrium parts
-        const R fs = wi * (k0 + c9 * eu * eF), fa = wi * c3 * eF;      // even / odd forcing parts
-        const R ni = s[i] - es - ea, no = s[io] - es + ea;             // non-equilibrium parts
-        s[i] = (es + fs) + (ea + fa) + om1 * ni;
-        s[io] = (es + fs) - (ea + fa) + om1 * no;
+        const T wi = B::of(L::w(i));
+        // e.u and e.F: the sum of the non-zero components with their signs
+        T eu = B::of(0), eF = B::of(0);
+        bool first = true;
+        if (L::ex(i)) { eu = L::ex(i) > 0 ? ux : op_sub(eu, ux); eF = L::ex(i) > 0 ? Fx : op_sub(eF, Fx); first = false; }
+        if (L::ey(i)) {
+            if (first) { eu = L::ey(i) > 0 ? uy : op_sub(eu, uy); eF = L::ey(i) > 0 ? Fy : op_sub(eF, Fy); }
+            else { eu = L::ey(i) > 0 ? op_add(eu, uy) : op_sub(eu, uy); eF = L::ey(i) > 0 ? op_add(eF, Fy) : op_sub(eF, Fy); }
+            first = false;
+        }
+        if (L::ez(i)) {
+            if (first) { eu = L::ez(i) > 0 ? uz : op_sub(eu, uz); eF = L::ez(i) > 0 ? Fz : op_sub(eF, Fz); }
+            else { eu = L::ez(i) > 0 ? op_add(eu, uz) : op_sub(eu, uz); eF = L::ez(i) > 0 ? op_add(eF, Fz) : op_sub(eF, Fz); }
+        }
+        const T es = op_mul(wi, op_fma(q0, op_mul(eu, eu), p0));  // even / odd equilibrium parts
+        const T ea = op_mul(op_mul(wi, r0), eu);
+        const T fs = op_mul(wi, op_fma(c9, op_mul(eu, eF), k0));  // even / odd forcing parts
+        const T fa = op_mul(op_mul(wi, c3), eF);
+        const T ni = op_sub(op_sub(s[i], es), ea);                // non-equilibrium parts
+        const T no = op_add(op_sub(s[io], es), ea);
+        const T a = op_add(es, fs), b = op_add(ea, fa);
+        s[i] = op_fma(om1, ni, op_add(a, b));
+        s[io] = op_fma(om1, no, op_sub(a, b));
     }
     // thermal, the same split: s_gk^eq = w_k dT + w_k (T / cs_T^2) e.u, source w_k cg Q_B
-    const R omg = (R)P.omg, om1g = (R)1 - omg;
-    const R gq = (R)P.cg * qb, kT = T * (R)L::inv_csT2;
+    const T om1g = B::of(P.om1g);
+    const T gq = op_mul(B::of(P.cg), qb), kT = op_mul(Tt, B::of(L::inv_csT2));
     {
-        const R seq = (R)L::wg(0) * dT;
-        sg[0] = seq + (R)L::wg(0) * gq + om1g * (sg[0] - seq);
+        const T w0 = B::of(L::wg(0));
+        const T seq = op_mul(w0, dT);
+        sg[0] = op_fma(om1g, op_sub(sg[0], seq), op_fma(w0, gq, seq));
     }
 #pragma unroll
     for (int k = 1; k < L::QG; k++) {
         if (L::opp(k) < k) continue;
         const int ko = L::opp(k);
-        const R wk = (R)L::wg(k);
-        R eu = 0;
-        if (L::ex(k)) eu += L::ex(k) * ux;
-        if (L::ey(k)) eu += L::ey(k) * uy;
-        if (L::ez(k)) eu += L::ez(k) * uz;
-        const R es = wk * dT, ea = wk * kT * eu, src = wk * gq;
-        const R ni = sg[k] - es - ea, no = sg[ko] - es + ea;
-        sg[k] = (es + src) + ea + om1g * ni;
-        sg[ko] = (es + src) - ea + om1g * no;
+        const T wk = B::of(L::wg(k));
+        T eu = L::ex(k) ? ux : (L::ey(k) ? uy : uz);
+        if (L::ex(k) + L::ey(k) + L::ez(k) < 0) eu = op_sub(B::of(0), eu);
+        const T es = op_mul(wk, dT), ea = op_mul(op_mul(wk, kT), eu), src = op_mul(wk, gq);
+        const T ni = op_sub(op_sub(sg[k], es), ea), no = op_add(op_sub(sg[ko], es), ea);
+        const T a = op_add(es, src);
+        sg[k] = op_fma(om1g, ni, op_add(a, ea));
+        sg[ko] = op_fma(om1g, no, op_sub(a, ea));
     }
 }
 
@@ -123,8 +169,7 @@ __device__ __forceinline__ void collide_node(R* s, R* sg, R fbx, R fby, R fbz, R
 // plane opp(i) at n - e_i, odd-step destinations plane i at n + e_i, even-step
 // loads plane i at n and stores plane opp(i) at n.  IX = int when every offset
 // fits in 32 bits (Q N < 2^31 elements): then each access is the thread's node
-// pointer plus a 32-bit offset, one multiply-add, which matters to the 16-bit
-// kernels (their time goes to issuing instructions, not to HBM).
+// pointer plus a 32-bit offset, one multiply-add.
 template <typename IX>
 struct AAOffsets {
     IX src[19], dst[19], ld[19], st[19];
@@ -156,7 +201,7 @@ __device__ __forceinline__ void odd_load_xface(const Geo& G, const CollideParams
         if (i < L::QG) {
             R v = Store<S>::ldg(gn[idx]);
             const int face = ex > 0 ? 0 : 1;  // face crossed by x - e_i
-            if (out && !per && face_iso(G, face)) v = P.abb[face] - v;
+            if (out && !per && face_iso(G, face)) v = op_sub(P.abb[face], v);
             sg[i < L::QG ? i : 0] = v;
         }
     }
@@ -180,9 +225,52 @@ __device__ __forceinline__ void odd_store_xface(const Geo& G, const CollideParam
         if (i < L::QG) {
             R v = sg[i < L::QG ? i : 0];
             const int face = ex > 0 ? 1 : 0;  // face crossed by x + e_i
-            if (out && !per && face_iso(G, face)) v = P.abb[face] - v;
+            if (out && !per && face_iso(G, face)) v = op_sub(P.abb[face], v);
             gn[idx] = Store<S>::stg(v);
         }
+    }
+}
+
+// Generic odd-step store of one node's post-collision populations (any boundary).
+template <int D, typename S>
+__device__ __forceinline__ void store_node(const Geo& G, const CollideParams<typename Store<S>::R>& P, S* f, S* g, int x,
+                                           int y, int z, const typename Store<S>::R* s, const typename Store<S>::R* sg) {
+    using L = Lat<D>;
+    using R = typename Store<S>::R;
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+        long long idx;
+        post_slot(G, x, y, z, L::ex(i), L::ey(i), L::ez(i), i, L::opp(i), 1, idx);
+        f[idx] = Store<S>::stf(s[i]);
+    }
+#pragma unroll
+    for (int k = 0; k < L::QG; k++) {
+        long long idx;
+        int face = post_slot(G, x, y, z, L::ex(k), L::ey(k), L::ez(k), k, L::opp(k), 1, idx);
+        R v = sg[k];
+        if (face_iso(G, face)) v = op_sub(P.abb[face], v);
+        g[idx] = Store<S>::stg(v);
+    }
+}
+
+// Generic-path thermal load (the anti-bounce-back uses the collision's rounding).
+template <int D, typename S, typename R>
+__device__ __forceinline__ void load_node_r(const Geo& G, const CollideParams<R>& P, const S* __restrict__ f,
+                                            const S* __restrict__ g, int x, int y, int z, int parity, R* s, R* sg) {
+    using L = Lat<D>;
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+        long long idx;
+        pop_slot(G, x, y, z, L::ex(i), L::ey(i), L::ez(i), i, L::opp(i), parity, idx);
+        s[i] = (R)Store<S>::ldf(f[idx]);
+    }
+#pragma unroll
+    for (int k = 0; k < L::QG; k++) {
+        long long idx;
+        int face = pop_slot(G, x, y, z, L::ex(k), L::ey(k), L::ez(k), k, L::opp(k), parity, idx);
+        R v = (R)Store<S>::ldg(g[idx]);
+        if (face_iso(G, face)) v = op_sub(P.abb[face], v);
+        sg[k] = v;
     }
 }
 
@@ -221,7 +309,7 @@ __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) 
     } else if (inner_yz) {
         odd_load_xface<D, S, IX>(G, P, fn, gn, x, O, s, sg);
     } else {
-        load_node<D, S, R>(G, f, g, x, y, z, 1, s, sg);
+        load_node_r<D, S, R>(G, P, f, g, x, y, z, 1, s, sg);
     }
     R fbx = 0, fby = 0, fbz = 0, qb = 0;
     if (flags[((long long)z * G.ny + y) * G.ntx + (x >> 5)]) {
@@ -231,7 +319,7 @@ __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) 
         fbz = v.z;
         qb = v.w;
     }
-    collide_node<D, R>(s, sg, fbx, fby, fbz, qb, P);
+    collide_node<D, R, R>(s, sg, fbx, fby, fbz, qb, P);
     if (PARITY == 0) {
 #pragma unroll
         for (int i = 0; i < L::Q; i++) fn[O.st[i]] = Store<S>::stf(s[i]);
@@ -245,29 +333,19 @@ __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) 
     } else if (inner_yz) {
         odd_store_xface<D, S, IX>(G, P, fn, gn, x, O, s, sg);
     } else {
-#pragma unroll
-        for (int i = 0; i < L::Q; i++) {
-            long long idx;
-            post_slot(G, x, y, z, L::ex(i), L::ey(i), L::ez(i), i, L::opp(i), 1, idx);
-            f[idx] = Store<S>::stf(s[i]);
-        }
-#pragma unroll
-        for (int k = 0; k < L::QG; k++) {
-            long long idx;
-            int face = post_slot(G, x, y, z, L::ex(k), L::ey(k), L::ez(k), k, L::opp(k), 1, idx);
-            R v = sg[k];
-            if (face_iso(G, face)) v = P.abb[face] - v;
-            g[idx] = Store<S>::stg(v);
-        }
+        store_node<D, S>(G, P, f, g, x, y, z, s, sg);
     }
 }
 
 template <typename R>
 static CollideParams<R> collide_params(const Ctx* c) {
     CollideParams<R> P;
-    P.omf = (R)(1.0 / c->tau_f);
-    P.omg = (R)(1.0 / c->tau_g);
-    P.cf = (R)(1.0 - 0.5 / c->tau_f);
+    const double cf = 1.0 - 0.5 / c->tau_f;
+    P.om1f = (R)(1.0 - 1.0 / c->tau_f);
+    P.om1g = (R)(1.0 - 1.0 / c->tau_g);
+    P.c9f = (R)(9.0 * cf);
+    P.c3f = (R)(3.0 * cf);
+    P.m3f = (R)(-3.0 * cf);
     P.cg = (R)(1.0 - 0.5 / c->tau_g);
     P.buoy = (R)c->buoy;
     P.Tref = (R)c->desc.T_ref;
@@ -277,192 +355,6 @@ static CollideParams<R> collide_params(const Ctx* c) {
     P.gaxis = c->desc.gravity_axis;
     P.buoyancy = c->desc.buoyancy;
     return P;
-}
-
-// Generic odd-step store of one node's post-collision populations (any boundary).
-template <int D, typename S>
-__device__ __forceinline__ void store_node(const Geo& G, const CollideParams<typename Store<S>::R>& P, S* f, S* g, int x,
-                                           int y, int z, const typename Store<S>::R* s, const typename Store<S>::R* sg) {
-    using L = Lat<D>;
-    using R = typename Store<S>::R;
-#pragma unroll
-    for (int i = 0; i < L::Q; i++) {
-        long long idx;
-        post_slot(G, x, y, z, L::ex(i), L::ey(i), L::ez(i), i, L::opp(i), 1, idx);
-        f[idx] = Store<S>::stf(s[i]);
-    }
-#pragma unroll
-    for (int k = 0; k < L::QG; k++) {
-        long long idx;
-        int face = post_slot(G, x, y, z, L::ex(k), L::ey(k), L::ez(k), k, L::opp(k), 1, idx);
-        R v = sg[k];
-        if (face_iso(G, face)) v = P.abb[face] - v;
-        g[idx] = Store<S>::stg(v);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// 16-bit storage, two nodes per thread.  The populations of the pair (x0, x0+1)
-// move as 32-bit words (low half node x0, high half node x0+1) and stay packed
-// in registers; the two nodes are collided one after the other (unpack to
-// FP32, collide, repack into the same words), so only one node's FP32 state is
-// live at a time.  In odd steps a direction with e_x = +1 reads x-1, the high
-// half of the left lane's word, through a warp shuffle; e_x = -1 reads x+1,
-// the low half of the right lane's word.  The element beyond the warp comes
-// from a 16-bit load that every lane issues at an in-row address (no branch,
-// and the sectors are the ones the word loads touch); at an x face that
-// address is the wrapped element or, at a wall, the node's own slot
-// (bounce-back; anti-bounce-back of the thermal populations is applied in
-// FP32 after unpacking and before repacking).  Stores mirror the loads.  Rows
-// on a y or z face take the generic path, one node at a time.  Requires nx to
-// be a multiple of 64 (whole warps per row).
-template <typename S> __device__ __forceinline__ S bits_to(uint32_t b);
-template <> __device__ __forceinline__ __half bits_to<__half>(uint32_t b) { return __ushort_as_half((unsigned short)b); }
-template <> __device__ __forceinline__ __nv_bfloat16 bits_to<__nv_bfloat16>(uint32_t b) {
-    return __ushort_as_bfloat16((unsigned short)b);
-}
-__device__ __forceinline__ uint32_t to_bits(__half v) { return __half_as_ushort(v); }
-__device__ __forceinline__ uint32_t to_bits(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
-__device__ __forceinline__ uint32_t ld32(const void* p) { return *reinterpret_cast<const uint32_t*>(p); }
-__device__ __forceinline__ void st32(void* p, uint32_t v) { *reinterpret_cast<uint32_t*>(p) = v; }
-__device__ __forceinline__ uint32_t ld16(const void* p) { return *reinterpret_cast<const unsigned short*>(p); }
-__device__ __forceinline__ void st16(void* p, uint32_t v) { *reinterpret_cast<unsigned short*>(p) = (unsigned short)v; }
-
-// Odd-step word (x0's value low, x0+1's value high) of one direction.  e is
-// the source element of node x0; own_lo / own_hi are the bounce-back slots of
-// the two nodes (plane i at the node itself).
-template <typename S>
-__device__ __forceinline__ uint32_t odd_gather(const S* p, long long e, int ex, int lane, bool lo_edge, bool hi_edge,
-                                               bool per, int nx, long long own_lo, long long own_hi) {
-    if (ex == 0) return ld32(p + e);
-    if (ex > 0) {  // node x reads x-1
-        const uint32_t v = ld32(p + e + 1);                      // elements (x0, x0+1)
-        const uint32_t left = __shfl_up_sync(0xffffffffu, v, 1);  // (x0-2, x0-1)
-        const uint32_t xe = ld16(p + (lo_edge ? (per ? e + nx : own_lo) : e));
-        return (lane == 0 ? xe : (left >> 16)) | (v << 16);
-    }
-    const uint32_t v = ld32(p + e - 1);                            // node x reads x+1; elements (x0, x0+1)
-    const uint32_t right = __shfl_down_sync(0xffffffffu, v, 1);     // (x0+2, x0+3)
-    const uint32_t xe = ld16(p + (hi_edge ? (per ? e + 1 - nx : own_hi) : e + 1));
-    return (v >> 16) | ((lane == 31 ? xe : (right & 0xffffu)) << 16);
-}
-
-// Odd-step stores of one direction: node x0 -> x0 + e_x, node x0+1 -> x0+1+e_x.
-// e is the destination element of node x0; own_lo / own_hi the bounce-back
-// slots (plane opp(i) at the node).  Each lane writes the aligned word
-// (x0, x0+1) of the destination row; the end lanes add the single element
-// that belongs to the neighbouring warp's word or lies beyond an x face.
-template <typename S>
-__device__ __forceinline__ void odd_scatter(S* p, long long e, int ex, int lane, bool lo_edge, bool hi_edge, bool per,
-                                            int nx, long long own_lo, long long own_hi, uint32_t w) {
-    if (ex == 0) {
-        st32(p + e, w);
-    } else if (ex > 0) {  // word (x0, x0+1) = (x0-1's value from the left lane, x0's value)
-        const uint32_t left = __shfl_up_sync(0xffffffffu, w, 1);
-        if (lane > 0) st32(p + e - 1, (left >> 16) | (w << 16));
-        else st16(p + e, w);
-        if (lane == 31) st16(p + (hi_edge ? (per ? e + 1 - nx : own_hi) : e + 1), w >> 16);
-    } else {  // word (x0, x0+1) = (x0+1's value, x0+2's value from the right lane)
-        const uint32_t right = __shfl_down_sync(0xffffffffu, w, 1);
-        if (lane < 31) st32(p + e + 1, (w >> 16) | (right << 16));
-        else st16(p + e + 1, w >> 16);
-        if (lane == 0) st16(p + (lo_edge ? (per ? e + nx : own_lo) : e), w);
-    }
-}
-
-template <int D, typename S, int PARITY>
-__global__ void __launch_bounds__(512) k_stream_collide_pair(Geo G, S* __restrict__ f, S* __restrict__ g,
-                                                             const float4* __restrict__ fb, const uint8_t* __restrict__ flags,
-                                                             CollideParams<float> P, AAOffsets<long long> O) {
-    using L = Lat<D>;
-    using St = Store<S>;
-    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
-    const int lane = threadIdx.x & 31;
-    if (x0 >= G.nx || y >= G.ny) return;  // whole warps only: nx / 2 and blockDim.x are multiples of 32
-    const long long n0 = node_index(G, x0, y, z);
-    const long long N = G.N;
-    const bool inner_yz = y > 0 && y < G.ny - 1 && (D == 2 || (z > 0 && z < G.nz - 1));
-    const bool tile = flags[((long long)z * G.ny + y) * G.ntx + (x0 >> 5)] != 0;  // x0, x0+1 share a tile
-    if (PARITY == 1 && !inner_yz) {  // a y or z face row: generic addressing, one node at a time
-#pragma unroll 1
-        for (int h = 0; h < 2; h++) {
-            float s[L::Q], sg[L::QG];
-            load_node<D, S, float>(G, f, g, x0 + h, y, z, 1, s, sg);
-            float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (tile) b = fb[n0 + h];
-            collide_node<D, float>(s, sg, b.x, b.y, b.z, b.w, P);
-            store_node<D, S>(G, P, f, g, x0 + h, y, z, s, sg);
-        }
-        return;
-    }
-    const bool lo_edge = x0 == 0, hi_edge = x0 + 1 == G.nx - 1, per = G.per[0] != 0;
-    uint32_t wf[L::Q], wt[L::QG];
-    if (PARITY == 0) {
-#pragma unroll
-        for (int i = 0; i < L::Q; i++) wf[i] = ld32(f + n0 + O.ld[i]);
-#pragma unroll
-        for (int k = 0; k < L::QG; k++) wt[k] = ld32(g + n0 + O.ld[k]);
-    } else {
-#pragma unroll
-        for (int i = 0; i < L::Q; i++)
-            wf[i] = odd_gather(f, n0 + O.src[i], L::ex(i), lane, lo_edge, hi_edge, per, G.nx, n0 + i * N, n0 + 1 + i * N);
-#pragma unroll
-        for (int k = 0; k < L::QG; k++)
-            wt[k] = odd_gather(g, n0 + O.src[k], L::ex(k), lane, lo_edge, hi_edge, per, G.nx, n0 + k * N, n0 + 1 + k * N);
-    }
-    // anti-bounce-back at an isothermal x wall (odd steps; face 0 for node x0, face 1 for node x0+1)
-    const bool abb_lo = PARITY == 1 && lo_edge && !per && face_iso(G, 0);
-    const bool abb_hi = PARITY == 1 && hi_edge && !per && face_iso(G, 1);
-#pragma unroll 1
-    for (int h = 0; h < 2; h++) {
-        const int sh = 16 * h;
-        const uint32_t keep = 0xffff0000u >> sh;
-        float s[L::Q], sg[L::QG];
-#pragma unroll
-        for (int i = 0; i < L::Q; i++) s[i] = St::ldf(bits_to<S>(wf[i] >> sh));
-#pragma unroll
-        for (int k = 0; k < L::QG; k++) {
-            float v = St::ldg(bits_to<S>(wt[k] >> sh));
-            // incoming across the low face (e_x > 0) for node x0, the high face (e_x < 0) for node x0+1
-            if (L::ex(k) > 0 && h == 0 && abb_lo) v = P.abb[0] - v;
-            if (L::ex(k) < 0 && h == 1 && abb_hi) v = P.abb[1] - v;
-            sg[k] = v;
-        }
-        float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (tile) b = fb[n0 + h];
-        collide_node<D, float>(s, sg, b.x, b.y, b.z, b.w, P);
-#pragma unroll
-        for (int i = 0; i < L::Q; i++) wf[i] = (wf[i] & keep) | (to_bits(St::stf(s[i])) << sh);
-#pragma unroll
-        for (int k = 0; k < L::QG; k++) {
-            float v = sg[k];
-            // outgoing across the low face (e_x < 0) for node x0, the high face (e_x > 0) for node x0+1
-            if (L::ex(k) < 0 && h == 0 && abb_lo) v = P.abb[0] - v;
-            if (L::ex(k) > 0 && h == 1 && abb_hi) v = P.abb[1] - v;
-            wt[k] = (wt[k] & keep) | (to_bits(St::stg(v)) << sh);
-        }
-    }
-    // Recompute the store addresses from an opaque copy of the node index:
-    // otherwise the compiler keeps the 26 load addresses (the same slots, in
-    // even steps) live in registers across both collisions.
-    long long ns;
-    asm volatile("mov.b64 %0, %1;" : "=l"(ns) : "l"(n0));
-    if (PARITY == 0) {
-#pragma unroll
-        for (int i = 0; i < L::Q; i++) st32(f + ns + O.st[i], wf[i]);
-#pragma unroll
-        for (int k = 0; k < L::QG; k++) st32(g + ns + O.st[k], wt[k]);
-    } else {
-#pragma unroll
-        for (int i = 0; i < L::Q; i++)
-            odd_scatter(f, ns + O.dst[i], L::ex(i), lane, lo_edge, hi_edge, per, G.nx, ns + L::opp(i) * N,
-                        ns + 1 + L::opp(i) * N, wf[i]);
-#pragma unroll
-        for (int k = 0; k < L::QG; k++)
-            odd_scatter(g, ns + O.dst[k], L::ex(k), lane, lo_edge, hi_edge, per, G.nx, ns + L::opp(k) * N,
-                        ns + 1 + L::opp(k) * N, wt[k]);
-    }
 }
 
 template <int D, typename IX>
@@ -488,44 +380,32 @@ static bool narrow_offsets(const Geo& G) {
     return (long long)Lat<D>::Q * G.N + 2LL * G.nx < (1LL << 31) - 1;
 }
 
-// Block shape of the lattice kernels for a row of `width` threads: bx threads
-// along x (a multiple of 32, at most 256) times by rows.  The default keeps
-// 256 threads per block for rows of 256 or more, 128 for shorter rows; the
-// tuning knob sets the threads per block (32 .. 512) and so the rows per block.
-static void lattice_shape(const Ctx* c, int width, dim3& block, dim3& grid) {
-    const int w32 = (width + 31) / 32 * 32;
+// Block shape of the lattice kernel: bx threads along x (a multiple of 32) times
+// by rows.  Default: bx = min(the row rounded up to 32, 256) and 256 threads per
+// block for rows of 256 or more nodes, 128 for shorter rows.  With
+// PIBM_TUNE_LATTICE_ROW_TILES = 1, bx is the largest multiple of 32 (at most
+// 256) that divides the row rounded up to 32, so that no block straddles a
+// row end with idle warps (a 384-node row: 192, not 256 + 128).  The tuning
+// knob PIBM_TUNE_LATTICE_THREADS sets the threads per block (32 .. 512).
+static void lattice_shape(const Ctx* c, dim3& block, dim3& grid) {
+    const int w32 = (c->G.nx + 31) / 32 * 32;
     const int threads = c->tune_lattice_threads > 0 ? c->tune_lattice_threads : (w32 >= 256 ? 256 : 128);
-    const int bx = w32 < threads ? w32 : (threads < 256 ? threads : 256);
+    int bx = w32 < threads ? w32 : (threads < 256 ? threads : 256);
+    if (c->tune_lattice_row_tiles) {
+        int best = 32;
+        for (int cand = 32; cand <= bx; cand += 32)
+            if (w32 % cand == 0) best = cand;
+        bx = best;
+    }
     const int by = threads / bx > 0 ? threads / bx : 1;
     block = dim3(bx, by, 1);
-    grid = dim3((width + bx - 1) / bx, (c->G.ny + by - 1) / by, c->G.nz);
-}
-
-template <int D, typename S>
-static cudaError_t pair_launch(Ctx* c, cudaStream_t s, int parity) {
-    if constexpr (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value) {
-        const int pairs = c->G.nx / 2;
-        dim3 block, grid;
-        lattice_shape(c, pairs, block, grid);
-        CollideParams<float> P = collide_params<float>(c);
-        AAOffsets<long long> O = aa_offsets<D, long long>(c->G);
-        if (parity == 0)
-            k_stream_collide_pair<D, S, 0><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const float4*)c->fb[parity],
-                                                                  c->flags[parity], P, O);
-        else
-            k_stream_collide_pair<D, S, 1><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const float4*)c->fb[parity],
-                                                                  c->flags[parity], P, O);
-        return cudaGetLastError();
-    }
-    return cudaErrorInvalidValue;
+    grid = dim3((c->G.nx + bx - 1) / bx, (c->G.ny + by - 1) / by, c->G.nz);
 }
 
 template <int D, typename S>
 static cudaError_t sc_launch(Ctx* c, cudaStream_t s, int parity) {
-    constexpr bool half = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
-    if (half && c->G.nx % 64 == 0 && c->tune_pair_lattice) return pair_launch<D, S>(c, s, parity);
     dim3 block, grid;
-    lattice_shape(c, c->G.nx, block, grid);
+    lattice_shape(c, block, grid);
     using R = typename Store<S>::R;
     CollideParams<R> P = collide_params<R>(c);
     using V = typename Store<S>::V4;

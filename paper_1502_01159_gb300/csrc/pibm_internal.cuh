@@ -324,7 +324,7 @@ struct Ctx {
     int adj_cap;
     int dem_cs;           // CTAs in the DEM cluster
     int tune_dem_particles_per_cta;  // 0: default (32)
-    int tune_pair_lattice;           // 1: two nodes per thread for 16-bit storage (nx a multiple of 64)
+    int tune_lattice_row_tiles;      // 1: lattice blocks span a divisor of the row (no block straddles a row end)
     int tune_lattice_threads;        // 0: default block shape; else threads per lattice block
     int tune_wide_index;             // 1: 64-bit slot offsets in the lattice kernel even where 32-bit suffice
     int dem_attr_ok;                 // the DEM kernel's launch attributes are set
