@@ -70,7 +70,11 @@ static void* dalloc(pibm_ctx* ctx, size_t bytes, int group) {
         p = nullptr;
     }
     if (!p) return nullptr;
-    if (cudaMemsetAsync(p, 0, bytes, c.s0) != cudaSuccess) return nullptr;
+    if (cudaMemsetAsync(p, 0, bytes, c.s0) != cudaSuccess) {  // give the block back: nothing leaks
+        if (c.alloc.free) c.alloc.free(p, c.alloc.user);
+        else cudaFree(p);
+        return nullptr;
+    }
     ctx->allocs.push_back({p, group});
     return p;
 }
@@ -274,6 +278,7 @@ pibm_status pibm_create(const pibm_desc* d, void* stream, const pibm_allocator* 
     c.desc = *d;
     c.D = d->dim;
     c.lat = c.D == 2 ? 2 : (d->flow_q == 15 ? 4 : 3);
+    c.sg.wait_polls = 1 << 22;
     c.Q = c.D == 2 ? 9 : (c.lat == 4 ? 15 : 19);
     c.QG = c.D == 2 ? 5 : 7;
     c.G.nx = d->nx, c.G.ny = d->ny, c.G.nz = d->nz;
@@ -923,6 +928,12 @@ pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value) {
     if (knob == PIBM_TUNE_LATTICE_ROW_TILES) {
         if (value != 0 && value != 1) return fail(ctx, PIBM_ERR_ARG, "invalid tuning value");
         c.tune_lattice_row_tiles = value;
+        drop_graphs(c);
+        return PIBM_OK;
+    }
+    if (knob == PIBM_TUNE_TC_WAIT_POLLS) {
+        if (value < 0) return fail(ctx, PIBM_ERR_ARG, "poll limit: 0 or more");
+        c.sg.wait_polls = value;
         drop_graphs(c);
         return PIBM_OK;
     }

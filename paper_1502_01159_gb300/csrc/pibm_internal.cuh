@@ -266,6 +266,7 @@ struct Surrogate {
     float *rows, *yrows, *J;         // [7n][16], [7n][8], [n][18]
     double* part;                    // gate partial sums
     int *J_on, *err;                 // device gate flag, tensor-core wait status
+    int wait_polls;                  // poll limit of a tensor-core completion wait
     double* stats;                   // [on steps, off steps, last relative error]
 };
 

@@ -81,9 +81,9 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// bounded wait on an mbarrier phase; false when the limit ran out
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 22); it++) {
+// bounded wait on an mbarrier phase: at most `limit` polls; false when they ran out
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, int limit) {
+    for (int it = 0; it < limit; it++) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
@@ -94,6 +94,8 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
     }
     return false;
 }
+
+constexpr int TC_WAIT_POLLS = 1 << 22;  // default poll limit of a tensor-core completion wait
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     uint32_t r[16];
@@ -114,9 +116,11 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 
 // rows x 16 FP32 standardised inputs (columns 12..15 ignored) -> rows x 8
 // FP32 standardised outputs (columns 7 ignored).  err: set to 1 when a bounded
-// wait gave up (the CTA then skips the rest of its work).
+// wait (at most wait_polls polls) gave up; the CTA then skips the rest of its
+// work, waits (with the default limit) for its own MMA still in flight, frees
+// its tensor memory and returns (err 2 if that drain also ran out).
 __global__ void __launch_bounds__(MLP_T) k_mlp_tc(const float* __restrict__ params, const float* __restrict__ in, int rows,
-                                                  float* __restrict__ out, int* err) {
+                                                  float* __restrict__ out, int* err, int wait_polls) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
@@ -174,7 +178,8 @@ __global__ void __launch_bounds__(MLP_T) k_mlp_tc(const float* __restrict__ para
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + SM_TMEM);
 
     bool ok = true;
-    for (int layer = 0; layer < 4 && ok; layer++) {
+    int layer = 0;
+    for (; layer < 4 && ok; layer++) {
         const int K = layer == 0 ? 16 : 64, N = layer == 3 ? 16 : 64;
         const uint32_t a0 = sbase + (layer == 0 ? SM_X : SM_H);
         const uint32_t b0 = sbase + (layer == 0 ? SM_W1 : layer == 1 ? SM_W2 : layer == 2 ? SM_W3 : SM_W4);
@@ -185,7 +190,7 @@ __global__ void __launch_bounds__(MLP_T) k_mlp_tc(const float* __restrict__ para
                          idesc_bf16(MLP_M, N), kk > 0);
             mma_commit(bar);
         }
-        const bool mine = bar_wait(bar, (uint32_t)(layer & 1));
+        const bool mine = bar_wait(bar, (uint32_t)(layer & 1), wait_polls);
         ok = __syncthreads_and(mine ? 1 : 0) != 0;  // one block-wide decision (no split barrier below)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!ok) break;
@@ -215,7 +220,13 @@ __global__ void __launch_bounds__(MLP_T) k_mlp_tc(const float* __restrict__ para
                 for (int k = 0; k < 8; k++) out[(long long)gr * 8 + k] = k < NO ? v[k] + bias[192 + k] : 0.f;
         }
     }
-    if (!ok && tid == 0) atomicExch(err, 1);
+    if (!ok) {
+        // the MMA of this layer may still be writing the accumulators: wait for
+        // its commit (bounded) before the tensor memory is released
+        const bool drained = bar_wait(bar, (uint32_t)(layer & 1), TC_WAIT_POLLS);
+        const bool all = __syncthreads_and(drained ? 1 : 0) != 0;
+        if (tid == 0) atomicExch(err, all ? 1 : 2);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -443,7 +454,7 @@ cudaError_t launch_mlp(Ctx* c, cudaStream_t s, const float* in, int rows, float*
         attr = true;
     }
     if (rows <= 0) return cudaSuccess;
-    k_mlp_tc<<<(rows + MLP_M - 1) / MLP_M, MLP_T, MLP_SMEM, s>>>(c->sg.params, in, rows, out, c->sg.err);
+    k_mlp_tc<<<(rows + MLP_M - 1) / MLP_M, MLP_T, MLP_SMEM, s>>>(c->sg.params, in, rows, out, c->sg.err, c->sg.wait_polls);
     return cudaGetLastError();
 }
 
