@@ -222,7 +222,8 @@ pibm_status pibm_step_timed(pibm_ctx* ctx, double* ms);
 enum { PIBM_PARTICLES_RESOLVED = 0, PIBM_PARTICLES_POINT = 1 };
 pibm_status pibm_set_particle_model(pibm_ctx* ctx, int model);
 
-/* Launch-shape tuning (used by autotuning sweeps; results do not depend on it).
+/* Launch-shape tuning (used by autotuning sweeps; results do not depend on it,
+ * except for PIBM_TUNE_TC_WAIT_POLLS below).
  * PIBM_TUNE_DEM_PARTICLES_PER_CTA: particles per CTA of the DEM cluster
  * (0 = default 32; at most 16 CTAs and 640 particles per CTA).
  * PIBM_TUNE_LATTICE_ROW_TILES: 1 = collide-and-stream blocks span the largest
@@ -235,9 +236,16 @@ pibm_status pibm_set_particle_model(pibm_ctx* ctx, int model);
  * width above) and as many rows as the remaining factor gives.
  * PIBM_TUNE_WIDE_INDEX: 1 = 64-bit slot offsets in the collide-and-stream
  * kernel even where 32-bit ones suffice (default 0: 32-bit offsets whenever
- * Q N < 2^31 elements, 64-bit beyond; the two give identical results). */
+ * Q N < 2^31 elements, 64-bit beyond; the two give identical results).
+ * PIBM_TUNE_TC_WAIT_POLLS: how many times a tensor-core kernel of the learned
+ * surrogate polls its completion barrier before it gives up (default
+ * 4194304).  It exists to exercise the timeout path: with 0 the next
+ * inference (pibm_surrogate_infer, or the surrogate pipeline of a step) gives
+ * up at once, waits with the default limit for its own work in flight, frees
+ * its tensor memory and the call returns PIBM_ERR_TIMEOUT; the context stays
+ * usable.  It is the one knob that changes results. */
 enum { PIBM_TUNE_DEM_PARTICLES_PER_CTA = 0, PIBM_TUNE_LATTICE_ROW_TILES = 1, PIBM_TUNE_LATTICE_THREADS = 2,
-       PIBM_TUNE_WIDE_INDEX = 3 };
+       PIBM_TUNE_WIDE_INDEX = 3, PIBM_TUNE_TC_WAIT_POLLS = 4 };
 pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value);
 
 /* Number of kernels one lattice step launches (for launch accounting). */
@@ -258,16 +266,23 @@ pibm_status pibm_kernels_per_step(pibm_ctx* ctx, int* n);
  *   dim, nlat[3]: lattice dimension and extents, walls at -0.5 and n - 0.5.
  *   cell_size: minimum cell side (> 0, at least the largest diameter; the
  *     library's default is 2 R_max + 1.5); at most 65536 cells.
- *   d_pairs: 2*cap ints (device); d_count: 2 ints (device): [0] total number
- *     of pairs (only the first cap are written), [1] 0, or 1 when a particle
- *     had more than 64 partners, or 2 when a diameter exceeds the cell side.
+ *   d_pairs: 2*cap ints (device); d_count: 2 ints (device): [0] number of
+ *     pairs found, keeping at most 64 partners j > i per particle i (the
+ *     first min(count, cap) are written, in order, with no gaps), [1] a bit
+ *     set: 1 when a particle had more than 64 partners (its extra pairs are
+ *     left out), 2 when a diameter exceeds the cell side (pairs may be
+ *     missed).
  *   stream: cudaStream_t or NULL.  Asynchronous; the results are valid once
  *     the stream has reached this call.
  * Sizes beyond the limits return PIBM_ERR_ARG (pibm_last_error(NULL, ...)
- * says which).  The first call on each device looks up the device address of
- * the scratch array with that device current; make that first call before any
- * stream capture.  Every call shares the one array and clears what it needs,
- * so calls that overlap on the GPU (on different streams) race. */
+ * says which).  The scratch array's device address belongs to the CUDA
+ * context current at the call: every call made outside stream capture looks
+ * it up again (after a device reset or with another context current, the next
+ * uncaptured call picks up the new address); a call inside a stream capture
+ * uses the address of the last uncaptured call on that device, so make one
+ * call before capturing (PIBM_ERR_STATE otherwise).  Every call shares the
+ * one array and clears what it needs, so calls that overlap on the GPU (on
+ * different streams) race. */
 pibm_status pibm_contacts_static(const double* d_X, const double* d_R, int n, int dim, const int32_t* nlat,
                                  double cell_size, int32_t* d_pairs, int cap, int32_t* d_count, void* stream);
 

@@ -91,10 +91,12 @@ __device__ __forceinline__ void na_visit(const NaGrid& G, const int* cell_start,
 }
 
 // Single CTA: cell list (counting sort, stable by index), per-particle pair
-// counts, offsets, then the pairs in (i, j) order.  Every scratch region that
-// must start at zero is cleared here, because the array keeps the previous
-// call's contents.  count[0]: number of pairs; count[1]: 1 if a particle had
-// more than 64 partners (pairs dropped), 2 if a diameter exceeds the cell side.
+// counts (at most 64 partners j > i kept per particle i), offsets, then the
+// pairs in (i, j) order.  Every scratch region that must start at zero is
+// cleared here, because the array keeps the previous call's contents.
+// count[0]: number of pairs kept (no holes: every kept pair is written while
+// it fits in cap); count[1]: a bit set -- 1 if a particle had more than 64
+// partners (the extra pairs dropped), 2 if a diameter exceeds the cell side.
 __global__ void __launch_bounds__(NA_THREADS) k_contacts_static(NaGrid G, int n, const double* __restrict__ X,
                                                                const double* __restrict__ R, int* pairs, int cap,
                                                                int* count, int* scratch) {
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_contacts_static(NaGrid G, int n,
     for (int c = t; c < G.ncell; c += T) cell_count[c] = 0;
     for (int p = t; p < n; p += T)  // a contact must lie within the 3^D neighbouring cells
         for (int a = 0; a < G.dim; a++)
-            if (2.0 * R[p] > G.side[a]) atomicExch(count + 1, 2);
+            if (2.0 * R[p] > G.side[a]) atomicOr(count + 1, 2);
     __syncthreads();
     for (int p = t; p < n; p += T) {
         int c[3];
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_contacts_static(NaGrid G, int n,
             double s = R[i] + R[j];
             if (j > i && na_dist2(X, i, j) < s * s) k++;
         });
-        pair_count[i] = k;
+        pair_count[i] = k < 64 ? k : 64;  // the pairs kept (the rest are reported by the flag)
     }
     __syncthreads();
     na_scan(pair_count, pair_offset, n, sh);
@@ -174,13 +176,18 @@ __global__ void __launch_bounds__(NA_THREADS) k_contacts_static(NaGrid G, int n,
                 pairs[2 * o] = i;
                 pairs[2 * o + 1] = cand[r];
             }
-        if (extra) atomicMax(count + 1, 1);  // more than 64 partners for one particle
+        if (extra) atomicOr(count + 1, 1);  // more than 64 partners for one particle
     }
     if (t == 0) count[0] = pair_offset[n];
 }
 
-// device address of the scratch array, looked up once per device (host code
-// must not pass the symbol itself: on the host it is only a stand-in)
+// Device address of the scratch array, per device.  Host code must not pass the
+// symbol itself (on the host it is only a stand-in), and a symbol's device
+// address belongs to the CUDA context that loaded the module: every call made
+// outside stream capture looks it up again with the caller's context current
+// (so a device reset or another context is picked up); a call inside a capture
+// (where the lookup may not be issued) uses the address of the device's last
+// uncaptured call.
 static int* g_scratch_addr[64];
 
 }  // namespace pibm
@@ -204,7 +211,12 @@ extern "C" pibm_status pibm_contacts_static(const double* d_X, const double* d_R
         set_global_error("pibm_contacts_static: no current CUDA device");
         return PIBM_ERR_CUDA;
     }
-    if (!g_scratch_addr[dev]) {  // first call on this device: look up the array's device address
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap_status) != cudaSuccess) {
+        set_global_error("pibm_contacts_static: invalid stream");
+        return PIBM_ERR_CUDA;
+    }
+    if (cap_status == cudaStreamCaptureStatusNone) {  // look up the array's device address in this context
         void* ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_contact_scratch);
         if (e != cudaSuccess || !ptr) {
@@ -212,6 +224,9 @@ extern "C" pibm_status pibm_contacts_static(const double* d_X, const double* d_R
             return PIBM_ERR_CUDA;
         }
         g_scratch_addr[dev] = (int*)ptr;
+    } else if (!g_scratch_addr[dev]) {
+        set_global_error("pibm_contacts_static: the first call on a device must come before any stream capture");
+        return PIBM_ERR_STATE;
     }
     NaGrid G;
     G.dim = dim;
@@ -225,8 +240,12 @@ extern "C" pibm_status pibm_contacts_static(const double* d_X, const double* d_R
         G.nc[a] = 1;
         G.inv[a] = 1.0 / (double)na;
         if (a < dim) {  // the library's cell grid: nc = floor(n / cell_min), side n / nc
-            G.nc[a] = (int)floor((double)na / cell_size);
-            if (G.nc[a] < 1) G.nc[a] = 1;
+            const double q = floor((double)na / cell_size);  // checked before it becomes an int
+            if (q > (double)NA_MAX_CELLS) {
+                set_global_error("pibm_contacts_static: more than 65536 cells (the fixed scratch limit)");
+                return PIBM_ERR_ARG;
+            }
+            G.nc[a] = q < 1.0 ? 1 : (int)q;
             G.inv[a] = (double)G.nc[a] / (double)na;
         }
         G.side[a] = (double)na / (double)G.nc[a];
