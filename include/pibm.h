@@ -243,9 +243,17 @@ pibm_status pibm_set_particle_model(pibm_ctx* ctx, int model);
  * inference (pibm_surrogate_infer, or the surrogate pipeline of a step) gives
  * up at once, waits with the default limit for its own work in flight, frees
  * its tensor memory and the call returns PIBM_ERR_TIMEOUT; the context stays
- * usable.  It is the one knob that changes results. */
+ * usable.  It is the one knob that changes results.
+ * PIBM_TUNE_COUPLING_THREADS: threads per block of the PIBM footprint and
+ * spread kernels (one block per particle), 0 (default: 256 in 3-D, sized to
+ * the largest disk's box in 2-D) or a multiple of 32 in [64, 256]; the force
+ * sums regroup (FP32 rounding of their partial sums).
+ * PIBM_TUNE_COUPLING_ORDER: 1 (default) = the footprint and spread blocks
+ * take the particles in the spatial order of the DEM's cell list; 0 = in
+ * index order (identical results). */
 enum { PIBM_TUNE_DEM_PARTICLES_PER_CTA = 0, PIBM_TUNE_LATTICE_ROW_TILES = 1, PIBM_TUNE_LATTICE_THREADS = 2,
-       PIBM_TUNE_WIDE_INDEX = 3, PIBM_TUNE_TC_WAIT_POLLS = 4 };
+       PIBM_TUNE_WIDE_INDEX = 3, PIBM_TUNE_TC_WAIT_POLLS = 4, PIBM_TUNE_COUPLING_THREADS = 5,
+       PIBM_TUNE_COUPLING_ORDER = 6 };
 pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value);
 
 /* Number of kernels one lattice step launches (for launch accounting). */

@@ -17,7 +17,8 @@ PERIODIC, WALL = 0, 1
 ADIABATIC, ISOTHERMAL = 0, 1
 SPRING_DASHPOT, HERTZ_MD = 0, 1
 STORE_F32, STORE_F64, STORE_F16, STORE_BF16 = 0, 1, 2, 3
-TUNE_DEM_PARTICLES_PER_CTA, TUNE_LATTICE_ROW_TILES, TUNE_LATTICE_THREADS, TUNE_WIDE_INDEX, TUNE_TC_WAIT_POLLS = 0, 1, 2, 3, 4
+(TUNE_DEM_PARTICLES_PER_CTA, TUNE_LATTICE_ROW_TILES, TUNE_LATTICE_THREADS, TUNE_WIDE_INDEX, TUNE_TC_WAIT_POLLS,
+ TUNE_COUPLING_THREADS, TUNE_COUPLING_ORDER) = range(7)
 STORAGE = {"f32": STORE_F32, "f64": STORE_F64, "f16": STORE_F16, "bf16": STORE_BF16}
 FIELDS = {"rho": 0, "ux": 1, "uy": 2, "uz": 3, "T": 4, "FBx": 5, "FBy": 6, "FBz": 7, "QB": 8}
 

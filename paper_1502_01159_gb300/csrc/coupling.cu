@@ -15,6 +15,8 @@
 //   spread    : F_B(r) = sum_d W(d) M(r + d), W = product of delta_h weights
 //               1/2, 1/4, 1/4 (Eqs lbm10-lbm12, lbm12.6) over the footprint
 //               grown by one node; overlapping boxes write identical values.
+// The footprint and spread blocks take the particles in the spatial order of
+// the DEM's cell list (results do not depend on the order).
 //
 // Static off-node markers (the cavity cylinder): one thread per marker does
 // the 4-point Lagrange interpolation (Eq lbm6) and forms A (F_f, Q); spreading
@@ -119,7 +121,8 @@ __global__ void __launch_bounds__(CP_THREADS, (Lat<D>::dim == 2 && !FEAT) ? 4 : 
                                                           const double* __restrict__ W, const double* __restrict__ Rr,
                                                           const double* __restrict__ Tp, const int* __restrict__ adj_start,
                                                           const int* __restrict__ adj_nb, double kappa, double Tref,
-                                                          int parity, double* Fh, double* Th, double* Hh, double* fsum) {
+                                                          int parity, double* Fh, double* Th, double* Hh, double* fsum,
+                                                          const int* __restrict__ order) {
     using L = Lat<D>;
     using R = typename Store<S>::R;
     __shared__ double sh_nb[CP_MAXNB][4];
@@ -133,7 +136,9 @@ __global__ void __launch_bounds__(CP_THREADS, (Lat<D>::dim == 2 && !FEAT) ? 4 : 
     // lanes 0-2 the position axes, 3-5 U, 6-8 omega, 9 T_p - T_ref, 10 2 kappa, 11 R
     __shared__ int s_box[6], s_base[3];
     __shared__ float s_cf[3], s_U[3], s_W[3], s_misc[3];
-    const int p = blockIdx.x;
+    // the particle: block b takes the b-th of a spatially sorted order (the DEM's
+    // cell list), so that blocks running together touch neighbouring nodes
+    const int p = order ? order[blockIdx.x] : (int)blockIdx.x;
     const double Xp[3] = {X[3 * p], X[3 * p + 1], X[3 * p + 2]};
     const double Rp = Rr[p];
     const int a0 = adj_start[p];
@@ -342,11 +347,11 @@ int spread_smem_bytes(int dim, double rmax, size_t v4) {
 template <int D, typename V>
 __global__ void __launch_bounds__(CP_THREADS) k_spread(Geo G, const double* __restrict__ X, const double* __restrict__ Rr,
                                                        const V* __restrict__ mk, V* __restrict__ fb, uint8_t* flags, int* box,
-                                                       int smem_bytes) {
+                                                       int smem_bytes, const int* __restrict__ order) {
     extern __shared__ __align__(32) unsigned char sm_raw[];
     V* tile = reinterpret_cast<V*>(sm_raw);
     using T = decltype(V().x);
-    const int p = blockIdx.x;
+    const int p = order ? order[blockIdx.x] : (int)blockIdx.x;  // as in k_footprint
     __shared__ int s_b[12];  // output box lo/hi, staged box lo/hi, computed once (lane a: axis a)
     if (threadIdx.x < 3) {
         const int a = threadIdx.x;
@@ -654,6 +659,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_points(Geo G, const S* __restric
 // pass without idle warps in the barriers and the block reduction; 3-D boxes take
 // several nodes per thread in blocks of CP_THREADS.
 static int footprint_threads(const Ctx* c) {
+    if (c->tune_coupling_threads > 0) return c->tune_coupling_threads;
     if (c->D != 2) return CP_THREADS;
     const long long e = (long long)floor(2.0 * c->rmax) + 2;
     const long long t = (e * e + 31) / 32 * 32;
@@ -669,19 +675,22 @@ static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
             c->G, (const S*)c->f, (const S*)c->g, c->np, c->X, c->U, c->R, c->Tp, c->desc.kappa_T, c->desc.T_ref, parity,
             (V*)c->fb[parity], c->flags[parity], c->box[parity], c->Fh, c->Th, c->Hh);
     } else if (c->np > 0) {
+        // the DEM's cell list orders the particles in space (a full permutation
+        // after every rebuild; the coupling runs after the DEM has finished)
+        const int* order = c->tune_coupling_order ? c->cell_ids : nullptr;
         if (c->sg.enabled)  // the surrogate's feature sums ride along
             k_footprint<D, S, true><<<c->np, footprint_threads(c), 0, s>>>(
                 c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk[parity], c->X, c->U, c->W, c->R, c->Tp, c->adj_start,
-                c->adj_nb, c->desc.kappa_T, c->desc.T_ref, parity, c->Fh, c->Th, c->Hh, c->sg.fsum);
+                c->adj_nb, c->desc.kappa_T, c->desc.T_ref, parity, c->Fh, c->Th, c->Hh, c->sg.fsum, order);
         else
             k_footprint<D, S, false><<<c->np, footprint_threads(c), 0, s>>>(
                 c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk[parity], c->X, c->U, c->W, c->R, c->Tp, c->adj_start,
-                c->adj_nb, c->desc.kappa_T, c->desc.T_ref, parity, c->Fh, c->Th, c->Hh, nullptr);
+                c->adj_nb, c->desc.kappa_T, c->desc.T_ref, parity, c->Fh, c->Th, c->Hh, nullptr, order);
         // programmatic dependent launch: the spread's CTAs start (and set up their boxes)
         // as the footprint's CTAs finish, then wait for the whole footprint grid
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(c->np, 1, 1);
-        cfg.blockDim = dim3(CP_THREADS, 1, 1);
+        cfg.blockDim = dim3(c->tune_coupling_threads > 0 ? c->tune_coupling_threads : CP_THREADS, 1, 1);
         cfg.dynamicSmemBytes = c->spread_smem;
         cfg.stream = s;
         cudaLaunchAttribute at[1];
@@ -691,7 +700,7 @@ static cudaError_t coupling_impl(Ctx* c, cudaStream_t s, int parity) {
         cfg.numAttrs = 1;
         cudaError_t e = cudaLaunchKernelEx(&cfg, k_spread<D, V>, c->G, (const double*)c->X, (const double*)c->R,
                                            (const V*)c->mk[parity], (V*)c->fb[parity], c->flags[parity], c->box[parity],
-                                           c->spread_smem);
+                                           c->spread_smem, order);
         if (e != cudaSuccess) return e;
     }
     if (c->nm > 0) {
@@ -717,7 +726,8 @@ static cudaError_t footprint_sums_impl(Ctx* c, cudaStream_t s, int parity) {
     if (!c->desc.pibm || c->np <= 0) return cudaSuccess;
     k_footprint<D, S, true><<<c->np, footprint_threads(c), 0, s>>>(c->G, (const S*)c->f, (const S*)c->g, (V*)c->mk[parity], c->X,
                                                          c->U, c->W, c->R, c->Tp, c->adj_start, c->adj_nb, c->desc.kappa_T,
-                                                         c->desc.T_ref, parity, c->Fh, c->Th, c->Hh, c->sg.fsum);
+                                                         c->desc.T_ref, parity, c->Fh, c->Th, c->Hh, c->sg.fsum,
+                                                         c->tune_coupling_order ? c->cell_ids : nullptr);
     return cudaGetLastError();
 }
 

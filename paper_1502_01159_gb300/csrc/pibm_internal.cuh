@@ -326,6 +326,8 @@ struct Ctx {
     int dem_cs;           // CTAs in the DEM cluster
     int tune_dem_particles_per_cta;  // 0: default (32)
     int tune_lattice_row_tiles;      // 1: lattice blocks span a divisor of the row (no block straddles a row end)
+    int tune_coupling_threads;       // 0: default; threads per footprint / spread block
+    int tune_coupling_order;         // 1 (default): coupling blocks take the particles in cell-list order
     int tune_lattice_threads;        // 0: default block shape; else threads per lattice block
     int tune_wide_index;             // 1: 64-bit slot offsets in the lattice kernel even where 32-bit suffice
     int dem_attr_ok;                 // the DEM kernel's launch attributes are set

@@ -531,3 +531,28 @@ def test_d3q15_poiseuille_closed_form_on_gpu():
     nu = sim.relaxation()["nu"]
     exact = case["body_force"][0] / (2 * nu) * (y + 0.5) * (16 - 0.5 - y)
     assert np.max(np.abs(ux - exact)) / exact.max() < 2e-5
+
+
+def test_coupling_particle_order_and_block_size():
+    from paper_1502_01159_gb300 import TUNE_COUPLING_ORDER, TUNE_COUPLING_THREADS
+    # the footprint and spread blocks take the particles in the cell list's
+    # spatial order or in index order: the same per-particle arithmetic, so the
+    # same state bit for bit; 128-thread blocks regroup the per-thread partial
+    # sums (FP32 rounding of the force reduction) and stay at the oracle bars
+    case = _small_sed3d(n_p=24, shape=(48, 40, 64), seed=4)
+    sims = []
+    for order, threads in ((1, 0), (0, 0), (1, 128)):
+        s = _sim(case)
+        s.set_tuning(TUNE_COUPLING_ORDER, order)
+        s.set_tuning(TUNE_COUPLING_THREADS, threads)
+        s.step(60)
+        sims.append(s)
+    fa, ga = sims[0].read_populations()
+    fb_, gb_ = sims[1].read_populations()
+    assert np.array_equal(fa, fb_) and np.array_equal(ga, gb_)
+    pa, pb = sims[0].read_particles(), sims[1].read_particles()
+    assert all(np.array_equal(pa[k], pb[k]) for k in pa)
+    orc = oracle.Oracle(case)
+    orc.step(60)
+    _compare_fields(sims[2], orc, FIELD_RTOL, 3)
+    assert np.max(np.abs(sims[2].read_particles()["X"] - orc.particles()["X"])) < POS_ATOL
