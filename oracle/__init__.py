@@ -93,6 +93,8 @@ def lib():
             "orc_time": (C.c_long, [P]),
             "orc_lagrange_weights": (C.c_int, [C.c_double, C.c_int, D]),
             "orc_delta_h": (C.c_double, [C.c_double]),
+            "orc_md_path": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_double, C.c_int, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -239,6 +241,19 @@ class Oracle:
 
     def nusselt(self) -> float:
         return float(self.L.orc_nusselt(self.h))
+
+    def md_path(self, n, a, Fn, ds):
+        """Tangential force after each update of one contact with the
+        Mindlin-Deresiewicz history (law 2), along the prescribed normal forces
+        Fn[k] and displacement increments ds[k] (k x 3), contact radius a."""
+        n = _f64(n)
+        Fn = _f64(Fn)
+        ds = _f64(ds, (-1, 3))
+        out = np.zeros((len(Fn), 3))
+        rc = self.L.orc_md_path(self.h, _dp(n), float(a), len(Fn), _dp(Fn), _dp(ds), _dp(out))
+        if rc != 0:
+            raise ValueError("the contact law is not the Mindlin-Deresiewicz history law")
+        return out
 
     def _pairs(self, fn):
         n = fn(self.h, None, 0)

@@ -75,9 +75,22 @@ static const double W3Q15[15] = {2.0 / 9,  1.0 / 9,  1.0 / 9,  1.0 / 9,  1.0 / 9
 static const double PI = 3.14159265358979323846;
 
 /* ---------------------------------------------------------------- state */
+/* Mindlin-Deresiewicz loading history of one contact (law ORC_HERTZ_MD_HIST):
+ * e the contact's reference tangential direction (set at its first tangential
+ * displacement, carried in the tangent plane), k the branch (0 loading,
+ * 1 unloading, 2 reloading), Ts / Tss the tangential force along e at the
+ * last unloading / reloading turning point, Fn_prev the normal force of the
+ * previous update. */
+typedef struct {
+    double e[3];
+    double Ts, Tss, Fn_prev;
+    int k;
+} md_state;
+
 typedef struct {
     int i, j;
     double ft[3];
+    md_state md;
 } contact;
 
 struct orc_sim {
@@ -104,6 +117,7 @@ struct orc_sim {
     double *J, *U0, *W0;  /* optional hydrodynamic Jacobian [np][18] and the velocities at the step start */
     int point;            /* particle model: 1 = one PIBM point per particle, d_p <= h (the paper's own regime) */
     double* wall_ft; /* [np][6][3] */
+    md_state* wall_md; /* [np][6] loading history of the wall contacts */
     contact* cont;
     int ncont;
     /* static off-node markers */
@@ -574,6 +588,7 @@ static contact* find_contacts(const orc_sim* s, int* count) {
                         out[n].i = i;
                         out[n].j = j;
                         out[n].ft[0] = out[n].ft[1] = out[n].ft[2] = 0.0;
+                        memset(&out[n].md, 0, sizeof(md_state));
                         n++;
                     }
                 }
@@ -660,7 +675,7 @@ int orc_point_cells(int dim, const int* nlat, double cell_size, int np, const do
 /* Hertz normal force (text after Eq demgov) and Mindlin-Deresiewicz loading stiffness
  * k_t = 8 G* r_a, or the linear spring-dashpot law; returns F_n and sets kt_eff */
 static double normal_law(const orc_sim* s, double delta, double vn, double Rstar, double* kt_eff) {
-    if (s->law == ORC_HERTZ_MD) {
+    if (s->law == ORC_HERTZ_MD || s->law == ORC_HERTZ_MD_HIST) {
         double Estar = s->E / (2.0 * (1.0 - s->pois * s->pois));
         double G = s->E / (2.0 * (1.0 + s->pois));
         double Gstar = G / (2.0 * (1.0 - s->pois * s->pois));
@@ -686,14 +701,87 @@ static void tangential(const orc_sim* s, double ft[3], const double n[3], const 
     for (int a = 0; a < 3; a++) Ft_total[a] = ft[a] - s->gt * vt[a];
 }
 
+/* Tangential force with the Mindlin-Deresiewicz loading history (text after
+ * Eq demgov: increment 8 G* r_a theta_k dd_t + (-1)^k mu dF_n (1 - theta_k)),
+ * theta_k by the closure of Thornton and Yin (1991) for loading (k = 0),
+ * unloading (k = 1) and reloading (k = 2):
+ *   theta_0^3 = 1 - (T + mu dF_n) / (mu F_n)
+ *   theta_1^3 = 1 - (T* - T + 2 mu dF_n) / (2 mu F_n)
+ *   theta_2^3 = 1 - (T - T** + 2 mu dF_n) / (2 mu F_n)
+ * with T the tangential force along the contact's reference direction e and
+ * T*, T** its values at the last turning points.  The branch changes when the
+ * tangential displacement increment along e changes sign (loading -> unloading
+ * at T*, unloading -> reloading at T**, reloading -> loading once T climbs back
+ * to T*).  The force increment acts along the displacement increment (vector
+ * form, e carried in the tangent plane); Coulomb cap mu |F_n| on the total.
+ * kt8a = 8 G* r_a. */
+static void tangential_md(const orc_sim* s, double ft[3], md_state* md, const double n[3], const double vt[3],
+                          double kt8a, double Fn, double dt, double Ft_total[3]) {
+    double fn = ft[0] * n[0] + ft[1] * n[1] + ft[2] * n[2];
+    double en = md->e[0] * n[0] + md->e[1] * n[1] + md->e[2] * n[2];
+    for (int a = 0; a < 3; a++) {
+        ft[a] -= fn * n[a];
+        md->e[a] -= en * n[a];
+    }
+    double el = sqrt(md->e[0] * md->e[0] + md->e[1] * md->e[1] + md->e[2] * md->e[2]);
+    double ds[3] = {vt[0] * dt, vt[1] * dt, vt[2] * dt};
+    double dsl = sqrt(ds[0] * ds[0] + ds[1] * ds[1] + ds[2] * ds[2]);
+    if (el > 0.0) {
+        for (int a = 0; a < 3; a++) md->e[a] /= el;
+    } else if (dsl > 0.0) { /* first tangential displacement: T grows along e */
+        for (int a = 0; a < 3; a++) md->e[a] = -ds[a] / dsl;
+    }
+    const double mu = s->mu, N = fabs(Fn);
+    /* a contact's first update carries no loading history: its normal force
+     * jump from zero is not an increment of the slip annulus */
+    const double dFn = md->Fn_prev > 0.0 ? N - md->Fn_prev : 0.0;
+    const double T = ft[0] * md->e[0] + ft[1] * md->e[1] + ft[2] * md->e[2];
+    const double sgn = -(ds[0] * md->e[0] + ds[1] * md->e[1] + ds[2] * md->e[2]); /* > 0: T increases */
+    if (md->k == 0 && sgn < 0.0) {
+        md->k = 1;
+        md->Ts = T;
+    } else if (md->k == 1 && sgn > 0.0) {
+        md->k = 2;
+        md->Tss = T;
+    } else if (md->k == 2) {
+        if (sgn < 0.0) {
+            md->k = 1;
+            md->Ts = T;
+        } else if (T >= md->Ts) {
+            md->k = 0;
+        }
+    }
+    double th3 = 0.0;
+    if (mu * N > 0.0) {
+        if (md->k == 0) th3 = 1.0 - (T + mu * dFn) / (mu * N);
+        else if (md->k == 1) th3 = 1.0 - (md->Ts - T + 2.0 * mu * dFn) / (2.0 * mu * N);
+        else th3 = 1.0 - (T - md->Tss + 2.0 * mu * dFn) / (2.0 * mu * N);
+    }
+    if (th3 < 0.0) th3 = 0.0;
+    if (th3 > 1.0) th3 = 1.0;
+    const double th = cbrt(th3);
+    const double sk = (md->k == 1) ? -1.0 : 1.0; /* (-1)^k */
+    for (int a = 0; a < 3; a++) ft[a] += -kt8a * th * ds[a] + sk * mu * dFn * (1.0 - th) * md->e[a];
+    double mag = sqrt(ft[0] * ft[0] + ft[1] * ft[1] + ft[2] * ft[2]);
+    double cap = mu * N;
+    if (mag > cap) {
+        double sc = (mag > 0.0) ? cap / mag : 0.0;
+        for (int a = 0; a < 3; a++) ft[a] *= sc;
+    }
+    md->Fn_prev = N;
+    for (int a = 0; a < 3; a++) Ft_total[a] = ft[a] - s->gt * vt[a];
+}
+
 static void contact_forces(orc_sim* s, double dt) {
     /* new contact list; carry the tangential history of pairs that stay in contact */
     int n;
     contact* nc = find_contacts(s, &n);
     for (int k = 0; k < n; k++) {
         contact* old = (contact*)bsearch(&nc[k], s->cont, s->ncont, sizeof(contact), cmp_contact);
-        if (old)
+        if (old) {
             for (int a = 0; a < 3; a++) nc[k].ft[a] = old->ft[a];
+            nc[k].md = old->md;
+        }
     }
     free(s->cont);
     s->cont = nc;
@@ -725,7 +813,8 @@ static void contact_forces(orc_sim* s, double dt) {
         double Rstar = s->R[i] * s->R[j] / (s->R[i] + s->R[j]), kt_eff;
         double Fn = normal_law(s, delta, vn, Rstar, &kt_eff);
         double Ft[3], Fi[3], Ti[3], Tj[3];
-        tangential(s, nc[k].ft, nrm, vt, kt_eff, Fn, dt, Ft);
+        if (s->law == ORC_HERTZ_MD_HIST) tangential_md(s, nc[k].ft, &nc[k].md, nrm, vt, kt_eff, Fn, dt, Ft);
+        else tangential(s, nc[k].ft, nrm, vt, kt_eff, Fn, dt, Ft);
         for (int a = 0; a < 3; a++) Fi[a] = -Fn * nrm[a] + Ft[a];
         cross(ri, Ft, Ti);
         double rjn[3] = {aj * nrm[0], aj * nrm[1], aj * nrm[2]};
@@ -742,11 +831,13 @@ static void contact_forces(orc_sim* s, double dt) {
         for (int face = 0; face < 2 * s->D; face++) {
             int a = face / 2, hi = face % 2;
             double* ft = &s->wall_ft[(6 * (long)i + face) * 3];
+            md_state* wmd = &s->wall_md[6 * (long)i + face];
             if (axis_periodic(s, a)) continue;
             double dist = hi ? (s->n[a] - 0.5) - s->X[3 * i + a] : s->X[3 * i + a] + 0.5;
             double delta = s->R[i] - dist;
             if (!(delta > 0.0)) {
                 ft[0] = ft[1] = ft[2] = 0.0;
+                memset(wmd, 0, sizeof(md_state));
                 continue;
             }
             double nrm[3] = {0, 0, 0};
@@ -761,7 +852,8 @@ static void contact_forces(orc_sim* s, double dt) {
             double kt_eff;
             double Fn = normal_law(s, delta, vn, s->R[i], &kt_eff);
             double Ft[3], Ti[3];
-            tangential(s, ft, nrm, vt, kt_eff, Fn, dt, Ft);
+            if (s->law == ORC_HERTZ_MD_HIST) tangential_md(s, ft, wmd, nrm, vt, kt_eff, Fn, dt, Ft);
+            else tangential(s, ft, nrm, vt, kt_eff, Fn, dt, Ft);
             cross(ri, Ft, Ti);
             for (int b = 0; b < 3; b++) {
                 s->Fc[3 * i + b] += -Fn * nrm[b] + Ft[b];
@@ -891,6 +983,8 @@ static void free_particles(orc_sim* s) {
     }
     free(s->fixed);
     s->fixed = NULL;
+    free(s->wall_md);
+    s->wall_md = NULL;
     free(s->cont);
     s->cont = NULL;
     s->ncont = 0;
@@ -963,6 +1057,7 @@ int orc_set_particles(orc_sim* s, int n, const double* X, const double* U, const
         for (int p = 0; p < n; p++)
             if (R[p] > 0.5) return -1; /* a point particle has d_p <= h */
     s->wall_ft = (double*)calloc(18 * (n + 1), sizeof(double));
+    s->wall_md = (md_state*)calloc(6 * (n + 1), sizeof(md_state));
     s->fixed = (unsigned char*)calloc(n + 1, 1);
     for (int p = 0; p < n; p++) {
         for (int a = 0; a < 3; a++) {
@@ -1146,3 +1241,23 @@ int orc_relaxation(orc_sim* s, double* out) {
 }
 
 long orc_time(orc_sim* s) { return s->t; }
+
+/* Test entry: the tangential update of one contact with the Mindlin-Deresiewicz
+ * history along a prescribed path.  Normal n, contact radius a (k_t base
+ * 8 G* a with the law's G*), normal force Fn[k] and tangential displacement
+ * increment ds[3k..3k+2] at update k; writes the tangential force after each
+ * update to T_out[3k..].  Returns 0, or -1 if the law is not ORC_HERTZ_MD_HIST. */
+int orc_md_path(const orc_sim* s, const double* n, double a, int nsteps, const double* Fn, const double* ds,
+                double* T_out) {
+    if (s->law != ORC_HERTZ_MD_HIST) return -1;
+    double G = s->E / (2.0 * (1.0 + s->pois));
+    double Gstar = G / (2.0 * (1.0 - s->pois * s->pois));
+    double ft[3] = {0.0, 0.0, 0.0}, Ft[3];
+    md_state md;
+    memset(&md, 0, sizeof md);
+    for (int k = 0; k < nsteps; k++) {
+        tangential_md(s, ft, &md, n, ds + 3 * k, 8.0 * Gstar * a, Fn[k], 1.0, Ft);
+        for (int c = 0; c < 3; c++) T_out[3 * k + c] = ft[c];
+    }
+    return 0;
+}

@@ -50,7 +50,10 @@ typedef struct {
 
 enum { ORC_PERIODIC = 0, ORC_WALL = 1 };
 enum { ORC_ADIABATIC = 0, ORC_ISOTHERMAL = 1 };
-enum { ORC_SPRING_DASHPOT = 0, ORC_HERTZ_MD = 1 };
+/* ORC_HERTZ_MD: Hertz normal force, Mindlin no-slip tangential spring (theta_k = 1);
+ * ORC_HERTZ_MD_HIST: the same with the Mindlin-Deresiewicz loading history (theta_k
+ * of Thornton and Yin for loading, unloading and reloading) */
+enum { ORC_SPRING_DASHPOT = 0, ORC_HERTZ_MD = 1, ORC_HERTZ_MD_HIST = 2 };
 enum { ORC_RHO = 0, ORC_UX, ORC_UY, ORC_UZ, ORC_T, ORC_FBX, ORC_FBY, ORC_FBZ, ORC_QB };
 
 orc_sim* orc_create(const orc_params* p);
@@ -90,6 +93,8 @@ int      orc_relaxation(orc_sim* s, double* out);
 long     orc_time(orc_sim* s);
 int      orc_lagrange_weights(double x, int npts, double* w);
 double   orc_delta_h(double a);
+int      orc_md_path(const orc_sim* s, const double* n, double a, int nsteps, const double* Fn, const double* ds,
+                     double* T_out);
 
 #ifdef __cplusplus
 }
