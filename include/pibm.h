@@ -69,7 +69,7 @@ typedef enum {
 
 enum { PIBM_PERIODIC = 0, PIBM_WALL = 1 };           /* wall kind per face */
 enum { PIBM_ADIABATIC = 0, PIBM_ISOTHERMAL = 1 };    /* thermal condition per wall face */
-enum { PIBM_SPRING_DASHPOT = 0, PIBM_HERTZ_MD = 1 }; /* contact law */
+enum { PIBM_SPRING_DASHPOT = 0, PIBM_HERTZ_MD = 1, PIBM_HERTZ_MD_HIST = 2 }; /* contact law */
 /* population storage (deviation form f - w, g - w T_ref; arithmetic in FP32
  * for F32 / F16 / BF16, FP64 for F64; F16 stores the deviations scaled by 2^10
  * (flow) and 2^8 (thermal), BF16 unscaled) */
@@ -129,8 +129,14 @@ pibm_status pibm_set_wall(pibm_ctx* ctx, int face, int kind, int thermal, double
 
 /* Contact law (text after Eq demgov).  HERTZ_MD: F_n = 4/3 E* sqrt(R*) d^1.5 +
  * gamma_n v_n with 1/E* = (1-nu^2)/E + (1-nu^2)/E, tangential stiffness
- * 8 G* sqrt(d R*).  SPRING_DASHPOT: F_n = kn d + gamma_n v_n, stiffness kt.
- * Both: tangential force capped at mu |F_n|, tangential damping gamma_t. */
+ * 8 G* sqrt(d R*) (the loading branch, theta_k = 1).  HERTZ_MD_HIST: the same
+ * normal force, tangential increment 8 G* r_a theta_k dd_t + (-1)^k mu dF_n
+ * (1 - theta_k) with the Mindlin-Deresiewicz loading history: theta_k of
+ * Thornton and Yin for loading (k = 0), unloading (1) and reloading (2) along
+ * the contact's reference direction, T* / T** the turning points; its history
+ * is evaluated and kept in FP64 (theta_k is a cube root that is not Lipschitz
+ * at full slip).  SPRING_DASHPOT: F_n = kn d + gamma_n v_n, stiffness kt.  All: tangential
+ * force capped at mu |F_n|, tangential damping gamma_t. */
 pibm_status pibm_set_contact_law(pibm_ctx* ctx, int law, double E, double poisson, double mu,
                                  double kn, double kt, double gamma_n, double gamma_t);
 

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libpibm.so")
 PIBM_OK, PIBM_ERR_ARG, PIBM_ERR_OOM, PIBM_ERR_CUDA, PIBM_ERR_STATE, PIBM_ERR_UNSTABLE, PIBM_ERR_TIMEOUT = range(7)
 PERIODIC, WALL = 0, 1
 ADIABATIC, ISOTHERMAL = 0, 1
-SPRING_DASHPOT, HERTZ_MD = 0, 1
+SPRING_DASHPOT, HERTZ_MD, HERTZ_MD_HIST = 0, 1, 2
 STORE_F32, STORE_F64, STORE_F16, STORE_BF16 = 0, 1, 2, 3
 (TUNE_DEM_PARTICLES_PER_CTA, TUNE_LATTICE_ROW_TILES, TUNE_LATTICE_THREADS, TUNE_WIDE_INDEX, TUNE_TC_WAIT_POLLS,
  TUNE_COUPLING_THREADS, TUNE_COUPLING_ORDER) = range(7)

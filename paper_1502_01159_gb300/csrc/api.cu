@@ -395,17 +395,19 @@ pibm_status pibm_set_contact_law(pibm_ctx* ctx, int law, double E, double poisso
                                  double gamma_n, double gamma_t) {
     if (!ctx) return PIBM_ERR_ARG;
     Ctx& c = ctx->c;
-    if ((law != PIBM_SPRING_DASHPOT && law != PIBM_HERTZ_MD) || mu < 0 || (law == PIBM_HERTZ_MD && !(E > 0)) ||
-        (law == PIBM_HERTZ_MD && !(poisson > -1 && poisson < 1)) || (law == PIBM_SPRING_DASHPOT && !(kn >= 0)))
+    const bool hertz = law == PIBM_HERTZ_MD || law == PIBM_HERTZ_MD_HIST;
+    if ((law != PIBM_SPRING_DASHPOT && !hertz) || mu < 0 || (hertz && !(E > 0)) ||
+        (hertz && !(poisson > -1 && poisson < 1)) || (law == PIBM_SPRING_DASHPOT && !(kn >= 0)))
         return fail(ctx, PIBM_ERR_ARG, "invalid contact law");
     c.dem.law = law;
     // text after Eq demgov: 1/E* = (1 - nu^2)/E_1 + (1 - nu^2)/E_2, same for G*; equal materials
-    double Estar = law == PIBM_HERTZ_MD ? E / (2.0 * (1.0 - poisson * poisson)) : 0.0;
-    double G = law == PIBM_HERTZ_MD ? E / (2.0 * (1.0 + poisson)) : 0.0;
-    double Gstar = law == PIBM_HERTZ_MD ? G / (2.0 * (1.0 - poisson * poisson)) : 0.0;
+    double Estar = hertz ? E / (2.0 * (1.0 - poisson * poisson)) : 0.0;
+    double G = hertz ? E / (2.0 * (1.0 + poisson)) : 0.0;
+    double Gstar = hertz ? G / (2.0 * (1.0 - poisson * poisson)) : 0.0;
     c.dem.E_star = (float)Estar;
     c.dem.G_star = (float)Gstar;
     c.dem.mu = (float)mu;
+    c.dem.mu_d = mu;
     c.dem.kn = (float)kn;
     c.dem.kt = (float)kt;
     c.dem.gn = (float)gamma_n;
@@ -544,18 +546,20 @@ pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const doub
         c.nb_i[b] = (int*)A(sizeof(int) * C.cap);
         c.nb_j[b] = (int*)A(sizeof(int) * C.cap);
         c.nb_ft[b] = (float*)A(sizeof(float4) * 2 * C.cap);  // two substep buffers of (history, stamp)
+        c.nb_md[b] = (double*)A(sizeof(double) * 2 * MD_REC * C.cap);  // two substep buffers (loading history)
     }
     c.adj_start = (int*)A(sizeof(int) * (n + 2));
     c.adj_nb = (int*)A(sizeof(int) * c.adj_cap);
     c.adj_k = (int*)A(sizeof(int) * c.adj_cap);
     c.wall_ft = (float*)A(sizeof(float) * 18 * (n + 1));
+    c.wall_md = (double*)A(sizeof(double) * 6 * MD_REC * (n + 1));
     c.contact_pairs = (int*)A(sizeof(int) * 2 * C.cap);
     c.contact_scratch = (int*)A(sizeof(int) * (2 * n + 8));
     void* need[] = {c.X, c.U, c.W, c.Xb, c.R, c.rho, c.Tp, c.Cp, c.m, c.I, c.mg, c.im, c.iI, c.fixed, c.Fh, c.Th, c.Hh, c.Fc,
                     c.Fh_prev, c.Th_prev, c.Hh_prev, c.have_prev, c.adj_start_new,
                     c.Tc, c.box[0], c.box[1], c.cell_of, c.cell_cnt, c.cell_start, c.cell_ids, c.cnt_hi, c.cnt_lo, c.nb_start[0],
                     c.nb_start[1], c.nb_i[0], c.nb_i[1], c.nb_j[0], c.nb_j[1], c.nb_ft[0], c.nb_ft[1], c.adj_start,
-                    c.adj_nb, c.adj_k, c.wall_ft, c.contact_pairs, c.contact_scratch};
+                    c.adj_nb, c.adj_k, c.wall_ft, c.contact_pairs, c.contact_scratch, c.nb_md[0], c.nb_md[1], c.wall_md};
     for (void* p : need)
         if (!p) {
             dfree_group(ctx, GRP_PARTICLES);
@@ -1001,11 +1005,13 @@ static std::vector<BufRef> state_buffers(Ctx& c) {
                        {"Hh", c.Hh, v1}, {"Fc", c.Fc, sizeof(float) * 3 * n}, {"Tc", c.Tc, sizeof(float) * 3 * n}, {"Fh_prev", c.Fh_prev, v3},
                        {"Th_prev", c.Th_prev, v3}, {"Hh_prev", c.Hh_prev, v1}, {"have_prev", c.have_prev, sizeof(int)},
                        {"box0", c.box[0], sizeof(int) * 6 * n}, {"box1", c.box[1], sizeof(int) * 6 * n},
-                       {"wall_ft", c.wall_ft, sizeof(float) * 18 * n},
+                       {"wall_ft", c.wall_ft, sizeof(float) * 18 * n}, {"wall_md", c.wall_md, sizeof(double) * 6 * MD_REC * n},
                        {"nb_start0", c.nb_start[0], sizeof(int) * (n + 1)}, {"nb_start1", c.nb_start[1], sizeof(int) * (n + 1)},
                        {"nb_i0", c.nb_i[0], sizeof(int) * c.dem.cap}, {"nb_i1", c.nb_i[1], sizeof(int) * c.dem.cap},
                        {"nb_j0", c.nb_j[0], sizeof(int) * c.dem.cap}, {"nb_j1", c.nb_j[1], sizeof(int) * c.dem.cap},
                        {"nb_ft0", c.nb_ft[0], sizeof(float4) * 2 * c.dem.cap}, {"nb_ft1", c.nb_ft[1], sizeof(float4) * 2 * c.dem.cap},
+                       {"nb_md0", c.nb_md[0], sizeof(double) * 2 * MD_REC * c.dem.cap},
+                       {"nb_md1", c.nb_md[1], sizeof(double) * 2 * MD_REC * c.dem.cap},
                        {"adj_start", c.adj_start, sizeof(int) * (n + 1)}, {"adj_nb", c.adj_nb, sizeof(int) * c.adj_cap},
                        {"adj_k", c.adj_k, sizeof(int) * c.adj_cap}};
         for (auto& b : pv) v.push_back(b);

@@ -43,9 +43,12 @@ struct DemState {
     int *cell_of, *cell_cnt, *cell_start, *cell_ids, *cnt_hi, *cnt_lo;
     int *nb_start0, *nb_start1, *nb_i0, *nb_i1, *nb_j0, *nb_j1;
     float4 *nb_ft0, *nb_ft1;  // per list: two substep buffers of cap entries (history xyz, substep stamp)
+    double *nb_md0, *nb_md1;  // per list: two substep buffers of cap FP64 records (MD_REC doubles) of the
+                              // Mindlin-Deresiewicz history of law PIBM_HERTZ_MD_HIST
     int* nb_cur;              // [0] current list, [1] global substep counter
     int *adj_start, *adj_nb, *adj_k;
     float* wall_ft;
+    double* wall_md;  // [n][6][MD_REC]: the Mindlin-Deresiewicz history of the wall contacts
     int* dstat;
     int* flag;  // cluster-wide overflow flag
     int adj_cap;
@@ -107,7 +110,7 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 
 // Contact law in FP32: returns F_n and the tangential stiffness.
 __device__ __forceinline__ float normal_law(const DemCfg& C, float delta, float vn, float Rstar, float* kt_eff) {
-    if (C.law == PIBM_HERTZ_MD) {
+    if (C.law != PIBM_SPRING_DASHPOT) {  // Hertz (with or without the Mindlin-Deresiewicz history)
         *kt_eff = 8.0f * C.G_star * sqrtf(delta * Rstar);
         return (4.0f / 3.0f) * C.E_star * sqrtf(Rstar) * delta * sqrtf(delta) + C.gn * vn;
     }
@@ -129,14 +132,112 @@ __device__ __forceinline__ float3 tangential(const DemCfg& C, float3& h, float3 
     return f3(h.x - C.gt * vt.x, h.y - C.gt * vt.y, h.z - C.gt * vt.z);
 }
 
+// Tangential force with the Mindlin-Deresiewicz loading history (law
+// PIBM_HERTZ_MD_HIST): increment 8 G* r_a theta_k dd_t + (-1)^k mu dF_n
+// (1 - theta_k) with theta_k of Thornton and Yin for loading (k = 0),
+// unloading (1) and reloading (2) along the contact's reference direction e
+// (set at its first tangential displacement, kept in the tangent plane):
+//   theta_0^3 = 1 - (T + mu dF_n)/(mu F_n), theta_1^3 = 1 - (T* - T + 2 mu dF_n)/(2 mu F_n),
+//   theta_2^3 = 1 - (T - T** + 2 mu dF_n)/(2 mu F_n),
+// T the force along e; the branch turns when the displacement along e
+// reverses (reloading rejoins loading at T*); no history increment on a
+// contact's first update; Coulomb cap on the total.  kt8a = 8 G* r_a.
+//
+// Evaluated in FP64 on an FP64 record: theta_k is the cube root of a
+// difference that vanishes at full slip, so a relative error eps in T or
+// mu F_n moves theta by about eps^(1/3) there (FP32: 4e-3 of the stiffness
+// 8 G* r_a; FP64: 5e-6).  The inputs n, v_t, F_n and kt8a stay the kernel's
+// FP32 values.
+struct MdRec {
+    double h[3], e[3], fnp, ts, tss, k;  // the MD_REC doubles of one contact
+};
+
+__device__ __forceinline__ void md_load(const double* p, MdRec& r) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2), d = __ldcg(q + 3), e = __ldcg(q + 4);
+    r.h[0] = a.x, r.h[1] = a.y, r.h[2] = b.x, r.e[0] = b.y, r.e[1] = c.x, r.e[2] = c.y;
+    r.fnp = d.x, r.ts = d.y, r.tss = e.x, r.k = e.y;
+}
+
+__device__ __forceinline__ void md_store(double* p, const MdRec& r) {
+    double2* q = reinterpret_cast<double2*>(p);
+    q[0] = make_double2(r.h[0], r.h[1]), q[1] = make_double2(r.h[2], r.e[0]), q[2] = make_double2(r.e[1], r.e[2]);
+    q[3] = make_double2(r.fnp, r.ts), q[4] = make_double2(r.tss, r.k);
+}
+
+__device__ __forceinline__ void md_zero(MdRec& r) {
+    r.h[0] = r.h[1] = r.h[2] = r.e[0] = r.e[1] = r.e[2] = 0.0;
+    r.fnp = r.ts = r.tss = r.k = 0.0;
+}
+
+__device__ __forceinline__ float3 tangential_md(const DemCfg& C, MdRec& r, float3 nf, float3 vtf, float kt8af, float Fnf,
+                                                float dtf) {
+    const double n[3] = {nf.x, nf.y, nf.z}, vt[3] = {vtf.x, vtf.y, vtf.z};
+    const double kt8a = kt8af, dt = dtf;
+    const double hn = r.h[0] * n[0] + r.h[1] * n[1] + r.h[2] * n[2];
+    const double en = r.e[0] * n[0] + r.e[1] * n[1] + r.e[2] * n[2];
+    for (int a = 0; a < 3; a++) {
+        r.h[a] -= hn * n[a];
+        r.e[a] -= en * n[a];
+    }
+    const double el = sqrt(r.e[0] * r.e[0] + r.e[1] * r.e[1] + r.e[2] * r.e[2]);
+    const double ds[3] = {vt[0] * dt, vt[1] * dt, vt[2] * dt};
+    const double dsl = sqrt(ds[0] * ds[0] + ds[1] * ds[1] + ds[2] * ds[2]);
+    if (el > 0.0) {
+        for (int a = 0; a < 3; a++) r.e[a] /= el;
+    } else if (dsl > 0.0) {
+        for (int a = 0; a < 3; a++) r.e[a] = -ds[a] / dsl;
+    }
+    const double mu = C.mu_d, N = fabs((double)Fnf);
+    const double dFn = r.fnp > 0.0 ? N - r.fnp : 0.0;
+    const double T = r.h[0] * r.e[0] + r.h[1] * r.e[1] + r.h[2] * r.e[2];
+    const double sgn = -(ds[0] * r.e[0] + ds[1] * r.e[1] + ds[2] * r.e[2]);  // > 0: T increases
+    int k = (int)r.k;
+    if (k == 0 && sgn < 0.0) {
+        k = 1;
+        r.ts = T;
+    } else if (k == 1 && sgn > 0.0) {
+        k = 2;
+        r.tss = T;
+    } else if (k == 2) {
+        if (sgn < 0.0) {
+            k = 1;
+            r.ts = T;
+        } else if (T >= r.ts) {
+            k = 0;
+        }
+    }
+    double th3 = 0.0;
+    if (mu * N > 0.0) {
+        if (k == 0) th3 = 1.0 - (T + mu * dFn) / (mu * N);
+        else if (k == 1) th3 = 1.0 - (r.ts - T + 2.0 * mu * dFn) / (2.0 * mu * N);
+        else th3 = 1.0 - (T - r.tss + 2.0 * mu * dFn) / (2.0 * mu * N);
+    }
+    th3 = fmin(fmax(th3, 0.0), 1.0);
+    const double th = cbrt(th3);
+    const double sk = k == 1 ? -1.0 : 1.0;
+    const double kd = kt8a * th, kn = sk * mu * dFn * (1.0 - th);
+    for (int a = 0; a < 3; a++) r.h[a] += -kd * ds[a] + kn * r.e[a];
+    const double mag = sqrt(r.h[0] * r.h[0] + r.h[1] * r.h[1] + r.h[2] * r.h[2]);
+    const double cap = mu * N;
+    if (mag > cap) {
+        const double sc = mag > 0.0 ? cap / mag : 0.0;
+        for (int a = 0; a < 3; a++) r.h[a] *= sc;
+    }
+    r.fnp = N;
+    r.k = k;
+    const double gt = C.gt;
+    return f3((float)(r.h[0] - gt * vt[0]), (float)(r.h[1] - gt * vt[1]), (float)(r.h[2] - gt * vt[2]));
+}
+
 // Pair (a < b) in canonical order, in contact (d2 < SS): force on a, torques
 // on a and b, new history.  d = X_b - X_a and d2 = |d|^2, SS = (R_a + R_b)^2
 // come from the caller's exact FP64 contact test; the only FP64 operation left
 // is the overlap S^2 - d^2, which cancels.  Both partners call this with the
 // same inputs and get the same bits.
 __device__ __forceinline__ void pair_force(const DemCfg& C, const Pub& A, const Pub& B, const double* d, double d2,
-                                           double SS, float Raf, float Rbf, float3& h, float dtf, float3& Fa, float3& Ta,
-                                           float3& Tb) {
+                                           double SS, float Raf, float Rbf, float3& h, MdRec& md, float dtf,
+                                           float3& Fa, float3& Ta, float3& Tb) {
     float distf = sqrtf((float)d2);
     const float Sf = Raf + Rbf;
     float delta = (float)(SS - d2) / (Sf + distf);
@@ -149,7 +250,13 @@ __device__ __forceinline__ void pair_force(const DemCfg& C, const Pub& A, const 
     float3 vt = f3(vr.x - vn * nn.x, vr.y - vn * nn.y, vr.z - vn * nn.z);
     float Rstar = Raf * Rbf / Sf, kt_eff;
     float Fn = normal_law(C, delta, vn, Rstar, &kt_eff);
-    float3 Ft = tangential(C, h, nn, vt, kt_eff, Fn, dtf);
+    float3 Ft;
+    if (C.law == PIBM_HERTZ_MD_HIST) {
+        Ft = tangential_md(C, md, nn, vt, kt_eff, Fn, dtf);
+        h = f3((float)md.h[0], (float)md.h[1], (float)md.h[2]);
+    } else {
+        Ft = tangential(C, h, nn, vt, kt_eff, Fn, dtf);
+    }
     Ta = cross3(f3(ai * nn.x, ai * nn.y, ai * nn.z), Ft);
     Tb = cross3(f3(aj * nn.x, aj * nn.y, aj * nn.z), Ft);
     Fa = f3(-Fn * nn.x + Ft.x, -Fn * nn.y + Ft.y, -Fn * nn.z + Ft.z);
@@ -204,6 +311,7 @@ __device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, 
         int a = face >> 1, hi = face & 1;
         if (!C.walled[a]) continue;
         float* ftp = S.wall_ft + 3 * (6 * p + face);
+        double* mdp = S.wall_md + MD_REC * (6 * p + face);
         // FP32 prefilter on the distance to the wall plane, exact FP64 test when close
         const float distf = hi ? C.hif[a] - me.xf[a] : me.xf[a] - C.lof[a];
         double dd = -1.0;
@@ -211,6 +319,8 @@ __device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, 
         if (!(dd > 0.0)) {
             if (mask & (1 << face)) {
                 ftp[0] = ftp[1] = ftp[2] = 0.f;
+                if (C.law == PIBM_HERTZ_MD_HIST)
+                    for (int q = 0; q < MD_REC; q++) mdp[q] = 0.0;
                 mask &= ~(1 << face);
             }
             continue;
@@ -231,7 +341,17 @@ __device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, 
         float3 h = f3(0.f, 0.f, 0.f);
         if (mask & (1 << face))
             h = hpre ? f3(hpre[3 * face], hpre[3 * face + 1], hpre[3 * face + 2]) : f3(__ldcg(ftp), __ldcg(ftp + 1), __ldcg(ftp + 2));
-        float3 Ft = tangential(C, h, nn, vt, kt_eff, Fn, dtf);
+        float3 Ft;
+        if (C.law == PIBM_HERTZ_MD_HIST) {
+            MdRec md;
+            if (mask & (1 << face)) md_load(mdp, md);
+            else md_zero(md);
+            Ft = tangential_md(C, md, nn, vt, kt_eff, Fn, dtf);
+            md_store(mdp, md);
+            h = f3((float)md.h[0], (float)md.h[1], (float)md.h[2]);
+        } else {
+            Ft = tangential(C, h, nn, vt, kt_eff, Fn, dtf);
+        }
         ftp[0] = h.x, ftp[1] = h.y, ftp[2] = h.z;
         mask |= 1 << face;
         float3 Ti = cross3(ri, Ft);
@@ -349,6 +469,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
     const int* nb_start = cur ? S.nb_start1 : S.nb_start0;
     const int* nb_j = cur ? S.nb_j1 : S.nb_j0;
     float4* nb_ft = cur ? S.nb_ft1 : S.nb_ft0;
+    double* nb_md = cur ? S.nb_md1 : S.nb_md0;
     const double dt = C.dt;
     const float dtf = (float)dt;
     int gnow = gbase;  // global substep counter after this launch
@@ -483,6 +604,9 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             const int gsub = gbase + sub;
             const float4* hist_old = nb_ft + (size_t)(gsub & 1) * C.cap;
             float4* hist_new = nb_ft + (size_t)((gsub + 1) & 1) * C.cap;
+            const double* md_old = nb_md + (size_t)(gsub & 1) * MD_REC * C.cap;
+            double* md_new = nb_md + (size_t)((gsub + 1) & 1) * MD_REC * C.cap;
+            const bool mdh = C.law == PIBM_HERTZ_MD_HIST;
             // tpp threads per particle (4 up to 64 particles per CTA, 2 up to 128, else
             // 1; 8 measured slower than 4 on 2-D beds): consecutive lanes, each taking
             // every tpp-th neighbour (the first also the walls, after the pairs);
@@ -533,6 +657,8 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                         const float dxf = other.xf[0] - me.xf[0], dyf = other.xf[1] - me.xf[1], dzf = other.xf[2] - me.xf[2];
                         const float sf = Rpf + other.rf + 1e-3f;
                         float3 Fa = f3(0.f, 0.f, 0.f), Ta = Fa, Tb = Fa, h = Fa;
+                        MdRec md;
+                        md_zero(md);
                         bool contact = false;
                         if (dxf * dxf + dyf * dyf + dzf * dzf < sf * sf) {
                             const Pub& A = first ? me : other;
@@ -546,12 +672,19 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                             const double SS = Ssum * Ssum;
                             contact = d2 < SS;
                             if (contact) {
-                                if (__float_as_int(hv.w) == gsub - 1) h = f3(hv.x, hv.y, hv.z);
-                                pair_force(C, A, B, d, d2, SS, first ? Rpf : other.rf, first ? other.rf : Rpf, h, dtf, Fa, Ta, Tb);
+                                if (__float_as_int(hv.w) == gsub - 1) {
+                                    h = f3(hv.x, hv.y, hv.z);
+                                    if (mdh) md_load(md_old + (size_t)MD_REC * k, md);
+                                }
+                                pair_force(C, A, B, d, d2, SS, first ? Rpf : other.rf, first ? other.rf : Rpf, h, md, dtf,
+                                           Fa, Ta, Tb);
                             }
                         }
                         if (first) {
-                            if (contact) hist_new[k] = make_float4(h.x, h.y, h.z, __int_as_float(gsub));
+                            if (contact) {
+                                hist_new[k] = make_float4(h.x, h.y, h.z, __int_as_float(gsub));
+                                if (mdh) md_store(md_new + (size_t)MD_REC * k, md);
+                            }
                             F[0] += Fa.x, F[1] += Fa.y, F[2] += Fa.z;
                             T[0] += Ta.x, T[1] += Ta.y, T[2] += Ta.z;
                         } else {
@@ -769,6 +902,8 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
     // old list; the new list gets them in the same buffer with the same stamp
     float4* nft = (cur ? S.nb_ft0 : S.nb_ft1) + (size_t)(gnow & 1) * C.cap;
     const float4* oft = nb_ft + (size_t)(gnow & 1) * C.cap;
+    double* nmd = (cur ? S.nb_md0 : S.nb_md1) + (size_t)(gnow & 1) * MD_REC * C.cap;
+    const double* omd = (cur ? S.nb_md1 : S.nb_md0) + (size_t)(gnow & 1) * MD_REC * C.cap;
     if (rank == 0) {
         cta_scan(S.cnt_hi, nst, n, sh);
         for (int i = threadIdx.x; i < n; i += blockDim.x) S.cnt_lo[i] += S.cnt_hi[i];
@@ -820,6 +955,12 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 else Hh = mid - 1;
             }
             nft[o + r] = found >= 0 ? __ldcg(oft + found) : make_float4(0.f, 0.f, 0.f, __int_as_float(-2));
+            if (C.law == PIBM_HERTZ_MD_HIST) {  // (a pair without history is stamped invalid above)
+                MdRec md;
+                if (found >= 0) md_load(omd + (size_t)MD_REC * found, md);
+                else md_zero(md);
+                md_store(nmd + (size_t)MD_REC * (o + r), md);
+            }
         }
     }
     cl.sync();
@@ -930,6 +1071,8 @@ static DemState dem_state(Ctx* c) {
     S.nb_i0 = c->nb_i[0], S.nb_i1 = c->nb_i[1];
     S.nb_j0 = c->nb_j[0], S.nb_j1 = c->nb_j[1];
     S.nb_ft0 = (float4*)c->nb_ft[0], S.nb_ft1 = (float4*)c->nb_ft[1];
+    S.nb_md0 = c->nb_md[0], S.nb_md1 = c->nb_md[1];
+    S.wall_md = c->wall_md;
     S.nb_cur = c->nb_cur;
     S.adj_start = c->adj_start, S.adj_nb = c->adj_nb, S.adj_k = c->adj_k;
     S.wall_ft = c->wall_ft;

@@ -223,6 +223,9 @@ __device__ __forceinline__ void load_node(const Geo& G, const S* __restrict__ f,
 }
 
 // ------------------------------------------------------------------ context
+// FP64 record of one contact's Mindlin-Deresiewicz loading history: tangential
+// force (3), loading direction e (3), previous normal force, T*, T**, branch k
+constexpr int MD_REC = 10;
 struct DemCfg {
     int n;            // particles
     int dim;
@@ -230,6 +233,7 @@ struct DemCfg {
     double dt;        // 1 / nsub
     int law;
     float E_star, G_star, mu, kn, kt, gn, gt;
+    double mu_d;      // mu in FP64 (the loading-history law evaluates in FP64)
     double g[3];      // particle gravity
     double lo[3], hi[3];  // wall planes (-0.5, n - 0.5)
     float lof[3], hif[3]; // the same in FP32 (prefilters)
@@ -319,6 +323,8 @@ struct Ctx {
     int* nb_i[2];
     int* nb_j[2];
     float* nb_ft[2];
+    double* nb_md[2];  // Mindlin-Deresiewicz history per pair (law PIBM_HERTZ_MD_HIST), MD_REC doubles per entry
+    double* wall_md;   // [n][6][MD_REC] the same for the wall contacts
     int* nb_cur;      // device ints: current list, current history buffer
     int *adj_start, *adj_nb, *adj_k;
     float* wall_ft;

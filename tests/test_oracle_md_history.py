@@ -113,3 +113,33 @@ def test_first_contact_update_has_no_history_increment():
     ds = np.array([[-1e-6, 0.0, 0.0]])
     T = o.md_path([0.0, 0.0, 1.0], A, [N], ds)
     assert abs(T[0, 0] - _k0() * 1e-6) < 1e-9 * _k0() * 1e-6 + 1e-18
+
+
+def _departure(case, steps, eps=1e-15):
+    """max |dX| between the oracle on `case` and on `case` with its positions
+    scaled by (1 + eps), after `steps` steps"""
+    import copy
+    other = copy.deepcopy(case)
+    other["particles"]["X"] = other["particles"]["X"] * (1.0 + eps)
+    a, b = oracle.Oracle(case), oracle.Oracle(other)
+    a.step(steps)
+    b.step(steps)
+    d = np.max(np.abs(a.particles()["X"] - b.particles()["X"]))
+    a.close()
+    b.close()
+    return d
+
+
+def test_history_trajectory_conditioning():
+    """The explicit theta_k update maps T to T + 8 G* a theta(T) dd, whose
+    slope 1 - 8 G* a |dd| / (3 theta^2 mu F_n) leaves [-1, 1] near full slip:
+    there the update amplifies differences, and the cube root turns a rounding
+    residual eps of the slip condition into eps^(1/3).  On the dense pile,
+    whose contacts sit at or near slip, a 1e-15 change of the positions moves
+    the law-2 trajectory by more than 1e-7 within one step, where law 1
+    (theta = 1) stays below 1e-10; on the dilute colliding gas law 2 stays
+    below 1e-9 over 100 steps.  Element-by-element parity of law 2 is
+    therefore checked on the gas, and on the pile only the whole state."""
+    assert _departure(W.dense_pile(law=2), 1) > 1e-7
+    assert _departure(W.dense_pile(law=1), 10) < 1e-10
+    assert _departure(W.colliding_gas(law=2), 100) < 1e-9

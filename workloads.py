@@ -235,3 +235,52 @@ def random_populations(case, config_index=7, amp=0.01):
     f = w[:, None, None, None] * (1.0 + amp * (gen.random((len(w), nz, ny, nx)) - 0.5))
     g = wg[:, None, None, None] * (0.5 + amp * (gen.random((len(wg), nz, ny, nx)) - 0.5))
     return f, g
+
+
+def dense_pile(seed=71, law=1, mu=0.3):
+    """DEM only: 7 x 7 x 6 spheres on a square lattice of spacing 4.98 resting on
+    the floor of a 36 x 36 x 40 walled box, diameters 4.94 .. 5.02 (neighbours
+    overlap by up to 0.04 or sit up to 0.04 apart), small random velocities and
+    spins; Hertz E = 200, nu = 0.33, normal and tangential damping; gravity 1e-3
+    along -z; no fluid coupling."""
+    gen = rng(seed)
+    nxs, nys, nzs, s, L = 7, 7, 6, 4.98, 36
+    idx = np.array([(i, j, k) for k in range(nzs) for j in range(nys) for i in range(nxs)], dtype=float)
+    n = len(idx)
+    X = np.zeros((n, 3))
+    X[:, 0] = (L - 1) / 2.0 + (idx[:, 0] - (nxs - 1) / 2.0) * s + 0.02 * (gen.random(n) - 0.5)
+    X[:, 1] = (L - 1) / 2.0 + (idx[:, 1] - (nys - 1) / 2.0) * s + 0.02 * (gen.random(n) - 0.5)
+    X[:, 2] = 2.0 + idx[:, 2] * s + 0.02 * (gen.random(n) - 0.5)
+    U = gen.normal(size=(n, 3)) * 2e-3
+    Wv = gen.normal(size=(n, 3)) * 1e-3
+    R = 2.47 + 0.04 * rng(seed + 1).random(n)
+    case = periodic_box(shape=(L, L, 40), dim=3, buoyancy=False)
+    case.update(walls=[(1, 1, 0.0)] * 6, pibm=False, g_particle=[0.0, 0.0, -1e-3],
+                contact=dict(hertz(E=200.0, poisson=0.33, mu=mu, gamma_n=10.0, gamma_t=2.0), law=law),
+                particles=dict(X=X, U=U, W=Wv, R=R, rho_p=np.full(n, 1.5), T_p=np.zeros(n)),
+                name=f"pile294_law{law}")
+    return case
+
+
+def colliding_gas(seed=5, n_p=160, L=56, speed=2e-2, law=2, mu=0.3):
+    """DEM only: n_p spheres of radius 2.4 .. 2.5 placed at random (centres at
+    least 5.3 apart) in an L^3 walled box, Gaussian velocities of scale `speed`
+    and spins of scale 0.3 speed, no gravity, no fluid coupling: binary
+    collisions with the wall and pair contacts of Hertz E = 200, nu = 0.33,
+    normal and tangential damping."""
+    gen = rng(seed)
+    X = []
+    while len(X) < n_p:
+        x = 4 + (L - 9) * gen.random(3)
+        if all(np.linalg.norm(x - y) > 5.3 for y in X):
+            X.append(x)
+    X = np.array(X)
+    U = gen.normal(size=(n_p, 3)) * speed
+    Wv = gen.normal(size=(n_p, 3)) * speed * 0.3
+    R = 2.4 + 0.1 * gen.random(n_p)
+    case = periodic_box(shape=(L, L, L), dim=3, buoyancy=False)
+    case.update(walls=[(1, 1, 0.0)] * 6, pibm=False, g_particle=[0.0, 0.0, 0.0],
+                contact=dict(hertz(E=200.0, poisson=0.33, mu=mu, gamma_n=10.0, gamma_t=2.0), law=law),
+                particles=dict(X=X, U=U, W=Wv, R=R, rho_p=np.full(n_p, 1.5), T_p=np.zeros(n_p)),
+                name=f"gas{n_p}_law{law}")
+    return case
