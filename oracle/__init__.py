@@ -225,12 +225,12 @@ class Oracle:
         return {"F": F, "T": T, "H": H}
 
     def set_hydro_jacobian(self, J=None):
-        """n x 18 Jacobian (J_FU row-major, then J_TW) or None."""
+        """n x 19 Jacobian (J_FU row-major, J_TW row-major, J_HT) or None."""
         if J is None:
             self.L.orc_set_hydro_jacobian(self.h, None)
             self._J = None
         else:
-            self._J = _f64(J, (-1, 18))
+            self._J = _f64(J, (-1, 19))
             self.L.orc_set_hydro_jacobian(self.h, _dp(self._J))
 
     def contact_forces(self):

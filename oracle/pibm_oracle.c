@@ -873,16 +873,17 @@ static double hydro(const orc_sim* s, const double* cur, const double* prev, int
 }
 
 /* Eq demgov: m dU/dt = m (1 - rho_f/rho_p) g + F_fpi + sum F_c ; I domega/dt = tau_p + sum T_c.
- * With a hydrodynamic Jacobian J set (a learned estimate of dF_fpi/dU and
- * dtau_p/domega), the held hydrodynamic load is corrected inside the step by
- * J_FU (U - U_start) and J_TW (omega - omega_start). */
+ * With a hydrodynamic Jacobian J set (19 values per particle: a learned
+ * estimate of dF_fpi/dU, dtau_p/domega and dH_p/dT_p), the held hydrodynamic
+ * load is corrected inside the step by J_FU (U - U_start) and J_TW (omega -
+ * omega_start); the heat row acts in the thermosensitive update (orc_step). */
 static void kick(orc_sim* s, double h) {
     for (int p = 0; p < s->np; p++) {
         if (s->fixed[p]) continue;
         double mg = s->m[p] * (1.0 - 1.0 / s->rho[p]);
         double dF[3] = {0, 0, 0}, dT[3] = {0, 0, 0};
         if (s->J) {
-            const double* J = s->J + 18 * p;
+            const double* J = s->J + 19 * p;
             for (int a = 0; a < 3; a++)
                 for (int b = 0; b < 3; b++) {
                     dF[a] += J[3 * a + b] * (s->U[3 * p + b] - s->U0[3 * p + b]);
@@ -1115,8 +1116,16 @@ int orc_step(orc_sim* s, int nsteps) {
     for (int k = 0; k < nsteps; k++) {
         lattice_step(s);
         dem(s);
-        for (int p = 0; p < s->np; p++) /* thermosensitive particles: C_p dT_p = -H_p dt */
-            if (s->Cp[p] > 0.0) s->Tp[p] -= hydro(s, s->Hh, s->Hp, p) / s->Cp[p];
+        /* thermosensitive particles: C_p dT_p = -H_p dt.  With a Jacobian set, the
+         * held heat flux is corrected by J_HT (T_p,new - T_p) as well, solved for
+         * T_p,new: C_p (T_new - T) = -(H + J_HT (T_new - T)); J_HT < 0 (a particle
+         * that warms drawing more heat) is taken as 0. */
+        for (int p = 0; p < s->np; p++)
+            if (s->Cp[p] > 0.0) {
+                double Jh = s->J ? s->J[19 * p + 18] : 0.0;
+                if (!(Jh > 0.0)) Jh = 0.0;
+                s->Tp[p] -= hydro(s, s->Hh, s->Hp, p) / (s->Cp[p] + Jh);
+            }
         s->t++;
         if (s->np > 0) {
             memcpy(s->Fp, s->Fh, sizeof(double) * 3 * s->np);
@@ -1182,10 +1191,10 @@ int orc_set_hydro_jacobian(orc_sim* s, const double* J) {
     free(s->W0);
     s->J = s->U0 = s->W0 = NULL;
     if (!J || s->np == 0) return 0;
-    s->J = (double*)malloc(sizeof(double) * 18 * s->np);
+    s->J = (double*)malloc(sizeof(double) * 19 * s->np);
     s->U0 = (double*)malloc(sizeof(double) * 3 * s->np);
     s->W0 = (double*)malloc(sizeof(double) * 3 * s->np);
-    memcpy(s->J, J, sizeof(double) * 18 * s->np);
+    memcpy(s->J, J, sizeof(double) * 19 * s->np);
     return 0;
 }
 

@@ -73,9 +73,9 @@ int      orc_read_populations(orc_sim* s, double* f, double* g);
 int      orc_read_particles(orc_sim* s, double* X, double* U, double* W, double* T_p);
 int      orc_read_particle_forces(orc_sim* s, double* F, double* T, double* H);
 int      orc_read_contact_forces(orc_sim* s, double* F, double* T);
-/* Optional hydrodynamic Jacobian, n*18 doubles per particle: J_FU (3x3,
- * row-major, dF_a/dU_b) then J_TW (dtau_a/domega_b); NULL removes it.  Kept
- * until replaced or until the particles are reset. */
+/* Optional hydrodynamic Jacobian, 19 doubles per particle: J_FU (3x3,
+ * row-major, dF_a/dU_b), J_TW (dtau_a/domega_b), then J_HT (dH/dT_p); NULL
+ * removes it.  Kept until replaced or until the particles are reset. */
 int      orc_set_hydro_jacobian(orc_sim* s, const double* J);
 /* Particle model for the next orc_set_particles: 0 resolved (the covered
  * nodes are the PIBM points), 1 one PIBM point per particle at its centre

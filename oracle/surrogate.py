@@ -22,28 +22,41 @@ features are taken against that fluid.  Definitions (lattice units):
   raw fields  the moments before the coupling's correction, u = j / rho with
               rho = sum f, j = sum e f, and T0 = sum g (see raw_fields): the
               coupling acts on exactly these (F_f = 2 (rho U_l - j))
-  V_s, Om_s   rigid-motion fit of the raw fluid velocity over S_p about X_p:
-              minimise sum |u(r) - V - Om x d|^2, d = r - X_p; the normal
-              equations, with n nodes, D = sum d, M = sum (|d|^2 I - d d^T):
-                  n V - D x Om = sum u,   D x V + M Om = sum d x u
-              (2-D: unknowns V_x, V_y, Om_z); exact for any rigid field
-  T_s         mean raw fluid temperature T0 over S_p
+  V_s, Om_s   rigid-motion fit of the raw fluid velocity over S_p about X_p,
+              weighted as the coupling weighs each node, w = epsilon rho:
+              minimise sum w |u(r) - V - Om x d|^2, d = r - X_p; with m =
+              sum w, D = sum w d, M = sum w (|d|^2 I - d d^T) the normal
+              equations are
+                  m V - D x Om = sum w u,   D x V + M Om = sum w d x u
+              (w u = epsilon j; 2-D: unknowns V_x, V_y, Om_z); exact for any
+              rigid field.  With these weights the coupling's load at a frozen
+              fluid state is exactly linear in the velocity features:
+                  F = -2 m (U_p - V_s) - 2 (omega_p - Om_s) x D,
+                  tau = -2 D x (U_p - V_s) - 2 M (omega_p - Om_s)
+  T_s         raw fluid temperature T0 averaged over S_p with weights
+              epsilon; then H = 2 kappa_T (sum epsilon) (T_p - T_s)
   features    U_p - V_s (3), omega_p - Om_s (3), T_p - T_s (1),
               phi_p = sum_{q != p, |X_q - X_p| < 4 R_p} (R_q / 4 R_p)^D (1),
               the four smallest surface gaps |X_q - X_p| - R_p - R_q, each
               capped at 2 R_p and padded with 2 R_p (4)
   targets     the PIBM coupling's force (3), torque (3) and heat flux (1) of
               the state (Eq lbm13 and its analogues)
-  network     12 -> 64 -> 64 -> 64 -> 7, tanh on the hidden layers, inputs
-              and outputs standardised with the training set's mean and
-              standard deviation (a standard deviation below 1e-12 counts as 1)
-  loss        mean over rows and outputs of the squared standardised error
+  network     12 -> 64 -> 64 -> 64 -> 7, tanh on the hidden layers, plus a
+              linear path from the inputs to the outputs (y = W4 a3 + b4 +
+              Ws x); inputs and outputs standardised with the training set's
+              mean and standard deviation (a standard deviation below 1e-12
+              counts as 1)
+  training    the linear path and the output bias first by least squares
+              over the training set (ridge 1e-8 per row), the hidden layers'
+              output weights W4 zero; then every parameter by Adam on the
+              mean squared standardised error
   Jacobian    secant over delta standard deviations of each of the six
-              velocity / spin features: J_FU[a][b] = dF_a / dU_b and
-              J_TW[a][b] = dtau_a / domega_b of the coupling; the DEM holds
-              the mean of the couplings of t and t-1 and a velocity change
-              enters only the newer one, so it applies half of it
-              (applied_jacobian)
+              velocity / spin features and of the temperature feature:
+              J_FU[a][b] = dF_a / dU_b, J_TW[a][b] = dtau_a / domega_b of the
+              coupling and J_HT = dH / dT_p; the DEM holds the mean of the
+              couplings of t and t-1 and a change of the particle's state
+              enters only the newer one, so it applies half of each
+              (applied_jacobian); 19 values per particle
   gate        e = sum_p |F_mlp,p - F_pibm,p| / sum_p |F_pibm,p|; the
               Jacobian is applied in the next step only when e <= bound
 """
@@ -112,23 +125,25 @@ def features(fields, X, U, W, R, Tp, dim):
     for p in range(n):
         nodes = owned(region(X[p], R[p], (nx, ny, nz), dim), p, X, R, dim)
         x, y, z = nodes[:, 0], nodes[:, 1], nodes[:, 2]
+        eps = np.minimum(_eps(nodes, X[p], R[p], dim), 1.0)
+        w = eps * fields["rho"][z, y, x]
         u = np.stack([fields["ux"][z, y, x], fields["uy"][z, y, x], uz[z, y, x]], axis=1)
-        Ts = fields["T"][z, y, x].mean()
+        Ts = np.sum(eps * fields["T"][z, y, x]) / np.sum(eps)
         d = nodes.astype(np.float64) - np.asarray(X[p])[None, :]
         if dim == 2:
             d[:, 2] = 0.0
-        m = len(nodes)
-        D = d.sum(axis=0)
-        su = u.sum(axis=0)
-        sdu = np.cross(d, u).sum(axis=0)
+        m = np.sum(w)
+        D = (w[:, None] * d).sum(axis=0)
+        su = (w[:, None] * u).sum(axis=0)
+        sdu = (w[:, None] * np.cross(d, u)).sum(axis=0)
         if dim == 3:
-            M = np.sum(d * d) * np.eye(3) - d.T @ d
+            M = np.sum(w * np.sum(d * d, axis=1)) * np.eye(3) - (w[:, None] * d).T @ d
             Dx = np.array([[0, -D[2], D[1]], [D[2], 0, -D[0]], [-D[1], D[0], 0]])
             A = np.block([[m * np.eye(3), -Dx], [Dx, M]])
             sol = np.linalg.solve(A, np.concatenate([su, sdu]))
             V, Om = sol[:3], sol[3:]
         else:
-            A = np.array([[m, 0.0, -D[1]], [0.0, m, D[0]], [-D[1], D[0], np.sum(d * d)]])
+            A = np.array([[m, 0.0, -D[1]], [0.0, m, D[0]], [-D[1], D[0], np.sum(w * np.sum(d * d, axis=1))]])
             sol = np.linalg.solve(A, np.array([su[0], su[1], sdu[2]]))
             V, Om = np.array([sol[0], sol[1], 0.0]), np.array([0.0, 0.0, sol[2]])
         out[p, 0:3] = np.asarray(U[p]) - V
@@ -152,13 +167,16 @@ def targets(F, T, H):
 
 
 # ---------------------------------------------------------------- the network
+# params: [(W1, b1), (W2, b2), (W3, b3), (W4, b4), (Ws, [])] with W[out][in];
+# Ws (7 x 12) is the linear path from the inputs to the outputs
 def init_params(seed):
-    """Glorot-uniform weights, zero biases (W[l] is out x in)."""
+    """Glorot-uniform weights, zero biases, zero linear path."""
     gen = np.random.Generator(np.random.PCG64(seed))
     params = []
     for fi, fo in SIZES:
         lim = np.sqrt(6.0 / (fi + fo))
         params.append((gen.uniform(-lim, lim, size=(fo, fi)), np.zeros(fo)))
+    params.append((np.zeros((N_OUT, N_FEAT)), np.zeros(0)))
     return params
 
 
@@ -174,10 +192,11 @@ def unflatten(vec):
         b = np.asarray(vec[k:k + fo], dtype=np.float64)
         k += fo
         params.append((W, b))
+    params.append((np.asarray(vec[k:k + N_OUT * N_FEAT], dtype=np.float64).reshape(N_OUT, N_FEAT), np.zeros(0)))
     return params
 
 
-N_PARAMS = sum(fo * fi + fo for fi, fo in SIZES)
+N_PARAMS = sum(fo * fi + fo for fi, fo in SIZES) + N_OUT * N_FEAT
 
 
 def standardise(A):
@@ -191,10 +210,13 @@ def forward(params, Xn):
     """Returns the list of layer outputs [x, a1, a2, a3, y] (FP64)."""
     acts = [Xn]
     a = Xn
-    for l, (W, b) in enumerate(params):
-        z = a @ W.T + b
-        a = np.tanh(z) if l < len(params) - 1 else z
+    for l in range(3):
+        W, b = params[l]
+        a = np.tanh(a @ W.T + b)
         acts.append(a)
+    W4, b4 = params[3]
+    Ws = params[4][0]
+    acts.append(a @ W4.T + b4 + Xn @ Ws.T)
     return acts
 
 
@@ -205,13 +227,26 @@ def loss_and_grads(params, Xn, Yn):
     diff = acts[-1] - Yn
     loss = float(np.mean(diff * diff))
     delta = 2.0 * diff / (B * Yn.shape[1])          # dL/dy
-    grads = [None] * len(params)
-    for l in range(len(params) - 1, -1, -1):
+    grads = [None] * 5
+    grads[4] = (delta.T @ Xn, np.zeros(0))           # the linear path
+    for l in range(3, -1, -1):
         W, _ = params[l]
         grads[l] = (delta.T @ acts[l], delta.sum(axis=0))
         if l > 0:
             delta = (delta @ W) * (1.0 - acts[l] ** 2)  # through tanh of layer l-1's output
     return loss, grads
+
+
+def linear_fit(params, Xn, Yn, ridge=1e-8):
+    """The linear path and output bias by least squares over the rows, the
+    output weights W4 zero: minimise |[Xn 1] C - Yn|^2 + ridge B |C|^2."""
+    B = Xn.shape[0]
+    A = np.concatenate([Xn, np.ones((B, 1))], axis=1)
+    C = np.linalg.solve(A.T @ A + ridge * B * np.eye(N_FEAT + 1), A.T @ Yn)
+    out = [(W.copy(), b.copy()) for W, b in params[:3]]
+    out.append((np.zeros_like(params[3][0]), C[N_FEAT].copy()))
+    out.append((C[:N_FEAT].T.copy(), np.zeros(0)))
+    return out
 
 
 def adam(params, grads, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
@@ -243,32 +278,36 @@ def to_bf16(a):
 def forward_bf16(params, Xn):
     """The tensor-core inference arithmetic: BF16 inputs, weights and hidden
     activations, wide accumulation, FP32 bias and tanh, FP32 output."""
-    a = to_bf16(Xn)
-    for l, (W, b) in enumerate(params):
-        z = a @ to_bf16(W).T + np.asarray(b, dtype=np.float32).astype(np.float64)
-        if l < len(params) - 1:
-            a = to_bf16(np.tanh(z))
-        else:
-            a = z
-    return a
+    x = to_bf16(Xn)
+    a = x
+    for l in range(3):
+        W, b = params[l]
+        a = to_bf16(np.tanh(a @ to_bf16(W).T + np.asarray(b, dtype=np.float32).astype(np.float64)))
+    W4, b4 = params[3]
+    return a @ to_bf16(W4).T + x @ to_bf16(params[4][0]).T + np.asarray(b4, dtype=np.float32).astype(np.float64)
+
+
+ROWS = 8  # rows per particle in the Jacobian: the state, six velocity / spin and one temperature perturbation
 
 
 def jacobian(params, xmu, xsd, ymu, ysd, Xraw, delta=0.25, infer=forward):
-    """Secant Jacobian of (F, tau) in (U, omega) and the value row.
-    Returns (Y (n, 7) de-standardised, J (n, 18): J_FU row-major, J_TW row-major)."""
+    """Secant Jacobian of (F, tau) in (U, omega) and of H in T_p, and the value
+    row.  Returns (Y (n, 7) de-standardised, J (n, 19): J_FU row-major, J_TW
+    row-major, J_HT)."""
     Xn = (Xraw - xmu) / xsd
     n = Xn.shape[0]
-    rows = np.repeat(Xn, 7, axis=0)
-    for j in range(6):
-        rows[j + 1::7, j] += delta
+    rows = np.repeat(Xn, ROWS, axis=0)
+    for j in range(7):
+        rows[j + 1::ROWS, j] += delta
     Yn = infer(params, rows) if infer is not forward else forward(params, rows)[-1]
     Y = Yn * ysd + ymu
-    Y = Y.reshape(n, 7, N_OUT)
+    Y = Y.reshape(n, ROWS, N_OUT)
     base = Y[:, 0, :]
-    J = np.zeros((n, 18))
+    J = np.zeros((n, 19))
     for b in range(3):
         J[:, b:9:3] = (Y[:, 1 + b, 0:3] - base[:, 0:3]) / (delta * xsd[b])
         J[:, 9 + b:18:3] = (Y[:, 4 + b, 3:6] - base[:, 3:6]) / (delta * xsd[3 + b])
+    J[:, 18] = (Y[:, 7, 6] - base[:, 6]) / (delta * xsd[6])
     return base, J
 
 

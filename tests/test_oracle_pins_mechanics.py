@@ -144,6 +144,52 @@ def test_thermosensitive_heat_balance():
     assert Ts[-1] > 0.5  # and not below the fluid's initial temperature
 
 
+def _heat_capacity_run(Cp, J_HT, steps):
+    case = _box((28, 28, 28))
+    case["pibm"] = True
+    case["particles"] = dict(X=np.array([[13.7, 14.2, 13.9]]), R=np.array([4.0]), rho_p=np.array([1.2]),
+                             T_p=np.array([1.0]), heat_cap=np.array([Cp]), fixed=np.array([1], dtype=np.uint8))
+    o = oracle.Oracle(case)
+    if J_HT is not None:
+        J = np.zeros((1, 19))
+        J[0, 18] = J_HT
+        o.set_hydro_jacobian(J)
+    Ts = [float(o.particles()["T_p"][0])]
+    for _ in range(steps):
+        o.step(1)
+        Ts.append(float(o.particles()["T_p"][0]))
+    o.close()
+    return np.array(Ts)
+
+
+def test_heat_jacobian_stabilises_small_heat_capacity():
+    """The heat row of the Jacobian in the thermosensitive update: C_p (T_new -
+    T) = -(H_held + J_HT (T_new - T)).  At a frozen fluid state the coupling's
+    heat flux is H = k (T_p - T_s) with k = 2 kappa_T sum epsilon (Eq lbm7.5
+    summed over the covered nodes), and the held flux is the mean of two
+    couplings, so the explicit update (J_HT = 0) has the recurrence
+    x^2 - (1 - a) x + a = 0, a = k / (2 C_p), unstable once C_p < k / 2; with
+    the applied J_HT = k / 2 the coefficient becomes k / (2 C_p + k) < 1 and the
+    update is stable for any C_p.  A particle with C_p = k / 14 in an adiabatic
+    box (the covered fluid responds too, so the decay rings): without the heat
+    row its temperature departs from the fluid's by orders of magnitude within
+    12 steps; with it, the ripple never exceeds the initial offset and decays
+    toward the fluid's temperature; a negative J_HT is taken as 0."""
+    from oracle import surrogate as S
+    nodes = S.region(np.array([13.7, 14.2, 13.9]), 4.0, (28, 28, 28), 3)
+    k = 2.0 * 1.0 * np.sum(S._eps(nodes, np.array([13.7, 14.2, 13.9]), 4.0, 3))
+    Cp = k / 14.0
+    plain = _heat_capacity_run(Cp, None, 12)
+    assert not np.all(np.isfinite(plain)) or np.max(np.abs(plain - 0.5)) > 100.0
+    held = _heat_capacity_run(Cp, 0.5 * k, 80)
+    assert np.all(np.isfinite(held))
+    assert np.max(np.abs(held - 0.5)) <= 0.5 + 1e-12  # never beyond the initial offset
+    assert np.max(np.abs(np.diff(held[-10:]))) < 5e-3  # the ripple has decayed to under 1 %
+    assert 0.5 < np.mean(held[-10:]) < 0.55  # near the fluid's temperature, above it
+    flipped = _heat_capacity_run(Cp, -0.5 * k, 12)  # taken as 0: the explicit update
+    assert np.array_equal(flipped, plain)
+
+
 # --------------------------------------------------------- 3. Jacobian kick
 M_FREE = 2.0 * 4.0 / 3.0 * np.pi * 8.0  # rho_p (4/3) pi R^3 of the free particle below
 
@@ -156,7 +202,7 @@ def _free_particle(nsub, J):
     case["particles"] = dict(X=np.array([[7.5, 7.5, 7.5]]), U=U0, R=np.array([2.0]), rho_p=np.array([rho_p]),
                              T_p=np.zeros(1))
     o = oracle.Oracle(case)
-    Jfull = np.zeros((1, 18))
+    Jfull = np.zeros((1, 19))
     Jfull[0, :9] = J.ravel()
     o.set_hydro_jacobian(Jfull)
     m = rho_p * 4.0 / 3.0 * np.pi * 8.0

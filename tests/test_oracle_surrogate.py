@@ -1,10 +1,15 @@
 """Pins of the surrogate's reference (oracle/surrogate.py) against closed forms:
 region statistics of uniform and rigidly rotating fields, gaps of a known
-arrangement, backpropagation against central differences, the first Adam step,
-BF16 rounding, and the secant Jacobian of a network whose answer is known."""
+arrangement, the coupling's load as the exact linear function of the
+coupling-weighted features (Eqs lbm7, lbm7.5, lbm8, lbm13 at a frozen fluid
+state), backpropagation against central differences, the least-squares linear
+path on exactly linear data, the first Adam step, BF16 rounding, and the
+secant Jacobian of a network whose answer is known."""
 import numpy as np
 import pytest
 
+import oracle
+import workloads as W
 from oracle import surrogate as S
 
 
@@ -68,6 +73,7 @@ def test_backprop_matches_central_differences():
     gen = np.random.default_rng(3)
     params = S.init_params(11)
     params = [(W, gen.normal(size=b.shape) * 0.1) for W, b in params]
+    params[4] = (gen.normal(size=(S.N_OUT, S.N_FEAT)) * 0.1, np.zeros(0))  # the linear path
     X = gen.normal(size=(9, S.N_FEAT))
     Y = gen.normal(size=(9, S.N_OUT))
     loss, grads = S.loss_and_grads(params, X, Y)
@@ -106,6 +112,7 @@ def test_secant_jacobian_of_a_linear_network():
     # same network and the de-standardisation by a known scale
     params = S.init_params(5)
     gen = np.random.default_rng(2)
+    params[4] = (gen.normal(size=(S.N_OUT, S.N_FEAT)) * 0.3, np.zeros(0))
     Xraw = gen.normal(size=(4, S.N_FEAT))
     xmu, xsd = np.zeros(S.N_FEAT), np.full(S.N_FEAT, 2.0)
     ymu, ysd = np.zeros(S.N_OUT), np.full(S.N_OUT, 3.0)
@@ -116,6 +123,16 @@ def test_secant_jacobian_of_a_linear_network():
         Xp[:, b] += 1e-6 * 2.0
         Yp = S.forward(params, (Xp - xmu) / xsd)[-1] * ysd + ymu
         assert np.allclose(J[:, b:9:3], (Yp[:, 0:3] - Y[:, 0:3]) / (1e-6 * 2.0), rtol=1e-6, atol=1e-8)
+    for b in range(3):  # torque in spin
+        Xp = Xraw.copy()
+        Xp[:, 3 + b] += 1e-6 * 2.0
+        Yp = S.forward(params, (Xp - xmu) / xsd)[-1] * ysd + ymu
+        assert np.allclose(J[:, 9 + b:18:3], (Yp[:, 3:6] - Y[:, 3:6]) / (1e-6 * 2.0), rtol=1e-6, atol=1e-8)
+    Xp = Xraw.copy()  # heat flux in the particle temperature
+    Xp[:, 6] += 1e-6 * 2.0
+    Yp = S.forward(params, (Xp - xmu) / xsd)[-1] * ysd + ymu
+    assert np.allclose(J[:, 18], (Yp[:, 6] - Y[:, 6]) / (1e-6 * 2.0), rtol=1e-6, atol=1e-8)
+    assert J.shape == (4, 19)
     assert np.allclose(Y, S.forward(params, (Xraw - xmu) / xsd)[-1] * ysd + ymu)
     assert S.gate_error(Y[:, 0:3], Y[:, 0:3]) == 0.0
 
@@ -159,3 +176,55 @@ def test_owned_regions_partition_overlapping_footprints():
         n = np.array([v])
         e0, e1 = S._eps(n, X[0], R[0], 2)[0], S._eps(n, X[1], R[1], 2)[0]
         assert (v in sa) == (e0 >= e1)
+
+
+def test_linear_path_least_squares_recovers_linear_data():
+    # targets exactly affine in the inputs: the least-squares linear path
+    # reproduces them (the ridge, 1e-8 per row, moves the answer by ~1e-8)
+    gen = np.random.default_rng(12)
+    X = gen.normal(size=(500, S.N_FEAT))
+    A = gen.normal(size=(S.N_OUT, S.N_FEAT))
+    c = gen.normal(size=S.N_OUT)
+    Y = X @ A.T + c
+    p = S.linear_fit(S.init_params(2), X, Y)
+    assert np.max(np.abs(S.forward(p, X)[-1] - Y)) < 1e-6
+    assert np.allclose(p[4][0], A, atol=1e-6) and np.allclose(p[3][1], c, atol=1e-6)
+    assert not np.any(p[3][0])  # the hidden layers start switched off
+
+
+def test_coupling_load_is_linear_in_the_weighted_features():
+    """With the coupling's own weights (epsilon rho for the rigid-motion fit,
+    epsilon for the fluid temperature) the oracle's coupling of a state equals
+    F = -2 m (U - V) - 2 (omega - Om) x D, tau = -2 D x (U - V) - 2 M (omega -
+    Om), H = 2 kappa_T (sum epsilon) (T_p - T_s) to round-off, with m, D, M the
+    weighted moments of the owned nodes.  The load comes from the oracle's C
+    coupling, the features from the Python reference: an unweighted fit, a
+    dropped epsilon or a sign error on either side fails by far more."""
+    case = W.sed3d(nx=32, ny=32, nz=40, n_p=6, d=7.0, config_index=11, T_p_random=True)
+    case["g_particle"] = [0.0, 0.0, -5e-4]
+    o = oracle.Oracle(case)
+    o.step(6)
+    f, g = o.populations()
+    fl = S.raw_fields(f, g, 3)
+    p = o.particles()
+    R = case["particles"]["R"]
+    load = o.particle_forces()
+    feat = S.features(fl, p["X"], p["U"], p["W"], R, p["T_p"], 3)
+    o.close()
+    kappa = case.get("kappa_T", 1.0)
+    for q in range(len(R)):
+        nodes = S.owned(S.region(p["X"][q], R[q], (32, 32, 40), 3), q, p["X"], R, 3)
+        eps = S._eps(nodes, p["X"][q], R[q], 3)
+        w = eps * fl["rho"][nodes[:, 2], nodes[:, 1], nodes[:, 0]]
+        d = nodes - p["X"][q][None, :]
+        m, D = np.sum(w), (w[:, None] * d).sum(axis=0)
+        M = np.sum(w * np.sum(d * d, axis=1)) * np.eye(3) - (w[:, None] * d).T @ d
+        dU, dW, dT = feat[q, 0:3], feat[q, 3:6], feat[q, 6]
+        F = -2.0 * m * dU - 2.0 * np.cross(dW, D)
+        T = -2.0 * np.cross(D, dU) - 2.0 * M @ dW
+        H = 2.0 * kappa * np.sum(eps) * dT
+        scale = np.linalg.norm(load["F"][q]) + 1e-30
+        assert np.linalg.norm(F - load["F"][q]) < 1e-9 * scale, q
+        assert np.linalg.norm(T - load["T"][q]) < 1e-9 * (np.linalg.norm(load["T"][q]) + 1e-30) + 1e-15, q
+        assert abs(H - load["H"][q]) < 1e-9 * abs(load["H"][q]) + 1e-15, q
+        assert scale > 1e-8  # a moving particle: the check is not trivially zero
