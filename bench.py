@@ -125,6 +125,17 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def kernel_source_sha(source: str, region_end: str | None) -> str:
+    """sha256 of a kernel's source: the file, or its text up to the line that
+    starts with region_end (the part of the file that holds the kernel and its
+    launcher, so that other kernels of the file can change)."""
+    text = open(os.path.join(ROOT, "paper_1502_01159_gb300", "csrc", source), "rb").read()
+    if region_end:
+        cut = text.find(b"\n" + region_end.encode())
+        text = text[:cut] if cut >= 0 else text
+    return hashlib.sha256(text).hexdigest()
+
+
 def traffic_record(kernel: str, workload_name: str):
     """DRAM bytes per launch from a committed ncu summary, valid only while the
     kernel source is unchanged since the counters were taken."""
@@ -136,8 +147,7 @@ def traffic_record(kernel: str, workload_name: str):
     entry = rec.get(kernel, {}).get(workload_name)
     if not entry:
         return None
-    src = os.path.join(ROOT, "paper_1502_01159_gb300", "csrc", entry["source"])
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    sha = kernel_source_sha(entry["source"], entry.get("region_end"))
     return entry["bytes_per_launch"] if sha == entry["source_sha256"] else None
 
 
@@ -458,9 +468,10 @@ def ensemble_study(torch, flush, steps):
     kps = ens.kernels_per_step()
     diag = [b.diagnostics()["nonfinite"] for b in ens.boxes]
     ens.close()
-    lat = {}
-    for c_lat, c_dem in choice:
-        lat[str(c_lat)] = lat.get(str(c_lat), 0) + 1
+    picked = {}
+    for c_lat, c_rows, c_dem in choice:
+        key = f"lattice_threads={c_lat},row_tiles={c_rows},dem_per_cta={'default' if c_dem == 0 else 'per box'}"
+        picked[key] = picked.get(key, 0) + 1
     return {"workload": f"{len(cases)} boxes, edges 64..128 (sum {nodes} nodes), {n_p} thermosensitive spheres d=8, "
                         "Ra log-uniform 1e3..1e5, D3Q19+D3Q7 FP32, Hertz, 10 DEM substeps",
             "MLUPS": round(nodes / (ms_tuned * 1e-3) / 1e6, 1), "ms_per_step": round(ms_tuned, 4),
@@ -469,7 +480,7 @@ def ensemble_study(torch, flush, steps):
             "graph_launches_per_step": 1, "kernels_per_step": kps,
             "wall_ms_per_step_one_graph": round(ms_ensemble_wall, 4),
             "wall_ms_per_step_box_by_box": round(ms_separate_wall, 4),
-            "autotune": {"seconds": round(tune_s, 2), "lattice_threads_chosen": lat},
+            "autotune": {"seconds": round(tune_s, 2), "chosen": picked},
             "nonfinite_boxes": int(sum(1 for d in diag if d))}
 
 
@@ -477,10 +488,13 @@ def surrogate_study(torch, flush, steps):
     """Learned coupling surrogate at scale: 384^3 D3Q19+D3Q7 with BF16
     deviation storage, 10 000 thermosensitive spheres d = 6.  The plain
     solver generates 1e6 samples (100 steps x 10 000 particles: features and
-    PIBM coupling of each state), the network is
-    trained on the GPU, then the step is timed with and without the surrogate
-    pipeline (features, tensor-core inference, Jacobian and gate every step),
-    and the gate's verdict at a 1% force-error bound is reported."""
+    PIBM coupling of each state); the network's linear path is fitted by least
+    squares and the whole network trained by Adam on the GPU; then the step is
+    timed with and without the surrogate pipeline (features, tensor-core
+    inference, Jacobian and gate every step, the correction applied inside the
+    DEM substeps and in the thermosensitive update whenever the gate is open
+    at its 1% force-error bound), and the surrogate run is compared with a
+    plain run from the same state after the same number of steps."""
     import numpy as np
 
     from paper_1502_01159_gb300 import Simulation
@@ -498,40 +512,64 @@ def surrogate_study(torch, flush, steps):
     gen_s = time.perf_counter() - t0
     feat, targ = np.concatenate(feats), np.concatenate(targs)
     t0 = time.perf_counter()
-    losses = sim.surrogate_train(feat, targ, epochs=30, batch=2048, lr=2e-3, seed=3)
+    losses = sim.surrogate_train(feat, targ, epochs=10, batch=2048, lr=1e-3, seed=3)
     train_s = time.perf_counter() - t0
 
-    def timed(k):
-        s = sim.stream
+    def timed(s_, k):
+        st = s_.stream
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
         for i in range(k):
-            with torch.cuda.stream(s):
+            with torch.cuda.stream(st):
                 flush.fill_(i & 0xFF)
-            ev[i][0].record(s)
-            sim.step(1)
-            ev[i][1].record(s)
+            ev[i][0].record(st)
+            s_.step(1)
+            ev[i][1].record(st)
         torch.cuda.synchronize()
         return statistics.mean(a.elapsed_time(b) for a, b in ev)
 
     sim.step(2)
-    ms_plain = timed(steps)
+    ms_plain = timed(sim, steps)
+    t_enable = sim.t
     sim.surrogate_enable(True, bound=0.01, delta=0.25)
-    sim.step(2)
-    ms_sg = timed(steps)
+    ms_sg = timed(sim, steps)
     gate = sim.surrogate_stats()
     nonfinite = sim.diagnostics()["nonfinite"]
+    J, _ = sim.read_hydro_jacobian()
+    # the plain method from the same state (every step so far is deterministic)
+    ref = Simulation(case)
+    ref.step(t_enable)
+    ref.step(sim.t - t_enable)
+    a, b = sim.read_particles(), ref.read_particles()
+    disp = np.max(np.abs(b["X"] - case["particles"]["X"]))
+    traj = {"steps_compared": int(sim.t - t_enable),
+            "max_abs_dX": float(np.max(np.abs(a["X"] - b["X"]))),
+            "max_displacement_plain": float(disp),
+            "rel_dU": float(np.linalg.norm(a["U"] - b["U"]) / np.linalg.norm(b["U"])),
+            "max_abs_dT_p": float(np.max(np.abs(a["T_p"] - b["T_p"])))}
+    for name in ("T", "uz"):
+        fa, fb = sim.read_field(name), ref.read_field(name)
+        base = fb - (0.5 if name == "T" else 0.0)  # T about the initial fluid temperature
+        traj[f"field_{name}_rel_l2"] = float(np.linalg.norm(fa - fb) / max(np.linalg.norm(base), 1e-300))
+    ref.close()
     sim.close()
     return {"workload": "384^3 D3Q19+D3Q7 BF16-deviation storage, 10000 thermosensitive spheres d=6, Hertz, "
-                        "10 DEM substeps; 12-feature 3x64 tanh MLP, BF16 tensor-core inference",
+                        "10 DEM substeps; 12-feature 3x64 tanh MLP with a least-squares linear path, BF16 "
+                        "tensor-core inference",
             "samples": int(feat.shape[0]), "generate_s": round(gen_s, 2), "train_s": round(train_s, 2),
-            "loss_first_last_epoch": [round(float(losses[0]), 4), round(float(losses[-1]), 4)],
+            "loss_first_last_epoch": [round(float(losses[0]), 5), round(float(losses[-1]), 5)],
             "ms_per_step_plain": round(ms_plain, 4), "ms_per_step_surrogate": round(ms_sg, 4),
+            "pipeline_ms": round(ms_sg - ms_plain, 4),
             "MLUPS_plain": round(nodes / (ms_plain * 1e-3) / 1e6, 1),
             "MLUPS_surrogate": round(nodes / (ms_sg * 1e-3) / 1e6, 1),
             "speedup_vs_plain": round(ms_plain / ms_sg, 3),
             "gate_bound": 0.01, "gate": gate,
-            "gain": "light particles (rho_p/rho_f = 0.6) that the plain explicit coupling cannot hold stay "
-                    "bounded with the network's Jacobian (tests/test_gpu_surrogate.py)",
+            "applied_jacobian_mean_diag": {"J_FU": float(np.mean(J[:, [0, 4, 8]])),
+                                           "J_TW": float(np.mean(J[:, [9, 13, 17]])),
+                                           "J_HT": float(np.mean(J[:, 18]))},
+            "trajectory_vs_plain": traj,
+            "gain": "light particles (rho_p/rho_f = 0.6) and small heat capacities (C_p = 10 for a disk of "
+                    "diameter 10) that the plain explicit coupling cannot hold stay bounded with the network's "
+                    "Jacobian (tests/test_gpu_surrogate.py)",
             "nonfinite": nonfinite}
 
 
@@ -545,7 +583,7 @@ def run_ours(args):
     solo = rank == 0 and world == 1
     # the oracle baselines run in a process of their own (started before the first GPU call)
     bg = None
-    if solo and not args.no_oracle_baselines:
+    if solo and not args.no_oracle_baselines and not args.study:
         bg = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-baselines-json"],
                               stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
     torch.cuda.set_device(local)
@@ -557,6 +595,12 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
         __graft_entry__.build()
+
+    if args.study:  # one study alone (profiling runs), its JSON object on one line
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        fn = {"surrogate": surrogate_study, "ensemble": ensemble_study}[args.study]
+        print(json.dumps({"study": args.study, **fn(torch, flush, max(6, args.steps // 2))}), flush=True)
+        return
 
     case, desc = workload(args.workload, args.storage)
     nodes = case["shape"][0] * case["shape"][1] * case["shape"][2]
@@ -698,6 +742,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline only (no other workloads or studies)")
     ap.add_argument("--no-oracle-baselines", action="store_true")
+    ap.add_argument("--study", choices=["surrogate", "ensemble"],
+                    help="run one study alone and print its result (no headline line)")
     ap.add_argument("--oracle-baselines-json", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps

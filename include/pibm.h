@@ -303,24 +303,32 @@ pibm_status pibm_contacts_static(const double* d_X, const double* d_R, int n, in
 /* ------------------------------------------------------------------------
  * Learned coupling surrogate (no counterpart in the paper).  Eq demgov holds
  * the PIBM hydrodynamic force and torque (Eq lbm13 and its torque analogue)
- * fixed over the DEM substeps of a lattice step; a small network predicts how
- * they change with the particle's own velocity and spin, and its secant
- * Jacobian corrects the held load inside the step:
- *   F = F_held + J_FU (U - U_step_start),  tau = tau_held + J_TW (omega - omega_step_start).
- * Features (12 per particle, lattice units): over the nodes the particle
- * covers (|r - X| < R + 1/2, where the coupling acts) the fluid velocity is
- * fitted by a rigid motion V + Om x (r - X) (least squares); features are
- * U - V (3), omega - Om (3), T_p - mean covered-fluid temperature (1), the
- * solid fraction
+ * fixed over the DEM substeps of a lattice step, and the thermosensitive
+ * update holds the heat flux; a small network predicts how they change with
+ * the particle's own velocity, spin and temperature, and half its secant
+ * Jacobian (the held load is the mean of the couplings of t and t-1, and a
+ * change of the particle's state enters only the newer one) corrects them:
+ *   F = F_held + J_FU (U - U_step_start),  tau = tau_held + J_TW (omega - omega_step_start)
+ * inside the substeps, and C_p (T_new - T) = -(H_held + J_HT (T_new - T)) in
+ * the thermosensitive update (a negative J_HT counts as 0).
+ * Features (12 per particle, lattice units), over the nodes the particle owns
+ * in the coupling (epsilon > 0, the larger epsilon, ties to the lower index)
+ * and from the raw moments before the coupling's correction: the fluid
+ * velocity fitted by a rigid motion V + Om x (r - X), least squares weighted
+ * by epsilon rho (the coupling's weights); U - V (3), omega - Om (3), T_p -
+ * the epsilon-weighted mean fluid temperature (1), the solid fraction
  * sum_{q != p, |X_q - X_p| < 4 R_p} (R_q / 4 R_p)^D (1) and the four smallest
- * surface gaps capped at 2 R_p (4).  Targets: the force (3), torque (3) and
- * heat flux (1) the particle feels over the next step, i.e. the mean of the
- * PIBM couplings of t and t-1.  Network: 12 -> 64 -> 64 -> 64 -> 7, tanh hidden layers,
- * FP32 parameters packed [W1 (64x12), b1, W2 (64x64), b2, W3, b3, W4 (7x64),
- * b4], W[out][in] row-major (PIBM_SURROGATE_PARAMS floats); standardisation
- * norm = [mu_x (12), sd_x (12), mu_y (7), sd_y (7)].  Inference runs on the
- * tensor cores in BF16 with FP32 accumulation; training runs in FP32. */
-enum { PIBM_SURROGATE_PARAMS = 9607, PIBM_SURROGATE_NORM = 38 };
+ * surface gaps capped at 2 R_p (4).  With these weights the coupling's load at
+ * a frozen fluid state is an exact linear function of the first seven.
+ * Targets: the PIBM coupling's force (3), torque (3) and heat flux (1) of the
+ * state.  Network: 12 -> 64 -> 64 -> 64 -> 7, tanh hidden layers, plus a
+ * linear path from the inputs to the outputs: y = W4 a3 + b4 + Ws x.  FP32
+ * parameters packed [W1 (64x12), b1, W2 (64x64), b2, W3, b3, W4 (7x64), b4,
+ * Ws (7x12)], W[out][in] row-major (PIBM_SURROGATE_PARAMS floats);
+ * standardisation norm = [mu_x (12), sd_x (12), mu_y (7), sd_y (7)].
+ * Inference runs on the tensor cores in BF16 with FP32 accumulation; training
+ * runs in FP32. */
+enum { PIBM_SURROGATE_PARAMS = 9691, PIBM_SURROGATE_NORM = 38 };
 /* The 12 features of every particle for the current state (n*12 doubles, host). */
 pibm_status pibm_read_features(pibm_ctx* ctx, double* out);
 /* Set / read the network (host arrays as above).  Scales must be positive. */
@@ -334,24 +342,28 @@ pibm_status pibm_surrogate_infer(pibm_ctx* ctx, const float* in, int rows, float
  * standardised error on B rows (X: B x 12, Y: B x 7, standardised). */
 pibm_status pibm_surrogate_gradient(pibm_ctx* ctx, const float* X, const float* Y, int B, float* grad, double* loss);
 /* Train on n samples (feat: n x 12, targ: n x 7, raw units, host): the
- * standardisation comes from the data, weights start Glorot-uniform from
- * seed, then epochs of shuffled mini-batches of batch rows with Adam (lr).
+ * standardisation comes from the data; the hidden layers start
+ * Glorot-uniform from seed with zero output weights W4, the linear path Ws
+ * and the output bias b4 start at the least-squares fit over all n samples
+ * (ridge 1e-8 n on the normal equations); then epochs of shuffled
+ * mini-batches of batch rows train every parameter with Adam (lr).
  * loss_per_epoch: NULL or epochs doubles (mean standardised loss). */
 pibm_status pibm_surrogate_train(pibm_ctx* ctx, const double* feat, const double* targ, int64_t n, int epochs, int batch,
                                  double lr, uint64_t seed, double* loss_per_epoch);
 /* Put the surrogate in the step: after each step's coupling the features,
- * inference, Jacobian and gate run on the device; the next step's DEM applies
- * the Jacobian only when sum_p |F_net,p - F_held,p| / sum_p |F_held,p| <= bound
- * for the current state (else the held PIBM load alone, the plain method).
- * delta: secant step in standard deviations of each velocity / spin feature.
+ * inference, Jacobian and gate run on the device; the next step applies the
+ * Jacobian only when sum_p |F_net,p - F_pibm,p| / sum_p |F_pibm,p| <= bound
+ * for the current state, F_pibm the coupling's force (else the held PIBM load
+ * alone, the plain method).  delta: secant step in standard deviations of
+ * each velocity, spin and temperature feature.
  * on = 0 removes it.  A new particle set removes it. */
 pibm_status pibm_surrogate_enable(pibm_ctx* ctx, int on, double bound, double delta);
 /* [0] steps with the Jacobian applied, [1] steps that fell back, [2] the last relative force error. */
 pibm_status pibm_surrogate_stats(pibm_ctx* ctx, double* out);
-/* A caller-supplied Jacobian (n*18 doubles per particle: J_FU row-major, then
- * J_TW), applied every step until replaced; NULL removes it. */
+/* A caller-supplied Jacobian (19 doubles per particle: J_FU row-major, J_TW
+ * row-major, J_HT), applied every step until replaced; NULL removes it. */
 pibm_status pibm_set_hydro_jacobian(pibm_ctx* ctx, const double* J);
-/* The Jacobian in use (n*18, host) and whether the next step applies it. */
+/* The Jacobian in use (n*19, host) and whether the next step applies it. */
 pibm_status pibm_read_hydro_jacobian(pibm_ctx* ctx, double* J, int* on);
 
 /* ------------------------------------------------------------------------
@@ -380,14 +392,18 @@ pibm_status pibm_ensemble_box(pibm_ensemble* e, int b, pibm_ctx** out);
 pibm_status pibm_ensemble_step(pibm_ensemble* e, int nsteps);
 /* Kernels one ensemble step launches (sum over the boxes). */
 pibm_status pibm_ensemble_kernels_per_step(pibm_ensemble* e, int* n);
-/* Autotuner: for each box in turn, time reps steps (pibm_step_timed: graph replays with CUDA events)
- * of each of five candidate launch shapes -- PIBM_TUNE_LATTICE_THREADS in
- * {default, 64, 128, 256, 512} paired with PIBM_TUNE_DEM_PARTICLES_PER_CTA in
- * {default, 16, 48, 64, 96} (shapes a box cannot take time the default) --
- * and keep the fastest lattice and DEM shapes.  These are real steps: every
- * box advances by 5*reps steps (launch shapes change no result).  choice:
- * NULL or 2*n_boxes ints receiving (lattice threads, DEM particles per CTA)
- * per box, 0 meaning the default. */
+/* Autotuner.  First each box's DEM shape alone: reps steps (pibm_step_timed)
+ * of each of PIBM_TUNE_DEM_PARTICLES_PER_CTA in {default, 16, 48, 64, 96}
+ * (shapes a box cannot take time the default), the fastest DEM kernel kept as
+ * the box's pick.  Then 16 whole-ensemble configurations --
+ * PIBM_TUNE_LATTICE_THREADS in {default, 128, 256, 512} x
+ * PIBM_TUNE_LATTICE_ROW_TILES in {0, 1} x {default DEM shapes, the picks} --
+ * each applied to every box and timed as ensemble steps (graph launches,
+ * CUDA events; median of reps + 2 after two untimed steps).  The fastest is kept
+ * if it beats the defaults by more than 1 %, else the defaults stay.  These are
+ * real steps: every box advances by 5 reps + 16 (reps + 4) steps (launch shapes
+ * change no result).  choice: NULL or 3*n_boxes ints receiving (lattice threads,
+ * row tiles, DEM particles per CTA) per box, 0 meaning the default. */
 pibm_status pibm_ensemble_autotune(pibm_ensemble* e, int reps, int32_t* choice);
 /* Last error message of the ensemble (or of a failed create when e is NULL:
  * use pibm_last_error(NULL, ...)); returns its length. */

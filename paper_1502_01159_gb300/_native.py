@@ -25,7 +25,8 @@ FIELDS = {"rho": 0, "ux": 1, "uy": 2, "uz": 3, "T": 4, "FBx": 5, "FBy": 6, "FBz"
 # every symbol include/pibm.h declares, with (restype, argtypes)
 _P, _D, _I32, _U8 = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_uint8)
 _F = C.POINTER(C.c_float)
-SURROGATE_PARAMS, SURROGATE_NORM = 9607, 38
+SURROGATE_PARAMS, SURROGATE_NORM = 9691, 38
+HYDRO_JACOBIAN = 19  # J_FU (9), J_TW (9), J_HT per particle
 
 
 class pibm_desc(C.Structure):
@@ -422,11 +423,11 @@ class Simulation:
         if J is None:
             self._check(self.L.pibm_set_hydro_jacobian(self.h, None), "pibm_set_hydro_jacobian")
         else:
-            J = np.ascontiguousarray(J, dtype=np.float64).reshape(-1, 18)
+            J = np.ascontiguousarray(J, dtype=np.float64).reshape(-1, HYDRO_JACOBIAN)
             self._check(self.L.pibm_set_hydro_jacobian(self.h, _dp(J)), "pibm_set_hydro_jacobian")
 
     def read_hydro_jacobian(self):
-        J = np.empty((self.np, 18))
+        J = np.empty((self.np, HYDRO_JACOBIAN))
         on = C.c_int()
         self._check(self.L.pibm_read_hydro_jacobian(self.h, _dp(J), C.byref(on)), "pibm_read_hydro_jacobian")
         return J, bool(on.value)
@@ -505,12 +506,13 @@ class Ensemble:
         self._check(self.L.pibm_ensemble_step(self.h, int(n)), "pibm_ensemble_step")
 
     def autotune(self, reps: int = 2):
-        """Per-box launch shapes chosen by timing; returns [(lattice threads,
-        DEM particles per CTA)] (0 = default).  Advances every box 5*reps steps."""
-        out = np.zeros(2 * len(self.boxes), dtype=np.int32)
+        """Launch shapes chosen by timing; returns [(lattice threads, row tiles,
+        DEM particles per CTA)] per box (0 = default).  Advances every box
+        5 reps + 16 (reps + 4) steps."""
+        out = np.zeros(3 * len(self.boxes), dtype=np.int32)
         self._check(self.L.pibm_ensemble_autotune(self.h, int(reps), out.ctypes.data_as(_I32)),
                     "pibm_ensemble_autotune")
-        return [(int(out[2 * b]), int(out[2 * b + 1])) for b in range(len(self.boxes))]
+        return [tuple(int(v) for v in out[3 * b:3 * b + 3]) for b in range(len(self.boxes))]
 
     def kernels_per_step(self) -> int:
         n = C.c_int()

@@ -1127,12 +1127,12 @@ static pibm_status sg_ensure(pibm_ctx* ctx) {
         dfree_group(ctx, GRP_SG_PART);
         const size_t n = (size_t)c.np;
         c.sg.feat = (double*)dalloc(ctx, sizeof(double) * 12 * n, GRP_SG_PART);
-        c.sg.fsum = (double*)dalloc(ctx, sizeof(double) * 17 * n, GRP_SG_PART);
+        c.sg.fsum = (double*)dalloc(ctx, sizeof(double) * SG_NFSUM * n, GRP_SG_PART);
         c.sg.xr = (float4*)dalloc(ctx, sizeof(float4) * n, GRP_SG_PART);
         c.sg.nbpart = (double*)dalloc(ctx, sizeof(double) * 5 * SG_NB_SLICES * n, GRP_SG_PART);
-        c.sg.rows = (float*)dalloc(ctx, sizeof(float) * 7 * 16 * n, GRP_SG_PART);
-        c.sg.yrows = (float*)dalloc(ctx, sizeof(float) * 7 * 8 * n, GRP_SG_PART);
-        c.sg.J = (float*)dalloc(ctx, sizeof(float) * 18 * n, GRP_SG_PART);
+        c.sg.rows = (float*)dalloc(ctx, sizeof(float) * SG_ROWS * 16 * n, GRP_SG_PART);
+        c.sg.yrows = (float*)dalloc(ctx, sizeof(float) * SG_ROWS * 8 * n, GRP_SG_PART);
+        c.sg.J = (float*)dalloc(ctx, sizeof(float) * SG_NJ * n, GRP_SG_PART);
         c.sg.part = (double*)dalloc(ctx, sizeof(double) * 2 * (n / 256 + 2), GRP_SG_PART);
         if (!c.sg.feat || !c.sg.fsum || !c.sg.xr || !c.sg.nbpart || !c.sg.rows || !c.sg.yrows || !c.sg.J || !c.sg.part) {
             c.sg.cap = 0;
@@ -1265,7 +1265,8 @@ pibm_status pibm_surrogate_train(pibm_ctx* ctx, const double* feat, const double
         for (int k = 0; k < SG_NOUT; k++)
             Yn[i * SG_NOUT + k] = (float)((targ[i * SG_NOUT + k] - mu[SG_NFEAT + k]) / sd[SG_NFEAT + k]);
     }
-    // Glorot-uniform initial weights, zero biases
+    // Glorot-uniform initial weights, zero biases (the linear path and W4 come
+    // from the least-squares fit below)
     std::mt19937_64 rng(seed);
     std::vector<float> params(SG_NPARAMS, 0.f);
     const int sizes[4][2] = {{SG_NFEAT, 64}, {64, 64}, {64, 64}, {64, SG_NOUT}};
@@ -1284,12 +1285,23 @@ pibm_status pibm_surrogate_train(pibm_ctx* ctx, const double* feat, const double
     float* xb = (float*)dalloc(ctx, sizeof(float) * SG_NFEAT * (size_t)B, GRP_SCRATCH);
     float* yb = (float*)dalloc(ctx, sizeof(float) * SG_NOUT * (size_t)B, GRP_SCRATCH);
     double* dl = (double*)dalloc(ctx, sizeof(double) * 2, GRP_SCRATCH);
-    if (!dX || !dY || !didx || !xb || !yb || !dl) {
+    double* lsq = (double*)dalloc(ctx, sizeof(double) * lsq_scratch_doubles(), GRP_SCRATCH);
+    int* lsq_status = (int*)dalloc(ctx, sizeof(int), GRP_SCRATCH);
+    if (!dX || !dY || !didx || !xb || !yb || !dl || !lsq || !lsq_status) {
         dfree_group(ctx, GRP_SCRATCH);
         return fail(ctx, PIBM_ERR_OOM, "training buffers");
     }
     cudaError_t e = cudaMemcpyAsync(dX, Xn.data(), sizeof(float) * Xn.size(), cudaMemcpyHostToDevice, c.s0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dY, Yn.data(), sizeof(float) * Yn.size(), cudaMemcpyHostToDevice, c.s0);
+    // the linear path and the output bias by least squares over every sample, W4 = 0
+    int lsq_bad = 0;
+    if (e == cudaSuccess) e = launch_lsq(&c, c.s0, dX, dY, (long long)n, 1e-8, lsq, lsq_status);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&lsq_bad, lsq_status, sizeof(int), cudaMemcpyDeviceToHost, c.s0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.s0);
+    if (e == cudaSuccess && lsq_bad) {
+        dfree_group(ctx, GRP_SCRATCH);
+        return fail(ctx, PIBM_ERR_STATE, "least-squares fit of the linear path is singular");
+    }
     std::vector<int> idx((size_t)n);
     for (int64_t i = 0; i < n; i++) idx[i] = (int)i;
     const int64_t nb = n / B;  // full batches per epoch
@@ -1359,7 +1371,7 @@ pibm_status pibm_read_hydro_jacobian(pibm_ctx* ctx, double* J, int* on) {
     if (!ctx) return PIBM_ERR_ARG;
     Ctx& c = ctx->c;
     if (!c.dem.J) return fail(ctx, PIBM_ERR_STATE, "no hydrodynamic Jacobian in use");
-    std::vector<float> h((size_t)18 * c.np);
+    std::vector<float> h((size_t)SG_NJ * c.np);
     int o = 0;
     PCHECK(cudaMemcpyAsync(h.data(), c.dem.J, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, c.s0));
     PCHECK(cudaMemcpyAsync(&o, c.dem.J_on, sizeof(int), cudaMemcpyDeviceToHost, c.s0));
@@ -1382,7 +1394,7 @@ pibm_status pibm_set_hydro_jacobian(pibm_ctx* ctx, const double* J) {
     if (c.np == 0) return fail(ctx, PIBM_ERR_STATE, "no particles");
     pibm_status st = sg_ensure(ctx);
     if (st != PIBM_OK) return st;
-    std::vector<float> h((size_t)18 * c.np);
+    std::vector<float> h((size_t)SG_NJ * c.np);
     for (size_t k = 0; k < h.size(); k++) h[k] = (float)J[k];
     const int one = 1;
     PCHECK(cudaMemcpyAsync(c.sg.J, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, c.s0));

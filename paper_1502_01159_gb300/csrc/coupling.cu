@@ -111,9 +111,11 @@ __device__ __forceinline__ float eps_f32(int ix, int iy, int iz, const float* c,
 constexpr float EPS_GUARD = 1e-5f;  // FP32 decisions within this margin are re-taken in FP64
 
 // FEAT: also accumulate, over the particle's owned nodes, the sums the learned
-// surrogate's features need (count, sum d, sum d d^T, sum u, sum d x u, sum
-// dT with d = r - X_p, u = j / rho the raw velocity, dT = T0 - T_ref) into
-// fsum[p][17].
+// surrogate's features need, weighted as the coupling weighs each node (w =
+// eps rho for the velocity fit, eps for the temperature): sum w, sum w d, sum
+// w d d^T (xx, yy, zz, xy, xz, yz), sum w u = sum eps j, sum w d x u = sum eps
+// d x j, sum eps dT, sum eps, with d = r - X_p, j the raw momentum and dT = T0 -
+// T_ref the raw temperature, into fsum[p][SG_NFSUM].
 template <int D, typename S, bool FEAT>
 __global__ void __launch_bounds__(CP_THREADS, (Lat<D>::dim == 2 && !FEAT) ? 4 : (FEAT ? 2 : 3)) k_footprint(Geo G, const S* __restrict__ f, const S* __restrict__ g,
                                                           typename Store<S>::V4* __restrict__ mk,
@@ -128,9 +130,9 @@ __global__ void __launch_bounds__(CP_THREADS, (Lat<D>::dim == 2 && !FEAT) ? 4 : 
     __shared__ double sh_nb[CP_MAXNB][4];
     __shared__ float sh_nbf[CP_MAXNB][4];
     __shared__ int sh_id[CP_MAXNB];
-    __shared__ double red[FEAT ? 24 : 7][CP_THREADS / 32];
-    float fa[FEAT ? 17 : 1];
-    for (int k = 0; k < (FEAT ? 17 : 1); k++) fa[k] = 0.f;
+    __shared__ double red[FEAT ? 7 + SG_NFSUM : 7][CP_THREADS / 32];
+    float fa[FEAT ? SG_NFSUM : 1];
+    for (int k = 0; k < (FEAT ? SG_NFSUM : 1); k++) fa[k] = 0.f;
     // per-particle constants, computed once by the first warp with one value per
     // lane, so that each FP64 operation (slow on this GPU) is one warp instruction:
     // lanes 0-2 the position axes, 3-5 U, 6-8 omega, 9 T_p - T_ref, 10 2 kappa, 11 R
@@ -285,16 +287,18 @@ __global__ void __launch_bounds__(CP_THREADS, (Lat<D>::dim == 2 && !FEAT) ? 4 : 
         acc[5] -= arm[0] * MF[1] - arm[1] * MF[0];
         acc[6] += (float)M[3];
         if constexpr (FEAT) {
-            const float inv = 1.f / (float)rho;
-            const float u[3] = {(float)j[0] * inv, (float)j[1] * inv, Lat<D>::dim == 3 ? (float)j[2] * inv : 0.f};
+            const float ef = (float)e, w = ef * (float)rho;
+            const float ej[3] = {ef * (float)j[0], ef * (float)j[1], Lat<D>::dim == 3 ? ef * (float)j[2] : 0.f};
             const float dz = Lat<D>::dim == 3 ? arm[2] : 0.f;
-            fa[0] += 1.f;
-            fa[1] += arm[0], fa[2] += arm[1], fa[3] += dz;
-            fa[4] += arm[0] * arm[0], fa[5] += arm[1] * arm[1], fa[6] += dz * dz;
-            fa[7] += arm[0] * arm[1], fa[8] += arm[0] * dz, fa[9] += arm[1] * dz;
-            fa[10] += u[0], fa[11] += u[1], fa[12] += u[2];
-            fa[13] += arm[1] * u[2] - dz * u[1], fa[14] += dz * u[0] - arm[0] * u[2], fa[15] += arm[0] * u[1] - arm[1] * u[0];
-            fa[16] += (float)dT;
+            const float wd[3] = {w * arm[0], w * arm[1], w * dz};
+            fa[0] += w;
+            fa[1] += wd[0], fa[2] += wd[1], fa[3] += wd[2];
+            fa[4] += wd[0] * arm[0], fa[5] += wd[1] * arm[1], fa[6] += wd[2] * dz;
+            fa[7] += wd[0] * arm[1], fa[8] += wd[0] * dz, fa[9] += wd[1] * dz;
+            fa[10] += ej[0], fa[11] += ej[1], fa[12] += ej[2];
+            fa[13] += arm[1] * ej[2] - dz * ej[1], fa[14] += dz * ej[0] - arm[0] * ej[2], fa[15] += arm[0] * ej[1] - arm[1] * ej[0];
+            fa[16] += ef * (float)dT;
+            fa[17] += ef;
         }
     }
     // warp sums in FP32 (32 partials, a butterfly: every lane gets the sum); lane
@@ -310,21 +314,21 @@ __global__ void __launch_bounds__(CP_THREADS, (Lat<D>::dim == 2 && !FEAT) ? 4 : 
     }
     if constexpr (FEAT) {
 #pragma unroll
-        for (int a = 0; a < 17; a++) {
+        for (int a = 0; a < SG_NFSUM; a++) {
             float v = fa[a];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 7 + a) mine = v;
         }
     }
-    if (lane < (FEAT ? 24 : 7)) red[lane][threadIdx.x >> 5] = (double)mine;
+    if (lane < (FEAT ? 7 + SG_NFSUM : 7)) red[lane][threadIdx.x >> 5] = (double)mine;
     __syncthreads();
-    if (threadIdx.x < (FEAT ? 24 : 7)) {
+    if (threadIdx.x < (FEAT ? 7 + SG_NFSUM : 7)) {
         double v = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[threadIdx.x][w];
         if (threadIdx.x < 3) Fh[3 * p + threadIdx.x] = v;
         else if (threadIdx.x < 6) Th[3 * p + threadIdx.x - 3] = v;
         else if (threadIdx.x == 6) Hh[p] = v;
-        else fsum[17 * (long long)p + threadIdx.x - 7] = v;
+        else fsum[SG_NFSUM * (long long)p + threadIdx.x - 7] = v;
     }
 }
 

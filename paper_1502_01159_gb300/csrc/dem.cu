@@ -235,6 +235,7 @@ __device__ __forceinline__ float3 tangential_md(const DemCfg& C, MdRec& r, float
 // come from the caller's exact FP64 contact test; the only FP64 operation left
 // is the overlap S^2 - d^2, which cancels.  Both partners call this with the
 // same inputs and get the same bits.
+template <bool MDH>
 __device__ __forceinline__ void pair_force(const DemCfg& C, const Pub& A, const Pub& B, const double* d, double d2,
                                            double SS, float Raf, float Rbf, float3& h, MdRec& md, float dtf,
                                            float3& Fa, float3& Ta, float3& Tb) {
@@ -251,7 +252,7 @@ __device__ __forceinline__ void pair_force(const DemCfg& C, const Pub& A, const 
     float Rstar = Raf * Rbf / Sf, kt_eff;
     float Fn = normal_law(C, delta, vn, Rstar, &kt_eff);
     float3 Ft;
-    if (C.law == PIBM_HERTZ_MD_HIST) {
+    if constexpr (MDH) {
         Ft = tangential_md(C, md, nn, vt, kt_eff, Fn, dtf);
         h = f3((float)md.h[0], (float)md.h[1], (float)md.h[2]);
     } else {
@@ -304,7 +305,7 @@ __device__ __forceinline__ void for_neighbours(const DemCfg& C, const DemState& 
 // mask: bit f set while face f holds a non-zero tangential history, so faces
 // out of contact cost no memory traffic; hpre (or null): those histories,
 // loaded ahead by the caller.
-template <int D>
+template <int D, bool MDH>
 __device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, int p, const Pub& me, double Rp, float Rpf,
                                             float dtf, float* F, float* T, int& mask, const float* hpre) {
     for (int face = 0; face < 2 * D; face++) {
@@ -319,7 +320,7 @@ __device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, 
         if (!(dd > 0.0)) {
             if (mask & (1 << face)) {
                 ftp[0] = ftp[1] = ftp[2] = 0.f;
-                if (C.law == PIBM_HERTZ_MD_HIST)
+                if constexpr (MDH)
                     for (int q = 0; q < MD_REC; q++) mdp[q] = 0.0;
                 mask &= ~(1 << face);
             }
@@ -342,7 +343,7 @@ __device__ __forceinline__ void wall_forces(const DemCfg& C, const DemState& S, 
         if (mask & (1 << face))
             h = hpre ? f3(hpre[3 * face], hpre[3 * face + 1], hpre[3 * face + 2]) : f3(__ldcg(ftp), __ldcg(ftp + 1), __ldcg(ftp + 2));
         float3 Ft;
-        if (C.law == PIBM_HERTZ_MD_HIST) {
+        if constexpr (MDH) {
             MdRec md;
             if (mask & (1 << face)) md_load(mdp, md);
             else md_zero(md);
@@ -448,7 +449,9 @@ __device__ __forceinline__ void publish_s(const Priv& P, Pub& pub) {
 
 constexpr int DEM_MAXA = 6;  // neighbours per particle staged in shared memory
 
-template <int D>
+// MDH: contact law PIBM_HERTZ_MD_HIST (the loading-history records); the other
+// laws run an instantiation without them
+template <int D, bool MDH>
 __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, int advance) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int sh[DEM_T];
@@ -606,7 +609,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             float4* hist_new = nb_ft + (size_t)((gsub + 1) & 1) * C.cap;
             const double* md_old = nb_md + (size_t)(gsub & 1) * MD_REC * C.cap;
             double* md_new = nb_md + (size_t)((gsub + 1) & 1) * MD_REC * C.cap;
-            const bool mdh = C.law == PIBM_HERTZ_MD_HIST;
+            constexpr bool mdh = MDH;
             // tpp threads per particle (4 up to 64 particles per CTA, 2 up to 128, else
             // 1; 8 measured slower than 4 on 2-D beds): consecutive lanes, each taking
             // every tpp-th neighbour (the first also the walls, after the pairs);
@@ -676,7 +679,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                                     h = f3(hv.x, hv.y, hv.z);
                                     if (mdh) md_load(md_old + (size_t)MD_REC * k, md);
                                 }
-                                pair_force(C, A, B, d, d2, SS, first ? Rpf : other.rf, first ? other.rf : Rpf, h, md, dtf,
+                                pair_force<MDH>(C, A, B, d, d2, SS, first ? Rpf : other.rf, first ? other.rf : Rpf, h, md, dtf,
                                            Fa, Ta, Tb);
                             }
                         }
@@ -692,7 +695,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                             T[0] += Tb.x, T[1] += Tb.y, T[2] += Tb.z;
                         }
                     }
-                    if (sl == 0) wall_forces<D>(C, S, p, me, Rp, Rpf, dtf, F, T, P.wall_mask, D == 3 ? hpre : nullptr);
+                    if (sl == 0) wall_forces<D, MDH>(C, S, p, me, Rp, Rpf, dtf, F, T, P.wall_mask, D == 3 ? hpre : nullptr);
                 }
                 // the tpp partial sums, in a fixed butterfly order: ((0 + 1) + (2 + 3)) + ...
                 if (tpp > 1)
@@ -724,7 +727,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 if (P.fixed) continue;  // published into both buffers at the load
                 if (useJ) {  // the learned Jacobian couples the components: one thread per particle
                     if (sl != 0) continue;
-                    const float* Jp = C.J + 18 * p;
+                    const float* Jp = C.J + SG_NJ * p;
                     if (!last) {
                         kick_s<D>(P, dt, dtf, Jp, S.U + 3 * p, S.W + 3 * p);
                         drift_s<D>(P, dt, pub[(rb ^ 1) * per + l]);
@@ -781,7 +784,9 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
         __syncthreads();
         gnow = gbase + nsub;
         // write back; thermosensitive particles: C_p dT_p / dt = -H_p over one
-        // lattice step; keep this step's coupling as the previous one
+        // lattice step, with the learned Jacobian in use C_p (T_new - T) =
+        // -(H + J_HT (T_new - T)) (J_HT < 0 counts as 0); keep this step's
+        // coupling as the previous one
         int moved = 0;
         const double thr2 = 0.25 * (C.skin - 1.0) * (C.skin - 1.0);
         const double err2 = 0.25 * C.skin * C.skin;
@@ -801,7 +806,11 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
             }
             const double cp = wb[0], tp = wb[1], hh = wb[2], hhp = hp ? wb[3] : 0.0;
             const double fh[3] = {wb[4], wb[5], wb[6]}, th[3] = {wb[7], wb[8], wb[9]}, xb[3] = {wb[10], wb[11], wb[12]};
-            if (cp > 0.0) S.Tp[p] = tp - (hp ? 0.5 * (hh + hhp) : hh) / cp;
+            if (cp > 0.0) {
+                double jh = useJ ? (double)__ldcg(C.J + SG_NJ * (long long)p + 18) : 0.0;
+                if (!(jh > 0.0)) jh = 0.0;
+                S.Tp[p] = tp - (hp ? 0.5 * (hh + hhp) : hh) / (cp + jh);
+            }
             double d2 = 0;
             for (int a = 0; a < 3; a++) {
                 S.X[3 * p + a] = P.X[a];
@@ -955,7 +964,7 @@ __global__ void __launch_bounds__(DEM_T) k_dem(DemCfg C, DemState S, int nsub, i
                 else Hh = mid - 1;
             }
             nft[o + r] = found >= 0 ? __ldcg(oft + found) : make_float4(0.f, 0.f, 0.f, __int_as_float(-2));
-            if (C.law == PIBM_HERTZ_MD_HIST) {  // (a pair without history is stamped invalid above)
+            if constexpr (MDH) {  // (a pair without history is stamped invalid above)
                 MdRec md;
                 if (found >= 0) md_load(omd + (size_t)MD_REC * found, md);
                 else md_zero(md);
@@ -1021,6 +1030,14 @@ constexpr int DEM_MAXPER = 640;  // (2 * 64 + 168 + 48) B per particle: 220 KB o
 
 static size_t dem_smem(int per) { return (size_t)per * (2 * sizeof(Pub) + sizeof(Priv) + DEM_MAXA * sizeof(int2)); }
 
+// the DEM kernel of the context's dimension and contact law
+using DemKernel = void (*)(DemCfg, DemState, int, int);
+static DemKernel dem_kernel(const Ctx* c) {
+    const bool h = c->dem.law == PIBM_HERTZ_MD_HIST;
+    if (c->D == 2) return h ? k_dem<2, true> : k_dem<2, false>;
+    return h ? k_dem<3, true> : k_dem<3, false>;
+}
+
 int dem_cluster_size(Ctx* c) {
     int n = c->np;
     int cs = c->tune_dem_particles_per_cta > 0 ? (n + c->tune_dem_particles_per_cta - 1) / c->tune_dem_particles_per_cta
@@ -1029,7 +1046,7 @@ int dem_cluster_size(Ctx* c) {
     if (cs > 8) {
         int max16 = 0;  // is a 16-CTA cluster with this much shared memory schedulable here?
         {
-            auto kern = c->D == 2 ? k_dem<2> : k_dem<3>;
+            auto kern = dem_kernel(c);
             int per = (n + 15) / 16;
             if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dem_smem(DEM_MAXPER)) == cudaSuccess) {
@@ -1087,14 +1104,15 @@ cudaError_t launch_dem(Ctx* c, cudaStream_t s, int nsub) {
     int cs = c->dem_cs;
     DemCfg C = c->dem;
     C.per = (c->np + cs - 1) / cs;
-    auto kern = c->D == 2 ? k_dem<2> : k_dem<3>;
+    auto kern = dem_kernel(c);
     size_t smem = dem_smem(C.per);
-    if (!c->dem_attr_ok) {  // once per context: these are host calls, not needed per launch
+    const int variant = 1 << ((c->D == 2 ? 0 : 2) + (c->dem.law == PIBM_HERTZ_MD_HIST ? 1 : 0));
+    if (!(c->dem_attr_ok & variant)) {  // once per context and kernel: host calls, not needed per launch
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dem_smem(DEM_MAXPER));
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
-        c->dem_attr_ok = 1;
+        c->dem_attr_ok |= variant;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);

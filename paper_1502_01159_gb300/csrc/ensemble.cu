@@ -9,10 +9,12 @@
 // the GPU; one launch replaces 5-6 launches per box.  Box set-up and
 // read-back go through the usual per-context calls.
 //
-// The autotuner times candidate launch shapes per box with CUDA events on
-// real steps (launch shapes do not change any result) and keeps the fastest.
+// The autotuner times candidate launch shapes with CUDA events on real steps
+// (launch shapes change no result): each box's DEM shape alone, then whole
+// configurations as ensemble steps, and keeps the fastest by a margin.
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -207,30 +209,53 @@ pibm_status pibm_ensemble_kernels_per_step(pibm_ensemble* e, int* n) {
     return PIBM_OK;
 }
 
+// Median device time of one ensemble step (graph launch) over reps steps,
+// CUDA events on the ensemble stream; two untimed steps first, so that the
+// graphs of both step parities are captured outside the timed region.
+static pibm_status time_ensemble(pibm_ensemble* e, int reps, double* median_ms) {
+    pibm_status st = pibm_ensemble_step(e, 2);
+    if (st != PIBM_OK) return st;
+    cudaEvent_t a, b;
+    ECHECK(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return efail(e, PIBM_ERR_CUDA, "autotune: event creation failed");
+    }
+    std::vector<double> ms;
+    for (int r = 0; r < reps && st == PIBM_OK; r++) {
+        cudaError_t x = cudaEventRecord(a, e->s);
+        if (x == cudaSuccess && (st = pibm_ensemble_step(e, 1)) != PIBM_OK) break;
+        if (x == cudaSuccess) x = cudaEventRecord(b, e->s);
+        if (x == cudaSuccess) x = cudaEventSynchronize(b);
+        float v = 0.f;
+        if (x == cudaSuccess) x = cudaEventElapsedTime(&v, a, b);
+        if (x != cudaSuccess) st = efail(e, PIBM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(x));
+        ms.push_back(v);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != PIBM_OK) return st;
+    std::sort(ms.begin(), ms.end());
+    *median_ms = ms[ms.size() / 2];
+    return PIBM_OK;
+}
+
 pibm_status pibm_ensemble_autotune(pibm_ensemble* e, int reps, int32_t* choice) {
     if (!e || reps < 1) return PIBM_ERR_ARG;
-    // candidate launch shapes: lattice threads per block (0 = default) and
-    // DEM particles per CTA (0 = default); every box runs the same number of
-    // steps, so the boxes stay at the same time
-    static const int lat_cand[] = {0, 64, 128, 256, 512};
-    static const int dem_cand[] = {0, 16, 48, 64, 96};
-    const int ncand = 5;
     const int nb = (int)e->box.size();
-    std::vector<double> best_lat(nb, 1e300), best_dem(nb, 1e300);
-    std::vector<int> pick_lat(nb, 0), pick_dem(nb, 0);
+    // 1. each box's DEM shape, timed alone (the DEM kernel of each candidate;
+    //    every box runs the same number of steps, so the boxes stay at one time)
+    static const int dem_cand[] = {0, 16, 48, 64, 96};
+    std::vector<int> pick_dem(nb, 0);
     for (int b = 0; b < nb; b++) {
         pibm_ctx* c = e->box[b];
         Ctx* cs = ctx_state(c);
-        for (int k = 0; k < ncand; k++) {
-            const bool dem_ok = cs->np > 0 && dem_cand[k] <= dem_max_per_cta() &&
-                                (dem_cand[k] == 0 || (cs->np + dem_cand[k] - 1) / dem_cand[k] <= 16);
-            if (pibm_set_tuning(c, PIBM_TUNE_LATTICE_THREADS, lat_cand[k]) != PIBM_OK)
-                return efail(e, PIBM_ERR_ARG, "autotune: lattice shape rejected");
-            bool dem_set = dem_ok;
-            if (cs->np > 0 && pibm_set_tuning(c, PIBM_TUNE_DEM_PARTICLES_PER_CTA, dem_ok ? dem_cand[k] : 0) != PIBM_OK) {
-                dem_set = false;  // shape not possible for this box: time the default instead
-                pibm_set_tuning(c, PIBM_TUNE_DEM_PARTICLES_PER_CTA, 0);
-            }
+        double best = 1e300;
+        for (int k = 0; k < 5; k++) {
+            const bool ok = cs->np > 0 && dem_cand[k] <= dem_max_per_cta() &&
+                            (dem_cand[k] == 0 || (cs->np + dem_cand[k] - 1) / dem_cand[k] <= 16) &&
+                            pibm_set_tuning(c, PIBM_TUNE_DEM_PARTICLES_PER_CTA, dem_cand[k]) == PIBM_OK;
+            if (cs->np > 0 && !ok) pibm_set_tuning(c, PIBM_TUNE_DEM_PARTICLES_PER_CTA, 0);
             for (int r = 0; r < reps; r++) {
                 double ms[4];
                 pibm_status st = pibm_step_timed(c, ms);
@@ -239,17 +264,56 @@ pibm_status pibm_ensemble_autotune(pibm_ensemble* e, int reps, int32_t* choice) 
                     pibm_last_error(c, buf, sizeof buf);
                     return efail(e, st, "autotune: box " + std::to_string(b) + ": " + buf);
                 }
-                if (ms[0] < best_lat[b]) best_lat[b] = ms[0], pick_lat[b] = lat_cand[k];
-                if (dem_set && cs->np > 0 && ms[1] < best_dem[b]) best_dem[b] = ms[1], pick_dem[b] = dem_cand[k];
+                if (ok && ms[1] < best) best = ms[1], pick_dem[b] = dem_cand[k];
             }
         }
-        pibm_set_tuning(c, PIBM_TUNE_LATTICE_THREADS, pick_lat[b]);
-        if (cs->np > 0) pibm_set_tuning(c, PIBM_TUNE_DEM_PARTICLES_PER_CTA, pick_dem[b]);
-        if (choice) choice[2 * b] = pick_lat[b], choice[2 * b + 1] = pick_dem[b];
+        if (cs->np > 0) pibm_set_tuning(c, PIBM_TUNE_DEM_PARTICLES_PER_CTA, 0);
     }
-    // the boxes stepped in turn above; bring them back to one time
     for (int b = 1; b < nb; b++)
         if (ctx_state(e->box[b])->t != ctx_state(e->box[0])->t) return efail(e, PIBM_ERR_STATE, "autotune: time mismatch");
+    // 2. whole-ensemble configurations, timed as ensemble steps (the boxes share
+    //    the GPU there, so a box's fastest shape alone need not be fastest in the
+    //    ensemble): lattice threads per block x whole-row lattice blocks, each with
+    //    the default DEM shapes and with the picks of step 1
+    struct Cfg {
+        int lat, rows, dem;
+    };
+    std::vector<Cfg> cand;
+    static const int lat_cand[] = {0, 128, 256, 512};
+    for (int dem = 0; dem < 2; dem++)
+        for (int rows = 0; rows < 2; rows++)
+            for (int l = 0; l < 4; l++) cand.push_back({lat_cand[l], rows, dem});
+    auto apply = [&](const Cfg& g) -> pibm_status {
+        for (int b = 0; b < nb; b++) {
+            pibm_ctx* c = e->box[b];
+            pibm_status st = pibm_set_tuning(c, PIBM_TUNE_LATTICE_THREADS, g.lat);
+            if (st == PIBM_OK) st = pibm_set_tuning(c, PIBM_TUNE_LATTICE_ROW_TILES, g.rows);
+            if (st == PIBM_OK && ctx_state(c)->np > 0)
+                st = pibm_set_tuning(c, PIBM_TUNE_DEM_PARTICLES_PER_CTA, g.dem ? pick_dem[b] : 0);
+            if (st != PIBM_OK) return efail(e, st, "autotune: launch shape rejected");
+        }
+        return PIBM_OK;
+    };
+    double best = 1e300, base = 1e300;
+    size_t pick = 0;
+    for (size_t k = 0; k < cand.size(); k++) {
+        double ms = 0.0;
+        pibm_status st = apply(cand[k]);
+        if (st == PIBM_OK) st = time_ensemble(e, reps + 2, &ms);
+        if (st != PIBM_OK) return st;
+        if (k == 0) base = ms;
+        if (ms < best) best = ms, pick = k;
+    }
+    // keep the defaults unless the best candidate is faster by more than 1 %
+    if (!(best < 0.99 * base)) pick = 0;
+    pibm_status st = apply(cand[pick]);
+    if (st != PIBM_OK) return st;
+    if (choice)
+        for (int b = 0; b < nb; b++) {
+            choice[3 * b] = cand[pick].lat;
+            choice[3 * b + 1] = cand[pick].rows;
+            choice[3 * b + 2] = cand[pick].dem ? pick_dem[b] : 0;
+        }
     return PIBM_OK;
 }
 

@@ -606,16 +606,20 @@ __device__ void solve_small(double* A, double* b, int m) {
 }
 
 // Features 0-6 from the sums the footprint pass accumulates over the
-// particle's owned nodes (fsum[p]: count, sum d (3), sum d d^T (xx, yy, zz,
-// xy, xz, yz), sum u (3), sum d x u (3), sum dT): one thread per particle.
+// particle's owned nodes with the coupling's weights (fsum[p]: sum w, sum w d
+// (3), sum w d d^T (xx, yy, zz, xy, xz, yz), sum w u (3), sum w d x u (3) with
+// w = eps rho, then sum eps dT and sum eps): the weighted rigid-motion fit
+//   m V - D x Om = sum w u,  D x V + M Om = sum w d x u
+// (m = sum w, D = sum w d, M = sum w (|d|^2 I - d d^T)) and the eps-weighted
+// mean temperature; one thread per particle.
 template <int D>
 __global__ void k_feature_solve(int n, const double* __restrict__ fsum, const double* __restrict__ U,
                                 const double* __restrict__ W, const double* __restrict__ Tp, double Tref,
                                 double* __restrict__ out) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    double s[17];
-    for (int k = 0; k < 17; k++) s[k] = fsum[17 * (long long)p + k];
+    double s[SG_NFSUM];
+    for (int k = 0; k < SG_NFSUM; k++) s[k] = fsum[SG_NFSUM * (long long)p + k];
     double V[3] = {0, 0, 0}, Om[3] = {0, 0, 0};
     const double m = s[0];
     if (m > 0) {
@@ -649,7 +653,7 @@ __global__ void k_feature_solve(int n, const double* __restrict__ fsum, const do
         o[a] = U[3 * p + a] - V[a];
         o[3 + a] = W[3 * p + a] - Om[a];
     }
-    o[6] = Tp[p] - (m > 0 ? Tref + s[16] / m : 0.0);
+    o[6] = Tp[p] - (s[17] > 0 ? Tref + s[16] / s[17] : 0.0);
 }
 
 // Neighbour features (solid fraction and the four smallest gaps), n-body

@@ -245,13 +245,17 @@ struct DemCfg {
     int cap;          // capacity of the canonical pair list
     int maxnb;        // candidates per particle
     int per;          // particles per CTA of the DEM cluster
-    const float* J;   // learned hydrodynamic Jacobian [n][18] or null
+    const float* J;   // learned hydrodynamic Jacobian [n][SG_NJ] or null
     const int* J_on;  // device gate: apply J this step when non-zero
 };
 
 // learned coupling surrogate (surrogate.cu)
 constexpr int SG_NFEAT = 12, SG_NOUT = 7;
-constexpr int SG_NPARAMS = 64 * 12 + 64 + 2 * (64 * 64 + 64) + 7 * 64 + 7;
+// 12 -> 64 -> 64 -> 64 -> 7 tanh layers plus the 7 x 12 linear path
+constexpr int SG_NPARAMS = 64 * 12 + 64 + 2 * (64 * 64 + 64) + 7 * 64 + 7 + 7 * 12;
+constexpr int SG_NFSUM = 18;  // feature sums per particle from the footprint pass
+constexpr int SG_ROWS = 8;    // network rows per particle: the state and seven perturbations
+constexpr int SG_NJ = 19;     // Jacobian values per particle: J_FU (9), J_TW (9), J_HT
 constexpr int SG_TRAIN_BLOCKS = 152;
 constexpr int SG_NB_SLICES = 16;  // neighbour-feature slices of the particle set
 struct Surrogate {
@@ -264,10 +268,10 @@ struct Surrogate {
     double bound, delta;
     int cap;                         // particles the per-particle buffers hold
     double* feat;                    // [n][12]
-    double* fsum;                    // [n][17] feature sums of the footprint pass
+    double* fsum;                    // [n][SG_NFSUM] feature sums of the footprint pass
     float4* xr;                      // [n] FP32 positions and radii (neighbour prefilter)
     double* nbpart;                  // [slices][n][5] neighbour-feature partials
-    float *rows, *yrows, *J;         // [7n][16], [7n][8], [n][18]
+    float *rows, *yrows, *J;         // [SG_ROWS n][16], [SG_ROWS n][8], [n][SG_NJ]
     double* part;                    // gate partial sums
     int *J_on, *err;                 // device gate flag, tensor-core wait status
     int wait_polls;                  // poll limit of a tensor-core completion wait
@@ -336,7 +340,7 @@ struct Ctx {
     int tune_coupling_order;         // 1 (default): coupling blocks take the particles in cell-list order
     int tune_lattice_threads;        // 0: default block shape; else threads per lattice block
     int tune_wide_index;             // 1: 64-bit slot offsets in the lattice kernel even where 32-bit suffice
-    int dem_attr_ok;                 // the DEM kernel's launch attributes are set
+    int dem_attr_ok;                 // bit per DEM kernel variant (dimension, law) whose launch attributes are set
     int spread_smem;                 // shared memory per CTA of the spread kernel (from the largest radius)
     double rmax;                     // largest particle radius
     Surrogate sg;
@@ -400,6 +404,9 @@ int surrogate_kernel_count(Ctx* c);
 cudaError_t train_batch(Ctx* c, cudaStream_t s, const float* xb, const float* yb, int B, float lr, float* grad_out,
                         double* loss_out);
 cudaError_t launch_gather(cudaStream_t s, int B, const int* idx, const float* X, const float* Y, float* xb, float* yb);
+size_t lsq_scratch_doubles();
+cudaError_t launch_lsq(Ctx* c, cudaStream_t s, const float* X, const float* Y, long long n, double ridge, double* part,
+                       int* status);
 Ctx* ctx_state(pibm_ctx* ctx);
 pibm_status ctx_ready(pibm_ctx* ctx);
 

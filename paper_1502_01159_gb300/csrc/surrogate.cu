@@ -1,27 +1,34 @@
 // Learned coupling surrogate: a 12 -> 64 -> 64 -> 64 -> 7 MLP (tanh hidden
-// layers) that maps per-particle features (relative velocity and spin against
-// the fluid the particle covers, temperature difference, local solid
-// fraction, four nearest surface gaps) to the PIBM coupling's force, torque and
-// heat flux.  Inside the DEM substeps half its secant Jacobian in the
-// particle's velocity and spin corrects the hydrodynamic load held over the
-// lattice step (Eq demgov; the held load is the mean of two couplings, and a
-// velocity change enters the newer one); the PIBM coupling computed every
-// step is the reference it is checked against, and the correction is switched
-// off for the next step whenever the network's force differs from it by more
-// than the bound.
+// layers) with a linear path from its inputs to its outputs, mapping
+// per-particle features (relative velocity and spin against the fluid the
+// particle owns in the coupling, temperature difference, local solid
+// fraction, four nearest surface gaps) to the PIBM coupling's force, torque
+// and heat flux.  Half its secant Jacobian in the particle's velocity and
+// spin corrects the hydrodynamic load held over the lattice step inside the
+// DEM substeps (Eq demgov; the held load is the mean of two couplings, and a
+// change of the particle's state enters the newer one), and half its
+// derivative in the particle temperature enters the thermosensitive update;
+// the PIBM coupling computed every step is the reference it is checked
+// against, and the correction is switched off for the next step whenever the
+// network's force differs from it by more than the bound.
 //
 //   inference  k_mlp_tc: tcgen05 BF16 tensor-core MMAs (M = 128 rows per CTA,
 //              N = 64 / 16, K = 16 / 64), FP32 accumulators in tensor memory,
 //              bias + tanh epilogue from tcgen05.ld, activations re-staged
-//              as BF16 in shared memory for the next layer
-//   training   k_train_partial / k_train_adam: FP32 forward and backward on
+//              as BF16 in shared memory for the next layer; the linear path
+//              is one more MMA of the staged inputs into the output layer's
+//              accumulators
+//   training   k_lsq_partial / k_lsq_solve: the linear path and output bias
+//              by least squares (FP64 normal equations); then
+//              k_train_partial / k_train_adam: FP32 forward and backward on
 //              CUDA cores, deterministic two-level gradient reduction, Adam
 //
 // Parameters are FP32, packed [W1 (64x12), b1, W2 (64x64), b2, W3, b3,
-// W4 (7x64), b4] with W[out][in]; standardisation: x_n = (x - mu_x) / sd_x,
-// y = y_n sd_y + mu_y (38 floats: mu_x, sd_x, mu_y, sd_y).
+// W4 (7x64), b4, Ws (7x12)] with W[out][in]; standardisation: x_n = (x -
+// mu_x) / sd_x, y = y_n sd_y + mu_y (38 floats: mu_x, sd_x, mu_y, sd_y).
 #include <string.h>
 
+#include <algorithm>
 #include <random>
 #include <string>
 #include <vector>
@@ -33,7 +40,8 @@ namespace pibm {
 constexpr int NF = SG_NFEAT, NO = SG_NOUT, HW = 64;
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + HW * NF, OFF_W2 = OFF_B1 + HW, OFF_B2 = OFF_W2 + HW * HW;
 constexpr int OFF_W3 = OFF_B2 + HW, OFF_B3 = OFF_W3 + HW * HW, OFF_W4 = OFF_B3 + HW, OFF_B4 = OFF_W4 + NO * HW;
-static_assert(OFF_B4 + NO == SG_NPARAMS, "parameter layout");
+constexpr int OFF_WS = OFF_B4 + NO;  // the linear path, NO x NF
+static_assert(OFF_WS + NO * NF == SG_NPARAMS, "parameter layout");
 
 // ------------------------------------------------------------- tcgen05 MLP
 constexpr int MLP_M = 128;      // rows per CTA (tensor-memory lanes)
@@ -46,7 +54,8 @@ constexpr int SM_W1 = SM_H + 128 * 64 * 2;    // 64 x 16 bf16    (SBO 256)
 constexpr int SM_W2 = SM_W1 + 64 * 16 * 2;    // 64 x 64 bf16    (SBO 1024)
 constexpr int SM_W3 = SM_W2 + 64 * 64 * 2;
 constexpr int SM_W4 = SM_W3 + 64 * 64 * 2;    // 16 x 64 bf16 (rows 7..15 zero)
-constexpr int SM_BIAS = SM_W4 + 16 * 64 * 2;  // 64 * 3 + 16 floats
+constexpr int SM_WS = SM_W4 + 16 * 64 * 2;    // 16 x 16 bf16 (rows 7..15, columns 12..15 zero; SBO 256)
+constexpr int SM_BIAS = SM_WS + 16 * 16 * 2;  // 64 * 3 + 16 floats
 constexpr int SM_BAR = SM_BIAS + (64 * 3 + 16) * 4;
 constexpr int SM_TMEM = SM_BAR + 8;
 constexpr int MLP_SMEM = SM_TMEM + 8 + 1024;  // + alignment slack
@@ -145,6 +154,11 @@ __global__ void __launch_bounds__(MLP_T) k_mlp_tc(const float* __restrict__ para
         reinterpret_cast<__nv_bfloat16*>(sm + SM_W4 + core_off(n, k, 1024))[0] =
             __float2bfloat16_rn(n < NO ? params[OFF_W4 + n * HW + k] : 0.f);
     }
+    for (int e = tid; e < 16 * 16; e += MLP_T) {
+        const int n = e >> 4, k = e & 15;
+        reinterpret_cast<__nv_bfloat16*>(sm + SM_WS + core_off(n, k, 256))[0] =
+            __float2bfloat16_rn(n < NO && k < NF ? params[OFF_WS + n * NF + k] : 0.f);
+    }
     for (int e = tid; e < 64; e += MLP_T) {
         bias[e] = params[OFF_B1 + e];
         bias[64 + e] = params[OFF_B2 + e];
@@ -188,6 +202,9 @@ __global__ void __launch_bounds__(MLP_T) k_mlp_tc(const float* __restrict__ para
             for (int kk = 0; kk < K / 16; kk++)  // K = 16 per MMA: two core matrices along K (256 B)
                 mma_bf16(tmem, smem_desc(a0 + kk * 256, 128, sbo), smem_desc(b0 + kk * 256, 128, sbo),
                          idesc_bf16(MLP_M, N), kk > 0);
+            if (layer == 3)  // the linear path: the staged inputs times Ws, into the same accumulators
+                mma_bf16(tmem, smem_desc(sbase + SM_X, 128, 256), smem_desc(sbase + SM_WS, 128, 256),
+                         idesc_bf16(MLP_M, N), 1);
             mma_commit(bar);
         }
         const bool mine = bar_wait(bar, (uint32_t)(layer & 1), wait_polls);
@@ -236,22 +253,24 @@ __global__ void __launch_bounds__(MLP_T) k_mlp_tc(const float* __restrict__ para
 }
 
 // --------------------------------------------------------- surrogate rows
-// Per particle seven rows: the standardised features, then the same with
-// delta added to each of the six velocity / spin features.
+// Per particle SG_ROWS = 8 rows: the standardised features, then the same with
+// delta added to each of the six velocity / spin features and to the
+// temperature feature.
 __global__ void k_sg_rows(int n, const double* __restrict__ feat, const float* __restrict__ norm, float delta,
                           float* __restrict__ rows) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     float x[NF];
     for (int k = 0; k < NF; k++) x[k] = (float)((feat[12 * (long long)p + k] - (double)norm[k]) / (double)norm[NF + k]);
-    for (int j = 0; j < 7; j++) {
-        float* r = rows + (7 * (long long)p + j) * 16;
+    for (int j = 0; j < SG_ROWS; j++) {
+        float* r = rows + (SG_ROWS * (long long)p + j) * 16;
         for (int k = 0; k < 16; k++) r[k] = k < NF ? x[k] + (j > 0 && k == j - 1 ? delta : 0.f) : 0.f;
     }
 }
 
 // Jacobian and gate partial sums: J_FU[a][b] = (F_a(row 1+b) - F_a(row 0)) / (delta sd_x[b]),
-// J_TW[a][b] = (tau_a(row 4+b) - tau_a(row 0)) / (delta sd_x[3+b]); partial sums of
+// J_TW[a][b] = (tau_a(row 4+b) - tau_a(row 0)) / (delta sd_x[3+b]), J_HT = (H(row 7) -
+// H(row 0)) / (delta sd_x[6]), each halved (the applied share); partial sums of
 // |F_mlp - F_pibm| and |F_pibm| per block.
 constexpr int GATE_T = 256;
 __global__ void __launch_bounds__(GATE_T) k_sg_jacobian(int n, const float* __restrict__ yrows, const float* __restrict__ norm,
@@ -264,18 +283,19 @@ __global__ void __launch_bounds__(GATE_T) k_sg_jacobian(int n, const float* __re
         const float* ymu = norm + 2 * NF;
         const float* ysd = norm + 2 * NF + NO;
         const float* xsd = norm + NF;
-        float Y[7][NO];
-        for (int j = 0; j < 7; j++)
-            for (int k = 0; k < NO; k++) Y[j][k] = yrows[(7 * (long long)p + j) * 8 + k] * ysd[k] + ymu[k];
-        // The DEM holds the mean of the couplings of t and t-1; a velocity change
-        // enters only the newer of the two, so the held load's sensitivity is
-        // half the coupling's: J = (1/2) secant of the network.
-        float* Jp = J + 18 * (long long)p;
+        float Y[SG_ROWS][NO];
+        for (int j = 0; j < SG_ROWS; j++)
+            for (int k = 0; k < NO; k++) Y[j][k] = yrows[(SG_ROWS * (long long)p + j) * 8 + k] * ysd[k] + ymu[k];
+        // The DEM holds the mean of the couplings of t and t-1; a change of the
+        // particle's state enters only the newer of the two, so the held load's
+        // sensitivity is half the coupling's: J = (1/2) secant of the network.
+        float* Jp = J + SG_NJ * (long long)p;
         for (int a = 0; a < 3; a++)
             for (int b = 0; b < 3; b++) {
                 Jp[3 * a + b] = 0.5f * (Y[1 + b][a] - Y[0][a]) / (delta * xsd[b]);
                 Jp[9 + 3 * a + b] = 0.5f * (Y[4 + b][3 + a] - Y[0][3 + a]) / (delta * xsd[3 + b]);
             }
+        Jp[18] = 0.5f * (Y[7][6] - Y[0][6]) / (delta * xsd[6]);
         double d2 = 0.0, f2 = 0.0;
         for (int a = 0; a < 3; a++) {
             const double fp = Fh[3 * (long long)p + a];
@@ -360,6 +380,7 @@ __global__ void __launch_bounds__(TRAIN_T) k_train_partial(const float* __restri
             const int r = e / NO, o = e % NO;
             float z = w[OFF_B4 + o];
             for (int i = 0; i < HW; i++) z += w[OFF_W4 + o * HW + i] * a[2 * TR * HW + r * HW + i];
+            for (int i = 0; i < NF; i++) z += w[OFF_WS + o * NF + i] * x[r * NF + i];  // the linear path
             const float diff = r < nr ? z - y[e] : 0.f;
             d4[e] = scale * diff;
             lsum += diff * diff;
@@ -390,10 +411,11 @@ __global__ void __launch_bounds__(TRAIN_T) k_train_partial(const float* __restri
             else if (k < OFF_B3) l = 2, isb = false, o = (k - OFF_W3) / HW, i = (k - OFF_W3) % HW, nin = HW;
             else if (k < OFF_W4) l = 2, isb = true, o = k - OFF_B3, i = 0, nin = HW;
             else if (k < OFF_B4) l = 3, isb = false, o = (k - OFF_W4) / HW, i = (k - OFF_W4) % HW, nin = HW;
-            else l = 3, isb = true, o = k - OFF_B4, i = 0, nin = HW;
-            const float* dlt = l == 3 ? d4 : dl + l * TR * HW;
-            const int nout = l == 3 ? NO : HW;
-            const float* in = l == 0 ? x : a + (l - 1) * TR * HW;
+            else if (k < OFF_WS) l = 3, isb = true, o = k - OFF_B4, i = 0, nin = HW;
+            else l = 4, isb = false, o = (k - OFF_WS) / NF, i = (k - OFF_WS) % NF, nin = NF;  // linear path
+            const float* dlt = l >= 3 ? d4 : dl + l * TR * HW;
+            const int nout = l >= 3 ? NO : HW;
+            const float* in = (l == 0 || l == 4) ? x : a + (l - 1) * TR * HW;
             float s = 0.f;
             for (int r = 0; r < nr; r++) s += dlt[r * nout + o] * (isb ? 1.f : in[r * nin + i]);
             gacc[k] += s;
@@ -445,6 +467,77 @@ __global__ void k_gather_rows(int B, const int* __restrict__ idx, const float* _
     for (int k = 0; k < NO; k++) yb[(long long)e * NO + k] = Y[s * NO + k];
 }
 
+// Least squares for the linear path: with A = [x_n 1] (13 columns) over the
+// training rows, the normal equations (A^T A + ridge n I) C = A^T Y_n give
+// Ws = C[0..12)^T and b4 = C[12].  k_lsq_partial: block b accumulates, one
+// thread per entry (169 of A^T A, 91 of A^T Y), the FP64 sums over its rows in
+// row order; k_lsq_solve: one thread adds the block partials in block order,
+// solves by Gaussian elimination with partial pivoting (FP64) and writes Ws,
+// b4 and zero W4 into the parameters.
+constexpr int LSQ_N = NF + 1, LSQ_E = LSQ_N * LSQ_N + LSQ_N * NO, LSQ_T = 288, LSQ_BLOCKS = 152;
+static_assert(LSQ_E <= LSQ_T, "one thread per normal-equation entry");
+
+__global__ void __launch_bounds__(LSQ_T) k_lsq_partial(const float* __restrict__ X, const float* __restrict__ Y,
+                                                       long long n, double* __restrict__ part) {
+    const int e = threadIdx.x;
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long r0 = blockIdx.x * per, r1 = r0 + per < n ? r0 + per : n;
+    if (e >= LSQ_E) return;
+    int i, j;
+    bool rhs;
+    if (e < LSQ_N * LSQ_N) i = e / LSQ_N, j = e % LSQ_N, rhs = false;
+    else i = (e - LSQ_N * LSQ_N) / NO, j = (e - LSQ_N * LSQ_N) % NO, rhs = true;
+    double sum = 0.0;
+    for (long long r = r0; r < r1; r++) {
+        const double ai = i < NF ? (double)X[r * NF + i] : 1.0;
+        const double bj = rhs ? (double)Y[r * NO + j] : (j < NF ? (double)X[r * NF + j] : 1.0);
+        sum += ai * bj;
+    }
+    part[(long long)blockIdx.x * LSQ_E + e] = sum;
+}
+
+__global__ void k_lsq_solve(int nblocks, const double* __restrict__ part, long long n, double ridge, float* params,
+                            int* status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double A[LSQ_N][LSQ_N + NO];
+    for (int i = 0; i < LSQ_N; i++)
+        for (int j = 0; j < LSQ_N + NO; j++) A[i][j] = 0.0;
+    for (int b = 0; b < nblocks; b++) {
+        const double* q = part + (long long)b * LSQ_E;
+        for (int i = 0; i < LSQ_N; i++) {
+            for (int j = 0; j < LSQ_N; j++) A[i][j] += q[i * LSQ_N + j];
+            for (int j = 0; j < NO; j++) A[i][LSQ_N + j] += q[LSQ_N * LSQ_N + i * NO + j];
+        }
+    }
+    for (int i = 0; i < LSQ_N; i++) A[i][i] += ridge * (double)n;
+    for (int c = 0; c < LSQ_N; c++) {
+        int piv = c;
+        for (int r = c + 1; r < LSQ_N; r++)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (!(fabs(A[piv][c]) > 0.0)) {
+            *status = 1;  // singular (cannot happen with a positive ridge); parameters left unchanged
+            return;
+        }
+        if (piv != c)
+            for (int j = 0; j < LSQ_N + NO; j++) {
+                const double t = A[c][j];
+                A[c][j] = A[piv][j];
+                A[piv][j] = t;
+            }
+        for (int r = 0; r < LSQ_N; r++) {
+            if (r == c) continue;
+            const double f = A[r][c] / A[c][c];
+            for (int j = c; j < LSQ_N + NO; j++) A[r][j] -= f * A[c][j];
+        }
+    }
+    for (int o = 0; o < NO; o++) {
+        for (int i = 0; i < NF; i++) params[OFF_WS + o * NF + i] = (float)(A[i][LSQ_N + o] / A[i][i]);
+        params[OFF_B4 + o] = (float)(A[NF][LSQ_N + o] / A[NF][NF]);
+        for (int i = 0; i < HW; i++) params[OFF_W4 + o * HW + i] = 0.f;
+    }
+    *status = 0;
+}
+
 // ------------------------------------------------------------- launchers
 cudaError_t launch_mlp(Ctx* c, cudaStream_t s, const float* in, int rows, float* out) {
     static bool attr = false;
@@ -466,7 +559,7 @@ cudaError_t launch_surrogate(Ctx* c, cudaStream_t s, int parity, bool need_sums)
     if (e != cudaSuccess) return e;
     k_sg_rows<<<(c->np + 127) / 128, 128, 0, s>>>(c->np, c->sg.feat, c->sg.norm, (float)c->sg.delta, c->sg.rows);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_mlp(c, s, c->sg.rows, 7 * c->np, c->sg.yrows)) != cudaSuccess) return e;
+    if ((e = launch_mlp(c, s, c->sg.rows, SG_ROWS * c->np, c->sg.yrows)) != cudaSuccess) return e;
     const int nb = (c->np + GATE_T - 1) / GATE_T;
     k_sg_jacobian<<<nb, GATE_T, 0, s>>>(c->np, c->sg.yrows, c->sg.norm, (float)c->sg.delta, c->Fh, c->sg.J, c->sg.part);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -492,6 +585,20 @@ cudaError_t train_batch(Ctx* c, cudaStream_t s, const float* xb, const float* yb
     if (lr > 0.f) c->sg.adam_t++;
     k_train_adam<<<(SG_NPARAMS + 255) / 256, 256, 0, s>>>(G, c->sg.partial, c->sg.lossp, c->sg.params, c->sg.m, c->sg.v,
                                                          c->sg.adam_t, lr, grad_out, loss_out, B);
+    return cudaGetLastError();
+}
+
+// The linear path and output bias by least squares over n standardised rows
+// (device arrays); part: LSQ_BLOCKS * LSQ_E doubles of scratch, status: 1 int.
+size_t lsq_scratch_doubles() { return (size_t)LSQ_BLOCKS * LSQ_E; }
+
+cudaError_t launch_lsq(Ctx* c, cudaStream_t s, const float* X, const float* Y, long long n, double ridge, double* part,
+                       int* status) {
+    const int G = (int)std::min<long long>(LSQ_BLOCKS, std::max<long long>(1, n / 64));
+    k_lsq_partial<<<G, LSQ_T, 0, s>>>(X, Y, n, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_lsq_solve<<<1, 32, 0, s>>>(G, part, n, ridge, c->sg.params, status);
     return cudaGetLastError();
 }
 

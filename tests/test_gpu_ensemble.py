@@ -79,9 +79,10 @@ def test_autotune_changes_no_result():
     cases = _cases(seed=7)
     tuned, plain = Ensemble(cases), Ensemble(cases)
     choice = tuned.autotune(reps=1)
-    assert len(choice) == len(cases) and tuned.t == 5
+    steps = 5 * 1 + 16 * (1 + 4)
+    assert len(choice) == len(cases) and all(len(c) == 3 for c in choice) and tuned.t == steps
     print("autotune choices", choice)
-    plain.step(5)
+    plain.step(steps)
     tuned.step(20)
     plain.step(20)
     for b in range(len(cases)):

@@ -1,8 +1,10 @@
 """Learned coupling surrogate on the GPU against its FP64 reference
 (oracle/surrogate.py) and the C oracle: features, FP32 training gradients,
-BF16 tensor-core inference, the hydrodynamic-Jacobian correction inside the
-DEM substeps, the device-side Jacobian and gate, and what the trained network
-gains over the plain method (stable light particles)."""
+the least-squares linear path, BF16 tensor-core inference, the
+hydrodynamic-Jacobian correction inside the DEM substeps and in the
+thermosensitive update, the device-side Jacobian and gate, and what the
+trained network gains over the plain method (stable light particles, stable
+particles of small heat capacity), with the gate at its 1 % bound."""
 import numpy as np
 import pytest
 
@@ -82,6 +84,7 @@ def test_training_gradient_matches_fp64_backprop():
     gen = np.random.default_rng(5)
     params = S.init_params(7)
     params = [(Wm, gen.normal(size=b.shape) * 0.1) for Wm, b in params]
+    params[4] = (gen.normal(size=(S.N_OUT, S.N_FEAT)) * 0.1, np.zeros(0))  # the linear path
     flat = S.flatten(params).astype(np.float32)
     norm = np.concatenate([np.zeros(12), np.ones(12), np.zeros(7), np.ones(7)]).astype(np.float32)
     sim.surrogate_set_params(flat, norm)
@@ -102,6 +105,7 @@ def test_tensor_core_inference_matches_bf16_reference():
     gen = np.random.default_rng(9)
     params = S.init_params(3)
     params = [(Wm, gen.normal(size=b.shape) * 0.2) for Wm, b in params]
+    params[4] = (gen.normal(size=(S.N_OUT, S.N_FEAT)) * 0.2, np.zeros(0))  # the linear path
     flat = S.flatten(params).astype(np.float32)
     norm = np.concatenate([np.zeros(12), np.ones(12), np.zeros(7), np.ones(7)]).astype(np.float32)
     sim.surrogate_set_params(flat, norm)
@@ -115,10 +119,13 @@ def test_tensor_core_inference_matches_bf16_reference():
         e_b = np.max(np.abs(Yg - Yb)) / scale
         e_64 = np.max(np.abs(Yg - Y64)) / scale
         print("inference", rows, e_b, e_64)
-        # same BF16 quantisation points as the reference; differences come from the
-        # accumulation order deciding a BF16 rounding of a hidden activation
-        assert e_b < 1e-2, (rows, e_b)
-        assert np.mean(np.abs(Yg - Yb)) / scale < 1e-3
+        # same BF16 quantisation points as the reference: within one tile the
+        # result is the reference's up to the FP32 accumulation of 64 + 16
+        # products (bound ~80 x 2^-24 = 5e-6 of the scale; measured 1e-7 to
+        # 8e-7); over many rows the accumulation order now and then decides a
+        # BF16 rounding of a hidden activation (measured ~5e-4 at 1 000 rows)
+        assert e_b < (2e-6 if rows <= 128 else 1e-3), (rows, e_b)
+        assert np.mean(np.abs(Yg - Yb)) / scale < 1e-5
         assert e_64 < 5e-2, (rows, e_64)  # BF16 against exact arithmetic
 
 
@@ -128,10 +135,11 @@ def test_fixed_jacobian_matches_oracle(dim):
     case = _case(dim, seed=23)
     n = len(case["particles"]["R"])
     gen = np.random.default_rng(4)
-    J = np.zeros((n, 18))
+    J = np.zeros((n, 19))
     for p in range(n):
         J[p, 0:9] = (-0.4 * np.eye(3) + 0.05 * gen.normal(size=(3, 3))).ravel()
         J[p, 9:18] = (-2.0 * np.eye(3) + 0.1 * gen.normal(size=(3, 3))).ravel()
+        J[p, 18] = 30.0 + 10.0 * gen.random()  # no effect here: no heat capacity
     J = J.astype(np.float32).astype(np.float64)  # the device keeps it in FP32
     sim, orc = _sim(case), oracle.Oracle(case)
     sim.set_hydro_jacobian(J)
@@ -148,6 +156,39 @@ def test_fixed_jacobian_matches_oracle(dim):
     assert np.max(np.abs(po["U"] - pp["U"])) > 1e-7  # the correction changes the motion
     Jr, on = sim.read_hydro_jacobian()
     assert on and np.array_equal(Jr, J)
+
+
+def _thermo_case(Cp, seed=51, rho_ratio=1.5):
+    """2-D: 14 disks of diameter 10 with random initial temperatures and heat
+    capacity Cp each (thermosensitive)."""
+    case = _case(2, seed=seed, rho_ratio=rho_ratio)
+    n = len(case["particles"]["R"])
+    case["particles"]["heat_cap"] = np.full(n, float(Cp))
+    case["particles"]["T_p"] = W.rng(seed + 100).random(n)
+    return case
+
+
+K_DISK = 157.629  # 2 kappa_T sum eps over the nodes a disk of diameter 10 covers (about 2 pi 25)
+
+
+def test_fixed_heat_jacobian_matches_oracle():
+    # the heat row: C_p (T_new - T) = -(H_held + J_HT (T_new - T)) at C_p = 10,
+    # where the explicit update (J_HT = 0) diverges within 10 steps (a = k /
+    # (2 C_p) = 7.9 > 1; oracle pin test_heat_jacobian_stabilises_small_heat_capacity)
+    case = _thermo_case(10.0)
+    n = len(case["particles"]["R"])
+    J = np.zeros((n, 19))
+    J[:, 18] = np.float32(0.5 * K_DISK)
+    sim, orc = _sim(case), oracle.Oracle(case)
+    sim.set_hydro_jacobian(J)
+    orc.set_hydro_jacobian(J)
+    sim.step(100)
+    orc.step(100)
+    Ts, To = sim.read_particles()["T_p"], orc.particles()["T_p"]
+    print("heat Jacobian: max |dT_p|", np.max(np.abs(Ts - To)), "range", To.min(), To.max())
+    assert np.all(np.isfinite(Ts)) and np.max(np.abs(To - 0.5)) < 0.5
+    assert np.max(np.abs(Ts - To)) < 1e-5
+    assert np.max(np.abs(sim.read_particles()["X"] - orc.particles()["X"])) < POS_ATOL
 
 
 def _collect(case, steps):
@@ -167,16 +208,28 @@ def test_training_and_device_jacobian_and_gate():
     case = _case(3, seed=25)
     feat, targ = _collect(case, 120)
     sim = _sim(case)
-    losses = sim.surrogate_train(feat, targ, epochs=40, batch=128, lr=2e-3, seed=1)
+    # zero epochs: the least-squares linear path alone, against the FP64 reference
+    sim.surrogate_train(feat, targ, epochs=0, batch=128, lr=2e-3, seed=1)
+    p0, norm0 = sim.surrogate_get_params()
+    mu, sd = S.standardise(feat)
+    ymu, ysd = S.standardise(targ)
+    ref = S.linear_fit(S.init_params(1), (feat - mu) / sd, (targ - ymu) / ysd)
+    got = S.unflatten(p0.astype(np.float64))
+    scale = np.max(np.abs(ref[4][0]))  # standardised data: the bias is ~0, the linear path O(1)
+    for a_, b_ in ((got[4][0], ref[4][0]), (got[3][1], ref[3][1])):
+        print("linear path vs reference", np.max(np.abs(a_ - b_)) / scale)
+        assert np.max(np.abs(a_ - b_)) <= 1e-4 * scale
+    assert not np.any(got[3][0])  # W4 = 0
+    losses = sim.surrogate_train(feat, targ, epochs=40, batch=128, lr=1e-3, seed=1)
     print("loss by epoch", losses[[0, 9, 19, 39]])
-    assert losses[-1] < 0.25 * losses[0]
+    assert losses[-1] < losses[0]
     params, norm = sim.surrogate_get_params()
     # the standardisation is the training set's
-    mu, sd = S.standardise(feat)
     assert np.allclose(norm[:12], mu, rtol=1e-5, atol=1e-9) and np.allclose(norm[12:24], sd, rtol=1e-5)
     sim.step(20)
-    # device Jacobian and gate against the reference arithmetic on the device's features
-    sim.surrogate_enable(True, bound=1e9, delta=0.25)
+    # device Jacobian and gate against the reference arithmetic on the device's features;
+    # the gate at its 1 % bound opens on this state
+    sim.surrogate_enable(True, bound=0.01, delta=0.25)
     fg = sim.read_features()
     Jd, on = sim.read_hydro_jacobian()
     p64 = S.unflatten(params.astype(np.float64))
@@ -186,12 +239,13 @@ def test_training_and_device_jacobian_and_gate():
     Jr = S.applied_jacobian(Jr)
     scale = np.max(np.abs(Jr))
     print("device Jacobian vs reference", np.max(np.abs(Jd - Jr)) / scale)
-    assert np.max(np.abs(Jd - Jr)) / scale < 5e-2
+    assert np.max(np.abs(Jd - Jr)) / scale < 1e-4
     F = sim.read_particle_forces()["F"]
     e_ref = S.gate_error(Yr[:, 0:3], F)
     st = sim.surrogate_stats()
     print("gate", st, e_ref)
-    assert on and abs(st["last_error"] - e_ref) < 0.05 * e_ref + 1e-6
+    assert abs(st["last_error"] - e_ref) < 1e-3 * e_ref + 1e-9
+    assert on and st["last_error"] < 0.01 and st["on_steps"] == 1
     # bound 0: the gate always falls back, and the run is the plain method bit for bit
     ref = _sim(case)
     ref.step(20)
@@ -234,8 +288,8 @@ def test_network_stabilises_light_particles():
             break
     assert diverged, "the plain method was expected to diverge for light particles"
     sim = _sim(light)
-    losses = sim.surrogate_train(feat, targ, epochs=60, batch=128, lr=2e-3, seed=4)
-    sim.surrogate_enable(True, bound=1e9, delta=0.25)
+    losses = sim.surrogate_train(feat, targ, epochs=60, batch=128, lr=1e-3, seed=4)
+    sim.surrogate_enable(True, bound=0.01, delta=0.25)
     J, on = sim.read_hydro_jacobian()
     rhoV = np.pi * 25.0  # fluid mass a disk of diameter 10 covers
     print("light particles: loss", losses[0], losses[-1], "applied diag J_FU / (rho_f V)", np.mean(J[:, [0, 4]]) / rhoV)
@@ -248,4 +302,58 @@ def test_network_stabilises_light_particles():
         assert umax < 0.02, (k, umax)  # stop early instead of running a diverging case on
     st = sim.surrogate_stats()
     print("light particles with the network: max |U| %.3g over 300 steps; gate" % umax, st)
-    assert st["on_steps"] >= 300
+    # the gate at its 1 % bound keeps the network in use on most steps (measured 217
+    # of 301: the light particles sit at the edge of the training data, where the
+    # network's force error is 0.5-1 %); the fallback steps do not let the run diverge
+    assert st["on_steps"] >= 200
+
+
+def test_network_stabilises_small_heat_capacity():
+    # The heat row.  The thermosensitive update is explicit too: below C_p = k / 2
+    # (k = dH/dT_p = 2 kappa_T sum eps, 158 for these disks) the particle
+    # temperature overshoots the fluid's and grows.  The network is trained on
+    # runs with heat capacities the plain method can do (500 and 2 000).  A run
+    # at C_p = 500 is stepped until the particles move, then its particles are
+    # given C_p = 10 (same positions, velocities, spins, temperatures; the fluid
+    # kept): the plain update then diverges within a few steps, while half the
+    # network's dH/dT_p, applied in the update with the gate at its 1 % bound,
+    # keeps the temperatures bounded.
+    from paper_1502_01159_gb300 import PibmError
+    feats, targs = [], []
+    for Cp, seed in ((500.0, 61), (2000.0, 62)):
+        f_, t_ = _collect(_thermo_case(Cp, seed=seed), 120)
+        feats.append(f_)
+        targs.append(t_)
+    feat, targ = np.concatenate(feats), np.concatenate(targs)
+
+    def switched(seed=63):
+        case = _thermo_case(500.0, seed=seed)
+        s_ = _sim(case)
+        s_.step(20)
+        p = s_.read_particles()
+        parts = dict(case["particles"])
+        parts.update(X=p["X"], U=p["U"], W=p["W"], T_p=p["T_p"], heat_cap=np.full(len(p["T_p"]), 10.0))
+        s_.set_particles(parts)
+        return s_
+
+    plain = switched()
+    try:
+        plain.step(6)
+        Tp = plain.read_particles()["T_p"]
+        diverged = not np.all(np.isfinite(Tp)) or np.max(np.abs(Tp)) > 100.0
+    except PibmError:
+        diverged = True  # the runaway temperature drove the flow until the DEM's displacement check tripped
+    assert diverged, "the plain update was expected to diverge"
+    plain.close()
+    sim = switched()
+    sim.surrogate_train(feat, targ, epochs=20, batch=128, lr=1e-3, seed=5)
+    sim.surrogate_enable(True, bound=0.01, delta=0.25)
+    J, on = sim.read_hydro_jacobian()
+    print("small heat capacity: applied J_HT / (k/2)", np.mean(J[:, 18]) / (0.5 * K_DISK), "gate on", on)
+    for k in range(10):
+        sim.step(20)
+        Tp = sim.read_particles()["T_p"]
+        assert np.all(np.isfinite(Tp)) and np.max(np.abs(Tp - 0.5)) < 0.6, (k, Tp.min(), Tp.max())
+    st = sim.surrogate_stats()
+    print("small heat capacity with the network: T_p in [%.3f, %.3f] after 200 steps; gate" % (Tp.min(), Tp.max()), st)
+    assert st["on_steps"] >= 190
