@@ -175,102 +175,82 @@ struct AAOffsets {
     IX src[19], dst[19], ld[19], st[19];
 };
 
-// Odd-step loads and stores of a warp that holds an x-face node, for rows whose
-// y/z neighbours are all inside: only the x neighbour can leave the lattice.
-// Every lane takes the interior slot (the fast path's offset); a lane whose x
-// neighbour in direction i lies beyond the face takes, by a select, the
-// periodic image (the interior slot shifted by nx) or, at a wall, its own
-// slot of direction i (loads) / opp(i) (stores), where bounce-back left or
-// leaves the value.  Interior lanes get the fast path's indices exactly, and
-// no lane diverges.
+// Odd-step loads and stores of a warp whose nodes can have a neighbour beyond
+// a face: a warp holding an x-face node, or a row on a y or z face.  Every lane
+// starts from the fast path's offset; per direction, a neighbour beyond a
+// periodic face is taken from the periodic image (the offset shifted by the
+// axis's extent times its stride), and a neighbour beyond a wall sends the
+// access to the node's own slot of direction i (loads) / opp(i) (stores),
+// where bounce-back left or leaves the value, with the anti-bounce-back of an
+// isothermal face for g.  When a diagonal neighbour leaves through two faces
+// the wall of the later axis (z, then y, then x) decides, as in pop_slot /
+// post_slot.  y and z are uniform across a warp and x only selects, so no warp
+// diverges; interior lanes get the fast path's offsets exactly.
 template <int D, typename S, typename IX>
-__device__ __forceinline__ void odd_load_xface(const Geo& G, const CollideParams<typename Store<S>::R>& P, const S* fn,
-                                               const S* gn, int x, const AAOffsets<IX>& O, typename Store<S>::R* s,
-                                               typename Store<S>::R* sg) {
+__device__ __forceinline__ void odd_load_face(const Geo& G, const CollideParams<typename Store<S>::R>& P, const S* fn,
+                                              const S* gn, int x, int y, int z, const AAOffsets<IX>& O,
+                                              typename Store<S>::R* s, typename Store<S>::R* sg) {
     using L = Lat<D>;
     using R = typename Store<S>::R;
-    const bool lo = x == 0, hi = x == G.nx - 1, per = G.per[0] != 0;
-    const IX nx = G.nx;
+    const bool xlo = x == 0, xhi = x == G.nx - 1, ylo = y == 0, yhi = y == G.ny - 1;
+    const bool zlo = L::dim == 3 && z == 0, zhi = L::dim == 3 && z == G.nz - 1;
+    const IX sx = (IX)G.nx, sy = (IX)G.nx * (IX)G.ny, sz = (IX)G.N;
 #pragma unroll
     for (int i = 0; i < L::Q; i++) {
-        const int ex = L::ex(i);
-        const bool out = (ex > 0 && lo) || (ex < 0 && hi);  // x - e_i beyond a face
+        const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+        // x - e_i beyond a face, per axis
+        const bool ox = (ex > 0 && xlo) || (ex < 0 && xhi);
+        const bool oy = (ey > 0 && ylo) || (ey < 0 && yhi);
+        const bool oz = (ez > 0 && zlo) || (ez < 0 && zhi);
+        int face = -1;
+        if (ox && !G.per[0]) face = ex > 0 ? 0 : 1;
+        if (oy && !G.per[1]) face = ey > 0 ? 2 : 3;
+        if (oz && !G.per[2]) face = ez > 0 ? 4 : 5;
         IX idx = O.src[i];
-        if (out) idx = per ? idx + ex * nx : O.ld[i];
+        if (ox) idx += (IX)ex * sx;
+        if (oy) idx += (IX)ey * sy;
+        if (oz) idx += (IX)ez * sz;
+        if (face >= 0) idx = O.ld[i];
         s[i] = Store<S>::ldf(fn[idx]);
         if (i < L::QG) {
             R v = Store<S>::ldg(gn[idx]);
-            const int face = ex > 0 ? 0 : 1;  // face crossed by x - e_i
-            if (out && !per && face_iso(G, face)) v = op_sub(P.abb[face], v);
+            if (face_iso(G, face)) v = op_sub(P.abb[face], v);
             sg[i < L::QG ? i : 0] = v;
         }
     }
 }
 
 template <int D, typename S, typename IX>
-__device__ __forceinline__ void odd_store_xface(const Geo& G, const CollideParams<typename Store<S>::R>& P, S* fn, S* gn,
-                                                int x, const AAOffsets<IX>& O, const typename Store<S>::R* s,
-                                                const typename Store<S>::R* sg) {
+__device__ __forceinline__ void odd_store_face(const Geo& G, const CollideParams<typename Store<S>::R>& P, S* fn, S* gn,
+                                               int x, int y, int z, const AAOffsets<IX>& O,
+                                               const typename Store<S>::R* s, const typename Store<S>::R* sg) {
     using L = Lat<D>;
     using R = typename Store<S>::R;
-    const bool lo = x == 0, hi = x == G.nx - 1, per = G.per[0] != 0;
-    const IX nx = G.nx;
+    const bool xlo = x == 0, xhi = x == G.nx - 1, ylo = y == 0, yhi = y == G.ny - 1;
+    const bool zlo = L::dim == 3 && z == 0, zhi = L::dim == 3 && z == G.nz - 1;
+    const IX sx = (IX)G.nx, sy = (IX)G.nx * (IX)G.ny, sz = (IX)G.N;
 #pragma unroll
     for (int i = 0; i < L::Q; i++) {
-        const int ex = L::ex(i);
-        const bool out = (ex > 0 && hi) || (ex < 0 && lo);  // x + e_i beyond a face
+        const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+        // x + e_i beyond a face, per axis
+        const bool ox = (ex > 0 && xhi) || (ex < 0 && xlo);
+        const bool oy = (ey > 0 && yhi) || (ey < 0 && ylo);
+        const bool oz = (ez > 0 && zhi) || (ez < 0 && zlo);
+        int face = -1;
+        if (ox && !G.per[0]) face = ex > 0 ? 1 : 0;
+        if (oy && !G.per[1]) face = ey > 0 ? 3 : 2;
+        if (oz && !G.per[2]) face = ez > 0 ? 5 : 4;
         IX idx = O.dst[i];
-        if (out) idx = per ? idx - ex * nx : O.st[i];
+        if (ox) idx -= (IX)ex * sx;
+        if (oy) idx -= (IX)ey * sy;
+        if (oz) idx -= (IX)ez * sz;
+        if (face >= 0) idx = O.st[i];
         fn[idx] = Store<S>::stf(s[i]);
         if (i < L::QG) {
             R v = sg[i < L::QG ? i : 0];
-            const int face = ex > 0 ? 1 : 0;  // face crossed by x + e_i
-            if (out && !per && face_iso(G, face)) v = op_sub(P.abb[face], v);
+            if (face_iso(G, face)) v = op_sub(P.abb[face], v);
             gn[idx] = Store<S>::stg(v);
         }
-    }
-}
-
-// Generic odd-step store of one node's post-collision populations (any boundary).
-template <int D, typename S>
-__device__ __forceinline__ void store_node(const Geo& G, const CollideParams<typename Store<S>::R>& P, S* f, S* g, int x,
-                                           int y, int z, const typename Store<S>::R* s, const typename Store<S>::R* sg) {
-    using L = Lat<D>;
-    using R = typename Store<S>::R;
-#pragma unroll
-    for (int i = 0; i < L::Q; i++) {
-        long long idx;
-        post_slot(G, x, y, z, L::ex(i), L::ey(i), L::ez(i), i, L::opp(i), 1, idx);
-        f[idx] = Store<S>::stf(s[i]);
-    }
-#pragma unroll
-    for (int k = 0; k < L::QG; k++) {
-        long long idx;
-        int face = post_slot(G, x, y, z, L::ex(k), L::ey(k), L::ez(k), k, L::opp(k), 1, idx);
-        R v = sg[k];
-        if (face_iso(G, face)) v = op_sub(P.abb[face], v);
-        g[idx] = Store<S>::stg(v);
-    }
-}
-
-// Generic-path thermal load (the anti-bounce-back uses the collision's rounding).
-template <int D, typename S, typename R>
-__device__ __forceinline__ void load_node_r(const Geo& G, const CollideParams<R>& P, const S* __restrict__ f,
-                                            const S* __restrict__ g, int x, int y, int z, int parity, R* s, R* sg) {
-    using L = Lat<D>;
-#pragma unroll
-    for (int i = 0; i < L::Q; i++) {
-        long long idx;
-        pop_slot(G, x, y, z, L::ex(i), L::ey(i), L::ez(i), i, L::opp(i), parity, idx);
-        s[i] = (R)Store<S>::ldf(f[idx]);
-    }
-#pragma unroll
-    for (int k = 0; k < L::QG; k++) {
-        long long idx;
-        int face = pop_slot(G, x, y, z, L::ex(k), L::ey(k), L::ez(k), k, L::opp(k), parity, idx);
-        R v = (R)Store<S>::ldg(g[idx]);
-        if (face_iso(G, face)) v = op_sub(P.abb[face], v);
-        sg[k] = v;
     }
 }
 
@@ -306,10 +286,8 @@ __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) 
         for (int i = 0; i < L::Q; i++) s[i] = Store<S>::ldf(fn[O.src[i]]);
 #pragma unroll
         for (int k = 0; k < L::QG; k++) sg[k] = Store<S>::ldg(gn[O.src[k]]);
-    } else if (inner_yz) {
-        odd_load_xface<D, S, IX>(G, P, fn, gn, x, O, s, sg);
     } else {
-        load_node_r<D, S, R>(G, P, f, g, x, y, z, 1, s, sg);
+        odd_load_face<D, S, IX>(G, P, fn, gn, x, y, z, O, s, sg);
     }
     R fbx = 0, fby = 0, fbz = 0, qb = 0;
     if (flags[((long long)z * G.ny + y) * G.ntx + (x >> 5)]) {
@@ -330,10 +308,8 @@ __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) 
         for (int i = 0; i < L::Q; i++) fn[O.dst[i]] = Store<S>::stf(s[i]);
 #pragma unroll
         for (int k = 0; k < L::QG; k++) gn[O.dst[k]] = Store<S>::stg(sg[k]);
-    } else if (inner_yz) {
-        odd_store_xface<D, S, IX>(G, P, fn, gn, x, O, s, sg);
     } else {
-        store_node<D, S>(G, P, f, g, x, y, z, s, sg);
+        odd_store_face<D, S, IX>(G, P, fn, gn, x, y, z, O, s, sg);
     }
 }
 
