@@ -249,6 +249,47 @@ def test_full_size_sed3d_properties():
     assert d1["min_height"] < d0["min_height"]  # the spheres sink
 
 
+def test_full_size_sed3d384_parity():
+    """The headline workload at full size, in the bench's launch configuration:
+    384^3 D3Q19 + D3Q7 in FP32, 10 000 thermosensitive spheres d = 6 (random
+    initial temperatures, C_p = rho_p V_p), 10 DEM substeps in one 16-CTA
+    cluster of 625 particles per CTA (one thread per particle).  Contacts and
+    cells bit-exact at the generated positions; then three steps (both step
+    parities) against the oracle run on the same 56.6M nodes: rho, T and u
+    within the FP32 bar, F_B and Q_B within 1e-4, positions within 1e-6, particle
+    temperatures within 1e-6, the couplings' force within 1e-4 of its scale."""
+    import os
+    host_gb = os.sysconf("SC_PHYS_PAGES") * os.sysconf("SC_PAGE_SIZE") / 2 ** 30
+    if host_gb < 96:  # the FP64 oracle holds about 26 GB at this size
+        pytest.skip(f"the full-size oracle needs about 26 GB of host memory ({host_gb:.0f} GB here)")
+    heat_cap = 1.2 * 4.0 / 3.0 * np.pi * 27.0
+    case = W.sed3d(nx=384, ny=384, nz=384, n_p=10000, d=6.0, config_index=4, heat_cap=heat_cap, T_p_random=True)
+    sim = _sim(case)
+    X, R = case["particles"]["X"], case["particles"]["R"]
+    assert np.array_equal(sim.read_contacts(), oracle.point_contacts(X, R))
+    cells, nc = sim.read_cells()
+    oc, onc = oracle.point_cells(3, case["shape"], 0.0, X, R)
+    assert nc == onc and np.array_equal(cells, oc)
+    orc = oracle.Oracle(case)
+    sim.step(3)
+    orc.step(3)
+    errs = {}  # the fields (the populations alone would be 12 GB per side on the host)
+    for name in ("rho", "T", "ux", "uy", "uz", "FBz", "QB"):
+        errs[name] = rel_l2(sim.read_field(name), orc.field(name))
+    for name, e in errs.items():  # the coupling fields at the coupling's bar, as in the sedimentation tests
+        assert e < (1e-4 if name in ("FBz", "QB") else FIELD_RTOL), errs
+    ps, po = sim.read_particles(), orc.particles()
+    Fs, Fo = sim.read_particle_forces(), orc.particle_forces()
+    dX = np.max(np.abs(ps["X"] - po["X"]))
+    dT = np.max(np.abs(ps["T_p"] - po["T_p"]))
+    dF = np.max(np.abs(Fs["F"] - Fo["F"])) / np.max(np.abs(Fo["F"]))
+    print("full-size 384^3:", errs, "max |dX|", dX, "max |dT_p|", dT, "force", dF)
+    assert np.max(np.abs(po["X"] - X)) > 0.0  # the spheres moved
+    assert dX < POS_ATOL and dT < 1e-6 and dF < 1e-4
+    orc.close()
+    sim.close()
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_footprint_ownership_ties(dim):
     # Particles placed mirror-symmetrically about the node plane x = 13: nodes on
