@@ -142,8 +142,9 @@ pibm_status pibm_set_contact_law(pibm_ctx* ctx, int law, double E, double poisso
 
 /* Particles (host arrays, copied).  X, U, W: n*3; R, rho_p, T_p: n;
  * heat_cap: n or NULL (isothermal); fixed: n bytes or NULL (all free).
- * Radii in (0, 600] nodes (PIBM_ERR_ARG otherwise).  Requires every axis to be
- * walled when n > 0.  Resets the contact history, rebuilds the cell list and
+ * Radii in (0, 600] nodes (PIBM_ERR_ARG otherwise).  At most 10 240 particles
+ * (the DEM runs as one cluster of 16 CTAs of at most 640 particles each;
+ * PIBM_ERR_ARG beyond).  Requires every axis to be walled when n > 0.  Resets the contact history, rebuilds the cell list and
  * recomputes the coupling of the current time. */
 pibm_status pibm_set_particles(pibm_ctx* ctx, int n, const double* X, const double* U, const double* W,
                                const double* R, const double* rho_p, const double* T_p,
