@@ -356,7 +356,11 @@ pibm_status pibm_surrogate_train(pibm_ctx* ctx, const double* feat, const double
  * Jacobian only when sum_p |F_net,p - F_pibm,p| / sum_p |F_pibm,p| <= bound
  * for the current state, F_pibm the coupling's force (else the held PIBM load
  * alone, the plain method).  delta: secant step in standard deviations of
- * each velocity, spin and temperature feature.
+ * each velocity, spin and temperature feature (widened to two BF16 spacings
+ * of a feature far out in the tails).  A particle's J_FU or J_TW block that
+ * cannot be physical for an explicit substep (a positive diagonal entry, a
+ * row not diagonally dominant, or |J_aa| h >= 2 m with h the substep and m
+ * the mass or moment of inertia) is zeroed for that step.
  * on = 0 removes it.  A new particle set removes it. */
 pibm_status pibm_surrogate_enable(pibm_ctx* ctx, int on, double bound, double delta);
 /* [0] steps with the Jacobian applied, [1] steps that fell back, [2] the last relative force error. */

@@ -51,12 +51,15 @@ features are taken against that fluid.  Definitions (lattice units):
               output weights W4 zero; then every parameter by Adam on the
               mean squared standardised error
   Jacobian    secant over delta standard deviations of each of the six
-              velocity / spin features and of the temperature feature:
+              velocity / spin features and of the temperature feature (in the
+              BF16 inference, delta is widened to two BF16 spacings of the
+              feature and the secant divides by the BF16 inputs' difference):
               J_FU[a][b] = dF_a / dU_b, J_TW[a][b] = dtau_a / domega_b of the
               coupling and J_HT = dH / dT_p; the DEM holds the mean of the
               couplings of t and t-1 and a change of the particle's state
               enters only the newer one, so it applies half of each
-              (applied_jacobian); 19 values per particle
+              (applied_jacobian); a block that cannot be physical for an
+              explicit substep is zeroed (admissible); 19 values per particle
   gate        e = sum_p |F_mlp,p - F_pibm,p| / sum_p |F_pibm,p|; the
               Jacobian is applied in the next step only when e <= bound
 """
@@ -290,25 +293,68 @@ def forward_bf16(params, Xn):
 ROWS = 8  # rows per particle in the Jacobian: the state, six velocity / spin and one temperature perturbation
 
 
+def secant_steps(Xn, delta):
+    """The secant step of each standardised feature: delta, widened to two BF16
+    spacings of the feature's value where that is larger (the network takes its
+    inputs in BF16, and a smaller step would vanish for features far out in the
+    tails).  Computed in FP32, as the device does."""
+    x = np.asarray(Xn, dtype=np.float32)
+    _, e = np.frexp(x)                                   # |x| in [2^(e-1), 2^e)
+    two_spacings = np.ldexp(np.float32(1.0), e - 7).astype(np.float32)
+    return np.where(x == 0, np.float32(delta), np.maximum(np.float32(delta), two_spacings)).astype(np.float32)
+
+
 def jacobian(params, xmu, xsd, ymu, ysd, Xraw, delta=0.25, infer=forward):
     """Secant Jacobian of (F, tau) in (U, omega) and of H in T_p, and the value
     row.  Returns (Y (n, 7) de-standardised, J (n, 19): J_FU row-major, J_TW
-    row-major, J_HT)."""
+    row-major, J_HT).  With infer=forward_bf16 (the tensor-core arithmetic) the
+    rows are formed in FP32, the steps widened by secant_steps, and each secant
+    divided by the difference of its two BF16 inputs, as on the device."""
+    bf16 = infer is forward_bf16
     Xn = (Xraw - xmu) / xsd
+    if bf16:
+        Xn = Xn.astype(np.float32)
     n = Xn.shape[0]
     rows = np.repeat(Xn, ROWS, axis=0)
+    step = secant_steps(Xn, delta) if bf16 else np.full(Xn.shape, delta)
     for j in range(7):
-        rows[j + 1::ROWS, j] += delta
-    Yn = infer(params, rows) if infer is not forward else forward(params, rows)[-1]
+        rows[j + 1::ROWS, j] = (rows[j + 1::ROWS, j] + step[:, j]).astype(rows.dtype)
+    Yn = infer(params, rows.astype(np.float64)) if infer is not forward else forward(params, rows)[-1]
     Y = Yn * ysd + ymu
     Y = Y.reshape(n, ROWS, N_OUT)
     base = Y[:, 0, :]
+    if bf16:
+        x32 = Xn[:, :7].astype(np.float32)
+        dq = (to_bf16((x32 + step[:, :7]).astype(np.float32)) - to_bf16(x32)) * np.asarray(xsd[:7])
+    else:
+        dq = np.broadcast_to(delta * np.asarray(xsd[:7]), (n, 7))
     J = np.zeros((n, 19))
     for b in range(3):
-        J[:, b:9:3] = (Y[:, 1 + b, 0:3] - base[:, 0:3]) / (delta * xsd[b])
-        J[:, 9 + b:18:3] = (Y[:, 4 + b, 3:6] - base[:, 3:6]) / (delta * xsd[3 + b])
-    J[:, 18] = (Y[:, 7, 6] - base[:, 6]) / (delta * xsd[6])
+        J[:, b:9:3] = (Y[:, 1 + b, 0:3] - base[:, 0:3]) / dq[:, b:b + 1]
+        J[:, 9 + b:18:3] = (Y[:, 4 + b, 3:6] - base[:, 3:6]) / dq[:, 3 + b:4 + b]
+    J[:, 18] = (Y[:, 7, 6] - base[:, 6]) / dq[:, 6]
     return base, J
+
+
+def admissible(J, mass, inertia, h, dim):
+    """Zero each Jacobian block (J_FU, J_TW; the axes that can move: x, y for
+    J_FU and z for J_TW in 2-D) that cannot be physical for an explicit substep:
+    a diagonal entry above 0, a row not diagonally dominant (then an eigenvalue
+    could have a positive real part), or |J_aa| h >= 2 m, m the mass (or the
+    moment of inertia), beyond which the substep kick is unstable."""
+    J = np.array(J, dtype=np.float64)
+    for p in range(J.shape[0]):
+        for off, lo, hi, m in ((0, 0, 2 if dim == 3 else 1, mass[p]), (9, 0 if dim == 3 else 2, 2, inertia[p])):
+            B = J[p, off:off + 9].reshape(3, 3)
+            ok = True
+            for a in range(lo, hi + 1):
+                d = B[a, a]
+                rest = sum(abs(B[a, b]) for b in range(lo, hi + 1) if b != a)
+                if not (d <= 0) or not (rest <= -d) or not (-d * h < 2 * m):
+                    ok = False
+            if not ok:
+                J[p, off:off + 9] = 0.0
+    return J
 
 
 def applied_jacobian(J):

@@ -253,29 +253,67 @@ __global__ void __launch_bounds__(MLP_T) k_mlp_tc(const float* __restrict__ para
 }
 
 // --------------------------------------------------------- surrogate rows
+// The secant step of a standardised feature x: delta, widened to two BF16
+// spacings of x where that is larger, so that the network (which takes its
+// inputs in BF16) sees a different input even for features far out in the
+// tails; the secant then divides by the difference of the two BF16 inputs.
+__device__ __forceinline__ float secant_step(float x, float delta) {
+    if (x == 0.f) return delta;
+    int e;
+    frexpf(x, &e);                       // |x| in [2^(e-1), 2^e): BF16 spacing 2^(e-8)
+    return fmaxf(delta, ldexpf(1.f, e - 7));
+}
+__device__ __forceinline__ float bf16_value(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+__device__ __forceinline__ float standardised(const double* feat, const float* norm, int p, int k) {
+    return (float)((feat[12 * (long long)p + k] - (double)norm[k]) / (double)norm[NF + k]);
+}
+
 // Per particle SG_ROWS = 8 rows: the standardised features, then the same with
-// delta added to each of the six velocity / spin features and to the
+// the secant step added to each of the six velocity / spin features and to the
 // temperature feature.
 __global__ void k_sg_rows(int n, const double* __restrict__ feat, const float* __restrict__ norm, float delta,
                           float* __restrict__ rows) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     float x[NF];
-    for (int k = 0; k < NF; k++) x[k] = (float)((feat[12 * (long long)p + k] - (double)norm[k]) / (double)norm[NF + k]);
+    for (int k = 0; k < NF; k++) x[k] = standardised(feat, norm, p, k);
     for (int j = 0; j < SG_ROWS; j++) {
         float* r = rows + (SG_ROWS * (long long)p + j) * 16;
-        for (int k = 0; k < 16; k++) r[k] = k < NF ? x[k] + (j > 0 && k == j - 1 ? delta : 0.f) : 0.f;
+        for (int k = 0; k < 16; k++) r[k] = k < NF ? x[k] + (j > 0 && k == j - 1 ? secant_step(x[k], delta) : 0.f) : 0.f;
     }
 }
 
-// Jacobian and gate partial sums: J_FU[a][b] = (F_a(row 1+b) - F_a(row 0)) / (delta sd_x[b]),
-// J_TW[a][b] = (tau_a(row 4+b) - tau_a(row 0)) / (delta sd_x[3+b]), J_HT = (H(row 7) -
-// H(row 0)) / (delta sd_x[6]), each halved (the applied share); partial sums of
-// |F_mlp - F_pibm| and |F_pibm| per block.
+// A Jacobian block (row-major 3x3, the axes lo..hi that can move) is applied
+// only if it can be physical for an explicit substep: every diagonal entry
+// <= 0, every row diagonally dominant (so every eigenvalue has a non-positive
+// real part), and |J_aa| h < 2 m (the substep kick stays stable; m the mass, or
+// the moment of inertia for J_TW).  Otherwise the block is zeroed: that
+// particle keeps the plain held load for that block.
+__device__ __forceinline__ bool admissible(const float* B, int lo, int hi, double mass, double h) {
+    for (int a = lo; a <= hi; a++) {
+        const float d = B[4 * a];
+        if (!(d <= 0.f)) return false;  // positive or not a number
+        float off = 0.f;
+        for (int b = lo; b <= hi; b++)
+            if (b != a) off += fabsf(B[3 * a + b]);
+        if (!(off <= -d)) return false;
+        if (!(-(double)d * h < 2.0 * mass)) return false;
+    }
+    return true;
+}
+
+// Jacobian and gate partial sums: J_FU[a][b] = (F_a(row 1+b) - F_a(row 0)) / (dq_b sd_x[b]),
+// J_TW[a][b] = (tau_a(row 4+b) - tau_a(row 0)) / (dq_{3+b} sd_x[3+b]), J_HT = (H(row 7) -
+// H(row 0)) / (dq_6 sd_x[6]), dq_j the difference of the BF16 inputs of the secant,
+// each halved (the applied share) and each block checked for admissibility; partial
+// sums of |F_mlp - F_pibm| and |F_pibm| per block.
 constexpr int GATE_T = 256;
-__global__ void __launch_bounds__(GATE_T) k_sg_jacobian(int n, const float* __restrict__ yrows, const float* __restrict__ norm,
-                                                        float delta, const double* __restrict__ Fh, float* __restrict__ J,
-                                                        double* __restrict__ part) {
+__global__ void __launch_bounds__(GATE_T) k_sg_jacobian(int n, int dim, const double* __restrict__ feat,
+                                                        const float* __restrict__ yrows, const float* __restrict__ norm,
+                                                        float delta, const double* __restrict__ Fh,
+                                                        const double* __restrict__ mass, const double* __restrict__ inertia,
+                                                        double h, float* __restrict__ J, double* __restrict__ part) {
     __shared__ double s0[GATE_T], s1[GATE_T];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     double e = 0.0, f = 0.0;
@@ -286,16 +324,26 @@ __global__ void __launch_bounds__(GATE_T) k_sg_jacobian(int n, const float* __re
         float Y[SG_ROWS][NO];
         for (int j = 0; j < SG_ROWS; j++)
             for (int k = 0; k < NO; k++) Y[j][k] = yrows[(SG_ROWS * (long long)p + j) * 8 + k] * ysd[k] + ymu[k];
+        float dx[7];  // the secant's input differences in raw units
+        for (int j = 0; j < 7; j++) {
+            const float x = standardised(feat, norm, p, j);
+            dx[j] = (bf16_value(x + secant_step(x, delta)) - bf16_value(x)) * xsd[j];
+        }
         // The DEM holds the mean of the couplings of t and t-1; a change of the
         // particle's state enters only the newer of the two, so the held load's
         // sensitivity is half the coupling's: J = (1/2) secant of the network.
         float* Jp = J + SG_NJ * (long long)p;
         for (int a = 0; a < 3; a++)
             for (int b = 0; b < 3; b++) {
-                Jp[3 * a + b] = 0.5f * (Y[1 + b][a] - Y[0][a]) / (delta * xsd[b]);
-                Jp[9 + 3 * a + b] = 0.5f * (Y[4 + b][3 + a] - Y[0][3 + a]) / (delta * xsd[3 + b]);
+                Jp[3 * a + b] = 0.5f * (Y[1 + b][a] - Y[0][a]) / dx[b];
+                Jp[9 + 3 * a + b] = 0.5f * (Y[4 + b][3 + a] - Y[0][3 + a]) / dx[3 + b];
             }
-        Jp[18] = 0.5f * (Y[7][6] - Y[0][6]) / (delta * xsd[6]);
+        Jp[18] = 0.5f * (Y[7][6] - Y[0][6]) / dx[6];
+        const bool three = dim == 3;
+        if (!admissible(Jp, 0, three ? 2 : 1, mass[p], h))
+            for (int k = 0; k < 9; k++) Jp[k] = 0.f;
+        if (!admissible(Jp + 9, three ? 0 : 2, 2, inertia[p], h))
+            for (int k = 9; k < 18; k++) Jp[k] = 0.f;
         double d2 = 0.0, f2 = 0.0;
         for (int a = 0; a < 3; a++) {
             const double fp = Fh[3 * (long long)p + a];
@@ -561,7 +609,8 @@ cudaError_t launch_surrogate(Ctx* c, cudaStream_t s, int parity, bool need_sums)
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_mlp(c, s, c->sg.rows, SG_ROWS * c->np, c->sg.yrows)) != cudaSuccess) return e;
     const int nb = (c->np + GATE_T - 1) / GATE_T;
-    k_sg_jacobian<<<nb, GATE_T, 0, s>>>(c->np, c->sg.yrows, c->sg.norm, (float)c->sg.delta, c->Fh, c->sg.J, c->sg.part);
+    k_sg_jacobian<<<nb, GATE_T, 0, s>>>(c->np, c->D == 2 ? 2 : 3, c->sg.feat, c->sg.yrows, c->sg.norm, (float)c->sg.delta,
+                                        c->Fh, c->m, c->I, c->dem.dt, c->sg.J, c->sg.part);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_sg_gate<<<1, 32, 0, s>>>(nb, c->sg.part, c->sg.bound, c->sg.err, c->sg.J_on, c->sg.stats);
     return cudaGetLastError();

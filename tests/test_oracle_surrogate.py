@@ -267,3 +267,38 @@ def test_closed_form_jacobian_stabilises_light_spheres():
         J[q, 9:18] = (-M).ravel()
     umax = run(J, 200)
     assert umax is not None and umax < 0.02
+
+
+def test_secant_steps_survive_bf16_inputs():
+    # near 0 the step is delta; far out in the tails it widens to two BF16
+    # spacings, so the two BF16 inputs of the secant always differ
+    x = np.array([0.0, 0.3, -1.7, 40.0, 100.0, -3000.0], dtype=np.float32)
+    st = S.secant_steps(x, 0.25)
+    assert st[0] == 0.25 and st[1] == 0.25 and st[2] == 0.25
+    assert st[4] == 1.0  # 100 lies in [64, 128): BF16 spacing 0.5
+    dq = S.to_bf16(x + st) - S.to_bf16(x)
+    assert np.all(dq > 0) and np.all(dq <= 4 * st)
+    # the plain step would vanish out there
+    assert S.to_bf16(np.float32(100.0) + np.float32(0.25)) == S.to_bf16(np.float32(100.0))
+
+
+def test_admissible_jacobian_blocks():
+    m, I, h = np.array([10.0] * 5), np.array([4.0] * 5), 0.1
+    J = np.zeros((5, 19))
+    phys = -3.0 * np.eye(3) + 0.2 * (np.ones((3, 3)) - np.eye(3))
+    for p in range(5):
+        J[p, 0:9] = phys.ravel()
+        J[p, 9:18] = (-2.0 * np.eye(3)).ravel()
+    J[1, 4] = 0.5                 # a positive diagonal entry
+    J[2, 1] = 5.0                 # a row no longer diagonally dominant
+    J[3, 9:18] = (-100.0 * np.eye(3)).ravel()  # |J| h = 10 >= 2 I: an unstable substep
+    A = S.admissible(J, m, I, h, 3)
+    assert np.array_equal(A[0], J[0])
+    assert not np.any(A[1, 0:9]) and np.array_equal(A[1, 9:18], J[1, 9:18])
+    assert not np.any(A[2, 0:9])
+    assert np.array_equal(A[3, 0:9], J[3, 0:9]) and not np.any(A[3, 9:18])
+    # 2-D: only x, y of J_FU and z of J_TW can move; a bad z row of J_FU is ignored
+    J2 = J[:1].copy()
+    J2[0, 8] = 7.0
+    assert np.array_equal(S.admissible(J2, m, I, h, 2), J2)
+    assert not np.any(S.admissible(J2, m, I, h, 3)[0, 0:9])
