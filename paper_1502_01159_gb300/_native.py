@@ -296,8 +296,13 @@ class Simulation:
         return dict(zip(["stream_collide", "dem", "coupling", "step"], ms.tolist()))
 
     # ------------------------------------------------------------ read-back
-    def read_field(self, name: str) -> np.ndarray:
-        out = np.empty(self.N)
+    def read_field(self, name: str, out=None) -> np.ndarray:
+        """The field as (nz, ny, nx) FP64; out: optional C-contiguous float64 array
+        of N elements to receive it (for instance in pinned host memory)."""
+        if out is None:
+            out = np.empty(self.N)
+        elif out.dtype != np.float64 or out.size != self.N or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a C-contiguous float64 array of N elements")
         self._check(self.L.pibm_read_field(self.h, FIELDS[name], _dp(out), self.N), "pibm_read_field")
         return out.reshape(self.shape)
 
@@ -307,11 +312,19 @@ class Simulation:
         self._check(self.L.pibm_read_populations(self.h, _dp(f), _dp(g)), "pibm_read_populations")
         return f.reshape((self.Q,) + self.shape), g.reshape((self.QG,) + self.shape)
 
-    def read_particles(self):
+    def read_particles(self, out=None):
+        """Positions, velocities, spins (n x 3) and temperatures (n); out: optional
+        dict of C-contiguous float64 arrays of those shapes to receive them."""
         n = self.np
-        X, U, W, T = np.empty((n, 3)), np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
-        self._check(self.L.pibm_read_particles(self.h, _dp(X), _dp(U), _dp(W), _dp(T)), "pibm_read_particles")
-        return {"X": X, "U": U, "W": W, "T_p": T}
+        if out is None:
+            out = {"X": np.empty((n, 3)), "U": np.empty((n, 3)), "W": np.empty((n, 3)), "T_p": np.empty(n)}
+        for k, shape in (("X", (n, 3)), ("U", (n, 3)), ("W", (n, 3)), ("T_p", (n,))):
+            a = out[k]
+            if a.dtype != np.float64 or a.shape != shape or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"out[{k!r}] must be a C-contiguous float64 array of shape {shape}")
+        self._check(self.L.pibm_read_particles(self.h, _dp(out["X"]), _dp(out["U"]), _dp(out["W"]), _dp(out["T_p"])),
+                    "pibm_read_particles")
+        return out
 
     def read_particle_forces(self):
         n = self.np
