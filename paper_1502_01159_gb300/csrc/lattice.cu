@@ -712,20 +712,23 @@ __global__ void k_neighbour_merge(int n, int nslice, const double* __restrict__ 
     for (int k = 0; k < 4; k++) out_p[8 + k] = best[k] < cap ? best[k] : cap;
 }
 
-// Features 7-11 from the DEM's cell list instead of all pairs: one thread per
+// Features 7-11 from the DEM's cell list instead of all pairs: one warp per
 // particle scans the cells that can hold a particle within the feature range
 // max(4 R_p, 3 R_p + R_max) of it, widened by half the neighbour skin (the list
 // was built where the particles stood at the last rebuild, and none has moved
-// more than that since).  The pair test is the all-pairs kernel's (FP32 prefilter,
-// exact FP64 distance), so the same neighbours are found; phi sums them in cell
-// order instead of index order (last-bit differences), the four smallest gaps are
-// the same.
+// more than that since).  The cells of an x-row are consecutive in the sorted
+// list, so each lane takes whole rows (one id range each); the pair test is the
+// all-pairs kernel's (FP32 prefilter, exact FP64 distance), so the same
+// neighbours are found.  phi is summed per lane, then over the lanes in a fixed
+// butterfly (last-bit differences from index order); the four smallest gaps are
+// merged across the lanes exactly.
 template <int D>
 __global__ void k_neighbour_cells(int n, const double* __restrict__ X, const double* __restrict__ R,
                                   const float4* __restrict__ xr, const int* __restrict__ cell_start,
                                   const int* __restrict__ cell_ids, DemCfg C, double rmax, double* __restrict__ out) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
+    const int p = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (p >= n) return;  // whole warps: p is uniform across the warp
     const float4 me = xr[p];
     const double xp = X[3 * p], yp = X[3 * p + 1], zp = X[3 * p + 2], Rp = R[p];
     const double Lr = fmax(4.0 * Rp, 3.0 * Rp + rmax) + 0.01 + 0.5 * C.skin + 1e-6;
@@ -741,42 +744,56 @@ __global__ void k_neighbour_cells(int n, const double* __restrict__ X, const dou
             clo[a] = chi[a] = 0;
         }
     }
+    const int ny_rows = chi[1] - clo[1] + 1, nrows = (chi[2] - clo[2] + 1) * ny_rows;
     double phi = 0.0;
     double gd4[4] = {1e300, 1e300, 1e300, 1e300};
-    for (int cz = clo[2]; cz <= chi[2]; cz++)
-        for (int cy = clo[1]; cy <= chi[1]; cy++) {
-            // the cells of an x-row are consecutive in the sorted list: one range per row
-            const int row = (cz * C.nc[1] + cy) * C.nc[0];
-            const int b = cell_start[row + clo[0]], e = cell_start[row + chi[0] + 1];
-            {
-                for (int k = b; k < e; k++) {
-                    const int q = cell_ids[k];
-                    if (q == p) continue;
-                    const float4 o = xr[q];
-                    const float fx = o.x - me.x, fy = o.y - me.y, fz = o.z - me.z;
-                    const float lim = fmaxf(4.f * me.w, 3.f * me.w + o.w) + 0.01f;
-                    if (fx * fx + fy * fy + fz * fz >= lim * lim) continue;
-                    const double ex = X[3 * q] - xp, ey = X[3 * q + 1] - yp, ez = X[3 * q + 2] - zp;
-                    const double dist = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
-                    const double Rq = R[q];
-                    if (dist < 4.0 * Rp) {
-                        const double sr = Rq / (4.0 * Rp);
-                        phi += Lat<D>::dim == 3 ? sr * sr * sr : sr * sr;
-                    }
-                    double gap = (dist - Rp) - Rq;
-                    for (int j = 0; j < 4; j++)  // insert into the sorted four
-                        if (gap < gd4[j]) {
-                            const double tt = gd4[j];
-                            gd4[j] = gap;
-                            gap = tt;
-                        }
-                }
+    for (int r = lane; r < nrows; r += 32) {
+        const int cz = clo[2] + r / ny_rows, cy = clo[1] + r % ny_rows;
+        const int row = (cz * C.nc[1] + cy) * C.nc[0];
+        const int b = cell_start[row + clo[0]], e = cell_start[row + chi[0] + 1];
+        for (int k = b; k < e; k++) {
+            const int q = cell_ids[k];
+            if (q == p) continue;
+            const float4 o = xr[q];
+            const float fx = o.x - me.x, fy = o.y - me.y, fz = o.z - me.z;
+            const float lim = fmaxf(4.f * me.w, 3.f * me.w + o.w) + 0.01f;
+            if (fx * fx + fy * fy + fz * fz >= lim * lim) continue;
+            const double ex = X[3 * q] - xp, ey = X[3 * q + 1] - yp, ez = X[3 * q + 2] - zp;
+            const double dist = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
+            const double Rq = R[q];
+            if (dist < 4.0 * Rp) {
+                const double sr = Rq / (4.0 * Rp);
+                phi += Lat<D>::dim == 3 ? sr * sr * sr : sr * sr;
             }
+            double gap = (dist - Rp) - Rq;
+            for (int j = 0; j < 4; j++)  // insert into the sorted four
+                if (gap < gd4[j]) {
+                    const double tt = gd4[j];
+                    gd4[j] = gap;
+                    gap = tt;
+                }
         }
-    double* out_p = out + 12 * (long long)p;
-    out_p[7] = phi;
-    const double cap = 2.0 * Rp;
-    for (int k = 0; k < 4; k++) out_p[8 + k] = gd4[k] < cap ? gd4[k] : cap;
+    }
+    // across the warp: phi by a butterfly sum, the four smallest gaps by merging
+    // the two sorted fours of each pair of lanes (every lane ends with the result)
+    for (int o = 16; o > 0; o >>= 1) {
+        phi += __shfl_xor_sync(0xffffffffu, phi, o);
+        double other[4];
+        for (int j = 0; j < 4; j++) other[j] = __shfl_xor_sync(0xffffffffu, gd4[j], o);
+        double merged[4];
+        int ia = 0, ib = 0;
+        for (int j = 0; j < 4; j++) {
+            if (gd4[ia] <= other[ib]) merged[j] = gd4[ia++];
+            else merged[j] = other[ib++];
+        }
+        for (int j = 0; j < 4; j++) gd4[j] = merged[j];
+    }
+    if (lane == 0) {
+        double* out_p = out + 12 * (long long)p;
+        out_p[7] = phi;
+        const double cap = 2.0 * Rp;
+        for (int k = 0; k < 4; k++) out_p[8 + k] = gd4[k] < cap ? gd4[k] : cap;
+    }
 }
 
 __global__ void k_pos_f32(int n, const double* X, const double* R, float4* xr) {
@@ -795,7 +812,7 @@ static cudaError_t features_launch(Ctx* c, cudaStream_t s, int parity, double* o
         bool cells = c->dem.ncell > 1;
         for (int a = 0; a < Lat<D>::dim; a++) cells = cells && L * c->dem.inv[a] < 3.5;
         if (cells) {
-            k_neighbour_cells<D><<<(c->np + 127) / 128, 128, 0, s>>>(c->np, c->X, c->R, c->sg.xr, c->cell_start,
+            k_neighbour_cells<D><<<(int)(((long long)c->np * 32 + 127) / 128), 128, 0, s>>>(c->np, c->X, c->R, c->sg.xr, c->cell_start,
                                                                      c->cell_ids, c->dem, c->rmax, out);
             return cudaGetLastError();
         }
