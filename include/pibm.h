@@ -135,7 +135,8 @@ pibm_status pibm_set_wall(pibm_ctx* ctx, int face, int kind, int thermal, double
  * Thornton and Yin for loading (k = 0), unloading (1) and reloading (2) along
  * the contact's reference direction, T* / T** the turning points; its history
  * is evaluated and kept in FP64 (theta_k is a cube root that is not Lipschitz
- * at full slip).  SPRING_DASHPOT: F_n = kn d + gamma_n v_n, stiffness kt.  All: tangential
+ * at full slip).  Switching to HERTZ_MD_HIST with particles in place starts
+ * every contact's tangential force and history afresh.  SPRING_DASHPOT: F_n = kn d + gamma_n v_n, stiffness kt.  All: tangential
  * force capped at mu |F_n|, tangential damping gamma_t. */
 pibm_status pibm_set_contact_law(pibm_ctx* ctx, int law, double E, double poisson, double mu,
                                  double kn, double kt, double gamma_n, double gamma_t);

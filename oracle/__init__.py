@@ -168,6 +168,10 @@ class Oracle:
 
     __del__ = close
 
+    def set_contact_law(self, law, E, poisson, mu, kn, kt, gamma_n, gamma_t):
+        self.L.orc_set_contact_law(self.h, int(law), float(E), float(poisson), float(mu), float(kn), float(kt),
+                                   float(gamma_n), float(gamma_t))
+
     def set_particles(self, parts: dict):
         X = _f64(parts["X"], (-1, 3))
         n = X.shape[0]

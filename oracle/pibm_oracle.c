@@ -1018,6 +1018,17 @@ int orc_set_wall(orc_sim* s, int face, int kind, int thermal, double T_w) {
 
 int orc_set_contact_law(orc_sim* s, int law, double E, double poisson, double mu, double kn, double kt,
                         double gamma_n, double gamma_t) {
+    /* entering the loading-history law: the other laws keep no such history, so
+     * every contact's tangential force and history start afresh (its next update
+     * is its first) */
+    if (law == ORC_HERTZ_MD_HIST && s->law != ORC_HERTZ_MD_HIST) {
+        for (int k = 0; k < s->ncont; k++) {
+            memset(&s->cont[k].md, 0, sizeof(md_state));
+            s->cont[k].ft[0] = s->cont[k].ft[1] = s->cont[k].ft[2] = 0.0;
+        }
+        if (s->wall_md) memset(s->wall_md, 0, sizeof(md_state) * 6 * (size_t)s->np);
+        if (s->wall_ft) memset(s->wall_ft, 0, sizeof(double) * 18 * (size_t)s->np);
+    }
     s->law = law;
     s->E = E;
     s->pois = poisson;

@@ -399,6 +399,14 @@ pibm_status pibm_set_contact_law(pibm_ctx* ctx, int law, double E, double poisso
     if ((law != PIBM_SPRING_DASHPOT && !hertz) || mu < 0 || (hertz && !(E > 0)) ||
         (hertz && !(poisson > -1 && poisson < 1)) || (law == PIBM_SPRING_DASHPOT && !(kn >= 0)))
         return fail(ctx, PIBM_ERR_ARG, "invalid contact law");
+    // entering the loading-history law with particles in place: its FP64 records
+    // were not kept by the other laws, so every contact's history starts afresh
+    // (a contact's next update is then its first)
+    if (law == PIBM_HERTZ_MD_HIST && c.dem.law != PIBM_HERTZ_MD_HIST && c.np > 0) {
+        for (int b = 0; b < 2; b++)
+            PCHECK(cudaMemsetAsync(c.nb_md[b], 0, sizeof(double) * 2 * MD_REC * c.dem.cap, c.s0));
+        PCHECK(cudaMemsetAsync(c.wall_md, 0, sizeof(double) * 6 * MD_REC * (c.np + 1), c.s0));
+    }
     c.dem.law = law;
     // text after Eq demgov: 1/E* = (1 - nu^2)/E_1 + (1 - nu^2)/E_2, same for G*; equal materials
     double Estar = hertz ? E / (2.0 * (1.0 - poisson * poisson)) : 0.0;

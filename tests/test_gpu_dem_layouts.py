@@ -152,6 +152,30 @@ def test_dense_pile_mindlin_deresiewicz_history_state(pile_history_reference, pe
     assert abs(got["nc"] - ref["nc"]) <= 0.02 * ref["nc"]
 
 
+def test_law_switches_match_oracle():
+    """Contact law 1 -> 2 -> 1 -> 2 on the colliding gas, 40 steps each:
+    entering the loading-history law with contacts in place starts every
+    contact's tangential force and history afresh, on both sides, so the
+    trajectories agree element by element (positions and spins within 1e-6)."""
+    from paper_1502_01159_gb300 import Simulation
+    case = W.colliding_gas(law=1)
+    law = dict(case["contact"])
+    args = lambda l: (l, law["E"], law["poisson"], law["mu"], law["kn"], law["kt"], law["gamma_n"], law["gamma_t"])
+    sim, orc = Simulation(case), oracle.Oracle(case)
+    for l in (1, 2, 1, 2):
+        sim.set_contact_law(*args(l))
+        orc.set_contact_law(*args(l))
+        sim.step(40)
+        orc.step(40)
+        assert np.array_equal(sim.read_contacts(), orc.contacts())
+    ps, po = sim.read_particles(), orc.particles()
+    dX, dW = np.max(np.abs(ps["X"] - po["X"])), np.max(np.abs(ps["W"] - po["W"]))
+    print("law switches: max |dX| %.3g, max |dW| %.3g" % (dX, dW))
+    assert dX < POS_ATOL and dW < 1e-6
+    sim.close()
+    orc.close()
+
+
 def test_history_checkpoint_resume_bit_exact(tmp_path):
     """Law 2 on the dense pile: 30 steps, save, 30 more; a fresh context loaded
     from the checkpoint and stepped 30 times reaches the same bits.  The pile

@@ -249,6 +249,27 @@ def test_full_size_sed3d_properties():
     assert d1["min_height"] < d0["min_height"]  # the spheres sink
 
 
+def test_read_back_into_caller_buffers():
+    # read_field / read_particles into caller-provided arrays (for instance pinned
+    # host memory) give the same values as the allocating form
+    import torch
+    case = _small_sed3d()
+    sim = _sim(case)
+    sim.step(3)
+    buf = torch.empty(sim.N, dtype=torch.float64, pin_memory=True).numpy()
+    T = sim.read_field("T", out=buf)
+    assert np.shares_memory(T, buf) and np.array_equal(T, sim.read_field("T"))
+    n = sim.np
+    out = {k: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+           for k, shape in (("X", (n, 3)), ("U", (n, 3)), ("W", (n, 3)), ("T_p", (n,)))}
+    p = sim.read_particles(out=out)
+    q = sim.read_particles()
+    assert all(np.array_equal(p[k], q[k]) and np.shares_memory(p[k], out[k]) for k in q)
+    with pytest.raises(ValueError):
+        sim.read_field("T", out=np.empty(3))
+    sim.close()
+
+
 def test_full_size_sed3d384_parity():
     """The headline workload at full size, in the bench's launch configuration:
     384^3 D3Q19 + D3Q7 in FP32, 10 000 thermosensitive spheres d = 6 (random
