@@ -1125,8 +1125,9 @@ static pibm_status sg_ensure(pibm_ctx* ctx) {
         c.sg.J_on = (int*)dalloc(ctx, sizeof(int) * 2, GRP_SURROGATE);
         c.sg.err = (int*)dalloc(ctx, sizeof(int) * 2, GRP_SURROGATE);
         c.sg.stats = (double*)dalloc(ctx, sizeof(double) * 4, GRP_SURROGATE);
+        c.sg.wimg = (unsigned char*)dalloc(ctx, mlp_image_bytes(), GRP_SURROGATE);
         if (!c.sg.params || !c.sg.m || !c.sg.v || !c.sg.norm || !c.sg.partial || !c.sg.lossp || !c.sg.J_on ||
-            !c.sg.err || !c.sg.stats) {
+            !c.sg.err || !c.sg.stats || !c.sg.wimg) {
             c.sg.params = nullptr;
             return fail(ctx, PIBM_ERR_OOM, "surrogate buffers");
         }
@@ -1177,6 +1178,7 @@ pibm_status pibm_surrogate_set_params(pibm_ctx* ctx, const float* params, const 
     PCHECK(cudaMemcpyAsync(c.sg.norm, norm, sizeof(float) * (2 * SG_NFEAT + 2 * SG_NOUT), cudaMemcpyHostToDevice, c.s0));
     PCHECK(cudaMemsetAsync(c.sg.m, 0, sizeof(float) * SG_NPARAMS, c.s0));
     PCHECK(cudaMemsetAsync(c.sg.v, 0, sizeof(float) * SG_NPARAMS, c.s0));
+    PCHECK(launch_mlp_image(&c, c.s0));
     PCHECK(cudaStreamSynchronize(c.s0));
     c.sg.adam_t = 0;
     c.sg.trained = 1;
@@ -1308,6 +1310,8 @@ pibm_status pibm_surrogate_train(pibm_ctx* ctx, const double* feat, const double
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.s0);
     if (e == cudaSuccess && lsq_bad) {
         dfree_group(ctx, GRP_SCRATCH);
+        if (launch_mlp_image(&c, c.s0) != cudaSuccess || cudaStreamSynchronize(c.s0) != cudaSuccess)
+            return fail(ctx, PIBM_ERR_CUDA, "inference weight image");
         return fail(ctx, PIBM_ERR_STATE, "least-squares fit of the linear path is singular");
     }
     std::vector<int> idx((size_t)n);
@@ -1330,6 +1334,7 @@ pibm_status pibm_surrogate_train(pibm_ctx* ctx, const double* feat, const double
         if (e == cudaSuccess) e = cudaStreamSynchronize(c.s0);
         if (loss_per_epoch) loss_per_epoch[ep] = nb > 0 ? loss_sum / (double)nb : 0.0;
     }
+    if (e == cudaSuccess) e = launch_mlp_image(&c, c.s0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.s0);
     dfree_group(ctx, GRP_SCRATCH);
     if (e != cudaSuccess) return fail(ctx, PIBM_ERR_CUDA, std::string("training: ") + cudaGetErrorString(e));

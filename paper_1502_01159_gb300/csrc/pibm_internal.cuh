@@ -260,6 +260,7 @@ constexpr int SG_TRAIN_BLOCKS = 152;
 constexpr int SG_NB_SLICES = 16;  // neighbour-feature slices of the particle set
 struct Surrogate {
     float *params, *m, *v, *norm;   // FP32 master parameters, Adam moments, standardisation (38)
+    unsigned char* wimg;             // BF16 weight image of the inference kernel (mlp_image_bytes())
     float *partial, *lossp;          // training reduction scratch
     int adam_t;
     int trained;                     // parameters set or trained
@@ -405,6 +406,8 @@ cudaError_t train_batch(Ctx* c, cudaStream_t s, const float* xb, const float* yb
                         double* loss_out);
 cudaError_t launch_gather(cudaStream_t s, int B, const int* idx, const float* X, const float* Y, float* xb, float* yb);
 size_t lsq_scratch_doubles();
+size_t mlp_image_bytes();
+cudaError_t launch_mlp_image(Ctx* c, cudaStream_t s);
 cudaError_t launch_lsq(Ctx* c, cudaStream_t s, const float* X, const float* Y, long long n, double ridge, double* part,
                        int* status);
 Ctx* ctx_state(pibm_ctx* ctx);

@@ -128,7 +128,45 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 // wait (at most wait_polls polls) gave up; the CTA then skips the rest of its
 // work, waits (with the default limit) for its own MMA still in flight, frees
 // its tensor memory and returns (err 2 if that drain also ran out).
-__global__ void __launch_bounds__(MLP_T) k_mlp_tc(const float* __restrict__ params, const float* __restrict__ in, int rows,
+// The weights and biases in the inference kernel's shared-memory layout (the
+// bytes from SM_W1 up to SM_BAR): BF16 weights in the core-matrix layout, FP32
+// biases.  Built by k_mlp_image whenever the parameters are written, copied by
+// every inference CTA with 16-byte loads.
+constexpr int MLP_IMG = SM_BAR - SM_W1;
+static_assert(MLP_IMG % 16 == 0 && SM_W1 % 16 == 0, "16-byte image copies");
+
+__global__ void __launch_bounds__(256) k_mlp_image(const float* __restrict__ params, unsigned char* __restrict__ img) {
+    unsigned char* const w = img - SM_W1;  // offsets below are the shared-memory ones
+    float* bias = reinterpret_cast<float*>(w + SM_BIAS);
+    for (int e = threadIdx.x; e < 64 * 16; e += blockDim.x) {
+        const int n = e >> 4, k = e & 15;
+        reinterpret_cast<__nv_bfloat16*>(w + SM_W1 + core_off(n, k, 256))[0] =
+            __float2bfloat16_rn(k < NF ? params[OFF_W1 + n * NF + k] : 0.f);
+    }
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+        const int n = e >> 6, k = e & 63;
+        reinterpret_cast<__nv_bfloat16*>(w + SM_W2 + core_off(n, k, 1024))[0] = __float2bfloat16_rn(params[OFF_W2 + e]);
+        reinterpret_cast<__nv_bfloat16*>(w + SM_W3 + core_off(n, k, 1024))[0] = __float2bfloat16_rn(params[OFF_W3 + e]);
+    }
+    for (int e = threadIdx.x; e < 16 * 64; e += blockDim.x) {
+        const int n = e >> 6, k = e & 63;
+        reinterpret_cast<__nv_bfloat16*>(w + SM_W4 + core_off(n, k, 1024))[0] =
+            __float2bfloat16_rn(n < NO ? params[OFF_W4 + n * HW + k] : 0.f);
+    }
+    for (int e = threadIdx.x; e < 16 * 16; e += blockDim.x) {
+        const int n = e >> 4, k = e & 15;
+        reinterpret_cast<__nv_bfloat16*>(w + SM_WS + core_off(n, k, 256))[0] =
+            __float2bfloat16_rn(n < NO && k < NF ? params[OFF_WS + n * NF + k] : 0.f);
+    }
+    for (int e = threadIdx.x; e < 64; e += blockDim.x) {
+        bias[e] = params[OFF_B1 + e];
+        bias[64 + e] = params[OFF_B2 + e];
+        bias[128 + e] = params[OFF_B3 + e];
+    }
+    if (threadIdx.x < 16) bias[192 + threadIdx.x] = threadIdx.x < NO ? params[OFF_B4 + threadIdx.x] : 0.f;
+}
+
+__global__ void __launch_bounds__(MLP_T) k_mlp_tc(const unsigned char* __restrict__ img, const float* __restrict__ in, int rows,
                                                   float* __restrict__ out, int* err, int wait_polls) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -138,33 +176,10 @@ __global__ void __launch_bounds__(MLP_T) k_mlp_tc(const float* __restrict__ para
     float* bias = reinterpret_cast<float*>(sm + SM_BIAS);
     const uint32_t bar = sbase + SM_BAR;
 
-    // weights -> BF16 core-matrix layout; biases; this tile's inputs
-    for (int e = tid; e < 64 * 16; e += MLP_T) {
-        const int n = e >> 4, k = e & 15;
-        reinterpret_cast<__nv_bfloat16*>(sm + SM_W1 + core_off(n, k, 256))[0] =
-            __float2bfloat16_rn(k < NF ? params[OFF_W1 + n * NF + k] : 0.f);
-    }
-    for (int e = tid; e < 64 * 64; e += MLP_T) {
-        const int n = e >> 6, k = e & 63;
-        reinterpret_cast<__nv_bfloat16*>(sm + SM_W2 + core_off(n, k, 1024))[0] = __float2bfloat16_rn(params[OFF_W2 + e]);
-        reinterpret_cast<__nv_bfloat16*>(sm + SM_W3 + core_off(n, k, 1024))[0] = __float2bfloat16_rn(params[OFF_W3 + e]);
-    }
-    for (int e = tid; e < 16 * 64; e += MLP_T) {
-        const int n = e >> 6, k = e & 63;
-        reinterpret_cast<__nv_bfloat16*>(sm + SM_W4 + core_off(n, k, 1024))[0] =
-            __float2bfloat16_rn(n < NO ? params[OFF_W4 + n * HW + k] : 0.f);
-    }
-    for (int e = tid; e < 16 * 16; e += MLP_T) {
-        const int n = e >> 4, k = e & 15;
-        reinterpret_cast<__nv_bfloat16*>(sm + SM_WS + core_off(n, k, 256))[0] =
-            __float2bfloat16_rn(n < NO && k < NF ? params[OFF_WS + n * NF + k] : 0.f);
-    }
-    for (int e = tid; e < 64; e += MLP_T) {
-        bias[e] = params[OFF_B1 + e];
-        bias[64 + e] = params[OFF_B2 + e];
-        bias[128 + e] = params[OFF_B3 + e];
-    }
-    if (tid < 16) bias[192 + tid] = tid < NO ? params[OFF_B4 + tid] : 0.f;
+    // the weight image (BF16 core-matrix weights, FP32 biases), then this tile's inputs
+#pragma unroll 4
+    for (int e = tid; e < MLP_IMG / 16; e += MLP_T)
+        reinterpret_cast<uint4*>(sm + SM_W1)[e] = __ldg(reinterpret_cast<const uint4*>(img) + e);
     {
         const int r = tid;  // one input row per thread
         const int gr = row0 + r;
@@ -595,7 +610,7 @@ cudaError_t launch_mlp(Ctx* c, cudaStream_t s, const float* in, int rows, float*
         attr = true;
     }
     if (rows <= 0) return cudaSuccess;
-    k_mlp_tc<<<(rows + MLP_M - 1) / MLP_M, MLP_T, MLP_SMEM, s>>>(c->sg.params, in, rows, out, c->sg.err, c->sg.wait_polls);
+    k_mlp_tc<<<(rows + MLP_M - 1) / MLP_M, MLP_T, MLP_SMEM, s>>>(c->sg.wimg, in, rows, out, c->sg.err, c->sg.wait_polls);
     return cudaGetLastError();
 }
 
@@ -617,6 +632,15 @@ cudaError_t launch_surrogate(Ctx* c, cudaStream_t s, int parity, bool need_sums)
 }
 
 int surrogate_kernel_count(Ctx* c) { return (c->sg.enabled && c->np > 0) ? 8 : 0; }
+
+size_t mlp_image_bytes() { return (size_t)MLP_IMG; }
+
+// Every write of the parameters (an upload, a training run) rebuilds the image
+// that the inference kernel copies; the step itself only reads it.
+cudaError_t launch_mlp_image(Ctx* c, cudaStream_t s) {
+    k_mlp_image<<<1, 256, 0, s>>>(c->sg.params, c->sg.wimg);
+    return cudaGetLastError();
+}
 
 // Gradient (and optionally an Adam step) of one batch already on the device.
 cudaError_t train_batch(Ctx* c, cudaStream_t s, const float* xb, const float* yb, int B, float lr, float* grad_out,
