@@ -239,7 +239,10 @@ pibm_status pibm_set_particle_model(pibm_ctx* ctx, int model);
  * no block straddles a row end with idle warps; 0 (default) = blocks span
  * min(256, row rounded up to 32) nodes.  Identical results either way.
  * PIBM_TUNE_LATTICE_THREADS: threads per block of the collide-and-stream
- * kernel, 0 (default shape) or a multiple of 32 in [32, 512]; a block spans
+ * kernel, 0 (default shape: 256 threads for rows of 256 or more nodes, 128
+ * for shorter rows and for FP16 / BF16 storage) or a multiple of 32 in
+ * [32, 512] (FP16 / BF16 storage: at most 384, larger values act as 384);
+ * a block spans
  * min(threads, row width rounded up to 32) nodes of a row (or the row-dividing
  * width above) and as many rows as the remaining factor gives.
  * PIBM_TUNE_WIDE_INDEX: 1 = 64-bit slot offsets in the collide-and-stream

@@ -164,6 +164,149 @@ __device__ __forceinline__ void collide_node(T* s, T* sg, T fbx, T fby, T fbz, T
     }
 }
 
+// The first non-zero component of e_i is positive: one direction of each
+// opposite pair (the other is opp(i)).
+template <int D>
+__host__ __device__ constexpr bool lead_positive(int i) {
+    using L = Lat<D>;
+    return L::ex(i) != 0 ? L::ex(i) > 0 : (L::ey(i) != 0 ? L::ey(i) > 0 : L::ez(i) > 0);
+}
+
+// The collision of the 16-bit storage forms, the same BGK update and Guo
+// forcing as collide_node, in the storage's own units (deviations times 2^KF
+// for f and 2^KG for g: FP16's exact scales; 0 for BF16) and regrouped so that
+// an opposite pair (i, i') costs nine operations past e.u and e.F:
+//   s_i* = om1 s_i + A + B,  s_i'* = om1 s_i' + A - B,  g = 1 - om1 = 1/tau
+//   A = w_i [e.u (4.5 g rho e.u + 9 cf e.F) + g p0 - 3 cf u.F]   (even in e)
+//   B = w_i [3 g rho e.u + 3 cf e.F]                              (odd in e)
+// with p0 = drho - 1.5 rho u^2 and cf = 1 - 1/(2 tau); the moments come from
+// the pair sums s_i + s_i' and differences s_i - s_i'.  collide_node's
+// non-equilibrium grouping costs about twice the operations; the rounding it
+// saves is FP32's, 2^-24 relative, against the 2^-8 (BF16) or 2^-11 (FP16) of
+// the stored result.  Thermal, likewise: s_k* = om1g s_k + w_k (g_g dT + cg Q_B)
+// +- w_k g_g (T / cs_T^2) e.u.
+template <int D, int KF, int KG>
+__device__ __forceinline__ void collide_lean(float* s, float* sg, float fbx, float fby, float fbz, float qb,
+                                             const CollideParams<float>& P) {
+    using L = Lat<D>;
+    constexpr double sf = (double)(1 << KF), sgs = (double)(1 << KG);
+    float drho = s[0], jx = 0.f, jy = 0.f, jz = 0.f;
+    bool fx = true, fy = true, fz = true;
+#pragma unroll
+    for (int i = 1; i < L::Q; i++) {
+        if (!lead_positive<D>(i)) continue;
+        const int io = L::opp(i);
+        const float sum = op_add(s[i], s[io]), dif = op_sub(s[i], s[io]);
+        drho = op_add(drho, sum);
+        if (L::ex(i)) { jx = fx ? (L::ex(i) > 0 ? dif : op_sub(0.f, dif)) : (L::ex(i) > 0 ? op_add(jx, dif) : op_sub(jx, dif)); fx = false; }
+        if (L::ey(i)) { jy = fy ? (L::ey(i) > 0 ? dif : op_sub(0.f, dif)) : (L::ey(i) > 0 ? op_add(jy, dif) : op_sub(jy, dif)); fy = false; }
+        if (L::ez(i)) { jz = fz ? (L::ez(i) > 0 ? dif : op_sub(0.f, dif)) : (L::ez(i) > 0 ? op_add(jz, dif) : op_sub(jz, dif)); fz = false; }
+    }
+    float dT = sg[0];
+#pragma unroll
+    for (int k = 1; k < L::QG; k++) dT = op_add(dT, sg[k]);
+    if (KF != 0) {
+        const float is = (float)(1.0 / sf);  // exact: a power of two
+        drho = op_mul(drho, is);
+        jx = op_mul(jx, is);
+        jy = op_mul(jy, is);
+        jz = op_mul(jz, is);
+    }
+    if (KG != 0) dT = op_mul(dT, (float)(1.0 / sgs));
+    dT = op_fma(0.5f, qb, dT);  // T - T_ref
+    const float Tt = op_add(P.Tref, dT);
+    float Fx = op_add(fbx, P.body[0]), Fy = op_add(fby, P.body[1]), Fz = op_add(fbz, P.body[2]);
+    if (P.buoyancy) {
+        const float fbu = op_mul(P.buoy, dT);
+        if (P.gaxis == 0) Fx = op_add(Fx, fbu);
+        else if (P.gaxis == 1) Fy = op_add(Fy, fbu);
+        else Fz = op_add(Fz, fbu);
+    }
+    const float rho = op_add(1.f, drho);
+    const float inv_rho = op_rcp(rho);
+    const float ux = op_mul(op_fma(0.5f, Fx, jx), inv_rho);
+    const float uy = op_mul(op_fma(0.5f, Fy, jy), inv_rho);
+    const float uz = op_mul(op_fma(0.5f, Fz, jz), inv_rho);
+    const float uu = op_fma(uz, uz, op_fma(uy, uy, op_mul(ux, ux)));
+    const float uF = op_fma(uz, Fz, op_fma(uy, Fy, op_mul(ux, Fx)));
+    const float om1 = P.om1f, g = op_sub(1.f, om1);  // 1/tau, so that g + om1 = 1 in FP32
+    const float p0 = op_fma(-1.5f, op_mul(rho, uu), drho);
+    const float grho = op_mul(g, rho);
+    const float Gq = op_mul(4.5f, grho), Gr = op_mul(3.f, grho);
+    const float P0 = op_fma(g, p0, op_mul(P.m3f, uF));
+    s[0] = op_fma(om1, s[0], op_mul((float)(L::w(0) * sf), P0));
+#pragma unroll
+    for (int i = 1; i < L::Q; i++) {
+        if (!lead_positive<D>(i)) continue;
+        const int io = L::opp(i);
+        // per weight class (the compiler shares these between pairs of one class)
+        const float wsf = (float)(L::w(i) * sf);
+        const float aq = op_mul(wsf, Gq), ar = op_mul(wsf, Gr), ap = op_mul(wsf, P0);
+        const float a9 = op_mul(wsf, P.c9f), a3 = op_mul(wsf, P.c3f);
+        // e.u and e.F, the leading component positive
+        float eu = ux, eF = Fx;
+        if (L::ex(i) == 0) {
+            eu = uy;
+            eF = Fy;
+            if (L::ey(i) == 0) {
+                eu = uz;
+                eF = Fz;
+            } else if (L::ez(i)) {
+                eu = L::ez(i) > 0 ? op_add(eu, uz) : op_sub(eu, uz);
+                eF = L::ez(i) > 0 ? op_add(eF, Fz) : op_sub(eF, Fz);
+            }
+        } else {
+            if (L::ey(i)) {
+                eu = L::ey(i) > 0 ? op_add(eu, uy) : op_sub(eu, uy);
+                eF = L::ey(i) > 0 ? op_add(eF, Fy) : op_sub(eF, Fy);
+            }
+            if (L::ez(i)) {
+                eu = L::ez(i) > 0 ? op_add(eu, uz) : op_sub(eu, uz);
+                eF = L::ez(i) > 0 ? op_add(eF, Fz) : op_sub(eF, Fz);
+            }
+        }
+        const float A = op_fma(eu, op_fma(aq, eu, op_mul(a9, eF)), ap);
+        const float B = op_fma(ar, eu, op_mul(a3, eF));
+        s[i] = op_fma(om1, s[i], op_add(A, B));
+        s[io] = op_fma(om1, s[io], op_sub(A, B));
+    }
+    const float om1g = P.om1g, gg = op_sub(1.f, om1g);
+    const float Ag = op_fma(gg, dT, op_mul(P.cg, qb));
+    const float Bg = op_mul(gg, op_mul(Tt, (float)L::inv_csT2));
+    sg[0] = op_fma(om1g, sg[0], op_mul((float)(L::wg(0) * sgs), Ag));
+#pragma unroll
+    for (int k = 1; k < L::QG; k++) {
+        if (!lead_positive<D>(k)) continue;
+        const int ko = L::opp(k);
+        const float wsg = (float)(L::wg(k) * sgs);
+        const float a = op_mul(wsg, Ag), bw = op_mul(wsg, Bg);
+        const float eu = L::ex(k) ? ux : (L::ey(k) ? uy : uz);
+        const float b = op_mul(bw, eu);
+        sg[k] = op_fma(om1g, sg[k], op_add(a, b));
+        sg[ko] = op_fma(om1g, sg[ko], op_sub(a, b));
+    }
+}
+
+// Loads and stores of the lattice kernel: in physical units (FP32, FP64), or
+// in the storage's own units for the 16-bit forms, which collide_lean takes.
+template <typename S, bool RAW> struct LatIo {
+    using R = typename Store<S>::R;
+    static __device__ __forceinline__ R ldf(S v) { return Store<S>::ldf(v); }
+    static __device__ __forceinline__ R ldg(S v) { return Store<S>::ldg(v); }
+    static __device__ __forceinline__ S stf(R v) { return Store<S>::stf(v); }
+    static __device__ __forceinline__ S stg(R v) { return Store<S>::stg(v); }
+    static __device__ __forceinline__ R gunit(R v) { return v; }  // a physical g value in these units
+};
+template <typename S> struct LatIo<S, true> {
+    static __device__ __forceinline__ float ldf(S v) { return Store<S>::rawf(v); }
+    static __device__ __forceinline__ float ldg(S v) { return Store<S>::rawf(v); }
+    static __device__ __forceinline__ S stf(float v) { return Store<S>::raws(v); }
+    static __device__ __forceinline__ S stg(float v) { return Store<S>::raws(v); }
+    static __device__ __forceinline__ float gunit(float v) {
+        return Store<S>::KG ? op_mul(v, (float)(1 << Store<S>::KG)) : v;
+    }
+};
+
 // Flat offsets of the A-A slots relative to the node index n, per direction
 // (uniform over the grid, computed once on the host): odd-step sources
 // plane opp(i) at n - e_i, odd-step destinations plane i at n + e_i, even-step
@@ -186,7 +329,7 @@ struct AAOffsets {
 // the wall of the later axis (z, then y, then x) decides, as in pop_slot /
 // post_slot.  y and z are uniform across a warp and x only selects, so no warp
 // diverges; interior lanes get the fast path's offsets exactly.
-template <int D, typename S, typename IX>
+template <int D, typename S, typename IX, bool RAW>
 __device__ __forceinline__ void odd_load_face(const Geo& G, const CollideParams<typename Store<S>::R>& P, const S* fn,
                                               const S* gn, int x, int y, int z, const AAOffsets<IX>& O,
                                               typename Store<S>::R* s, typename Store<S>::R* sg) {
@@ -211,16 +354,20 @@ __device__ __forceinline__ void odd_load_face(const Geo& G, const CollideParams<
         if (oy) idx += (IX)ey * sy;
         if (oz) idx += (IX)ez * sz;
         if (face >= 0) idx = O.ld[i];
-        s[i] = Store<S>::ldf(fn[idx]);
+        s[i] = LatIo<S, RAW>::ldf(fn[idx]);
         if (i < L::QG) {
-            R v = Store<S>::ldg(gn[idx]);
-            if (face_iso(G, face)) v = op_sub(P.abb[face], v);
+            R v = LatIo<S, RAW>::ldg(gn[idx]);
+            if constexpr (RAW) {
+                if (face_iso(G, face)) v = op_sub(LatIo<S, RAW>::gunit(P.abb[face]), v);
+            } else {
+                if (face_iso(G, face)) v = op_sub(P.abb[face], v);
+            }
             sg[i < L::QG ? i : 0] = v;
         }
     }
 }
 
-template <int D, typename S, typename IX>
+template <int D, typename S, typename IX, bool RAW>
 __device__ __forceinline__ void odd_store_face(const Geo& G, const CollideParams<typename Store<S>::R>& P, S* fn, S* gn,
                                                int x, int y, int z, const AAOffsets<IX>& O,
                                                const typename Store<S>::R* s, const typename Store<S>::R* sg) {
@@ -245,17 +392,34 @@ __device__ __forceinline__ void odd_store_face(const Geo& G, const CollideParams
         if (oy) idx -= (IX)ey * sy;
         if (oz) idx -= (IX)ez * sz;
         if (face >= 0) idx = O.st[i];
-        fn[idx] = Store<S>::stf(s[i]);
+        fn[idx] = LatIo<S, RAW>::stf(s[i]);
         if (i < L::QG) {
             R v = sg[i < L::QG ? i : 0];
-            if (face_iso(G, face)) v = op_sub(P.abb[face], v);
-            gn[idx] = Store<S>::stg(v);
+            if constexpr (RAW) {
+                if (face_iso(G, face)) v = op_sub(LatIo<S, RAW>::gunit(P.abb[face]), v);
+            } else {
+                if (face_iso(G, face)) v = op_sub(P.abb[face], v);
+            }
+            gn[idx] = LatIo<S, RAW>::stg(v);
         }
     }
 }
 
+// One thread per node.  FP32 and FP64 storage: at most 64 registers for the
+// odd step of FP32 (two 512-thread blocks per SM).  16-bit storage: the node's
+// 26 populations occupy as many registers as in FP32 for half the bytes, so
+// the kernel waits on memory with too few warps resident.  Bounded to 384
+// threads and three blocks of them (56 registers, no spills) and launched in
+// 128-thread blocks, nine blocks (36 warps) fit an SM instead of eight; at
+// 384^3 (BF16) that took the kernel from 1.44 to 1.29 ms.  48 registers spill
+// and lose.
+template <typename S>
+constexpr int sc_max_threads() { return sizeof(S) == 2 ? 384 : 512; }
+template <typename S, int PARITY>
+constexpr int sc_min_blocks() { return sizeof(S) == 2 ? 3 : ((PARITY == 1 && sizeof(S) != 8) ? 2 : 0); }
+
 template <int D, typename S, int PARITY, typename IX>
-__global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) k_stream_collide(Geo G, S* __restrict__ f, S* __restrict__ g,
+__global__ void __launch_bounds__(sc_max_threads<S>(), (sc_min_blocks<S, PARITY>())) k_stream_collide(Geo G, S* __restrict__ f, S* __restrict__ g,
                                                         const typename Store<S>::V4* __restrict__ fb,
                                                         const uint8_t* __restrict__ flags,
                                                         CollideParams<typename Store<S>::R> P, AAOffsets<IX> O) {
@@ -270,6 +434,10 @@ __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) 
     S* const gn = g + n;
     // y and z are uniform across a warp, so this test never splits one
     const bool inner_yz = y > 0 && y < G.ny - 1 && (D == 2 || (z > 0 && z < G.nz - 1));
+    // 16-bit storage collides in its own units (collide_lean); FP32 and FP64 in
+    // physical units with every rounding of collide_node
+    constexpr bool LEAN = sizeof(S) == 2;
+    using IO = LatIo<S, LEAN>;
     R s[L::Q], sg[L::QG];
     // warps holding a node on an x face take the per-lane-select path as a
     // whole (it is exact for interior lanes too), so no warp splits in two;
@@ -278,16 +446,16 @@ __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) 
     const bool xedge = xw == 0 || xw + 31 >= G.nx - 1;
     if (PARITY == 0) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) s[i] = Store<S>::ldf(fn[O.ld[i]]);
+        for (int i = 0; i < L::Q; i++) s[i] = IO::ldf(fn[O.ld[i]]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) sg[k] = Store<S>::ldg(gn[O.ld[k]]);
+        for (int k = 0; k < L::QG; k++) sg[k] = IO::ldg(gn[O.ld[k]]);
     } else if (inner_yz && !xedge) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) s[i] = Store<S>::ldf(fn[O.src[i]]);
+        for (int i = 0; i < L::Q; i++) s[i] = IO::ldf(fn[O.src[i]]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) sg[k] = Store<S>::ldg(gn[O.src[k]]);
+        for (int k = 0; k < L::QG; k++) sg[k] = IO::ldg(gn[O.src[k]]);
     } else {
-        odd_load_face<D, S, IX>(G, P, fn, gn, x, y, z, O, s, sg);
+        odd_load_face<D, S, IX, LEAN>(G, P, fn, gn, x, y, z, O, s, sg);
     }
     R fbx = 0, fby = 0, fbz = 0, qb = 0;
     if (flags[((long long)z * G.ny + y) * G.ntx + (x >> 5)]) {
@@ -297,20 +465,29 @@ __global__ void __launch_bounds__(512, (PARITY == 1 && sizeof(S) != 8) ? 2 : 0) 
         fbz = v.z;
         qb = v.w;
     }
-    collide_node<D, R, R>(s, sg, fbx, fby, fbz, qb, P);
+    if constexpr (LEAN) collide_lean<D, Store<S>::KF, Store<S>::KG>(s, sg, fbx, fby, fbz, qb, P);
+    else collide_node<D, R, R>(s, sg, fbx, fby, fbz, qb, P);
     if (PARITY == 0) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) fn[O.st[i]] = Store<S>::stf(s[i]);
+        for (int i = 0; i < L::Q; i++) fn[O.st[i]] = IO::stf(s[i]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) gn[O.st[k]] = Store<S>::stg(sg[k]);
+        for (int k = 0; k < L::QG; k++) gn[O.st[k]] = IO::stg(sg[k]);
     } else if (inner_yz && !xedge) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) fn[O.dst[i]] = Store<S>::stf(s[i]);
+        for (int i = 0; i < L::Q; i++) fn[O.dst[i]] = IO::stf(s[i]);
 #pragma unroll
-        for (int k = 0; k < L::QG; k++) gn[O.dst[k]] = Store<S>::stg(sg[k]);
+        for (int k = 0; k < L::QG; k++) gn[O.dst[k]] = IO::stg(sg[k]);
     } else {
-        odd_store_face<D, S, IX>(G, P, fn, gn, x, y, z, O, s, sg);
+        odd_store_face<D, S, IX, LEAN>(G, P, fn, gn, x, y, z, O, s, sg);
     }
+}
+
+template <int D, typename S, int PARITY, typename IX>
+static void sc_go(const Ctx* c, cudaStream_t s, dim3 grid, dim3 block, int parity,
+                  const CollideParams<typename Store<S>::R>& P, const AAOffsets<IX>& O) {
+    using V = typename Store<S>::V4;
+    k_stream_collide<D, S, PARITY, IX><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb[parity],
+                                                              c->flags[parity], P, O);
 }
 
 template <typename R>
@@ -358,14 +535,19 @@ static bool narrow_offsets(const Geo& G) {
 
 // Block shape of the lattice kernel: bx threads along x (a multiple of 32) times
 // by rows.  Default: bx = min(the row rounded up to 32, 256) and 256 threads per
-// block for rows of 256 or more nodes, 128 for shorter rows.  With
+// block for rows of 256 or more nodes, 128 for shorter rows and for 16-bit
+// storage (its 56-register bound fits nine 128-thread blocks per SM, four of
+// 256; a block of 16-bit storage has at most 384 threads, larger requests are
+// cut to 384).  With
 // PIBM_TUNE_LATTICE_ROW_TILES = 1, bx is the largest multiple of 32 (at most
 // 256) that divides the row rounded up to 32, so that no block straddles a
 // row end with idle warps (a 384-node row: 192, not 256 + 128).  The tuning
 // knob PIBM_TUNE_LATTICE_THREADS sets the threads per block (32 .. 512).
 static void lattice_shape(const Ctx* c, dim3& block, dim3& grid) {
     const int w32 = (c->G.nx + 31) / 32 * 32;
-    const int threads = c->tune_lattice_threads > 0 ? c->tune_lattice_threads : (w32 >= 256 ? 256 : 128);
+    const bool st16 = c->desc.storage == PIBM_STORE_F16 || c->desc.storage == PIBM_STORE_BF16;
+    int threads = c->tune_lattice_threads > 0 ? c->tune_lattice_threads : (w32 >= 256 && !st16 ? 256 : 128);
+    if (st16 && threads > sc_max_threads<__half>()) threads = sc_max_threads<__half>();
     int bx = w32 < threads ? w32 : (threads < 256 ? threads : 256);
     if (c->tune_lattice_row_tiles) {
         int best = 32;
@@ -384,19 +566,14 @@ static cudaError_t sc_launch(Ctx* c, cudaStream_t s, int parity) {
     lattice_shape(c, block, grid);
     using R = typename Store<S>::R;
     CollideParams<R> P = collide_params<R>(c);
-    using V = typename Store<S>::V4;
     if (narrow_offsets<D>(c->G) && !c->tune_wide_index) {
         const AAOffsets<int> O = aa_offsets<D, int>(c->G);
-        if (parity == 0)
-            k_stream_collide<D, S, 0, int><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb[parity], c->flags[parity], P, O);
-        else
-            k_stream_collide<D, S, 1, int><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb[parity], c->flags[parity], P, O);
+        if (parity == 0) sc_go<D, S, 0, int>(c, s, grid, block, parity, P, O);
+        else sc_go<D, S, 1, int>(c, s, grid, block, parity, P, O);
     } else {
         const AAOffsets<long long> O = aa_offsets<D, long long>(c->G);
-        if (parity == 0)
-            k_stream_collide<D, S, 0, long long><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb[parity], c->flags[parity], P, O);
-        else
-            k_stream_collide<D, S, 1, long long><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb[parity], c->flags[parity], P, O);
+        if (parity == 0) sc_go<D, S, 0, long long>(c, s, grid, block, parity, P, O);
+        else sc_go<D, S, 1, long long>(c, s, grid, block, parity, P, O);
     }
     return cudaGetLastError();
 }

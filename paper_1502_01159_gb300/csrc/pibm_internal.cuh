@@ -75,9 +75,12 @@ template <> struct Vec4<double> { using T = double4_32a; };
 // of two (exact), so that deviations of order 1e-4 .. 1e-1 sit in the normal
 // FP16 range (flow x 1024, thermal x 256); BF16 keeps FP32's exponent range
 // and needs no scale.  All collision arithmetic is in R = FP32 for both.
+// rawf / raws convert without the scale: the 16-bit lattice kernel collides in
+// the storage's own units (deviations times 2^KF for f, 2^KG for g).
 template <typename S> struct Store {
     using R = S;
     using V4 = typename Vec4<S>::T;
+    static constexpr int KF = 0, KG = 0;
     static __host__ __device__ __forceinline__ R ldf(S v) { return v; }
     static __host__ __device__ __forceinline__ R ldg(S v) { return v; }
     static __host__ __device__ __forceinline__ S stf(R v) { return v; }
@@ -90,6 +93,9 @@ template <> struct Store<__half> {
     static __device__ __forceinline__ float ldg(__half v) { return __half2float(v) * 0.00390625f; }
     static __device__ __forceinline__ __half stf(float v) { return __float2half_rn(v * 1024.0f); }
     static __device__ __forceinline__ __half stg(float v) { return __float2half_rn(v * 256.0f); }
+    static constexpr int KF = 10, KG = 8;
+    static __device__ __forceinline__ float rawf(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half raws(float v) { return __float2half_rn(v); }
 };
 template <> struct Store<__nv_bfloat16> {
     using R = float;
@@ -98,6 +104,9 @@ template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ float ldg(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ __nv_bfloat16 stf(float v) { return __float2bfloat16_rn(v); }
     static __device__ __forceinline__ __nv_bfloat16 stg(float v) { return __float2bfloat16_rn(v); }
+    static constexpr int KF = 0, KG = 0;
+    static __device__ __forceinline__ float rawf(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 raws(float v) { return __float2bfloat16_rn(v); }
 };
 
 // Run FN<D, S>(args...) for the context's dimension and storage type.
