@@ -261,10 +261,14 @@ pibm_status pibm_set_particle_model(pibm_ctx* ctx, int model);
  * sums regroup (FP32 rounding of their partial sums).
  * PIBM_TUNE_COUPLING_ORDER: 1 (default) = the footprint and spread blocks
  * take the particles in the spatial order of the DEM's cell list; 0 = in
- * index order (identical results). */
+ * index order (identical results).
+ * PIBM_TUNE_LATTICE_PAIRS: 1 (default) = the even (own-slot) step of FP16 /
+ * BF16 storage updates two x-adjacent nodes per thread with 32-bit accesses
+ * when the row length is even (blocks of PIBM_TUNE_LATTICE_THREADS threads
+ * over the row's node pairs); 0 = one node per thread (identical results). */
 enum { PIBM_TUNE_DEM_PARTICLES_PER_CTA = 0, PIBM_TUNE_LATTICE_ROW_TILES = 1, PIBM_TUNE_LATTICE_THREADS = 2,
        PIBM_TUNE_WIDE_INDEX = 3, PIBM_TUNE_TC_WAIT_POLLS = 4, PIBM_TUNE_COUPLING_THREADS = 5,
-       PIBM_TUNE_COUPLING_ORDER = 6 };
+       PIBM_TUNE_COUPLING_ORDER = 6, PIBM_TUNE_LATTICE_PAIRS = 7 };
 pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value);
 
 /* Number of kernels one lattice step launches (for launch accounting). */

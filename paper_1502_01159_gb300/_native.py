@@ -18,7 +18,7 @@ ADIABATIC, ISOTHERMAL = 0, 1
 SPRING_DASHPOT, HERTZ_MD, HERTZ_MD_HIST = 0, 1, 2
 STORE_F32, STORE_F64, STORE_F16, STORE_BF16 = 0, 1, 2, 3
 (TUNE_DEM_PARTICLES_PER_CTA, TUNE_LATTICE_ROW_TILES, TUNE_LATTICE_THREADS, TUNE_WIDE_INDEX, TUNE_TC_WAIT_POLLS,
- TUNE_COUPLING_THREADS, TUNE_COUPLING_ORDER) = range(7)
+ TUNE_COUPLING_THREADS, TUNE_COUPLING_ORDER, TUNE_LATTICE_PAIRS) = range(8)
 STORAGE = {"f32": STORE_F32, "f64": STORE_F64, "f16": STORE_F16, "bf16": STORE_BF16}
 FIELDS = {"rho": 0, "ux": 1, "uy": 2, "uz": 3, "T": 4, "FBx": 5, "FBy": 6, "FBz": 7, "QB": 8}
 

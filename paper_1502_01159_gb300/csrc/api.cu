@@ -280,6 +280,7 @@ pibm_status pibm_create(const pibm_desc* d, void* stream, const pibm_allocator* 
     c.lat = c.D == 2 ? 2 : (d->flow_q == 15 ? 4 : 3);
     c.sg.wait_polls = 1 << 22;
     c.tune_coupling_order = 1;
+    c.tune_lattice_pairs = 1;
     c.Q = c.D == 2 ? 9 : (c.lat == 4 ? 15 : 19);
     c.QG = c.D == 2 ? 5 : 7;
     c.G.nx = d->nx, c.G.ny = d->ny, c.G.nz = d->nz;
@@ -948,6 +949,12 @@ pibm_status pibm_set_tuning(pibm_ctx* ctx, int knob, int value) {
         if (value != 0 && (value < 64 || value > 256 || value % 32 != 0))
             return fail(ctx, PIBM_ERR_ARG, "coupling threads per block: 0 or a multiple of 32 in [64, 256]");
         c.tune_coupling_threads = value;
+        drop_graphs(c);
+        return PIBM_OK;
+    }
+    if (knob == PIBM_TUNE_LATTICE_PAIRS) {
+        if (value != 0 && value != 1) return fail(ctx, PIBM_ERR_ARG, "invalid tuning value");
+        c.tune_lattice_pairs = value;
         drop_graphs(c);
         return PIBM_OK;
     }

@@ -482,10 +482,133 @@ __global__ void __launch_bounds__(sc_max_threads<S>(), (sc_min_blocks<S, PARITY>
     }
 }
 
+// Two 16-bit values of x-adjacent nodes in one 32-bit word (the lower x in
+// the low half): the storage-unit values and the round-to-nearest packing of
+// two of them, bit for bit what the one-node path loads and stores.
+template <typename S> struct Pair16;
+template <> struct Pair16<__nv_bfloat16> {
+    static __device__ __forceinline__ float lo(uint32_t w) { return __uint_as_float(w << 16); }
+    static __device__ __forceinline__ float hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+    static __device__ __forceinline__ uint32_t pack(float a, float b) {
+        const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const uint32_t*>(&v);
+    }
+};
+template <> struct Pair16<__half> {
+    static __device__ __forceinline__ float lo(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
+    static __device__ __forceinline__ float hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+    static __device__ __forceinline__ uint32_t pack(float a, float b) {
+        const __half2 v = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const uint32_t*>(&v);
+    }
+};
+
+// The even (own-slot) step of 16-bit storage with two x-adjacent nodes per
+// thread: one 32-bit load and one 32-bit store per population and node pair
+// instead of two 16-bit ones, and twice the bytes in flight per warp.  The
+// even step has no face logic (every node reads and writes its own slots), so
+// the pair needs none either.  Needs an even row length (then n and every
+// plane offset i N are even: 4-byte aligned words).  Each node goes through
+// collide_lean as in the one-node kernel, so the results are identical.  The
+// first node's results wait as packed pairs of directions while the second
+// node collides; byte permutes then form the (first, second) words.
+// At most 72 registers (24-56 bytes of spills; 98 unbounded): at 384^3 BF16,
+// one node per thread 1.323 ms per lattice step (mean of both parities), node
+// pairs 1.303 / 1.254 / 1.281 ms at 64 / 72 / 80 registers, 1.41 unbounded
+// (128-thread blocks of 128 pairs).
+#ifndef PIBM_EVEN2_REGS
+#define PIBM_EVEN2_REGS 72
+#endif
+template <int D, typename S, typename IX>
+__global__ void __maxnreg__(PIBM_EVEN2_REGS) k_stream_collide_even2(Geo G, S* __restrict__ f, S* __restrict__ g,
+                                                             const float4* __restrict__ fb,
+                                                             const uint8_t* __restrict__ flags,
+                                                             CollideParams<float> P, AAOffsets<IX> O) {
+    using L = Lat<D>;
+    using W = Pair16<S>;
+    constexpr int QP = (L::Q + 1) / 2, QGP = (L::QG + 1) / 2;
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+    if (x >= G.nx || y >= G.ny) return;
+    const long long n = node_index(G, x, y, z);
+    S* const fn = f + n;
+    S* const gn = g + n;
+    uint32_t wf[L::Q], wg[L::QG];
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) wf[i] = *reinterpret_cast<const uint32_t*>(fn + O.ld[i]);
+#pragma unroll
+    for (int k = 0; k < L::QG; k++) wg[k] = *reinterpret_cast<const uint32_t*>(gn + O.ld[k]);
+    // x and x + 1 share a 32-node tile (x is even)
+    const bool flagged = flags[((long long)z * G.ny + y) * G.ntx + (x >> 5)] != 0;
+    float s[L::Q], sg[L::QG];
+    uint32_t pf[QP], pg[QGP];
+    {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (flagged) v = fb[n];
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) s[i] = W::lo(wf[i]);
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) sg[k] = W::lo(wg[k]);
+        collide_lean<D, Store<S>::KF, Store<S>::KG>(s, sg, v.x, v.y, v.z, v.w, P);
+#pragma unroll
+        for (int j = 0; j < QP; j++) pf[j] = W::pack(s[2 * j], 2 * j + 1 < L::Q ? s[2 * j + 1] : 0.f);
+#pragma unroll
+        for (int j = 0; j < QGP; j++) pg[j] = W::pack(sg[2 * j], 2 * j + 1 < L::QG ? sg[2 * j + 1] : 0.f);
+    }
+    {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (flagged) v = fb[n + 1];
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) s[i] = W::hi(wf[i]);
+#pragma unroll
+        for (int k = 0; k < L::QG; k++) sg[k] = W::hi(wg[k]);
+        collide_lean<D, Store<S>::KF, Store<S>::KG>(s, sg, v.x, v.y, v.z, v.w, P);
+    }
+#pragma unroll
+    for (int j = 0; j < QP; j++) {
+        const uint32_t q = W::pack(s[2 * j], 2 * j + 1 < L::Q ? s[2 * j + 1] : 0.f);
+        *reinterpret_cast<uint32_t*>(fn + O.st[2 * j]) = __byte_perm(pf[j], q, 0x5410);
+        if (2 * j + 1 < L::Q) *reinterpret_cast<uint32_t*>(fn + O.st[2 * j + 1]) = __byte_perm(pf[j], q, 0x7632);
+    }
+#pragma unroll
+    for (int j = 0; j < QGP; j++) {
+        const uint32_t q = W::pack(sg[2 * j], 2 * j + 1 < L::QG ? sg[2 * j + 1] : 0.f);
+        *reinterpret_cast<uint32_t*>(gn + O.st[2 * j]) = __byte_perm(pg[j], q, 0x5410);
+        if (2 * j + 1 < L::QG) *reinterpret_cast<uint32_t*>(gn + O.st[2 * j + 1]) = __byte_perm(pg[j], q, 0x7632);
+    }
+}
+
+// The node-pair form applies: 16-bit storage, an even step, an even row
+// length, and the tuning knob on.
+template <typename S>
+static bool even_pairs(const Ctx* c, int parity) {
+    return sizeof(S) == 2 && parity == 0 && c->G.nx % 2 == 0 && c->tune_lattice_pairs;
+}
+
 template <int D, typename S, int PARITY, typename IX>
 static void sc_go(const Ctx* c, cudaStream_t s, dim3 grid, dim3 block, int parity,
                   const CollideParams<typename Store<S>::R>& P, const AAOffsets<IX>& O) {
     using V = typename Store<S>::V4;
+    if constexpr (sizeof(S) == 2 && PARITY == 0) {
+        if (even_pairs<S>(c, parity)) {
+            // the same threads per block over the node pairs, in blocks that
+            // span the widest multiple of 32 pairs dividing both the row's
+            // pairs rounded up to 32 and the threads (no idle tail warps: at
+            // 384^3, 64 x 2 blocks; 128 x 1 left a quarter of every second
+            // block idle and measured 2 % slower over both parities)
+            const int pairs = c->G.nx / 2, p32 = (pairs + 31) / 32 * 32;
+            const int threads = (int)(block.x * block.y);
+            const int cap = (int)block.x < p32 ? (int)block.x : p32;
+            int bx = 32;
+            for (int cand = 32; cand <= cap; cand += 32)
+                if (p32 % cand == 0 && threads % cand == 0) bx = cand;
+            const int by = threads / bx;
+            const dim3 b2(bx, by, 1), g2((pairs + bx - 1) / bx, (c->G.ny + by - 1) / by, grid.z);
+            k_stream_collide_even2<D, S, IX><<<g2, b2, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb[parity],
+                                                                c->flags[parity], P, O);
+            return;
+        }
+    }
     k_stream_collide<D, S, PARITY, IX><<<grid, block, 0, s>>>(c->G, (S*)c->f, (S*)c->g, (const V*)c->fb[parity],
                                                               c->flags[parity], P, O);
 }

@@ -350,6 +350,7 @@ struct Ctx {
     int tune_coupling_order;         // 1 (default): coupling blocks take the particles in cell-list order
     int tune_lattice_threads;        // 0: default block shape; else threads per lattice block
     int tune_wide_index;             // 1: 64-bit slot offsets in the lattice kernel even where 32-bit suffice
+    int tune_lattice_pairs;          // 1 (default): two nodes per thread in the even step of 16-bit storage
     int dem_attr_ok;                 // bit per DEM kernel variant (dimension, law) whose launch attributes are set
     int spread_smem;                 // shared memory per CTA of the spread kernel (from the largest radius)
     double rmax;                     // largest particle radius

@@ -69,3 +69,29 @@ def test_missing_library_fails_loudly(tmp_path):
             _native.load(str(tmp_path / "libpibm.so"))
         finally:
             _native._lib = _native._lib_saved
+
+
+def test_binding_constants_match_header_enums():
+    # every PIBM_* enumerator of the header has the value the binding uses
+    from paper_1502_01159_gb300 import _native
+    src = open(os.path.join(ROOT, "include", "pibm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    values = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+        nxt = 0
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            name, _, val = item.partition("=")
+            name = name.strip()
+            nxt = int(val.strip(), 0) if val.strip() else nxt
+            values[name] = nxt
+            nxt += 1
+    tunes = {k: v for k, v in values.items() if k.startswith("PIBM_TUNE_")}
+    assert "PIBM_TUNE_LATTICE_PAIRS" in tunes
+    for name, v in tunes.items():
+        assert getattr(_native, name[len("PIBM_"):]) == v, name
+    for name in ("PIBM_STORE_F32", "PIBM_STORE_F64", "PIBM_STORE_F16", "PIBM_STORE_BF16", "PIBM_HERTZ_MD_HIST"):
+        if name in values:
+            assert getattr(_native, name[len("PIBM_"):]) == values[name], name

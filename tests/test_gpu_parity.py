@@ -399,14 +399,15 @@ def _tiling_cases():
 def test_lattice_block_shapes_agree(storage, ci):
     from paper_1502_01159_gb300 import TUNE_LATTICE_ROW_TILES, TUNE_LATTICE_THREADS
     # the collide-and-stream kernel with its default blocks, one-warp blocks,
-    # 96-thread blocks that divide the row and row-dividing default blocks:
-    # every node is updated once by the same arithmetic, so the populations
-    # agree bit for bit after every step, both parities
+    # 96-thread blocks that divide the row, row-dividing default blocks and
+    # 512-thread blocks (cut to 384 for 16-bit storage, whose kernel is bounded
+    # to 384 threads): every node is updated once by the same arithmetic, so the
+    # populations agree bit for bit after every step, both parities
     case = _tiling_cases()[ci]
     case["storage"] = storage
     f, g = W.random_populations(case, amp=0.02, config_index=9)
     sims = []
-    for threads, rowtiles in ((0, 0), (32, 0), (96, 1), (0, 1)):
+    for threads, rowtiles in ((0, 0), (32, 0), (96, 1), (0, 1), (512, 0)):
         s = _sim(case)
         s.set_tuning(TUNE_LATTICE_THREADS, threads)
         s.set_tuning(TUNE_LATTICE_ROW_TILES, rowtiles)
@@ -424,7 +425,36 @@ def test_lattice_block_shapes_agree(storage, ci):
         assert s.diagnostics()["nonfinite"] == 0
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("ci", range(8))
+def test_even_step_node_pairs_agree(storage, ci):
+    from paper_1502_01159_gb300 import TUNE_LATTICE_PAIRS, TUNE_LATTICE_THREADS
+    # the even step of 16-bit storage with two nodes per thread (32-bit words)
+    # and with one: the same per-node arithmetic, so the populations agree bit
+    # for bit after every step; rows of odd length take the one-node kernel
+    case = _tiling_cases()[ci]
+    case["storage"] = storage
+    f, g = W.random_populations(case, amp=0.02, config_index=9)
+    sims = []
+    for pairs, threads in ((1, 0), (0, 0), (1, 32), (1, 384)):
+        s = _sim(case)
+        s.set_tuning(TUNE_LATTICE_PAIRS, pairs)
+        s.set_tuning(TUNE_LATTICE_THREADS, threads)
+        s.set_populations(f.ravel(), g.ravel())
+        sims.append(s)
+    for k in (1, 1, 1, 17):
+        for s in sims:
+            s.step(k)
+        fa, ga = sims[0].read_populations()
+        for other in sims[1:]:
+            fb_, gb_ = other.read_populations()
+            assert np.array_equal(fa, fb_), (storage, case["shape"], k, np.argwhere(fa != fb_)[:5])
+            assert np.array_equal(ga, gb_), (storage, case["shape"], k, np.argwhere(ga != gb_)[:5])
+    for s in sims:
+        assert s.diagnostics()["nonfinite"] == 0
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("ci", range(4))
 def test_wide_and_narrow_slot_offsets_agree(storage, ci):
     from paper_1502_01159_gb300 import TUNE_WIDE_INDEX
