@@ -512,15 +512,20 @@ template <> struct Pair16<__half> {
 // collide_lean as in the one-node kernel, so the results are identical.  The
 // first node's results wait as packed pairs of directions while the second
 // node collides; byte permutes then form the (first, second) words.
-// At most 72 registers (24-56 bytes of spills; 98 unbounded): at 384^3 BF16,
+// At most 72 registers for BF16 (24 bytes of spills; 98 unbounded): at 384^3,
 // one node per thread 1.323 ms per lattice step (mean of both parities), node
 // pairs 1.303 / 1.254 / 1.281 ms at 64 / 72 / 80 registers, 1.41 unbounded
-// (128-thread blocks of 128 pairs).
+// (128-thread blocks of 128 pairs).  FP16 at most 80 (no spills; at 72 it
+// spilled 52 bytes): 1.245 ms against 1.301 at 72.
 #ifndef PIBM_EVEN2_REGS
 #define PIBM_EVEN2_REGS 72
 #endif
+#ifndef PIBM_EVEN2_REGS_F16
+#define PIBM_EVEN2_REGS_F16 80
+#endif
 template <int D, typename S, typename IX>
-__global__ void __maxnreg__(PIBM_EVEN2_REGS) k_stream_collide_even2(Geo G, S* __restrict__ f, S* __restrict__ g,
+__global__ void __maxnreg__((std::is_same<S, __half>::value ? PIBM_EVEN2_REGS_F16 : PIBM_EVEN2_REGS))
+    k_stream_collide_even2(Geo G, S* __restrict__ f, S* __restrict__ g,
                                                              const float4* __restrict__ fb,
                                                              const uint8_t* __restrict__ flags,
                                                              CollideParams<float> P, AAOffsets<IX> O) {
