@@ -311,6 +311,33 @@ def test_full_size_sed3d384_parity():
     sim.close()
 
 
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_full_size_sed3d384_node_pairs_agree(storage):
+    """The headline workload at full size with 16-bit storage, in the bench's
+    launch configuration: the even step's node-pair kernel (the default) and
+    one node per thread update every node with the same arithmetic, so after
+    four steps (both parities twice, with the coupling and the DEM between them)
+    the fields and the particle states agree bit for bit."""
+    from paper_1502_01159_gb300 import TUNE_LATTICE_PAIRS
+    heat_cap = 1.2 * 4.0 / 3.0 * np.pi * 27.0
+    case = W.sed3d(nx=384, ny=384, nz=384, n_p=10000, d=6.0, config_index=4, heat_cap=heat_cap, T_p_random=True)
+    case["storage"] = storage
+    a = _sim(case)
+    b = _sim(case)
+    b.set_tuning(TUNE_LATTICE_PAIRS, 0)
+    a.step(4)
+    b.step(4)
+    for name in ("rho", "T", "ux", "uy", "uz", "FBz", "QB"):
+        fa, fb_ = a.read_field(name), b.read_field(name)
+        assert np.array_equal(fa, fb_), (storage, name, np.argwhere(fa != fb_)[:5])
+    pa, pb = a.read_particles(), b.read_particles()
+    for key in ("X", "U", "W", "T_p"):
+        assert np.array_equal(pa[key], pb[key]), (storage, key)
+    assert a.diagnostics()["nonfinite"] == 0
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_footprint_ownership_ties(dim):
     # Particles placed mirror-symmetrically about the node plane x = 13: nodes on
